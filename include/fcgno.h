@@ -1,0 +1,155 @@
+/*
+ * fcgno.h - C ABI of the GB300 FCG-NO library.
+ *
+ * The library runs the flexible conjugate gradient method of Algorithm 1 (Section 2.3 of
+ * Rudikov et al., "Neural operators meet conjugate gradients: the FCG-NO method",
+ * arXiv 2402.05598), preconditioned by a Fourier neural operator (Section 2.4.2,
+ * Appendix A), on the 5-point finite-volume discretisation of -div(k grad u) = f on the
+ * unit square with zero Dirichlet data (Eq. (1)-(2)).
+ *
+ * Conventions shared by every call
+ *  - Grid: N x N interior nodes, h = 1/(N+1), node (p, q) at ((p+1)h, (q+1)h). A field is
+ *    a contiguous row-major double array [N][N] indexed [q][p] (p fastest); a batch of B
+ *    instances is [B][N][N]. Face coefficients are harmonic means of neighbouring k, a
+ *    boundary face takes the k of its node; the operator includes the 1/h^2 factor.
+ *  - Pointers are DEVICE pointers owned by the caller unless a parameter says "host".
+ *    The library never frees caller memory. Handles (fcgno_op_t, fcgno_model_t) are owned
+ *    by the library and released with their destroy call.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream). Calls are
+ *    asynchronous on that stream except where stated.
+ *  - No C++ exception crosses this boundary. Argument errors return FCGNO_EINVAL before
+ *    any launch; CUDA failures return FCGNO_ECUDA (fcgno_last_error() gives the text).
+ *  - Per-instance solve outcomes are reported in fcgno_solve_info[b].status.
+ *  - Every computation runs in CUDA kernels of this library (sm_103a); there is no host
+ *    fallback.
+ */
+#ifndef FCGNO_H
+#define FCGNO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  FCGNO_OK = 0,
+  FCGNO_EINVAL = 1,     /* bad argument (checked before any launch)                      */
+  FCGNO_ENOMEM = 2,     /* device allocation failed                                        */
+  FCGNO_ECUDA = 3,      /* a CUDA call or kernel failed                                    */
+  FCGNO_ENOCONV = 4,    /* instance status: max_iter reached before tol                    */
+  FCGNO_EBREAKDOWN = 5, /* instance status: (p_i, s_i) zero or non-finite (Algorithm 1)    */
+  FCGNO_ETIMEOUT = 6    /* a bounded device wait gave up (kernel returned an error flag)   */
+} fcgno_status;
+
+typedef enum {
+  FCGNO_FP64 = 0, /* preconditioner computed in FP64 on CUDA cores                         */
+  FCGNO_BF16 = 1, /* preconditioner GEMMs in BF16 on tcgen05 tensor cores, FP32 accumulate */
+  FCGNO_FP16 = 2, /* as BF16 with FP16 operands                                            */
+  FCGNO_FP32 = 3  /* preconditioner computed in FP32 on CUDA cores                         */
+} fcgno_prec;
+
+typedef struct fcgno_op* fcgno_op_t;
+typedef struct fcgno_model* fcgno_model_t;
+
+/* Shape of the Fourier neural operator (Appendix A: encoder, `layers` Fourier layers,
+ * decoder). modes = M keeps x1-frequencies 0..M-1 and -M..-1 and x2-frequencies 0..M-1;
+ * requires N >= 2M for every grid it is applied to. in_channels must be 2. */
+typedef struct {
+  int width;       /* C   */
+  int layers;      /* L   */
+  int modes;       /* M   */
+  int proj_width;  /* C_p */
+  int in_channels; /* 2: (r / rms(r), log k) */
+} fcgno_model_desc;
+
+typedef struct {
+  double tol;      /* stop instance b when ||r_i|| <= tol * ||r_0|| (Table 1 criterion)    */
+  int m_max;       /* truncation m_max of Algorithm 1, 1 <= m_max <= 8                       */
+  int max_iter;    /* iteration cap                                                          */
+  int fixed_iters; /* nonzero: ignore tol and run exactly max_iter iterations                */
+  int check_every; /* host reads the convergence counter every this many iterations (>=1)  */
+} fcgno_solve_opts;
+
+typedef struct {
+  int32_t iters;   /* iterations performed                                                   */
+  int32_t status;  /* FCGNO_OK (converged), FCGNO_ENOCONV or FCGNO_EBREAKDOWN                */
+  double relres;   /* ||r_iters|| / ||r_0|| on the recursively updated residual              */
+  double r0norm;   /* ||r_0||                                                                */
+} fcgno_solve_info;
+
+/* Stencil assembly (Eq. (1)-(2)): k is [batch][N][N] (k > 0). Builds the face
+ * coefficients and log k on the device and returns a handle that owns them.
+ * Errors: EINVAL if N < 2, batch < 1, k or out NULL; ENOMEM; ECUDA. */
+fcgno_status fcgno_assemble(int N, int batch, const double* k, void* stream, fcgno_op_t* out);
+fcgno_status fcgno_op_destroy(fcgno_op_t op);
+/* y = A x for every instance (x, y: [batch][N][N], may not alias). */
+fcgno_status fcgno_apply_A(fcgno_op_t op, const double* x, double* y, void* stream);
+
+/* Neural operator handle. `weights` is a DEVICE float32 blob of fcgno_weight_count(desc)
+ * elements in this order (row-major): lift_w [C][2], lift_b [C]; per layer l: w_l [C][C]
+ * (out, in), b_l [C], r_l [2M][M][C][C][2] (x1-mode slot j -> frequency j or j-2M, x2-mode,
+ * in, out, re/im); proj1_w [Cp][C], proj1_b [Cp], proj2_w [Cp], proj2_b [1].
+ * The handle keeps the pointer (caller keeps the blob alive) and derives reduced-precision
+ * copies from it; call fcgno_model_sync after the blob changes. */
+size_t fcgno_weight_count(const fcgno_model_desc* desc);
+fcgno_status fcgno_model_create(const fcgno_model_desc* desc, const float* weights, void* stream,
+                                fcgno_model_t* out);
+fcgno_status fcgno_model_sync(fcgno_model_t model, void* stream);
+fcgno_status fcgno_model_destroy(fcgno_model_t model);
+
+/* z = NO(r, log k) for every instance of op (Algorithm 1, w_i = B(r_i); Appendix A):
+ * z = rms(r) * decoder(Fourier layers(encoder(r / rms(r), log k))), z = 0 where r = 0.
+ * r, z: [batch][N][N]. prec selects the arithmetic (FP64, FP32, BF16, FP16).
+ * Errors: EINVAL if N < 2*modes or the precision is unsupported. */
+fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, const double* r, double* z,
+                                 fcgno_prec prec, void* stream);
+
+/* Algorithm 1 for every instance of A: x holds u_0 on entry and the iterate on exit;
+ * b is [batch][N][N]; Bpc NULL runs the identity preconditioner (plain CG for m_max = 1).
+ * info is a HOST array of batch entries. Synchronises on `stream` every check_every
+ * iterations and at exit (the call returns when every instance has stopped).
+ * Errors: EINVAL for bad opts (tol < 0, m_max outside 1..8, max_iter < 0). */
+fcgno_status fcgno_solve(fcgno_op_t A, fcgno_model_t Bpc, const double* b, double* x,
+                         const fcgno_solve_opts* opts, fcgno_prec prec, fcgno_solve_info* info,
+                         void* stream);
+
+/* End-to-end variant of fcgno_solve on HOST buffers: k_host, b_host, x_host are
+ * [batch][N][N] host arrays (pinned memory gives the fastest copies). Copies k, b, x in,
+ * assembles, solves, copies x out; info is a host array. Synchronous. */
+fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const double* b_host,
+                              double* x_host, fcgno_model_t Bpc, const fcgno_solve_opts* opts,
+                              fcgno_prec prec, fcgno_solve_info* info, void* stream);
+
+/* Krylov-subspace sampling (Eq. (9), Section 3.1): runs K iterations of CG (Algorithm 1
+ * with B = I, m_max = 1) from x0 on every instance and stores, for i = 1..K, the
+ * residual r_i and the error e_i = u_star - u_i:
+ * r_out, e_out are [K][batch][N][N]; u_star is [batch][N][N] (the converged solution).
+ * Rows after an instance has converged repeat its last iterate. info: host array. */
+fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x0,
+                                  const double* u_star, int K, double* r_out, double* e_out,
+                                  fcgno_solve_info* info, void* stream);
+
+/* One training step on the energy-norm loss of Eq. (11):
+ * loss = mean_b ||z_b - e_b||_A / ||e_b||_A with z_b = NO(r_b, log k_b), and its gradient
+ * with respect to every weight of the blob. r, e: [batch][N][N] (batch = op's batch).
+ * loss: device float scalar; grad: device float blob (same layout as the weights), both
+ * overwritten. prec: FCGNO_FP32 (forward/backward on CUDA cores, FP32) or FCGNO_FP64.
+ * Uses the FP32 master blob given to fcgno_model_create. */
+fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
+                              int batch, fcgno_prec prec, float* loss, float* grad, void* stream);
+
+/* Device bytes fcgno_solve needs for one op of this shape (operator, Krylov state and the
+ * preconditioner's activations), for admission against an HBM budget. */
+size_t fcgno_workspace_bytes(int N, int batch, int m_max, const fcgno_model_desc* desc, fcgno_prec prec);
+
+const char* fcgno_status_str(fcgno_status s);
+const char* fcgno_last_error(void);
+/* Number of CUDA kernels this library has launched since load (all threads). */
+uint64_t fcgno_launch_count(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FCGNO_H */

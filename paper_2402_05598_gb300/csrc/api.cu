@@ -1,0 +1,206 @@
+// Handle management and the remaining C-ABI entry points.
+#include "internal.cuh"
+
+#include <mutex>
+#include <string>
+
+namespace fcgno {
+
+std::atomic<uint64_t> g_launches{0};
+static thread_local std::string t_last_error;
+
+void set_last_error(const std::string& msg) { t_last_error = msg; }
+
+void solver_ws_free(fcgno_op* op);
+
+BlobLayout blob_layout(const fcgno_model_desc& d) {
+  BlobLayout L{};
+  const size_t C = d.width, Cp = d.proj_width, M = d.modes, ci = d.in_channels;
+  size_t pos = 0;
+  L.lift_w = pos;
+  pos += C * ci;
+  L.lift_b = pos;
+  pos += C;
+  for (int l = 0; l < d.layers; ++l) {
+    L.w[l] = pos;
+    pos += C * C;
+    L.b[l] = pos;
+    pos += C;
+    L.r[l] = pos;
+    pos += 2 * M * M * C * C * 2;
+  }
+  L.proj1_w = pos;
+  pos += Cp * C;
+  L.proj1_b = pos;
+  pos += Cp;
+  L.proj2_w = pos;
+  pos += Cp;
+  L.proj2_b = pos;
+  pos += 1;
+  L.total = pos;
+  return L;
+}
+
+__global__ void widen_kernel(size_t n, const float* __restrict__ in, double* __restrict__ out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+
+static bool desc_ok(const fcgno_model_desc* d) {
+  return d && d->width >= 1 && d->width <= 64 && d->layers >= 1 && d->layers <= 16 && d->modes >= 1 &&
+         d->modes <= 16 && d->proj_width >= 1 && d->proj_width <= 64 && d->in_channels == 2;
+}
+
+}  // namespace fcgno
+
+using namespace fcgno;
+
+extern "C" size_t fcgno_weight_count(const fcgno_model_desc* desc) {
+  if (!desc_ok(desc)) return 0;
+  return blob_layout(*desc).total;
+}
+
+extern "C" fcgno_status fcgno_model_sync(fcgno_model_t m, void* stream) {
+  if (!m) {
+    set_last_error("fcgno_model_sync: null model");
+    return FCGNO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  widen_kernel<<<ceil_div(m->count, 256), 256, 0, st>>>(m->count, m->w32, m->w64);
+  FCGNO_LAUNCHED();
+  return tc_model_sync(m, st);
+}
+
+extern "C" fcgno_status fcgno_model_create(const fcgno_model_desc* desc, const float* weights, void* stream,
+                                           fcgno_model_t* out) {
+  if (!out || !weights || !desc_ok(desc)) {
+    set_last_error("fcgno_model_create: need width, proj_width in 1..64, layers in 1..16, modes in 1..16, "
+                   "in_channels == 2 and non-null weights/out");
+    return FCGNO_EINVAL;
+  }
+  *out = nullptr;
+  fcgno_model* m = new fcgno_model();
+  m->desc = *desc;
+  m->w32 = weights;
+  m->count = blob_layout(*desc).total;
+  if (cudaMalloc(&m->w64, m->count * sizeof(double)) != cudaSuccess) {
+    cudaGetLastError();
+    delete m;
+    set_last_error("fcgno_model_create: out of device memory");
+    return FCGNO_ENOMEM;
+  }
+  fcgno_status rc = fcgno_model_sync(m, stream);
+  if (rc != FCGNO_OK) {
+    fcgno_model_destroy(m);
+    return rc;
+  }
+  *out = m;
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_model_destroy(fcgno_model_t m) {
+  if (!m) return FCGNO_OK;
+  no_workspace_free(m);
+  tc_model_free(m);
+  if (m->w64) cudaFree(m->w64);
+  delete m;
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_op_destroy(fcgno_op_t op) {
+  if (!op) return FCGNO_OK;
+  solver_ws_free(op);
+  double* p[] = {op->aE, op->aN, op->diag, op->logk};
+  for (double* x : p)
+    if (x) cudaFree(x);
+  delete op;
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, const double* r, double* z,
+                                            fcgno_prec prec, void* stream) {
+  if (!model || !op || !r || !z) {
+    set_last_error("fcgno_precond_apply: null argument");
+    return FCGNO_EINVAL;
+  }
+  if (op->N < 2 * model->desc.modes) {
+    set_last_error("fcgno_precond_apply: grid smaller than 2*modes");
+    return FCGNO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // per-instance rms lives in a small scratch owned by the op's solver workspace
+  double* rms = nullptr;
+  FCGNO_CUDA_TRY(cudaMallocAsync(&rms, sizeof(double) * op->B, st));
+  fcgno_status rc = launch_rms(r, op->B, op->n, rms, st);
+  if (rc == FCGNO_OK) {
+    switch (prec) {
+      case FCGNO_FP64:
+        rc = no_apply_simt(model, op, r, rms, nullptr, z, true, st);
+        break;
+      case FCGNO_FP32:
+        rc = no_apply_simt(model, op, r, rms, nullptr, z, false, st);
+        break;
+      case FCGNO_BF16:
+      case FCGNO_FP16:
+        rc = no_apply_tc(model, op, r, rms, nullptr, z, prec == FCGNO_FP16, st);
+        break;
+      default:
+        set_last_error("fcgno_precond_apply: unknown precision");
+        rc = FCGNO_EINVAL;
+    }
+  }
+  cudaFreeAsync(rms, st);
+  return rc;
+}
+
+extern "C" fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
+                                         int batch, fcgno_prec prec, float* loss, float* grad, void* stream) {
+  if (!model || !op || !r || !e || !loss || !grad || batch != op->B) {
+    set_last_error("fcgno_train_step: null argument or batch != op batch");
+    return FCGNO_EINVAL;
+  }
+  if (prec != FCGNO_FP32 && prec != FCGNO_FP64) {
+    set_last_error("fcgno_train_step: precision must be FCGNO_FP32 or FCGNO_FP64");
+    return FCGNO_EINVAL;
+  }
+  if (op->N < 2 * model->desc.modes) {
+    set_last_error("fcgno_train_step: grid smaller than 2*modes");
+    return FCGNO_EINVAL;
+  }
+  return train_step_simt(model, op, r, e, loss, grad, prec == FCGNO_FP64, (cudaStream_t)stream);
+}
+
+extern "C" size_t fcgno_workspace_bytes(int N, int batch, int m_max, const fcgno_model_desc* desc, fcgno_prec prec) {
+  if (N < 2 || batch < 1 || m_max < 1) return 0;
+  const size_t n = (size_t)N * N, vec = n * batch * sizeof(double);
+  size_t bytes = 4 * vec;                      // operator: east, north, diagonal, log k
+  bytes += vec;                                // caller's right-hand side is not counted; x is
+  bytes += 2 * vec;                            // r, w
+  bytes += 2 * (size_t)(m_max + 1) * vec;      // direction ring (p_k, s_k)
+  bytes += (size_t)batch * 256;                // per-instance scalars and partials
+  if (desc_ok(desc)) {
+    const size_t C = desc->width, M = desc->modes;
+    const size_t esz = (prec == FCGNO_FP64) ? 8 : (prec == FCGNO_FP32 ? 4 : 2);
+    bytes += 2 * n * batch * C * esz;                         // activation ping-pong
+    bytes += (size_t)batch * M * N * C * 2 * 8;               // separable-transform intermediate
+    bytes += 2 * (size_t)batch * 2 * M * M * C * 2 * 8;       // spectral coefficients
+  }
+  return bytes;
+}
+
+extern "C" const char* fcgno_status_str(fcgno_status s) {
+  switch (s) {
+    case FCGNO_OK: return "ok";
+    case FCGNO_EINVAL: return "invalid argument";
+    case FCGNO_ENOMEM: return "out of device memory";
+    case FCGNO_ECUDA: return "CUDA error";
+    case FCGNO_ENOCONV: return "not converged within max_iter";
+    case FCGNO_EBREAKDOWN: return "breakdown: (p, A p) zero or not finite";
+    case FCGNO_ETIMEOUT: return "device wait timed out";
+  }
+  return "unknown status";
+}
+
+extern "C" const char* fcgno_last_error(void) { return t_last_error.c_str(); }
+
+extern "C" uint64_t fcgno_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }

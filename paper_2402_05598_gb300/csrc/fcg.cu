@@ -1,0 +1,681 @@
+// Flexible conjugate gradients (Algorithm 1, Section 2.3) for a batch of independent
+// instances, FP64 throughout the Krylov loop.
+//
+// Iteration i of instance b:
+//   w_i = B(r_i)                                  (preconditioner, another translation unit)
+//   m_i = min(i, max(1, i mod (m_max+1)))
+//   beta_k = (w_i, s_k) / (p_k, s_k),   k = i-m_i .. i-1   (all from w_i)
+//   p_i = w_i - sum_k beta_k p_k,  s_i = A p_i
+//   alpha = (p_i, r_i) / (p_i, s_i),  u += alpha p_i,  r -= alpha s_i
+//   stop when ||r_{i+1}|| <= tol ||r_0|| (Table 1 criterion), or on breakdown
+// Directions p_k and s_k = A p_k live in a ring of m_max+1 slots; slot(k) = k mod (m_max+1).
+//
+// Two implementations of the vector part:
+//  - fused: one CTA per instance holds the whole instance in registers (+ p in shared
+//    memory for the stencil halo) and performs the step in one launch with block-level
+//    fixed-order reductions (grids up to 90 x 90);
+//  - tiled: any N; seven launches per iteration (dots, beta, direction, stencil+dots,
+//    alpha, update+norm, norm) with per-tile partial sums reduced in a fixed order.
+// Both are deterministic: every sum has a fixed association order.
+#include "internal.cuh"
+
+#include <vector>
+#include <algorithm>
+#include <cmath>
+
+namespace fcgno {
+
+constexpr int kTile = 2048;     // elements per CTA (tiled path)
+constexpr int kThreads = 256;   // threads per CTA (tiled path)
+constexpr int kEPT = kTile / kThreads;
+constexpr int kParts = kMaxWindow + 2;
+constexpr int kFusedEPT = 8;    // elements per thread (fused path)
+constexpr int kFusedMaxN = 90;  // n/8 <= 1024 threads
+
+struct IterArgs {
+  int N;
+  int B;
+  size_t n;
+  int tiles;
+  int i;          // iteration index
+  int m_i;        // window length
+  int slot_new;   // ring slot of p_i, s_i
+  int slots[kMaxWindow];
+  double tol;
+  int fixed;      // 1: ignore tol
+};
+
+struct State {
+  const double* aE;
+  const double* aN;
+  const double* diag;
+  const double* b;
+  double* u;
+  double* r;
+  const double* w;
+  double* P;
+  double* S;
+  double* ps;
+  double* beta;
+  double* alpha;
+  double* r0;
+  double* rr;
+  double* rms;
+  double* part;
+  int* status;
+  int* iters;
+  int* ndone;
+};
+
+__device__ __forceinline__ double stencil_at(const State& s, size_t gi, int p, int q, int N, double c,
+                                             double e, double w, double nn, double so) {
+  // (A x)_P = diag x_P - aE_P x_E - aE_W x_W - aN_P x_N - aN_S x_S   (couplings pre-scaled)
+  double acc = s.diag[gi] * c;
+  if (p < N - 1) acc = fma(-s.aE[gi], e, acc);
+  if (p > 0) acc = fma(-s.aE[gi - 1], w, acc);
+  if (q < N - 1) acc = fma(-s.aN[gi], nn, acc);
+  if (q > 0) acc = fma(-s.aN[gi - N], so, acc);
+  return acc;
+}
+
+// ------------------------------------ initialisation -----------------------------------
+// r_0 = b - A u_0, partial ||r_0||^2 per tile.
+__global__ void __launch_bounds__(kThreads) init_kernel(IterArgs a, State s) {
+  __shared__ double scratch[32];
+  const int b = blockIdx.y;
+  const size_t off = (size_t)b * a.n;
+  double acc[1] = {0.0};
+  for (int j = 0; j < kEPT; ++j) {
+    const size_t e = (size_t)blockIdx.x * kTile + j * kThreads + threadIdx.x;
+    if (e < a.n) {
+      const int q = (int)(e / a.N), p = (int)(e - (size_t)q * a.N);
+      const double* u = s.u + off;
+      const double c = u[e];
+      const double ue = (p < a.N - 1) ? u[e + 1] : 0.0;
+      const double uw = (p > 0) ? u[e - 1] : 0.0;
+      const double un = (q < a.N - 1) ? u[e + a.N] : 0.0;
+      const double us = (q > 0) ? u[e - a.N] : 0.0;
+      const double Au = stencil_at(s, off + e, p, q, a.N, c, ue, uw, un, us);
+      const double rv = s.b[off + e] - Au;
+      s.r[off + e] = rv;
+      acc[0] = fma(rv, rv, acc[0]);
+    }
+  }
+  block_sum<double, 1>(acc, scratch);
+  if (threadIdx.x == 0) s.part[((size_t)b * a.tiles + blockIdx.x) * kParts] = acc[0];
+}
+
+__global__ void init_finalize_kernel(IterArgs a, State s) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B) return;
+  double rr = 0.0;
+  for (int t = 0; t < a.tiles; ++t) rr += s.part[((size_t)b * a.tiles + t) * kParts];
+  s.rr[b] = rr;
+  s.r0[b] = sqrt(rr);
+  s.rms[b] = sqrt(rr / (double)a.n);
+  s.iters[b] = 0;
+  if (rr == 0.0) {
+    s.status[b] = FCGNO_OK;
+    atomicAdd(s.ndone, 1);
+  } else {
+    s.status[b] = kRunning;
+  }
+}
+
+// ------------------------------------ tiled path ---------------------------------------
+__global__ void __launch_bounds__(kThreads) dots_w_kernel(IterArgs a, State s) {
+  __shared__ double scratch[32 * kMaxWindow];
+  const int b = blockIdx.y;
+  if (s.status[b] != kRunning) return;
+  const size_t off = (size_t)b * a.n;
+  double acc[kMaxWindow];
+#pragma unroll
+  for (int j = 0; j < kMaxWindow; ++j) acc[j] = 0.0;
+  for (int t = 0; t < kEPT; ++t) {
+    const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
+    if (e < a.n) {
+      const double wv = s.w[off + e];
+#pragma unroll
+      for (int j = 0; j < kMaxWindow; ++j)
+        if (j < a.m_i) acc[j] = fma(wv, s.S[(size_t)a.slots[j] * a.B * a.n + off + e], acc[j]);
+    }
+  }
+  block_sum<double, kMaxWindow>(acc, scratch);
+  if (threadIdx.x < a.m_i) {
+    double v = acc[0];
+#pragma unroll
+    for (int j = 1; j < kMaxWindow; ++j)
+      if (threadIdx.x == j) v = acc[j];
+    s.part[((size_t)b * a.tiles + blockIdx.x) * kParts + threadIdx.x] = v;
+  }
+}
+
+__global__ void beta_kernel(IterArgs a, State s) {
+  const int b = blockIdx.x;
+  const int j = threadIdx.x;
+  if (s.status[b] != kRunning || j >= a.m_i) return;
+  double sum = 0.0;
+  for (int t = 0; t < a.tiles; ++t) sum += s.part[((size_t)b * a.tiles + t) * kParts + j];
+  s.beta[b * kMaxWindow + j] = sum / s.ps[(size_t)a.slots[j] * a.B + b];
+}
+
+__global__ void __launch_bounds__(kThreads) direction_kernel(IterArgs a, State s) {
+  const int b = blockIdx.y;
+  if (s.status[b] != kRunning) return;
+  const size_t off = (size_t)b * a.n;
+  double beta[kMaxWindow];
+#pragma unroll
+  for (int j = 0; j < kMaxWindow; ++j) beta[j] = (j < a.m_i) ? s.beta[b * kMaxWindow + j] : 0.0;
+  double* pn = s.P + (size_t)a.slot_new * a.B * a.n + off;
+  for (int t = 0; t < kEPT; ++t) {
+    const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
+    if (e < a.n) {
+      double p = s.w[off + e];
+#pragma unroll
+      for (int j = 0; j < kMaxWindow; ++j)
+        if (j < a.m_i) p = fma(-beta[j], s.P[(size_t)a.slots[j] * a.B * a.n + off + e], p);
+      pn[e] = p;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(kThreads) stencil_dots_kernel(IterArgs a, State s) {
+  __shared__ double scratch[32 * 2];
+  const int b = blockIdx.y;
+  if (s.status[b] != kRunning) return;
+  const size_t off = (size_t)b * a.n;
+  const double* pv = s.P + (size_t)a.slot_new * a.B * a.n + off;
+  double* sv = s.S + (size_t)a.slot_new * a.B * a.n + off;
+  double acc[2] = {0.0, 0.0};
+  for (int t = 0; t < kEPT; ++t) {
+    const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
+    if (e < a.n) {
+      const int q = (int)(e / a.N), p = (int)(e - (size_t)q * a.N);
+      const double c = pv[e];
+      const double ue = (p < a.N - 1) ? pv[e + 1] : 0.0;
+      const double uw = (p > 0) ? pv[e - 1] : 0.0;
+      const double un = (q < a.N - 1) ? pv[e + a.N] : 0.0;
+      const double us = (q > 0) ? pv[e - a.N] : 0.0;
+      const double Ap = stencil_at(s, off + e, p, q, a.N, c, ue, uw, un, us);
+      sv[e] = Ap;
+      acc[0] = fma(c, Ap, acc[0]);
+      acc[1] = fma(c, s.r[off + e], acc[1]);
+    }
+  }
+  block_sum<double, 2>(acc, scratch);
+  if (threadIdx.x == 0) {
+    double* pp = s.part + ((size_t)b * a.tiles + blockIdx.x) * kParts;
+    pp[0] = acc[0];
+    pp[1] = acc[1];
+  }
+}
+
+__global__ void alpha_kernel(IterArgs a, State s) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B || s.status[b] != kRunning) return;
+  double ps = 0.0, pr = 0.0;
+  for (int t = 0; t < a.tiles; ++t) {
+    const double* pp = s.part + ((size_t)b * a.tiles + t) * kParts;
+    ps += pp[0];
+    pr += pp[1];
+  }
+  if (!(ps != 0.0 && isfinite(ps) && isfinite(pr))) {
+    s.status[b] = FCGNO_EBREAKDOWN;
+    atomicAdd(s.ndone, 1);
+    return;
+  }
+  s.alpha[b] = pr / ps;
+  s.ps[(size_t)a.slot_new * a.B + b] = ps;
+}
+
+__global__ void __launch_bounds__(kThreads) update_kernel(IterArgs a, State s) {
+  __shared__ double scratch[32];
+  const int b = blockIdx.y;
+  if (s.status[b] != kRunning) return;
+  const size_t off = (size_t)b * a.n;
+  const double alpha = s.alpha[b];
+  const double* pv = s.P + (size_t)a.slot_new * a.B * a.n + off;
+  const double* sv = s.S + (size_t)a.slot_new * a.B * a.n + off;
+  double acc[1] = {0.0};
+  for (int t = 0; t < kEPT; ++t) {
+    const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
+    if (e < a.n) {
+      s.u[off + e] = fma(alpha, pv[e], s.u[off + e]);
+      const double rv = fma(-alpha, sv[e], s.r[off + e]);
+      s.r[off + e] = rv;
+      acc[0] = fma(rv, rv, acc[0]);
+    }
+  }
+  block_sum<double, 1>(acc, scratch);
+  if (threadIdx.x == 0) s.part[((size_t)b * a.tiles + blockIdx.x) * kParts + 2] = acc[0];
+}
+
+__global__ void norm_kernel(IterArgs a, State s) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= a.B || s.status[b] != kRunning) return;
+  double rr = 0.0;
+  for (int t = 0; t < a.tiles; ++t) rr += s.part[((size_t)b * a.tiles + t) * kParts + 2];
+  s.rr[b] = rr;
+  s.rms[b] = sqrt(rr / (double)a.n);
+  s.iters[b] = a.i + 1;
+  const double rn = sqrt(rr);
+  if (rr == 0.0 || (!a.fixed && rn <= a.tol * s.r0[b])) {
+    s.status[b] = FCGNO_OK;
+    atomicAdd(s.ndone, 1);
+  }
+}
+
+// ------------------------------------ fused path ---------------------------------------
+// One CTA per instance; thread t owns elements t + j*blockDim (j < 8); p staged in shared
+// memory for the stencil. Four fixed-order block reductions per iteration.
+__global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
+  extern __shared__ double sp[];  // n doubles
+  __shared__ double scratch[32 * kMaxWindow];
+  const int b = blockIdx.x;
+  if (s.status[b] != kRunning) return;
+  const size_t off = (size_t)b * a.n;
+  const int T = blockDim.x;
+  const int n = (int)a.n;
+  double wv[kFusedEPT], rv[kFusedEPT], sv[kFusedEPT];
+#pragma unroll
+  for (int j = 0; j < kFusedEPT; ++j) {
+    const int e = threadIdx.x + j * T;
+    wv[j] = (e < n) ? s.w[off + e] : 0.0;
+  }
+  // beta_k = (w, s_k) / (p_k, s_k)
+  double acc[kMaxWindow];
+#pragma unroll
+  for (int k = 0; k < kMaxWindow; ++k) {
+    acc[k] = 0.0;
+    if (k < a.m_i) {
+      const double* Sk = s.S + (size_t)a.slots[k] * a.B * a.n + off;
+#pragma unroll
+      for (int j = 0; j < kFusedEPT; ++j) {
+        const int e = threadIdx.x + j * T;
+        if (e < n) acc[k] = fma(wv[j], Sk[e], acc[k]);
+      }
+    }
+  }
+  block_sum<double, kMaxWindow>(acc, scratch);
+  // p = w - sum beta_k p_k (kept in wv)
+#pragma unroll
+  for (int k = 0; k < kMaxWindow; ++k) {
+    if (k < a.m_i) {
+      const double beta = acc[k] / s.ps[(size_t)a.slots[k] * a.B + b];
+      const double* Pk = s.P + (size_t)a.slots[k] * a.B * a.n + off;
+#pragma unroll
+      for (int j = 0; j < kFusedEPT; ++j) {
+        const int e = threadIdx.x + j * T;
+        if (e < n) wv[j] = fma(-beta, Pk[e], wv[j]);
+      }
+    }
+  }
+  double* Pn = s.P + (size_t)a.slot_new * a.B * a.n + off;
+#pragma unroll
+  for (int j = 0; j < kFusedEPT; ++j) {
+    const int e = threadIdx.x + j * T;
+    if (e < n) {
+      sp[e] = wv[j];
+      Pn[e] = wv[j];
+    }
+  }
+  __syncthreads();
+  // s = A p, (p, s), (p, r)
+  double d2[2] = {0.0, 0.0};
+#pragma unroll
+  for (int j = 0; j < kFusedEPT; ++j) {
+    const int e = threadIdx.x + j * T;
+    sv[j] = 0.0;
+    rv[j] = 0.0;
+    if (e < n) {
+      const int q = e / a.N, p = e - q * a.N;
+      const double ue = (p < a.N - 1) ? sp[e + 1] : 0.0;
+      const double uw = (p > 0) ? sp[e - 1] : 0.0;
+      const double un = (q < a.N - 1) ? sp[e + a.N] : 0.0;
+      const double us = (q > 0) ? sp[e - a.N] : 0.0;
+      sv[j] = stencil_at(s, off + e, p, q, a.N, wv[j], ue, uw, un, us);
+      rv[j] = s.r[off + e];
+      d2[0] = fma(wv[j], sv[j], d2[0]);
+      d2[1] = fma(wv[j], rv[j], d2[1]);
+    }
+  }
+  block_sum<double, 2>(d2, scratch);
+  const double ps = d2[0], pr = d2[1];
+  if (!(ps != 0.0 && isfinite(ps) && isfinite(pr))) {
+    if (threadIdx.x == 0) {
+      s.status[b] = FCGNO_EBREAKDOWN;
+      atomicAdd(s.ndone, 1);
+    }
+    return;
+  }
+  const double alpha = pr / ps;
+  double* Sn = s.S + (size_t)a.slot_new * a.B * a.n + off;
+  double rr[1] = {0.0};
+#pragma unroll
+  for (int j = 0; j < kFusedEPT; ++j) {
+    const int e = threadIdx.x + j * T;
+    if (e < n) {
+      Sn[e] = sv[j];
+      s.u[off + e] = fma(alpha, wv[j], s.u[off + e]);
+      const double r1 = fma(-alpha, sv[j], rv[j]);
+      s.r[off + e] = r1;
+      rr[0] = fma(r1, r1, rr[0]);
+    }
+  }
+  block_sum<double, 1>(rr, scratch);
+  if (threadIdx.x == 0) {
+    s.ps[(size_t)a.slot_new * a.B + b] = ps;
+    s.alpha[b] = alpha;
+    s.rr[b] = rr[0];
+    s.rms[b] = sqrt(rr[0] / (double)a.n);
+    s.iters[b] = a.i + 1;
+    if (rr[0] == 0.0 || (!a.fixed && sqrt(rr[0]) <= a.tol * s.r0[b])) {
+      s.status[b] = FCGNO_OK;
+      atomicAdd(s.ndone, 1);
+    }
+  }
+}
+
+// Krylov sampling helper: r_out[i] = r, e_out[i] = u_star - u for every instance.
+__global__ void harvest_copy_kernel(size_t total, const double* __restrict__ r, const double* __restrict__ u,
+                                    const double* __restrict__ ustar, double* __restrict__ r_out,
+                                    double* __restrict__ e_out) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  r_out[i] = r[i];
+  e_out[i] = ustar[i] - u[i];
+}
+
+// ------------------------------------ host side ----------------------------------------
+static void free_ws(SolverWorkspace& w) {
+  double** dp[] = {&w.r, &w.w, &w.P, &w.S, &w.ps, &w.beta, &w.alpha, &w.r0, &w.rr, &w.rms, &w.part};
+  for (auto p : dp) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  int** ip[] = {&w.status, &w.iters, &w.ndone};
+  for (auto p : ip) {
+    if (*p) cudaFree(*p);
+    *p = nullptr;
+  }
+  w.cap_B = w.cap_n = w.cap_slots = w.cap_tiles = 0;
+}
+
+void solver_ws_free(fcgno_op* op) { free_ws(op->ws); }
+
+static fcgno_status ensure_ws(fcgno_op* op, int slots) {
+  SolverWorkspace& w = op->ws;
+  const int tiles = (int)ceil_div(op->n, kTile);
+  if (w.cap_B == op->B && w.cap_n == (int)op->n && w.cap_slots >= slots && w.cap_tiles >= tiles) return FCGNO_OK;
+  free_ws(w);
+  const size_t vec = op->n * op->B * sizeof(double);
+  bool ok = true;
+  auto alloc = [&](void** p, size_t bytes) {
+    if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
+  };
+  alloc((void**)&w.r, vec);
+  alloc((void**)&w.w, vec);
+  alloc((void**)&w.P, vec * slots);
+  alloc((void**)&w.S, vec * slots);
+  alloc((void**)&w.ps, sizeof(double) * slots * op->B);
+  alloc((void**)&w.beta, sizeof(double) * kMaxWindow * op->B);
+  alloc((void**)&w.alpha, sizeof(double) * op->B);
+  alloc((void**)&w.r0, sizeof(double) * op->B);
+  alloc((void**)&w.rr, sizeof(double) * op->B);
+  alloc((void**)&w.rms, sizeof(double) * op->B);
+  alloc((void**)&w.part, sizeof(double) * op->B * tiles * kParts);
+  alloc((void**)&w.status, sizeof(int) * op->B);
+  alloc((void**)&w.iters, sizeof(int) * op->B);
+  alloc((void**)&w.ndone, sizeof(int));
+  if (!ok) {
+    cudaGetLastError();
+    free_ws(w);
+    set_last_error("solver workspace: out of device memory");
+    return FCGNO_ENOMEM;
+  }
+  w.cap_B = op->B;
+  w.cap_n = (int)op->n;
+  w.cap_slots = slots;
+  w.cap_tiles = tiles;
+  return FCGNO_OK;
+}
+
+static State make_state(fcgno_op* op, const double* b, double* x, const double* wptr) {
+  SolverWorkspace& w = op->ws;
+  State s;
+  s.aE = op->aE;
+  s.aN = op->aN;
+  s.diag = op->diag;
+  s.b = b;
+  s.u = x;
+  s.r = w.r;
+  s.w = wptr;
+  s.P = w.P;
+  s.S = w.S;
+  s.ps = w.ps;
+  s.beta = w.beta;
+  s.alpha = w.alpha;
+  s.r0 = w.r0;
+  s.rr = w.rr;
+  s.rms = w.rms;
+  s.part = w.part;
+  s.status = w.status;
+  s.iters = w.iters;
+  s.ndone = w.ndone;
+  return s;
+}
+
+struct HarvestHook {
+  const double* ustar = nullptr;
+  double* r_out = nullptr;
+  double* e_out = nullptr;
+};
+
+static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b, double* x,
+                               const fcgno_solve_opts& o, fcgno_prec prec, fcgno_solve_info* info,
+                               cudaStream_t st, const HarvestHook* hook) {
+  const int slots = o.m_max + 1;
+  FCGNO_TRY(ensure_ws(op, slots));
+  SolverWorkspace& w = op->ws;
+  const bool identity = (model == nullptr);
+  // with the identity preconditioner w_i = r_i: read r in place of w
+  State s = make_state(op, b, x, identity ? w.r : w.w);
+  IterArgs a{};
+  a.N = op->N;
+  a.B = op->B;
+  a.n = op->n;
+  a.tiles = (int)ceil_div(op->n, kTile);
+  a.tol = o.tol;
+  a.fixed = o.fixed_iters ? 1 : 0;
+  const bool fused = op->N <= kFusedMaxN;
+  const int fusedThreads = ((int)ceil_div(op->n, kFusedEPT) + 31) / 32 * 32;
+  const size_t fusedSmem = op->n * sizeof(double);
+  if (fused && fusedSmem > 48 * 1024)
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fusedSmem));
+
+  FCGNO_CUDA_TRY(cudaMemsetAsync(w.ndone, 0, sizeof(int), st));
+  init_kernel<<<dim3(a.tiles, op->B), kThreads, 0, st>>>(a, s);
+  FCGNO_LAUNCHED();
+  init_finalize_kernel<<<ceil_div(op->B, 128), 128, 0, st>>>(a, s);
+  FCGNO_LAUNCHED();
+
+  int* h_ndone = nullptr;
+  FCGNO_CUDA_TRY(cudaMallocHost(&h_ndone, sizeof(int)));
+  struct PinnedGuard {
+    int* p;
+    ~PinnedGuard() { cudaFreeHost(p); }
+  } guard{h_ndone};
+  const int check_every = std::max(1, o.check_every);
+  for (int i = 0; i < o.max_iter; ++i) {
+    a.i = i;
+    a.m_i = std::min(i, std::max(1, i % slots));
+    a.slot_new = i % slots;
+    for (int j = 0; j < kMaxWindow; ++j) a.slots[j] = (j < a.m_i) ? (i - a.m_i + j) % slots : 0;
+    if (!identity) {
+      if (prec == FCGNO_BF16 || prec == FCGNO_FP16) {
+        FCGNO_TRY(no_apply_tc(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP16, st));
+      } else {
+        FCGNO_TRY(no_apply_simt(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP64, st));
+      }
+    }
+    if (fused) {
+      fused_step_kernel<<<op->B, fusedThreads, fusedSmem, st>>>(a, s);
+      FCGNO_LAUNCHED();
+    } else {
+      const dim3 grid(a.tiles, op->B);
+      if (a.m_i > 0) {
+        dots_w_kernel<<<grid, kThreads, 0, st>>>(a, s);
+        FCGNO_LAUNCHED();
+        beta_kernel<<<op->B, 32, 0, st>>>(a, s);
+        FCGNO_LAUNCHED();
+      }
+      direction_kernel<<<grid, kThreads, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+      stencil_dots_kernel<<<grid, kThreads, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+      alpha_kernel<<<ceil_div(op->B, 128), 128, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+      update_kernel<<<grid, kThreads, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+      norm_kernel<<<ceil_div(op->B, 128), 128, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+    }
+    if (hook) {
+      const size_t total = op->n * op->B;
+      const size_t o2 = (size_t)i * total;
+      harvest_copy_kernel<<<ceil_div(total, 256), 256, 0, st>>>(total, w.r, x, hook->ustar, hook->r_out + o2,
+                                                                 hook->e_out + o2);
+      FCGNO_LAUNCHED();
+    }
+    if ((i + 1) % check_every == 0 || i + 1 == o.max_iter) {
+      FCGNO_CUDA_TRY(cudaMemcpyAsync(h_ndone, w.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+      if (*h_ndone >= op->B && !hook) break;
+    }
+  }
+  if (info) {
+    std::vector<int> hs(op->B), hi(op->B);
+    std::vector<double> hrr(op->B), hr0(op->B);
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.status, sizeof(int) * op->B, cudaMemcpyDeviceToHost, st));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hi.data(), w.iters, sizeof(int) * op->B, cudaMemcpyDeviceToHost, st));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hrr.data(), w.rr, sizeof(double) * op->B, cudaMemcpyDeviceToHost, st));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hr0.data(), w.r0, sizeof(double) * op->B, cudaMemcpyDeviceToHost, st));
+    FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+    for (int bi = 0; bi < op->B; ++bi) {
+      info[bi].iters = hi[bi];
+      int stt = hs[bi];
+      if (stt == kRunning) stt = o.fixed_iters ? FCGNO_OK : FCGNO_ENOCONV;
+      info[bi].status = stt;
+      info[bi].r0norm = hr0[bi];
+      info[bi].relres = hr0[bi] > 0 ? std::sqrt(hrr[bi]) / hr0[bi] : 0.0;
+    }
+  } else {
+    FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  return FCGNO_OK;
+}
+
+static fcgno_status check_opts(const fcgno_solve_opts* o) {
+  if (!o || !(o->tol >= 0.0) || o->m_max < 1 || o->m_max > kMaxWindow || o->max_iter < 0) {
+    set_last_error("fcgno_solve: need tol >= 0, 1 <= m_max <= 8, max_iter >= 0");
+    return FCGNO_EINVAL;
+  }
+  return FCGNO_OK;
+}
+
+}  // namespace fcgno
+
+using namespace fcgno;
+
+extern "C" fcgno_status fcgno_solve(fcgno_op_t A, fcgno_model_t Bpc, const double* b, double* x,
+                                    const fcgno_solve_opts* opts, fcgno_prec prec, fcgno_solve_info* info,
+                                    void* stream) {
+  if (!A || !b || !x) {
+    set_last_error("fcgno_solve: null operator, b or x");
+    return FCGNO_EINVAL;
+  }
+  FCGNO_TRY(check_opts(opts));
+  if (Bpc && A->N < 2 * Bpc->desc.modes) {
+    set_last_error("fcgno_solve: grid smaller than 2*modes");
+    return FCGNO_EINVAL;
+  }
+  if (prec < FCGNO_FP64 || prec > FCGNO_FP32) {
+    set_last_error("fcgno_solve: unknown precision");
+    return FCGNO_EINVAL;
+  }
+  return solve_impl(A, Bpc, b, x, *opts, prec, info, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const double* b_host,
+                                         double* x_host, fcgno_model_t Bpc, const fcgno_solve_opts* opts,
+                                         fcgno_prec prec, fcgno_solve_info* info, void* stream) {
+  if (N < 2 || batch < 1 || !k_host || !b_host || !x_host) {
+    set_last_error("fcgno_solve_host: bad arguments");
+    return FCGNO_EINVAL;
+  }
+  FCGNO_TRY(check_opts(opts));
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = (size_t)N * N * batch * sizeof(double);
+  double *dk = nullptr, *db = nullptr, *dx = nullptr;
+  if (cudaMallocAsync(&dk, bytes, st) != cudaSuccess || cudaMallocAsync(&db, bytes, st) != cudaSuccess ||
+      cudaMallocAsync(&dx, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (dk) cudaFreeAsync(dk, st);
+    if (db) cudaFreeAsync(db, st);
+    set_last_error("fcgno_solve_host: out of device memory");
+    return FCGNO_ENOMEM;
+  }
+  fcgno_status rc = FCGNO_OK;
+  fcgno_op_t op = nullptr;
+  do {
+    if (cudaMemcpyAsync(dk, k_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(db, b_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+      set_last_error("fcgno_solve_host: host-to-device copy failed");
+      rc = FCGNO_ECUDA;
+      break;
+    }
+    rc = fcgno_assemble(N, batch, dk, stream, &op);
+    if (rc != FCGNO_OK) break;
+    rc = fcgno_solve(op, Bpc, db, dx, opts, prec, info, stream);
+    if (rc != FCGNO_OK) break;
+    if (cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      set_last_error("fcgno_solve_host: device-to-host copy failed");
+      rc = FCGNO_ECUDA;
+    }
+  } while (0);
+  if (op) fcgno_op_destroy(op);
+  cudaFreeAsync(dk, st);
+  cudaFreeAsync(db, st);
+  cudaFreeAsync(dx, st);
+  return rc;
+}
+
+extern "C" fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x0,
+                                             const double* u_star, int K, double* r_out, double* e_out,
+                                             fcgno_solve_info* info, void* stream) {
+  if (!A || !b || !x0 || !u_star || K < 1 || !r_out || !e_out) {
+    set_last_error("fcgno_krylov_harvest: bad arguments");
+    return FCGNO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = A->n * A->B * sizeof(double);
+  double* u = nullptr;
+  if (cudaMallocAsync(&u, bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("fcgno_krylov_harvest: out of device memory");
+    return FCGNO_ENOMEM;
+  }
+  fcgno_status rc = FCGNO_OK;
+  if (cudaMemcpyAsync(u, x0, bytes, cudaMemcpyDeviceToDevice, st) != cudaSuccess) {
+    set_last_error("fcgno_krylov_harvest: copy failed");
+    rc = FCGNO_ECUDA;
+  } else {
+    fcgno_solve_opts o{1e-13, 1, K, 0, K};  // converged instances keep their last iterate
+    HarvestHook h{u_star, r_out, e_out};
+    rc = solve_impl(A, nullptr, b, u, o, FCGNO_FP64, info, st, &h);
+  }
+  cudaFreeAsync(u, st);
+  return rc;
+}

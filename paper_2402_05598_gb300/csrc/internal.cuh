@@ -1,0 +1,179 @@
+// Internal definitions shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cstdint>
+#include <cstddef>
+#include <atomic>
+#include <string>
+
+#include "../../include/fcgno.h"
+
+namespace fcgno {
+
+// ---------------------------------------------------------------------------------------
+// Error handling and launch accounting
+// ---------------------------------------------------------------------------------------
+void set_last_error(const std::string& msg);
+extern std::atomic<uint64_t> g_launches;
+
+#define FCGNO_CUDA_TRY(call)                                                                 \
+  do {                                                                                       \
+    cudaError_t e_ = (call);                                                                 \
+    if (e_ != cudaSuccess) {                                                                 \
+      ::fcgno::set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));           \
+      return FCGNO_ECUDA;                                                                    \
+    }                                                                                        \
+  } while (0)
+
+// Records a launch of one of this library's kernels and checks the launch itself.
+#define FCGNO_LAUNCHED()                                                                     \
+  do {                                                                                       \
+    ::fcgno::g_launches.fetch_add(1, std::memory_order_relaxed);                             \
+    cudaError_t e_ = cudaGetLastError();                                                     \
+    if (e_ != cudaSuccess) {                                                                 \
+      ::fcgno::set_last_error(std::string("kernel launch: ") + cudaGetErrorString(e_));      \
+      return FCGNO_ECUDA;                                                                    \
+    }                                                                                        \
+  } while (0)
+
+#define FCGNO_TRY(call)                                                                      \
+  do {                                                                                       \
+    fcgno_status s_ = (call);                                                                \
+    if (s_ != FCGNO_OK) return s_;                                                           \
+  } while (0)
+
+// Per-instance solver status codes kept on the device (negative = still iterating).
+constexpr int kRunning = -1;
+constexpr int kMaxWindow = 8;  // largest m_max supported
+
+// ---------------------------------------------------------------------------------------
+// Handles
+// ---------------------------------------------------------------------------------------
+struct SolverWorkspace {
+  int cap_B = 0, cap_n = 0, cap_slots = 0, cap_tiles = 0;
+  double* r = nullptr;      // [B][n]
+  double* w = nullptr;      // [B][n]  preconditioned residual
+  double* P = nullptr;      // [slots][B][n] directions p_k
+  double* S = nullptr;      // [slots][B][n] A p_k
+  double* ps = nullptr;     // [slots][B]    (p_k, s_k)
+  double* beta = nullptr;   // [B][kMaxWindow]
+  double* alpha = nullptr;  // [B]
+  double* r0 = nullptr;     // [B] ||r_0||
+  double* rr = nullptr;     // [B] ||r_i||^2
+  double* rms = nullptr;    // [B] sqrt(||r_i||^2 / n)
+  double* part = nullptr;   // [B][tiles][kParts] partial sums
+  int* status = nullptr;    // [B]
+  int* iters = nullptr;     // [B]
+  int* ndone = nullptr;     // [1] count of stopped instances
+};
+
+}  // namespace fcgno
+
+struct fcgno_op {
+  int N = 0, B = 0;
+  size_t n = 0;
+  double* aE = nullptr;    // [B][n] east-face coefficient / h^2 (boundary face at p = N-1)
+  double* aN = nullptr;    // [B][n] north-face coefficient / h^2 (boundary face at q = N-1)
+  double* diag = nullptr;  // [B][n] sum of the four face coefficients / h^2
+  double* logk = nullptr;  // [B][n]
+  fcgno::SolverWorkspace ws;
+};
+
+namespace fcgno {
+
+struct NoWorkspace;  // activations of the preconditioner (defined per implementation)
+struct TcModel;      // tensor-core copies of the weights
+
+}  // namespace fcgno
+
+struct fcgno_model {
+  fcgno_model_desc desc{};
+  const float* w32 = nullptr;   // caller's FP32 master blob (device)
+  double* w64 = nullptr;        // FP64 copy of the blob (device)
+  size_t count = 0;             // floats in the blob
+  fcgno::NoWorkspace* ws = nullptr;
+  fcgno::TcModel* tc = nullptr;
+};
+
+namespace fcgno {
+
+// Blob offsets (in elements) -- same order as documented in fcgno.h.
+struct BlobLayout {
+  size_t lift_w, lift_b, proj1_w, proj1_b, proj2_w, proj2_b, total;
+  size_t w[16], b[16], r[16];
+};
+BlobLayout blob_layout(const fcgno_model_desc& d);
+
+// Stencil matvec y = A x for all instances (FP64).
+fcgno_status launch_apply_A(const fcgno_op* op, const double* x, double* y, cudaStream_t st);
+
+// Preconditioner entry points implemented by the CUDA-core (SIMT) and tensor-core paths.
+// rms: [B] per-instance rms of r (device); active: [B] status array (nullptr = all
+// active; an instance is skipped when active[b] >= 0).
+fcgno_status no_apply_simt(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms,
+                           const int* active, double* z, bool fp64, cudaStream_t st);
+fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms,
+                         const int* active, double* z, bool fp16, cudaStream_t st);
+fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t st);
+void tc_model_free(fcgno_model* m);
+void no_workspace_free(fcgno_model* m);
+
+// Per-instance rms of r: rms[b] = sqrt(mean(r_b^2)).
+fcgno_status launch_rms(const double* r, int B, size_t n, double* rms, cudaStream_t st);
+
+// Training (energy-norm loss, Eq. (11)).
+fcgno_status train_step_simt(fcgno_model* m, fcgno_op* op, const double* r, const double* e,
+                             float* loss, float* grad, bool fp64, cudaStream_t st);
+
+inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
+
+// ---------------------------------------------------------------------------------------
+// Device helpers
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Fixed-order block reduction of NV values per thread; the result is valid in every
+// thread. scratch must hold 32*NV entries of T. Contains __syncthreads().
+template <typename T, int NV>
+__device__ __forceinline__ void block_sum(T (&v)[NV], T* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = warp_sum(v[j]);
+  __syncthreads();
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j) scratch[wid * NV + j] = v[j];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    T s = 0;
+    for (int w = 0; w < nw; ++w) s += scratch[w * NV + j];
+    v[j] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double gelu_d(double x) { return 0.5 * x * (1.0 + erf(x * 0.70710678118654752440)); }
+__device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752440f)); }
+// d/dx GELU(x) = Phi(x) + x phi(x)
+__device__ __forceinline__ double gelu_grad_d(double x) {
+  return 0.5 * (1.0 + erf(x * 0.70710678118654752440)) + x * 0.39894228040143267794 * exp(-0.5 * x * x);
+}
+__device__ __forceinline__ float gelu_grad_f(float x) {
+  return 0.5f * (1.0f + erff(x * 0.70710678118654752440f)) + x * 0.39894228040143267794f * expf(-0.5f * x * x);
+}
+
+}  // namespace fcgno

@@ -1,0 +1,120 @@
+// Stencil assembly and matrix-free application of the discretised Eq. (1)-(2).
+//
+// -div(k grad u) = f on (0,1)^2, u = 0 on the boundary, 5-point finite volume on the N x N
+// interior nodes (h = 1/(N+1)). Interior faces carry the harmonic mean 2 k_P k_Q/(k_P+k_Q),
+// a boundary face the k of its node. The operator is stored as three FP64 arrays already
+// scaled by 1/h^2: the east face aE (at p = N-1 it is the boundary face), the north face aN
+// (boundary face at q = N-1) and the diagonal (sum of the four faces). West/south couplings
+// are the neighbour's aE/aN, so A is exactly symmetric.
+#include "internal.cuh"
+
+#include <cmath>
+
+namespace fcgno {
+
+__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
+
+__global__ void assemble_kernel(int N, size_t n, size_t total, const double* __restrict__ k,
+                                double* __restrict__ aE, double* __restrict__ aN,
+                                double* __restrict__ diag, double* __restrict__ logk) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const size_t b = i / n;
+  const int x = (int)(i - b * n);
+  const int q = x / N, p = x - q * N;
+  const double* kb = k + b * n;
+  const double kP = kb[x];
+  const double inv_h2 = (double)(N + 1) * (double)(N + 1);
+  // each interior face is formed once with the (lower node, upper node) argument order so
+  // that the coupling seen from both sides is bit-identical
+  const double e = (p < N - 1) ? harmonic(kP, kb[x + 1]) : kP;
+  const double w = (p > 0) ? harmonic(kb[x - 1], kP) : kP;
+  const double nn = (q < N - 1) ? harmonic(kP, kb[x + N]) : kP;
+  const double s = (q > 0) ? harmonic(kb[x - N], kP) : kP;
+  aE[i] = e * inv_h2;
+  aN[i] = nn * inv_h2;
+  diag[i] = (e + w + nn + s) * inv_h2;
+  logk[i] = log(kP);
+}
+
+__global__ void apply_A_kernel(int N, size_t n, size_t total, const double* __restrict__ aE,
+                               const double* __restrict__ aN, const double* __restrict__ diag,
+                               const double* __restrict__ x, double* __restrict__ y) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const size_t b = i / n;
+  const int xi = (int)(i - b * n);
+  const int q = xi / N, p = xi - q * N;
+  double acc = diag[i] * x[i];
+  if (p < N - 1) acc = fma(-aE[i], x[i + 1], acc);
+  if (p > 0) acc = fma(-aE[i - 1], x[i - 1], acc);
+  if (q < N - 1) acc = fma(-aN[i], x[i + N], acc);
+  if (q > 0) acc = fma(-aN[i - N], x[i - N], acc);
+  y[i] = acc;
+}
+
+__global__ void rms_kernel(const double* __restrict__ r, size_t n, double* __restrict__ rms) {
+  __shared__ double scratch[32];
+  const double* rb = r + blockIdx.x * n;
+  double v[1] = {0.0};
+  for (size_t i = threadIdx.x; i < n; i += blockDim.x) v[0] = fma(rb[i], rb[i], v[0]);
+  block_sum<double, 1>(v, scratch);
+  if (threadIdx.x == 0) rms[blockIdx.x] = sqrt(v[0] / (double)n);
+}
+
+fcgno_status launch_apply_A(const fcgno_op* op, const double* x, double* y, cudaStream_t st) {
+  const size_t total = op->n * op->B;
+  apply_A_kernel<<<ceil_div(total, 256), 256, 0, st>>>(op->N, op->n, total, op->aE, op->aN, op->diag, x, y);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+fcgno_status launch_rms(const double* r, int B, size_t n, double* rms, cudaStream_t st) {
+  rms_kernel<<<B, 512, 0, st>>>(r, n, rms);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+}  // namespace fcgno
+
+using namespace fcgno;
+
+extern "C" fcgno_status fcgno_assemble(int N, int batch, const double* k, void* stream, fcgno_op_t* out) {
+  if (N < 2 || batch < 1 || !k || !out) {
+    set_last_error("fcgno_assemble: need N >= 2, batch >= 1, non-null k and out");
+    return FCGNO_EINVAL;
+  }
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  fcgno_op* op = new fcgno_op();
+  op->N = N;
+  op->B = batch;
+  op->n = (size_t)N * N;
+  const size_t bytes = op->n * batch * sizeof(double);
+  if (cudaMalloc(&op->aE, bytes) != cudaSuccess || cudaMalloc(&op->aN, bytes) != cudaSuccess ||
+      cudaMalloc(&op->diag, bytes) != cudaSuccess || cudaMalloc(&op->logk, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    fcgno_op_destroy(op);
+    set_last_error("fcgno_assemble: out of device memory");
+    return FCGNO_ENOMEM;
+  }
+  const size_t total = op->n * batch;
+  assemble_kernel<<<ceil_div(total, 256), 256, 0, st>>>(N, op->n, total, k, op->aE, op->aN, op->diag, op->logk);
+  g_launches.fetch_add(1, std::memory_order_relaxed);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    set_last_error(std::string("assemble launch: ") + cudaGetErrorString(e));
+    fcgno_op_destroy(op);
+    return FCGNO_ECUDA;
+  }
+  *out = op;
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_apply_A(fcgno_op_t op, const double* x, double* y, void* stream) {
+  if (!op || !x || !y || x == y) {
+    set_last_error("fcgno_apply_A: null or aliasing arguments");
+    return FCGNO_EINVAL;
+  }
+  return launch_apply_A(op, x, y, (cudaStream_t)stream);
+}

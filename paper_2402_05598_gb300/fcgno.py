@@ -1,0 +1,227 @@
+"""Python binding of the C ABI in ``include/fcgno.h`` (ctypes; argument marshalling only).
+
+Functions keep the C names. Tensors are passed as raw device pointers (torch tensors
+must be contiguous float64/float32 CUDA tensors). Every computation happens inside
+``libfcgno.so``; importing this module on a machine without the built library raises.
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, Structure, c_char_p, c_double, c_int, c_int32, c_size_t, c_uint64, c_void_p
+from pathlib import Path
+
+import numpy as np
+
+_LIB_PATH = Path(__file__).resolve().parent / "libfcgno.so"
+
+FCGNO_OK, FCGNO_EINVAL, FCGNO_ENOMEM, FCGNO_ECUDA, FCGNO_ENOCONV, FCGNO_EBREAKDOWN, FCGNO_ETIMEOUT = range(7)
+FCGNO_FP64, FCGNO_BF16, FCGNO_FP16, FCGNO_FP32 = range(4)
+PREC = {"fp64": FCGNO_FP64, "bf16": FCGNO_BF16, "fp16": FCGNO_FP16, "fp32": FCGNO_FP32}
+
+
+class fcgno_model_desc(Structure):
+    _fields_ = [("width", c_int), ("layers", c_int), ("modes", c_int), ("proj_width", c_int), ("in_channels", c_int)]
+
+
+class fcgno_solve_opts(Structure):
+    _fields_ = [("tol", c_double), ("m_max", c_int), ("max_iter", c_int), ("fixed_iters", c_int),
+                ("check_every", c_int)]
+
+
+class fcgno_solve_info(Structure):
+    _fields_ = [("iters", c_int32), ("status", c_int32), ("relres", c_double), ("r0norm", c_double)]
+
+
+class FcgnoError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {status_str(code)} ({last_error()})")
+        self.code = code
+
+
+def _load():
+    if not _LIB_PATH.exists():
+        raise ImportError(f"{_LIB_PATH} is missing: run __graft_entry__.build() (the library has no CPU fallback)")
+    lib = ctypes.CDLL(str(_LIB_PATH))
+    P = c_void_p
+    sig = {
+        "fcgno_assemble": (c_int, [c_int, c_int, P, P, POINTER(P)]),
+        "fcgno_op_destroy": (c_int, [P]),
+        "fcgno_apply_A": (c_int, [P, P, P, P]),
+        "fcgno_weight_count": (c_size_t, [POINTER(fcgno_model_desc)]),
+        "fcgno_model_create": (c_int, [POINTER(fcgno_model_desc), P, P, POINTER(P)]),
+        "fcgno_model_sync": (c_int, [P, P]),
+        "fcgno_model_destroy": (c_int, [P]),
+        "fcgno_precond_apply": (c_int, [P, P, P, P, c_int, P]),
+        "fcgno_solve": (c_int, [P, P, P, P, POINTER(fcgno_solve_opts), c_int, POINTER(fcgno_solve_info), P]),
+        "fcgno_solve_host": (c_int, [c_int, c_int, P, P, P, P, POINTER(fcgno_solve_opts), c_int,
+                                     POINTER(fcgno_solve_info), P]),
+        "fcgno_krylov_harvest": (c_int, [P, P, P, P, c_int, P, P, POINTER(fcgno_solve_info), P]),
+        "fcgno_train_step": (c_int, [P, P, P, P, c_int, c_int, P, P, P]),
+        "fcgno_workspace_bytes": (c_size_t, [c_int, c_int, c_int, POINTER(fcgno_model_desc), c_int]),
+        "fcgno_status_str": (c_char_p, [c_int]),
+        "fcgno_last_error": (c_char_p, []),
+        "fcgno_launch_count": (c_uint64, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+lib = _load()
+
+# Exported symbol names, in the order of include/fcgno.h.
+EXPORTS = [
+    "fcgno_assemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
+    "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
+    "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_workspace_bytes", "fcgno_status_str",
+    "fcgno_last_error", "fcgno_launch_count",
+]
+
+
+def status_str(code: int) -> str:
+    return lib.fcgno_status_str(code).decode()
+
+
+def last_error() -> str:
+    return lib.fcgno_last_error().decode()
+
+
+def launch_count() -> int:
+    return int(lib.fcgno_launch_count())
+
+
+def _check(code: int, where: str):
+    if code != FCGNO_OK:
+        raise FcgnoError(code, where)
+
+
+def _ptr(t) -> int:
+    if t is None:
+        return None
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def make_desc(width=32, layers=4, modes=12, proj_width=None, in_channels=2) -> fcgno_model_desc:
+    return fcgno_model_desc(width, layers, modes, proj_width if proj_width is not None else width, in_channels)
+
+
+def weight_count(desc: fcgno_model_desc) -> int:
+    return int(lib.fcgno_weight_count(ctypes.byref(desc)))
+
+
+class Operator:
+    """fcgno_assemble handle over a [B][N][N] float64 CUDA tensor k."""
+
+    def __init__(self, k, stream=None):
+        import torch
+        assert k.dtype == torch.float64 and k.is_cuda and k.dim() == 3 and k.shape[1] == k.shape[2]
+        self.B, self.N = int(k.shape[0]), int(k.shape[1])
+        self.handle = c_void_p()
+        _check(lib.fcgno_assemble(self.N, self.B, _ptr(k), _stream(stream), ctypes.byref(self.handle)),
+               "fcgno_assemble")
+
+    def apply(self, x, y, stream=None):
+        _check(lib.fcgno_apply_A(self.handle, _ptr(x), _ptr(y), _stream(stream)), "fcgno_apply_A")
+
+    def close(self):
+        if self.handle:
+            lib.fcgno_op_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Model:
+    """fcgno_model_create handle; keeps a reference to the float32 CUDA weight blob."""
+
+    def __init__(self, desc: fcgno_model_desc, weights, stream=None):
+        import torch
+        assert weights.dtype == torch.float32 and weights.is_cuda and weights.numel() == weight_count(desc)
+        self.desc = desc
+        self.weights = weights
+        self.handle = c_void_p()
+        _check(lib.fcgno_model_create(ctypes.byref(desc), _ptr(weights), _stream(stream), ctypes.byref(self.handle)),
+               "fcgno_model_create")
+
+    def sync(self, stream=None):
+        _check(lib.fcgno_model_sync(self.handle, _stream(stream)), "fcgno_model_sync")
+
+    def close(self):
+        if self.handle:
+            lib.fcgno_model_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def precond_apply(model: Model, op: Operator, r, z, prec="bf16", stream=None):
+    _check(lib.fcgno_precond_apply(model.handle, op.handle, _ptr(r), _ptr(z), PREC[prec], _stream(stream)),
+           "fcgno_precond_apply")
+
+
+def _opts(tol, m_max, max_iter, fixed_iters, check_every):
+    return fcgno_solve_opts(float(tol), int(m_max), int(max_iter), int(bool(fixed_iters)), int(check_every))
+
+
+def _info_list(arr):
+    return [{"iters": int(i.iters), "status": int(i.status), "relres": float(i.relres), "r0norm": float(i.r0norm)}
+            for i in arr]
+
+
+def solve(op: Operator, model, b, x, tol=1e-6, m_max=1, max_iter=1000, prec="bf16", fixed_iters=False,
+          check_every=8, stream=None):
+    """fcgno_solve: x (u_0 on entry) is overwritten with the iterate; returns per-instance info."""
+    info = (fcgno_solve_info * op.B)()
+    opts = _opts(tol, m_max, max_iter, fixed_iters, check_every)
+    _check(lib.fcgno_solve(op.handle, model.handle if model is not None else None, _ptr(b), _ptr(x),
+                           ctypes.byref(opts), PREC[prec], info, _stream(stream)), "fcgno_solve")
+    return _info_list(info)
+
+
+def solve_host(k: np.ndarray, b: np.ndarray, x: np.ndarray, model=None, tol=1e-6, m_max=1, max_iter=1000,
+               prec="bf16", fixed_iters=False, check_every=8, stream=None):
+    """fcgno_solve_host on host float64 arrays [B][N][N] (x overwritten in place)."""
+    for a in (k, b, x):
+        assert a.dtype == np.float64 and a.flags["C_CONTIGUOUS"] and a.shape == k.shape
+    B, N = k.shape[0], k.shape[1]
+    info = (fcgno_solve_info * B)()
+    opts = _opts(tol, m_max, max_iter, fixed_iters, check_every)
+    _check(lib.fcgno_solve_host(N, B, k.ctypes.data, b.ctypes.data, x.ctypes.data,
+                                model.handle if model is not None else None, ctypes.byref(opts), PREC[prec], info,
+                                _stream(stream)), "fcgno_solve_host")
+    return _info_list(info)
+
+
+def krylov_harvest(op: Operator, b, x0, u_star, K, r_out, e_out, stream=None):
+    info = (fcgno_solve_info * op.B)()
+    _check(lib.fcgno_krylov_harvest(op.handle, _ptr(b), _ptr(x0), _ptr(u_star), int(K), _ptr(r_out), _ptr(e_out),
+                                    info, _stream(stream)), "fcgno_krylov_harvest")
+    return _info_list(info)
+
+
+def train_step(model: Model, op: Operator, r, e, loss, grad, prec="fp32", stream=None):
+    _check(lib.fcgno_train_step(model.handle, op.handle, _ptr(r), _ptr(e), op.B, PREC[prec], _ptr(loss), _ptr(grad),
+                                _stream(stream)), "fcgno_train_step")
+
+
+def workspace_bytes(N, batch, m_max, desc, prec="bf16") -> int:
+    return int(lib.fcgno_workspace_bytes(int(N), int(batch), int(m_max), ctypes.byref(desc), PREC[prec]))

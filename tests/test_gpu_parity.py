@@ -1,0 +1,198 @@
+"""GPU parity: the CUDA path (called through the C ABI) against the FP64 oracle on the same
+seeded inputs. Sizes span several tiles and ragged tails; tolerances are stated per test."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import fcgno_oracle as O
+from paper_2402_05598_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def to_dev(x, dev, dtype=None):
+    import torch
+    t = torch.from_numpy(np.ascontiguousarray(x))
+    if dtype is not None:
+        t = t.to(dtype)
+    return t.to(dev)
+
+
+def batch(N, B, seed0, sigma=1.0, ell=0.1):
+    return I.make_batch(N, range(seed0, seed0 + B), sigma, ell)
+
+
+def model_pair(lib, dev, C, M, L=4, seed=0):
+    desc_np = I.ModelDesc(width=C, layers=L, modes=M, proj_width=C)
+    blob = I.xavier_weights(desc_np, seed)
+    # give the biases nonzero values so that every parameter is exercised
+    off = I.weight_offsets(desc_np)
+    rng = np.random.default_rng(seed + 77)
+    for name in ["lift_b", "proj1_b", "proj2_b"] + [f"b{l}" for l in range(L)]:
+        o, s = off[name]
+        blob[o:o + s] = rng.uniform(-0.3, 0.3, s)
+    wdev = to_dev(blob, dev)
+    model = lib.Model(lib.make_desc(C, L, M, C), wdev)
+    return desc_np, O.unpack_weights(blob, desc_np), model, wdev
+
+
+# ------------------------------------------------------------------------------- stencil
+@pytest.mark.parametrize("N,B", [(8, 3), (33, 2), (64, 2), (130, 1)])
+def test_stencil_matches_oracle(lib, dev, N, B):
+    import torch
+    k, f = batch(N, B, 100 + N)
+    op = lib.Operator(to_dev(k, dev))
+    y = torch.empty_like(to_dev(f, dev))
+    op.apply(to_dev(f, dev), y)
+    torch.cuda.synchronize()
+    for b in range(B):
+        assert rel(y[b].cpu().numpy(), O.apply_A(k[b], f[b])) < 1e-14
+
+
+# ------------------------------------------------------------------------------- CG / FCG(B=I)
+@pytest.mark.parametrize("N,B,m", [(33, 2, 1), (64, 3, 5), (100, 2, 1), (130, 1, 3)])
+def test_identity_preconditioned_iterates_match_oracle(lib, dev, N, B, m):
+    """Fused path (N <= 90) and tiled path (N > 90): 20 fixed iterations of Algorithm 1 with
+    B = I, iterate compared with the oracle (rel 1e-10)."""
+    import torch
+    k, f = batch(N, B, 200 + N)
+    x0 = np.random.default_rng(N).standard_normal((B, N, N))
+    op = lib.Operator(to_dev(k, dev))
+    x = to_dev(x0, dev)
+    info = lib.solve(op, None, to_dev(f, dev), x, m_max=m, max_iter=20, fixed_iters=True, prec="fp64")
+    xs = x.cpu().numpy()
+    for b in range(B):
+        ref = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: r, f[b], x0[b], m, 20)
+        assert info[b]["iters"] == 20
+        assert rel(xs[b], ref["u"]) < 1e-10
+        assert abs(info[b]["relres"] - ref["relres"][-1]) <= 1e-8 * ref["relres"][-1]
+
+
+def test_identity_solve_to_tolerance_and_zero_rhs(lib, dev):
+    """A zero right-hand side converges at iteration 0 while its batch-mates iterate on."""
+    N, B = 48, 3
+    k, f = batch(N, B, 300)
+    f[1] = 0.0
+    op = lib.Operator(to_dev(k, dev))
+    x = to_dev(np.zeros((B, N, N)), dev)
+    info = lib.solve(op, None, to_dev(f, dev), x, tol=1e-8, m_max=1, max_iter=3000, prec="fp64")
+    assert info[1]["iters"] == 0 and info[1]["status"] == lib.FCGNO_OK
+    xs = x.cpu().numpy()
+    for b in (0, 2):
+        ref = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: r, f[b], np.zeros((N, N)), 1, 3000, tol=1e-8)
+        assert info[b]["status"] == lib.FCGNO_OK
+        # several hundred iterations: rounding order may move the stopping iteration by ~1%
+        assert abs(info[b]["iters"] - ref["iterations"]) <= max(2, ref["iterations"] // 100)
+        assert info[b]["relres"] <= 1e-8
+        true_res = np.linalg.norm(f[b] - O.apply_A(k[b], xs[b])) / np.linalg.norm(f[b])
+        assert true_res <= 1e-7
+
+
+# ------------------------------------------------------------------------------- preconditioner
+@pytest.mark.parametrize("N,C,M,B", [(32, 16, 8, 2), (20, 8, 5, 3), (64, 32, 12, 2)])
+def test_fp64_preconditioner_matches_oracle(lib, dev, N, C, M, B):
+    import torch
+    k, r = batch(N, B, 400 + N)
+    desc, P, model, _w = model_pair(lib, dev, C, M)
+    op = lib.Operator(to_dev(k, dev))
+    z = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    lib.precond_apply(model, op, to_dev(r, dev), z, prec="fp64")
+    zs = z.cpu().numpy()
+    for b in range(B):
+        assert rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b]))) < 1e-12
+
+
+@pytest.mark.parametrize("N,C,M,B", [(32, 16, 8, 2), (64, 32, 12, 2)])
+def test_fp32_preconditioner_matches_oracle(lib, dev, N, C, M, B):
+    import torch
+    k, r = batch(N, B, 500 + N)
+    desc, P, model, _w = model_pair(lib, dev, C, M)
+    op = lib.Operator(to_dev(k, dev))
+    z = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    lib.precond_apply(model, op, to_dev(r, dev), z, prec="fp32")
+    zs = z.cpu().numpy()
+    for b in range(B):
+        assert rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b]))) < 2e-5
+
+
+def test_fcg_no_fp64_thirty_iterations_match_oracle(lib, dev):
+    """Plain FCG-NO parity workload: N = 32, one instance, k = exp(GRF(0.1, 1)), f ~ N(0,1),
+    x0 = 0, NO width 16, 4 layers, 8 modes, Xavier seed 0, m = 1; 30 fixed iterations,
+    iterate within 1e-10 of the oracle; then an identity-preconditioned solve to 1e-8."""
+    import torch
+    N = 32
+    k, f = I.make_problem(N, 1000)
+    k, f = k[None], f[None]
+    desc = I.ModelDesc(width=16, layers=4, modes=8, proj_width=16)
+    blob = I.xavier_weights(desc, 0)
+    P = O.unpack_weights(blob, desc)
+    wdev = to_dev(blob, dev)
+    model = lib.Model(lib.make_desc(16, 4, 8, 16), wdev)
+    op = lib.Operator(to_dev(k, dev))
+    x = torch.zeros((1, N, N), dtype=torch.float64, device=dev)
+    info = lib.solve(op, model, to_dev(f, dev), x, m_max=1, max_iter=30, fixed_iters=True, prec="fp64")
+    ref = O.fcg(lambda u: O.apply_A(k[0], u), lambda r: O.no_forward(P, desc, r, np.log(k[0])), f[0],
+                np.zeros((N, N)), 1, 30)
+    assert info[0]["iters"] == 30
+    assert rel(x[0].cpu().numpy(), ref["u"]) < 1e-10
+    x.zero_()
+    info = lib.solve(op, None, to_dev(f, dev), x, tol=1e-8, m_max=1, max_iter=5000, prec="fp64")
+    ref = O.fcg(lambda u: O.apply_A(k[0], u), lambda r: r, f[0], np.zeros((N, N)), 1, 5000, tol=1e-8)
+    assert info[0]["status"] == lib.FCGNO_OK
+    assert abs(info[0]["iters"] - ref["iterations"]) <= max(2, ref["iterations"] // 100)
+    assert rel(x[0].cpu().numpy(), ref["u"]) < 1e-7
+
+
+@pytest.mark.parametrize("N,m", [(40, 5), (96, 2)])
+def test_fcg_no_fp64_window_matches_oracle(lib, dev, N, m):
+    """Truncation window m > 1 on the fused (N = 40) and tiled (N = 96) paths."""
+    import torch
+    B = 2
+    k, f = batch(N, B, 600 + N)
+    desc, P, model, _w = model_pair(lib, dev, 8, 4, L=2, seed=5)
+    op = lib.Operator(to_dev(k, dev))
+    x = torch.zeros((B, N, N), dtype=torch.float64, device=dev)
+    lib.solve(op, model, to_dev(f, dev), x, m_max=m, max_iter=12, fixed_iters=True, prec="fp64")
+    xs = x.cpu().numpy()
+    for b in range(B):
+        ref = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: O.no_forward(P, desc, r, np.log(k[b])), f[b],
+                    np.zeros((N, N)), m, 12)
+        assert rel(xs[b], ref["u"]) < 1e-10
+
+
+def test_solve_host_matches_device_solve(lib, dev):
+    import torch
+    N, B = 24, 2
+    k, f = batch(N, B, 700)
+    x_host = np.zeros((B, N, N))
+    info_h = lib.solve_host(k, f, x_host, None, tol=1e-9, m_max=1, max_iter=2000, prec="fp64")
+    op = lib.Operator(to_dev(k, dev))
+    x = torch.zeros((B, N, N), dtype=torch.float64, device=dev)
+    info_d = lib.solve(op, None, to_dev(f, dev), x, tol=1e-9, m_max=1, max_iter=2000, prec="fp64")
+    assert [i["iters"] for i in info_h] == [i["iters"] for i in info_d]
+    assert np.array_equal(x_host, x.cpu().numpy())
+
+
+def test_krylov_harvest_matches_oracle_cg(lib, dev):
+    """Eq. (9): residuals r_i and errors e_i = u* - u_i of CG from u_0 ~ N(0, 1)."""
+    import torch
+    N, B, K = 16, 2, 6
+    k, f = batch(N, B, 800)
+    x0 = np.random.default_rng(3).standard_normal((B, N, N))
+    ustar = np.stack([np.linalg.solve(O.dense_A(k[b]), f[b].ravel()).reshape(N, N) for b in range(B)])
+    op = lib.Operator(to_dev(k, dev))
+    r_out = torch.empty((K, B, N, N), dtype=torch.float64, device=dev)
+    e_out = torch.empty_like(r_out)
+    lib.krylov_harvest(op, to_dev(f, dev), to_dev(x0, dev), to_dev(ustar, dev), K, r_out, e_out)
+    rs, es = r_out.cpu().numpy(), e_out.cpu().numpy()
+    for b in range(B):
+        ref = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: r, f[b], x0[b], 1, K, record=True)
+        for i in range(K):
+            assert rel(rs[i, b], ref["rs"][i + 1]) < 1e-11
+            assert rel(es[i, b], ustar[b] - ref["us"][i + 1]) < 1e-11
