@@ -196,3 +196,46 @@ def test_krylov_harvest_matches_oracle_cg(lib, dev):
         for i in range(K):
             assert rel(rs[i, b], ref["rs"][i + 1]) < 1e-11
             assert rel(es[i, b], ustar[b] - ref["us"][i + 1]) < 1e-11
+
+
+# ------------------------------------------------------------------------------- tensor cores
+@pytest.mark.parametrize("N,C,M,B,prec,tol", [
+    (32, 16, 8, 2, "bf16", 2e-2),
+    (64, 32, 12, 3, "bf16", 2e-2),
+    (64, 32, 12, 2, "fp16", 4e-3),
+    (128, 32, 12, 2, "bf16", 2e-2),
+    (64, 32, 16, 2, "bf16", 2e-2),
+])
+def test_tensor_core_preconditioner_matches_oracle(lib, dev, N, C, M, B, prec, tol):
+    """tcgen05 BF16/FP16 preconditioner (FP32 accumulation) against the FP64 oracle:
+    relative 2-norm error per instance within 2e-2 (BF16) / 4e-3 (FP16)."""
+    import torch
+    k, r = batch(N, B, 900 + N + M)
+    desc, P, model, _w = model_pair(lib, dev, C, M)
+    op = lib.Operator(to_dev(k, dev))
+    z = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    lib.precond_apply(model, op, to_dev(r, dev), z, prec=prec)
+    zs = z.cpu().numpy()
+    for b in range(B):
+        err = rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b])))
+        assert err < tol, (b, err)
+
+
+def test_tensor_core_preconditioner_inside_solve(lib, dev):
+    """Algorithm 1 with the BF16 preconditioner: every iterate keeps the exact line-search
+    property (monotone energy error), and instances that stop leave their batch-mates intact."""
+    import torch
+    N, B = 64, 3
+    k, f = batch(N, B, 1200)
+    f[2] = 0.0
+    desc, P, model, _w = model_pair(lib, dev, 32, 12)
+    op = lib.Operator(to_dev(k, dev))
+    x = torch.zeros((B, N, N), dtype=torch.float64, device=dev)
+    info = lib.solve(op, model, to_dev(f, dev), x, m_max=1, max_iter=15, fixed_iters=True, prec="bf16")
+    assert info[2]["iters"] == 0
+    for b in range(2):
+        assert info[b]["iters"] == 15 and np.isfinite(info[b]["relres"])
+        ustar = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: r, f[b], np.zeros((N, N)), 1, 4000, tol=1e-12)["u"]
+        e15 = O.energy_norm(k[b], ustar - x[b].cpu().numpy())
+        e0 = O.energy_norm(k[b], ustar)
+        assert e15 <= e0
