@@ -1,0 +1,380 @@
+"""Benchmark: FCG-NO solves/s to relative residual 1e-6 on one GB300 (or N replicas).
+
+Workload (the training-plus-solve configuration on a 64 x 64 grid): 256 held-out diffusion
+instances (seeds 10000 + 256*rank + i), k = exp(GRF(length 0.1, sigma 1)), f iid N(0, 1),
+u_0 iid N(0, 1) (Algorithm 1), FNO preconditioner of width 32, 4 Fourier layers, 12 x 12
+modes, trained in the setup phase with the energy-norm loss on Krylov vectors harvested
+from CG on seeded training instances. One step = one batched solve of all 256 instances to
+||r_i|| <= 1e-6 ||r_0|| (truncation m = 1) with the BF16 tensor-core preconditioner and the
+FP64 Krylov loop. Inputs are resident in HBM when a timed step starts; L2 is flushed
+(256 MB write) between timed steps.
+
+--impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N_GRID = 64
+WIDTH, LAYERS, MODES = 32, 4, 12
+EVAL_BATCH = 256
+TOL = 1e-6
+METRIC = "solves/s to rel-residual 1e-6 (BF16-NO FCG, FP64 Krylov loop)"
+UNIT = "solves/s"
+
+
+# --------------------------------------------------------------------------------------- clocks
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": float(max(smax)), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------------------- oracle
+def _oracle_worker(args):
+    """One instance of the workload solved by the FP64 CPU oracle (runs in a spawned process)."""
+    N, seed, blob, m_max, max_iter, fixed_iters = args
+    os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
+    from oracle import fcgno_oracle as O
+    from paper_2402_05598_gb300 import inputs as I
+    desc = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=MODES, proj_width=WIDTH)
+    P = O.unpack_weights(blob, desc)
+    k, f = I.make_problem(N, seed)
+    u0 = np.random.default_rng(seed + 777).standard_normal((N, N))
+    lk = np.log(k)
+    t = time.perf_counter()
+    out = O.fcg(lambda u: O.apply_A(k, u), lambda r: O.no_forward(P, desc, r, lk), f, u0, m_max, max_iter,
+                tol=None if fixed_iters else TOL)
+    return time.perf_counter() - t, out["iterations"]
+
+
+def oracle_sample(blob: np.ndarray, n_inst: int, iters: int, cores: int):
+    """Times the oracle FCG-NO on n_inst instances, `iters` fixed iterations each, in a pool of
+    `cores` spawned single-threaded processes. Returns (wall seconds, total iterations)."""
+    import multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    env_old = {k: os.environ.get(k) for k in ("OPENBLAS_NUM_THREADS", "OMP_NUM_THREADS", "MKL_NUM_THREADS")}
+    for k in env_old:
+        os.environ[k] = "1"
+    try:
+        jobs = [(N_GRID, 10000 + i, blob, 1, iters, True) for i in range(n_inst)]
+        t = time.perf_counter()
+        with ctx.Pool(processes=cores) as pool:
+            res = pool.map(_oracle_worker, jobs)
+        wall = time.perf_counter() - t
+    finally:
+        for k, v in env_old.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return wall, sum(r[1] for r in res)
+
+
+# --------------------------------------------------------------------------------------- helpers
+def roofline_synthesis(active_per_iter, N, C, M, layers):
+    """Algorithmic HBM bytes of all synthesis launches: per active instance and layer, read
+    the layer input (n*C*2 B) and the mixed coefficients (M*C*4M*2 B); hidden layers write
+    the next activation (n*C*2 B), the last layer writes z (n*8 B)."""
+    n = N * N
+    chat = M * C * 4 * M * 2
+    hidden = 2 * n * C * 2 + chat
+    last = n * C * 2 + chat + n * 8
+    per_inst = (layers - 1) * hidden + last
+    return float(sum(active_per_iter)) * per_inst, int(len(active_per_iter)) * layers
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    from paper_2402_05598_gb300 import inputs as I
+    cores = min(16, os.cpu_count() or 1)
+    desc = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=MODES, proj_width=WIDTH)
+    blob = I.xavier_weights(desc, 0)
+    iters = args.ref_iters
+    vals = []
+    for s in range(args.warmup + args.steps):
+        wall, tot_it = oracle_sample(blob, cores, iters, cores)
+        if s >= args.warmup:
+            vals.append((wall, tot_it))
+    wall = sum(v[0] for v in vals)
+    n_inst = cores * args.steps
+    value = n_inst / wall
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"FCG-NO eval, {N_GRID}x{N_GRID} diffusion, width {WIDTH}, {LAYERS} layers, "
+                                   f"{MODES}x{MODES} modes, m=1, tol 1e-6", "grid": N_GRID},
+            "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores,
+                             "sample": f"{cores} instances per step, {iters} FCG-NO iterations each (the GPU arm's "
+                                       f"iterations per solve), one single-threaded process per core"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+# --------------------------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16"])
+    ap.add_argument("--m", type=int, default=1)
+    ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--train-instances", type=int, default=256)
+    ap.add_argument("--max-iter", type=int, default=2000)
+    ap.add_argument("--ref-iters", type=int, default=60)
+    ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("nccl", rank=rank, world_size=world, device_id=dev)
+    from paper_2402_05598_gb300 import fcgno as F
+    from paper_2402_05598_gb300 import inputs as I
+    from paper_2402_05598_gb300 import train as T
+
+    # ---- setup: model, training (untimed)
+    desc_np = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=MODES, proj_width=WIDTH)
+    blob = torch.from_numpy(I.xavier_weights(desc_np, 0)).to(dev)
+    model = F.Model(F.make_desc(WIDTH, LAYERS, MODES, WIDTH), blob)
+    tr = None
+    if args.train_steps > 0:
+        tr = T.train(model, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3, steps=args.train_steps)
+
+    # ---- eval inputs (resident)
+    seeds = range(10000 + EVAL_BATCH * rank, 10000 + EVAL_BATCH * (rank + 1))
+    k_np, f_np = I.make_batch(N_GRID, seeds)
+    u0_np = np.stack([np.random.default_rng(s + 777).standard_normal((N_GRID, N_GRID)) for s in seeds])
+    k = torch.from_numpy(k_np).to(dev)
+    f = torch.from_numpy(f_np).to(dev)
+    u0 = torch.from_numpy(u0_np).to(dev)
+    op = F.Operator(k)
+    x = torch.empty_like(u0)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def solve_once():
+        x.copy_(u0)
+        return F.solve(op, model, f, x, tol=TOL, m_max=args.m, max_iter=args.max_iter, prec=args.prec,
+                       check_every=4)
+
+    for _ in range(args.warmup):
+        info = solve_once()
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+
+    # ---- timed region
+    clocks = ClockSampler(local)
+    clocks.start()
+    time.sleep(0.4)
+    F.trace_set("tc_synthesis")
+    F.trace_collect()
+    launches0 = F.launch_count()
+    step_ms = []
+    infos = []
+    for s in range(args.steps):
+        flush.fill_(float(s))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        infos.append(solve_once())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+    launches = F.launch_count() - launches0
+    syn_ms, syn_launches = F.trace_collect()
+    F.trace_set("")
+    clk = clocks.stop()
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(t.item())
+    solved = sum(sum(1 for i in inf if i["status"] == F.FCGNO_OK) for inf in infos)
+    iters = [i["iters"] for i in infos[-1]]
+    value = EVAL_BATCH * world * args.steps / (total_ms / 1000.0)
+
+    # ---- roofline of the dominant kernel (synthesis): algorithmic bytes / traced device time
+    max_it = max(iters)
+    active = [sum(1 for it in iters if it > i) for i in range(max_it)]
+    alg_bytes_one, syn_per_step = roofline_synthesis(active, N_GRID, WIDTH, MODES, LAYERS)
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peak, peak_src = 6800.0, "fallback"
+    if os.path.exists(peaks_path):
+        with open(peaks_path) as fh:
+            peak, peak_src = float(json.load(fh)["hbm_gbs"]), "measured"
+    syn_avg_ms = syn_ms / max(syn_launches, 1)
+    achieved = alg_bytes_one * args.steps / (syn_ms / 1000.0) / 1e9 if syn_ms > 0 else None
+
+    # ---- kernel shares over one more (untimed) step per family
+    shares = {}
+    for fam in ("tc_synthesis", "tc_analysis", "tc_mix", "tc_lift", "fcg_fused"):
+        F.trace_set(fam)
+        F.trace_collect()
+        solve_once()
+        ms, cnt = F.trace_collect()
+        shares[fam] = {"ms": round(ms, 3), "launches": cnt}
+    F.trace_set("")
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16" if args.prec == "bf16" else "f16", "data": "synthetic",
+            "config": {"workload": f"FCG-NO eval: {EVAL_BATCH} instances/GPU, {N_GRID}x{N_GRID} diffusion "
+                                   f"(k=exp(GRF 0.1, 1)), FNO width {WIDTH}, {LAYERS} layers, {MODES}x{MODES} modes, "
+                                   f"m={args.m}, tol {TOL}", "grid": N_GRID, "instances_per_gpu": EVAL_BATCH,
+                       "l2": "flushed (256 MB write) between timed steps",
+                       "training": None if tr is None else {"steps": tr.steps, "batch": 32, "instances":
+                                                            args.train_instances, "krylov_K": 100,
+                                                            "seconds": round(tr.seconds, 2)},
+                       "parallelism": f"replicas x{world}"},
+            "iterations": {"mean": float(np.mean(iters)), "max": int(max(iters)), "converged": solved,
+                           "solves": EVAL_BATCH * args.steps},
+            "unknowns_iterations_per_s": float(np.sum(iters)) * N_GRID * N_GRID * world / (step_ms[-1] / 1000.0),
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": {"kernel": "tc_synthesis_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
+                         "peak_source": peak_src, "unit": "GB/s",
+                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "avg_launch_ms": syn_avg_ms, "launches": syn_launches},
+            "kernel_ms_one_step": shares}
+
+    # ---- comparison paths on the same instances (untimed here, reported for context)
+    if rank == 0:
+        sub = 32
+        op_s = F.Operator(k[:sub].contiguous())
+        xs = u0[:sub].clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        inf64 = F.solve(op_s, model, f[:sub].contiguous(), xs, tol=TOL, m_max=args.m, max_iter=args.max_iter,
+                        prec="fp64", check_every=4)
+        torch.cuda.synchronize()
+        t64 = time.perf_counter() - t0
+        line["fp64_no"] = {"value": sub / t64, "unit": UNIT, "instances": sub,
+                           "iterations_mean": float(np.mean([i["iters"] for i in inf64]))}
+        xs = u0[:sub].clone()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        infcg = F.solve(op_s, None, f[:sub].contiguous(), xs, tol=TOL, m_max=1, max_iter=20000, prec="fp64",
+                        check_every=16)
+        torch.cuda.synchronize()
+        tcg = time.perf_counter() - t0
+        line["cg"] = {"value": sub / tcg, "unit": UNIT, "instances": sub,
+                      "iterations_mean": float(np.mean([i["iters"] for i in infcg]))}
+
+    # ---- end to end through the host-buffer entry point
+    kh = torch.from_numpy(k_np).pin_memory()
+    fh = torch.from_numpy(f_np).pin_memory()
+    xh = torch.from_numpy(u0_np).pin_memory()
+    e2e_t = 0.0
+    for s in range(args.e2e_steps + 1):
+        xh.copy_(torch.from_numpy(u0_np))
+        t0 = time.perf_counter()
+        F.solve_host(kh.numpy(), fh.numpy(), xh.numpy(), model, tol=TOL, m_max=args.m, max_iter=args.max_iter,
+                     prec=args.prec, check_every=4)
+        if s > 0:
+            e2e_t += time.perf_counter() - t0
+    vec = EVAL_BATCH * N_GRID * N_GRID * 8
+    line["e2e"] = {"value": EVAL_BATCH * world * args.e2e_steps / e2e_t, "unit": UNIT,
+                   "h2d_bytes_per_step": 3 * vec, "d2h_bytes_per_step": vec}
+
+    # ---- CPU oracle baseline (bounded sample)
+    if rank == 0 and args.cpu_baseline:
+        cores = min(16, os.cpu_count() or 1)
+        it_solve = max(1, int(round(np.mean(iters))))
+        # the oracle's cost per iteration does not depend on the weight values: it runs the seeded
+        # initial weights (no value produced by the CUDA path enters the oracle)
+        wall, tot_it = oracle_sample(I.xavier_weights(desc_np, 0), cores, it_solve, cores)
+        line["cpu_baseline"] = {"kind": "oracle", "value": cores / wall, "unit": UNIT, "cores": cores,
+                                "sample": f"{cores} instances, {it_solve} FCG-NO iterations each (the GPU solve's "
+                                          f"mean iterations per solve), FP64 numpy oracle, one single-threaded "
+                                          f"process per core"}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -100,7 +100,8 @@ fcgno_status fcgno_model_sync(fcgno_model_t model, void* stream);
 fcgno_status fcgno_model_destroy(fcgno_model_t model);
 
 /* z = NO(r, log k) for every instance of op (Algorithm 1, w_i = B(r_i); Appendix A):
- * z = rms(r) * decoder(Fourier layers(encoder(r / rms(r), log k))), z = 0 where r = 0.
+ * z = h^2 rms(r) * decoder(Fourier layers(encoder(r / rms(r), log k))), z = 0 where r = 0
+ * (h = 1/(N+1); the h^2 factor gives the output the units of A^-1).
  * r, z: [batch][N][N]. prec selects the arithmetic (FP64, FP32, BF16, FP16).
  * Errors: EINVAL if N < 2*modes or the precision is unsupported. */
 fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, const double* r, double* z,
@@ -148,6 +149,14 @@ const char* fcgno_status_str(fcgno_status s);
 const char* fcgno_last_error(void);
 /* Number of CUDA kernels this library has launched since load (all threads). */
 uint64_t fcgno_launch_count(void);
+
+/* Kernel tracing (not part of the method): select a kernel family by name ("tc_synthesis",
+ * "tc_analysis", "tc_mix", "tc_lift", "fcg_fused", "fcg_tiled", "" = off). Every later launch
+ * of that family is bracketed by two CUDA events recorded on its launch stream.
+ * fcgno_trace_collect waits for the recorded events and returns the summed device time
+ * (ms) and the number of traced launches since the previous collect. */
+fcgno_status fcgno_trace_set(const char* family);
+fcgno_status fcgno_trace_collect(double* total_ms, uint64_t* launches);
 
 #ifdef __cplusplus
 }

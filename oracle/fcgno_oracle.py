@@ -20,8 +20,11 @@ Readings of points the paper leaves open (the same readings the library implemen
 - Section 2.4.2 / Appendix A (neural operator): Fourier layers
   v <- act(W v + b + Re S R A v), act = GELU on all but the last layer, an encoder
   (lift, 2 -> C, linear) and a decoder (C -> C_p, GELU, -> 1) with C_p = C; the input
-  channels are (r / rms(r), log k) and the output is rescaled by rms(r), so the map is
-  positively homogeneous in r and returns 0 for r = 0.
+  channels are (r / rms(r), log k) and the output is rescaled by h^2 rms(r), so the map is
+  positively homogeneous in r and returns 0 for r = 0. The h^2 factor gives the network
+  output the units of A^-1 (A carries 1/h^2); FCG is invariant to a constant scale of w_i,
+  so it only conditions the training loss, whose target e = A^-1 r is ~h^2 r at high
+  frequencies.
 - Retained modes: x1-frequencies 0..M-1 and -M..-1, x2-frequencies 0..M-1. Analysis
   c(k) = (1/n) sum_x v(x) exp(-2 pi i k.x / N), synthesis
   v(x) = Re sum_k w_k2 c(k) exp(+2 pi i k.x / N) with w_0 = 1, w_{k2>0} = 2.
@@ -55,6 +58,10 @@ __all__ = [
     "l2_loss",
     "jacobi_precond",
     "energy_norm",
+    "synthesis_adjoint",
+    "analysis_adjoint",
+    "gelu_grad",
+    "notay_loss_and_grad",
 ]
 
 STATUS_RUNNING = -1
@@ -365,7 +372,7 @@ def no_forward(params: dict, desc, r: np.ndarray, logk: np.ndarray) -> np.ndarra
 
     r, logk: [N][N]. Encoder: v0 = lift_w [r/rms, log k] + lift_b. Processor: the Fourier
     layers, GELU after all but the last. Decoder: proj2_w . GELU(proj1_w v + proj1_b) +
-    proj2_b. Output multiplied back by rms(r); zero when r = 0.
+    proj2_b. Output multiplied by h^2 rms(r); zero when r = 0.
     """
     rms = math.sqrt(float(np.mean(r * r)))
     if rms == 0.0:
@@ -377,7 +384,7 @@ def no_forward(params: dict, desc, r: np.ndarray, logk: np.ndarray) -> np.ndarra
         v = fourier_layer(v, layer, desc.modes, activate=(l < L - 1))
     hid = gelu(v @ params["proj1_w"].T + params["proj1_b"])
     zt = hid @ params["proj2_w"] + params["proj2_b"][0]
-    return rms * zt
+    return grid_h(r.shape[0]) ** 2 * rms * zt
 
 
 # ---------------------------------------------------------------------------------------
@@ -393,3 +400,102 @@ def l2_loss(zs, es) -> float:
     """Eq. (12): mean over samples of ||z - e||_2 / ||e||_2."""
     vals = [np.linalg.norm(z - e) / np.linalg.norm(e) for z, e in zip(zs, es)]
     return float(np.mean(vals))
+
+
+# ---------------------------------------------------------------------------------------
+# Training gradient of the energy-norm loss (Eq. (11)), hand-written reverse mode
+# ---------------------------------------------------------------------------------------
+def synthesis_adjoint(g: np.ndarray, M: int) -> np.ndarray:
+    """Adjoint of ``synthesis`` w.r.t. its complex input read as (re, im) pairs:
+    dc(k) = w_k2 sum_x g(x) exp(-2 pi i k.x / N), g: [N][N][C] -> [2M][M][C]."""
+    N = g.shape[0]
+    E1 = _twiddle(kx_frequencies(M), N, -1.0)
+    E2 = _twiddle(np.arange(M), N, -1.0)
+    w = np.full(M, 2.0)
+    w[0] = 1.0
+    t = np.tensordot(E2, g, axes=([1], [0]))
+    c = np.tensordot(E1, t, axes=([1], [1]))
+    return c * w[None, :, None]
+
+
+def analysis_adjoint(dc: np.ndarray, N: int) -> np.ndarray:
+    """Adjoint of ``analysis`` (real input) w.r.t. its (re, im) outputs:
+    dv(x) = (1/n) sum_k Re(dc(k) exp(+2 pi i k.x / N)), dc: [2M][M][C] -> [N][N][C]."""
+    M = dc.shape[1]
+    F1 = _twiddle(kx_frequencies(M), N, 1.0)
+    F2 = _twiddle(np.arange(M), N, 1.0)
+    t = np.tensordot(F1, dc, axes=([0], [0]))
+    v = np.tensordot(F2, t, axes=([0], [1]))
+    return np.real(v) / (N * N)
+
+
+def gelu_grad(x: np.ndarray) -> np.ndarray:
+    """d/dx GELU(x) = Phi(x) + x phi(x)."""
+    return 0.5 * (1.0 + erf(x / math.sqrt(2.0))) + x * np.exp(-0.5 * x * x) / math.sqrt(2.0 * math.pi)
+
+
+def _forward_saved(params: dict, desc, r: np.ndarray, logk: np.ndarray) -> dict:
+    rms = math.sqrt(float(np.mean(r * r)))
+    x0 = np.stack([r / rms, logk], axis=-1)
+    v = x0 @ params["lift_w"].T + params["lift_b"]
+    vs, hs, cs = [v], [], []
+    L = len(params["layers"])
+    for l, layer in enumerate(params["layers"]):
+        c = analysis(v, desc.modes)
+        h = v @ layer["w"].T + layer["b"] + synthesis(mode_mix(c, layer["r"]), v.shape[0])
+        v = gelu(h) if l < L - 1 else h
+        cs.append(c)
+        hs.append(h)
+        vs.append(v)
+    a = v @ params["proj1_w"].T + params["proj1_b"]
+    g = gelu(a)
+    zt = g @ params["proj2_w"] + params["proj2_b"][0]
+    scale = grid_h(r.shape[0]) ** 2 * rms
+    return {"rms": rms, "scale": scale, "x0": x0, "vs": vs, "hs": hs, "cs": cs, "a": a, "g": g, "z": scale * zt}
+
+
+def notay_loss_and_grad(params: dict, desc, ks, rs, es):
+    """Eq. (11) over a batch: L = mean_j ||z_j - e_j||_A / ||e_j||_A with z_j = NO(r_j, log k_j),
+    and dL/d(weights) as a flat float64 array in the weight-blob order.
+
+    dL/dz_j = A (z_j - e_j) / (||z_j - e_j||_A ||e_j||_A) / batch; the rest is the chain rule
+    through the decoder, the Fourier layers (pointwise path, the per-mode mixing and the
+    adjoints of the truncated transforms) and the encoder.
+    """
+    L = len(params["layers"])
+    grads = {k: np.zeros_like(params[k]) for k in ("lift_w", "lift_b", "proj1_w", "proj1_b", "proj2_w", "proj2_b")}
+    glayers = [{"w": np.zeros_like(p["w"]), "b": np.zeros_like(p["b"]), "r": np.zeros_like(p["r"])}
+               for p in params["layers"]]
+    B = len(ks)
+    loss = 0.0
+    for k, r, e in zip(ks, rs, es):
+        S = _forward_saved(params, desc, r, np.log(k))
+        d = S["z"] - e
+        Ad = apply_A(k, d)
+        nd = math.sqrt(float(np.sum(d * Ad)))
+        ne = energy_norm(k, e)
+        loss += nd / ne / B
+        dz = Ad / (nd * ne) / B
+        dzt = S["scale"] * dz
+        grads["proj2_w"] += np.einsum("qp,qph->h", dzt, S["g"])
+        grads["proj2_b"] += np.sum(dzt)
+        da = dzt[..., None] * params["proj2_w"] * gelu_grad(S["a"])
+        grads["proj1_w"] += np.einsum("qph,qpc->hc", da, S["vs"][L])
+        grads["proj1_b"] += np.sum(da, axis=(0, 1))
+        dv = da @ params["proj1_w"]
+        for l in range(L - 1, -1, -1):
+            layer = params["layers"][l]
+            dh = dv * gelu_grad(S["hs"][l]) if l < L - 1 else dv
+            glayers[l]["w"] += np.einsum("qpo,qpi->oi", dh, S["vs"][l])
+            glayers[l]["b"] += np.sum(dh, axis=(0, 1))
+            dcp = synthesis_adjoint(dh, desc.modes)                              # d/d c'
+            glayers[l]["r"] += np.einsum("jki,jko->jkio", np.conj(S["cs"][l]), dcp)
+            dc = np.einsum("jkio,jko->jki", np.conj(layer["r"]), dcp)             # d/d c
+            dv = dh @ layer["w"] + analysis_adjoint(dc, r.shape[0])
+        grads["lift_w"] += np.einsum("qpc,qpi->ci", dv, S["x0"])
+        grads["lift_b"] += np.sum(dv, axis=(0, 1))
+    parts = [grads["lift_w"].ravel(), grads["lift_b"].ravel()]
+    for gl in glayers:
+        parts += [gl["w"].ravel(), gl["b"].ravel(), np.stack([gl["r"].real, gl["r"].imag], axis=-1).ravel()]
+    parts += [grads["proj1_w"].ravel(), grads["proj1_b"].ravel(), grads["proj2_w"].ravel(), grads["proj2_b"].ravel()]
+    return loss, np.concatenate(parts)

@@ -3,6 +3,7 @@
 
 #include <mutex>
 #include <string>
+#include <vector>
 
 namespace fcgno {
 
@@ -10,6 +11,41 @@ std::atomic<uint64_t> g_launches{0};
 static thread_local std::string t_last_error;
 
 void set_last_error(const std::string& msg) { t_last_error = msg; }
+
+// ---- kernel tracing (CUDA events around selected launches)
+static std::mutex g_trace_mu;
+static std::string g_trace_family;
+static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_trace_events;
+static std::vector<cudaEvent_t> g_trace_pool;
+static cudaEvent_t g_trace_open = nullptr;
+
+static cudaEvent_t trace_event() {
+  if (!g_trace_pool.empty()) {
+    cudaEvent_t e = g_trace_pool.back();
+    g_trace_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+bool trace_enabled(const char* family) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  return !g_trace_family.empty() && g_trace_family == family;
+}
+void trace_begin(const char*, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace_open = trace_event();
+  cudaEventRecord(g_trace_open, st);
+}
+void trace_end(const char*, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  cudaEvent_t e = trace_event();
+  cudaEventRecord(e, st);
+  g_trace_events.emplace_back(g_trace_open, e);
+  g_trace_open = nullptr;
+}
 
 void solver_ws_free(fcgno_op* op);
 
@@ -204,3 +240,33 @@ extern "C" const char* fcgno_status_str(fcgno_status s) {
 extern "C" const char* fcgno_last_error(void) { return t_last_error.c_str(); }
 
 extern "C" uint64_t fcgno_launch_count(void) { return g_launches.load(std::memory_order_relaxed); }
+
+extern "C" fcgno_status fcgno_trace_set(const char* family) {
+  std::lock_guard<std::mutex> lk(fcgno::g_trace_mu);
+  fcgno::g_trace_family = family ? family : "";
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_trace_collect(double* total_ms, uint64_t* launches) {
+  if (!total_ms || !launches) {
+    set_last_error("fcgno_trace_collect: null output");
+    return FCGNO_EINVAL;
+  }
+  std::lock_guard<std::mutex> lk(fcgno::g_trace_mu);
+  double tot = 0.0;
+  for (auto& pr : fcgno::g_trace_events) {
+    if (cudaEventSynchronize(pr.second) != cudaSuccess) {
+      set_last_error("fcgno_trace_collect: event synchronisation failed");
+      return FCGNO_ECUDA;
+    }
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, pr.first, pr.second);
+    tot += ms;
+    fcgno::g_trace_pool.push_back(pr.first);
+    fcgno::g_trace_pool.push_back(pr.second);
+  }
+  *total_ms = tot;
+  *launches = fcgno::g_trace_events.size();
+  fcgno::g_trace_events.clear();
+  return FCGNO_OK;
+}

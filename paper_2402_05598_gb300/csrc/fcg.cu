@@ -519,9 +519,13 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
       }
     }
     if (fused) {
-      fused_step_kernel<<<op->B, fusedThreads, fusedSmem, st>>>(a, s);
+      {
+        TraceScope ts("fcg_fused", st);
+        fused_step_kernel<<<op->B, fusedThreads, fusedSmem, st>>>(a, s);
+      }
       FCGNO_LAUNCHED();
     } else {
+      TraceScope ts("fcg_tiled", st);
       const dim3 grid(a.tiles, op->B);
       if (a.m_i > 0) {
         dots_w_kernel<<<grid, kThreads, 0, st>>>(a, s);

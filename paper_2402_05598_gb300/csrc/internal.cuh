@@ -45,6 +45,23 @@ extern std::atomic<uint64_t> g_launches;
     if (s_ != FCGNO_OK) return s_;                                                           \
   } while (0)
 
+// Kernel tracing: when a kernel family is selected with fcgno_trace_set, its launch sites
+// bracket the launch with a pair of CUDA events on the launch stream.
+bool trace_enabled(const char* family);
+void trace_begin(const char* family, cudaStream_t st);
+void trace_end(const char* family, cudaStream_t st);
+struct TraceScope {
+  const char* fam;
+  cudaStream_t st;
+  bool on;
+  TraceScope(const char* f, cudaStream_t s) : fam(f), st(s), on(trace_enabled(f)) {
+    if (on) trace_begin(fam, st);
+  }
+  ~TraceScope() {
+    if (on) trace_end(fam, st);
+  }
+};
+
 // Per-instance solver status codes kept on the device (negative = still iterating).
 constexpr int kRunning = -1;
 constexpr int kMaxWindow = 8;  // largest m_max supported

@@ -5,7 +5,7 @@
 //   v0 = lift_w [r/rms, log k] + lift_b
 //   layer l: c = A v (truncated analysis), c' = R_l c (per-mode complex C x C),
 //            h = W_l v + b_l + S c' (truncated synthesis), v = GELU(h) (no GELU on the last)
-//   z = rms * (proj2_w . GELU(proj1_w v + proj1_b) + proj2_b)
+//   z = h^2 rms(r) * (proj2_w . GELU(proj1_w v + proj1_b) + proj2_b)
 // The truncated transforms are separable: analysis first sums over q (x2-frequencies
 // k2 = 0..M-1), then over p (x1-frequencies j -> k1 = j or j-2M); synthesis runs the two
 // stages in reverse. Twiddles come from tables built on the device with sincospi of the
@@ -344,13 +344,14 @@ __global__ void synthesis_q_pointwise_kernel(int N, int C, int Ky, const int* __
   out[oi] = activate ? act_gelu<T>(acc) : acc;
 }
 
-// z[b][x] = rms * (p2 . GELU(P1 v + p1) + p2b); optional saves of the decoder's
-// pre-activation and GELU output.
+// z[b][x] = h^2 rms * (p2 . GELU(P1 v + p1) + p2b) (hh = h^2); optional saves of the
+// decoder's pre-activation and GELU output.
 template <typename T>
 __global__ void project_kernel(size_t n, int C, int Cp, const int* __restrict__ active, const T* __restrict__ v,
                                const T* __restrict__ P1, const T* __restrict__ p1, const T* __restrict__ p2,
-                               const T* __restrict__ p2b, const double* __restrict__ rms, double* __restrict__ z,
-                               T* __restrict__ asave, T* __restrict__ gsave, double* __restrict__ ztsave) {
+                               const T* __restrict__ p2b, const double* __restrict__ rms, double hh,
+                               double* __restrict__ z, T* __restrict__ asave, T* __restrict__ gsave,
+                               double* __restrict__ ztsave) {
   extern __shared__ unsigned char smraw[];
   T* P1s = reinterpret_cast<T*>(smraw);  // Cp*C
   for (int t = threadIdx.x; t < Cp * C; t += blockDim.x) P1s[t] = P1[t];
@@ -373,7 +374,7 @@ __global__ void project_kernel(size_t n, int C, int Cp, const int* __restrict__ 
     zt += p2[h] * g;
   }
   if (ztsave) ztsave[(size_t)b * n + x] = (double)zt;
-  z[(size_t)b * n + x] = rms[b] * (double)zt;
+  z[(size_t)b * n + x] = rms[b] * hh * (double)zt;
 }
 
 // ------------------------------------ host: forward ------------------------------------
@@ -501,7 +502,8 @@ static fcgno_status forward_simt(fcgno_model* m, const fcgno_op* op, const T* wb
   }
   const size_t smem = (size_t)Cp * C * sizeof(T);
   project_kernel<T><<<dim3(ceil_div(n, 128), B), 128, smem, st>>>(n, C, Cp, active, cur, W.proj1_w, W.proj1_b,
-                                                                   W.proj2_w, W.proj2_b, rms, z,
+                                                                   W.proj2_w, W.proj2_b, rms,
+                                                                   1.0 / ((double)(N + 1) * (N + 1)), z,
                                                                    tr ? (T*)tr->apre : nullptr,
                                                                    tr ? (T*)tr->ghid : nullptr, ztsave);
   FCGNO_LAUNCHED();
@@ -614,15 +616,15 @@ __global__ void loss_value_kernel(int B, const double* __restrict__ norms, float
   *loss = (float)(s / B);
 }
 
-// dL/dzt[b][x] = rms_b * (1/B) * (A d)_x / (||d||_A ||e||_A)   (zt = z / rms)
+// dL/dzt[b][x] = h^2 rms_b * (1/B) * (A d)_x / (||d||_A ||e||_A)   (zt = z / (h^2 rms))
 template <typename T>
-__global__ void dzt_kernel(int B, size_t n, const double* __restrict__ Ad, const double* __restrict__ norms,
-                           const double* __restrict__ rms, T* __restrict__ gzt) {
+__global__ void dzt_kernel(int B, size_t n, double hh, const double* __restrict__ Ad,
+                           const double* __restrict__ norms, const double* __restrict__ rms, T* __restrict__ gzt) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= (size_t)B * n) return;
   const int b = (int)(i / n);
   const double den = norms[2 * b] * norms[2 * b + 1];
-  gzt[i] = (den > 0.0) ? (T)(rms[b] * Ad[i] / (den * B)) : (T)0;
+  gzt[i] = (den > 0.0) ? (T)(hh * rms[b] * Ad[i] / (den * B)) : (T)0;
 }
 
 // Decoder backward: ga[x][h] = gzt[x] p2[h] GELU'(a[x][h]); gv[x][c] = sum_h ga[x][h] P1[h][c].
@@ -794,7 +796,8 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
   const T *tw1, *tw2;
   tw_ptrs<T>(m->ws->tw, tw1, tw2);
   T* gzt = (T*)t.gz;
-  dzt_kernel<T><<<ceil_div(pts, 256), 256, 0, st>>>(B, n, Ad, t.lossb, t.rms, gzt);
+  dzt_kernel<T><<<ceil_div(pts, 256), 256, 0, st>>>(B, n, 1.0 / ((double)(N + 1) * (N + 1)), Ad, t.lossb, t.rms,
+                                                    gzt);
   FCGNO_LAUNCHED();
   // decoder: proj2 grads (A = gzt [pts][1], V = GELU(a) [pts][Cp])
   FCGNO_TRY(outer_reduce<T>(pts, 1, Cp, gzt, (const T*)t.ghid, (T*)t.partials, grad + BL.proj2_w,

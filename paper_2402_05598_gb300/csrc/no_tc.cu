@@ -10,7 +10,7 @@
 //   synthesis stage 2 + pointwise, per tile of 128 grid points:
 //       h[x][c] = sum_c' v[x][c'] W[c][c'] + sum_(pl,k2,t') Asyn[x][(pl,k2,t')] U[c][(pl,k2,t')]
 //     (Asyn is block diagonal over the tile's grid columns when N < 128), then bias, GELU;
-//     the last layer also runs the decoder C -> C_p (second MMA), GELU, -> 1, times rms(r).
+//     the last layer also runs the decoder C -> C_p (second MMA), GELU, -> 1, times h^2 rms(r).
 // Tables: E2 = (cos, -sin)(2 pi k2 q / N); G = analysis twiddles over p with the 1/n factor;
 // H = synthesis twiddles over p; Asyn = w_k2 (cos, -sin)(2 pi k2 q / N), w_0 = 1, w_{k2>0} = 2.
 // Real and imaginary parts are interleaved along the contracted dimension, so every complex
@@ -594,6 +594,7 @@ struct SynArgs {
   const float* p2;
   const float* p2b;
   const double* rms;
+  double hh;              // h^2 output scale
   double* z;              // [B][N][N]
   int* err;
 };
@@ -828,7 +829,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_synthesis_kernel(SynArgs a) 
 #pragma unroll
         for (int i = 0; i < 16; ++i) zt = fmaf(a.p2[c0 + i], gelu_f(val[i] + a.p1[c0 + i]), zt);
       }
-      if (valid) a.z[((size_t)b * N + q) * N + p] = a.rms[b] * (double)zt;
+      if (valid) a.z[((size_t)b * N + q) * N + p] = a.rms[b] * a.hh * (double)zt;
     }
     fence_before_sync();
   }
@@ -889,9 +890,12 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   }
   BlobLayout BL = blob_layout(d);
   const bool bf16 = !fp16;
-  tc_lift_kernel<<<dim3(ceil_div(n * (C / 8), 256), B), 256, 0, st>>>(n, C, r, op->logk, rms, active,
-                                                                      m->w32 + BL.lift_w, m->w32 + BL.lift_b, T.va,
-                                                                      bf16);
+  {
+    TraceScope ts("tc_lift", st);
+    tc_lift_kernel<<<dim3(ceil_div(n * (C / 8), 256), B), 256, 0, st>>>(n, C, r, op->logk, rms, active,
+                                                                        m->w32 + BL.lift_w, m->w32 + BL.lift_b, T.va,
+                                                                        bf16);
+  }
   FCGNO_LAUNCHED();
   const size_t sa = analysis_smem(g), ss = synthesis_smem(g), sm = mix_smem(C);
   FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_analysis_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
@@ -900,11 +904,17 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   uint16_t* cur = T.va;
   uint16_t* nxt = T.vb;
   for (int l = 0; l < d.layers; ++l) {
-    tc_analysis_kernel<C><<<dim3(g.nchunks, B), kTcThreads, sa, st>>>(g, bf16, active, cur, tab->E2, tab->G, T.part,
-                                                                     d_err);
+    {
+      TraceScope ts("tc_analysis", st);
+      tc_analysis_kernel<C><<<dim3(g.nchunks, B), kTcThreads, sa, st>>>(g, bf16, active, cur, tab->E2, tab->G,
+                                                                       T.part, d_err);
+    }
     FCGNO_LAUNCHED();
-    tc_mix_kernel<C><<<dim3(g.nmodes, ceil_div(B, 128)), kTcThreads, sm, st>>>(g, B, bf16, T.part, P.Rr[l], T.chat,
-                                                                              d_err);
+    {
+      TraceScope ts("tc_mix", st);
+      tc_mix_kernel<C><<<dim3(g.nmodes, ceil_div(B, 128)), kTcThreads, sm, st>>>(g, B, bf16, T.part, P.Rr[l],
+                                                                                T.chat, d_err);
+    }
     FCGNO_LAUNCHED();
     SynArgs s{};
     s.g = g;
@@ -925,9 +935,13 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     s.p2 = m->w32 + BL.proj2_w;
     s.p2b = m->w32 + BL.proj2_b;
     s.rms = rms;
+    s.hh = 1.0 / ((double)(op->N + 1) * (op->N + 1));
     s.z = z;
     s.err = d_err;
-    tc_synthesis_kernel<C><<<dim3(g.nchunks, B), kTcThreads, ss, st>>>(s);
+    {
+      TraceScope ts("tc_synthesis", st);
+      tc_synthesis_kernel<C><<<dim3(g.nchunks, B), kTcThreads, ss, st>>>(s);
+    }
     FCGNO_LAUNCHED();
     std::swap(cur, nxt);
   }

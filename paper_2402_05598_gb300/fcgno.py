@@ -61,6 +61,8 @@ def _load():
         "fcgno_status_str": (c_char_p, [c_int]),
         "fcgno_last_error": (c_char_p, []),
         "fcgno_launch_count": (c_uint64, []),
+        "fcgno_trace_set": (c_int, [c_char_p]),
+        "fcgno_trace_collect": (c_int, [POINTER(c_double), POINTER(c_uint64)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -76,7 +78,7 @@ EXPORTS = [
     "fcgno_assemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
     "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_workspace_bytes", "fcgno_status_str",
-    "fcgno_last_error", "fcgno_launch_count",
+    "fcgno_last_error", "fcgno_launch_count", "fcgno_trace_set", "fcgno_trace_collect",
 ]
 
 
@@ -90,6 +92,19 @@ def last_error() -> str:
 
 def launch_count() -> int:
     return int(lib.fcgno_launch_count())
+
+
+def trace_set(family: str):
+    """Select the kernel family whose launches are bracketed by CUDA events ("" = off)."""
+    _check(lib.fcgno_trace_set(family.encode()), "fcgno_trace_set")
+
+
+def trace_collect():
+    """(total device ms, traced launches) since the previous collect."""
+    ms = c_double()
+    cnt = c_uint64()
+    _check(lib.fcgno_trace_collect(ctypes.byref(ms), ctypes.byref(cnt)), "fcgno_trace_collect")
+    return float(ms.value), int(cnt.value)
 
 
 def _check(code: int, where: str):

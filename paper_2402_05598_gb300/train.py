@@ -1,0 +1,90 @@
+"""Training the neural-operator preconditioner (Section 3.1, Fig. 2(a)-(b)).
+
+Data (Eq. (9)): for every training instance, u_0 ~ N(0, 1); CG (Algorithm 1 with B = I)
+runs K iterations and every iterate gives a residual r_i and an error e_i = u* - u_i, where
+u* is the same problem solved to a relative residual of 1e-12. The loss is Eq. (11),
+mean ||NO(r) - e||_A / ||e||_A, and its gradient comes from the library's hand-written
+backward (fcgno_train_step). PyTorch's Adam updates the FP32 master blob.
+
+Batches hold one sample from each instance of a group of ``batch`` instances (one
+assembled operator per group); the sample index inside each instance's Krylov sequence is
+drawn at random every step.
+"""
+from __future__ import annotations
+
+import time
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import fcgno as F
+from . import inputs as I
+
+
+@dataclass
+class TrainResult:
+    steps: int
+    seconds: float
+    harvest_seconds: float
+    losses: list = field(default_factory=list)
+
+
+class KrylovData:
+    """Harvested (r_i, e_i) pairs of one group of instances, resident on the device."""
+
+    def __init__(self, N, seeds, K, device, sigma=1.0, ell=0.1, x0_seed=12345, stream=None):
+        import torch
+        k, f = I.make_batch(N, seeds, sigma, ell)
+        B = len(seeds)
+        self.B, self.N, self.K = B, N, K
+        self.k = torch.from_numpy(k).to(device)
+        self.op = F.Operator(self.k, stream)
+        fb = torch.from_numpy(f).to(device)
+        ustar = torch.zeros_like(fb)
+        F.solve(self.op, None, fb, ustar, tol=1e-12, m_max=1, max_iter=20 * N * N, prec="fp64", check_every=64,
+                stream=stream)
+        x0 = torch.from_numpy(np.random.default_rng(x0_seed).standard_normal((B, N, N))).to(device)
+        self.r = torch.empty((K, B, N, N), dtype=torch.float64, device=device)
+        self.e = torch.empty_like(self.r)
+        F.krylov_harvest(self.op, fb, x0, ustar, K, self.r, self.e, stream)
+
+
+def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, lr: float = 1e-3,
+          steps: int = 1000, seconds: float | None = None, prec: str = "fp32", seed: int = 0,
+          sigma: float = 1.0, ell: float = 0.1, log_every: int = 0) -> TrainResult:
+    """Trains ``model.weights`` in place; returns the loss history."""
+    import torch
+    dev = model.weights.device
+    t0 = time.perf_counter()
+    groups = []
+    seeds = list(train_seeds)
+    for g0 in range(0, len(seeds) - batch + 1, batch):
+        groups.append(KrylovData(N, seeds[g0:g0 + batch], K, dev, sigma, ell, x0_seed=1000 + g0))
+    torch.cuda.synchronize()
+    t_h = time.perf_counter() - t0
+    param = model.weights
+    opt = torch.optim.Adam([param], lr=lr)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(seed)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    grad = torch.zeros_like(param)
+    ar = torch.arange(batch, device=dev)
+    losses = []
+    t1 = time.perf_counter()
+    step = 0
+    while step < steps and (seconds is None or time.perf_counter() - t1 < seconds):
+        d = groups[step % len(groups)]
+        idx = torch.randint(0, K, (batch,), generator=gen, device=dev)
+        r = d.r[idx, ar].contiguous()
+        e = d.e[idx, ar].contiguous()
+        F.train_step(model, d.op, r, e, loss, grad, prec=prec)
+        param.grad = grad
+        opt.step()
+        if prec == "fp64":
+            model.sync()
+        if log_every and step % log_every == 0:
+            losses.append((step, float(loss.item())))
+        step += 1
+    model.sync()
+    torch.cuda.synchronize()
+    return TrainResult(steps=step, seconds=time.perf_counter() - t1, harvest_seconds=t_h, losses=losses)

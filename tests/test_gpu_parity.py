@@ -239,3 +239,29 @@ def test_tensor_core_preconditioner_inside_solve(lib, dev):
         e15 = O.energy_norm(k[b], ustar - x[b].cpu().numpy())
         e0 = O.energy_norm(k[b], ustar)
         assert e15 <= e0
+
+
+# ------------------------------------------------------------------------------- training step
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("fp32", 2e-4)])
+def test_train_step_matches_oracle_gradient(lib, dev, prec, tol):
+    """Energy-norm loss (Eq. (11)) and its gradient w.r.t. the whole weight blob, from the
+    hand-written CUDA backward, against the oracle's reverse mode (itself pinned by finite
+    differences). Relative 2-norm error of the gradient: 1e-6 (FP64 arithmetic, FP32 output), 2e-4 (FP32)."""
+    import torch
+    N, B, C, M = 32, 3, 16, 8
+    k, f = batch(N, B, 1300)
+    es = np.stack([np.linalg.solve(O.dense_A(k[b]), f[b].ravel()).reshape(N, N) for b in range(B)])
+    desc, P, model, wdev = model_pair(lib, dev, C, M, L=4, seed=2)
+    op = lib.Operator(to_dev(k, dev))
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    grad = torch.zeros(wdev.numel(), dtype=torch.float32, device=dev)
+    lib.train_step(model, op, to_dev(f, dev), to_dev(es, dev), loss, grad, prec=prec)
+    L_ref, g_ref = O.notay_loss_and_grad(P, desc, list(k), list(f), list(es))
+    assert abs(float(loss.item()) - L_ref) <= max(tol, 1e-6) * L_ref
+    g = grad.double().cpu().numpy()
+    assert rel(g, g_ref) < tol
+    # every parameter group is exercised
+    off = I.weight_offsets(desc)
+    for name, (o, s) in off.items():
+        if name != "_total":
+            assert rel(g[o:o + s], g_ref[o:o + s]) < max(tol * 10, 1e-7), name

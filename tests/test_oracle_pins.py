@@ -300,3 +300,64 @@ def test_grf_sample_covariance():
     for dp in (0, 1, 3):
         emp = np.mean(g[:, 5, 4] * g[:, 5, 4 + dp])
         assert abs(emp - sigma**2 * math.exp(-((dp * h) ** 2) / (2 * ell**2))) < 0.12 * sigma**2
+
+
+# --------------------------------------------------------------------------- training gradient
+def test_transform_adjoints_by_inner_products():
+    """<S c, g> = <c, S^T g> and <A v, d> = <v, A^T d> with complex inputs read as (re, im)."""
+    N, M, C = 12, 3, 2
+    rng = np.random.default_rng(4)
+    c = rng.standard_normal((2 * M, M, C)) + 1j * rng.standard_normal((2 * M, M, C))
+    g = rng.standard_normal((N, N, C))
+    lhs = np.sum(O.synthesis(c, N) * g)
+    adj = O.synthesis_adjoint(g, M)
+    rhs = np.sum(c.real * adj.real + c.imag * adj.imag)
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+    v = rng.standard_normal((N, N, C))
+    d = rng.standard_normal((2 * M, M, C)) + 1j * rng.standard_normal((2 * M, M, C))
+    a = O.analysis(v, M)
+    lhs = np.sum(a.real * d.real + a.imag * d.imag)
+    rhs = np.sum(v * O.analysis_adjoint(d, N))
+    assert abs(lhs - rhs) < 1e-11 * abs(lhs)
+
+
+def test_notay_gradient_matches_central_differences():
+    """The hand-written reverse mode against central finite differences on every parameter
+    group (random coordinates), FP64, agreement to 1e-6 relative."""
+    N = 10
+    desc = I.ModelDesc(width=4, layers=2, modes=3, proj_width=4)
+    blob = I.xavier_weights(desc, 1).astype(np.float64)
+    off = I.weight_offsets(desc)
+    rng = np.random.default_rng(0)
+    for name in ["lift_b", "proj1_b", "proj2_b", "b0", "b1"]:
+        o, s = off[name]
+        blob[o:o + s] = rng.uniform(-0.3, 0.3, s)
+    ks, rs, es = [], [], []
+    for s in range(2):
+        k, f = I.make_problem(N, 40 + s)
+        e = np.linalg.solve(O.dense_A(k), f.ravel()).reshape(N, N)
+        ks.append(k)
+        rs.append(f)
+        es.append(e)
+
+    def loss_of(b):
+        return O.notay_loss_and_grad(O.unpack_weights(b, desc), desc, ks, rs, es)[0]
+
+    L0, g = O.notay_loss_and_grad(O.unpack_weights(blob, desc), desc, ks, rs, es)
+    assert abs(L0 - O.notay_loss(ks, [O.no_forward(O.unpack_weights(blob, desc), desc, r, np.log(k))
+                                       for k, r in zip(ks, rs)], es)) < 1e-14
+    checked = 0
+    for name, (o, s) in off.items():
+        if name == "_total":
+            continue
+        for idx in rng.choice(s, size=min(s, 3), replace=False):
+            i = o + idx
+            h = 1e-6 * max(1.0, abs(blob[i]))
+            bp = blob.copy()
+            bm = blob.copy()
+            bp[i] += h
+            bm[i] -= h
+            fd = (loss_of(bp) - loss_of(bm)) / (2 * h)
+            assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), 1e-3), (name, idx, fd, g[i])
+            checked += 1
+    assert checked >= 20
