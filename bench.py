@@ -196,6 +196,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--profile", type=int, default=0,
+                    help="profiling mode: no training, two solves of --profile-iters fixed iterations")
+    ap.add_argument("--profile-iters", type=int, default=8)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -218,6 +221,21 @@ def main():
     blob = torch.from_numpy(I.xavier_weights(desc_np, 0)).to(dev)
     model = F.Model(F.make_desc(WIDTH, LAYERS, MODES, WIDTH), blob)
     tr = None
+    if args.profile:
+        # short fixed-iteration solves with every instance active (the ncu capture workload)
+        seeds = range(10000, 10000 + EVAL_BATCH)
+        k_np, f_np = I.make_batch(N_GRID, seeds)
+        op = F.Operator(torch.from_numpy(k_np).to(dev))
+        f = torch.from_numpy(f_np).to(dev)
+        x = torch.zeros_like(f)
+        for rep in range(2):
+            x.zero_()
+            info = F.solve(op, model, f, x, tol=TOL, m_max=args.m, max_iter=args.profile_iters, prec=args.prec,
+                           fixed_iters=True, check_every=args.profile_iters)
+        torch.cuda.synchronize()
+        print(json.dumps({"profile": True, "iters": info[0]["iters"], "instances": EVAL_BATCH,
+                          "launches": F.launch_count()}))
+        return
     if args.train_steps > 0:
         tr = T.train(model, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3, steps=args.train_steps)
 
