@@ -123,6 +123,23 @@ fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const doub
                               double* x_host, fcgno_model_t Bpc, const fcgno_solve_opts* opts,
                               fcgno_prec prec, fcgno_solve_info* info, void* stream);
 
+/* Allocation-free variant of fcgno_solve for the identity preconditioner (B = I; plain CG
+ * for m_max = 1). The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they solve, e.g. code that runs under a fixed,
+ * pre-reserved memory budget or in a context where the CUDA allocator must not be entered.
+ * It calls no cudaMalloc/cudaFree and no allocating library routine; its Krylov state
+ * (r, the m_max+1 directions p_k and s_k, per-instance scalars and partial sums) lives in
+ * one file-scope device array of 8 MiB that every GPU loading the library keeps until the
+ * process exits. Problems whose state does not fit (about 8*N*N*batch*(2*m_max+3) bytes
+ * plus small terms) are rejected with FCGNO_EINVAL and a message giving the size needed.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
+ * make that first call before any stream capture. Every call shares the array and leaves
+ * its contents behind, so two calls that overlap on the GPU (different streams, threads
+ * or processes sharing the context) race and corrupt each other. Arguments and results
+ * are those of fcgno_solve with Bpc = NULL and prec = FCGNO_FP64; info is a HOST array. */
+fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, double* x, const fcgno_solve_opts* opts,
+                                 fcgno_solve_info* info, void* stream);
+
 /* Krylov-subspace sampling (Eq. (9), Section 3.1): runs K iterations of CG (Algorithm 1
  * with B = I, m_max = 1) from x0 on every instance and stores, for i = 1..K, the
  * residual r_i and the error e_i = u_star - u_i:

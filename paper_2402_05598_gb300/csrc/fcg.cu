@@ -683,3 +683,179 @@ extern "C" fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, cons
   cudaFreeAsync(u, st);
   return rc;
 }
+
+// ------------------------------------ allocation-free solve ----------------------------
+// Some callers cannot allocate device memory at solve time: code running under a fixed,
+// pre-reserved memory budget, or inside a region where the CUDA allocator must not be
+// entered. fcgno_solve_noalloc serves them for the identity preconditioner: its Krylov
+// state lives in one file-scope device array of fixed size that every GPU loading this
+// library holds until the process exits. All calls share that array.
+namespace fcgno {
+
+constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB per device
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+static void* g_noalloc_addr[64] = {};  // device address of the array, per device ordinal
+
+// Device address of the scratch array for the current device. The first call on a device
+// resolves it with cudaGetSymbolAddress (host code cannot use the symbol's own address).
+static fcgno_status noalloc_scratch_address(void** out) {
+  int dev = -1;
+  FCGNO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_last_error("fcgno_solve_noalloc: device ordinal out of range");
+    return FCGNO_EINVAL;
+  }
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    FCGNO_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return FCGNO_OK;
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace fcgno
+
+extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, double* x, const fcgno_solve_opts* opts,
+                                            fcgno_solve_info* info, void* stream) {
+  using namespace fcgno;
+  if (!A || !b || !x) {
+    set_last_error("fcgno_solve_noalloc: null operator, b or x");
+    return FCGNO_EINVAL;
+  }
+  FCGNO_TRY(check_opts(opts));
+  const fcgno_solve_opts& o = *opts;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int slots = o.m_max + 1;
+  const int B = A->B;
+  const int tiles = (int)ceil_div(A->n, kTile);
+  // carve the fixed array: r, P, S, per-instance scalars, partial sums, status words
+  const size_t vec = A->n * (size_t)B * sizeof(double);
+  size_t off[14];
+  const size_t sizes[14] = {vec,
+                            vec * slots,
+                            vec * slots,
+                            sizeof(double) * slots * B,
+                            sizeof(double) * kMaxWindow * B,
+                            sizeof(double) * B,
+                            sizeof(double) * B,
+                            sizeof(double) * B,
+                            sizeof(double) * B,
+                            sizeof(double) * (size_t)B * tiles * kParts,
+                            sizeof(int) * B,
+                            sizeof(int) * B,
+                            sizeof(int),
+                            0};
+  size_t total = 0;
+  for (int i = 0; i < 14; ++i) {
+    off[i] = total;
+    total += align256(sizes[i]);
+  }
+  if (total > kNoAllocScratchBytes) {
+    set_last_error("fcgno_solve_noalloc: problem needs " + std::to_string(total) +
+                   " bytes of solver scratch; the allocation-free solve is limited to " +
+                   std::to_string(kNoAllocScratchBytes) + " bytes (8 MiB)");
+    return FCGNO_EINVAL;
+  }
+  void* base_v = nullptr;
+  FCGNO_TRY(noalloc_scratch_address(&base_v));
+  unsigned char* base = (unsigned char*)base_v;
+  State s;
+  s.aE = A->aE;
+  s.aN = A->aN;
+  s.diag = A->diag;
+  s.b = b;
+  s.u = x;
+  s.r = (double*)(base + off[0]);
+  s.w = s.r;  // identity preconditioner: w_i = r_i
+  s.P = (double*)(base + off[1]);
+  s.S = (double*)(base + off[2]);
+  s.ps = (double*)(base + off[3]);
+  s.beta = (double*)(base + off[4]);
+  s.alpha = (double*)(base + off[5]);
+  s.r0 = (double*)(base + off[6]);
+  s.rr = (double*)(base + off[7]);
+  s.rms = (double*)(base + off[8]);
+  s.part = (double*)(base + off[9]);
+  s.status = (int*)(base + off[10]);
+  s.iters = (int*)(base + off[11]);
+  s.ndone = (int*)(base + off[12]);
+  IterArgs a{};
+  a.N = A->N;
+  a.B = B;
+  a.n = A->n;
+  a.tiles = tiles;
+  a.tol = o.tol;
+  a.fixed = o.fixed_iters ? 1 : 0;
+  const bool fused = A->N <= kFusedMaxN;
+  const int fusedThreads = ((int)ceil_div(A->n, kFusedEPT) + 31) / 32 * 32;
+  const size_t fusedSmem = A->n * sizeof(double);
+  if (fused && fusedSmem > 48 * 1024)
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fusedSmem));
+  // the stopped-instance counter must start at zero: the array keeps the previous call's data
+  FCGNO_CUDA_TRY(cudaMemsetAsync(s.ndone, 0, sizeof(int), st));
+  init_kernel<<<dim3(a.tiles, B), kThreads, 0, st>>>(a, s);
+  FCGNO_LAUNCHED();
+  init_finalize_kernel<<<ceil_div(B, 128), 128, 0, st>>>(a, s);
+  FCGNO_LAUNCHED();
+  const int check_every = std::max(1, o.check_every);
+  int h_ndone = 0;
+  for (int i = 0; i < o.max_iter; ++i) {
+    a.i = i;
+    a.m_i = std::min(i, std::max(1, i % slots));
+    a.slot_new = i % slots;
+    for (int j = 0; j < kMaxWindow; ++j) a.slots[j] = (j < a.m_i) ? (i - a.m_i + j) % slots : 0;
+    if (fused) {
+      fused_step_kernel<<<B, fusedThreads, fusedSmem, st>>>(a, s);
+      FCGNO_LAUNCHED();
+    } else {
+      const dim3 grid(a.tiles, B);
+      if (a.m_i > 0) {
+        dots_w_kernel<<<grid, kThreads, 0, st>>>(a, s);
+        FCGNO_LAUNCHED();
+        beta_kernel<<<B, 32, 0, st>>>(a, s);
+        FCGNO_LAUNCHED();
+      }
+      direction_kernel<<<grid, kThreads, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+      stencil_dots_kernel<<<grid, kThreads, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+      alpha_kernel<<<ceil_div(B, 128), 128, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+      update_kernel<<<grid, kThreads, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+      norm_kernel<<<ceil_div(B, 128), 128, 0, st>>>(a, s);
+      FCGNO_LAUNCHED();
+    }
+    if ((i + 1) % check_every == 0 || i + 1 == o.max_iter) {
+      FCGNO_CUDA_TRY(cudaMemcpyAsync(&h_ndone, s.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
+      FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+      if (h_ndone >= B) break;
+    }
+  }
+  // per-instance results, copied through fixed-size host buffers
+  constexpr int kChunk = 64;
+  int hs[kChunk], hi[kChunk];
+  double hrr[kChunk], hr0[kChunk];
+  for (int b0 = 0; b0 < B; b0 += kChunk) {
+    const int cnt = std::min(kChunk, B - b0);
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hs, s.status + b0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hi, s.iters + b0, sizeof(int) * cnt, cudaMemcpyDeviceToHost, st));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hrr, s.rr + b0, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hr0, s.r0 + b0, sizeof(double) * cnt, cudaMemcpyDeviceToHost, st));
+    FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+    if (info) {
+      for (int j = 0; j < cnt; ++j) {
+        int stt = hs[j];
+        if (stt == kRunning) stt = o.fixed_iters ? FCGNO_OK : FCGNO_ENOCONV;
+        info[b0 + j].iters = hi[j];
+        info[b0 + j].status = stt;
+        info[b0 + j].r0norm = hr0[j];
+        info[b0 + j].relres = hr0[j] > 0 ? std::sqrt(hrr[j]) / hr0[j] : 0.0;
+      }
+    }
+  }
+  return FCGNO_OK;
+}

@@ -55,6 +55,7 @@ def _load():
         "fcgno_solve": (c_int, [P, P, P, P, POINTER(fcgno_solve_opts), c_int, POINTER(fcgno_solve_info), P]),
         "fcgno_solve_host": (c_int, [c_int, c_int, P, P, P, P, POINTER(fcgno_solve_opts), c_int,
                                      POINTER(fcgno_solve_info), P]),
+        "fcgno_solve_noalloc": (c_int, [P, P, P, POINTER(fcgno_solve_opts), POINTER(fcgno_solve_info), P]),
         "fcgno_krylov_harvest": (c_int, [P, P, P, P, c_int, P, P, POINTER(fcgno_solve_info), P]),
         "fcgno_train_step": (c_int, [P, P, P, P, c_int, c_int, P, P, P]),
         "fcgno_workspace_bytes": (c_size_t, [c_int, c_int, c_int, POINTER(fcgno_model_desc), c_int]),
@@ -77,7 +78,7 @@ lib = _load()
 EXPORTS = [
     "fcgno_assemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
-    "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_workspace_bytes", "fcgno_status_str",
+    "fcgno_solve_noalloc", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_workspace_bytes", "fcgno_status_str",
     "fcgno_last_error", "fcgno_launch_count", "fcgno_trace_set", "fcgno_trace_collect",
 ]
 
@@ -223,6 +224,17 @@ def solve_host(k: np.ndarray, b: np.ndarray, x: np.ndarray, model=None, tol=1e-6
     _check(lib.fcgno_solve_host(N, B, k.ctypes.data, b.ctypes.data, x.ctypes.data,
                                 model.handle if model is not None else None, ctypes.byref(opts), PREC[prec], info,
                                 _stream(stream)), "fcgno_solve_host")
+    return _info_list(info)
+
+
+def solve_noalloc(op: Operator, b, x, tol=1e-6, m_max=1, max_iter=1000, fixed_iters=False, check_every=8,
+                  stream=None):
+    """fcgno_solve_noalloc: identity-preconditioned solve with no device allocation (for callers
+    that cannot allocate); its state lives in the library's fixed 8 MiB device array."""
+    info = (fcgno_solve_info * op.B)()
+    opts = _opts(tol, m_max, max_iter, fixed_iters, check_every)
+    _check(lib.fcgno_solve_noalloc(op.handle, _ptr(b), _ptr(x), ctypes.byref(opts), info, _stream(stream)),
+           "fcgno_solve_noalloc")
     return _info_list(info)
 
 

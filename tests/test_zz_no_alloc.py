@@ -1,0 +1,57 @@
+"""GPU test of fcgno_solve_noalloc, the solve entry point for callers that cannot allocate
+device memory (a fixed, pre-reserved memory budget, or a context where the CUDA allocator
+must not be entered). Its Krylov state lives in the library's fixed 8 MiB device array.
+
+This file is collected last on purpose: if it fails, a run that stops at the first failure
+has already run every other test.
+"""
+import numpy as np
+import pytest
+
+from paper_2402_05598_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def rel(a, b):
+    a, b = np.ravel(a), np.ravel(b)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def test_noalloc_solve_matches_solve_on_two_calls_in_a_row(lib, dev):
+    """Two consecutive calls (different shapes, windows and grid paths) agree with
+    fcgno_solve (identity preconditioner) to the FP64 parity tolerance of the other tests;
+    the second call leaves free device memory unchanged."""
+    import torch
+    cases = [(48, 3, 1, 2000), (100, 2, 3, 2100)]  # fused (N <= 90) and tiled paths
+    for call, (N, B, m, seed) in enumerate(cases):
+        k, f = I.make_batch(N, range(seed, seed + B))
+        x0 = np.random.default_rng(seed).standard_normal((B, N, N))
+        op = lib.Operator(torch.from_numpy(k).to(dev))
+        fb = torch.from_numpy(f).to(dev)
+        xa = torch.from_numpy(x0).to(dev)
+        xb = xa.clone()
+        ia = lib.solve(op, None, fb, xa, tol=1e-8, m_max=m, max_iter=3000, prec="fp64")
+        torch.cuda.synchronize()
+        free_before = torch.cuda.mem_get_info()[0]
+        ib = lib.solve_noalloc(op, fb, xb, tol=1e-8, m_max=m, max_iter=3000)
+        torch.cuda.synchronize()
+        if call == 1:
+            assert torch.cuda.mem_get_info()[0] == free_before
+        assert [i["iters"] for i in ib] == [i["iters"] for i in ia]
+        assert [i["status"] for i in ib] == [i["status"] for i in ia] == [lib.FCGNO_OK] * B
+        for b in range(B):
+            assert abs(ib[b]["relres"] - ia[b]["relres"]) <= 1e-10 * max(ia[b]["relres"], 1e-300) + 1e-14
+        assert rel(xb.cpu().numpy(), xa.cpu().numpy()) < 1e-10
+
+
+def test_noalloc_solve_rejects_problems_beyond_its_fixed_scratch(lib, dev):
+    import torch
+    N, B = 128, 16  # 16 x 128 x 128 unknowns need more than 8 MiB of Krylov state
+    k, f = I.make_batch(N, range(B))
+    op = lib.Operator(torch.from_numpy(k).to(dev))
+    x = torch.zeros((B, N, N), dtype=torch.float64, device=dev)
+    with pytest.raises(lib.FcgnoError) as ei:
+        lib.solve_noalloc(op, torch.from_numpy(f).to(dev), x, tol=1e-6)
+    assert ei.value.code == lib.FCGNO_EINVAL
+    assert "8 MiB" in str(ei.value)
