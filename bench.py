@@ -190,9 +190,10 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--prec", default="bf16", choices=["bf16", "fp16"])
     ap.add_argument("--m", type=int, default=1)
-    ap.add_argument("--train-steps", type=int, default=4000)
+    ap.add_argument("--train-steps", type=int, default=8000)
     ap.add_argument("--train-instances", type=int, default=256)
-    ap.add_argument("--max-iter", type=int, default=2000)
+    ap.add_argument("--max-iter", type=int, default=400,
+                    help="iteration cap (CG needs ~400 on this workload); capped instances are not counted")
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -237,7 +238,8 @@ def main():
                           "launches": F.launch_count()}))
         return
     if args.train_steps > 0:
-        tr = T.train(model, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3, steps=args.train_steps)
+        tr = T.train(model, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3, steps=args.train_steps,
+                     log_every=1000)
 
     # ---- eval inputs (resident)
     seeds = range(10000 + EVAL_BATCH * rank, 10000 + EVAL_BATCH * (rank + 1))
@@ -254,7 +256,7 @@ def main():
     def solve_once():
         x.copy_(u0)
         return F.solve(op, model, f, x, tol=TOL, m_max=args.m, max_iter=args.max_iter, prec=args.prec,
-                       check_every=4)
+                       check_every=8)
 
     for _ in range(args.warmup):
         info = solve_once()
@@ -283,6 +285,7 @@ def main():
         step_ms.append(e0.elapsed_time(e1))
     launches = F.launch_count() - launches0
     syn_ms, syn_launches = F.trace_collect()
+    trace_note = F.last_error() if "trace" in F.last_error() else ""
     F.trace_set("")
     clk = clocks.stop()
     total_ms = float(sum(step_ms))
@@ -292,7 +295,13 @@ def main():
         total_ms = float(t.item())
     solved = sum(sum(1 for i in inf if i["status"] == F.FCGNO_OK) for inf in infos)
     iters = [i["iters"] for i in infos[-1]]
-    value = EVAL_BATCH * world * args.steps / (total_ms / 1000.0)
+    # only solves that reached the tolerance count (capped instances are reported, not counted)
+    solved_all = solved
+    if world > 1:
+        t = torch.tensor([float(solved)], device=dev)
+        torch.distributed.all_reduce(t)
+        solved_all = int(t.item())
+    value = solved_all / (total_ms / 1000.0)
 
     # ---- roofline of the dominant kernel (synthesis): algorithmic bytes / traced device time
     max_it = max(iters)
@@ -325,7 +334,9 @@ def main():
                        "l2": "flushed (256 MB write) between timed steps",
                        "training": None if tr is None else {"steps": tr.steps, "batch": 32, "instances":
                                                             args.train_instances, "krylov_K": 100,
-                                                            "seconds": round(tr.seconds, 2)},
+                                                            "seconds": round(tr.seconds, 2),
+                                                            "loss_log": [(s_, round(l_, 4)) for s_, l_ in tr.losses]},
+                       "max_iter": args.max_iter,
                        "parallelism": f"replicas x{world}"},
             "iterations": {"mean": float(np.mean(iters)), "max": int(max(iters)), "converged": solved,
                            "solves": EVAL_BATCH * args.steps},
@@ -335,7 +346,8 @@ def main():
             "roofline": {"kernel": "tc_synthesis_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": None,
-                         "avg_launch_ms": syn_avg_ms, "launches": syn_launches},
+                         "avg_launch_ms": syn_avg_ms, "launches": syn_launches,
+                         "note": trace_note or None},
             "kernel_ms_one_step": shares}
 
     # ---- comparison paths on the same instances (untimed here, reported for context)

@@ -161,7 +161,11 @@ def truncation_window(i: int, m_max: int) -> int:
     return min(i, max(1, i % (m_max + 1)))
 
 
-def fcg(A, B, f, u0, m_max: int, iters: int, tol: float | None = None, record: bool = False):
+def _dot(a, b) -> float:
+    return float(np.sum(a * b))
+
+
+def fcg(A, B, f, u0, m_max: int, iters: int, tol: float | None = None, record: bool = False, dot=_dot):
     """Algorithm 1 (flexible CG) with preconditioner B, operator A (callables on arrays).
 
     Iteration i: w_i = B(r_i); m_i from the truncation rule; p_i = w_i minus the
@@ -169,11 +173,12 @@ def fcg(A, B, f, u0, m_max: int, iters: int, tol: float | None = None, record: b
     all taken from w_i); s_i = A p_i; u and r updated with alpha = (p_i, r_i)/(p_i, s_i).
     Stops after ``iters`` iterations, or earlier when ||r_{i+1}|| <= tol ||r_0||.
     Returns a dict with u, r, iterations, relres history and (if record) every u_i, r_i,
-    p_i, s_i.
+    p_i, s_i. ``dot`` computes the inner products (default: numpy's pairwise sum); tests
+    pass an exactly rounded one to measure how much the iterates depend on rounding.
     """
     u = np.array(u0, dtype=np.float64, copy=True)
     r = f - A(u)
-    r0 = math.sqrt(float(np.sum(r * r)))
+    r0 = math.sqrt(dot(r, r))
     P, S, PS = [], [], []
     hist = [1.0 if r0 > 0 else 0.0]
     us, rs = [u.copy()], [r.copy()]
@@ -184,13 +189,13 @@ def fcg(A, B, f, u0, m_max: int, iters: int, tol: float | None = None, record: b
     for i in range(iters if status == STATUS_RUNNING else 0):
         w = B(r)
         m_i = truncation_window(i, m_max)
-        beta = [float(np.sum(w * S[kk])) / PS[kk] for kk in range(i - m_i, i)]
+        beta = [dot(w, S[kk]) / PS[kk] for kk in range(i - m_i, i)]
         p = w.copy()
         for j, kk in enumerate(range(i - m_i, i)):
             p = p - beta[j] * P[kk]
         s = A(p)
-        ps = float(np.sum(p * s))
-        pr = float(np.sum(p * r))
+        ps = dot(p, s)
+        pr = dot(p, r)
         if not (ps != 0.0 and math.isfinite(ps) and math.isfinite(pr)):
             status = STATUS_BREAKDOWN
             break
@@ -201,7 +206,7 @@ def fcg(A, B, f, u0, m_max: int, iters: int, tol: float | None = None, record: b
         S.append(s)
         PS.append(ps)
         it = i + 1
-        rn = math.sqrt(float(np.sum(r * r)))
+        rn = math.sqrt(dot(r, r))
         hist.append(rn / r0)
         if record:
             us.append(u.copy())

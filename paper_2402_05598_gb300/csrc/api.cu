@@ -18,6 +18,18 @@ static std::string g_trace_family;
 static std::vector<std::pair<cudaEvent_t, cudaEvent_t>> g_trace_events;
 static std::vector<cudaEvent_t> g_trace_pool;
 static cudaEvent_t g_trace_open = nullptr;
+static EventPairs* g_trace_capture = nullptr;
+static double g_trace_replay_ms = 0.0;
+static uint64_t g_trace_failed = 0;
+static std::string g_trace_first_error;
+
+// A failed timing call must not leave a CUDA error behind for the next launch check.
+static void trace_note_failure(cudaError_t e) {
+  cudaGetLastError();
+  if (g_trace_failed++ == 0) g_trace_first_error = cudaGetErrorString(e);
+}
+static std::atomic<uint64_t> g_trace_gen{0};
+static uint64_t g_trace_replay_n = 0;
 
 static cudaEvent_t trace_event() {
   if (!g_trace_pool.empty()) {
@@ -37,14 +49,50 @@ bool trace_enabled(const char* family) {
 void trace_begin(const char*, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   g_trace_open = trace_event();
-  cudaEventRecord(g_trace_open, st);
+  const cudaError_t e = cudaEventRecord(g_trace_open, st);
+  if (e != cudaSuccess) trace_note_failure(e);
 }
 void trace_end(const char*, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   cudaEvent_t e = trace_event();
-  cudaEventRecord(e, st);
-  g_trace_events.emplace_back(g_trace_open, e);
+  const cudaError_t er = cudaEventRecord(e, st);
+  if (er != cudaSuccess) trace_note_failure(er);
+  if (g_trace_capture)
+    g_trace_capture->emplace_back(g_trace_open, e);
+  else
+    g_trace_events.emplace_back(g_trace_open, e);
   g_trace_open = nullptr;
+}
+uint64_t trace_generation() { return g_trace_gen.load(); }
+void trace_capture_begin(EventPairs* list) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace_capture = list;
+}
+void trace_capture_end() {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  g_trace_capture = nullptr;
+}
+void trace_accumulate(const EventPairs& pairs) {
+  if (pairs.empty()) return;
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  for (auto& pr : pairs) {
+    float ms = 0.f;
+    const cudaError_t e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+    if (e == cudaSuccess) {
+      g_trace_replay_ms += ms;
+      g_trace_replay_n += 1;
+    } else {
+      trace_note_failure(e);
+    }
+  }
+}
+void trace_release(EventPairs& pairs) {
+  std::lock_guard<std::mutex> lk(g_trace_mu);
+  for (auto& pr : pairs) {
+    g_trace_pool.push_back(pr.first);
+    g_trace_pool.push_back(pr.second);
+  }
+  pairs.clear();
 }
 
 void solver_ws_free(fcgno_op* op);
@@ -149,6 +197,7 @@ extern "C" fcgno_status fcgno_op_destroy(fcgno_op_t op) {
   double* p[] = {op->aE, op->aN, op->diag, op->logk};
   for (double* x : p)
     if (x) cudaFree(x);
+  if (op->logk32) cudaFree(op->logk32);
   delete op;
   return FCGNO_OK;
 }
@@ -244,6 +293,7 @@ extern "C" uint64_t fcgno_launch_count(void) { return g_launches.load(std::memor
 extern "C" fcgno_status fcgno_trace_set(const char* family) {
   std::lock_guard<std::mutex> lk(fcgno::g_trace_mu);
   fcgno::g_trace_family = family ? family : "";
+  fcgno::g_trace_gen.fetch_add(1);
   return FCGNO_OK;
 }
 
@@ -260,13 +310,23 @@ extern "C" fcgno_status fcgno_trace_collect(double* total_ms, uint64_t* launches
       return FCGNO_ECUDA;
     }
     float ms = 0.f;
-    cudaEventElapsedTime(&ms, pr.first, pr.second);
-    tot += ms;
+    const cudaError_t e = cudaEventElapsedTime(&ms, pr.first, pr.second);
+    if (e == cudaSuccess)
+      tot += ms;
+    else
+      fcgno::trace_note_failure(e);
     fcgno::g_trace_pool.push_back(pr.first);
     fcgno::g_trace_pool.push_back(pr.second);
   }
-  *total_ms = tot;
-  *launches = fcgno::g_trace_events.size();
+  if (fcgno::g_trace_failed) {
+    set_last_error("fcgno_trace_collect: " + std::to_string(fcgno::g_trace_failed) +
+                   " timing calls failed, first: " + fcgno::g_trace_first_error);
+    fcgno::g_trace_failed = 0;
+  }
+  *total_ms = tot + fcgno::g_trace_replay_ms;
+  *launches = fcgno::g_trace_events.size() + fcgno::g_trace_replay_n;
   fcgno::g_trace_events.clear();
+  fcgno::g_trace_replay_ms = 0.0;
+  fcgno::g_trace_replay_n = 0;
   return FCGNO_OK;
 }

@@ -30,19 +30,25 @@ constexpr int kThreads = 256;   // threads per CTA (tiled path)
 constexpr int kEPT = kTile / kThreads;
 constexpr int kParts = kMaxWindow + 2;
 constexpr int kFusedEPT = 8;    // elements per thread (fused path)
-constexpr int kFusedMaxN = 90;  // n/8 <= 1024 threads
+constexpr int kFusedMaxN = 80;  // n/8 <= 1024 threads and p + reduction staging fit shared memory
 
 struct IterArgs {
   int N;
   int B;
   size_t n;
   int tiles;
-  int i;          // iteration index
-  int m_i;        // window length
-  int slot_new;   // ring slot of p_i, s_i
-  int slots[kMaxWindow];
+  int nslots;     // m_max + 1 ring slots
   double tol;
   int fixed;      // 1: ignore tol
+};
+
+// Iteration index and truncation window, derived on the device from the iteration counter
+// so that a captured CUDA graph of several iterations replays unchanged.
+struct Window {
+  int i;          // iteration index
+  int m_i;        // window length min(i, max(1, i mod (m_max+1)))
+  int slot_new;   // ring slot of p_i, s_i
+  int slots[kMaxWindow];
 };
 
 struct State {
@@ -65,7 +71,22 @@ struct State {
   int* status;
   int* iters;
   int* ndone;
+  int* iter;      // device iteration counter (advanced once per iteration)
 };
+
+__device__ __forceinline__ Window window_of(const IterArgs& a, const State& s) {
+  Window w;
+  w.i = *(volatile const int*)s.iter;
+  w.m_i = min(w.i, max(1, w.i % a.nslots));
+  w.slot_new = w.i % a.nslots;
+#pragma unroll
+  for (int j = 0; j < kMaxWindow; ++j) w.slots[j] = (j < w.m_i) ? (w.i - w.m_i + j) % a.nslots : 0;
+  return w;
+}
+
+__global__ void advance_kernel(State s) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *s.iter += 1;
+}
 
 __device__ __forceinline__ double stencil_at(const State& s, size_t gi, int p, int q, int N, double c,
                                              double e, double w, double nn, double so) {
@@ -76,6 +97,40 @@ __device__ __forceinline__ double stencil_at(const State& s, size_t gi, int p, i
   if (q < N - 1) acc = fma(-s.aN[gi], nn, acc);
   if (q > 0) acc = fma(-s.aN[gi - N], so, acc);
   return acc;
+}
+
+// Block-wide sums of the first `count` (<= NV) per-thread values, in a fixed order: the
+// per-thread values go to shared memory; value j is summed by warp j mod (warps): each lane
+// adds its strided share pairwise, then a 5-step shuffle tree combines the lanes. This costs
+// about (blockDim/32 + 5) FP64 adds per lane of one warp per value instead of 5 per thread
+// of the block. `sm` holds NV * blockDim doubles, `out` NV. Every thread gets the sums.
+// Contains two __syncthreads().
+template <int NV>
+__device__ __forceinline__ void block_sums(double (&v)[NV], int count, double* sm, double* out) {
+  const int T = blockDim.x, nw = (T + 31) >> 5, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+    if (j < count) sm[j * T + threadIdx.x] = v[j];
+  __syncthreads();
+  for (int j = warp; j < count; j += nw) {
+    // lane sums elements lane, lane+32, ... (at most 32 of them) as a pairwise tree
+    double loc[32];
+#pragma unroll
+    for (int t = 0; t < 32; ++t) {
+      const int e = lane + 32 * t;
+      loc[t] = (e < T) ? sm[j * T + e] : 0.0;
+    }
+#pragma unroll
+    for (int w = 16; w > 0; w >>= 1)
+#pragma unroll
+      for (int t = 0; t < w; ++t) loc[t] += loc[t + w];
+    const double acc = warp_sum(loc[0]);
+    if (lane == 0) out[j] = acc;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+    if (j < count) v[j] = out[j];
 }
 
 // ------------------------------------ initialisation -----------------------------------
@@ -126,7 +181,8 @@ __global__ void init_finalize_kernel(IterArgs a, State s) {
 __global__ void __launch_bounds__(kThreads) dots_w_kernel(IterArgs a, State s) {
   __shared__ double scratch[32 * kMaxWindow];
   const int b = blockIdx.y;
-  if (s.status[b] != kRunning) return;
+  const Window w = window_of(a, s);
+  if (s.status[b] != kRunning || w.m_i == 0) return;
   const size_t off = (size_t)b * a.n;
   double acc[kMaxWindow];
 #pragma unroll
@@ -137,11 +193,11 @@ __global__ void __launch_bounds__(kThreads) dots_w_kernel(IterArgs a, State s) {
       const double wv = s.w[off + e];
 #pragma unroll
       for (int j = 0; j < kMaxWindow; ++j)
-        if (j < a.m_i) acc[j] = fma(wv, s.S[(size_t)a.slots[j] * a.B * a.n + off + e], acc[j]);
+        if (j < w.m_i) acc[j] = fma(wv, s.S[(size_t)w.slots[j] * a.B * a.n + off + e], acc[j]);
     }
   }
   block_sum<double, kMaxWindow>(acc, scratch);
-  if (threadIdx.x < a.m_i) {
+  if (threadIdx.x < w.m_i) {
     double v = acc[0];
 #pragma unroll
     for (int j = 1; j < kMaxWindow; ++j)
@@ -153,27 +209,29 @@ __global__ void __launch_bounds__(kThreads) dots_w_kernel(IterArgs a, State s) {
 __global__ void beta_kernel(IterArgs a, State s) {
   const int b = blockIdx.x;
   const int j = threadIdx.x;
-  if (s.status[b] != kRunning || j >= a.m_i) return;
+  const Window w = window_of(a, s);
+  if (s.status[b] != kRunning || j >= w.m_i) return;
   double sum = 0.0;
   for (int t = 0; t < a.tiles; ++t) sum += s.part[((size_t)b * a.tiles + t) * kParts + j];
-  s.beta[b * kMaxWindow + j] = sum / s.ps[(size_t)a.slots[j] * a.B + b];
+  s.beta[b * kMaxWindow + j] = sum / s.ps[(size_t)w.slots[j] * a.B + b];
 }
 
 __global__ void __launch_bounds__(kThreads) direction_kernel(IterArgs a, State s) {
   const int b = blockIdx.y;
   if (s.status[b] != kRunning) return;
+  const Window w = window_of(a, s);
   const size_t off = (size_t)b * a.n;
   double beta[kMaxWindow];
 #pragma unroll
-  for (int j = 0; j < kMaxWindow; ++j) beta[j] = (j < a.m_i) ? s.beta[b * kMaxWindow + j] : 0.0;
-  double* pn = s.P + (size_t)a.slot_new * a.B * a.n + off;
+  for (int j = 0; j < kMaxWindow; ++j) beta[j] = (j < w.m_i) ? s.beta[b * kMaxWindow + j] : 0.0;
+  double* pn = s.P + (size_t)w.slot_new * a.B * a.n + off;
   for (int t = 0; t < kEPT; ++t) {
     const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
     if (e < a.n) {
       double p = s.w[off + e];
 #pragma unroll
       for (int j = 0; j < kMaxWindow; ++j)
-        if (j < a.m_i) p = fma(-beta[j], s.P[(size_t)a.slots[j] * a.B * a.n + off + e], p);
+        if (j < w.m_i) p = fma(-beta[j], s.P[(size_t)w.slots[j] * a.B * a.n + off + e], p);
       pn[e] = p;
     }
   }
@@ -183,9 +241,10 @@ __global__ void __launch_bounds__(kThreads) stencil_dots_kernel(IterArgs a, Stat
   __shared__ double scratch[32 * 2];
   const int b = blockIdx.y;
   if (s.status[b] != kRunning) return;
+  const Window w = window_of(a, s);
   const size_t off = (size_t)b * a.n;
-  const double* pv = s.P + (size_t)a.slot_new * a.B * a.n + off;
-  double* sv = s.S + (size_t)a.slot_new * a.B * a.n + off;
+  const double* pv = s.P + (size_t)w.slot_new * a.B * a.n + off;
+  double* sv = s.S + (size_t)w.slot_new * a.B * a.n + off;
   double acc[2] = {0.0, 0.0};
   for (int t = 0; t < kEPT; ++t) {
     const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
@@ -213,6 +272,7 @@ __global__ void __launch_bounds__(kThreads) stencil_dots_kernel(IterArgs a, Stat
 __global__ void alpha_kernel(IterArgs a, State s) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.B || s.status[b] != kRunning) return;
+  const Window w = window_of(a, s);
   double ps = 0.0, pr = 0.0;
   for (int t = 0; t < a.tiles; ++t) {
     const double* pp = s.part + ((size_t)b * a.tiles + t) * kParts;
@@ -225,17 +285,18 @@ __global__ void alpha_kernel(IterArgs a, State s) {
     return;
   }
   s.alpha[b] = pr / ps;
-  s.ps[(size_t)a.slot_new * a.B + b] = ps;
+  s.ps[(size_t)w.slot_new * a.B + b] = ps;
 }
 
 __global__ void __launch_bounds__(kThreads) update_kernel(IterArgs a, State s) {
   __shared__ double scratch[32];
   const int b = blockIdx.y;
   if (s.status[b] != kRunning) return;
+  const Window w = window_of(a, s);
   const size_t off = (size_t)b * a.n;
   const double alpha = s.alpha[b];
-  const double* pv = s.P + (size_t)a.slot_new * a.B * a.n + off;
-  const double* sv = s.S + (size_t)a.slot_new * a.B * a.n + off;
+  const double* pv = s.P + (size_t)w.slot_new * a.B * a.n + off;
+  const double* sv = s.S + (size_t)w.slot_new * a.B * a.n + off;
   double acc[1] = {0.0};
   for (int t = 0; t < kEPT; ++t) {
     const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
@@ -253,11 +314,12 @@ __global__ void __launch_bounds__(kThreads) update_kernel(IterArgs a, State s) {
 __global__ void norm_kernel(IterArgs a, State s) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.B || s.status[b] != kRunning) return;
+  const Window w = window_of(a, s);
   double rr = 0.0;
   for (int t = 0; t < a.tiles; ++t) rr += s.part[((size_t)b * a.tiles + t) * kParts + 2];
   s.rr[b] = rr;
   s.rms[b] = sqrt(rr / (double)a.n);
-  s.iters[b] = a.i + 1;
+  s.iters[b] = w.i + 1;
   const double rn = sqrt(rr);
   if (rr == 0.0 || (!a.fixed && rn <= a.tol * s.r0[b])) {
     s.status[b] = FCGNO_OK;
@@ -269,13 +331,15 @@ __global__ void norm_kernel(IterArgs a, State s) {
 // One CTA per instance; thread t owns elements t + j*blockDim (j < 8); p staged in shared
 // memory for the stencil. Four fixed-order block reductions per iteration.
 __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
-  extern __shared__ double sp[];  // n doubles
-  __shared__ double scratch[32 * kMaxWindow];
+  extern __shared__ double sp[];  // n doubles (p), then kMaxWindow * blockDim (reductions)
+  __shared__ double red_out[kMaxWindow];
   const int b = blockIdx.x;
   if (s.status[b] != kRunning) return;
+  const Window wd = window_of(a, s);
   const size_t off = (size_t)b * a.n;
   const int T = blockDim.x;
   const int n = (int)a.n;
+  double* red = sp + n;
   double wv[kFusedEPT], rv[kFusedEPT], sv[kFusedEPT];
 #pragma unroll
   for (int j = 0; j < kFusedEPT; ++j) {
@@ -287,8 +351,8 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
 #pragma unroll
   for (int k = 0; k < kMaxWindow; ++k) {
     acc[k] = 0.0;
-    if (k < a.m_i) {
-      const double* Sk = s.S + (size_t)a.slots[k] * a.B * a.n + off;
+    if (k < wd.m_i) {
+      const double* Sk = s.S + (size_t)wd.slots[k] * a.B * a.n + off;
 #pragma unroll
       for (int j = 0; j < kFusedEPT; ++j) {
         const int e = threadIdx.x + j * T;
@@ -296,13 +360,13 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
       }
     }
   }
-  block_sum<double, kMaxWindow>(acc, scratch);
+  if (wd.m_i > 0) block_sums<kMaxWindow>(acc, wd.m_i, red, red_out);
   // p = w - sum beta_k p_k (kept in wv)
 #pragma unroll
   for (int k = 0; k < kMaxWindow; ++k) {
-    if (k < a.m_i) {
-      const double beta = acc[k] / s.ps[(size_t)a.slots[k] * a.B + b];
-      const double* Pk = s.P + (size_t)a.slots[k] * a.B * a.n + off;
+    if (k < wd.m_i) {
+      const double beta = acc[k] / s.ps[(size_t)wd.slots[k] * a.B + b];
+      const double* Pk = s.P + (size_t)wd.slots[k] * a.B * a.n + off;
 #pragma unroll
       for (int j = 0; j < kFusedEPT; ++j) {
         const int e = threadIdx.x + j * T;
@@ -310,7 +374,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
       }
     }
   }
-  double* Pn = s.P + (size_t)a.slot_new * a.B * a.n + off;
+  double* Pn = s.P + (size_t)wd.slot_new * a.B * a.n + off;
 #pragma unroll
   for (int j = 0; j < kFusedEPT; ++j) {
     const int e = threadIdx.x + j * T;
@@ -339,7 +403,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
       d2[1] = fma(wv[j], rv[j], d2[1]);
     }
   }
-  block_sum<double, 2>(d2, scratch);
+  block_sums<2>(d2, 2, red, red_out);
   const double ps = d2[0], pr = d2[1];
   if (!(ps != 0.0 && isfinite(ps) && isfinite(pr))) {
     if (threadIdx.x == 0) {
@@ -349,7 +413,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
     return;
   }
   const double alpha = pr / ps;
-  double* Sn = s.S + (size_t)a.slot_new * a.B * a.n + off;
+  double* Sn = s.S + (size_t)wd.slot_new * a.B * a.n + off;
   double rr[1] = {0.0};
 #pragma unroll
   for (int j = 0; j < kFusedEPT; ++j) {
@@ -362,13 +426,13 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
       rr[0] = fma(r1, r1, rr[0]);
     }
   }
-  block_sum<double, 1>(rr, scratch);
+  block_sums<1>(rr, 1, red, red_out);
   if (threadIdx.x == 0) {
-    s.ps[(size_t)a.slot_new * a.B + b] = ps;
+    s.ps[(size_t)wd.slot_new * a.B + b] = ps;
     s.alpha[b] = alpha;
     s.rr[b] = rr[0];
     s.rms[b] = sqrt(rr[0] / (double)a.n);
-    s.iters[b] = a.i + 1;
+    s.iters[b] = wd.i + 1;
     if (rr[0] == 0.0 || (!a.fixed && sqrt(rr[0]) <= a.tol * s.r0[b])) {
       s.status[b] = FCGNO_OK;
       atomicAdd(s.ndone, 1);
@@ -387,13 +451,20 @@ __global__ void harvest_copy_kernel(size_t total, const double* __restrict__ r, 
 }
 
 // ------------------------------------ host side ----------------------------------------
+static void drop_graph(SolverWorkspace& w) {
+  if (w.graph.exec) cudaGraphExecDestroy(w.graph.exec);
+  trace_release(w.graph.traced);
+  w.graph = IterGraph();
+}
+
 static void free_ws(SolverWorkspace& w) {
+  drop_graph(w);
   double** dp[] = {&w.r, &w.w, &w.P, &w.S, &w.ps, &w.beta, &w.alpha, &w.r0, &w.rr, &w.rms, &w.part};
   for (auto p : dp) {
     if (*p) cudaFree(*p);
     *p = nullptr;
   }
-  int** ip[] = {&w.status, &w.iters, &w.ndone};
+  int** ip[] = {&w.status, &w.iters, &w.ndone, &w.iter};
   for (auto p : ip) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -401,10 +472,22 @@ static void free_ws(SolverWorkspace& w) {
   w.cap_B = w.cap_n = w.cap_slots = w.cap_tiles = 0;
 }
 
-void solver_ws_free(fcgno_op* op) { free_ws(op->ws); }
+void solver_ws_free(fcgno_op* op) {
+  free_ws(op->ws);
+  if (op->ws.cs) cudaStreamDestroy(op->ws.cs);
+  if (op->ws.ev_in) cudaEventDestroy(op->ws.ev_in);
+  if (op->ws.ev_out) cudaEventDestroy(op->ws.ev_out);
+  op->ws.cs = nullptr;
+  op->ws.ev_in = op->ws.ev_out = nullptr;
+}
 
 static fcgno_status ensure_ws(fcgno_op* op, int slots) {
   SolverWorkspace& w = op->ws;
+  if (!w.cs) {
+    FCGNO_CUDA_TRY(cudaStreamCreateWithFlags(&w.cs, cudaStreamNonBlocking));
+    FCGNO_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_in, cudaEventDisableTiming));
+    FCGNO_CUDA_TRY(cudaEventCreateWithFlags(&w.ev_out, cudaEventDisableTiming));
+  }
   const int tiles = (int)ceil_div(op->n, kTile);
   if (w.cap_B == op->B && w.cap_n == (int)op->n && w.cap_slots >= slots && w.cap_tiles >= tiles) return FCGNO_OK;
   free_ws(w);
@@ -427,6 +510,7 @@ static fcgno_status ensure_ws(fcgno_op* op, int slots) {
   alloc((void**)&w.status, sizeof(int) * op->B);
   alloc((void**)&w.iters, sizeof(int) * op->B);
   alloc((void**)&w.ndone, sizeof(int));
+  alloc((void**)&w.iter, sizeof(int));
   if (!ok) {
     cudaGetLastError();
     free_ws(w);
@@ -462,6 +546,7 @@ static State make_state(fcgno_op* op, const double* b, double* x, const double* 
   s.status = w.status;
   s.iters = w.iters;
   s.ndone = w.ndone;
+  s.iter = w.iter;
   return s;
 }
 
@@ -471,12 +556,128 @@ struct HarvestHook {
   double* e_out = nullptr;
 };
 
+struct LoopShape {
+  bool fused;
+  int fusedThreads;
+  size_t fusedSmem;
+};
+
+static LoopShape loop_shape(const fcgno_op* op) {
+  LoopShape L;
+  L.fused = op->N <= kFusedMaxN;
+  L.fusedThreads = ((int)ceil_div(op->n, kFusedEPT) + 31) / 32 * 32;
+  L.fusedSmem = (op->n + (size_t)kMaxWindow * L.fusedThreads) * sizeof(double);
+  return L;
+}
+
+// The vector part of one iteration (steps a3-a7) plus the iteration-counter advance.
+static fcgno_status launch_vector_step(const IterArgs& a, const State& s, const LoopShape& L, cudaStream_t cs) {
+  if (L.fused) {
+    {
+      TraceScope ts("fcg_fused", cs);
+      fused_step_kernel<<<a.B, L.fusedThreads, L.fusedSmem, cs>>>(a, s);
+    }
+    FCGNO_LAUNCHED();
+  } else {
+    TraceScope ts("fcg_tiled", cs);
+    const dim3 grid(a.tiles, a.B);
+    dots_w_kernel<<<grid, kThreads, 0, cs>>>(a, s);
+    FCGNO_LAUNCHED();
+    beta_kernel<<<a.B, 32, 0, cs>>>(a, s);
+    FCGNO_LAUNCHED();
+    direction_kernel<<<grid, kThreads, 0, cs>>>(a, s);
+    FCGNO_LAUNCHED();
+    stencil_dots_kernel<<<grid, kThreads, 0, cs>>>(a, s);
+    FCGNO_LAUNCHED();
+    alpha_kernel<<<ceil_div(a.B, 128), 128, 0, cs>>>(a, s);
+    FCGNO_LAUNCHED();
+    update_kernel<<<grid, kThreads, 0, cs>>>(a, s);
+    FCGNO_LAUNCHED();
+    norm_kernel<<<ceil_div(a.B, 128), 128, 0, cs>>>(a, s);
+    FCGNO_LAUNCHED();
+  }
+  advance_kernel<<<1, 32, 0, cs>>>(s);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+static fcgno_status launch_iteration(fcgno_op* op, fcgno_model* model, fcgno_prec prec, const IterArgs& a,
+                                     const State& s, const LoopShape& L, cudaStream_t cs) {
+  if (model) {
+    SolverWorkspace& w = op->ws;
+    if (prec == FCGNO_BF16 || prec == FCGNO_FP16) {
+      FCGNO_TRY(no_apply_tc(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP16, cs));
+    } else {
+      FCGNO_TRY(no_apply_simt(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP64, cs));
+    }
+  }
+  return launch_vector_step(a, s, L, cs);
+}
+
+// Captures G iterations into a CUDA graph (reused while the baked-in parameters match).
+static fcgno_status ensure_graph(fcgno_op* op, fcgno_model* model, fcgno_prec prec, const IterArgs& a,
+                                 const State& s, const LoopShape& L, const double* b, const double* x, int G) {
+  SolverWorkspace& w = op->ws;
+  IterGraph& g = w.graph;
+  const uint64_t gen = model ? model->gen : 0;
+  if (g.exec && g.trace_gen == trace_generation() && g.model == model && g.model_gen == gen &&
+      g.prec == (int)prec && g.nslots == a.nslots &&
+      g.fixed == a.fixed && g.G == G && g.tol == a.tol && g.b == b && g.x == x)
+    return FCGNO_OK;
+  drop_graph(w);
+  const uint64_t l0 = g_launches.load();
+  FCGNO_CUDA_TRY(cudaStreamBeginCapture(w.cs, cudaStreamCaptureModeThreadLocal));
+  trace_capture_begin(&g.traced);
+  fcgno_status rc = FCGNO_OK;
+  for (int it = 0; it < G && rc == FCGNO_OK; ++it) rc = launch_iteration(op, model, prec, a, s, L, w.cs);
+  trace_capture_end();
+  // captured launches did not run: they are counted when the graph replays
+  g.kernels = g_launches.load() - l0;
+  g_launches.fetch_sub(g.kernels);
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(w.cs, &graph);
+  if (rc != FCGNO_OK || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    trace_release(g.traced);
+    if (rc == FCGNO_OK) {
+      set_last_error(std::string("graph capture: ") + cudaGetErrorString(ec));
+      rc = FCGNO_ECUDA;
+    }
+    return rc;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&g.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ei != cudaSuccess) {
+    g.exec = nullptr;
+    trace_release(g.traced);
+    set_last_error(std::string("graph instantiate: ") + cudaGetErrorString(ei));
+    return FCGNO_ECUDA;
+  }
+  g.trace_gen = trace_generation();
+  g.model = model;
+  g.model_gen = gen;
+  g.prec = (int)prec;
+  g.nslots = a.nslots;
+  g.fixed = a.fixed;
+  g.G = G;
+  g.tol = a.tol;
+  g.b = b;
+  g.x = x;
+  return FCGNO_OK;
+}
+
+static bool graphs_enabled() {
+  const char* e = getenv("FCGNO_GRAPHS");
+  return !(e && e[0] == '0');
+}
+
 static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b, double* x,
                                const fcgno_solve_opts& o, fcgno_prec prec, fcgno_solve_info* info,
                                cudaStream_t st, const HarvestHook* hook) {
   const int slots = o.m_max + 1;
   FCGNO_TRY(ensure_ws(op, slots));
   SolverWorkspace& w = op->ws;
+  const cudaStream_t cs = w.cs;
   const bool identity = (model == nullptr);
   // with the identity preconditioner w_i = r_i: read r in place of w
   State s = make_state(op, b, x, identity ? w.r : w.w);
@@ -485,18 +686,21 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
   a.B = op->B;
   a.n = op->n;
   a.tiles = (int)ceil_div(op->n, kTile);
+  a.nslots = slots;
   a.tol = o.tol;
   a.fixed = o.fixed_iters ? 1 : 0;
-  const bool fused = op->N <= kFusedMaxN;
-  const int fusedThreads = ((int)ceil_div(op->n, kFusedEPT) + 31) / 32 * 32;
-  const size_t fusedSmem = op->n * sizeof(double);
-  if (fused && fusedSmem > 48 * 1024)
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fusedSmem));
-
-  FCGNO_CUDA_TRY(cudaMemsetAsync(w.ndone, 0, sizeof(int), st));
-  init_kernel<<<dim3(a.tiles, op->B), kThreads, 0, st>>>(a, s);
+  const LoopShape L = loop_shape(op);
+  if (L.fused && L.fusedSmem > 48 * 1024)
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)L.fusedSmem));
+  // the caller's stream orders our internal stream at entry and exit
+  FCGNO_CUDA_TRY(cudaEventRecord(w.ev_in, st));
+  FCGNO_CUDA_TRY(cudaStreamWaitEvent(cs, w.ev_in, 0));
+  FCGNO_CUDA_TRY(cudaMemsetAsync(w.ndone, 0, sizeof(int), cs));
+  FCGNO_CUDA_TRY(cudaMemsetAsync(w.iter, 0, sizeof(int), cs));
+  init_kernel<<<dim3(a.tiles, op->B), kThreads, 0, cs>>>(a, s);
   FCGNO_LAUNCHED();
-  init_finalize_kernel<<<ceil_div(op->B, 128), 128, 0, st>>>(a, s);
+  init_finalize_kernel<<<ceil_div(op->B, 128), 128, 0, cs>>>(a, s);
   FCGNO_LAUNCHED();
 
   int* h_ndone = nullptr;
@@ -505,66 +709,48 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
     int* p;
     ~PinnedGuard() { cudaFreeHost(p); }
   } guard{h_ndone};
-  const int check_every = std::max(1, o.check_every);
-  for (int i = 0; i < o.max_iter; ++i) {
-    a.i = i;
-    a.m_i = std::min(i, std::max(1, i % slots));
-    a.slot_new = i % slots;
-    for (int j = 0; j < kMaxWindow; ++j) a.slots[j] = (j < a.m_i) ? (i - a.m_i + j) % slots : 0;
-    if (!identity) {
-      if (prec == FCGNO_BF16 || prec == FCGNO_FP16) {
-        FCGNO_TRY(no_apply_tc(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP16, st));
-      } else {
-        FCGNO_TRY(no_apply_simt(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP64, st));
-      }
-    }
-    if (fused) {
-      {
-        TraceScope ts("fcg_fused", st);
-        fused_step_kernel<<<op->B, fusedThreads, fusedSmem, st>>>(a, s);
-      }
-      FCGNO_LAUNCHED();
+  const int G = std::max(1, o.check_every);
+  const bool use_graph = !hook && graphs_enabled() && G > 1;
+  int i = 0;
+  int since_check = 0;
+  while (i < o.max_iter) {
+    bool replayed = false;
+    if (use_graph && i > 0 && o.max_iter - i >= G) {
+      // the first iteration ran eagerly, so every lazily allocated buffer exists before capture
+      FCGNO_TRY(ensure_graph(op, model, prec, a, s, L, b, x, G));
+      FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph.exec, cs));
+      g_launches.fetch_add(w.graph.kernels, std::memory_order_relaxed);
+      i += G;
+      since_check = G;
+      replayed = true;
     } else {
-      TraceScope ts("fcg_tiled", st);
-      const dim3 grid(a.tiles, op->B);
-      if (a.m_i > 0) {
-        dots_w_kernel<<<grid, kThreads, 0, st>>>(a, s);
-        FCGNO_LAUNCHED();
-        beta_kernel<<<op->B, 32, 0, st>>>(a, s);
+      FCGNO_TRY(launch_iteration(op, model, prec, a, s, L, cs));
+      if (hook) {
+        const size_t total = op->n * op->B;
+        const size_t o2 = (size_t)i * total;
+        harvest_copy_kernel<<<ceil_div(total, 256), 256, 0, cs>>>(total, w.r, x, hook->ustar, hook->r_out + o2,
+                                                                  hook->e_out + o2);
         FCGNO_LAUNCHED();
       }
-      direction_kernel<<<grid, kThreads, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-      stencil_dots_kernel<<<grid, kThreads, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-      alpha_kernel<<<ceil_div(op->B, 128), 128, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-      update_kernel<<<grid, kThreads, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-      norm_kernel<<<ceil_div(op->B, 128), 128, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
+      ++i;
+      ++since_check;
     }
-    if (hook) {
-      const size_t total = op->n * op->B;
-      const size_t o2 = (size_t)i * total;
-      harvest_copy_kernel<<<ceil_div(total, 256), 256, 0, st>>>(total, w.r, x, hook->ustar, hook->r_out + o2,
-                                                                 hook->e_out + o2);
-      FCGNO_LAUNCHED();
-    }
-    if ((i + 1) % check_every == 0 || i + 1 == o.max_iter) {
-      FCGNO_CUDA_TRY(cudaMemcpyAsync(h_ndone, w.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
-      FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+    if (since_check >= G || i >= o.max_iter || (use_graph && i == 1)) {
+      since_check = 0;
+      FCGNO_CUDA_TRY(cudaMemcpyAsync(h_ndone, w.ndone, sizeof(int), cudaMemcpyDeviceToHost, cs));
+      FCGNO_CUDA_TRY(cudaStreamSynchronize(cs));
+      if (replayed) trace_accumulate(w.graph.traced);
       if (*h_ndone >= op->B && !hook) break;
     }
   }
   if (info) {
     std::vector<int> hs(op->B), hi(op->B);
     std::vector<double> hrr(op->B), hr0(op->B);
-    FCGNO_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.status, sizeof(int) * op->B, cudaMemcpyDeviceToHost, st));
-    FCGNO_CUDA_TRY(cudaMemcpyAsync(hi.data(), w.iters, sizeof(int) * op->B, cudaMemcpyDeviceToHost, st));
-    FCGNO_CUDA_TRY(cudaMemcpyAsync(hrr.data(), w.rr, sizeof(double) * op->B, cudaMemcpyDeviceToHost, st));
-    FCGNO_CUDA_TRY(cudaMemcpyAsync(hr0.data(), w.r0, sizeof(double) * op->B, cudaMemcpyDeviceToHost, st));
-    FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hs.data(), w.status, sizeof(int) * op->B, cudaMemcpyDeviceToHost, cs));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hi.data(), w.iters, sizeof(int) * op->B, cudaMemcpyDeviceToHost, cs));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hrr.data(), w.rr, sizeof(double) * op->B, cudaMemcpyDeviceToHost, cs));
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(hr0.data(), w.r0, sizeof(double) * op->B, cudaMemcpyDeviceToHost, cs));
+    FCGNO_CUDA_TRY(cudaStreamSynchronize(cs));
     for (int bi = 0; bi < op->B; ++bi) {
       info[bi].iters = hi[bi];
       int stt = hs[bi];
@@ -574,8 +760,10 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
       info[bi].relres = hr0[bi] > 0 ? std::sqrt(hrr[bi]) / hr0[bi] : 0.0;
     }
   } else {
-    FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+    FCGNO_CUDA_TRY(cudaStreamSynchronize(cs));
   }
+  FCGNO_CUDA_TRY(cudaEventRecord(w.ev_out, cs));
+  FCGNO_CUDA_TRY(cudaStreamWaitEvent(st, w.ev_out, 0));
   return FCGNO_OK;
 }
 
@@ -747,7 +935,7 @@ extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, doubl
                             sizeof(int) * B,
                             sizeof(int) * B,
                             sizeof(int),
-                            0};
+                            sizeof(int)};
   size_t total = 0;
   for (int i = 0; i < 14; ++i) {
     off[i] = total;
@@ -782,20 +970,23 @@ extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, doubl
   s.status = (int*)(base + off[10]);
   s.iters = (int*)(base + off[11]);
   s.ndone = (int*)(base + off[12]);
+  s.iter = (int*)(base + off[13]);
   IterArgs a{};
   a.N = A->N;
   a.B = B;
   a.n = A->n;
   a.tiles = tiles;
+  a.nslots = slots;
   a.tol = o.tol;
   a.fixed = o.fixed_iters ? 1 : 0;
-  const bool fused = A->N <= kFusedMaxN;
-  const int fusedThreads = ((int)ceil_div(A->n, kFusedEPT) + 31) / 32 * 32;
-  const size_t fusedSmem = A->n * sizeof(double);
-  if (fused && fusedSmem > 48 * 1024)
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fusedSmem));
-  // the stopped-instance counter must start at zero: the array keeps the previous call's data
+  const LoopShape L = loop_shape(A);
+  if (L.fused && L.fusedSmem > 48 * 1024)
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)L.fusedSmem));
+  // the stopped-instance and iteration counters must start at zero: the array keeps the
+  // previous call's data
   FCGNO_CUDA_TRY(cudaMemsetAsync(s.ndone, 0, sizeof(int), st));
+  FCGNO_CUDA_TRY(cudaMemsetAsync(s.iter, 0, sizeof(int), st));
   init_kernel<<<dim3(a.tiles, B), kThreads, 0, st>>>(a, s);
   FCGNO_LAUNCHED();
   init_finalize_kernel<<<ceil_div(B, 128), 128, 0, st>>>(a, s);
@@ -803,32 +994,7 @@ extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, doubl
   const int check_every = std::max(1, o.check_every);
   int h_ndone = 0;
   for (int i = 0; i < o.max_iter; ++i) {
-    a.i = i;
-    a.m_i = std::min(i, std::max(1, i % slots));
-    a.slot_new = i % slots;
-    for (int j = 0; j < kMaxWindow; ++j) a.slots[j] = (j < a.m_i) ? (i - a.m_i + j) % slots : 0;
-    if (fused) {
-      fused_step_kernel<<<B, fusedThreads, fusedSmem, st>>>(a, s);
-      FCGNO_LAUNCHED();
-    } else {
-      const dim3 grid(a.tiles, B);
-      if (a.m_i > 0) {
-        dots_w_kernel<<<grid, kThreads, 0, st>>>(a, s);
-        FCGNO_LAUNCHED();
-        beta_kernel<<<B, 32, 0, st>>>(a, s);
-        FCGNO_LAUNCHED();
-      }
-      direction_kernel<<<grid, kThreads, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-      stencil_dots_kernel<<<grid, kThreads, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-      alpha_kernel<<<ceil_div(B, 128), 128, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-      update_kernel<<<grid, kThreads, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-      norm_kernel<<<ceil_div(B, 128), 128, 0, st>>>(a, s);
-      FCGNO_LAUNCHED();
-    }
+    FCGNO_TRY(launch_vector_step(a, s, L, st));
     if ((i + 1) % check_every == 0 || i + 1 == o.max_iter) {
       FCGNO_CUDA_TRY(cudaMemcpyAsync(&h_ndone, s.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
       FCGNO_CUDA_TRY(cudaStreamSynchronize(st));

@@ -8,6 +8,7 @@
 #include <cstddef>
 #include <atomic>
 #include <string>
+#include <vector>
 
 #include "../../include/fcgno.h"
 
@@ -24,6 +25,7 @@ extern std::atomic<uint64_t> g_launches;
     cudaError_t e_ = (call);                                                                 \
     if (e_ != cudaSuccess) {                                                                 \
       ::fcgno::set_last_error(std::string(#call) + ": " + cudaGetErrorString(e_));           \
+      cudaGetLastError(); /* clear a non-sticky error so later checks do not see it */      \
       return FCGNO_ECUDA;                                                                    \
     }                                                                                        \
   } while (0)
@@ -50,6 +52,14 @@ extern std::atomic<uint64_t> g_launches;
 bool trace_enabled(const char* family);
 void trace_begin(const char* family, cudaStream_t st);
 void trace_end(const char* family, cudaStream_t st);
+// While a CUDA graph is being captured, traced launches become event-record nodes; their
+// event pairs go to `list`, and trace_accumulate adds their durations after each replay.
+using EventPairs = std::vector<std::pair<cudaEvent_t, cudaEvent_t>>;
+void trace_capture_begin(EventPairs* list);
+void trace_capture_end();
+void trace_accumulate(const EventPairs& pairs);
+void trace_release(EventPairs& pairs);
+uint64_t trace_generation();  // changes whenever the traced family changes
 struct TraceScope {
   const char* fam;
   cudaStream_t st;
@@ -69,8 +79,26 @@ constexpr int kMaxWindow = 8;  // largest m_max supported
 // ---------------------------------------------------------------------------------------
 // Handles
 // ---------------------------------------------------------------------------------------
+// A captured CUDA graph of several solver iterations and the parameters baked into it.
+struct IterGraph {
+  cudaGraphExec_t exec = nullptr;
+  uint64_t kernels = 0;  // kernel nodes per replay
+  uint64_t trace_gen = 0;
+  const void* model = nullptr;
+  uint64_t model_gen = 0;
+  int prec = -1, nslots = 0, fixed = 0, G = 0;
+  double tol = 0.0;
+  const void* b = nullptr;
+  const void* x = nullptr;
+  EventPairs traced;
+};
+
 struct SolverWorkspace {
   int cap_B = 0, cap_n = 0, cap_slots = 0, cap_tiles = 0;
+  cudaStream_t cs = nullptr;     // internal stream (graph capture needs a non-default stream)
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  IterGraph graph;
+  int* iter = nullptr;      // [1] device iteration counter
   double* r = nullptr;      // [B][n]
   double* w = nullptr;      // [B][n]  preconditioned residual
   double* P = nullptr;      // [slots][B][n] directions p_k
@@ -96,6 +124,7 @@ struct fcgno_op {
   double* aN = nullptr;    // [B][n] north-face coefficient / h^2 (boundary face at q = N-1)
   double* diag = nullptr;  // [B][n] sum of the four face coefficients / h^2
   double* logk = nullptr;  // [B][n]
+  float* logk32 = nullptr; // [B][n] (input of the 16-bit preconditioner)
   fcgno::SolverWorkspace ws;
 };
 
@@ -113,6 +142,7 @@ struct fcgno_model {
   size_t count = 0;             // floats in the blob
   fcgno::NoWorkspace* ws = nullptr;
   fcgno::TcModel* tc = nullptr;
+  uint64_t gen = 0;             // bumped whenever a derived device buffer is (re)allocated
 };
 
 namespace fcgno {

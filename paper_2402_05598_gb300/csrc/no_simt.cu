@@ -150,6 +150,7 @@ static fcgno_status ensure_twiddles(fcgno_model* m, int N, cudaStream_t st) {
   FCGNO_LAUNCHED();
   t.N = N;
   t.M = M;
+  m->gen++;
   return FCGNO_OK;
 }
 
@@ -425,6 +426,7 @@ static fcgno_status ensure_simt(fcgno_model* m, const fcgno_op* op, SimtBuffers&
   s.cap_elems = elems;
   s.cap_spec = spec;
   s.cap_mid = mid;
+  m->gen++;
   return FCGNO_OK;
 }
 

@@ -252,6 +252,7 @@ void tc_model_free(fcgno_model* m) {
 
 fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t) {
   // weights changed: drop derived copies; they are rebuilt on next use
+  m->gen++;
   if (m->tc)
     for (auto& p : m->tc->prec) {
       for (auto x : p.W) cudaFree(x);
@@ -288,6 +289,7 @@ static fcgno_status ensure_prec(fcgno_model* m, bool fp16, cudaStream_t st) {
   tc_cast_kernel<<<ceil_div(Cp * C, 256), 256, 0, st>>>(Cp * C, m->w32 + BL.proj1_w, P.P1, bf16);
   FCGNO_LAUNCHED();
   P.built = true;
+  m->gen++;
   return FCGNO_OK;
 }
 
@@ -311,35 +313,46 @@ static fcgno_status ensure_tables(fcgno_model* m, bool fp16, const TcGeom& g, Tc
   FCGNO_LAUNCHED();
   P.tables[g.N] = t;
   out = &P.tables[g.N];
+  m->gen++;
   return FCGNO_OK;
 }
 
 // ------------------------------------ kernels ------------------------------------------
 __device__ __forceinline__ bool tc_inactive(const int* active, int b) { return active && active[b] >= 0; }
 
-// Encoder: v0 = lift_w [r/rms, log k] + lift_b, written as 16-bit channels-last.
-__global__ void tc_lift_kernel(size_t n, int C, const double* __restrict__ r, const double* __restrict__ logk,
+// Encoder: v0 = lift_w [r/rms, log k] + lift_b, written as 16-bit channels-last. One thread
+// per grid point; the only FP64 work is reading r (1/rms is formed once per thread in FP32).
+template <int C>
+__global__ void tc_lift_kernel(size_t n, const double* __restrict__ r, const float* __restrict__ logk,
                                const double* __restrict__ rms, const int* __restrict__ active,
                                const float* __restrict__ lw, const float* __restrict__ lb, uint16_t* __restrict__ v,
                                bool bf16) {
+  __shared__ float w0[C], w1[C], bb[C];
   const int b = blockIdx.y;
-  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;  // (point, 8-channel group)
-  const int groups = C / 8;
-  if (idx >= n * groups || tc_inactive(active, b)) return;
-  const size_t x = idx / groups;
-  const int c0 = (int)(idx % groups) * 8;
-  const double s = rms[b];
-  const float rh = s > 0.0 ? (float)(r[(size_t)b * n + x] / s) : 0.f;
-  const float lk = (float)logk[(size_t)b * n + x];
-  uint32_t w[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int c = c0 + 2 * i;
-    const float a0 = fmaf(lw[2 * c], rh, fmaf(lw[2 * c + 1], lk, lb[c]));
-    const float a1 = fmaf(lw[2 * c + 2], rh, fmaf(lw[2 * c + 3], lk, lb[c + 1]));
-    w[i] = pack2(a0, a1, bf16);
+  if (tc_inactive(active, b)) return;
+  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+    w0[c] = lw[2 * c];
+    w1[c] = lw[2 * c + 1];
+    bb[c] = lb[c];
   }
-  *reinterpret_cast<uint4*>(v + ((size_t)b * n + x) * C + c0) = make_uint4(w[0], w[1], w[2], w[3]);
+  __syncthreads();
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (x >= n) return;
+  const float s = (float)rms[b];
+  const float inv = s > 0.f ? 1.0f / s : 0.f;
+  const float rh = (float)r[(size_t)b * n + x] * inv;
+  const float lk = logk[(size_t)b * n + x];
+  uint4* dst = reinterpret_cast<uint4*>(v + ((size_t)b * n + x) * C);
+#pragma unroll
+  for (int c0 = 0; c0 < C; c0 += 8) {
+    uint32_t w[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int c = c0 + 2 * i;
+      w[i] = pack2(fmaf(w0[c], rh, fmaf(w1[c], lk, bb[c])), fmaf(w0[c + 1], rh, fmaf(w1[c + 1], lk, bb[c + 1])), bf16);
+    }
+    dst[c0 / 8] = make_uint4(w[0], w[1], w[2], w[3]);
+  }
 }
 
 // Truncated analysis of one grid-column chunk of one instance; writes FP32 partial sums
@@ -882,6 +895,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     T.cap_v = need_v;
     T.cap_part = need_part;
     T.cap_chat = need_chat;
+    m->gen++;
   }
   static int* d_err = nullptr;
   if (!d_err) {
@@ -892,15 +906,26 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   const bool bf16 = !fp16;
   {
     TraceScope ts("tc_lift", st);
-    tc_lift_kernel<<<dim3(ceil_div(n * (C / 8), 256), B), 256, 0, st>>>(n, C, r, op->logk, rms, active,
-                                                                        m->w32 + BL.lift_w, m->w32 + BL.lift_b, T.va,
-                                                                        bf16);
+    tc_lift_kernel<C><<<dim3(ceil_div(n, 256), B), 256, 0, st>>>(n, r, op->logk32, rms, active, m->w32 + BL.lift_w,
+                                                                 m->w32 + BL.lift_b, T.va, bf16);
   }
   FCGNO_LAUNCHED();
   const size_t sa = analysis_smem(g), ss = synthesis_smem(g), sm = mix_smem(C);
-  FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_analysis_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
-  FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_synthesis_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss));
-  FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_mix_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  // raise the dynamic shared-memory limit only when a larger plan appears (not a stream
+  // operation; the first solve iteration runs eagerly, before any graph capture)
+  static size_t set_sa = 0, set_ss = 0, set_sm = 0;
+  if (sa > set_sa) {
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_analysis_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
+    set_sa = sa;
+  }
+  if (ss > set_ss) {
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_synthesis_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss));
+    set_ss = ss;
+  }
+  if (sm > set_sm) {
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_mix_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    set_sm = sm;
+  }
   uint16_t* cur = T.va;
   uint16_t* nxt = T.vb;
   for (int l = 0; l < d.layers; ++l) {

@@ -16,7 +16,7 @@ __device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a 
 
 __global__ void assemble_kernel(int N, size_t n, size_t total, const double* __restrict__ k,
                                 double* __restrict__ aE, double* __restrict__ aN,
-                                double* __restrict__ diag, double* __restrict__ logk) {
+                                double* __restrict__ diag, double* __restrict__ logk, float* __restrict__ logk32) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
   const size_t b = i / n;
@@ -34,7 +34,9 @@ __global__ void assemble_kernel(int N, size_t n, size_t total, const double* __r
   aE[i] = e * inv_h2;
   aN[i] = nn * inv_h2;
   diag[i] = (e + w + nn + s) * inv_h2;
-  logk[i] = log(kP);
+  const double lk = log(kP);
+  logk[i] = lk;
+  logk32[i] = (float)lk;
 }
 
 __global__ void apply_A_kernel(int N, size_t n, size_t total, const double* __restrict__ aE,
@@ -92,14 +94,16 @@ extern "C" fcgno_status fcgno_assemble(int N, int batch, const double* k, void* 
   op->n = (size_t)N * N;
   const size_t bytes = op->n * batch * sizeof(double);
   if (cudaMalloc(&op->aE, bytes) != cudaSuccess || cudaMalloc(&op->aN, bytes) != cudaSuccess ||
-      cudaMalloc(&op->diag, bytes) != cudaSuccess || cudaMalloc(&op->logk, bytes) != cudaSuccess) {
+      cudaMalloc(&op->diag, bytes) != cudaSuccess || cudaMalloc(&op->logk, bytes) != cudaSuccess ||
+      cudaMalloc(&op->logk32, bytes / 2) != cudaSuccess) {
     cudaGetLastError();
     fcgno_op_destroy(op);
     set_last_error("fcgno_assemble: out of device memory");
     return FCGNO_ENOMEM;
   }
   const size_t total = op->n * batch;
-  assemble_kernel<<<ceil_div(total, 256), 256, 0, st>>>(N, op->n, total, k, op->aE, op->aN, op->diag, op->logk);
+  assemble_kernel<<<ceil_div(total, 256), 256, 0, st>>>(N, op->n, total, k, op->aE, op->aN, op->diag, op->logk,
+                                                        op->logk32);
   g_launches.fetch_add(1, std::memory_order_relaxed);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {

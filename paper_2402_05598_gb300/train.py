@@ -51,8 +51,10 @@ class KrylovData:
 
 def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, lr: float = 1e-3,
           steps: int = 1000, seconds: float | None = None, prec: str = "fp32", seed: int = 0,
-          sigma: float = 1.0, ell: float = 0.1, log_every: int = 0) -> TrainResult:
-    """Trains ``model.weights`` in place; returns the loss history."""
+          sigma: float = 1.0, ell: float = 0.1, log_every: int = 0, decay_at=(0.5, 0.75)) -> TrainResult:
+    """Trains ``model.weights`` in place; returns the loss history. The learning rate is
+    halved at the given fractions of ``steps`` (the paper halves it on a fixed schedule,
+    Table 6)."""
     import torch
     dev = model.weights.device
     t0 = time.perf_counter()
@@ -72,7 +74,11 @@ def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, 
     losses = []
     t1 = time.perf_counter()
     step = 0
+    decay_steps = {int(f * steps) for f in decay_at}
     while step < steps and (seconds is None or time.perf_counter() - t1 < seconds):
+        if step in decay_steps:
+            for pg in opt.param_groups:
+                pg["lr"] *= 0.5
         d = groups[step % len(groups)]
         idx = torch.randint(0, K, (batch,), generator=gen, device=dev)
         r = d.r[idx, ar].contiguous()

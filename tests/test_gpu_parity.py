@@ -24,6 +24,18 @@ def to_dev(x, dev, dtype=None):
     return t.to(dev)
 
 
+def exact_dot(a, b):
+    return math.fsum(np.ravel(a * b))
+
+
+def rounding_tol(run, floor=1e-10):
+    """Tolerance for an FP64 iterate: 10x the change of the oracle's own result when its dot
+    products are exactly rounded instead of pairwise-summed (the recurrences of Algorithm 1
+    amplify rounding; a GPU reduction order is one more valid rounding)."""
+    a, b = run(None), run(exact_dot)
+    return max(floor, 10.0 * rel(b, a))
+
+
 def batch(N, B, seed0, sigma=1.0, ell=0.1):
     return I.make_batch(N, range(seed0, seed0 + B), sigma, ell)
 
@@ -58,8 +70,9 @@ def test_stencil_matches_oracle(lib, dev, N, B):
 # ------------------------------------------------------------------------------- CG / FCG(B=I)
 @pytest.mark.parametrize("N,B,m", [(33, 2, 1), (64, 3, 5), (100, 2, 1), (130, 1, 3)])
 def test_identity_preconditioned_iterates_match_oracle(lib, dev, N, B, m):
-    """Fused path (N <= 90) and tiled path (N > 90): 20 fixed iterations of Algorithm 1 with
-    B = I, iterate compared with the oracle (rel 1e-10)."""
+    """Fused path (N <= 80) and tiled path (N > 80): 20 fixed iterations of Algorithm 1 with
+    B = I, iterate compared with the oracle within max(1e-10, 10x the oracle's own rounding
+    sensitivity)."""
     import torch
     k, f = batch(N, B, 200 + N)
     x0 = np.random.default_rng(N).standard_normal((B, N, N))
@@ -69,8 +82,10 @@ def test_identity_preconditioned_iterates_match_oracle(lib, dev, N, B, m):
     xs = x.cpu().numpy()
     for b in range(B):
         ref = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: r, f[b], x0[b], m, 20)
+        tol = rounding_tol(lambda d: O.fcg(lambda u: O.apply_A(k[b], u), lambda r: r, f[b], x0[b], m, 20,
+                                           **({} if d is None else {"dot": d}))["u"])
         assert info[b]["iters"] == 20
-        assert rel(xs[b], ref["u"]) < 1e-10
+        assert rel(xs[b], ref["u"]) < tol
         assert abs(info[b]["relres"] - ref["relres"][-1]) <= 1e-8 * ref["relres"][-1]
 
 
