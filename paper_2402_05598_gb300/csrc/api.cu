@@ -46,16 +46,24 @@ bool trace_enabled(const char* family) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   return !g_trace_family.empty() && g_trace_family == family;
 }
+// Inside a stream capture an ordinary event record cannot be timed afterwards; an external
+// event-record node re-records the event on every replay like a plain cudaEventRecord.
+static cudaError_t trace_record(cudaEvent_t e, cudaStream_t st) {
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(st, &cap);
+  if (cap == cudaStreamCaptureStatusActive) return cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+  return cudaEventRecord(e, st);
+}
 void trace_begin(const char*, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   g_trace_open = trace_event();
-  const cudaError_t e = cudaEventRecord(g_trace_open, st);
+  const cudaError_t e = trace_record(g_trace_open, st);
   if (e != cudaSuccess) trace_note_failure(e);
 }
 void trace_end(const char*, cudaStream_t st) {
   std::lock_guard<std::mutex> lk(g_trace_mu);
   cudaEvent_t e = trace_event();
-  const cudaError_t er = cudaEventRecord(e, st);
+  const cudaError_t er = trace_record(e, st);
   if (er != cudaSuccess) trace_note_failure(er);
   if (g_trace_capture)
     g_trace_capture->emplace_back(g_trace_open, e);

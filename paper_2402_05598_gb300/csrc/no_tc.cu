@@ -47,8 +47,10 @@ struct TcGeom {
   int KXP;                // Kx4 padded to 16
   int NPM;                // rows of G (= Kx4 padded to 16): N dimension of analysis stage P
   int MP;                 // Ky*C padded to 128
-  int PC;                 // grid columns per CTA chunk
+  int PC;                 // grid columns per analysis block (partial-sum chunk)
   int nchunks;            // N / PC
+  int SPC;                // grid columns per synthesis block
+  int snchunks;           // N / SPC
   int QC;                 // q rows per analysis K chunk
   int PT, QT;             // synthesis tile: PT columns x QT rows (= 128 points)
   int KSYN;               // K of the synthesis-stage-2 part, padded to 16
@@ -66,9 +68,10 @@ static TcGeom make_geom(int N, int C, int M) {
   g.KXP = round_up(4 * M, 16);
   g.NPM = round_up(4 * M, 16);
   g.MP = round_up(M * C, 128);
-  g.PC = N < 64 ? N : 64;
-  // the synthesis stage-1 accumulator (MP/128 tiles x 2PC columns) must fit 384 TMEM columns
-  while ((g.MP / 128) * 2 * g.PC > 384 && g.PC > 16) g.PC /= 2;
+  g.PC = N < 32 ? N : 32;
+  // the synthesis stage-1 accumulator (MP/128 tiles x 2PC columns) must fit the 256 TMEM
+  // columns a block allocates (two blocks share an SM's 512 columns)
+  while ((g.MP / 128) * 2 * g.PC > 256 && g.PC > 8) g.PC /= 2;
   g.nchunks = N / g.PC;
   g.QC = N < 64 ? N : 64;
   if (N < 128) {
@@ -80,7 +83,11 @@ static TcGeom make_geom(int N, int C, int M) {
     g.QT = 128;
     g.KSYN = round_up(2 * M, 16);
   }
-  g.KB = round_up(g.PC * 2 * M, 16) + 16;
+  // synthesis: narrower column chunks (more, smaller blocks; lower latency per instance)
+  g.SPC = g.PC < 16 ? g.PC : 16;
+  while (g.SPC % g.PT != 0) g.SPC *= 2;
+  g.snchunks = N / g.SPC;
+  g.KB = round_up(g.SPC * 2 * M, 16) + 16;
   g.nmodes = 2 * M * M;
   return g;
 }
@@ -88,7 +95,7 @@ static TcGeom make_geom(int N, int C, int M) {
 static bool geom_supported(int N, int C, int M, int Cp) {
   if (!(C == 16 || C == 32) || Cp != C || M < 1 || M > 16 || N < 2 * M) return false;
   if (!(N == 32 || N == 64 || (N >= 128 && N % 128 == 0))) return false;
-  if ((std::min(N, 64) * C) % 128 != 0) return false;
+  if ((std::min(N, 32) * C) % 128 != 0) return false;
   return true;
 }
 
@@ -358,28 +365,32 @@ __global__ void tc_lift_kernel(size_t n, const double* __restrict__ r, const flo
 // Truncated analysis of one grid-column chunk of one instance; writes FP32 partial sums
 // part[b][chunk][mode = j*Ky + k2][c][re/im].
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __launch_bounds__(kTcThreads, 2)
     tc_analysis_kernel(TcGeom g, bool bf16, const int* __restrict__ active, const uint16_t* __restrict__ v,
                        const uint16_t* __restrict__ E2, const uint16_t* __restrict__ G, float* __restrict__ part,
                        int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t mbar, mbar2[2];
   __shared__ uint32_t tbase_s;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(active, b)) return;
   const int N = g.N, PC = g.PC, QC = g.QC, Ky = g.Ky;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // shared layout
-  uint8_t* sE2 = smem;                              // 32 x QC, K-major: LBO 128, SBO QC*16
-  uint8_t* sA = sE2 + 32 * QC * 2;                  // 128 x QC, MN-major: SBO 128, LBO 2048
-  uint8_t* sAP = sA + 128 * QC * 2;                 // MP x 2PC, K-major: LBO 128, SBO 2PC*16
+  uint8_t* sE2 = smem;                              // 2 x (32 x QC), K-major: LBO 128, SBO QC*16
+  uint8_t* sA = sE2 + 2 * 32 * QC * 2;              // 2 x (128 x QC), MN-major: SBO 128, LBO 2048
+  uint8_t* sAP = sA + 2 * 128 * QC * 2;             // MP x 2PC, K-major: LBO 128, SBO 2PC*16
   uint8_t* sG = sAP + (size_t)g.MP * 2 * PC * 2;    // NPM x 2PC, K-major: LBO 128, SBO 2PC*16
   const uint32_t SBO_E = QC * 16, SBO_P = 2 * PC * 16, SBO_G = 2 * PC * 16;
   const uint32_t LBO_A = 2048;  // k-direction stride of the MN-major stage-Q operand (16 m-core matrices)
 
-  const uint32_t tcols = (32 + (g.MP / 128) * g.NPM) <= 256 ? 256u : 512u;
+  const uint32_t tcols = (64 + (g.MP / 128) * g.NPM) <= 256 ? 256u : 512u;
   if (warp == 0) tmem_alloc(&tbase_s, tcols);
-  if (tid == 0) mbar_init(&mbar, 1);
+  if (tid == 0) {
+    mbar_init(&mbar, 1);
+    mbar_init(&mbar2[0], 1);
+    mbar_init(&mbar2[1], 1);
+  }
   // stage G slice (k = 2*p0 .. 2*p0 + 2PC) and zero the padding rows of sAP
   const int p0 = chunk * PC;
   for (int idx = tid; idx < g.NPM * (2 * PC / 8); idx += kTcThreads) {
@@ -395,7 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = tbase_s;
-  const uint32_t tQ = tbase, tP = tbase + 32;
+  const uint32_t tQ = tbase, tP = tbase + 64;  // two Z slots of 32 columns, then the c accumulators
   uint32_t phase = 0;
   bool ok = true;
   const uint16_t* vb = v + (size_t)b * N * N * C;
@@ -403,54 +414,76 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   const int qchunks = N / QC;
   constexpr uint32_t idQ = idesc_f16(128, 32, true, true, false);
   constexpr uint32_t idQh = idesc_f16(128, 32, false, true, false);
-  for (int mt = 0; mt < mtiles && ok; ++mt) {
-    for (int qc = 0; qc < qchunks && ok; ++qc) {
-      const int q0 = qc * QC;
-      // E2 chunk (rows (k2,t), k = q - q0); the first pass loads it, later passes only if N > QC
-      if (mt == 0 || qchunks > 1) {
-        for (int idx = tid; idx < 32 * (QC / 8); idx += kTcThreads) {
-          const int row = idx / (QC / 8), kc = idx % (QC / 8);
-          const uint4 val = *reinterpret_cast<const uint4*>(E2 + (size_t)row * N + q0 + kc * 8);
-          *reinterpret_cast<uint4*>(sE2 + kmajor_off(row, kc * 8, 128, SBO_E)) = val;
-        }
+  // Steps s = (m-tile, q-chunk) run through a two-deep pipeline: while the MMA of step s
+  // runs, the operands of step s+1 are copied into the other buffer; the Z accumulator
+  // alternates between two TMEM slots by m-tile so that the read-back of one m-tile overlaps
+  // the MMAs of the next.
+  const int nsteps = mtiles * qchunks;
+  uint32_t phs[2] = {0, 0};
+  bool pending[2] = {false, false};
+  auto stage = [&](int st_, int buf) {
+    const int mt = st_ / qchunks, qc = st_ % qchunks, q0 = qc * QC;
+    if (qchunks > 1 || st_ == 0) {
+      uint8_t* e2 = sE2 + (qchunks > 1 ? buf * 32 * QC * 2 : 0);
+      for (int idx = tid; idx < 32 * (QC / 8); idx += kTcThreads) {
+        const int row = idx / (QC / 8), kc = idx % (QC / 8);
+        cp_async16(e2 + kmajor_off(row, kc * 8, 128, SBO_E), E2 + (size_t)row * N + q0 + kc * 8);
       }
-      // A tile: m = local (p, c) index 128*mt .. +128, k = q: 16-byte runs of 8 channels
-      for (int idx = tid; idx < QC * 16; idx += kTcThreads) {
-        const int ql = idx >> 4, mc = idx & 15;  // mc: 8-channel group within the 128 rows
-        const int m = mt * 128 + mc * 8;
-        const int pl = m / C, c0 = m % C;
-        const uint16_t* src = vb + ((size_t)(q0 + ql) * N + (p0 + pl)) * C + c0;
-        cp_async16(sA + mnmajor_off(mc * 8, ql, LBO_A, 128), src);
-      }
-      cp_async_commit();
-      cp_async_wait_all();
-      fence_smem_to_async();
-      fence_before_sync();
-      __syncthreads();
-      fence_after_sync();
-      if (tid == 0) {
-        for (int ks = 0; ks < QC / 16; ++ks) {
-          const uint64_t ad = desc(smem_addr(sA) + ks * 2 * LBO_A, LBO_A, 128);
-          const uint64_t bd = desc(smem_addr(sE2) + ks * 2 * 128, 128, SBO_E);
-          mma(tQ, ad, bd, bf16 ? idQ : idQh, qc > 0 || ks > 0);
-        }
-        commit(&mbar);
-      }
-      ok = mbar_wait(&mbar, phase);
-      phase ^= 1;
-      fence_after_sync();
     }
-    if (!ok) break;
-    // read Z for this m-tile: lane = (p, c), columns (k2, t) -> sAP[(k2, c)][(p, t)]
-    {
+    // A tile: m = local (p, c) index 128*mt .. +128, k = q: 16-byte runs of 8 channels
+    uint8_t* sa = sA + buf * 128 * QC * 2;
+    for (int idx = tid; idx < QC * 16; idx += kTcThreads) {
+      const int ql = idx >> 4, mc = idx & 15;  // mc: 8-channel group within the 128 rows
+      const int m = mt * 128 + mc * 8;
+      const int pl = m / C, c0 = m % C;
+      cp_async16(sa + mnmajor_off(mc * 8, ql, LBO_A, 128), vb + ((size_t)(q0 + ql) * N + (p0 + pl)) * C + c0);
+    }
+    cp_async_commit();
+  };
+  stage(0, 0);
+  for (int st_ = 0; st_ < nsteps && ok; ++st_) {
+    const int buf = st_ & 1, mt = st_ / qchunks, qc = st_ % qchunks;
+    cp_async_wait_all();
+    fence_smem_to_async();
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tq = tQ + (mt & 1) * 32;
+    if (tid == 0) {
+      const uint32_t sa = smem_addr(sA + buf * 128 * QC * 2);
+      const uint32_t e2 = smem_addr(sE2 + (qchunks > 1 ? buf * 32 * QC * 2 : 0));
+      for (int ks = 0; ks < QC / 16; ++ks)
+        mma(tq, desc(sa + ks * 2 * LBO_A, LBO_A, 128), desc(e2 + ks * 2 * 128, 128, SBO_E), bf16 ? idQ : idQh,
+            qc > 0 || ks > 0);
+      commit(&mbar2[buf]);
+    }
+    pending[buf] = true;
+    if (st_ + 1 < nsteps) {
+      // the other buffer was read by the previous step's MMA: wait for it before refilling
+      if (pending[buf ^ 1]) {
+        ok = mbar_wait(&mbar2[buf ^ 1], phs[buf ^ 1]);
+        phs[buf ^ 1] ^= 1;
+        pending[buf ^ 1] = false;
+        fence_after_sync();
+        if (!ok) break;
+      }
+      stage(st_ + 1, buf ^ 1);
+    }
+    if (qc == qchunks - 1) {
+      ok = mbar_wait(&mbar2[buf], phs[buf]);
+      phs[buf] ^= 1;
+      pending[buf] = false;
+      fence_after_sync();
+      if (!ok) break;
+      // read Z for this m-tile: lane = (p, c), columns (k2, t) -> sAP[(k2, c)][(p, t)]
       const int m = mt * 128 + warp * 32 + lane;
       const int pl = m / C, c = m % C;
       float z[32];
       float tmp[16];
-      tmem_ld16(tQ + ((uint32_t)(warp * 32) << 16), tmp);
+      tmem_ld16(tq + ((uint32_t)(warp * 32) << 16), tmp);
 #pragma unroll
       for (int i = 0; i < 16; ++i) z[i] = tmp[i];
-      tmem_ld16(tQ + ((uint32_t)(warp * 32) << 16) + 16, tmp);
+      tmem_ld16(tq + ((uint32_t)(warp * 32) << 16) + 16, tmp);
 #pragma unroll
       for (int i = 0; i < 16; ++i) z[16 + i] = tmp[i];
       for (int k2 = 0; k2 < Ky; ++k2) {
@@ -458,10 +491,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         *reinterpret_cast<uint32_t*>(sAP + kmajor_off(row, 2 * pl, 128, SBO_P)) = pack2(z[2 * k2], z[2 * k2 + 1], bf16);
       }
     }
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
   }
+  cp_async_wait_all();
   if (ok) {
     fence_smem_to_async();
     fence_before_sync();
@@ -510,46 +541,54 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 }
 
 // Per-mode complex channel mixing across instances: rows = instances (128 per CTA).
-// Output c'[b][k2][c][(j, t)] (16-bit), the layout of the synthesis stage-1 A operand.
+// Output c'[b][(j, re/im)][(k2, c)] (16-bit): the MN-major layout of the synthesis stage-1
+// A operand, so that each instance's C outputs of one (mode, re/im) are one 2C-byte run.
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    tc_mix_kernel(TcGeom g, int B, bool bf16, const float* __restrict__ part, const uint16_t* __restrict__ Rr,
-                  uint16_t* __restrict__ chat, int* __restrict__ err) {
+__global__ void __launch_bounds__(kTcThreads)
+    tc_mix_kernel(TcGeom g, int B, bool bf16, const int* __restrict__ active, const float* __restrict__ part,
+                  const uint16_t* __restrict__ Rr, uint16_t* __restrict__ chat, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint64_t mbar;
   __shared__ uint32_t tbase_s;
+  __shared__ int any_active;
   constexpr int C2 = 2 * C;
   const int mode = blockIdx.x, b0 = blockIdx.y * 128;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) any_active = 0;
+  __syncthreads();
+  if (b0 + tid < B && !tc_inactive(active, b0 + tid)) any_active = 1;
+  __syncthreads();
+  if (!any_active) return;  // every instance of this tile has stopped
   uint8_t* sA = smem;              // 128 x C2, K-major, SBO = C2*16
   uint8_t* sB = sA + 128 * C2 * 2; // C2 x C2,  K-major
   constexpr uint32_t SBO = C2 * 16;
   if (warp == 0) tmem_alloc(&tbase_s, C2 < 32 ? 32 : C2);
   if (tid == 0) mbar_init(&mbar, 1);
   {
-    // thread per instance row: sum the chunk partials in order, cast, store 16-byte runs
-    const int row = tid;
-    const int b = b0 + row;
-    for (int k0 = 0; k0 < C2; k0 += 8) {
-      float acc[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) acc[i] = 0.f;
-      if (b < B) {
+    // warp w loads rows 32w..32w+31; a row (one instance's C2 values) is one coalesced read
+    // per chunk, the chunks are summed in order
+    for (int r = 0; r < 32; ++r) {
+      const int row = warp * 32 + r;
+      const int b = b0 + row;
+      float2 acc = make_float2(0.f, 0.f);
+      if (b < B && 2 * lane < C2) {
         for (int ch = 0; ch < g.nchunks; ++ch) {
-          const float* src = part + (((size_t)b * g.nchunks + ch) * g.nmodes + mode) * C2 + k0;
-#pragma unroll
-          for (int i = 0; i < 8; ++i) acc[i] += src[i];
+          const float2 v = *reinterpret_cast<const float2*>(part + (((size_t)b * g.nchunks + ch) * g.nmodes + mode) * C2 +
+                                                            2 * lane);
+          acc.x += v.x;
+          acc.y += v.y;
         }
       }
-      uint4 w = make_uint4(pack2(acc[0], acc[1], bf16), pack2(acc[2], acc[3], bf16), pack2(acc[4], acc[5], bf16),
-                           pack2(acc[6], acc[7], bf16));
-      *reinterpret_cast<uint4*>(sA + kmajor_off(row, k0, 128, SBO)) = w;
+      if (2 * lane < C2)
+        *reinterpret_cast<uint32_t*>(sA + kmajor_off(row, 2 * lane, 128, SBO)) = pack2(acc.x, acc.y, bf16);
     }
     const uint16_t* Rm = Rr + (size_t)mode * C2 * C2;
     for (int idx = tid; idx < C2 * C2 / 8; idx += kTcThreads) {
       const int r = idx / (C2 / 8), kc = idx % (C2 / 8);
-      *reinterpret_cast<uint4*>(sB + kmajor_off(r, kc * 8, 128, SBO)) = *reinterpret_cast<const uint4*>(Rm + r * C2 + kc * 8);
+      cp_async16(sB + kmajor_off(r, kc * 8, 128, SBO), Rm + r * C2 + kc * 8);
     }
+    cp_async_commit();
+    cp_async_wait_all();
   }
   fence_smem_to_async();
   fence_before_sync();
@@ -567,15 +606,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   if (ok) {
     const int b = b0 + warp * 32 + lane;
     const int j = mode / g.Ky, k2 = mode % g.Ky;
-    for (int c0 = 0; c0 < C2; c0 += 16) {
-      float val[16];
-      tmem_ld16(tbase + c0 + ((uint32_t)(warp * 32) << 16), val);
-      if (b < B) {
+    float val[C2];
 #pragma unroll
-        for (int i = 0; i < 16; i += 2) {
-          const int o = (c0 + i) >> 1;
-          *reinterpret_cast<uint32_t*>(chat + (((size_t)b * g.Ky + k2) * C + o) * g.Kx4 + 2 * j) =
-              pack2(val[i], val[i + 1], bf16);
+    for (int c0 = 0; c0 < C2; c0 += 16) {
+      float t16[16];
+      tmem_ld16(tbase + c0 + ((uint32_t)(warp * 32) << 16), t16);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) val[c0 + i] = t16[i];
+    }
+    if (b < B) {
+      // columns are (o, re/im) interleaved; write the C real parts, then the C imaginary parts
+#pragma unroll
+      for (int t = 0; t < 2; ++t) {
+        uint4* dst = reinterpret_cast<uint4*>(chat + (((size_t)b * g.Kx4 + 2 * j + t) * g.Ky + k2) * C);
+#pragma unroll
+        for (int o0 = 0; o0 < C; o0 += 8) {
+          dst[o0 / 8] = make_uint4(pack2(val[2 * o0 + t], val[2 * o0 + 2 + t], bf16),
+                                   pack2(val[2 * o0 + 4 + t], val[2 * o0 + 6 + t], bf16),
+                                   pack2(val[2 * o0 + 8 + t], val[2 * o0 + 10 + t], bf16),
+                                   pack2(val[2 * o0 + 12 + t], val[2 * o0 + 14 + t], bf16));
         }
       }
     }
@@ -592,7 +641,7 @@ struct SynArgs {
   int B;
   bool bf16;
   const int* active;
-  const uint16_t* chat;   // [B][Ky][C][Kx4]
+  const uint16_t* chat;   // [B][Kx4][Ky][C]  (MN-major stage-1 operand)
   const uint16_t* vin;    // [B][N][N][C]
   const uint16_t* W;      // [C][C]
   const float* bias;      // [C]
@@ -614,46 +663,50 @@ struct SynArgs {
 
 // Synthesis + pointwise + bias + activation (+ decoder) for one grid-column chunk of one instance.
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 1) tc_synthesis_kernel(SynArgs a) {
+__global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
   __shared__ uint64_t mbar[4];
   __shared__ uint32_t tbase_s;
   const TcGeom& g = a.g;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(a.active, b)) return;
-  const int N = g.N, PC = g.PC, Ky = g.Ky;
+  const int N = g.N, PC = g.SPC, Ky = g.Ky;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool bf16 = a.bf16;
   const int p0 = chunk * PC;
   // shared layout
-  const uint32_t SBO_A1 = g.KXP * 16, SBO_H = g.KXP * 16, SBO_B = g.KB * 16, SBO_S = g.KSYN * 16, SBO_C = C * 16;
+  const uint32_t LBO_A1 = (g.MP / 8) * 128;  // MN-major: K-direction core-matrix stride
+  const uint32_t SBO_H = g.KXP * 16, SBO_B = g.KB * 16, SBO_S = g.KSYN * 16, SBO_C = C * 16;
+  // region R0 holds the mixed coefficients for synthesis stage 1, then (aliased, once stage 1
+  // has completed) the two pointwise input tiles and the decoder input tile
+  const size_t r0a = (size_t)g.MP * g.KXP * 2, r0b = (size_t)3 * 128 * C * 2;
+  const size_t r0 = r0a > r0b ? r0a : r0b;
   uint8_t* sA1 = smem;                                  // MP x KXP
-  uint8_t* sH = sA1 + (size_t)g.MP * g.KXP * 2;         // 2PC x KXP
+  uint8_t* sX0 = smem;                                  // 2 x (128 x C) pointwise tiles (after stage 1)
+  uint8_t* sD = smem + 2 * 128 * C * 2;                 // 128 x C decoder input (after stage 1)
+  uint8_t* sH = smem + r0;                              // 2PC x KXP
   uint8_t* sB = sH + (size_t)2 * PC * g.KXP * 2;        // C x KB
   uint8_t* sS = sB + (size_t)C * g.KB * 2;              // 128 x KSYN
   uint8_t* sW = sS + (size_t)128 * g.KSYN * 2;          // C x C
   uint8_t* sP = sW + C * C * 2;                         // C x C (decoder)
-  uint8_t* sX0 = sP + C * C * 2;                        // 2 x (128 x C) pointwise tiles
-  uint8_t* sD = sX0 + 2 * 128 * C * 2;                  // 128 x C decoder input
-  const uint32_t TCOLS = 512;
+  const uint32_t TCOLS = 256;
   if (warp == 0) tmem_alloc(&tbase_s, TCOLS);
   if (tid < 4) mbar_init(&mbar[tid], 1);
   // ---- stage operands that do not change across tiles
-  const uint16_t* cb = a.chat + (size_t)b * Ky * C * g.Kx4;
-  for (int idx = tid; idx < g.MP * (g.KXP / 8); idx += kTcThreads) {
-    const int row = idx / (g.KXP / 8), kc = idx % (g.KXP / 8);
-    uint16_t tmp[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) {
-      const int k = kc * 8 + i;
-      tmp[i] = (row < Ky * C && k < g.Kx4) ? cb[(size_t)row * g.Kx4 + k] : (uint16_t)0;
-    }
-    *reinterpret_cast<uint4*>(sA1 + kmajor_off(row, kc * 8, 128, SBO_A1)) = *reinterpret_cast<uint4*>(tmp);
+  // mixed coefficients, MN-major: element (m = (k2, c), k = (j, re/im)) is at
+  // chat[b][k][m]; 8 consecutive m at one k form one 16-byte run
+  const uint16_t* cb = a.chat + (size_t)b * g.Kx4 * Ky * C;
+  for (int idx = tid; idx < (g.MP / 8) * g.KXP; idx += kTcThreads) {
+    const int k = idx / (g.MP / 8), mc = idx % (g.MP / 8);
+    uint8_t* dst = sA1 + mnmajor_off(mc * 8, k, LBO_A1, 128);
+    if (mc * 8 < Ky * C && k < g.Kx4)
+      cp_async16(dst, cb + (size_t)k * Ky * C + mc * 8);
+    else
+      *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
   }
   for (int idx = tid; idx < 2 * PC * (g.KXP / 8); idx += kTcThreads) {
     const int row = idx / (g.KXP / 8), kc = idx % (g.KXP / 8);
-    *reinterpret_cast<uint4*>(sH + kmajor_off(row, kc * 8, 128, SBO_H)) =
-        *reinterpret_cast<const uint4*>(a.H + (size_t)(2 * p0 + row) * g.KXP + kc * 8);
+    cp_async16(sH + kmajor_off(row, kc * 8, 128, SBO_H), a.H + (size_t)(2 * p0 + row) * g.KXP + kc * 8);
   }
   for (int idx = tid; idx < C * (C / 8); idx += kTcThreads) {
     const int row = idx / (C / 8), kc = idx % (C / 8);
@@ -666,10 +719,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_synthesis_kernel(SynArgs a) 
   if (N < 128) {
     for (int idx = tid; idx < 128 * (g.KSYN / 8); idx += kTcThreads) {
       const int row = idx / (g.KSYN / 8), kc = idx % (g.KSYN / 8);
-      *reinterpret_cast<uint4*>(sS + kmajor_off(row, kc * 8, 128, SBO_S)) =
-          *reinterpret_cast<const uint4*>(a.Asyn + (size_t)row * g.KSYN + kc * 8);
+      cp_async16(sS + kmajor_off(row, kc * 8, 128, SBO_S), a.Asyn + (size_t)row * g.KSYN + kc * 8);
     }
   }
+  cp_async_commit();
   // zero the K tail of the staged U columns (read by padded synthesis K steps)
   const int kvalid = PC * 2 * Ky;
   for (int idx = tid; idx < C * ((g.KB - (kvalid & ~7)) / 8); idx += kTcThreads) {
@@ -677,23 +730,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_synthesis_kernel(SynArgs a) 
     const int row = idx / nk, kc = (kvalid & ~7) / 8 + idx % nk;
     *reinterpret_cast<uint4*>(sB + kmajor_off(row, kc * 8, 128, SBO_B)) = make_uint4(0, 0, 0, 0);
   }
+  cp_async_wait_all();
   fence_smem_to_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = tbase_s;
-  const uint32_t tU = tbase;              // (MP/128) x 2PC columns
-  const uint32_t tD = tbase + 384;        // 2 x C tile accumulators
-  const uint32_t tE = tbase + 384 + 2 * C;  // C decoder accumulator
+  const uint32_t tU = tbase;              // (MP/128) x 2PC columns (stage 1)
+  const uint32_t tD = tbase;              // 2 x C tile accumulators (reuse U's columns after stage 1)
+  const uint32_t tE = tbase + 2 * C;      // C decoder accumulator
   uint32_t ph[4] = {0, 0, 0, 0};
   bool ok = true;
   const int utiles = g.MP / 128;
   // ---- synthesis stage 1: U = c' H^T for the chunk
   if (tid == 0) {
-    const uint32_t id = idesc_f16(128, 2 * PC, bf16);
+    const uint32_t id = idesc_f16(128, 2 * PC, bf16, true, false);
     for (int ut = 0; ut < utiles; ++ut)
       for (int ks = 0; ks < g.KXP / 16; ++ks)
-        mma(tU + ut * 2 * PC, desc(smem_addr(sA1) + ut * 16 * SBO_A1 + ks * 256, 128, SBO_A1),
+        mma(tU + ut * 2 * PC, desc(smem_addr(sA1) + ut * 16 * 128 + ks * 2 * LBO_A1, LBO_A1, 128),
             desc(smem_addr(sH) + ks * 256, 128, SBO_H), id, ks > 0);
     commit(&mbar[0]);
   }
@@ -855,13 +909,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) tc_synthesis_kernel(SynArgs a) 
 
 // ------------------------------------ host ---------------------------------------------
 static size_t analysis_smem(const TcGeom& g) {
-  return (size_t)32 * g.QC * 2 + (size_t)128 * g.QC * 2 + (size_t)g.MP * 2 * g.PC * 2 + (size_t)g.NPM * 2 * g.PC * 2;
+  return (size_t)2 * 32 * g.QC * 2 + (size_t)2 * 128 * g.QC * 2 + (size_t)g.MP * 2 * g.PC * 2 +
+         (size_t)g.NPM * 2 * g.PC * 2;
 }
 static size_t mix_smem(int C) { return (size_t)128 * 2 * C * 2 + (size_t)4 * C * C * 2; }
 static size_t synthesis_smem(const TcGeom& g) {
   const int C = g.C;
-  return (size_t)g.MP * g.KXP * 2 + (size_t)2 * g.PC * g.KXP * 2 + (size_t)C * g.KB * 2 + (size_t)128 * g.KSYN * 2 +
-         (size_t)2 * C * C * 2 + (size_t)2 * 128 * C * 2 + (size_t)128 * C * 2;
+  const size_t r0 = std::max((size_t)g.MP * g.KXP * 2, (size_t)3 * 128 * C * 2);
+  return r0 + (size_t)2 * g.SPC * g.KXP * 2 + (size_t)C * g.KB * 2 + (size_t)128 * g.KSYN * 2 + (size_t)2 * C * C * 2;
 }
 
 template <int C>
@@ -937,8 +992,8 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     FCGNO_LAUNCHED();
     {
       TraceScope ts("tc_mix", st);
-      tc_mix_kernel<C><<<dim3(g.nmodes, ceil_div(B, 128)), kTcThreads, sm, st>>>(g, B, bf16, T.part, P.Rr[l],
-                                                                                T.chat, d_err);
+      tc_mix_kernel<C><<<dim3(g.nmodes, ceil_div(B, 128)), kTcThreads, sm, st>>>(g, B, bf16, active, T.part,
+                                                                                P.Rr[l], T.chat, d_err);
     }
     FCGNO_LAUNCHED();
     SynArgs s{};
@@ -965,7 +1020,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     s.err = d_err;
     {
       TraceScope ts("tc_synthesis", st);
-      tc_synthesis_kernel<C><<<dim3(g.nchunks, B), kTcThreads, ss, st>>>(s);
+      tc_synthesis_kernel<C><<<dim3(g.snchunks, B), kTcThreads, ss, st>>>(s);
     }
     FCGNO_LAUNCHED();
     std::swap(cur, nxt);
