@@ -145,6 +145,57 @@ def roofline_synthesis(active_per_iter, N, C, M, layers):
     return float(sum(active_per_iter)) * per_inst, int(len(active_per_iter)) * layers
 
 
+SERVE_SIZES = {64: 0.40, 128: 0.25, 256: 0.20, 512: 0.10, 1024: 0.05}
+SERVE_SIGMAS = (0.5, 1.0, 2.0)
+
+
+def run_serving(args, model, desc_np, dev, pool_per_key=4, budget_gb=80.0):
+    """Serving stream of the configured mix: exponential inter-arrival times (mean 1/rate,
+    seed 5), grid sizes drawn with the configured probabilities, sigma uniform in
+    {0.5, 1, 2}, ell = 0.1, f iid N(0,1), u_0 iid N(0,1); problems come from a seeded pool of
+    `pool_per_key` instances per (size, sigma)."""
+    import torch
+    from paper_2402_05598_gb300 import fcgno as F
+    from paper_2402_05598_gb300 import inputs as I
+    from paper_2402_05598_gb300 import serve as S
+    rng = np.random.default_rng(5)
+    pool = {}
+    for N in SERVE_SIZES:
+        for si, sg in enumerate(SERVE_SIGMAS):
+            for j in range(pool_per_key):
+                seed = 50000 + 1000 * si + 100 * int(np.log2(N)) + j
+                kk, ff = I.make_problem(N, seed, sigma=sg, ell=0.1)
+                x0 = np.random.default_rng(seed + 777).standard_normal((N, N))
+                pool[(N, si, j)] = tuple(torch.from_numpy(a).to(dev) for a in (kk, ff, x0))
+    sizes = list(SERVE_SIZES)
+    probs = np.array([SERVE_SIZES[N] for N in sizes])
+    gaps = rng.exponential(1.0 / args.serve_rate, args.serve_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    Ns = rng.choice(sizes, size=args.serve_requests, p=probs / probs.sum())
+    sis = rng.integers(0, len(SERVE_SIGMAS), args.serve_requests)
+    js = rng.integers(0, pool_per_key, args.serve_requests)
+    reqs = [S.Request(i, float(arrivals[i]), int(Ns[i]), *pool[(int(Ns[i]), int(sis[i]), int(js[i]))])
+            for i in range(args.serve_requests)]
+    caps = S.plan_capacities(SERVE_SIZES, int(budget_gb * 2**30), args.m, F.make_desc(WIDTH, LAYERS, MODES, WIDTH),
+                             args.prec, max_slots=64)
+    srv = S.Server(model, caps, prec=args.prec, m_max=args.m, tol=TOL, max_iter=args.max_iter, iters_per_step=8)
+    # warm every bucket once (first steps run eagerly and allocate), outside the measurement
+    warm = [S.Request(-1, 0.0, N, *pool[(N, 0, 0)]) for N in sizes]
+    srv.run(warm, S.ServeStats())
+    stats = S.ServeStats(offered_rate=args.serve_rate)
+    stats.bucket_bytes = sum(cap * S.slot_bytes(N, args.m, F.make_desc(WIDTH, LAYERS, MODES, WIDTH), args.prec)
+                             for N, cap in caps.items())
+    srv.run(reqs, stats)
+    srv.close()
+    out = stats.summary()
+    out.update({"capacities": {str(N): c for N, c in caps.items()}, "budget_gb": budget_gb,
+                "sizes": {str(N): p for N, p in SERVE_SIZES.items()}, "tol": TOL, "m": args.m,
+                "max_iter": args.max_iter,
+                "iterations_mean_by_size": {str(N): float(np.mean([r.iters for r in reqs if r.N == N] or [0]))
+                                            for N in sizes}})
+    return out
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -197,6 +248,9 @@ def main():
     ap.add_argument("--ref-iters", type=int, default=60)
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--serve-requests", type=int, default=2000,
+                    help="requests in the serving stream (0 = skip the serving measurement)")
+    ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate of the serving stream (1/s)")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling mode: no training, two solves of --profile-iters fixed iterations")
     ap.add_argument("--profile-iters", type=int, default=8)
@@ -372,6 +426,10 @@ def main():
         tcg = time.perf_counter() - t0
         line["cg"] = {"value": sub / tcg, "unit": UNIT, "instances": sub,
                       "iterations_mean": float(np.mean([i["iters"] for i in infcg]))}
+
+    # ---- serving stream: continuous batching over size buckets (latency incl. queueing)
+    if rank == 0 and args.serve_requests > 0:
+        line["serve"] = run_serving(args, model, desc_np, dev)
 
     # ---- end to end through the host-buffer entry point
     kh = torch.from_numpy(k_np).pin_memory()

@@ -116,6 +116,13 @@ fcgno_status fcgno_solve(fcgno_op_t A, fcgno_model_t Bpc, const double* b, doubl
                          const fcgno_solve_opts* opts, fcgno_prec prec, fcgno_solve_info* info,
                          void* stream);
 
+/* Algorithm 1 preconditioned by Jacobi(steps) (Eq. (15); the Jacobi column of Table 1):
+ * w_i = x_steps with x_0 = 0, x_{j+1} = x_j + D(A)^-1 (r_i - A x_j), FP64. The classical
+ * baseline the paper compares the neural preconditioner against. Same arguments and
+ * results as fcgno_solve; EINVAL for steps outside 1..64. */
+fcgno_status fcgno_solve_jacobi(fcgno_op_t A, int steps, const double* b, double* x, const fcgno_solve_opts* opts,
+                                fcgno_solve_info* info, void* stream);
+
 /* End-to-end variant of fcgno_solve on HOST buffers: k_host, b_host, x_host are
  * [batch][N][N] host arrays (pinned memory gives the fastest copies). Copies k, b, x in,
  * assembles, solves, copies x out; info is a host array. Synchronous. */
@@ -157,6 +164,31 @@ fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x
  * Uses the FP32 master blob given to fcgno_model_create. */
 fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
                               int batch, fcgno_prec prec, float* loss, float* grad, void* stream);
+
+/* Serving buckets (continuous batching of independent solves of one grid size). A bucket
+ * keeps `capacity` solves resident (operator, iterate, right-hand side and Krylov state of
+ * Algorithm 1) and advances all running slots together, `iters_per_step` iterations per
+ * fcgno_bucket_step (replayed as one CUDA graph after the first step). Slots are admitted
+ * and retired independently; each slot's truncation window follows its own iteration
+ * count, so a slot's result does not depend on the other slots. Bpc NULL = identity.
+ *  - create: all slots start stopped. Errors: EINVAL, ENOMEM.
+ *  - admit: copy k, f, x0 (DEVICE [N][N]) into `slot`, assemble its operator, form r_0; the
+ *    slot runs from its next step on. The slot must be free (stopped).
+ *  - step: asynchronous on `stream`.
+ *  - poll: synchronises; fills HOST arrays of `capacity` entries: status (-1 running,
+ *    FCGNO_OK converged, FCGNO_EBREAKDOWN, FCGNO_ENOCONV once iters >= max_iter), iterations,
+ *    relative residual.
+ *  - take: copy the slot's iterate to x_out (DEVICE [N][N], may be NULL) and stop the slot,
+ *    freeing it for the next admit. */
+typedef struct fcgno_bucket* fcgno_bucket_t;
+fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t Bpc, fcgno_prec prec, int m_max, double tol,
+                                 int max_iter, int iters_per_step, void* stream, fcgno_bucket_t* out);
+fcgno_status fcgno_bucket_admit(fcgno_bucket_t bucket, int slot, const double* k, const double* f, const double* x0,
+                                void* stream);
+fcgno_status fcgno_bucket_step(fcgno_bucket_t bucket, void* stream);
+fcgno_status fcgno_bucket_poll(fcgno_bucket_t bucket, int32_t* status, int32_t* iters, double* relres, void* stream);
+fcgno_status fcgno_bucket_take(fcgno_bucket_t bucket, int slot, double* x_out, void* stream);
+fcgno_status fcgno_bucket_destroy(fcgno_bucket_t bucket);
 
 /* Device bytes fcgno_solve needs for one op of this shape (operator, Krylov state and the
  * preconditioner's activations), for admission against an HBM budget. */

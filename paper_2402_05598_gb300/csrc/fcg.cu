@@ -42,8 +42,9 @@ struct IterArgs {
   int fixed;      // 1: ignore tol
 };
 
-// Iteration index and truncation window, derived on the device from the iteration counter
-// so that a captured CUDA graph of several iterations replays unchanged.
+// Iteration index and truncation window of one instance, derived on the device from that
+// instance's own iteration count: captured CUDA graphs replay unchanged, and instances that
+// started at different times (serving slots) can share a batch.
 struct Window {
   int i;          // iteration index
   int m_i;        // window length min(i, max(1, i mod (m_max+1)))
@@ -74,9 +75,9 @@ struct State {
   int* iter;      // device iteration counter (advanced once per iteration)
 };
 
-__device__ __forceinline__ Window window_of(const IterArgs& a, const State& s) {
+__device__ __forceinline__ Window window_of(const IterArgs& a, const State& s, int b) {
   Window w;
-  w.i = *(volatile const int*)s.iter;
+  w.i = s.iters[b];
   w.m_i = min(w.i, max(1, w.i % a.nslots));
   w.slot_new = w.i % a.nslots;
 #pragma unroll
@@ -84,9 +85,7 @@ __device__ __forceinline__ Window window_of(const IterArgs& a, const State& s) {
   return w;
 }
 
-__global__ void advance_kernel(State s) {
-  if (threadIdx.x == 0 && blockIdx.x == 0) *s.iter += 1;
-}
+
 
 __device__ __forceinline__ double stencil_at(const State& s, size_t gi, int p, int q, int N, double c,
                                              double e, double w, double nn, double so) {
@@ -181,7 +180,7 @@ __global__ void init_finalize_kernel(IterArgs a, State s) {
 __global__ void __launch_bounds__(kThreads) dots_w_kernel(IterArgs a, State s) {
   __shared__ double scratch[32 * kMaxWindow];
   const int b = blockIdx.y;
-  const Window w = window_of(a, s);
+  const Window w = window_of(a, s, b);
   if (s.status[b] != kRunning || w.m_i == 0) return;
   const size_t off = (size_t)b * a.n;
   double acc[kMaxWindow];
@@ -209,7 +208,7 @@ __global__ void __launch_bounds__(kThreads) dots_w_kernel(IterArgs a, State s) {
 __global__ void beta_kernel(IterArgs a, State s) {
   const int b = blockIdx.x;
   const int j = threadIdx.x;
-  const Window w = window_of(a, s);
+  const Window w = window_of(a, s, b);
   if (s.status[b] != kRunning || j >= w.m_i) return;
   double sum = 0.0;
   for (int t = 0; t < a.tiles; ++t) sum += s.part[((size_t)b * a.tiles + t) * kParts + j];
@@ -219,7 +218,7 @@ __global__ void beta_kernel(IterArgs a, State s) {
 __global__ void __launch_bounds__(kThreads) direction_kernel(IterArgs a, State s) {
   const int b = blockIdx.y;
   if (s.status[b] != kRunning) return;
-  const Window w = window_of(a, s);
+  const Window w = window_of(a, s, b);
   const size_t off = (size_t)b * a.n;
   double beta[kMaxWindow];
 #pragma unroll
@@ -241,7 +240,7 @@ __global__ void __launch_bounds__(kThreads) stencil_dots_kernel(IterArgs a, Stat
   __shared__ double scratch[32 * 2];
   const int b = blockIdx.y;
   if (s.status[b] != kRunning) return;
-  const Window w = window_of(a, s);
+  const Window w = window_of(a, s, b);
   const size_t off = (size_t)b * a.n;
   const double* pv = s.P + (size_t)w.slot_new * a.B * a.n + off;
   double* sv = s.S + (size_t)w.slot_new * a.B * a.n + off;
@@ -272,7 +271,7 @@ __global__ void __launch_bounds__(kThreads) stencil_dots_kernel(IterArgs a, Stat
 __global__ void alpha_kernel(IterArgs a, State s) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.B || s.status[b] != kRunning) return;
-  const Window w = window_of(a, s);
+  const Window w = window_of(a, s, b);
   double ps = 0.0, pr = 0.0;
   for (int t = 0; t < a.tiles; ++t) {
     const double* pp = s.part + ((size_t)b * a.tiles + t) * kParts;
@@ -292,7 +291,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(IterArgs a, State s) {
   __shared__ double scratch[32];
   const int b = blockIdx.y;
   if (s.status[b] != kRunning) return;
-  const Window w = window_of(a, s);
+  const Window w = window_of(a, s, b);
   const size_t off = (size_t)b * a.n;
   const double alpha = s.alpha[b];
   const double* pv = s.P + (size_t)w.slot_new * a.B * a.n + off;
@@ -314,7 +313,7 @@ __global__ void __launch_bounds__(kThreads) update_kernel(IterArgs a, State s) {
 __global__ void norm_kernel(IterArgs a, State s) {
   const int b = blockIdx.x * blockDim.x + threadIdx.x;
   if (b >= a.B || s.status[b] != kRunning) return;
-  const Window w = window_of(a, s);
+  const Window w = window_of(a, s, b);
   double rr = 0.0;
   for (int t = 0; t < a.tiles; ++t) rr += s.part[((size_t)b * a.tiles + t) * kParts + 2];
   s.rr[b] = rr;
@@ -335,7 +334,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   __shared__ double red_out[kMaxWindow];
   const int b = blockIdx.x;
   if (s.status[b] != kRunning) return;
-  const Window wd = window_of(a, s);
+  const Window wd = window_of(a, s, b);
   const size_t off = (size_t)b * a.n;
   const int T = blockDim.x;
   const int n = (int)a.n;
@@ -440,6 +439,35 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   }
 }
 
+// Jacobi(k) preconditioner, Eq. (15): x_0 = 0, x_{j+1} = x_j + D^-1 (r - A x_j); the first
+// sweep reduces to D^-1 r. x_in == nullptr marks the first sweep.
+__global__ void inv_diag_kernel(size_t total, const double* __restrict__ diag, double* __restrict__ inv) {
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i < total) inv[i] = 1.0 / diag[i];
+}
+
+__global__ void jacobi_sweep_kernel(int N, size_t n, const int* __restrict__ status, const double* __restrict__ aE,
+                                    const double* __restrict__ aN, const double* __restrict__ diag,
+                                    const double* __restrict__ inv, const double* __restrict__ r,
+                                    const double* __restrict__ xin, double* __restrict__ xout) {
+  const int b = blockIdx.y;
+  if (status[b] != kRunning) return;
+  const size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (e >= n) return;
+  const size_t gi = (size_t)b * n + e;
+  if (!xin) {
+    xout[gi] = r[gi] * inv[gi];
+    return;
+  }
+  const int q = (int)(e / N), p = (int)(e - (size_t)q * N);
+  double Ax = diag[gi] * xin[gi];
+  if (p < N - 1) Ax = fma(-aE[gi], xin[gi + 1], Ax);
+  if (p > 0) Ax = fma(-aE[gi - 1], xin[gi - 1], Ax);
+  if (q < N - 1) Ax = fma(-aN[gi], xin[gi + N], Ax);
+  if (q > 0) Ax = fma(-aN[gi - N], xin[gi - N], Ax);
+  xout[gi] = fma(r[gi] - Ax, inv[gi], xin[gi]);
+}
+
 // Krylov sampling helper: r_out[i] = r, e_out[i] = u_star - u for every instance.
 __global__ void harvest_copy_kernel(size_t total, const double* __restrict__ r, const double* __restrict__ u,
                                     const double* __restrict__ ustar, double* __restrict__ r_out,
@@ -459,7 +487,7 @@ static void drop_graph(SolverWorkspace& w) {
 
 static void free_ws(SolverWorkspace& w) {
   drop_graph(w);
-  double** dp[] = {&w.r, &w.w, &w.P, &w.S, &w.ps, &w.beta, &w.alpha, &w.r0, &w.rr, &w.rms, &w.part};
+  double** dp[] = {&w.r, &w.w, &w.wt, &w.inv_diag, &w.P, &w.S, &w.ps, &w.beta, &w.alpha, &w.r0, &w.rr, &w.rms, &w.part};
   for (auto p : dp) {
     if (*p) cudaFree(*p);
     *p = nullptr;
@@ -498,6 +526,8 @@ static fcgno_status ensure_ws(fcgno_op* op, int slots) {
   };
   alloc((void**)&w.r, vec);
   alloc((void**)&w.w, vec);
+  alloc((void**)&w.wt, vec);
+  alloc((void**)&w.inv_diag, vec);
   alloc((void**)&w.P, vec * slots);
   alloc((void**)&w.S, vec * slots);
   alloc((void**)&w.ps, sizeof(double) * slots * op->B);
@@ -596,14 +626,31 @@ static fcgno_status launch_vector_step(const IterArgs& a, const State& s, const 
     norm_kernel<<<ceil_div(a.B, 128), 128, 0, cs>>>(a, s);
     FCGNO_LAUNCHED();
   }
-  advance_kernel<<<1, 32, 0, cs>>>(s);
-  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+static fcgno_status launch_jacobi(fcgno_op* op, int steps, cudaStream_t cs) {
+  SolverWorkspace& w = op->ws;
+  // sweeps alternate between w and wt so that the last one lands in w
+  double* bufs[2] = {w.w, w.wt};
+  int cur = (steps % 2 == 1) ? 0 : 1;
+  const double* xin = nullptr;
+  for (int j = 0; j < steps; ++j) {
+    double* xout = bufs[cur];
+    jacobi_sweep_kernel<<<dim3(ceil_div(op->n, 256), op->B), 256, 0, cs>>>(op->N, op->n, w.status, op->aE, op->aN,
+                                                                          op->diag, w.inv_diag, w.r, xin, xout);
+    FCGNO_LAUNCHED();
+    xin = xout;
+    cur ^= 1;
+  }
   return FCGNO_OK;
 }
 
 static fcgno_status launch_iteration(fcgno_op* op, fcgno_model* model, fcgno_prec prec, const IterArgs& a,
-                                     const State& s, const LoopShape& L, cudaStream_t cs) {
-  if (model) {
+                                     const State& s, const LoopShape& L, cudaStream_t cs, int jacobi = 0) {
+  if (jacobi > 0) {
+    FCGNO_TRY(launch_jacobi(op, jacobi, cs));
+  } else if (model) {
     SolverWorkspace& w = op->ws;
     if (prec == FCGNO_BF16 || prec == FCGNO_FP16) {
       FCGNO_TRY(no_apply_tc(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP16, cs));
@@ -616,12 +663,13 @@ static fcgno_status launch_iteration(fcgno_op* op, fcgno_model* model, fcgno_pre
 
 // Captures G iterations into a CUDA graph (reused while the baked-in parameters match).
 static fcgno_status ensure_graph(fcgno_op* op, fcgno_model* model, fcgno_prec prec, const IterArgs& a,
-                                 const State& s, const LoopShape& L, const double* b, const double* x, int G) {
+                                 const State& s, const LoopShape& L, const double* b, const double* x, int G,
+                                 int jacobi) {
   SolverWorkspace& w = op->ws;
   IterGraph& g = w.graph;
   const uint64_t gen = model ? model->gen : 0;
   if (g.exec && g.trace_gen == trace_generation() && g.model == model && g.model_gen == gen &&
-      g.prec == (int)prec && g.nslots == a.nslots &&
+      g.prec == (int)prec && g.nslots == a.nslots && g.jacobi == jacobi &&
       g.fixed == a.fixed && g.G == G && g.tol == a.tol && g.b == b && g.x == x)
     return FCGNO_OK;
   drop_graph(w);
@@ -629,7 +677,7 @@ static fcgno_status ensure_graph(fcgno_op* op, fcgno_model* model, fcgno_prec pr
   FCGNO_CUDA_TRY(cudaStreamBeginCapture(w.cs, cudaStreamCaptureModeThreadLocal));
   trace_capture_begin(&g.traced);
   fcgno_status rc = FCGNO_OK;
-  for (int it = 0; it < G && rc == FCGNO_OK; ++it) rc = launch_iteration(op, model, prec, a, s, L, w.cs);
+  for (int it = 0; it < G && rc == FCGNO_OK; ++it) rc = launch_iteration(op, model, prec, a, s, L, w.cs, jacobi);
   trace_capture_end();
   // captured launches did not run: they are counted when the graph replays
   g.kernels = g_launches.load() - l0;
@@ -654,6 +702,7 @@ static fcgno_status ensure_graph(fcgno_op* op, fcgno_model* model, fcgno_prec pr
     return FCGNO_ECUDA;
   }
   g.trace_gen = trace_generation();
+  g.jacobi = jacobi;
   g.model = model;
   g.model_gen = gen;
   g.prec = (int)prec;
@@ -673,12 +722,12 @@ static bool graphs_enabled() {
 
 static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b, double* x,
                                const fcgno_solve_opts& o, fcgno_prec prec, fcgno_solve_info* info,
-                               cudaStream_t st, const HarvestHook* hook) {
+                               cudaStream_t st, const HarvestHook* hook, int jacobi = 0) {
   const int slots = o.m_max + 1;
   FCGNO_TRY(ensure_ws(op, slots));
   SolverWorkspace& w = op->ws;
   const cudaStream_t cs = w.cs;
-  const bool identity = (model == nullptr);
+  const bool identity = (model == nullptr && jacobi == 0);
   // with the identity preconditioner w_i = r_i: read r in place of w
   State s = make_state(op, b, x, identity ? w.r : w.w);
   IterArgs a{};
@@ -702,6 +751,10 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
   FCGNO_LAUNCHED();
   init_finalize_kernel<<<ceil_div(op->B, 128), 128, 0, cs>>>(a, s);
   FCGNO_LAUNCHED();
+  if (jacobi > 0) {
+    inv_diag_kernel<<<ceil_div(op->n * op->B, 256), 256, 0, cs>>>(op->n * op->B, op->diag, w.inv_diag);
+    FCGNO_LAUNCHED();
+  }
 
   int* h_ndone = nullptr;
   FCGNO_CUDA_TRY(cudaMallocHost(&h_ndone, sizeof(int)));
@@ -717,14 +770,14 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
     bool replayed = false;
     if (use_graph && i > 0 && o.max_iter - i >= G) {
       // the first iteration ran eagerly, so every lazily allocated buffer exists before capture
-      FCGNO_TRY(ensure_graph(op, model, prec, a, s, L, b, x, G));
+      FCGNO_TRY(ensure_graph(op, model, prec, a, s, L, b, x, G, jacobi));
       FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph.exec, cs));
       g_launches.fetch_add(w.graph.kernels, std::memory_order_relaxed);
       i += G;
       since_check = G;
       replayed = true;
     } else {
-      FCGNO_TRY(launch_iteration(op, model, prec, a, s, L, cs));
+      FCGNO_TRY(launch_iteration(op, model, prec, a, s, L, cs, jacobi));
       if (hook) {
         const size_t total = op->n * op->B;
         const size_t o2 = (size_t)i * total;
@@ -796,6 +849,16 @@ extern "C" fcgno_status fcgno_solve(fcgno_op_t A, fcgno_model_t Bpc, const doubl
     return FCGNO_EINVAL;
   }
   return solve_impl(A, Bpc, b, x, *opts, prec, info, (cudaStream_t)stream, nullptr);
+}
+
+extern "C" fcgno_status fcgno_solve_jacobi(fcgno_op_t A, int steps, const double* b, double* x,
+                                           const fcgno_solve_opts* opts, fcgno_solve_info* info, void* stream) {
+  if (!A || !b || !x || steps < 1 || steps > 64) {
+    set_last_error("fcgno_solve_jacobi: null operator, b or x, or steps outside 1..64");
+    return FCGNO_EINVAL;
+  }
+  FCGNO_TRY(check_opts(opts));
+  return solve_impl(A, nullptr, b, x, *opts, FCGNO_FP64, info, (cudaStream_t)stream, nullptr, steps);
 }
 
 extern "C" fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const double* b_host,
@@ -1023,5 +1086,218 @@ extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, doubl
       }
     }
   }
+  return FCGNO_OK;
+}
+
+// ------------------------------------ serving buckets ----------------------------------
+// A bucket keeps `capacity` same-size solves resident on the device (operator, iterate,
+// right-hand side, Krylov state) and advances every active slot together. Slots are
+// admitted and retired independently: every kernel derives the truncation window from the
+// slot's own iteration count and skips slots whose status is not "running", so a slot's
+// arithmetic does not depend on what the other slots are doing.
+struct fcgno_bucket {
+  fcgno_op* op = nullptr;
+  fcgno_model* model = nullptr;
+  fcgno_prec prec = FCGNO_BF16;
+  double* x = nullptr;  // [capacity][n]
+  double* b = nullptr;  // [capacity][n]
+  fcgno::IterArgs a{};
+  fcgno::State s{};
+  fcgno::LoopShape L{};
+  int G = 8;
+  int max_iter = 1000;
+  bool warmed = false;
+  int* h_status = nullptr;  // pinned mirrors
+  int* h_iters = nullptr;
+  double* h_rr = nullptr;
+  double* h_r0 = nullptr;
+};
+
+extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t model, fcgno_prec prec, int m_max,
+                                            double tol, int max_iter, int iters_per_step, void* stream,
+                                            fcgno_bucket_t* out) {
+  using namespace fcgno;
+  if (N < 2 || capacity < 1 || m_max < 1 || m_max > kMaxWindow || !(tol >= 0.0) || max_iter < 1 ||
+      iters_per_step < 1 || !out || (model && N < 2 * model->desc.modes)) {
+    set_last_error("fcgno_bucket_create: bad arguments");
+    return FCGNO_EINVAL;
+  }
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  fcgno_bucket* k = new fcgno_bucket();
+  fcgno_op* op = new fcgno_op();
+  op->N = N;
+  op->B = capacity;
+  op->n = (size_t)N * N;
+  k->op = op;
+  k->model = model;
+  k->prec = prec;
+  k->G = iters_per_step;
+  k->max_iter = max_iter;
+  const size_t vec = op->n * capacity * sizeof(double);
+  bool ok = cudaMalloc(&op->aE, vec) == cudaSuccess && cudaMalloc(&op->aN, vec) == cudaSuccess &&
+            cudaMalloc(&op->diag, vec) == cudaSuccess && cudaMalloc(&op->logk, vec) == cudaSuccess &&
+            cudaMalloc(&op->logk32, vec / 2) == cudaSuccess && cudaMalloc(&k->x, vec) == cudaSuccess &&
+            cudaMalloc(&k->b, vec) == cudaSuccess &&
+            cudaMallocHost(&k->h_status, sizeof(int) * capacity) == cudaSuccess &&
+            cudaMallocHost(&k->h_iters, sizeof(int) * capacity) == cudaSuccess &&
+            cudaMallocHost(&k->h_rr, sizeof(double) * capacity) == cudaSuccess &&
+            cudaMallocHost(&k->h_r0, sizeof(double) * capacity) == cudaSuccess;
+  fcgno_status rc = ok ? ensure_ws(op, m_max + 1) : FCGNO_ENOMEM;
+  if (rc != FCGNO_OK) {
+    cudaGetLastError();
+    fcgno_bucket_destroy(k);
+    set_last_error("fcgno_bucket_create: out of memory");
+    return rc;
+  }
+  // unused slots: neutral operator values, status "stopped" so that every kernel skips them
+  cudaMemsetAsync(op->aE, 0, vec, st);
+  cudaMemsetAsync(op->aN, 0, vec, st);
+  cudaMemsetAsync(op->logk, 0, vec, st);
+  cudaMemsetAsync(op->logk32, 0, vec / 2, st);
+  cudaMemsetAsync(k->x, 0, vec, st);
+  cudaMemsetAsync(k->b, 0, vec, st);
+  cudaMemsetAsync(op->ws.r, 0, vec, st);
+  cudaMemsetAsync(op->ws.rms, 0, sizeof(double) * capacity, st);
+  cudaMemsetAsync(op->ws.iters, 0, sizeof(int) * capacity, st);
+  std::vector<int> stopped(capacity, FCGNO_OK);
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(op->ws.status, stopped.data(), sizeof(int) * capacity, cudaMemcpyHostToDevice, st));
+  FCGNO_CUDA_TRY(cudaMemsetAsync(op->diag, 0, vec, st));
+  FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+  SolverWorkspace& w = op->ws;
+  const bool identity = (model == nullptr);
+  k->s = make_state(op, k->b, k->x, identity ? w.r : w.w);
+  k->a.N = N;
+  k->a.B = capacity;
+  k->a.n = op->n;
+  k->a.tiles = (int)ceil_div(op->n, kTile);
+  k->a.nslots = m_max + 1;
+  k->a.tol = tol;
+  k->a.fixed = 0;
+  k->L = loop_shape(op);
+  if (k->L.fused && k->L.fusedSmem > 48 * 1024)
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        (int)k->L.fusedSmem));
+  *out = k;
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_bucket_admit(fcgno_bucket_t k, int slot, const double* kcoef, const double* f,
+                                           const double* x0, void* stream) {
+  using namespace fcgno;
+  if (!k || slot < 0 || slot >= k->op->B || !kcoef || !f || !x0) {
+    set_last_error("fcgno_bucket_admit: bad arguments");
+    return FCGNO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  fcgno_op* op = k->op;
+  const size_t n = op->n, off = (size_t)slot * n;
+  // the slot's operator, right-hand side and initial guess
+  FCGNO_TRY(launch_assemble(op->N, n, n, kcoef, op->aE + off, op->aN + off, op->diag + off, op->logk + off,
+                            op->logk32 + off, st));
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(k->b + off, f, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(k->x + off, x0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // r_0, ||r_0||, status "running", iteration 0 for this slot only
+  IterArgs a1 = k->a;
+  a1.B = 1;
+  State s1 = k->s;
+  s1.aE += off;
+  s1.aN += off;
+  s1.diag += off;
+  s1.b += off;
+  s1.u += off;
+  s1.r += off;
+  s1.part += (size_t)slot * a1.tiles * kParts;
+  s1.rr += slot;
+  s1.r0 += slot;
+  s1.rms += slot;
+  s1.status += slot;
+  s1.iters += slot;
+  init_kernel<<<dim3(a1.tiles, 1), kThreads, 0, st>>>(a1, s1);
+  FCGNO_LAUNCHED();
+  init_finalize_kernel<<<1, 128, 0, st>>>(a1, s1);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_bucket_step(fcgno_bucket_t k, void* stream) {
+  using namespace fcgno;
+  if (!k) {
+    set_last_error("fcgno_bucket_step: null bucket");
+    return FCGNO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  SolverWorkspace& w = k->op->ws;
+  FCGNO_CUDA_TRY(cudaEventRecord(w.ev_in, st));
+  FCGNO_CUDA_TRY(cudaStreamWaitEvent(w.cs, w.ev_in, 0));
+  if (!k->warmed || !graphs_enabled() || k->G == 1) {
+    // first step eagerly (lazily allocated buffers exist before any capture)
+    for (int i = 0; i < k->G; ++i) FCGNO_TRY(launch_iteration(k->op, k->model, k->prec, k->a, k->s, k->L, w.cs));
+    k->warmed = true;
+  } else {
+    FCGNO_TRY(ensure_graph(k->op, k->model, k->prec, k->a, k->s, k->L, k->b, k->x, k->G, 0));
+    FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph.exec, w.cs));
+    g_launches.fetch_add(w.graph.kernels, std::memory_order_relaxed);
+  }
+  FCGNO_CUDA_TRY(cudaEventRecord(w.ev_out, w.cs));
+  FCGNO_CUDA_TRY(cudaStreamWaitEvent(st, w.ev_out, 0));
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_bucket_poll(fcgno_bucket_t k, int32_t* status, int32_t* iters, double* relres,
+                                          void* stream) {
+  using namespace fcgno;
+  if (!k || !status || !iters || !relres) {
+    set_last_error("fcgno_bucket_poll: bad arguments");
+    return FCGNO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  SolverWorkspace& w = k->op->ws;
+  const int B = k->op->B;
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(k->h_status, w.status, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(k->h_iters, w.iters, sizeof(int) * B, cudaMemcpyDeviceToHost, st));
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(k->h_rr, w.rr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(k->h_r0, w.r0, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
+  FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < B; ++i) {
+    int stt = k->h_status[i];
+    if (stt == kRunning && k->h_iters[i] >= k->max_iter) stt = FCGNO_ENOCONV;
+    status[i] = stt;
+    iters[i] = k->h_iters[i];
+    relres[i] = k->h_r0[i] > 0 ? std::sqrt(k->h_rr[i]) / k->h_r0[i] : 0.0;
+  }
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_bucket_take(fcgno_bucket_t k, int slot, double* x_out, void* stream) {
+  using namespace fcgno;
+  if (!k || slot < 0 || slot >= k->op->B) {
+    set_last_error("fcgno_bucket_take: bad arguments");
+    return FCGNO_EINVAL;
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t n = k->op->n, off = (size_t)slot * n;
+  if (x_out) FCGNO_CUDA_TRY(cudaMemcpyAsync(x_out, k->x + off, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  // stop the slot (a capped slot is still "running" on the device)
+  const int stopped = FCGNO_ENOCONV;
+  int cur = 0;
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(&cur, k->op->ws.status + slot, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (cur == kRunning)
+    FCGNO_CUDA_TRY(cudaMemcpyAsync(k->op->ws.status + slot, &stopped, sizeof(int), cudaMemcpyHostToDevice, st));
+  FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_bucket_destroy(fcgno_bucket_t k) {
+  if (!k) return FCGNO_OK;
+  if (k->op) fcgno_op_destroy(k->op);
+  if (k->x) cudaFree(k->x);
+  if (k->b) cudaFree(k->b);
+  if (k->h_status) cudaFreeHost(k->h_status);
+  if (k->h_iters) cudaFreeHost(k->h_iters);
+  if (k->h_rr) cudaFreeHost(k->h_rr);
+  if (k->h_r0) cudaFreeHost(k->h_r0);
+  delete k;
   return FCGNO_OK;
 }

@@ -86,7 +86,7 @@ struct IterGraph {
   uint64_t trace_gen = 0;
   const void* model = nullptr;
   uint64_t model_gen = 0;
-  int prec = -1, nslots = 0, fixed = 0, G = 0;
+  int prec = -1, nslots = 0, fixed = 0, G = 0, jacobi = 0;
   double tol = 0.0;
   const void* b = nullptr;
   const void* x = nullptr;
@@ -101,6 +101,8 @@ struct SolverWorkspace {
   int* iter = nullptr;      // [1] device iteration counter
   double* r = nullptr;      // [B][n]
   double* w = nullptr;      // [B][n]  preconditioned residual
+  double* wt = nullptr;     // [B][n]  Jacobi sweep scratch
+  double* inv_diag = nullptr;  // [B][n] 1 / diag (Jacobi)
   double* P = nullptr;      // [slots][B][n] directions p_k
   double* S = nullptr;      // [slots][B][n] A p_k
   double* ps = nullptr;     // [slots][B]    (p_k, s_k)
@@ -154,6 +156,9 @@ struct BlobLayout {
 };
 BlobLayout blob_layout(const fcgno_model_desc& d);
 
+// Face coefficients, diagonal and log k of `total` grid points (all instances or one slot).
+fcgno_status launch_assemble(int N, size_t n, size_t total, const double* k, double* aE, double* aN, double* diag,
+                             double* logk, float* logk32, cudaStream_t st);
 // Stencil matvec y = A x for all instances (FP64).
 fcgno_status launch_apply_A(const fcgno_op* op, const double* x, double* y, cudaStream_t st);
 

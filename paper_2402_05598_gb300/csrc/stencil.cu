@@ -71,6 +71,13 @@ fcgno_status launch_apply_A(const fcgno_op* op, const double* x, double* y, cuda
   return FCGNO_OK;
 }
 
+fcgno_status launch_assemble(int N, size_t n, size_t total, const double* k, double* aE, double* aN, double* diag,
+                             double* logk, float* logk32, cudaStream_t st) {
+  assemble_kernel<<<ceil_div(total, 256), 256, 0, st>>>(N, n, total, k, aE, aN, diag, logk, logk32);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
 fcgno_status launch_rms(const double* r, int B, size_t n, double* rms, cudaStream_t st) {
   rms_kernel<<<B, 512, 0, st>>>(r, n, rms);
   FCGNO_LAUNCHED();

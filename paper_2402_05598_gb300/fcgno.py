@@ -56,12 +56,19 @@ def _load():
         "fcgno_solve_host": (c_int, [c_int, c_int, P, P, P, P, POINTER(fcgno_solve_opts), c_int,
                                      POINTER(fcgno_solve_info), P]),
         "fcgno_solve_noalloc": (c_int, [P, P, P, POINTER(fcgno_solve_opts), POINTER(fcgno_solve_info), P]),
+        "fcgno_solve_jacobi": (c_int, [P, c_int, P, P, POINTER(fcgno_solve_opts), POINTER(fcgno_solve_info), P]),
         "fcgno_krylov_harvest": (c_int, [P, P, P, P, c_int, P, P, POINTER(fcgno_solve_info), P]),
         "fcgno_train_step": (c_int, [P, P, P, P, c_int, c_int, P, P, P]),
         "fcgno_workspace_bytes": (c_size_t, [c_int, c_int, c_int, POINTER(fcgno_model_desc), c_int]),
         "fcgno_status_str": (c_char_p, [c_int]),
         "fcgno_last_error": (c_char_p, []),
         "fcgno_launch_count": (c_uint64, []),
+        "fcgno_bucket_create": (c_int, [c_int, c_int, P, c_int, c_int, c_double, c_int, c_int, P, POINTER(P)]),
+        "fcgno_bucket_admit": (c_int, [P, c_int, P, P, P, P]),
+        "fcgno_bucket_step": (c_int, [P, P]),
+        "fcgno_bucket_poll": (c_int, [P, P, P, P, P]),
+        "fcgno_bucket_take": (c_int, [P, c_int, P, P]),
+        "fcgno_bucket_destroy": (c_int, [P]),
         "fcgno_trace_set": (c_int, [c_char_p]),
         "fcgno_trace_collect": (c_int, [POINTER(c_double), POINTER(c_uint64)]),
     }
@@ -78,8 +85,10 @@ lib = _load()
 EXPORTS = [
     "fcgno_assemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
-    "fcgno_solve_noalloc", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_workspace_bytes", "fcgno_status_str",
+    "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_workspace_bytes", "fcgno_status_str",
     "fcgno_last_error", "fcgno_launch_count", "fcgno_trace_set", "fcgno_trace_collect",
+    "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
+    "fcgno_bucket_destroy",
 ]
 
 
@@ -227,6 +236,16 @@ def solve_host(k: np.ndarray, b: np.ndarray, x: np.ndarray, model=None, tol=1e-6
     return _info_list(info)
 
 
+def solve_jacobi(op: Operator, steps, b, x, tol=1e-6, m_max=1, max_iter=1000, fixed_iters=False, check_every=8,
+                 stream=None):
+    """fcgno_solve_jacobi: Algorithm 1 with the Jacobi(steps) preconditioner (Eq. (15))."""
+    info = (fcgno_solve_info * op.B)()
+    opts = _opts(tol, m_max, max_iter, fixed_iters, check_every)
+    _check(lib.fcgno_solve_jacobi(op.handle, int(steps), _ptr(b), _ptr(x), ctypes.byref(opts), info,
+                                  _stream(stream)), "fcgno_solve_jacobi")
+    return _info_list(info)
+
+
 def solve_noalloc(op: Operator, b, x, tol=1e-6, m_max=1, max_iter=1000, fixed_iters=False, check_every=8,
                   stream=None):
     """fcgno_solve_noalloc: identity-preconditioned solve with no device allocation (for callers
@@ -252,3 +271,45 @@ def train_step(model: Model, op: Operator, r, e, loss, grad, prec="fp32", stream
 
 def workspace_bytes(N, batch, m_max, desc, prec="bf16") -> int:
     return int(lib.fcgno_workspace_bytes(int(N), int(batch), int(m_max), ctypes.byref(desc), PREC[prec]))
+
+
+class Bucket:
+    """fcgno_bucket_*: a resident batch of same-size solves with independent slots."""
+
+    def __init__(self, N, capacity, model=None, prec="bf16", m_max=1, tol=1e-6, max_iter=1000, iters_per_step=8,
+                 stream=None):
+        self.N, self.capacity = int(N), int(capacity)
+        self.handle = c_void_p()
+        _check(lib.fcgno_bucket_create(self.N, self.capacity, model.handle if model is not None else None, PREC[prec],
+                                       int(m_max), float(tol), int(max_iter), int(iters_per_step), _stream(stream),
+                                       ctypes.byref(self.handle)), "fcgno_bucket_create")
+        self._status = np.zeros(self.capacity, dtype=np.int32)
+        self._iters = np.zeros(self.capacity, dtype=np.int32)
+        self._relres = np.zeros(self.capacity, dtype=np.float64)
+
+    def admit(self, slot, k, f, x0, stream=None):
+        _check(lib.fcgno_bucket_admit(self.handle, int(slot), _ptr(k), _ptr(f), _ptr(x0), _stream(stream)),
+               "fcgno_bucket_admit")
+
+    def step(self, stream=None):
+        _check(lib.fcgno_bucket_step(self.handle, _stream(stream)), "fcgno_bucket_step")
+
+    def poll(self, stream=None):
+        _check(lib.fcgno_bucket_poll(self.handle, self._status.ctypes.data, self._iters.ctypes.data,
+                                     self._relres.ctypes.data, _stream(stream)), "fcgno_bucket_poll")
+        return self._status.copy(), self._iters.copy(), self._relres.copy()
+
+    def take(self, slot, x_out=None, stream=None):
+        _check(lib.fcgno_bucket_take(self.handle, int(slot), _ptr(x_out) if x_out is not None else None,
+                                     _stream(stream)), "fcgno_bucket_take")
+
+    def close(self):
+        if self.handle:
+            lib.fcgno_bucket_destroy(self.handle)
+            self.handle = c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,125 @@
+"""Request loop for serving FCG-NO solves (continuous batching over size buckets).
+
+Requests (grid size N, coefficient field k, right-hand side f, initial guess u_0) arrive
+over time. Each grid size has one resident bucket (``fcgno.Bucket``) whose capacity was
+admitted against an HBM budget when the server started. The loop repeatedly
+  1. admits every arrived request whose bucket has a free slot (first come, first served;
+     the others wait in their bucket's queue),
+  2. advances every bucket that has running slots by one step (a few FCG-NO iterations,
+     replayed as one CUDA graph),
+  3. polls the buckets and retires finished slots (converged, breakdown, or capped),
+     recording each request's completion time.
+Latency = completion time - arrival time (queueing included).
+"""
+from __future__ import annotations
+
+import time
+from collections import deque
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import fcgno as F
+
+
+@dataclass
+class Request:
+    rid: int
+    arrival: float          # seconds from the start of the run
+    N: int
+    k: object               # device [N][N] float64
+    f: object
+    x0: object
+    done: float = -1.0
+    iters: int = 0
+    status: int = -1
+    relres: float = 0.0
+
+
+@dataclass
+class ServeStats:
+    latencies_ms: list = field(default_factory=list)
+    completed: int = 0
+    converged: int = 0
+    wall_s: float = 0.0
+    offered_rate: float = 0.0
+    bucket_bytes: int = 0
+
+    def summary(self) -> dict:
+        lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
+        return {"requests": self.completed, "converged": self.converged,
+                "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                "mean_ms": float(lat.mean()), "solves_per_s": self.completed / max(self.wall_s, 1e-9),
+                "offered_per_s": self.offered_rate, "wall_s": self.wall_s, "bucket_bytes": self.bucket_bytes}
+
+
+def slot_bytes(N: int, m_max: int, desc, prec: str) -> int:
+    """Device bytes one resident solve of an N x N grid needs (solver state and operator)."""
+    return F.workspace_bytes(N, 1, m_max, desc, prec) + 2 * 8 * N * N  # + iterate and right-hand side
+
+
+def plan_capacities(sizes_weights: dict, budget_bytes: int, m_max: int, desc, prec: str, max_slots: int = 256) -> dict:
+    """Split an HBM budget across buckets in proportion to each size's share of the offered
+    unknowns (weight x N^2), capped at max_slots slots per bucket."""
+    tot = sum(w * N * N for N, w in sizes_weights.items())
+    caps = {}
+    for N, w in sizes_weights.items():
+        share = budget_bytes * (w * N * N) / tot
+        caps[N] = int(max(1, min(max_slots, share // slot_bytes(N, m_max, desc, prec))))
+    return caps
+
+
+class Server:
+    def __init__(self, model, capacities: dict, prec="bf16", m_max=1, tol=1e-6, max_iter=400, iters_per_step=8):
+        self.buckets = {N: F.Bucket(N, cap, model, prec=prec, m_max=m_max, tol=tol, max_iter=max_iter,
+                                    iters_per_step=iters_per_step) for N, cap in capacities.items()}
+        self.slots = {N: [None] * cap for N, cap in capacities.items()}
+        self.queues = {N: deque() for N in capacities}
+
+    def run(self, requests: list, stats: ServeStats) -> ServeStats:
+        """Serves the requests (sorted by arrival) and returns latency statistics."""
+        import torch
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        t0 = time.perf_counter()
+        outstanding = len(pending)
+        while outstanding:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                r = pending.popleft()
+                self.queues[r.N].append(r)
+            # admit into free slots
+            for N, q in self.queues.items():
+                slots = self.slots[N]
+                for i in range(len(slots)):
+                    if not q:
+                        break
+                    if slots[i] is None:
+                        r = q.popleft()
+                        self.buckets[N].admit(i, r.k, r.f, r.x0)
+                        slots[i] = r
+            busy = [N for N, slots in self.slots.items() if any(s is not None for s in slots)]
+            if not busy:
+                if pending:  # idle until the next arrival
+                    time.sleep(max(0.0, min(0.001, pending[0].arrival - (time.perf_counter() - t0))))
+                continue
+            for N in busy:
+                self.buckets[N].step()
+            for N in busy:
+                st, it, rr = self.buckets[N].poll()
+                tnow = time.perf_counter() - t0
+                for i, r in enumerate(self.slots[N]):
+                    if r is not None and st[i] != -1:
+                        self.buckets[N].take(i)
+                        r.done, r.iters, r.status, r.relres = tnow, int(it[i]), int(st[i]), float(rr[i])
+                        stats.latencies_ms.append(1000.0 * (r.done - r.arrival))
+                        stats.completed += 1
+                        stats.converged += int(r.status == F.FCGNO_OK)
+                        self.slots[N][i] = None
+                        outstanding -= 1
+        torch.cuda.synchronize()
+        stats.wall_s = time.perf_counter() - t0
+        return stats
+
+    def close(self):
+        for b in self.buckets.values():
+            b.close()

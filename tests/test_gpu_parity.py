@@ -280,3 +280,20 @@ def test_train_step_matches_oracle_gradient(lib, dev, prec, tol):
     for name, (o, s) in off.items():
         if name != "_total":
             assert rel(g[o:o + s], g_ref[o:o + s]) < max(tol * 10, 1e-7), name
+
+
+@pytest.mark.parametrize("N,B,steps,m", [(32, 2, 4, 1), (100, 2, 3, 2)])
+def test_jacobi_preconditioned_iterates_match_oracle(lib, dev, N, B, steps, m):
+    """Algorithm 1 with the Jacobi(k) preconditioner of Eq. (15), fused (N <= 80) and tiled
+    paths: 15 fixed iterations against the oracle within its rounding sensitivity."""
+    k, f = batch(N, B, 1400 + N)
+    x0 = np.random.default_rng(7).standard_normal((B, N, N))
+    op = lib.Operator(to_dev(k, dev))
+    x = to_dev(x0, dev)
+    info = lib.solve_jacobi(op, steps, to_dev(f, dev), x, m_max=m, max_iter=15, fixed_iters=True)
+    xs = x.cpu().numpy()
+    for b in range(B):
+        run = lambda d: O.fcg(lambda u: O.apply_A(k[b], u), lambda r: O.jacobi_precond(k[b], r, steps), f[b], x0[b],
+                              m, 15, **({} if d is None else {"dot": d}))["u"]
+        assert info[b]["iters"] == 15
+        assert rel(xs[b], run(None)) < rounding_tol(run)

@@ -1,0 +1,97 @@
+"""Serving buckets (continuous batching): a solve's result does not depend on the other
+slots of its bucket, on when it was admitted, or on slots admitted and retired around it."""
+import numpy as np
+import pytest
+
+from oracle import fcgno_oracle as O
+from paper_2402_05598_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def dev_arrays(N, seed, dev):
+    import torch
+    k, f = I.make_problem(N, seed)
+    x0 = np.random.default_rng(seed + 777).standard_normal((N, N))
+    return tuple(torch.from_numpy(a).to(dev) for a in (k, f, x0))
+
+
+def run_alone(lib, dev, model, N, seed, prec, steps, **kw):
+    import torch
+    bk = lib.Bucket(N, 4, model, prec=prec, iters_per_step=8, **kw)
+    k, f, x0 = dev_arrays(N, seed, dev)
+    bk.admit(0, k, f, x0)
+    for _ in range(steps):
+        bk.step()
+    st, it, rr = bk.poll()
+    x = torch.empty((N, N), dtype=torch.float64, device=dev)
+    bk.take(0, x)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), int(it[0]), float(rr[0]), int(st[0])
+
+
+def run_in_mix(lib, dev, model, N, seed, prec, steps, **kw):
+    """The same request admitted into slot 2 after two steps of other traffic; another
+    request joins one step later and one leaves while ours runs."""
+    import torch
+    bk = lib.Bucket(N, 4, model, prec=prec, iters_per_step=8, **kw)
+    a = dev_arrays(N, seed + 1, dev)
+    c = dev_arrays(N, seed + 2, dev)
+    d = dev_arrays(N, seed + 3, dev)
+    bk.admit(1, *a)
+    bk.step()
+    bk.admit(3, *d)
+    bk.step()
+    k, f, x0 = dev_arrays(N, seed, dev)
+    bk.admit(2, k, f, x0)
+    for s in range(steps):
+        bk.step()
+        if s == 0:
+            bk.admit(0, *c)
+        if s == 1:
+            bk.take(3)  # a neighbour retires early
+    st, it, rr = bk.poll()
+    x = torch.empty((N, N), dtype=torch.float64, device=dev)
+    bk.take(2, x)
+    torch.cuda.synchronize()
+    return x.cpu().numpy(), int(it[2]), float(rr[2]), int(st[2])
+
+
+@pytest.mark.parametrize("prec,C,M,N", [("bf16", 32, 12, 64), ("fp64", 16, 8, 32)])
+def test_result_is_the_same_alone_and_in_the_mix(lib, dev, prec, C, M, N):
+    import torch
+    desc = I.ModelDesc(width=C, layers=4, modes=M, proj_width=C)
+    w = torch.from_numpy(I.xavier_weights(desc, 4)).to(dev)
+    model = lib.Model(lib.make_desc(C, 4, M, C), w)
+    xa, ia, ra, sa = run_alone(lib, dev, model, N, 3000, prec, 3, max_iter=24)
+    xb, ib, rb, sb = run_in_mix(lib, dev, model, N, 3000, prec, 3, max_iter=24)
+    assert ia == ib == 24 and sa == sb == lib.FCGNO_ENOCONV
+    assert np.array_equal(xa, xb)
+    assert ra == rb
+
+
+def test_bucket_slot_matches_oracle_cg_and_stops_itself(lib, dev):
+    """Identity preconditioner: a slot converges on its own (status FCGNO_OK), with the
+    oracle's iteration count, while a neighbour keeps running."""
+    import torch
+    N = 24
+    bk = lib.Bucket(N, 3, None, prec="fp64", tol=1e-8, max_iter=5000, iters_per_step=8)
+    k, f, x0 = dev_arrays(N, 3100, dev)
+    other = dev_arrays(N, 3101, dev)
+    bk.admit(1, *other)
+    bk.step()
+    bk.admit(0, k, f, x0)
+    for _ in range(400):
+        bk.step()
+        st, it, rr = bk.poll()
+        if st[0] != -1:
+            break
+    assert st[0] == lib.FCGNO_OK
+    x = torch.empty((N, N), dtype=torch.float64, device=dev)
+    bk.take(0, x)
+    kn, fn, x0n = (t.cpu().numpy() for t in (k, f, x0))
+    ref = O.fcg(lambda u: O.apply_A(kn, u), lambda r: r, fn, x0n, 1, 5000, tol=1e-8)
+    assert abs(int(it[0]) - ref["iterations"]) <= max(2, ref["iterations"] // 100)
+    assert rr[0] <= 1e-8
+    true_res = np.linalg.norm(fn - O.apply_A(kn, x.cpu().numpy())) / np.linalg.norm(fn - O.apply_A(kn, x0n))
+    assert true_res < 1e-7

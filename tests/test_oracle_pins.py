@@ -361,3 +361,17 @@ def test_notay_gradient_matches_central_differences():
             assert abs(fd - g[i]) <= 1e-6 * max(abs(fd), 1e-3), (name, idx, fd, g[i])
             checked += 1
     assert checked >= 20
+
+
+def test_table1_jacobi4_iteration_counts_soft_pin():
+    """Table 1: FCG with Jacobi(4) needs 30/58 iterations (Poisson) and 32/61 (Diffusion) at
+    grid 32/64 to reach 1e-6 from u_0 ~ N(0, 1). Soft pin (+-20%)."""
+    for N, poisson, diffusion in ((32, 30, 32), (64, 58, 61)):
+        for gen, target in ((I.poisson_problem, poisson), (I.diffusion_problem, diffusion)):
+            its = []
+            for s in range(2):
+                k, f = gen(N, s)
+                u0 = np.random.default_rng(100 + s).standard_normal((N, N))
+                out = O.fcg(lambda u: O.apply_A(k, u), lambda r: O.jacobi_precond(k, r, 4), f, u0, 1, 1000, tol=1e-6)
+                its.append(out["iterations"])
+            assert abs(np.mean(its) - target) <= 0.2 * target, (N, gen.__name__, its)
