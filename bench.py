@@ -270,6 +270,7 @@ def main():
     from paper_2402_05598_gb300 import fcgno as F
     from paper_2402_05598_gb300 import inputs as I
     from paper_2402_05598_gb300 import train as T
+    from paper_2402_05598_gb300 import replicas as R
 
     # ---- setup: model, training (untimed)
     desc_np = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=MODES, proj_width=WIDTH)
@@ -296,7 +297,7 @@ def main():
                      log_every=1000)
 
     # ---- eval inputs (resident)
-    seeds = range(10000 + EVAL_BATCH * rank, 10000 + EVAL_BATCH * (rank + 1))
+    seeds = R.rank_seeds(rank, EVAL_BATCH)
     k_np, f_np = I.make_batch(N_GRID, seeds)
     u0_np = np.stack([np.random.default_rng(s + 777).standard_normal((N_GRID, N_GRID)) for s in seeds])
     k = torch.from_numpy(k_np).to(dev)
@@ -342,19 +343,10 @@ def main():
     trace_note = F.last_error() if "trace" in F.last_error() else ""
     F.trace_set("")
     clk = clocks.stop()
-    total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
     solved = sum(sum(1 for i in inf if i["status"] == F.FCGNO_OK) for inf in infos)
+    total_ms, solved_all = R.reduce_timing(float(sum(step_ms)), solved, dev)
     iters = [i["iters"] for i in infos[-1]]
     # only solves that reached the tolerance count (capped instances are reported, not counted)
-    solved_all = solved
-    if world > 1:
-        t = torch.tensor([float(solved)], device=dev)
-        torch.distributed.all_reduce(t)
-        solved_all = int(t.item())
     value = solved_all / (total_ms / 1000.0)
 
     # ---- roofline of the dominant kernel (synthesis): algorithmic bytes / traced device time
