@@ -37,9 +37,24 @@ __device__ __forceinline__ uint16_t f2h16(float x, bool bf16) {
   return *reinterpret_cast<uint16_t*>(&h);
 }
 __device__ __forceinline__ uint32_t pack2(float a, float b, bool bf16) {
-  return (uint32_t)f2h16(a, bf16) | ((uint32_t)f2h16(b, bf16) << 16);
+  if (bf16) {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a, b);  // one conversion for the pair
+    return *reinterpret_cast<const uint32_t*>(&h);
+  }
+  const __half2 h = __floats2half2_rn(a, b);
+  return *reinterpret_cast<const uint32_t*>(&h);
 }
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
+
+// GELU of the 16-bit path in the tanh form of Hendrycks & Gimpel (2016),
+// 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))), evaluated as x * sigmoid(2 sqrt(2/pi) (...))
+// so that nothing cancels for negative x. It departs from the erf form by at most 4.7e-4
+// (absolute), below the 16-bit rounding of the values it produces, and costs a few
+// instructions instead of a branchy erf.
+__device__ __forceinline__ float gelu16(float x) {
+  const float u = 1.5957691216057308f * fmaf(0.044715f * x, x * x, x);
+  return __fdividef(x, 1.0f + __expf(-u));
+}
 
 // Geometry shared by host and device.
 struct TcGeom {
@@ -370,16 +385,17 @@ __global__ void __launch_bounds__(kTcThreads, 2)
                        const uint16_t* __restrict__ E2, const uint16_t* __restrict__ G, float* __restrict__ part,
                        int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t mbar, mbar2[2];
+  __shared__ uint64_t mbar, mbar2[3];
   __shared__ uint32_t tbase_s;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(active, b)) return;
   const int N = g.N, PC = g.PC, QC = g.QC, Ky = g.Ky;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // shared layout
-  uint8_t* sE2 = smem;                              // 2 x (32 x QC), K-major: LBO 128, SBO QC*16
-  uint8_t* sA = sE2 + 2 * 32 * QC * 2;              // 2 x (128 x QC), MN-major: SBO 128, LBO 2048
-  uint8_t* sAP = sA + 2 * 128 * QC * 2;             // MP x 2PC, K-major: LBO 128, SBO 2PC*16
+  const int ne2 = (N / QC > 1) ? 3 : 1;             // E2 changes per q chunk only when N > QC
+  uint8_t* sE2 = smem;                              // ne2 x (32 x QC), K-major: LBO 128, SBO QC*16
+  uint8_t* sA = sE2 + ne2 * 32 * QC * 2;            // 3 x (128 x QC), MN-major: SBO 128, LBO 2048
+  uint8_t* sAP = sA + 3 * 128 * QC * 2;             // MP x 2PC, K-major: LBO 128, SBO 2PC*16
   uint8_t* sG = sAP + (size_t)g.MP * 2 * PC * 2;    // NPM x 2PC, K-major: LBO 128, SBO 2PC*16
   const uint32_t SBO_E = QC * 16, SBO_P = 2 * PC * 16, SBO_G = 2 * PC * 16;
   const uint32_t LBO_A = 2048;  // k-direction stride of the MN-major stage-Q operand (16 m-core matrices)
@@ -390,6 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     mbar_init(&mbar, 1);
     mbar_init(&mbar2[0], 1);
     mbar_init(&mbar2[1], 1);
+    mbar_init(&mbar2[2], 1);
   }
   // stage G slice (k = 2*p0 .. 2*p0 + 2PC) and zero the padding rows of sAP
   const int p0 = chunk * PC;
@@ -414,13 +431,14 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const int qchunks = N / QC;
   constexpr uint32_t idQ = idesc_f16(128, 32, true, true, false);
   constexpr uint32_t idQh = idesc_f16(128, 32, false, true, false);
-  // Steps s = (m-tile, q-chunk) run through a two-deep pipeline: while the MMA of step s
-  // runs, the operands of step s+1 are copied into the other buffer; the Z accumulator
-  // alternates between two TMEM slots by m-tile so that the read-back of one m-tile overlaps
-  // the MMAs of the next.
+  // Steps s = (m-tile, q-chunk) run through a three-slot pipeline: while the MMA of step s
+  // runs, the operands of steps s+1 and s+2 are in flight; the Z accumulator alternates
+  // between two TMEM slots by m-tile so that the read-back of one m-tile overlaps the MMAs
+  // of the next.
+  constexpr int NS = 3;
   const int nsteps = mtiles * qchunks;
-  uint32_t phs[2] = {0, 0};
-  bool pending[2] = {false, false};
+  uint32_t phs[NS] = {0, 0, 0};
+  bool pending[NS] = {false, false, false};
   auto stage = [&](int st_, int buf) {
     const int mt = st_ / qchunks, qc = st_ % qchunks, q0 = qc * QC;
     if (qchunks > 1 || st_ == 0) {
@@ -440,10 +458,22 @@ __global__ void __launch_bounds__(kTcThreads, 2)
     }
     cp_async_commit();
   };
+  auto wait_slot = [&](int buf) -> bool {
+    if (!pending[buf]) return true;
+    const bool r = mbar_wait(&mbar2[buf], phs[buf]);
+    phs[buf] ^= 1;
+    pending[buf] = false;
+    fence_after_sync();
+    return r;
+  };
   stage(0, 0);
+  if (nsteps > 1) stage(1, 1);
   for (int st_ = 0; st_ < nsteps && ok; ++st_) {
-    const int buf = st_ & 1, mt = st_ / qchunks, qc = st_ % qchunks;
-    cp_async_wait_all();
+    const int buf = st_ % NS, mt = st_ / qchunks, qc = st_ % qchunks;
+    if (st_ + 1 < nsteps)
+      cp_async_wait_all_but_one();  // step st_'s copies done, step st_+1's may still fly
+    else
+      cp_async_wait_all();
     fence_smem_to_async();
     fence_before_sync();
     __syncthreads();
@@ -458,22 +488,15 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       commit(&mbar2[buf]);
     }
     pending[buf] = true;
-    if (st_ + 1 < nsteps) {
-      // the other buffer was read by the previous step's MMA: wait for it before refilling
-      if (pending[buf ^ 1]) {
-        ok = mbar_wait(&mbar2[buf ^ 1], phs[buf ^ 1]);
-        phs[buf ^ 1] ^= 1;
-        pending[buf ^ 1] = false;
-        fence_after_sync();
-        if (!ok) break;
-      }
-      stage(st_ + 1, buf ^ 1);
+    if (st_ + 2 < nsteps) {
+      // the slot of step st_-1: its MMA must have finished before it is refilled
+      const int nb = (st_ + 2) % NS;
+      ok = wait_slot(nb);
+      if (!ok) break;
+      stage(st_ + 2, nb);
     }
     if (qc == qchunks - 1) {
-      ok = mbar_wait(&mbar2[buf], phs[buf]);
-      phs[buf] ^= 1;
-      pending[buf] = false;
-      fence_after_sync();
+      ok = wait_slot(buf);
       if (!ok) break;
       // read Z for this m-tile: lane = (p, c), columns (k2, t) -> sAP[(k2, c)][(p, t)]
       const int m = mt * 128 + warp * 32 + lane;
@@ -486,9 +509,13 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       tmem_ld16(tq + ((uint32_t)(warp * 32) << 16) + 16, tmp);
 #pragma unroll
       for (int i = 0; i < 16; ++i) z[16 + i] = tmp[i];
-      for (int k2 = 0; k2 < Ky; ++k2) {
-        const int row = k2 * C + c;
-        *reinterpret_cast<uint32_t*>(sAP + kmajor_off(row, 2 * pl, 128, SBO_P)) = pack2(z[2 * k2], z[2 * k2 + 1], bf16);
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {  // Ky <= 16: static indices keep z in registers
+        if (k2 < Ky) {
+          const int row = k2 * C + c;
+          *reinterpret_cast<uint32_t*>(sAP + kmajor_off(row, 2 * pl, 128, SBO_P)) =
+              pack2(z[2 * k2], z[2 * k2 + 1], bf16);
+        }
       }
     }
   }
@@ -567,6 +594,7 @@ __global__ void __launch_bounds__(kTcThreads)
   {
     // warp w loads rows 32w..32w+31; a row (one instance's C2 values) is one coalesced read
     // per chunk, the chunks are summed in order
+#pragma unroll 8
     for (int r = 0; r < 32; ++r) {
       const int row = warp * 32 + r;
       const int b = b0 + row;
@@ -678,16 +706,19 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) 
   const uint32_t LBO_A1 = (g.MP / 8) * 128;  // MN-major: K-direction core-matrix stride
   const uint32_t SBO_H = g.KXP * 16, SBO_B = g.KB * 16, SBO_S = g.KSYN * 16, SBO_C = C * 16;
   // region R0 holds the mixed coefficients for synthesis stage 1, then (aliased, once stage 1
-  // has completed) the two pointwise input tiles and the decoder input tile
-  const size_t r0a = (size_t)g.MP * g.KXP * 2, r0b = (size_t)3 * 128 * C * 2;
+  // has completed) a ring of three pointwise input tiles, the decoder input tile and, for
+  // N >= 128, the per-tile rows of the synthesis table
+  const size_t TB = (size_t)128 * C * 2, SB = (size_t)128 * g.KSYN * 2;
+  const size_t r0a = (size_t)g.MP * g.KXP * 2, r0b = 4 * TB + (N >= 128 ? 3 * SB : 0);
   const size_t r0 = r0a > r0b ? r0a : r0b;
   uint8_t* sA1 = smem;                                  // MP x KXP
-  uint8_t* sX0 = smem;                                  // 2 x (128 x C) pointwise tiles (after stage 1)
-  uint8_t* sD = smem + 2 * 128 * C * 2;                 // 128 x C decoder input (after stage 1)
+  uint8_t* sX0 = smem;                                  // 3 x (128 x C) pointwise tiles (after stage 1)
+  uint8_t* sD = smem + 3 * TB;                          // 128 x C decoder input (after stage 1)
+  uint8_t* sSb = smem + 4 * TB;                         // 3 x (128 x KSYN) table rows (N >= 128)
   uint8_t* sH = smem + r0;                              // 2PC x KXP
   uint8_t* sB = sH + (size_t)2 * PC * g.KXP * 2;        // C x KB
-  uint8_t* sS = sB + (size_t)C * g.KB * 2;              // 128 x KSYN
-  uint8_t* sW = sS + (size_t)128 * g.KSYN * 2;          // C x C
+  uint8_t* sS = sB + (size_t)C * g.KB * 2;              // 128 x KSYN (N < 128: one table for all tiles)
+  uint8_t* sW = sS + (N < 128 ? SB : 0);                // C x C
   uint8_t* sP = sW + C * C * 2;                         // C x C (decoder)
   const uint32_t TCOLS = 256;
   if (warp == 0) tmem_alloc(&tbase_s, TCOLS);
@@ -780,33 +811,39 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) 
   // ---- tiles of 128 grid points
   const int ntiles = (N < 128) ? PC / g.PT : PC * (N / 128);
   const uint16_t* vb = a.vin + (size_t)b * N * N * C;
-  auto tile_point = [&](int t, int m, int& q, int& p) -> bool {
+  // Thread tid owns tile row m = tid of every tile: its grid point within the tile is fixed,
+  // so the row's (q, column offset) and shared-memory offsets are computed once.
+  const int m_own = tid;
+  const int own_pl = (N < 128) ? m_own / N : 0;     // column within the tile (N < 128)
+  const int own_q = (N < 128) ? m_own % N : m_own;  // row (N < 128) or row within the q-tile
+  const bool own_valid = (N < 128) ? own_pl < g.PT : true;
+  const uint32_t own_xoff = kmajor_off(m_own, 0, 128, SBO_C);
+  auto tile_point = [&](int t, int& q, int& p) {
     if (N < 128) {
-      const int pl = m / N;
-      q = m % N;
-      p = p0 + t * g.PT + pl;
-      return pl < g.PT;
+      q = own_q;
+      p = p0 + t * g.PT + own_pl;
+    } else {
+      const int col = t / (N / 128), qt = t % (N / 128);
+      p = p0 + col;
+      q = qt * 128 + own_q;
     }
-    const int col = t / (N / 128), qt = t % (N / 128);
-    p = p0 + col;
-    q = qt * 128 + m;
-    return true;
   };
   auto prefetch = [&](int t, int buf) {
-    uint8_t* dst = sX0 + buf * 128 * C * 2;
-    for (int idx = tid; idx < 128 * (C / 8); idx += kTcThreads) {
-      const int m = idx % 128, kc = idx / 128;
-      int q, p;
-      if (tile_point(t, m, q, p)) {
-        cp_async16(dst + kmajor_off(m, kc * 8, 128, SBO_C), vb + ((size_t)q * N + p) * C + kc * 8);
-      } else {
-        *reinterpret_cast<uint4*>(dst + kmajor_off(m, kc * 8, 128, SBO_C)) = make_uint4(0, 0, 0, 0);
-      }
+    uint8_t* dst = sX0 + buf * TB + own_xoff;
+    int q, p;
+    tile_point(t, q, p);
+    const uint16_t* src = vb + ((size_t)q * N + p) * C;
+#pragma unroll
+    for (int kc = 0; kc < C / 8; ++kc) {
+      if (own_valid)
+        cp_async16(dst + kc * 128, src + kc * 8);
+      else
+        *reinterpret_cast<uint4*>(dst + kc * 128) = make_uint4(0, 0, 0, 0);
     }
     if (N >= 128) {
-      // synthesis rows of this tile's q range (same for every column)
+      // synthesis-table rows of this tile's q range, in the tile's ring slot
       const int qt = t % (N / 128);
-      uint8_t* sdst = sS + buf * 0;  // single buffer: loaded together with the tile
+      uint8_t* sdst = sSb + buf * SB;
       for (int idx = tid; idx < 128 * (g.KSYN / 8); idx += kTcThreads) {
         const int row = idx / (g.KSYN / 8), kc = idx % (g.KSYN / 8);
         cp_async16(sdst + kmajor_off(row, kc * 8, 128, SBO_S), a.Asyn + (size_t)(qt * 128 + row) * g.KSYN + kc * 8);
@@ -815,37 +852,59 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) 
     cp_async_commit();
   };
   const uint32_t idD = idesc_f16(128, C, bf16);
-  if (ok) prefetch(0, 0);
-  for (int t = 0; t < ntiles && ok; ++t) {
-    const int buf = t & 1;
-    cp_async_wait_all();
+  // tile t: ring slot t % 3, accumulator slot t % 2; issued by thread 0
+  auto mma_tile = [&](int t) {
+    const int buf = t % 3, acc = t & 1;
+    const uint32_t sx = smem_addr(sX0 + buf * TB);
+    const uint32_t ss = (N < 128) ? smem_addr(sS) : smem_addr(sSb + buf * SB);
+    for (int ks = 0; ks < C / 16; ++ks)
+      mma(tD + acc * C, desc(sx + ks * 256, 128, SBO_C), desc(smem_addr(sW) + ks * 256, 128, SBO_C), idD, ks > 0);
+    const int kb0 = (N < 128) ? t * g.PT * 2 * Ky : (t / (N / 128)) * 2 * Ky;
+    for (int ks = 0; ks < g.KSYN / 16; ++ks)
+      mma(tD + acc * C, desc(ss + ks * 256, 128, SBO_S), desc(smem_addr(sB) + (kb0 / 8) * 128 + ks * 256, 128, SBO_B),
+          idD, true);
+    commit(&mbar[1 + acc]);
+  };
+  float bias[C];
+#pragma unroll
+  for (int c = 0; c < C; ++c) bias[c] = a.bias[c];
+  // Software pipeline: while tile t's epilogue runs, tile t+1's MMA runs on the tensor core
+  // (other accumulator) and tile t+2's operands are being copied (third ring slot).
+  if (ok && ntiles > 0) {
+    prefetch(0, 0);
+    if (ntiles > 1) {
+      prefetch(1, 1);
+      cp_async_wait_all_but_one();
+    } else {
+      cp_async_wait_all();
+    }
     fence_smem_to_async();
     fence_before_sync();
     __syncthreads();
     fence_after_sync();
-    if (tid == 0) {
-      const uint32_t sx = smem_addr(sX0 + buf * 128 * C * 2);
-      for (int ks = 0; ks < C / 16; ++ks)
-        mma(tD + buf * C, desc(sx + ks * 256, 128, SBO_C), desc(smem_addr(sW) + ks * 256, 128, SBO_C), idD, ks > 0);
-      int kb0;
-      if (N < 128) kb0 = t * g.PT * 2 * Ky;
-      else kb0 = (t / (N / 128)) * 2 * Ky;
-      for (int ks = 0; ks < g.KSYN / 16; ++ks)
-        mma(tD + buf * C, desc(smem_addr(sS) + ks * 256, 128, SBO_S),
-            desc(smem_addr(sB) + (kb0 / 8) * 128 + ks * 256, 128, SBO_B), idD, true);
-      commit(&mbar[1 + buf]);
+    if (tid == 0) mma_tile(0);
+  }
+  for (int t = 0; t < ntiles && ok; ++t) {
+    if (t + 1 < ntiles) {
+      cp_async_wait_all();  // tile t+1's copies (the only group in flight)
+      fence_smem_to_async();
+      fence_before_sync();
+      __syncthreads();
+      fence_after_sync();
+      if (tid == 0) mma_tile(t + 1);
+      // ring slot of tile t-1, whose MMA completed before its epilogue
+      if (t + 2 < ntiles) prefetch(t + 2, (t + 2) % 3);
     }
-    // the next tile's loads overlap this tile's MMA and epilogue (N < 128: Asyn is static)
-    if (t + 1 < ntiles && N < 128) prefetch(t + 1, buf ^ 1);
+    const int buf = t & 1;
     ok = mbar_wait(&mbar[1 + buf], ph[1 + buf]);
     ph[1 + buf] ^= 1;
     fence_after_sync();
     if (!ok) break;
-    if (t + 1 < ntiles && N >= 128) prefetch(t + 1, buf ^ 1);
     // epilogue: lane = grid point, C columns
-    const int m = warp * 32 + lane;
+    const int m = m_own;
     int q, p;
-    const bool valid = tile_point(t, m, q, p);
+    tile_point(t, q, p);
+    const bool valid = own_valid;
     float h[C];
 #pragma unroll
     for (int c0 = 0; c0 < C; c0 += 16) {
@@ -853,8 +912,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) 
       tmem_ld16(tD + buf * C + c0 + ((uint32_t)(warp * 32) << 16), val);
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
-        float x = val[i] + a.bias[c0 + i];
-        h[c0 + i] = a.activate ? gelu_f(x) : x;
+        float x = val[i] + bias[c0 + i];
+        h[c0 + i] = a.activate ? gelu16(x) : x;
       }
     }
     if (!a.project) {
@@ -894,7 +953,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) 
         float val[16];
         tmem_ld16(tE + c0 + ((uint32_t)(warp * 32) << 16), val);
 #pragma unroll
-        for (int i = 0; i < 16; ++i) zt = fmaf(a.p2[c0 + i], gelu_f(val[i] + a.p1[c0 + i]), zt);
+        for (int i = 0; i < 16; ++i) zt = fmaf(a.p2[c0 + i], gelu16(val[i] + a.p1[c0 + i]), zt);
       }
       if (valid) a.z[((size_t)b * N + q) * N + p] = a.rms[b] * a.hh * (double)zt;
     }
@@ -909,14 +968,16 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) 
 
 // ------------------------------------ host ---------------------------------------------
 static size_t analysis_smem(const TcGeom& g) {
-  return (size_t)2 * 32 * g.QC * 2 + (size_t)2 * 128 * g.QC * 2 + (size_t)g.MP * 2 * g.PC * 2 +
+  const int ne2 = (g.N / g.QC > 1) ? 3 : 1;
+  return (size_t)ne2 * 32 * g.QC * 2 + (size_t)3 * 128 * g.QC * 2 + (size_t)g.MP * 2 * g.PC * 2 +
          (size_t)g.NPM * 2 * g.PC * 2;
 }
 static size_t mix_smem(int C) { return (size_t)128 * 2 * C * 2 + (size_t)4 * C * C * 2; }
 static size_t synthesis_smem(const TcGeom& g) {
   const int C = g.C;
-  const size_t r0 = std::max((size_t)g.MP * g.KXP * 2, (size_t)3 * 128 * C * 2);
-  return r0 + (size_t)2 * g.SPC * g.KXP * 2 + (size_t)C * g.KB * 2 + (size_t)128 * g.KSYN * 2 + (size_t)2 * C * C * 2;
+  const size_t TB = (size_t)128 * C * 2, SB = (size_t)128 * g.KSYN * 2;
+  const size_t r0 = std::max((size_t)g.MP * g.KXP * 2, 4 * TB + (g.N >= 128 ? 3 * SB : 0));
+  return r0 + (size_t)2 * g.SPC * g.KXP * 2 + (size_t)C * g.KB * 2 + (g.N < 128 ? SB : 0) + (size_t)2 * C * C * 2;
 }
 
 template <int C>
