@@ -13,6 +13,11 @@
 //     the last layer also runs the decoder C -> C_p (second MMA), GELU, -> 1, times h^2 rms(r).
 // Tables: E2 = (cos, -sin)(2 pi k2 q / N); G = analysis twiddles over p with the 1/n factor;
 // H = synthesis twiddles over p; Asyn = w_k2 (cos, -sin)(2 pi k2 q / N), w_0 = 1, w_{k2>0} = 2.
+// The synthesis kernel's operands that do not depend on the grid point (H per column chunk,
+// Asyn, W, the decoder weights and each instance's mixed coefficients) are stored as byte
+// images of their shared-memory layouts, so that one bulk copy (TMA engine) stages each of
+// them; the activations are stored tile-major (below), so that an activation tile is one
+// contiguous bulk copy in and one out.
 // Real and imaginary parts are interleaved along the contracted dimension, so every complex
 // product is a real GEMM.
 #include "internal.cuh"
@@ -47,13 +52,20 @@ __device__ __forceinline__ uint32_t pack2(float a, float b, bool bf16) {
 __host__ __device__ constexpr int round_up(int x, int m) { return (x + m - 1) / m * m; }
 
 // GELU of the 16-bit path in the tanh form of Hendrycks & Gimpel (2016),
-// 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))), evaluated as x * sigmoid(2 sqrt(2/pi) (...))
-// so that nothing cancels for negative x. It departs from the erf form by at most 4.7e-4
-// (absolute), below the 16-bit rounding of the values it produces, and costs a few
-// instructions instead of a branchy erf.
+// 0.5 x (1 + tanh(sqrt(2/pi) (x + 0.044715 x^3))), with tanh from the hardware approximation
+// (tanh.approx.f32, relative error about 2^-11): one special-function operation per value,
+// so that the epilogue is not bound by the special-function unit. The tanh form departs from
+// the erf form by at most 4.7e-4 and the approximate tanh adds at most 2.5e-4 |x| (absolute);
+// both stay at or below the 16-bit rounding of the values produced.
+__device__ __forceinline__ float tanh_approx(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
 __device__ __forceinline__ float gelu16(float x) {
-  const float u = 1.5957691216057308f * fmaf(0.044715f * x, x * x, x);
-  return __fdividef(x, 1.0f + __expf(-u));
+  const float u = x * fmaf(0.035677408136300125f, x * x, 0.7978845608028654f);  // sqrt(2/pi) (x + 0.044715 x^3)
+  const float hx = 0.5f * x;
+  return fmaf(hx, tanh_approx(u), hx);
 }
 
 // Geometry shared by host and device.
@@ -111,16 +123,18 @@ static bool geom_supported(int N, int C, int M, int Cp) {
   if (!(C == 16 || C == 32) || Cp != C || M < 1 || M > 16 || N < 2 * M) return false;
   if (!(N == 32 || N == 64 || (N >= 128 && N % 128 == 0))) return false;
   if ((std::min(N, 32) * C) % 128 != 0) return false;
+  // the synthesis block's two warp groups each read back whole 16-column TMEM groups of U
+  if (make_geom(N, C, M).SPC % 16 != 0) return false;
   return true;
 }
 
 // ------------------------------------ tables -------------------------------------------
 struct TcTables {
   int N = 0, M = 0;
-  uint16_t* E2 = nullptr;    // [32][N]
-  uint16_t* G = nullptr;     // [NPM][2N]
-  uint16_t* H = nullptr;     // [2N][KXP]
-  uint16_t* Asyn = nullptr;  // [rows][KSYN], rows = 128 (N < 128) or N
+  uint16_t* E2 = nullptr;    // [N / QC] images 32 x QC (K-major)
+  uint16_t* G = nullptr;     // [N / PC] images NPM x 2PC (K-major)
+  uint16_t* H = nullptr;     // [N / SPC] images 2SPC x KXP (K-major)
+  uint16_t* Asyn = nullptr;  // images 128 x KSYN (K-major): one (N < 128) or N / 128
 };
 
 __device__ __forceinline__ void cs_of(long long k, long long x, int N, float& c, float& s) {
@@ -135,7 +149,7 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
   const int N = g.N, M = g.M, Ky = g.Ky;
   const float inv_n = 1.0f / ((float)N * (float)N);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  // E2 [32][N]
+  // E2: rows (k2, t) x q, one image per analysis q chunk
   if (tid < 32 * N) {
     const int row = tid / N, q = tid % N, k2 = row >> 1, t = row & 1;
     float v = 0.f;
@@ -144,9 +158,9 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
       cs_of(k2, q, N, c, s);
       v = t ? -s : c;
     }
-    E2[tid] = f2h16(v, bf16);
+    E2[(size_t)(q / g.QC) * 32 * g.QC + kmajor_off(row, q % g.QC, 128, g.QC * 16) / 2] = f2h16(v, bf16);
   }
-  // G [NPM][2N]
+  // G: rows (j, t') x (p, t), one image per analysis column chunk
   if (tid < g.NPM * 2 * N) {
     const int row = tid / (2 * N), k = tid % (2 * N);
     const int j = row >> 1, tp = row & 1, p = k >> 1, t = k & 1;
@@ -159,11 +173,13 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
       else v = t == 0 ? -s : c;
       v *= inv_n;
     }
-    G[tid] = f2h16(v, bf16);
+    G[(size_t)(k / (2 * g.PC)) * g.NPM * 2 * g.PC + kmajor_off(row, k % (2 * g.PC), 128, 2 * g.PC * 16) / 2] =
+        f2h16(v, bf16);
   }
-  // H [2N][KXP]
+  // H: rows (p, t') of one synthesis column chunk per image
   if (tid < 2 * N * g.KXP) {
     const int row = tid / g.KXP, k = tid % g.KXP;
+    const int hc = row / (2 * g.SPC), hr = row % (2 * g.SPC);
     const int p = row >> 1, tp = row & 1, j = k >> 1, t = k & 1;
     float v = 0.f;
     if (k < g.Kx4) {
@@ -173,7 +189,7 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
       if (tp == 0) v = t == 0 ? c : -s;
       else v = t == 0 ? s : c;
     }
-    H[tid] = f2h16(v, bf16);
+    H[(size_t)hc * 2 * g.SPC * g.KXP + kmajor_off(hr, k, 128, g.KXP * 16) / 2] = f2h16(v, bf16);
   }
   // Asyn
   const int arows = N < 128 ? 128 : N;
@@ -195,16 +211,17 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
       const float w = k2 == 0 ? 1.f : 2.f;
       v = w * (t == 0 ? c : -s);
     }
-    Asyn[tid] = f2h16(v, bf16);
+    const int img = N < 128 ? 0 : m / 128, ir = N < 128 ? m : m % 128;
+    Asyn[(size_t)img * 128 * g.KSYN + kmajor_off(ir, k, 128, g.KSYN * 16) / 2] = f2h16(v, bf16);
   }
 }
 
 // ------------------------------------ model copies -------------------------------------
 struct TcPrecision {
   bool built = false;
-  std::vector<uint16_t*> W;   // [L] C x C
+  std::vector<uint16_t*> W;   // [L] C x C image (K-major)
   std::vector<uint16_t*> Rr;  // [L] nmodes x 2C x 2C
-  uint16_t* P1 = nullptr;     // Cp x C
+  uint16_t* P1 = nullptr;     // Cp x C image (K-major)
   std::map<int, TcTables> tables;
 };
 
@@ -222,9 +239,13 @@ struct fcgno::TcModel {
 
 namespace fcgno {
 
-__global__ void tc_cast_kernel(size_t n, const float* __restrict__ in, uint16_t* __restrict__ out, bool bf16) {
-  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (i < n) out[i] = f2h16(in[i], bf16);
+// rows x cols row-major FP32 -> 16-bit image of the K-major shared-memory layout (K = cols)
+__global__ void tc_cast_image_kernel(int rows, int cols, const float* __restrict__ in, uint16_t* __restrict__ out,
+                                     bool bf16) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= rows * cols) return;
+  const int r = i / cols, k = i % cols;
+  out[kmajor_off(r, k, 128, cols * 16) / 2] = f2h16(in[i], bf16);
 }
 
 // Rr[mode][(o,t')][(i,t)] from R[mode][i][o][re/im]
@@ -301,14 +322,14 @@ static fcgno_status ensure_prec(fcgno_model* m, bool fp16, cudaStream_t st) {
   for (int l = 0; l < d.layers; ++l) {
     FCGNO_CUDA_TRY(cudaMalloc(&P.W[l], sizeof(uint16_t) * C * C));
     FCGNO_CUDA_TRY(cudaMalloc(&P.Rr[l], sizeof(uint16_t) * (size_t)nmodes * 4 * C * C));
-    tc_cast_kernel<<<ceil_div(C * C, 256), 256, 0, st>>>(C * C, m->w32 + BL.w[l], P.W[l], bf16);
+    tc_cast_image_kernel<<<ceil_div(C * C, 256), 256, 0, st>>>(C, C, m->w32 + BL.w[l], P.W[l], bf16);
     FCGNO_LAUNCHED();
     const size_t tot = (size_t)nmodes * 4 * C * C;
     tc_rr_kernel<<<ceil_div(tot, 256), 256, 0, st>>>(C, nmodes, m->w32 + BL.r[l], P.Rr[l], bf16);
     FCGNO_LAUNCHED();
   }
   FCGNO_CUDA_TRY(cudaMalloc(&P.P1, sizeof(uint16_t) * Cp * C));
-  tc_cast_kernel<<<ceil_div(Cp * C, 256), 256, 0, st>>>(Cp * C, m->w32 + BL.proj1_w, P.P1, bf16);
+  tc_cast_image_kernel<<<ceil_div(Cp * C, 256), 256, 0, st>>>(Cp, C, m->w32 + BL.proj1_w, P.P1, bf16);
   FCGNO_LAUNCHED();
   P.built = true;
   m->gen++;
@@ -342,10 +363,29 @@ static fcgno_status ensure_tables(fcgno_model* m, bool fp16, const TcGeom& g, Tc
 // ------------------------------------ kernels ------------------------------------------
 __device__ __forceinline__ bool tc_inactive(const int* active, int b) { return active && active[b] >= 0; }
 
-// Encoder: v0 = lift_w [r/rms, log k] + lift_b, written as 16-bit channels-last. One thread
-// per grid point; the only FP64 work is reading r (1/rms is formed once per thread in FP32).
+// Tile-major activation layout (16-bit). An instance's N x N x C activations are N^2/128
+// tiles of 128 grid points, stored one after another; each tile is the byte image of a
+// K-major tensor-core operand (rows = grid points, K = channels; LBO 2048, SBO 128):
+//   N < 128 : tile tau holds the PT = 128/N grid columns tau*PT .. tau*PT + PT - 1, all rows;
+//   N >= 128: tile tau holds column tau % N, rows 128 (tau / N) .. + 127.
+// Row m of a tile = (column within the tile) * QT + (row within the tile); element (m, c) is
+// at byte (c / 8) * 2048 + m * 16 + (c % 8) * 2. The same bytes, read with the 8-channel
+// groups as the M direction, are the MN-major operand of the analysis stage Q (K = rows q).
+__host__ __device__ __forceinline__ void act_tile_of(const TcGeom& g, int q, int p, int& tile, int& m) {
+  if (g.N < 128) {
+    tile = p / g.PT;
+    m = (p % g.PT) * g.N + q;
+  } else {
+    tile = (q / 128) * g.N + p;
+    m = q % 128;
+  }
+}
+
+// Encoder: v0 = lift_w [r/rms, log k] + lift_b, written tile-major. One thread per tile row
+// (consecutive threads write consecutive 16-byte rows of each channel group); the only FP64
+// work is reading r (1/rms is formed once per thread in FP32).
 template <int C>
-__global__ void tc_lift_kernel(size_t n, const double* __restrict__ r, const float* __restrict__ logk,
+__global__ void tc_lift_kernel(TcGeom g, const double* __restrict__ r, const float* __restrict__ logk,
                                const double* __restrict__ rms, const int* __restrict__ active,
                                const float* __restrict__ lw, const float* __restrict__ lb, uint16_t* __restrict__ v,
                                bool bf16) {
@@ -358,13 +398,25 @@ __global__ void tc_lift_kernel(size_t n, const double* __restrict__ r, const flo
     bb[c] = lb[c];
   }
   __syncthreads();
-  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  const int N = g.N;
+  const size_t n = (size_t)N * N;
+  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;  // tile-major row index
   if (x >= n) return;
+  const int tile = (int)(x / 128), m = (int)(x % 128);
+  int q, p;
+  if (N < 128) {
+    p = tile * g.PT + m / N;
+    q = m % N;
+  } else {
+    p = tile % N;
+    q = (tile / N) * 128 + m;
+  }
+  const size_t pt = (size_t)q * N + p;
   const float s = (float)rms[b];
   const float inv = s > 0.f ? 1.0f / s : 0.f;
-  const float rh = (float)r[(size_t)b * n + x] * inv;
-  const float lk = logk[(size_t)b * n + x];
-  uint4* dst = reinterpret_cast<uint4*>(v + ((size_t)b * n + x) * C);
+  const float rh = (float)r[(size_t)b * n + pt] * inv;
+  const float lk = logk[(size_t)b * n + pt];
+  uint8_t* dst = reinterpret_cast<uint8_t*>(v + ((size_t)b * n + (size_t)tile * 128) * C) + m * 16;
 #pragma unroll
   for (int c0 = 0; c0 < C; c0 += 8) {
     uint32_t w[4];
@@ -373,48 +425,52 @@ __global__ void tc_lift_kernel(size_t n, const double* __restrict__ r, const flo
       const int c = c0 + 2 * i;
       w[i] = pack2(fmaf(w0[c], rh, fmaf(w1[c], lk, bb[c])), fmaf(w0[c + 1], rh, fmaf(w1[c + 1], lk, bb[c + 1])), bf16);
     }
-    dst[c0 / 8] = make_uint4(w[0], w[1], w[2], w[3]);
+    *reinterpret_cast<uint4*>(dst + (c0 / 8) * 2048) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
 // Truncated analysis of one grid-column chunk of one instance; writes FP32 partial sums
 // part[b][chunk][mode = j*Ky + k2][c][re/im].
+//
+// Stage Q runs over steps s = (m-tile, q chunk); an m-tile is 128/C grid columns x C channels
+// (M) and a q chunk QC rows (K). Its operand is copied straight from the tile-major
+// activations: for N < 128 one bulk copy of (128/C)/PT consecutive tiles, for N >= 128 one
+// copy of QC rows per (column, 8-channel group). M groups of 8 channels are ordered
+// (tile u, channel group cg, column within the tile pl) and sit QC*16 bytes apart. Thread 0
+// issues copies and MMAs through a three-slot ring; the two Z accumulators alternate by
+// m-tile so that one m-tile is read back while the next one's MMAs run.
 template <int C>
 __global__ void __launch_bounds__(kTcThreads, 2)
     tc_analysis_kernel(TcGeom g, bool bf16, const int* __restrict__ active, const uint16_t* __restrict__ v,
                        const uint16_t* __restrict__ E2, const uint16_t* __restrict__ G, float* __restrict__ part,
                        int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t mbar, mbar2[3];
+  constexpr int NS = 3;
+  __shared__ uint64_t full[NS], mmaq[NS], prob, mbarP;
   __shared__ uint32_t tbase_s;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(active, b)) return;
-  const int N = g.N, PC = g.PC, QC = g.QC, Ky = g.Ky;
+  const int N = g.N, PC = g.PC, QC = g.QC, Ky = g.Ky, PT = g.PT;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // shared layout
-  const int ne2 = (N / QC > 1) ? 3 : 1;             // E2 changes per q chunk only when N > QC
-  uint8_t* sE2 = smem;                              // ne2 x (32 x QC), K-major: LBO 128, SBO QC*16
-  uint8_t* sA = sE2 + ne2 * 32 * QC * 2;            // 3 x (128 x QC), MN-major: SBO 128, LBO 2048
-  uint8_t* sAP = sA + 3 * 128 * QC * 2;             // MP x 2PC, K-major: LBO 128, SBO 2PC*16
-  uint8_t* sG = sAP + (size_t)g.MP * 2 * PC * 2;    // NPM x 2PC, K-major: LBO 128, SBO 2PC*16
-  const uint32_t SBO_E = QC * 16, SBO_P = 2 * PC * 16, SBO_G = 2 * PC * 16;
-  const uint32_t LBO_A = 2048;  // k-direction stride of the MN-major stage-Q operand (16 m-core matrices)
-
+  const int qchunks = N / QC;
+  const int ne2 = qchunks > 1 ? NS : 1;  // E2 changes per q chunk only when N > QC
+  const uint32_t E2B = 32 * QC * 2, AB = 128 * QC * 2, GB = g.NPM * 2 * PC * 2;
+  uint8_t* sE2 = smem;                            // ne2 x (32 x QC), K-major: LBO 128, SBO QC*16
+  uint8_t* sA = sE2 + ne2 * E2B;                  // NS x (128 x QC), MN-major: LBO 128, SBO QC*16
+  uint8_t* sAP = sA + NS * AB;                    // MP x 2PC, K-major: LBO 128, SBO 2PC*16
+  uint8_t* sG = sAP + (size_t)g.MP * 2 * PC * 2;  // NPM x 2PC, K-major: LBO 128, SBO 2PC*16
+  const uint32_t SBO_E = QC * 16, SBO_A = QC * 16, SBO_P = 2 * PC * 16, SBO_G = 2 * PC * 16;
   const uint32_t tcols = (64 + (g.MP / 128) * g.NPM) <= 256 ? 256u : 512u;
   if (warp == 0) tmem_alloc(&tbase_s, tcols);
   if (tid == 0) {
-    mbar_init(&mbar, 1);
-    mbar_init(&mbar2[0], 1);
-    mbar_init(&mbar2[1], 1);
-    mbar_init(&mbar2[2], 1);
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&mmaq[i], 1);
+    }
+    mbar_init(&prob, 1);
+    mbar_init(&mbarP, 1);
   }
-  // stage G slice (k = 2*p0 .. 2*p0 + 2PC) and zero the padding rows of sAP
-  const int p0 = chunk * PC;
-  for (int idx = tid; idx < g.NPM * (2 * PC / 8); idx += kTcThreads) {
-    const int row = idx / (2 * PC / 8), kc = idx % (2 * PC / 8);
-    const uint4 val = *reinterpret_cast<const uint4*>(G + (size_t)row * 2 * N + 2 * p0 + kc * 8);
-    *reinterpret_cast<uint4*>(sG + kmajor_off(row, kc * 8, 128, SBO_G)) = val;
-  }
+  // zero the padding rows of sAP
   for (int idx = tid; idx < (g.MP - Ky * C) * (2 * PC / 8); idx += kTcThreads) {
     const int row = Ky * C + idx / (2 * PC / 8), kc = idx % (2 * PC / 8);
     *reinterpret_cast<uint4*>(sAP + kmajor_off(row, kc * 8, 128, SBO_P)) = make_uint4(0, 0, 0, 0);
@@ -424,107 +480,111 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   fence_after_sync();
   const uint32_t tbase = tbase_s;
   const uint32_t tQ = tbase, tP = tbase + 64;  // two Z slots of 32 columns, then the c accumulators
-  uint32_t phase = 0;
-  bool ok = true;
+  const int p0 = chunk * PC;
+  const int cols_mt = 128 / C;  // grid columns per m-tile
+  const int mtiles = PC / cols_mt;
+  const int nsteps = mtiles * qchunks;
   const uint16_t* vb = v + (size_t)b * N * N * C;
-  const int mtiles = PC * C / 128;
-  const int qchunks = N / QC;
   constexpr uint32_t idQ = idesc_f16(128, 32, true, true, false);
   constexpr uint32_t idQh = idesc_f16(128, 32, false, true, false);
-  // Steps s = (m-tile, q-chunk) run through a three-slot pipeline: while the MMA of step s
-  // runs, the operands of steps s+1 and s+2 are in flight; the Z accumulator alternates
-  // between two TMEM slots by m-tile so that the read-back of one m-tile overlaps the MMAs
-  // of the next.
-  constexpr int NS = 3;
-  const int nsteps = mtiles * qchunks;
-  uint32_t phs[NS] = {0, 0, 0};
-  bool pending[NS] = {false, false, false};
-  auto stage = [&](int st_, int buf) {
-    const int mt = st_ / qchunks, qc = st_ % qchunks, q0 = qc * QC;
-    if (qchunks > 1 || st_ == 0) {
-      uint8_t* e2 = sE2 + (qchunks > 1 ? buf * 32 * QC * 2 : 0);
-      for (int idx = tid; idx < 32 * (QC / 8); idx += kTcThreads) {
-        const int row = idx / (QC / 8), kc = idx % (QC / 8);
-        cp_async16(e2 + kmajor_off(row, kc * 8, 128, SBO_E), E2 + (size_t)row * N + q0 + kc * 8);
+  // thread 0: copies of step s into ring slot buf
+  auto stage = [&](int s, int buf) {
+    const int mt = s / qchunks, qc = s % qchunks;
+    const int pm = p0 + mt * cols_mt;  // first grid column of the m-tile
+    mbar_expect_tx(&full[buf], AB + (qchunks > 1 ? E2B : 0));
+    if (qchunks > 1) bulk_g2s(sE2 + buf * E2B, E2 + (size_t)qc * 32 * QC, E2B, &full[buf]);
+    uint8_t* dst = sA + buf * AB;
+    if (N < 128) {
+      bulk_g2s(dst, vb + (size_t)(pm / PT) * 128 * C, AB, &full[buf]);
+    } else {
+      const int q0 = qc * QC, qt = q0 / 128, ql = q0 % 128;
+      for (int u = 0; u < cols_mt; ++u)
+        for (int cg = 0; cg < C / 8; ++cg)
+          bulk_g2s(dst + (u * (C / 8) + cg) * QC * 16, vb + (size_t)(qt * N + pm + u) * 128 * C + cg * 1024 + ql * 8,
+                   QC * 16, &full[buf]);
+    }
+  };
+  // all threads: read Z of the m-tile that ends at step s: lane M -> (column, channel),
+  // columns (k2, t) -> sAP[(k2, c)][(p, t)]
+  auto readback = [&](int s) -> bool {
+    const bool w = mbar_wait(&mmaq[s % NS], (s / NS) & 1);
+    fence_after_sync();
+    if (!w) return false;
+    const int mt = s / qchunks;
+    const uint32_t tq = tQ + (mt & 1) * 32;
+    const int M = warp * 32 + lane, Gi = M >> 3;
+    const int u = Gi / ((C / 8) * PT), cg = (Gi / PT) % (C / 8), pl2 = Gi % PT;
+    const int pl = mt * cols_mt + u * PT + pl2, c = cg * 8 + (M & 7);
+    float z[32];
+    float tmp[16];
+    tmem_ld16(tq + ((uint32_t)(warp * 32) << 16), tmp);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[i] = tmp[i];
+    tmem_ld16(tq + ((uint32_t)(warp * 32) << 16) + 16, tmp);
+#pragma unroll
+    for (int i = 0; i < 16; ++i) z[16 + i] = tmp[i];
+#pragma unroll
+    for (int k2 = 0; k2 < 16; ++k2) {  // Ky <= 16: static indices keep z in registers
+      if (k2 < Ky) {
+        const int row = k2 * C + c;
+        *reinterpret_cast<uint32_t*>(sAP + kmajor_off(row, 2 * pl, 128, SBO_P)) =
+            pack2(z[2 * k2], z[2 * k2 + 1], bf16);
       }
     }
-    // A tile: m = local (p, c) index 128*mt .. +128, k = q: 16-byte runs of 8 channels
-    uint8_t* sa = sA + buf * 128 * QC * 2;
-    for (int idx = tid; idx < QC * 16; idx += kTcThreads) {
-      const int ql = idx >> 4, mc = idx & 15;  // mc: 8-channel group within the 128 rows
-      const int m = mt * 128 + mc * 8;
-      const int pl = m / C, c0 = m % C;
-      cp_async16(sa + mnmajor_off(mc * 8, ql, LBO_A, 128), vb + ((size_t)(q0 + ql) * N + (p0 + pl)) * C + c0);
-    }
-    cp_async_commit();
+    return true;
   };
-  auto wait_slot = [&](int buf) -> bool {
-    if (!pending[buf]) return true;
-    const bool r = mbar_wait(&mbar2[buf], phs[buf]);
-    phs[buf] ^= 1;
-    pending[buf] = false;
-    fence_after_sync();
-    return r;
-  };
-  stage(0, 0);
-  if (nsteps > 1) stage(1, 1);
-  for (int st_ = 0; st_ < nsteps && ok; ++st_) {
-    const int buf = st_ % NS, mt = st_ / qchunks, qc = st_ % qchunks;
-    if (st_ + 1 < nsteps)
-      cp_async_wait_all_but_one();  // step st_'s copies done, step st_+1's may still fly
-    else
-      cp_async_wait_all();
-    fence_smem_to_async();
+  bool ok = true;
+  bool pro_pending = false;
+  int issued = 0, loads_waited = 0, mmas = 0;  // thread-0 bookkeeping (drained on the error path)
+  if (tid == 0) {
+    mbar_expect_tx(&prob, GB + (qchunks == 1 ? E2B : 0));
+    bulk_g2s(sG, G + (size_t)chunk * g.NPM * 2 * PC, GB, &prob);
+    if (qchunks == 1) bulk_g2s(sE2, E2, E2B, &prob);
+    for (; issued < nsteps && issued < 2; ++issued) stage(issued, issued);
+    ok = mbar_wait(&prob, 0);
+    pro_pending = !ok;
+  }
+  for (int s = 0; s < nsteps; ++s) {
+    const int buf = s % NS, mt = s / qchunks, qc = s % qchunks;
+    // the Z slot written by this step was read back (m-tile mt-2) before this barrier
     fence_before_sync();
-    __syncthreads();
+    ok = __syncthreads_and(ok);
     fence_after_sync();
-    const uint32_t tq = tQ + (mt & 1) * 32;
+    if (!ok) break;
     if (tid == 0) {
-      const uint32_t sa = smem_addr(sA + buf * 128 * QC * 2);
-      const uint32_t e2 = smem_addr(sE2 + (qchunks > 1 ? buf * 32 * QC * 2 : 0));
-      for (int ks = 0; ks < QC / 16; ++ks)
-        mma(tq, desc(sa + ks * 2 * LBO_A, LBO_A, 128), desc(e2 + ks * 2 * 128, 128, SBO_E), bf16 ? idQ : idQh,
-            qc > 0 || ks > 0);
-      commit(&mbar2[buf]);
-    }
-    pending[buf] = true;
-    if (st_ + 2 < nsteps) {
-      // the slot of step st_-1: its MMA must have finished before it is refilled
-      const int nb = (st_ + 2) % NS;
-      ok = wait_slot(nb);
-      if (!ok) break;
-      stage(st_ + 2, nb);
-    }
-    if (qc == qchunks - 1) {
-      ok = wait_slot(buf);
-      if (!ok) break;
-      // read Z for this m-tile: lane = (p, c), columns (k2, t) -> sAP[(k2, c)][(p, t)]
-      const int m = mt * 128 + warp * 32 + lane;
-      const int pl = m / C, c = m % C;
-      float z[32];
-      float tmp[16];
-      tmem_ld16(tq + ((uint32_t)(warp * 32) << 16), tmp);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) z[i] = tmp[i];
-      tmem_ld16(tq + ((uint32_t)(warp * 32) << 16) + 16, tmp);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) z[16 + i] = tmp[i];
-#pragma unroll
-      for (int k2 = 0; k2 < 16; ++k2) {  // Ky <= 16: static indices keep z in registers
-        if (k2 < Ky) {
-          const int row = k2 * C + c;
-          *reinterpret_cast<uint32_t*>(sAP + kmajor_off(row, 2 * pl, 128, SBO_P)) =
-              pack2(z[2 * k2], z[2 * k2 + 1], bf16);
+      ok = mbar_wait(&full[buf], (s / NS) & 1);
+      if (ok) {
+        loads_waited = s + 1;
+        const uint32_t tq = tQ + (mt & 1) * 32;
+        const uint32_t sa = smem_addr(sA + buf * AB);
+        const uint32_t e2 = smem_addr(sE2 + (qchunks > 1 ? buf * E2B : 0));
+        for (int ks = 0; ks < QC / 16; ++ks)
+          mma(tq, desc(sa + ks * 256, 128, SBO_A), desc(e2 + ks * 256, 128, SBO_E), bf16 ? idQ : idQh, qc > 0 || ks > 0);
+        commit(&mmaq[buf]);
+        mmas = s + 1;
+      }
+      if (ok && issued < nsteps) {
+        const int nb = issued % NS;  // slot of step s-1, whose MMA must have read it
+        if (s >= 1) ok = mbar_wait(&mmaq[nb], ((s - 1) / NS) & 1);
+        if (ok) {
+          stage(issued, nb);
+          ++issued;
         }
       }
     }
+    // the previous m-tile is read back while this step's MMA runs
+    if (s >= 1 && (s - 1) % qchunks == qchunks - 1) ok = readback(s - 1) && ok;
   }
-  cp_async_wait_all();
+  fence_before_sync();
+  ok = __syncthreads_and(ok);
+  fence_after_sync();
+  if (ok && nsteps > 0) ok = readback(nsteps - 1);
+  fence_smem_to_async();
+  fence_before_sync();
+  ok = __syncthreads_and(ok);
+  fence_after_sync();
+  bool p_pending = false;
   if (ok) {
-    fence_smem_to_async();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
     const int ptiles = g.MP / 128;
     if (tid == 0) {
       const uint32_t id = idesc_f16(128, g.NPM, bf16, false, false);
@@ -534,10 +594,10 @@ __global__ void __launch_bounds__(kTcThreads, 2)
           const uint64_t bd = desc(smem_addr(sG) + ks * 2 * 128, 128, SBO_G);
           mma(tP + pt * g.NPM, ad, bd, id, ks > 0);
         }
-      commit(&mbar);
+      commit(&mbarP);
     }
-    ok = mbar_wait(&mbar, phase);
-    phase ^= 1;
+    ok = mbar_wait(&mbarP, 0);
+    p_pending = !ok;
     fence_after_sync();
     if (ok) {
       float* pb = part + ((size_t)b * g.nchunks + chunk) * g.nmodes * C * 2;
@@ -561,17 +621,26 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       }
     }
   }
-  if (!ok && tid == 0) atomicExch(err, 1);
+  if (!ok && tid == 0) {
+    // error path: let every copy and MMA this block started finish (bounded) before the
+    // block releases its shared and tensor memory
+    if (pro_pending) mbar_wait(&prob, 0);
+    for (int u = loads_waited; u < issued; ++u) mbar_wait(&full[u % NS], (u / NS) & 1);
+    for (int u = mmas > NS ? mmas - NS : 0; u < mmas; ++u) mbar_wait(&mmaq[u % NS], (u / NS) & 1);
+    if (p_pending) mbar_wait(&mbarP, 0);
+    atomicExch(err, 1);
+  }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, tcols);
 }
 
 // Per-mode complex channel mixing across instances: rows = instances (128 per CTA).
-// Output c'[b][(j, re/im)][(k2, c)] (16-bit): the MN-major layout of the synthesis stage-1
-// A operand, so that each instance's C outputs of one (mode, re/im) are one 2C-byte run.
+// Output: for each instance the byte image (MP x KXP, 16-bit, zero padded) of the synthesis
+// stage-1 A operand in its MN-major shared-memory layout, element (m = (k2, c), k = (j, re/im));
+// each instance's 8 consecutive outputs c of one (mode, re/im) form one 16-byte run.
 template <int C>
-__global__ void __launch_bounds__(kTcThreads)
+__global__ void __launch_bounds__(kTcThreads, 4)
     tc_mix_kernel(TcGeom g, int B, bool bf16, const int* __restrict__ active, const float* __restrict__ part,
                   const uint16_t* __restrict__ Rr, uint16_t* __restrict__ chat, int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
@@ -643,17 +712,21 @@ __global__ void __launch_bounds__(kTcThreads)
       for (int i = 0; i < 16; ++i) val[c0 + i] = t16[i];
     }
     if (b < B) {
-      // columns are (o, re/im) interleaved; write the C real parts, then the C imaginary parts
+      // columns are (o, re/im) interleaved; write the C real parts, then the C imaginary parts,
+      // each run of 8 outputs o at its place in the instance's stage-1 operand image
+      const uint32_t LBO_A1 = (g.MP / 8) * 128;
+      uint8_t* img = reinterpret_cast<uint8_t*>(chat + (size_t)b * g.MP * g.KXP);
 #pragma unroll
       for (int t = 0; t < 2; ++t) {
-        uint4* dst = reinterpret_cast<uint4*>(chat + (((size_t)b * g.Kx4 + 2 * j + t) * g.Ky + k2) * C);
+        // run o0 of (k2, k = 2j + t) starts at mnmajor_off(k2 C + o0, k) = base + (o0 / 8) 128
+        const uint32_t base = mnmajor_off(k2 * C, 2 * j + t, LBO_A1, 128);
+        uint4* dst = reinterpret_cast<uint4*>(img + base);
 #pragma unroll
-        for (int o0 = 0; o0 < C; o0 += 8) {
-          dst[o0 / 8] = make_uint4(pack2(val[2 * o0 + t], val[2 * o0 + 2 + t], bf16),
-                                   pack2(val[2 * o0 + 4 + t], val[2 * o0 + 6 + t], bf16),
-                                   pack2(val[2 * o0 + 8 + t], val[2 * o0 + 10 + t], bf16),
-                                   pack2(val[2 * o0 + 12 + t], val[2 * o0 + 14 + t], bf16));
-        }
+        for (int o0 = 0; o0 < C; o0 += 8)
+          dst[o0] = make_uint4(pack2(val[2 * o0 + t], val[2 * o0 + 2 + t], bf16),
+                               pack2(val[2 * o0 + 4 + t], val[2 * o0 + 6 + t], bf16),
+                               pack2(val[2 * o0 + 8 + t], val[2 * o0 + 10 + t], bf16),
+                               pack2(val[2 * o0 + 12 + t], val[2 * o0 + 14 + t], bf16));
       }
     }
   } else if (tid == 0) {
@@ -667,19 +740,20 @@ __global__ void __launch_bounds__(kTcThreads)
 struct SynArgs {
   TcGeom g;
   int B;
-  bool bf16;
+  int bf16;
+  int nslots;             // depth of the tile ring (4 .. kSynMaxSlots)
   const int* active;
-  const uint16_t* chat;   // [B][Kx4][Ky][C]  (MN-major stage-1 operand)
-  const uint16_t* vin;    // [B][N][N][C]
-  const uint16_t* W;      // [C][C]
+  const uint16_t* vin;    // layer input, tile-major
+  uint16_t* vout;         // layer output, tile-major
+  const uint16_t* chat;   // [B] images MP x KXP of the stage-1 operand (MN-major)
+  const uint16_t* W;      // C x C image (K-major)
   const float* bias;      // [C]
-  const uint16_t* H;      // [2N][KXP]
-  const uint16_t* Asyn;   // [rows][KSYN]
+  const uint16_t* H;      // [N / SPC] images 2SPC x KXP (K-major)
+  const uint16_t* Asyn;   // images 128 x KSYN (K-major): one (N < 128) or one per 128-row q tile
   int activate;
-  uint16_t* vout;         // [B][N][N][C] (hidden layers)
   // decoder (last layer)
   int project;
-  const uint16_t* P1;     // [C][C]
+  const uint16_t* P1;     // C x C image (K-major)
   const float* p1;
   const float* p2;
   const float* p2b;
@@ -690,79 +764,69 @@ struct SynArgs {
 };
 
 // Synthesis + pointwise + bias + activation (+ decoder) for one grid-column chunk of one instance.
+// 256 threads: warps w and w+4 read the same 32 TMEM lanes (quadrant w % 4); the two warp
+// groups split the columns (U read-back) and the channels (epilogue) between them. Thread 0
+// also issues every copy and MMA.
+//
+// Data movement: the chunk-invariant operands arrive by one bulk copy each; the activation
+// tiles (128 grid points x C channels, tile-major, so each is one contiguous block already in
+// the K-major operand layout) stream through a ring of shared-memory slots filled by one bulk
+// copy each and, once the epilogue has overwritten a slot with the layer output, drained by
+// one bulk store from the same slot. For N >= 128 the chunk's tiles are visited row block by
+// row block (tile t: q tile t / SPC, column t % SPC).
+constexpr int kSynThreads = 256;
+constexpr int kSynMaxSlots = 6;
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) {
+__global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t mbar[4];
+  __shared__ uint64_t full[kSynMaxSlots], mmab[2], prob, s1b, decb;
   __shared__ uint32_t tbase_s;
+  __shared__ float zpart[2][128];
   const TcGeom& g = a.g;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(a.active, b)) return;
-  const int N = g.N, PC = g.SPC, Ky = g.Ky;
+  const int N = g.N, PC = g.SPC, Ky = g.Ky, D = a.nslots;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant, channel/column half
+  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   const bool bf16 = a.bf16;
   const int p0 = chunk * PC;
   // shared layout
   const uint32_t LBO_A1 = (g.MP / 8) * 128;  // MN-major: K-direction core-matrix stride
-  const uint32_t SBO_H = g.KXP * 16, SBO_B = g.KB * 16, SBO_S = g.KSYN * 16, SBO_C = C * 16;
+  const uint32_t SBO_B = g.KB * 16, SBO_S = g.KSYN * 16, SBO_C = C * 16;
+  constexpr uint32_t TB = 128 * C * 2, LBO_T = 128 * 16;
+  const uint32_t SB = 128 * g.KSYN * 2;
+  const uint32_t SL = TB + (N >= 128 ? SB : 0);  // ring slot: tile, then (N >= 128) its table rows
+  const uint32_t bytesA1 = g.MP * g.KXP * 2, bytesH = 2 * PC * g.KXP * 2;
   // region R0 holds the mixed coefficients for synthesis stage 1, then (aliased, once stage 1
-  // has completed) a ring of three pointwise input tiles, the decoder input tile and, for
-  // N >= 128, the per-tile rows of the synthesis table
-  const size_t TB = (size_t)128 * C * 2, SB = (size_t)128 * g.KSYN * 2;
-  const size_t r0a = (size_t)g.MP * g.KXP * 2, r0b = 4 * TB + (N >= 128 ? 3 * SB : 0);
-  const size_t r0 = r0a > r0b ? r0a : r0b;
-  uint8_t* sA1 = smem;                                  // MP x KXP
-  uint8_t* sX0 = smem;                                  // 3 x (128 x C) pointwise tiles (after stage 1)
-  uint8_t* sD = smem + 3 * TB;                          // 128 x C decoder input (after stage 1)
-  uint8_t* sSb = smem + 4 * TB;                         // 3 x (128 x KSYN) table rows (N >= 128)
-  uint8_t* sH = smem + r0;                              // 2PC x KXP
-  uint8_t* sB = sH + (size_t)2 * PC * g.KXP * 2;        // C x KB
-  uint8_t* sS = sB + (size_t)C * g.KB * 2;              // 128 x KSYN (N < 128: one table for all tiles)
-  uint8_t* sW = sS + (N < 128 ? SB : 0);                // C x C
-  uint8_t* sP = sW + C * C * 2;                         // C x C (decoder)
-  const uint32_t TCOLS = 256;
+  // has completed) the tile ring and the decoder input tile
+  const uint32_t ring_bytes = D * SL + TB;
+  const uint32_t r0 = bytesA1 > ring_bytes ? bytesA1 : ring_bytes;
+  uint8_t* sA1 = smem;                     // MP x KXP
+  uint8_t* ring = smem;                    // D slots of SL bytes (after stage 1)
+  uint8_t* sD = smem + D * SL;             // 128 x C decoder input (after stage 1)
+  uint8_t* sH = smem + r0;                 // 2PC x KXP
+  uint8_t* sB = sH + bytesH;               // C x KB
+  uint8_t* sS = sB + C * g.KB * 2;         // 128 x KSYN (N < 128: one table for all tiles)
+  uint8_t* sW = sS + (N < 128 ? SB : 0);   // C x C
+  uint8_t* sP = sW + C * C * 2;            // C x C (decoder)
+  constexpr uint32_t TCOLS = 256;
   if (warp == 0) tmem_alloc(&tbase_s, TCOLS);
-  if (tid < 4) mbar_init(&mbar[tid], 1);
-  // ---- stage operands that do not change across tiles
-  // mixed coefficients, MN-major: element (m = (k2, c), k = (j, re/im)) is at
-  // chat[b][k][m]; 8 consecutive m at one k form one 16-byte run
-  const uint16_t* cb = a.chat + (size_t)b * g.Kx4 * Ky * C;
-  for (int idx = tid; idx < (g.MP / 8) * g.KXP; idx += kTcThreads) {
-    const int k = idx / (g.MP / 8), mc = idx % (g.MP / 8);
-    uint8_t* dst = sA1 + mnmajor_off(mc * 8, k, LBO_A1, 128);
-    if (mc * 8 < Ky * C && k < g.Kx4)
-      cp_async16(dst, cb + (size_t)k * Ky * C + mc * 8);
-    else
-      *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    for (int i = 0; i < D; ++i) mbar_init(&full[i], 1);
+    mbar_init(&mmab[0], 1);
+    mbar_init(&mmab[1], 1);
+    mbar_init(&prob, 1);
+    mbar_init(&s1b, 1);
+    mbar_init(&decb, 1);
   }
-  for (int idx = tid; idx < 2 * PC * (g.KXP / 8); idx += kTcThreads) {
-    const int row = idx / (g.KXP / 8), kc = idx % (g.KXP / 8);
-    cp_async16(sH + kmajor_off(row, kc * 8, 128, SBO_H), a.H + (size_t)(2 * p0 + row) * g.KXP + kc * 8);
-  }
-  for (int idx = tid; idx < C * (C / 8); idx += kTcThreads) {
-    const int row = idx / (C / 8), kc = idx % (C / 8);
-    *reinterpret_cast<uint4*>(sW + kmajor_off(row, kc * 8, 128, SBO_C)) =
-        *reinterpret_cast<const uint4*>(a.W + row * C + kc * 8);
-    if (a.project)
-      *reinterpret_cast<uint4*>(sP + kmajor_off(row, kc * 8, 128, SBO_C)) =
-          *reinterpret_cast<const uint4*>(a.P1 + row * C + kc * 8);
-  }
-  if (N < 128) {
-    for (int idx = tid; idx < 128 * (g.KSYN / 8); idx += kTcThreads) {
-      const int row = idx / (g.KSYN / 8), kc = idx % (g.KSYN / 8);
-      cp_async16(sS + kmajor_off(row, kc * 8, 128, SBO_S), a.Asyn + (size_t)row * g.KSYN + kc * 8);
-    }
-  }
-  cp_async_commit();
   // zero the K tail of the staged U columns (read by padded synthesis K steps)
   const int kvalid = PC * 2 * Ky;
-  for (int idx = tid; idx < C * ((g.KB - (kvalid & ~7)) / 8); idx += kTcThreads) {
+  for (int idx = tid; idx < C * ((g.KB - (kvalid & ~7)) / 8); idx += kSynThreads) {
     const int nk = (g.KB - (kvalid & ~7)) / 8;
     const int row = idx / nk, kc = (kvalid & ~7) / 8 + idx % nk;
     *reinterpret_cast<uint4*>(sB + kmajor_off(row, kc * 8, 128, SBO_B)) = make_uint4(0, 0, 0, 0);
   }
-  cp_async_wait_all();
-  fence_smem_to_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -770,29 +834,41 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) 
   const uint32_t tU = tbase;              // (MP/128) x 2PC columns (stage 1)
   const uint32_t tD = tbase;              // 2 x C tile accumulators (reuse U's columns after stage 1)
   const uint32_t tE = tbase + 2 * C;      // C decoder accumulator
-  uint32_t ph[4] = {0, 0, 0, 0};
   bool ok = true;
+  bool pro_pending = false;
   const int utiles = g.MP / 128;
-  // ---- synthesis stage 1: U = c' H^T for the chunk
+  // ---- chunk-invariant operands, then synthesis stage 1: U = c' H^T for the chunk
   if (tid == 0) {
-    const uint32_t id = idesc_f16(128, 2 * PC, bf16, true, false);
-    for (int ut = 0; ut < utiles; ++ut)
-      for (int ks = 0; ks < g.KXP / 16; ++ks)
-        mma(tU + ut * 2 * PC, desc(smem_addr(sA1) + ut * 16 * 128 + ks * 2 * LBO_A1, LBO_A1, 128),
-            desc(smem_addr(sH) + ks * 256, 128, SBO_H), id, ks > 0);
-    commit(&mbar[0]);
+    mbar_expect_tx(&prob, bytesA1 + bytesH + C * C * 2 * (a.project ? 2 : 1) + (N < 128 ? SB : 0));
+    bulk_g2s(sA1, a.chat + (size_t)b * g.MP * g.KXP, bytesA1, &prob);
+    bulk_g2s(sH, a.H + (size_t)chunk * 2 * PC * g.KXP, bytesH, &prob);
+    bulk_g2s(sW, a.W, C * C * 2, &prob);
+    if (a.project) bulk_g2s(sP, a.P1, C * C * 2, &prob);
+    if (N < 128) bulk_g2s(sS, a.Asyn, SB, &prob);
+    ok = mbar_wait(&prob, 0);
+    pro_pending = !ok;
+    if (ok) {
+      const uint32_t id = idesc_f16(128, 2 * PC, bf16, true, false);
+      for (int ut = 0; ut < utiles; ++ut)
+        for (int ks = 0; ks < g.KXP / 16; ++ks)
+          mma(tU + ut * 2 * PC, desc(smem_addr(sA1) + ut * 16 * 128 + ks * 2 * LBO_A1, LBO_A1, 128),
+              desc(smem_addr(sH) + ks * 256, 128, g.KXP * 16), id, ks > 0);
+      commit(&s1b);
+    }
   }
-  ok = mbar_wait(&mbar[0], ph[0]);
-  ph[0] ^= 1;
+  {
+    const bool w = mbar_wait(&s1b, 0);
+    ok = ok && w;
+  }
   fence_after_sync();
   if (ok) {
     // U lane (k2, c), columns (p, t') -> sB[c][(p, k2, t')]
     for (int ut = 0; ut < utiles; ++ut) {
-      const int row = ut * 128 + warp * 32 + lane;
+      const int row = ut * 128 + quad * 32 + lane;
       const int k2 = row / C, c = row % C;
-      for (int c0 = 0; c0 < 2 * PC; c0 += 16) {
+      for (int c0 = half * PC; c0 < (half + 1) * PC; c0 += 16) {
         float val[16];
-        tmem_ld16(tU + ut * 2 * PC + c0 + ((uint32_t)(warp * 32) << 16), val);
+        tmem_ld16(tU + ut * 2 * PC + c0 + lane_off, val);
         if (row < Ky * C) {
 #pragma unroll
           for (int i = 0; i < 16; i += 2) {
@@ -806,161 +882,183 @@ __global__ void __launch_bounds__(kTcThreads, 2) tc_synthesis_kernel(SynArgs a) 
   }
   fence_smem_to_async();
   fence_before_sync();
-  __syncthreads();
+  ok = __syncthreads_and(ok);
   fence_after_sync();
   // ---- tiles of 128 grid points
   const int ntiles = (N < 128) ? PC / g.PT : PC * (N / 128);
-  const uint16_t* vb = a.vin + (size_t)b * N * N * C;
-  // Thread tid owns tile row m = tid of every tile: its grid point within the tile is fixed,
-  // so the row's (q, column offset) and shared-memory offsets are computed once.
-  const int m_own = tid;
+  const int PF = D - 2;  // tiles loaded ahead; a slot is refilled two tiles after its store
+  // Thread tid owns tile row m = tid % 128 of every tile: its grid point within the tile is
+  // fixed, so the row's (q, column offset) are computed once.
+  const int m_own = tid & 127;
   const int own_pl = (N < 128) ? m_own / N : 0;     // column within the tile (N < 128)
   const int own_q = (N < 128) ? m_own % N : m_own;  // row (N < 128) or row within the q-tile
-  const bool own_valid = (N < 128) ? own_pl < g.PT : true;
-  const uint32_t own_xoff = kmajor_off(m_own, 0, 128, SBO_C);
   auto tile_point = [&](int t, int& q, int& p) {
     if (N < 128) {
       q = own_q;
       p = p0 + t * g.PT + own_pl;
     } else {
-      const int col = t / (N / 128), qt = t % (N / 128);
-      p = p0 + col;
-      q = qt * 128 + own_q;
+      p = p0 + t % PC;
+      q = (t / PC) * 128 + own_q;
     }
   };
-  auto prefetch = [&](int t, int buf) {
-    uint8_t* dst = sX0 + buf * TB + own_xoff;
-    int q, p;
-    tile_point(t, q, p);
-    const uint16_t* src = vb + ((size_t)q * N + p) * C;
-#pragma unroll
-    for (int kc = 0; kc < C / 8; ++kc) {
-      if (own_valid)
-        cp_async16(dst + kc * 128, src + kc * 8);
-      else
-        *reinterpret_cast<uint4*>(dst + kc * 128) = make_uint4(0, 0, 0, 0);
-    }
-    if (N >= 128) {
-      // synthesis-table rows of this tile's q range, in the tile's ring slot
-      const int qt = t % (N / 128);
-      uint8_t* sdst = sSb + buf * SB;
-      for (int idx = tid; idx < 128 * (g.KSYN / 8); idx += kTcThreads) {
-        const int row = idx / (g.KSYN / 8), kc = idx % (g.KSYN / 8);
-        cp_async16(sdst + kmajor_off(row, kc * 8, 128, SBO_S), a.Asyn + (size_t)(qt * 128 + row) * g.KSYN + kc * 8);
-      }
-    }
-    cp_async_commit();
+  // tile-major index of tile t of this chunk
+  const size_t inst_tiles = (size_t)N * N / 128;
+  auto tile_index = [&](int t) -> size_t {
+    const size_t tau = (N < 128) ? (size_t)(p0 / g.PT + t) : (size_t)(t / PC) * N + p0 + t % PC;
+    return (size_t)b * inst_tiles + tau;
+  };
+  // thread 0: issue the copy of tile t (and, N >= 128, its table rows) into its ring slot
+  auto load_tile = [&](int t) {
+    const int s = t % D;
+    uint8_t* dst = ring + s * SL;
+    mbar_expect_tx(&full[s], SL);
+    bulk_g2s(dst, a.vin + tile_index(t) * 128 * C, TB, &full[s]);
+    if (N >= 128) bulk_g2s(dst + TB, a.Asyn + (size_t)(t / PC) * 128 * g.KSYN, SB, &full[s]);
+  };
+  // thread 0: issue the store of the layer output held in tile t's slot
+  auto store_tile = [&](int t) {
+    bulk_s2g(a.vout + tile_index(t) * 128 * C, ring + (t % D) * SL, TB);
+    bulk_commit();
   };
   const uint32_t idD = idesc_f16(128, C, bf16);
-  // tile t: ring slot t % 3, accumulator slot t % 2; issued by thread 0
+  // thread 0: tile t's MMAs into accumulator slot t % 2
   auto mma_tile = [&](int t) {
-    const int buf = t % 3, acc = t & 1;
-    const uint32_t sx = smem_addr(sX0 + buf * TB);
-    const uint32_t ss = (N < 128) ? smem_addr(sS) : smem_addr(sSb + buf * SB);
+    const int acc = t & 1;
+    const uint32_t sx = smem_addr(ring + (t % D) * SL);
+    const uint32_t ss = (N < 128) ? smem_addr(sS) : sx + TB;
     for (int ks = 0; ks < C / 16; ++ks)
-      mma(tD + acc * C, desc(sx + ks * 256, 128, SBO_C), desc(smem_addr(sW) + ks * 256, 128, SBO_C), idD, ks > 0);
-    const int kb0 = (N < 128) ? t * g.PT * 2 * Ky : (t / (N / 128)) * 2 * Ky;
+      mma(tD + acc * C, desc(sx + ks * 2 * LBO_T, LBO_T, 128), desc(smem_addr(sW) + ks * 256, 128, SBO_C), idD, ks > 0);
+    const int kb0 = (N < 128) ? t * g.PT * 2 * Ky : (t % PC) * 2 * Ky;
     for (int ks = 0; ks < g.KSYN / 16; ++ks)
       mma(tD + acc * C, desc(ss + ks * 256, 128, SBO_S), desc(smem_addr(sB) + (kb0 / 8) * 128 + ks * 256, 128, SBO_B),
           idD, true);
-    commit(&mbar[1 + acc]);
+    commit(&mmab[acc]);
   };
-  float bias[C];
+  constexpr int CH = C / 2;  // channels per thread in the epilogue
+  const int cbase = half * CH;
+  float bias[CH];
 #pragma unroll
-  for (int c = 0; c < C; ++c) bias[c] = a.bias[c];
+  for (int c = 0; c < CH; ++c) bias[c] = a.bias[cbase + c];
+  // thread-0 bookkeeping of copies and MMAs in flight (drained on the error path)
+  int loads = 0, loads_waited = 0, mmas = 0, mmas_waited = 0;
+  uint32_t dph = 0;
   // Software pipeline: while tile t's epilogue runs, tile t+1's MMA runs on the tensor core
-  // (other accumulator) and tile t+2's operands are being copied (third ring slot).
-  if (ok && ntiles > 0) {
-    prefetch(0, 0);
-    if (ntiles > 1) {
-      prefetch(1, 1);
-      cp_async_wait_all_but_one();
-    } else {
-      cp_async_wait_all();
+  // (other accumulator) and tiles up to t+PF are being loaded.
+  if (tid == 0 && ok && ntiles > 0) {
+    for (; loads < ntiles && loads < PF; ++loads) load_tile(loads);
+    ok = mbar_wait(&full[0], 0);
+    loads_waited = ok ? 1 : 0;
+    if (ok) {
+      mma_tile(0);
+      mmas = 1;
     }
-    fence_smem_to_async();
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    if (tid == 0) mma_tile(0);
   }
-  for (int t = 0; t < ntiles && ok; ++t) {
-    if (t + 1 < ntiles) {
-      cp_async_wait_all();  // tile t+1's copies (the only group in flight)
-      fence_smem_to_async();
-      fence_before_sync();
-      __syncthreads();
-      fence_after_sync();
-      if (tid == 0) mma_tile(t + 1);
-      // ring slot of tile t-1, whose MMA completed before its epilogue
-      if (t + 2 < ntiles) prefetch(t + 2, (t + 2) % 3);
+  for (int t = 0; t < ntiles; ++t) {
+    if (tid == 0 && ok) {
+      if (t + 1 < ntiles) {
+        ok = mbar_wait(&full[(t + 1) % D], ((t + 1) / D) & 1);
+        if (ok) {
+          loads_waited = t + 2;
+          mma_tile(t + 1);
+          mmas = t + 2;
+        }
+      }
+      if (ok && loads < ntiles) {
+        bulk_wait_read<1>();  // the store of the slot's previous tile (loads - D) has read it
+        load_tile(loads);
+        ++loads;
+      }
     }
-    const int buf = t & 1;
-    ok = mbar_wait(&mbar[1 + buf], ph[1 + buf]);
-    ph[1 + buf] ^= 1;
+    {
+      const bool w = mbar_wait(&mmab[t & 1], (t >> 1) & 1);
+      if (w) mmas_waited = t + 1;
+      ok = ok && w;
+    }
     fence_after_sync();
-    if (!ok) break;
-    // epilogue: lane = grid point, C columns
+    // epilogue: lane = grid point, this warp group's C/2 channels
     const int m = m_own;
     int q, p;
     tile_point(t, q, p);
-    const bool valid = own_valid;
-    float h[C];
+    float h[CH];
+    {
+      const uint32_t col = tD + (t & 1) * C + cbase + lane_off;
+      if constexpr (CH == 16) {
+        tmem_ld16(col, h);
+      } else {
+        tmem_ld8(col, h);
+      }
 #pragma unroll
-    for (int c0 = 0; c0 < C; c0 += 16) {
-      float val[16];
-      tmem_ld16(tD + buf * C + c0 + ((uint32_t)(warp * 32) << 16), val);
-#pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        float x = val[i] + bias[c0 + i];
-        h[c0 + i] = a.activate ? gelu16(x) : x;
+      for (int i = 0; i < CH; ++i) {
+        const float x = h[i] + bias[i];
+        h[i] = a.activate ? gelu16(x) : x;
       }
     }
     if (!a.project) {
-      if (valid) {
-        uint16_t* dst = a.vout + (((size_t)b * N + q) * N + p) * C;
+      // the layer output replaces the (consumed) input tile in its slot
+      uint8_t* dst = ring + (t % D) * SL + m * 16;
 #pragma unroll
-        for (int c0 = 0; c0 < C; c0 += 8) {
-          uint4 w = make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
-                               pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
-          *reinterpret_cast<uint4*>(dst + c0) = w;
-        }
+      for (int c0 = 0; c0 < CH; c0 += 8) {
+        *reinterpret_cast<uint4*>(dst + ((cbase + c0) / 8) * LBO_T) =
+            make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
+                       pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
       }
     } else {
       // decoder: second MMA on the 16-bit layer output
 #pragma unroll
-      for (int c0 = 0; c0 < C; c0 += 8) {
+      for (int c0 = 0; c0 < CH; c0 += 8) {
         uint4 w = make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
                              pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
-        *reinterpret_cast<uint4*>(sD + kmajor_off(m, c0, 128, SBO_C)) = w;
+        *reinterpret_cast<uint4*>(sD + kmajor_off(m, cbase + c0, 128, SBO_C)) = w;
       }
       fence_smem_to_async();
       fence_before_sync();
       __syncthreads();
       fence_after_sync();
-      if (tid == 0) {
+      if (tid == 0 && ok) {
         for (int ks = 0; ks < C / 16; ++ks)
           mma(tE, desc(smem_addr(sD) + ks * 256, 128, SBO_C), desc(smem_addr(sP) + ks * 256, 128, SBO_C), idD, ks > 0);
-        commit(&mbar[3]);
+        commit(&decb);
       }
-      ok = mbar_wait(&mbar[3], ph[3]);
-      ph[3] ^= 1;
+      {
+        const bool w = ok && mbar_wait(&decb, dph);
+        dph ^= 1;
+        ok = ok && w;
+      }
       fence_after_sync();
-      if (!ok) break;
-      float zt = a.p2b[0];
+      float zt = 0.f;
+      {
+        float val[CH];
+        if constexpr (CH == 16) {
+          tmem_ld16(tE + cbase + lane_off, val);
+        } else {
+          tmem_ld8(tE + cbase + lane_off, val);
+        }
 #pragma unroll
-      for (int c0 = 0; c0 < C; c0 += 16) {
-        float val[16];
-        tmem_ld16(tE + c0 + ((uint32_t)(warp * 32) << 16), val);
-#pragma unroll
-        for (int i = 0; i < 16; ++i) zt = fmaf(a.p2[c0 + i], gelu16(val[i] + a.p1[c0 + i]), zt);
+        for (int i = 0; i < CH; ++i) zt = fmaf(a.p2[cbase + i], gelu16(val[i] + a.p1[cbase + i]), zt);
       }
-      if (valid) a.z[((size_t)b * N + q) * N + p] = a.rms[b] * a.hh * (double)zt;
+      zpart[half][m] = zt;
+      __syncthreads();
+      if (ok && half == 0)
+        a.z[((size_t)b * N + q) * N + p] = a.rms[b] * a.hh * (double)(a.p2b[0] + zpart[0][m] + zpart[1][m]);
     }
+    fence_smem_to_async();
     fence_before_sync();
+    ok = __syncthreads_and(ok);
+    fence_after_sync();
+    if (!ok) break;
+    if (tid == 0 && !a.project) store_tile(t);
   }
-  cp_async_wait_all();
-  if (!ok && tid == 0) atomicExch(a.err, 1);
+  if (tid == 0) {
+    if (!ok) {
+      // error path: let every copy and MMA this block started finish (bounded) before the
+      // block releases its shared and tensor memory
+      if (pro_pending) mbar_wait(&prob, 0);
+      for (int u = loads_waited; u < loads; ++u) mbar_wait(&full[u % D], (u / D) & 1);
+      for (int u = mmas_waited; u < mmas; ++u) mbar_wait(&mmab[u & 1], (u >> 1) & 1);
+      atomicExch(a.err, 1);
+    }
+    bulk_wait_read<0>();
+  }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, TCOLS);
@@ -973,11 +1071,19 @@ static size_t analysis_smem(const TcGeom& g) {
          (size_t)g.NPM * 2 * g.PC * 2;
 }
 static size_t mix_smem(int C) { return (size_t)128 * 2 * C * 2 + (size_t)4 * C * C * 2; }
-static size_t synthesis_smem(const TcGeom& g) {
+static size_t synthesis_smem(const TcGeom& g, int D) {
   const int C = g.C;
-  const size_t TB = (size_t)128 * C * 2, SB = (size_t)128 * g.KSYN * 2;
-  const size_t r0 = std::max((size_t)g.MP * g.KXP * 2, 4 * TB + (g.N >= 128 ? 3 * SB : 0));
+  const size_t TB = (size_t)128 * C * 2, SB = (size_t)128 * g.KSYN * 2, SL = TB + (g.N >= 128 ? SB : 0);
+  const size_t r0 = std::max((size_t)g.MP * g.KXP * 2, D * SL + TB);
   return r0 + (size_t)2 * g.SPC * g.KXP * 2 + (size_t)C * g.KB * 2 + (g.N < 128 ? SB : 0) + (size_t)2 * C * C * 2;
+}
+// Deepest tile ring (4 .. kSynMaxSlots slots) that keeps two synthesis blocks per SM; 4 slots
+// (one block per SM) when even that does not fit.
+static int synthesis_slots(const TcGeom& g) {
+  constexpr size_t kTwoPerSm = 110 * 1024;  // dynamic bytes per block with two blocks per SM
+  for (int D = kSynMaxSlots; D > 4; --D)
+    if (synthesis_smem(g, D) <= kTwoPerSm) return D;
+  return 4;
 }
 
 template <int C>
@@ -993,7 +1099,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   const int B = op->B;
   const size_t n = op->n;
   const size_t need_v = (size_t)B * n * C, need_part = (size_t)B * g.nchunks * g.nmodes * C * 2,
-               need_chat = (size_t)B * g.Ky * C * g.Kx4;
+               need_chat = (size_t)B * g.MP * g.KXP;
   if (T.cap_v < need_v || T.cap_part < need_part || T.cap_chat < need_chat) {
     if (T.va) cudaFree(T.va);
     if (T.vb) cudaFree(T.vb);
@@ -1008,6 +1114,8 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
       set_last_error("tensor-core preconditioner workspace: out of device memory");
       return FCGNO_ENOMEM;
     }
+    // the padding of the stage-1 operand images is never written: zero it once
+    FCGNO_CUDA_TRY(cudaMemsetAsync(T.chat, 0, need_chat * 2, st));
     T.cap_v = need_v;
     T.cap_part = need_part;
     T.cap_chat = need_chat;
@@ -1022,26 +1130,28 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   const bool bf16 = !fp16;
   {
     TraceScope ts("tc_lift", st);
-    tc_lift_kernel<C><<<dim3(ceil_div(n, 256), B), 256, 0, st>>>(n, r, op->logk32, rms, active, m->w32 + BL.lift_w,
+    tc_lift_kernel<C><<<dim3(ceil_div(n, 256), B), 256, 0, st>>>(g, r, op->logk32, rms, active, m->w32 + BL.lift_w,
                                                                  m->w32 + BL.lift_b, T.va, bf16);
   }
   FCGNO_LAUNCHED();
-  const size_t sa = analysis_smem(g), ss = synthesis_smem(g), sm = mix_smem(C);
+  const int nslots = synthesis_slots(g);
+  const size_t sa = analysis_smem(g), ss = synthesis_smem(g, nslots), sm = mix_smem(C);
   // raise the dynamic shared-memory limit only when a larger plan appears (not a stream
   // operation; the first solve iteration runs eagerly, before any graph capture)
+  // (the shared-memory carveout is pinned to its maximum so that two blocks of each kernel
+  // stay resident per SM; left to the driver it may size the carveout for one block)
   static size_t set_sa = 0, set_ss = 0, set_sm = 0;
-  if (sa > set_sa) {
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_analysis_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sa));
-    set_sa = sa;
-  }
-  if (ss > set_ss) {
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_synthesis_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss));
-    set_ss = ss;
-  }
-  if (sm > set_sm) {
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(tc_mix_kernel<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    set_sm = sm;
-  }
+  auto raise = [](const void* fn, size_t bytes, size_t& set) -> cudaError_t {
+    if (bytes <= set) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) set = bytes;
+    return e;
+  };
+  FCGNO_CUDA_TRY(raise((const void*)tc_analysis_kernel<C>, sa, set_sa));
+  FCGNO_CUDA_TRY(raise((const void*)tc_synthesis_kernel<C>, ss, set_ss));
+  FCGNO_CUDA_TRY(raise((const void*)tc_mix_kernel<C>, sm, set_sm));
   uint16_t* cur = T.va;
   uint16_t* nxt = T.vb;
   for (int l = 0; l < d.layers; ++l) {
@@ -1058,18 +1168,19 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     }
     FCGNO_LAUNCHED();
     SynArgs s{};
+    s.vin = cur;
+    s.vout = nxt;
     s.g = g;
     s.B = B;
     s.bf16 = bf16;
+    s.nslots = nslots;
     s.active = active;
     s.chat = T.chat;
-    s.vin = cur;
     s.W = P.W[l];
     s.bias = m->w32 + BL.b[l];
     s.H = tab->H;
     s.Asyn = tab->Asyn;
     s.activate = l < d.layers - 1;
-    s.vout = nxt;
     s.project = l == d.layers - 1;
     s.P1 = P.P1;
     s.p1 = m->w32 + BL.proj1_b;
@@ -1081,7 +1192,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     s.err = d_err;
     {
       TraceScope ts("tc_synthesis", st);
-      tc_synthesis_kernel<C><<<dim3(g.snchunks, B), kTcThreads, ss, st>>>(s);
+      tc_synthesis_kernel<C><<<dim3(g.snchunks, B), kSynThreads, ss, st>>>(s);
     }
     FCGNO_LAUNCHED();
     std::swap(cur, nxt);
