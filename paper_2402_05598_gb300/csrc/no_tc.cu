@@ -764,9 +764,12 @@ struct SynArgs {
 };
 
 // Synthesis + pointwise + bias + activation (+ decoder) for one grid-column chunk of one instance.
-// 256 threads: warps w and w+4 read the same 32 TMEM lanes (quadrant w % 4); the two warp
-// groups split the columns (U read-back) and the channels (epilogue) between them. Thread 0
-// also issues every copy and MMA.
+//
+// Warp-specialised: warps 0-7 (256 threads) are the epilogue; warps w and w+4 read the same
+// 32 TMEM lanes (quadrant w % 4) and split the columns (U read-back) and the channels (tile
+// epilogue) between them. Lane 0 of warp 8 issues every MMA, lane 0 of warp 9 every bulk copy.
+// The three roles meet only on mbarriers; four TMEM accumulators let the MMAs run up to three
+// tiles ahead of the epilogue, so that their latency is hidden.
 //
 // Data movement: the chunk-invariant operands arrive by one bulk copy each; the activation
 // tiles (128 grid points x C channels, tile-major, so each is one contiguous block already in
@@ -774,12 +777,19 @@ struct SynArgs {
 // copy each and, once the epilogue has overwritten a slot with the layer output, drained by
 // one bulk store from the same slot. For N >= 128 the chunk's tiles are visited row block by
 // row block (tile t: q tile t / SPC, column t % SPC).
-constexpr int kSynThreads = 256;
+constexpr int kSynEpi = 256;                 // epilogue threads
+constexpr int kSynThreads = kSynEpi + 64;    // + the MMA warp and the copy warp
 constexpr int kSynMaxSlots = 6;
+constexpr int kSynAcc = 4;                   // TMEM tile accumulators
 template <int C>
 __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t full[kSynMaxSlots], mmab[2], prob, s1b, decb;
+  // barriers: full[s] tile copied in; mmadone[s] tile MMA done (slot free, decoder layer);
+  // accfull[a] accumulator a ready; accempty[a] accumulator a read back (8 warp arrivals);
+  // outready[s] layer output written into slot s (8); prob prologue copies; s1b stage 1 done;
+  // ubar U staged in shared memory (8); decin decoder input written (8); decdone decoder MMA done
+  __shared__ uint64_t full[kSynMaxSlots], mmadone[kSynMaxSlots], outready[kSynMaxSlots];
+  __shared__ uint64_t accfull[kSynAcc], accempty[kSynAcc], prob, s1b, ubar, decin, decdone;
   __shared__ uint32_t tbase_s;
   __shared__ float zpart[2][128];
   const TcGeom& g = a.g;
@@ -787,8 +797,6 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
   if (tc_inactive(a.active, b)) return;
   const int N = g.N, PC = g.SPC, Ky = g.Ky, D = a.nslots;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant, channel/column half
-  const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
   const bool bf16 = a.bf16;
   const int p0 = chunk * PC;
   // shared layout
@@ -812,13 +820,21 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
   uint8_t* sP = sW + C * C * 2;            // C x C (decoder)
   constexpr uint32_t TCOLS = 256;
   if (warp == 0) tmem_alloc(&tbase_s, TCOLS);
-  if (tid == 0) {
-    for (int i = 0; i < D; ++i) mbar_init(&full[i], 1);
-    mbar_init(&mmab[0], 1);
-    mbar_init(&mmab[1], 1);
+  if (tid == kSynEpi) {
+    for (int i = 0; i < D; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&mmadone[i], 1);
+      mbar_init(&outready[i], kSynEpi / 32);
+    }
+    for (int i = 0; i < kSynAcc; ++i) {
+      mbar_init(&accfull[i], 1);
+      mbar_init(&accempty[i], kSynEpi / 32);
+    }
     mbar_init(&prob, 1);
     mbar_init(&s1b, 1);
-    mbar_init(&decb, 1);
+    mbar_init(&ubar, kSynEpi / 32);
+    mbar_init(&decin, kSynEpi / 32);
+    mbar_init(&decdone, 1);
   }
   // zero the K tail of the staged U columns (read by padded synthesis K steps)
   const int kvalid = PC * 2 * Ky;
@@ -827,237 +843,262 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
     const int row = idx / nk, kc = (kvalid & ~7) / 8 + idx % nk;
     *reinterpret_cast<uint4*>(sB + kmajor_off(row, kc * 8, 128, SBO_B)) = make_uint4(0, 0, 0, 0);
   }
+  fence_smem_to_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = tbase_s;
-  const uint32_t tU = tbase;              // (MP/128) x 2PC columns (stage 1)
-  const uint32_t tD = tbase;              // 2 x C tile accumulators (reuse U's columns after stage 1)
-  const uint32_t tE = tbase + 2 * C;      // C decoder accumulator
-  bool ok = true;
-  bool pro_pending = false;
+  const uint32_t tU = tbase;                   // (MP/128) x 2PC columns (stage 1)
+  const uint32_t tD = tbase;                   // kSynAcc x C tile accumulators (reuse U's columns)
+  const uint32_t tE = tbase + kSynAcc * C;     // C decoder accumulator
   const int utiles = g.MP / 128;
-  // ---- chunk-invariant operands, then synthesis stage 1: U = c' H^T for the chunk
-  if (tid == 0) {
-    mbar_expect_tx(&prob, bytesA1 + bytesH + C * C * 2 * (a.project ? 2 : 1) + (N < 128 ? SB : 0));
-    bulk_g2s(sA1, a.chat + (size_t)b * g.MP * g.KXP, bytesA1, &prob);
-    bulk_g2s(sH, a.H + (size_t)chunk * 2 * PC * g.KXP, bytesH, &prob);
-    bulk_g2s(sW, a.W, C * C * 2, &prob);
-    if (a.project) bulk_g2s(sP, a.P1, C * C * 2, &prob);
-    if (N < 128) bulk_g2s(sS, a.Asyn, SB, &prob);
-    ok = mbar_wait(&prob, 0);
-    pro_pending = !ok;
-    if (ok) {
-      const uint32_t id = idesc_f16(128, 2 * PC, bf16, true, false);
-      for (int ut = 0; ut < utiles; ++ut)
-        for (int ks = 0; ks < g.KXP / 16; ++ks)
-          mma(tU + ut * 2 * PC, desc(smem_addr(sA1) + ut * 16 * 128 + ks * 2 * LBO_A1, LBO_A1, 128),
-              desc(smem_addr(sH) + ks * 256, 128, g.KXP * 16), id, ks > 0);
-      commit(&s1b);
-    }
-  }
-  {
-    const bool w = mbar_wait(&s1b, 0);
-    ok = ok && w;
-  }
-  fence_after_sync();
-  if (ok) {
-    // U lane (k2, c), columns (p, t') -> sB[c][(p, k2, t')]
-    for (int ut = 0; ut < utiles; ++ut) {
-      const int row = ut * 128 + quad * 32 + lane;
-      const int k2 = row / C, c = row % C;
-      for (int c0 = half * PC; c0 < (half + 1) * PC; c0 += 16) {
-        float val[16];
-        tmem_ld16(tU + ut * 2 * PC + c0 + lane_off, val);
-        if (row < Ky * C) {
-#pragma unroll
-          for (int i = 0; i < 16; i += 2) {
-            const int pl = (c0 + i) >> 1;
-            *reinterpret_cast<uint32_t*>(sB + kmajor_off(c, pl * 2 * Ky + 2 * k2, 128, SBO_B)) =
-                pack2(val[i], val[i + 1], bf16);
-          }
-        }
-      }
-    }
-  }
-  fence_smem_to_async();
-  fence_before_sync();
-  ok = __syncthreads_and(ok);
-  fence_after_sync();
-  // ---- tiles of 128 grid points
   const int ntiles = (N < 128) ? PC / g.PT : PC * (N / 128);
-  const int PF = D - 2;  // tiles loaded ahead; a slot is refilled two tiles after its store
-  // Thread tid owns tile row m = tid % 128 of every tile: its grid point within the tile is
-  // fixed, so the row's (q, column offset) are computed once.
-  const int m_own = tid & 127;
-  const int own_pl = (N < 128) ? m_own / N : 0;     // column within the tile (N < 128)
-  const int own_q = (N < 128) ? m_own % N : m_own;  // row (N < 128) or row within the q-tile
-  auto tile_point = [&](int t, int& q, int& p) {
-    if (N < 128) {
-      q = own_q;
-      p = p0 + t * g.PT + own_pl;
-    } else {
-      p = p0 + t % PC;
-      q = (t / PC) * 128 + own_q;
-    }
-  };
-  // tile-major index of tile t of this chunk
   const size_t inst_tiles = (size_t)N * N / 128;
+  // tile-major index of tile t of this chunk
   auto tile_index = [&](int t) -> size_t {
     const size_t tau = (N < 128) ? (size_t)(p0 / g.PT + t) : (size_t)(t / PC) * N + p0 + t % PC;
     return (size_t)b * inst_tiles + tau;
   };
-  // thread 0: issue the copy of tile t (and, N >= 128, its table rows) into its ring slot
-  auto load_tile = [&](int t) {
-    const int s = t % D;
-    uint8_t* dst = ring + s * SL;
-    mbar_expect_tx(&full[s], SL);
-    bulk_g2s(dst, a.vin + tile_index(t) * 128 * C, TB, &full[s]);
-    if (N >= 128) bulk_g2s(dst + TB, a.Asyn + (size_t)(t / PC) * 128 * g.KSYN, SB, &full[s]);
-  };
-  // thread 0: issue the store of the layer output held in tile t's slot
-  auto store_tile = [&](int t) {
-    bulk_s2g(a.vout + tile_index(t) * 128 * C, ring + (t % D) * SL, TB);
-    bulk_commit();
-  };
-  const uint32_t idD = idesc_f16(128, C, bf16);
-  // thread 0: tile t's MMAs into accumulator slot t % 2
-  auto mma_tile = [&](int t) {
-    const int acc = t & 1;
-    const uint32_t sx = smem_addr(ring + (t % D) * SL);
-    const uint32_t ss = (N < 128) ? smem_addr(sS) : sx + TB;
-    for (int ks = 0; ks < C / 16; ++ks)
-      mma(tD + acc * C, desc(sx + ks * 2 * LBO_T, LBO_T, 128), desc(smem_addr(sW) + ks * 256, 128, SBO_C), idD, ks > 0);
-    const int kb0 = (N < 128) ? t * g.PT * 2 * Ky : (t % PC) * 2 * Ky;
-    for (int ks = 0; ks < g.KSYN / 16; ++ks)
-      mma(tD + acc * C, desc(ss + ks * 256, 128, SBO_S), desc(smem_addr(sB) + (kb0 / 8) * 128 + ks * 256, 128, SBO_B),
-          idD, true);
-    commit(&mmab[acc]);
-  };
-  constexpr int CH = C / 2;  // channels per thread in the epilogue
-  const int cbase = half * CH;
-  float bias[CH];
+  bool ok = true;
+  if (warp == kSynEpi / 32) {
+    // ================================ MMA issuer (one lane) ============================
+    if (lane == 0) {
+      int mmas = 0, decs = 0;
+      bool s1_pending = false;
+      const uint32_t idD = idesc_f16(128, C, bf16);
+      // descriptors with the address field advanced per slot / K step (address >> 4 in the
+      // low bits, no carry: shared addresses are below 256 KB)
+      const uint64_t dX0 = desc(smem_addr(ring), LBO_T, 128);
+      const uint64_t dW0 = desc(smem_addr(sW), 128, SBO_C);
+      const uint64_t dS0 = desc(smem_addr(N < 128 ? sS : ring + TB), 128, SBO_S);
+      const uint64_t dB0 = desc(smem_addr(sB), 128, SBO_B);
+      const uint64_t dD0 = desc(smem_addr(sD), 128, SBO_C), dP0 = desc(smem_addr(sP), 128, SBO_C);
+      const int ksyn = g.KSYN / 16;
+      auto mma_tile = [&](int t) {
+        const int acc = t % kSynAcc;
+        const uint64_t slot = (uint64_t)(((t % D) * SL) >> 4);
 #pragma unroll
-  for (int c = 0; c < CH; ++c) bias[c] = a.bias[cbase + c];
-  // thread-0 bookkeeping of copies and MMAs in flight (drained on the error path)
-  int loads = 0, loads_waited = 0, mmas = 0, mmas_waited = 0;
-  uint32_t dph = 0;
-  // Software pipeline: while tile t's epilogue runs, tile t+1's MMA runs on the tensor core
-  // (other accumulator) and tiles up to t+PF are being loaded.
-  if (tid == 0 && ok && ntiles > 0) {
-    for (; loads < ntiles && loads < PF; ++loads) load_tile(loads);
-    ok = mbar_wait(&full[0], 0);
-    loads_waited = ok ? 1 : 0;
-    if (ok) {
-      mma_tile(0);
-      mmas = 1;
+        for (int ks = 0; ks < C / 16; ++ks)
+          mma(tD + acc * C, dX0 + slot + ks * (2 * LBO_T >> 4), dW0 + ks * 16, idD, ks > 0);
+        const int kb0 = (N < 128) ? t * g.PT * 2 * Ky : (t % PC) * 2 * Ky;
+        const uint64_t dS = dS0 + (N < 128 ? 0 : slot), dB = dB0 + (uint64_t)((kb0 / 8) * 8);
+        for (int ks = 0; ks < ksyn; ++ks) mma(tD + acc * C, dS + ks * 16, dB + ks * 16, idD, true);
+        commit(&accfull[acc]);
+        if (a.project) commit(&mmadone[t % D]);
+      };
+      // decoder MMA of tile u once its (GELU'd) layer output is in sD
+      auto decode = [&](int u) -> bool {
+        if (!mbar_wait(&decin, u & 1)) return false;
+        fence_after_sync();
+#pragma unroll
+        for (int ks = 0; ks < C / 16; ++ks) mma(tE, dD0 + ks * 16, dP0 + ks * 16, idD, ks > 0);
+        commit(&decdone);
+        decs = u + 1;
+        return true;
+      };
+      // synthesis stage 1: U = c' H^T for the chunk
+      ok = mbar_wait(&prob, 0);
+      if (ok) {
+        const uint32_t id = idesc_f16(128, 2 * PC, bf16, true, false);
+        for (int ut = 0; ut < utiles; ++ut)
+          for (int ks = 0; ks < g.KXP / 16; ++ks)
+            mma(tU + ut * 2 * PC, desc(smem_addr(sA1) + ut * 16 * 128 + ks * 2 * LBO_A1, LBO_A1, 128),
+                desc(smem_addr(sH) + ks * 256, 128, g.KXP * 16), id, ks > 0);
+        commit(&s1b);
+        s1_pending = true;
+        ok = mbar_wait(&ubar, 0);  // U read back and staged in sB by the epilogue warps
+        if (ok) s1_pending = false;
+        fence_after_sync();
+      }
+      constexpr int LAG = kSynAcc - 1;  // decoder of tile t - LAG issued after tile t's MMAs
+      for (int t = 0; t < ntiles && ok; ++t) {
+        ok = mbar_wait(&full[t % D], (t / D) & 1);
+        if (ok && t >= kSynAcc) ok = mbar_wait(&accempty[t % kSynAcc], ((t / kSynAcc) - 1) & 1);
+        if (!ok) break;
+        fence_after_sync();
+        mma_tile(t);
+        mmas = t + 1;
+        if (a.project && t >= LAG) ok = decode(t - LAG);
+      }
+      for (int u = decs; ok && a.project && u < ntiles; ++u) ok = decode(u);
+      if (!ok) {
+        // error path: let the MMAs this block started finish (bounded) before the block
+        // releases its tensor memory
+        if (s1_pending) mbar_wait(&s1b, 0);
+        for (int u = mmas > kSynAcc ? mmas - kSynAcc : 0; u < mmas; ++u)
+          mbar_wait(&accfull[u % kSynAcc], (u / kSynAcc) & 1);
+        if (decs > 0) mbar_wait(&decdone, (decs - 1) & 1);
+        atomicExch(a.err, 1);
+      }
     }
-  }
-  for (int t = 0; t < ntiles; ++t) {
-    if (tid == 0 && ok) {
-      if (t + 1 < ntiles) {
-        ok = mbar_wait(&full[(t + 1) % D], ((t + 1) / D) & 1);
-        if (ok) {
-          loads_waited = t + 2;
-          mma_tile(t + 1);
-          mmas = t + 2;
+  } else if (warp == kSynEpi / 32 + 1) {
+    // ================================ copy issuer (one lane) ===========================
+    if (lane == 0) {
+      int loads = 0;
+      bool pro_pending = false;
+      auto load_tile = [&](int t) {
+        const int s = t % D;
+        uint8_t* dst = ring + s * SL;
+        mbar_expect_tx(&full[s], SL);
+        bulk_g2s(dst, a.vin + tile_index(t) * 128 * C, TB, &full[s]);
+        if (N >= 128) bulk_g2s(dst + TB, a.Asyn + (size_t)(t / PC) * 128 * g.KSYN, SB, &full[s]);
+        loads = t + 1;
+      };
+      mbar_expect_tx(&prob, bytesA1 + bytesH + C * C * 2 * (a.project ? 2 : 1) + (N < 128 ? SB : 0));
+      bulk_g2s(sA1, a.chat + (size_t)b * g.MP * g.KXP, bytesA1, &prob);
+      bulk_g2s(sH, a.H + (size_t)chunk * 2 * PC * g.KXP, bytesH, &prob);
+      bulk_g2s(sW, a.W, C * C * 2, &prob);
+      if (a.project) bulk_g2s(sP, a.P1, C * C * 2, &prob);
+      if (N < 128) bulk_g2s(sS, a.Asyn, SB, &prob);
+      ok = mbar_wait(&prob, 0);
+      pro_pending = !ok;
+      if (ok) ok = mbar_wait(&s1b, 0);  // stage 1 has read sA1: the ring may overwrite it
+      if (ok)
+        while (loads < ntiles && loads < D) load_tile(loads);
+      for (int u = 0; u < ntiles && ok; ++u) {
+        if (!a.project) {
+          // store the layer output of tile u, then refill the slot of tile u - 1 (its store,
+          // not the latest one, has finished reading the slot)
+          ok = mbar_wait(&outready[u % D], (u / D) & 1);
+          if (!ok) break;
+          bulk_s2g(a.vout + tile_index(u) * 128 * C, ring + (u % D) * SL, TB);
+          bulk_commit();
+          if (u >= 1 && u - 1 + D < ntiles) {
+            bulk_wait_read<1>();
+            load_tile(u - 1 + D);
+          }
+        } else if (u + D < ntiles) {
+          ok = mbar_wait(&mmadone[u % D], (u / D) & 1);  // tile u's MMA has read its slot
+          if (ok) load_tile(u + D);
         }
       }
-      if (ok && loads < ntiles) {
-        bulk_wait_read<1>();  // the store of the slot's previous tile (loads - D) has read it
-        load_tile(loads);
-        ++loads;
+      if (!ok) {
+        // error path: let every copy this block started finish (bounded)
+        if (pro_pending) mbar_wait(&prob, 0);
+        for (int u = loads > D ? loads - D : 0; u < loads; ++u) mbar_wait(&full[u % D], (u / D) & 1);
+        atomicExch(a.err, 1);
       }
+      bulk_wait_read<0>();
     }
-    {
-      const bool w = mbar_wait(&mmab[t & 1], (t >> 1) & 1);
-      if (w) mmas_waited = t + 1;
-      ok = ok && w;
-    }
+  } else {
+    // ================================ epilogue (256 threads) ===========================
+    const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant, channel/column half
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
+    ok = mbar_wait(&s1b, 0);
     fence_after_sync();
-    // epilogue: lane = grid point, this warp group's C/2 channels
-    const int m = m_own;
-    int q, p;
-    tile_point(t, q, p);
-    float h[CH];
-    {
-      const uint32_t col = tD + (t & 1) * C + cbase + lane_off;
-      if constexpr (CH == 16) {
-        tmem_ld16(col, h);
-      } else {
-        tmem_ld8(col, h);
-      }
+    if (ok) {
+      // U lane (k2, c), columns (p, t') -> sB[c][(p, k2, t')]
+      for (int ut = 0; ut < utiles; ++ut) {
+        const int row = ut * 128 + quad * 32 + lane;
+        const int k2 = row / C, c = row % C;
+        for (int c0 = half * PC; c0 < (half + 1) * PC; c0 += 16) {
+          float val[16];
+          tmem_ld16(tU + ut * 2 * PC + c0 + lane_off, val);
+          if (row < Ky * C) {
 #pragma unroll
-      for (int i = 0; i < CH; ++i) {
-        const float x = h[i] + bias[i];
-        h[i] = a.activate ? gelu16(x) : x;
-      }
-    }
-    if (!a.project) {
-      // the layer output replaces the (consumed) input tile in its slot
-      uint8_t* dst = ring + (t % D) * SL + m * 16;
-#pragma unroll
-      for (int c0 = 0; c0 < CH; c0 += 8) {
-        *reinterpret_cast<uint4*>(dst + ((cbase + c0) / 8) * LBO_T) =
-            make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
-                       pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
-      }
-    } else {
-      // decoder: second MMA on the 16-bit layer output
-#pragma unroll
-      for (int c0 = 0; c0 < CH; c0 += 8) {
-        uint4 w = make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
-                             pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
-        *reinterpret_cast<uint4*>(sD + kmajor_off(m, cbase + c0, 128, SBO_C)) = w;
+            for (int i = 0; i < 16; i += 2) {
+              const int pl = (c0 + i) >> 1;
+              *reinterpret_cast<uint32_t*>(sB + kmajor_off(c, pl * 2 * Ky + 2 * k2, 128, SBO_B)) =
+                  pack2(val[i], val[i + 1], bf16);
+            }
+          }
+        }
       }
       fence_smem_to_async();
       fence_before_sync();
-      __syncthreads();
-      fence_after_sync();
-      if (tid == 0 && ok) {
-        for (int ks = 0; ks < C / 16; ++ks)
-          mma(tE, desc(smem_addr(sD) + ks * 256, 128, SBO_C), desc(smem_addr(sP) + ks * 256, 128, SBO_C), idD, ks > 0);
-        commit(&decb);
-      }
-      {
-        const bool w = ok && mbar_wait(&decb, dph);
-        dph ^= 1;
-        ok = ok && w;
-      }
-      fence_after_sync();
-      float zt = 0.f;
-      {
-        float val[CH];
-        if constexpr (CH == 16) {
-          tmem_ld16(tE + cbase + lane_off, val);
-        } else {
-          tmem_ld8(tE + cbase + lane_off, val);
-        }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&ubar);
+    }
+    // Thread tid owns tile row m = tid % 128 of every tile: its grid point within the tile is
+    // fixed, so the row's (q, column offset) are computed once.
+    const int m = tid & 127;
+    const int own_pl = (N < 128) ? m / N : 0;     // column within the tile (N < 128)
+    const int own_q = (N < 128) ? m % N : m;      // row (N < 128) or row within the q-tile
+    constexpr int CH = C / 2;  // channels per thread in the epilogue
+    const int cbase = half * CH;
+    float bias[CH];
 #pragma unroll
-        for (int i = 0; i < CH; ++i) zt = fmaf(a.p2[cbase + i], gelu16(val[i] + a.p1[cbase + i]), zt);
+    for (int c = 0; c < CH; ++c) bias[c] = a.bias[cbase + c];
+    for (int t = 0; t < ntiles; ++t) {
+      if (ok) {
+        ok = mbar_wait(&accfull[t % kSynAcc], (t / kSynAcc) & 1);
+        fence_after_sync();
       }
-      zpart[half][m] = zt;
-      __syncthreads();
-      if (ok && half == 0)
-        a.z[((size_t)b * N + q) * N + p] = a.rms[b] * a.hh * (double)(a.p2b[0] + zpart[0][m] + zpart[1][m]);
+      float h[CH];
+      if (ok) {
+        const uint32_t col = tD + (t % kSynAcc) * C + cbase + lane_off;
+        if constexpr (CH == 16) {
+          tmem_ld16(col, h);
+        } else {
+          tmem_ld8(col, h);
+        }
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&accempty[t % kSynAcc]);
+#pragma unroll
+        for (int i = 0; i < CH; ++i) {
+          const float x = h[i] + bias[i];
+          h[i] = a.activate ? gelu16(x) : x;
+        }
+      }
+      if (!a.project) {
+        if (!ok) break;
+        // the layer output replaces the (consumed) input tile in its slot
+        uint8_t* dst = ring + (t % D) * SL + m * 16;
+#pragma unroll
+        for (int c0 = 0; c0 < CH; c0 += 8) {
+          *reinterpret_cast<uint4*>(dst + ((cbase + c0) / 8) * LBO_T) =
+              make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
+                         pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
+        }
+        fence_smem_to_async();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&outready[t % D]);
+      } else {
+        // decoder: second MMA on the 16-bit layer output (sD is free: the previous tile's
+        // decoder MMA completed before this thread left that tile)
+        if (ok) {
+#pragma unroll
+          for (int c0 = 0; c0 < CH; c0 += 8) {
+            uint4 w = make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
+                                 pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
+            *reinterpret_cast<uint4*>(sD + kmajor_off(m, cbase + c0, 128, SBO_C)) = w;
+          }
+          fence_smem_to_async();
+          __syncwarp();
+          if (lane == 0) mbar_arrive(&decin);
+          ok = mbar_wait(&decdone, t & 1);
+          fence_after_sync();
+        }
+        float zt = 0.f;
+        if (ok) {
+          float val[CH];
+          if constexpr (CH == 16) {
+            tmem_ld16(tE + cbase + lane_off, val);
+          } else {
+            tmem_ld8(tE + cbase + lane_off, val);
+          }
+#pragma unroll
+          for (int i = 0; i < CH; ++i) zt = fmaf(a.p2[cbase + i], gelu16(val[i] + a.p1[cbase + i]), zt);
+        }
+        zpart[half][m] = zt;
+        // epilogue-only barrier (named barrier 1); every epilogue thread reaches it once per
+        // tile, and the AND keeps the decision to stop uniform
+        ok = named_barrier_and(1, kSynEpi, ok);
+        if (!ok) break;
+        if (half == 0) {
+          int q, p;
+          if (N < 128) {
+            q = own_q;
+            p = p0 + t * g.PT + own_pl;
+          } else {
+            p = p0 + t % PC;
+            q = (t / PC) * 128 + own_q;
+          }
+          a.z[((size_t)b * N + q) * N + p] = a.rms[b] * a.hh * (double)(a.p2b[0] + zpart[0][m] + zpart[1][m]);
+        }
+      }
     }
-    fence_smem_to_async();
-    fence_before_sync();
-    ok = __syncthreads_and(ok);
-    fence_after_sync();
-    if (!ok) break;
-    if (tid == 0 && !a.project) store_tile(t);
-  }
-  if (tid == 0) {
-    if (!ok) {
-      // error path: let every copy and MMA this block started finish (bounded) before the
-      // block releases its shared and tensor memory
-      if (pro_pending) mbar_wait(&prob, 0);
-      for (int u = loads_waited; u < loads; ++u) mbar_wait(&full[u % D], (u / D) & 1);
-      for (int u = mmas_waited; u < mmas; ++u) mbar_wait(&mmab[u & 1], (u >> 1) & 1);
-      atomicExch(a.err, 1);
-    }
-    bulk_wait_read<0>();
   }
   fence_before_sync();
   __syncthreads();

@@ -62,6 +62,23 @@ __device__ __forceinline__ uint64_t globaltimer() {
   return t;
 }
 
+// Plain arrival (count 1) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(mbar)) : "memory");
+}
+
+// Barrier over the first `count` threads of the block on hardware barrier `id` (1..15),
+// returning the AND of `pred` over them.
+__device__ __forceinline__ bool named_barrier_and(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n.reg .pred p, q;\nsetp.ne.u32 p, %1, 0;\nbar.red.and.pred q, %2, %3, p;\nselp.u32 %0, 1, 0, q;\n}"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
 // Bounded wait for the given phase parity. Returns false after ~1 s without completion.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
   const uint32_t a = smem_addr(mbar);
