@@ -85,6 +85,17 @@ struct TcGeom {
   int nmodes;
 };
 
+// Dynamic shared memory of a synthesis block with column chunk spc and a tile ring of din
+// input and dout output slots (fields of g other than SPC and KB must be set).
+constexpr size_t kSynTwoPerSm = 114000;  // dynamic bytes per block that keep two blocks per SM
+static size_t synthesis_bytes(const TcGeom& g, int spc, int din, int dout) {
+  const size_t C = g.C, TB = 128 * C * 2, SB = (size_t)128 * g.KSYN * 2;
+  const size_t SL = TB + (g.N >= 128 ? SB : 0);
+  const size_t KB = (size_t)round_up(spc * 2 * g.M, 16) + 16;
+  const size_t r0 = std::max((size_t)g.MP * g.KXP * 2, din * SL + dout * TB);
+  return r0 + (size_t)2 * spc * g.KXP * 2 + C * KB * 2 + (g.N < 128 ? SB : 0) + 2 * C * C * 2;
+}
+
 static TcGeom make_geom(int N, int C, int M) {
   TcGeom g{};
   g.N = N;
@@ -110,8 +121,10 @@ static TcGeom make_geom(int N, int C, int M) {
     g.QT = 128;
     g.KSYN = round_up(2 * M, 16);
   }
-  // synthesis: narrower column chunks (more, smaller blocks; lower latency per instance)
-  g.SPC = g.PC < 16 ? g.PC : 16;
+  // synthesis column chunk: 32 columns (fewer blocks, half the per-block set-up per tile)
+  // when two blocks per SM still fit with a 3 + 2 slot tile ring, otherwise 16
+  g.SPC = 16;
+  if (N < 128 && g.PC >= 32 && (g.MP / 128) * 64 <= 256 && synthesis_bytes(g, 32, 3, 2) <= kSynTwoPerSm) g.SPC = 32;
   while (g.SPC % g.PT != 0) g.SPC *= 2;
   g.snchunks = N / g.SPC;
   g.KB = round_up(g.SPC * 2 * M, 16) + 16;
@@ -741,7 +754,7 @@ struct SynArgs {
   TcGeom g;
   int B;
   int bf16;
-  int nslots;             // depth of the tile ring (4 .. kSynMaxSlots)
+  int din, dout;          // input / output tile ring depths
   const int* active;
   const uint16_t* vin;    // layer input, tile-major
   uint16_t* vout;         // layer output, tile-major
@@ -767,35 +780,37 @@ struct SynArgs {
 //
 // Warp-specialised: warps 0-7 (256 threads) are the epilogue; warps w and w+4 read the same
 // 32 TMEM lanes (quadrant w % 4) and split the columns (U read-back) and the channels (tile
-// epilogue) between them. Lane 0 of warp 8 issues every MMA, lane 0 of warp 9 every bulk copy.
+// epilogue) between them. Lane 0 of warp 8 issues every MMA, lane 0 of warp 9 every bulk copy
+// into shared memory and lane 0 of warp 10 every bulk store.
 // The three roles meet only on mbarriers; four TMEM accumulators let the MMAs run up to three
 // tiles ahead of the epilogue, so that their latency is hidden.
 //
-// Data movement: the chunk-invariant operands arrive by one bulk copy each; the activation
+// Data movement: the chunk-invariant operands arrive by one bulk copy each. The activation
 // tiles (128 grid points x C channels, tile-major, so each is one contiguous block already in
-// the K-major operand layout) stream through a ring of shared-memory slots filled by one bulk
-// copy each and, once the epilogue has overwritten a slot with the layer output, drained by
-// one bulk store from the same slot. For N >= 128 the chunk's tiles are visited row block by
-// row block (tile t: q tile t / SPC, column t % SPC).
+// the K-major operand layout) stream through a ring of din input slots, each filled by one
+// bulk copy and released as soon as its MMA has completed; the epilogue writes the layer
+// output into a ring of dout output slots (same layout), each drained by one bulk store (or,
+// in the last layer, read by the decoder MMA). For N >= 128 the chunk's tiles are visited row
+// block by row block (tile t: q tile t / SPC, column t % SPC).
 constexpr int kSynEpi = 256;                 // epilogue threads
-constexpr int kSynThreads = kSynEpi + 64;    // + the MMA warp and the copy warp
-constexpr int kSynMaxSlots = 6;
+constexpr int kSynThreads = kSynEpi + 96;    // + the MMA, load and store warps
+constexpr int kSynMaxIn = 4, kSynMaxOut = 2;
 constexpr int kSynAcc = 4;                   // TMEM tile accumulators
 template <int C>
 __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  // barriers: full[s] tile copied in; mmadone[s] tile MMA done (slot free, decoder layer);
-  // accfull[a] accumulator a ready; accempty[a] accumulator a read back (8 warp arrivals);
-  // outready[s] layer output written into slot s (8); prob prologue copies; s1b stage 1 done;
-  // ubar U staged in shared memory (8); decin decoder input written (8); decdone decoder MMA done
-  __shared__ uint64_t full[kSynMaxSlots], mmadone[kSynMaxSlots], outready[kSynMaxSlots];
-  __shared__ uint64_t accfull[kSynAcc], accempty[kSynAcc], prob, s1b, ubar, decin, decdone;
+  // barriers: full[s] input tile copied in; infree[s] its MMA done; accfull[a] accumulator a
+  // ready; accempty[a] accumulator a read back (8 warp arrivals); outready[o] output slot o
+  // written (8); outfree[o] output slot o read by its store or decoder MMA; prob prologue
+  // copies; s1b stage 1 done; ubar U staged in shared memory (8); decdone decoder MMA done
+  __shared__ uint64_t full[kSynMaxIn], infree[kSynMaxIn], outready[kSynMaxOut], outfree[kSynMaxOut];
+  __shared__ uint64_t accfull[kSynAcc], accempty[kSynAcc], prob, s1b, ubar, decdone;
   __shared__ uint32_t tbase_s;
   __shared__ float zpart[2][128];
   const TcGeom& g = a.g;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(a.active, b)) return;
-  const int N = g.N, PC = g.SPC, Ky = g.Ky, D = a.nslots;
+  const int N = g.N, PC = g.SPC, Ky = g.Ky, DI = a.din, DO = a.dout;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const bool bf16 = a.bf16;
   const int p0 = chunk * PC;
@@ -804,15 +819,15 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
   const uint32_t SBO_B = g.KB * 16, SBO_S = g.KSYN * 16, SBO_C = C * 16;
   constexpr uint32_t TB = 128 * C * 2, LBO_T = 128 * 16;
   const uint32_t SB = 128 * g.KSYN * 2;
-  const uint32_t SL = TB + (N >= 128 ? SB : 0);  // ring slot: tile, then (N >= 128) its table rows
+  const uint32_t SL = TB + (N >= 128 ? SB : 0);  // input slot: tile, then (N >= 128) its table rows
   const uint32_t bytesA1 = g.MP * g.KXP * 2, bytesH = 2 * PC * g.KXP * 2;
   // region R0 holds the mixed coefficients for synthesis stage 1, then (aliased, once stage 1
-  // has completed) the tile ring and the decoder input tile
-  const uint32_t ring_bytes = D * SL + TB;
+  // has completed) the input and output rings
+  const uint32_t ring_bytes = DI * SL + DO * TB;
   const uint32_t r0 = bytesA1 > ring_bytes ? bytesA1 : ring_bytes;
   uint8_t* sA1 = smem;                     // MP x KXP
-  uint8_t* ring = smem;                    // D slots of SL bytes (after stage 1)
-  uint8_t* sD = smem + D * SL;             // 128 x C decoder input (after stage 1)
+  uint8_t* ring = smem;                    // DI input slots of SL bytes (after stage 1)
+  uint8_t* oring = smem + DI * SL;         // DO output slots of TB bytes (after stage 1)
   uint8_t* sH = smem + r0;                 // 2PC x KXP
   uint8_t* sB = sH + bytesH;               // C x KB
   uint8_t* sS = sB + C * g.KB * 2;         // 128 x KSYN (N < 128: one table for all tiles)
@@ -821,10 +836,13 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
   constexpr uint32_t TCOLS = 256;
   if (warp == 0) tmem_alloc(&tbase_s, TCOLS);
   if (tid == kSynEpi) {
-    for (int i = 0; i < D; ++i) {
+    for (int i = 0; i < DI; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&mmadone[i], 1);
+      mbar_init(&infree[i], 1);
+    }
+    for (int i = 0; i < DO; ++i) {
       mbar_init(&outready[i], kSynEpi / 32);
+      mbar_init(&outfree[i], 1);
     }
     for (int i = 0; i < kSynAcc; ++i) {
       mbar_init(&accfull[i], 1);
@@ -833,7 +851,6 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
     mbar_init(&prob, 1);
     mbar_init(&s1b, 1);
     mbar_init(&ubar, kSynEpi / 32);
-    mbar_init(&decin, kSynEpi / 32);
     mbar_init(&decdone, 1);
   }
   // zero the K tail of the staged U columns (read by padded synthesis K steps)
@@ -869,14 +886,15 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
       // descriptors with the address field advanced per slot / K step (address >> 4 in the
       // low bits, no carry: shared addresses are below 256 KB)
       const uint64_t dX0 = desc(smem_addr(ring), LBO_T, 128);
+      const uint64_t dO0 = desc(smem_addr(oring), LBO_T, 128);
       const uint64_t dW0 = desc(smem_addr(sW), 128, SBO_C);
       const uint64_t dS0 = desc(smem_addr(N < 128 ? sS : ring + TB), 128, SBO_S);
       const uint64_t dB0 = desc(smem_addr(sB), 128, SBO_B);
-      const uint64_t dD0 = desc(smem_addr(sD), 128, SBO_C), dP0 = desc(smem_addr(sP), 128, SBO_C);
+      const uint64_t dP0 = desc(smem_addr(sP), 128, SBO_C);
       const int ksyn = g.KSYN / 16;
       auto mma_tile = [&](int t) {
         const int acc = t % kSynAcc;
-        const uint64_t slot = (uint64_t)(((t % D) * SL) >> 4);
+        const uint64_t slot = (uint64_t)(((t % DI) * SL) >> 4);
 #pragma unroll
         for (int ks = 0; ks < C / 16; ++ks)
           mma(tD + acc * C, dX0 + slot + ks * (2 * LBO_T >> 4), dW0 + ks * 16, idD, ks > 0);
@@ -884,15 +902,18 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         const uint64_t dS = dS0 + (N < 128 ? 0 : slot), dB = dB0 + (uint64_t)((kb0 / 8) * 8);
         for (int ks = 0; ks < ksyn; ++ks) mma(tD + acc * C, dS + ks * 16, dB + ks * 16, idD, true);
         commit(&accfull[acc]);
-        if (a.project) commit(&mmadone[t % D]);
+        commit(&infree[t % DI]);
       };
-      // decoder MMA of tile u once its (GELU'd) layer output is in sD
+      // decoder MMA of tile u once its (GELU'd) layer output is in its output slot
       auto decode = [&](int u) -> bool {
-        if (!mbar_wait(&decin, u & 1)) return false;
+        if (!mbar_wait(&outready[u % DO], (u / DO) & 1)) return false;
         fence_after_sync();
+        const uint64_t slot = (uint64_t)(((u % DO) * TB) >> 4);
 #pragma unroll
-        for (int ks = 0; ks < C / 16; ++ks) mma(tE, dD0 + ks * 16, dP0 + ks * 16, idD, ks > 0);
+        for (int ks = 0; ks < C / 16; ++ks)
+          mma(tE, dO0 + slot + ks * (2 * LBO_T >> 4), dP0 + ks * 16, idD, ks > 0);
         commit(&decdone);
+        commit(&outfree[u % DO]);
         decs = u + 1;
         return true;
       };
@@ -912,7 +933,7 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
       }
       constexpr int LAG = kSynAcc - 1;  // decoder of tile t - LAG issued after tile t's MMAs
       for (int t = 0; t < ntiles && ok; ++t) {
-        ok = mbar_wait(&full[t % D], (t / D) & 1);
+        ok = mbar_wait(&full[t % DI], (t / DI) & 1);
         if (ok && t >= kSynAcc) ok = mbar_wait(&accempty[t % kSynAcc], ((t / kSynAcc) - 1) & 1);
         if (!ok) break;
         fence_after_sync();
@@ -932,12 +953,12 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
       }
     }
   } else if (warp == kSynEpi / 32 + 1) {
-    // ================================ copy issuer (one lane) ===========================
+    // ================================ load issuer (one lane) ===========================
     if (lane == 0) {
       int loads = 0;
       bool pro_pending = false;
       auto load_tile = [&](int t) {
-        const int s = t % D;
+        const int s = t % DI;
         uint8_t* dst = ring + s * SL;
         mbar_expect_tx(&full[s], SL);
         bulk_g2s(dst, a.vin + tile_index(t) * 128 * C, TB, &full[s]);
@@ -952,32 +973,37 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
       if (N < 128) bulk_g2s(sS, a.Asyn, SB, &prob);
       ok = mbar_wait(&prob, 0);
       pro_pending = !ok;
-      if (ok) ok = mbar_wait(&s1b, 0);  // stage 1 has read sA1: the ring may overwrite it
+      if (ok) ok = mbar_wait(&s1b, 0);  // stage 1 has read sA1: the rings may overwrite it
       if (ok)
-        while (loads < ntiles && loads < D) load_tile(loads);
-      for (int u = 0; u < ntiles && ok; ++u) {
-        if (!a.project) {
-          // store the layer output of tile u, then refill the slot of tile u - 1 (its store,
-          // not the latest one, has finished reading the slot)
-          ok = mbar_wait(&outready[u % D], (u / D) & 1);
-          if (!ok) break;
-          bulk_s2g(a.vout + tile_index(u) * 128 * C, ring + (u % D) * SL, TB);
-          bulk_commit();
-          if (u >= 1 && u - 1 + D < ntiles) {
-            bulk_wait_read<1>();
-            load_tile(u - 1 + D);
-          }
-        } else if (u + D < ntiles) {
-          ok = mbar_wait(&mmadone[u % D], (u / D) & 1);  // tile u's MMA has read its slot
-          if (ok) load_tile(u + D);
-        }
+        while (loads < ntiles && loads < DI) load_tile(loads);
+      // refill the input slot of tile u as soon as its MMA has read it
+      for (int u = 0; u + DI < ntiles && ok; ++u) {
+        ok = mbar_wait(&infree[u % DI], (u / DI) & 1);
+        if (ok) load_tile(u + DI);
       }
       if (!ok) {
         // error path: let every copy this block started finish (bounded)
         if (pro_pending) mbar_wait(&prob, 0);
-        for (int u = loads > D ? loads - D : 0; u < loads; ++u) mbar_wait(&full[u % D], (u / D) & 1);
+        for (int u = loads > DI ? loads - DI : 0; u < loads; ++u) mbar_wait(&full[u % DI], (u / DI) & 1);
         atomicExch(a.err, 1);
       }
+    }
+  } else if (warp == kSynEpi / 32 + 2) {
+    // ================================ store issuer (one lane) ==========================
+    if (lane == 0 && !a.project) {
+      // store the layer output of tile u; release the output slot of tile u - 1 once its
+      // store (not the latest one) has read it
+      for (int u = 0; u < ntiles && ok; ++u) {
+        ok = mbar_wait(&outready[u % DO], (u / DO) & 1);
+        if (!ok) break;
+        bulk_s2g(a.vout + tile_index(u) * 128 * C, oring + (u % DO) * TB, TB);
+        bulk_commit();
+        if (u >= 1) {
+          bulk_wait_read<1>();
+          mbar_arrive(&outfree[(u - 1) % DO]);
+        }
+      }
+      if (!ok) atomicExch(a.err, 1);
       bulk_wait_read<0>();
     }
   } else {
@@ -1040,11 +1066,11 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
           const float x = h[i] + bias[i];
           h[i] = a.activate ? gelu16(x) : x;
         }
+        // the output slot's previous tile (t - DO) has been stored / decoded
+        if (t >= DO) ok = mbar_wait(&outfree[t % DO], ((t / DO) - 1) & 1);
       }
-      if (!a.project) {
-        if (!ok) break;
-        // the layer output replaces the (consumed) input tile in its slot
-        uint8_t* dst = ring + (t % D) * SL + m * 16;
+      if (ok) {
+        uint8_t* dst = oring + (t % DO) * TB + m * 16;
 #pragma unroll
         for (int c0 = 0; c0 < CH; c0 += 8) {
           *reinterpret_cast<uint4*>(dst + ((cbase + c0) / 8) * LBO_T) =
@@ -1053,20 +1079,13 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         }
         fence_smem_to_async();
         __syncwarp();
-        if (lane == 0) mbar_arrive(&outready[t % D]);
+        if (lane == 0) mbar_arrive(&outready[t % DO]);
+      }
+      if (!a.project) {
+        if (!ok) break;
       } else {
-        // decoder: second MMA on the 16-bit layer output (sD is free: the previous tile's
-        // decoder MMA completed before this thread left that tile)
+        // decoder: the MMA warp multiplies the output slot by the decoder weights into tE
         if (ok) {
-#pragma unroll
-          for (int c0 = 0; c0 < CH; c0 += 8) {
-            uint4 w = make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
-                                 pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
-            *reinterpret_cast<uint4*>(sD + kmajor_off(m, cbase + c0, 128, SBO_C)) = w;
-          }
-          fence_smem_to_async();
-          __syncwarp();
-          if (lane == 0) mbar_arrive(&decin);
           ok = mbar_wait(&decdone, t & 1);
           fence_after_sync();
         }
@@ -1083,7 +1102,9 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         }
         zpart[half][m] = zt;
         // epilogue-only barrier (named barrier 1); every epilogue thread reaches it once per
-        // tile, and the AND keeps the decision to stop uniform
+        // tile, and the AND keeps the decision to stop uniform. It also orders every thread's
+        // read of tE before the next tile's outready arrival, which releases the next decoder MMA.
+        fence_before_sync();
         ok = named_barrier_and(1, kSynEpi, ok);
         if (!ok) break;
         if (half == 0) {
@@ -1112,19 +1133,13 @@ static size_t analysis_smem(const TcGeom& g) {
          (size_t)g.NPM * 2 * g.PC * 2;
 }
 static size_t mix_smem(int C) { return (size_t)128 * 2 * C * 2 + (size_t)4 * C * C * 2; }
-static size_t synthesis_smem(const TcGeom& g, int D) {
-  const int C = g.C;
-  const size_t TB = (size_t)128 * C * 2, SB = (size_t)128 * g.KSYN * 2, SL = TB + (g.N >= 128 ? SB : 0);
-  const size_t r0 = std::max((size_t)g.MP * g.KXP * 2, D * SL + TB);
-  return r0 + (size_t)2 * g.SPC * g.KXP * 2 + (size_t)C * g.KB * 2 + (g.N < 128 ? SB : 0) + (size_t)2 * C * C * 2;
-}
-// Deepest tile ring (4 .. kSynMaxSlots slots) that keeps two synthesis blocks per SM; 4 slots
-// (one block per SM) when even that does not fit.
-static int synthesis_slots(const TcGeom& g) {
-  constexpr size_t kTwoPerSm = 110 * 1024;  // dynamic bytes per block with two blocks per SM
-  for (int D = kSynMaxSlots; D > 4; --D)
-    if (synthesis_smem(g, D) <= kTwoPerSm) return D;
-  return 4;
+// Tile rings of the synthesis kernel: the deepest input ring (2 .. 4 slots, 2 output slots)
+// that keeps two blocks per SM; 4 + 2 (one block per SM) when none does.
+static void synthesis_rings(const TcGeom& g, int& din, int& dout) {
+  dout = kSynMaxOut;
+  for (din = kSynMaxIn; din >= 2; --din)
+    if (synthesis_bytes(g, g.SPC, din, dout) <= kSynTwoPerSm) return;
+  din = kSynMaxIn;
 }
 
 template <int C>
@@ -1175,8 +1190,9 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
                                                                  m->w32 + BL.lift_b, T.va, bf16);
   }
   FCGNO_LAUNCHED();
-  const int nslots = synthesis_slots(g);
-  const size_t sa = analysis_smem(g), ss = synthesis_smem(g, nslots), sm = mix_smem(C);
+  int din, dout;
+  synthesis_rings(g, din, dout);
+  const size_t sa = analysis_smem(g), ss = synthesis_bytes(g, g.SPC, din, dout), sm = mix_smem(C);
   // raise the dynamic shared-memory limit only when a larger plan appears (not a stream
   // operation; the first solve iteration runs eagerly, before any graph capture)
   // (the shared-memory carveout is pinned to its maximum so that two blocks of each kernel
@@ -1214,7 +1230,8 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     s.g = g;
     s.B = B;
     s.bf16 = bf16;
-    s.nslots = nslots;
+    s.din = din;
+    s.dout = dout;
     s.active = active;
     s.chat = T.chat;
     s.W = P.W[l];
