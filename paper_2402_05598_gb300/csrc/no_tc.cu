@@ -233,7 +233,7 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
 struct TcPrecision {
   bool built = false;
   std::vector<uint16_t*> W;   // [L] C x C image (K-major)
-  std::vector<uint16_t*> Rr;  // [L] nmodes x 2C x 2C
+  std::vector<uint16_t*> Rr;  // [L] nmodes images 2C x 2C (K-major)
   uint16_t* P1 = nullptr;     // Cp x C image (K-major)
   std::map<int, TcTables> tables;
 };
@@ -246,7 +246,7 @@ struct fcgno::TcModel {
   size_t cap_v = 0, cap_part = 0, cap_chat = 0;
   uint16_t* va = nullptr;
   uint16_t* vb = nullptr;
-  float* part = nullptr;
+  uint16_t* part = nullptr;  // partial-coefficient images [mode][chunk][block of 128][128 x 2C]
   uint16_t* chat = nullptr;
 };
 
@@ -261,7 +261,7 @@ __global__ void tc_cast_image_kernel(int rows, int cols, const float* __restrict
   out[kmajor_off(r, k, 128, cols * 16) / 2] = f2h16(in[i], bf16);
 }
 
-// Rr[mode][(o,t')][(i,t)] from R[mode][i][o][re/im]
+// Rr[mode]: image (K-major, 2C x 2C) of the real form [(o,t')][(i,t)] of R[mode][i][o][re/im]
 __global__ void tc_rr_kernel(int C, int nmodes, const float* __restrict__ R, uint16_t* __restrict__ Rr, bool bf16) {
   const size_t total = (size_t)nmodes * 4 * C * C;
   const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
@@ -275,7 +275,7 @@ __global__ void tc_rr_kernel(int C, int nmodes, const float* __restrict__ R, uin
   float v;
   if (tp == 0) v = t == 0 ? re : -im;
   else v = t == 0 ? im : re;
-  Rr[idx] = f2h16(v, bf16);
+  Rr[(size_t)mode * C2 * C2 + kmajor_off(row, col, 128, C2 * 16) / 2] = f2h16(v, bf16);
 }
 
 static void free_prec(TcPrecision& p) {
@@ -442,24 +442,29 @@ __global__ void tc_lift_kernel(TcGeom g, const double* __restrict__ r, const flo
   }
 }
 
-// Truncated analysis of one grid-column chunk of one instance; writes FP32 partial sums
-// part[b][chunk][mode = j*Ky + k2][c][re/im].
+// Truncated analysis of one grid-column chunk of one instance; writes its 16-bit partial
+// coefficients into the mode-mixing operand images (see tc_mix_kernel).
 //
 // Stage Q runs over steps s = (m-tile, q chunk); an m-tile is 128/C grid columns x C channels
 // (M) and a q chunk QC rows (K). Its operand is copied straight from the tile-major
 // activations: for N < 128 one bulk copy of (128/C)/PT consecutive tiles, for N >= 128 one
 // copy of QC rows per (column, 8-channel group). M groups of 8 channels are ordered
-// (tile u, channel group cg, column within the tile pl) and sit QC*16 bytes apart. Thread 0
-// issues copies and MMAs through a three-slot ring; the two Z accumulators alternate by
-// m-tile so that one m-tile is read back while the next one's MMAs run.
+// (tile u, channel group cg, column within the tile pl) and sit QC*16 bytes apart.
+// Warp-specialised: warps 0-3 read the Z accumulators back (two TMEM slots alternating by
+// m-tile) and store the result; lane 0 of warp 4 issues the MMAs and lane 0 of warp 5 the
+// bulk copies, through a three-slot ring; the roles meet only on mbarriers.
+constexpr int kAnaThreads = 192;
 template <int C>
-__global__ void __launch_bounds__(kTcThreads, 2)
-    tc_analysis_kernel(TcGeom g, bool bf16, const int* __restrict__ active, const uint16_t* __restrict__ v,
-                       const uint16_t* __restrict__ E2, const uint16_t* __restrict__ G, float* __restrict__ part,
+__global__ void __launch_bounds__(kAnaThreads, 2)
+    tc_analysis_kernel(TcGeom g, int nbt, bool bf16, const int* __restrict__ active, const uint16_t* __restrict__ v,
+                       const uint16_t* __restrict__ E2, const uint16_t* __restrict__ G, uint16_t* __restrict__ part,
                        int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int NS = 3;
-  __shared__ uint64_t full[NS], mmaq[NS], prob, mbarP;
+  // full[s] step copied in; sfree[s] its MMAs done; zfull[z] / zempty[z] Z slot ready / read
+  // back (4 warp arrivals); prob prologue copies; apready stage-P operand complete (4); pfull
+  // stage-P accumulators ready
+  __shared__ uint64_t full[NS], sfree[NS], zfull[2], zempty[2], prob, apready, pfull;
   __shared__ uint32_t tbase_s;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(active, b)) return;
@@ -475,19 +480,25 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const uint32_t SBO_E = QC * 16, SBO_A = QC * 16, SBO_P = 2 * PC * 16, SBO_G = 2 * PC * 16;
   const uint32_t tcols = (64 + (g.MP / 128) * g.NPM) <= 256 ? 256u : 512u;
   if (warp == 0) tmem_alloc(&tbase_s, tcols);
-  if (tid == 0) {
+  if (tid == 128) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
-      mbar_init(&mmaq[i], 1);
+      mbar_init(&sfree[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&zfull[i], 1);
+      mbar_init(&zempty[i], 4);
     }
     mbar_init(&prob, 1);
-    mbar_init(&mbarP, 1);
+    mbar_init(&apready, 4);
+    mbar_init(&pfull, 1);
   }
   // zero the padding rows of sAP
-  for (int idx = tid; idx < (g.MP - Ky * C) * (2 * PC / 8); idx += kTcThreads) {
+  for (int idx = tid; idx < (g.MP - Ky * C) * (2 * PC / 8); idx += kAnaThreads) {
     const int row = Ky * C + idx / (2 * PC / 8), kc = idx % (2 * PC / 8);
     *reinterpret_cast<uint4*>(sAP + kmajor_off(row, kc * 8, 128, SBO_P)) = make_uint4(0, 0, 0, 0);
   }
+  fence_smem_to_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
@@ -497,126 +508,132 @@ __global__ void __launch_bounds__(kTcThreads, 2)
   const int cols_mt = 128 / C;  // grid columns per m-tile
   const int mtiles = PC / cols_mt;
   const int nsteps = mtiles * qchunks;
-  const uint16_t* vb = v + (size_t)b * N * N * C;
-  constexpr uint32_t idQ = idesc_f16(128, 32, true, true, false);
-  constexpr uint32_t idQh = idesc_f16(128, 32, false, true, false);
-  // thread 0: copies of step s into ring slot buf
-  auto stage = [&](int s, int buf) {
-    const int mt = s / qchunks, qc = s % qchunks;
-    const int pm = p0 + mt * cols_mt;  // first grid column of the m-tile
-    mbar_expect_tx(&full[buf], AB + (qchunks > 1 ? E2B : 0));
-    if (qchunks > 1) bulk_g2s(sE2 + buf * E2B, E2 + (size_t)qc * 32 * QC, E2B, &full[buf]);
-    uint8_t* dst = sA + buf * AB;
-    if (N < 128) {
-      bulk_g2s(dst, vb + (size_t)(pm / PT) * 128 * C, AB, &full[buf]);
-    } else {
-      const int q0 = qc * QC, qt = q0 / 128, ql = q0 % 128;
-      for (int u = 0; u < cols_mt; ++u)
-        for (int cg = 0; cg < C / 8; ++cg)
-          bulk_g2s(dst + (u * (C / 8) + cg) * QC * 16, vb + (size_t)(qt * N + pm + u) * 128 * C + cg * 1024 + ql * 8,
-                   QC * 16, &full[buf]);
-    }
-  };
-  // all threads: read Z of the m-tile that ends at step s: lane M -> (column, channel),
-  // columns (k2, t) -> sAP[(k2, c)][(p, t)]
-  auto readback = [&](int s) -> bool {
-    const bool w = mbar_wait(&mmaq[s % NS], (s / NS) & 1);
-    fence_after_sync();
-    if (!w) return false;
-    const int mt = s / qchunks;
-    const uint32_t tq = tQ + (mt & 1) * 32;
-    const int M = warp * 32 + lane, Gi = M >> 3;
-    const int u = Gi / ((C / 8) * PT), cg = (Gi / PT) % (C / 8), pl2 = Gi % PT;
-    const int pl = mt * cols_mt + u * PT + pl2, c = cg * 8 + (M & 7);
-    float z[32];
-    float tmp[16];
-    tmem_ld16(tq + ((uint32_t)(warp * 32) << 16), tmp);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) z[i] = tmp[i];
-    tmem_ld16(tq + ((uint32_t)(warp * 32) << 16) + 16, tmp);
-#pragma unroll
-    for (int i = 0; i < 16; ++i) z[16 + i] = tmp[i];
-#pragma unroll
-    for (int k2 = 0; k2 < 16; ++k2) {  // Ky <= 16: static indices keep z in registers
-      if (k2 < Ky) {
-        const int row = k2 * C + c;
-        *reinterpret_cast<uint32_t*>(sAP + kmajor_off(row, 2 * pl, 128, SBO_P)) =
-            pack2(z[2 * k2], z[2 * k2 + 1], bf16);
-      }
-    }
-    return true;
-  };
+  const int ptiles = g.MP / 128;
   bool ok = true;
-  bool pro_pending = false;
-  int issued = 0, loads_waited = 0, mmas = 0;  // thread-0 bookkeeping (drained on the error path)
-  if (tid == 0) {
-    mbar_expect_tx(&prob, GB + (qchunks == 1 ? E2B : 0));
-    bulk_g2s(sG, G + (size_t)chunk * g.NPM * 2 * PC, GB, &prob);
-    if (qchunks == 1) bulk_g2s(sE2, E2, E2B, &prob);
-    for (; issued < nsteps && issued < 2; ++issued) stage(issued, issued);
-    ok = mbar_wait(&prob, 0);
-    pro_pending = !ok;
-  }
-  for (int s = 0; s < nsteps; ++s) {
-    const int buf = s % NS, mt = s / qchunks, qc = s % qchunks;
-    // the Z slot written by this step was read back (m-tile mt-2) before this barrier
-    fence_before_sync();
-    ok = __syncthreads_and(ok);
-    fence_after_sync();
-    if (!ok) break;
-    if (tid == 0) {
-      ok = mbar_wait(&full[buf], (s / NS) & 1);
-      if (ok) {
-        loads_waited = s + 1;
+  if (warp == 4) {
+    // ================================ MMA issuer (one lane) ============================
+    if (lane == 0) {
+      int mmas = 0;
+      bool p_pending = false;
+      const uint32_t idQ = idesc_f16(128, 32, bf16, true, false);
+      ok = mbar_wait(&prob, 0);
+      for (int s = 0; s < nsteps && ok; ++s) {
+        const int buf = s % NS, mt = s / qchunks, qc = s % qchunks;
+        ok = mbar_wait(&full[buf], (s / NS) & 1);
+        if (ok && qc == 0 && mt >= 2) ok = mbar_wait(&zempty[mt & 1], ((mt >> 1) - 1) & 1);
+        if (!ok) break;
+        fence_after_sync();
         const uint32_t tq = tQ + (mt & 1) * 32;
         const uint32_t sa = smem_addr(sA + buf * AB);
         const uint32_t e2 = smem_addr(sE2 + (qchunks > 1 ? buf * E2B : 0));
         for (int ks = 0; ks < QC / 16; ++ks)
-          mma(tq, desc(sa + ks * 256, 128, SBO_A), desc(e2 + ks * 256, 128, SBO_E), bf16 ? idQ : idQh, qc > 0 || ks > 0);
-        commit(&mmaq[buf]);
+          mma(tq, desc(sa + ks * 256, 128, SBO_A), desc(e2 + ks * 256, 128, SBO_E), idQ, qc > 0 || ks > 0);
+        commit(&sfree[buf]);
+        if (qc == qchunks - 1) commit(&zfull[mt & 1]);
         mmas = s + 1;
       }
-      if (ok && issued < nsteps) {
-        const int nb = issued % NS;  // slot of step s-1, whose MMA must have read it
-        if (s >= 1) ok = mbar_wait(&mmaq[nb], ((s - 1) / NS) & 1);
-        if (ok) {
-          stage(issued, nb);
-          ++issued;
+      if (ok) ok = mbar_wait(&apready, 0);  // every Z read back into sAP
+      if (ok) {
+        fence_after_sync();
+        const uint32_t id = idesc_f16(128, g.NPM, bf16, false, false);
+        for (int pt = 0; pt < ptiles; ++pt)
+          for (int ks = 0; ks < 2 * PC / 16; ++ks) {
+            const uint64_t ad = desc(smem_addr(sAP) + pt * 16 * SBO_P + ks * 2 * 128, 128, SBO_P);
+            const uint64_t bd = desc(smem_addr(sG) + ks * 2 * 128, 128, SBO_G);
+            mma(tP + pt * g.NPM, ad, bd, id, ks > 0);
+          }
+        commit(&pfull);
+        p_pending = true;
+      }
+      if (!ok) {
+        // error path: let the MMAs this block started finish (bounded)
+        for (int u = mmas > NS ? mmas - NS : 0; u < mmas; ++u) mbar_wait(&sfree[u % NS], (u / NS) & 1);
+        atomicExch(err, 1);
+      }
+      if (p_pending) mbar_wait(&pfull, 0);  // (the read-back warps wait on it too)
+    }
+  } else if (warp == 5) {
+    // ================================ load issuer (one lane) ===========================
+    if (lane == 0) {
+      const uint16_t* vb = v + (size_t)b * N * N * C;
+      int loads = 0;
+      auto stage = [&](int s) {
+        const int buf = s % NS, mt = s / qchunks, qc = s % qchunks;
+        const int pm = p0 + mt * cols_mt;  // first grid column of the m-tile
+        mbar_expect_tx(&full[buf], AB + (qchunks > 1 ? E2B : 0));
+        if (qchunks > 1) bulk_g2s(sE2 + buf * E2B, E2 + (size_t)qc * 32 * QC, E2B, &full[buf]);
+        uint8_t* dst = sA + buf * AB;
+        if (N < 128) {
+          bulk_g2s(dst, vb + (size_t)(pm / PT) * 128 * C, AB, &full[buf]);
+        } else {
+          const int q0 = qc * QC, qt = q0 / 128, ql = q0 % 128;
+          for (int u = 0; u < cols_mt; ++u)
+            for (int cg = 0; cg < C / 8; ++cg)
+              bulk_g2s(dst + (u * (C / 8) + cg) * QC * 16,
+                       vb + (size_t)(qt * N + pm + u) * 128 * C + cg * 1024 + ql * 8, QC * 16, &full[buf]);
+        }
+        loads = s + 1;
+      };
+      mbar_expect_tx(&prob, GB + (qchunks == 1 ? E2B : 0));
+      bulk_g2s(sG, G + (size_t)chunk * g.NPM * 2 * PC, GB, &prob);
+      if (qchunks == 1) bulk_g2s(sE2, E2, E2B, &prob);
+      for (int s = 0; s < nsteps && ok; ++s) {
+        if (s >= NS) ok = mbar_wait(&sfree[s % NS], ((s / NS) - 1) & 1);  // step s-NS's MMAs read the slot
+        if (ok) stage(s);
+      }
+      if (!ok) {
+        for (int u = loads > NS ? loads - NS : 0; u < loads; ++u) mbar_wait(&full[u % NS], (u / NS) & 1);
+        atomicExch(err, 1);
+      }
+      mbar_wait(&prob, 0);
+    }
+  } else {
+    // ================================ read-back warps 0-3 ==============================
+    // Z of m-tile mt: lane M -> (column, channel), columns (k2, t) -> sAP[(k2, c)][(p, t)]
+    const int M = warp * 32 + lane, Gi = M >> 3;
+    const int u = Gi / ((C / 8) * PT), cg = (Gi / PT) % (C / 8), pl2 = Gi % PT;
+    const int c = cg * 8 + (M & 7);
+    for (int mt = 0; mt < mtiles && ok; ++mt) {
+      ok = mbar_wait(&zfull[mt & 1], (mt >> 1) & 1);
+      if (!ok) break;
+      fence_after_sync();
+      const uint32_t tq = tQ + (mt & 1) * 32 + ((uint32_t)(warp * 32) << 16);
+      float z[32];
+      float tmp[16];
+      tmem_ld16(tq, tmp);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) z[i] = tmp[i];
+      tmem_ld16(tq + 16, tmp);
+#pragma unroll
+      for (int i = 0; i < 16; ++i) z[16 + i] = tmp[i];
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&zempty[mt & 1]);
+      const int pl = mt * cols_mt + u * PT + pl2;
+#pragma unroll
+      for (int k2 = 0; k2 < 16; ++k2) {  // Ky <= 16: static indices keep z in registers
+        if (k2 < Ky) {
+          const int row = k2 * C + c;
+          *reinterpret_cast<uint32_t*>(sAP + kmajor_off(row, 2 * pl, 128, SBO_P)) =
+              pack2(z[2 * k2], z[2 * k2 + 1], bf16);
         }
       }
     }
-    // the previous m-tile is read back while this step's MMA runs
-    if (s >= 1 && (s - 1) % qchunks == qchunks - 1) ok = readback(s - 1) && ok;
-  }
-  fence_before_sync();
-  ok = __syncthreads_and(ok);
-  fence_after_sync();
-  if (ok && nsteps > 0) ok = readback(nsteps - 1);
-  fence_smem_to_async();
-  fence_before_sync();
-  ok = __syncthreads_and(ok);
-  fence_after_sync();
-  bool p_pending = false;
-  if (ok) {
-    const int ptiles = g.MP / 128;
-    if (tid == 0) {
-      const uint32_t id = idesc_f16(128, g.NPM, bf16, false, false);
-      for (int pt = 0; pt < ptiles; ++pt)
-        for (int ks = 0; ks < 2 * PC / 16; ++ks) {
-          const uint64_t ad = desc(smem_addr(sAP) + pt * 16 * SBO_P + ks * 2 * 128, 128, SBO_P);
-          const uint64_t bd = desc(smem_addr(sG) + ks * 2 * 128, 128, SBO_G);
-          mma(tP + pt * g.NPM, ad, bd, id, ks > 0);
-        }
-      commit(&mbarP);
-    }
-    ok = mbar_wait(&mbarP, 0);
-    p_pending = !ok;
-    fence_after_sync();
     if (ok) {
-      float* pb = part + ((size_t)b * g.nchunks + chunk) * g.nmodes * C * 2;
+      fence_smem_to_async();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&apready);
+      ok = mbar_wait(&pfull, 0);
+      fence_after_sync();
+    }
+    if (ok) {
+      // P row (k2, c), columns (j, t') -> image of mode j*Ky + k2, row b % 128, K (c, t')
+      const size_t img = (size_t)128 * 2 * C;  // elements per image
+      const int bt = b / 128, br = b % 128;
       for (int pt = 0; pt < ptiles; ++pt) {
         const int row = pt * 128 + warp * 32 + lane;
-        const int k2 = row / C, c = row % C;
+        const int k2 = row / C, cc = row % C;
+        const uint32_t off = kmajor_off(br, 2 * cc, 128, 2 * C * 16) / 2;
         for (int c0 = 0; c0 < g.NPM; c0 += 16) {
           float val[16];
           tmem_ld16(tP + pt * g.NPM + c0 + ((uint32_t)(warp * 32) << 16), val);
@@ -625,8 +642,9 @@ __global__ void __launch_bounds__(kTcThreads, 2)
             for (int i = 0; i < 16; i += 2) {
               const int j = (c0 + i) >> 1;
               if (j < 2 * g.M) {
-                float2 w2 = make_float2(val[i], val[i + 1]);
-                *reinterpret_cast<float2*>(pb + ((size_t)(j * Ky + k2) * C + c) * 2) = w2;
+                const int mode = j * Ky + k2;
+                uint16_t* dst = part + (((size_t)mode * g.nchunks + chunk) * nbt + bt) * img + off;
+                *reinterpret_cast<uint32_t*>(dst) = pack2(val[i], val[i + 1], bf16);
               }
             }
           }
@@ -634,84 +652,93 @@ __global__ void __launch_bounds__(kTcThreads, 2)
       }
     }
   }
-  if (!ok && tid == 0) {
-    // error path: let every copy and MMA this block started finish (bounded) before the
-    // block releases its shared and tensor memory
-    if (pro_pending) mbar_wait(&prob, 0);
-    for (int u = loads_waited; u < issued; ++u) mbar_wait(&full[u % NS], (u / NS) & 1);
-    for (int u = mmas > NS ? mmas - NS : 0; u < mmas; ++u) mbar_wait(&mmaq[u % NS], (u / NS) & 1);
-    if (p_pending) mbar_wait(&mbarP, 0);
-    atomicExch(err, 1);
-  }
   fence_before_sync();
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, tcols);
 }
 
 // Per-mode complex channel mixing across instances: rows = instances (128 per CTA).
-// Output: for each instance the byte image (MP x KXP, 16-bit, zero padded) of the synthesis
-// stage-1 A operand in its MN-major shared-memory layout, element (m = (k2, c), k = (j, re/im));
-// each instance's 8 consecutive outputs c of one (mode, re/im) form one 16-byte run.
+// Input: for each column chunk the 16-bit partial-coefficient image of this (mode, block of
+// 128 instances), 128 x 2C K-major (K = (c, re/im)); the MMA sums the chunks in its FP32
+// accumulator. Output: for each instance the byte image (MP x KXP, 16-bit, zero padded) of
+// the synthesis stage-1 A operand in its MN-major shared-memory layout, element
+// (m = (k2, c), k = (j, re/im)); each instance's 8 consecutive outputs c of one
+// (mode, re/im) form one 16-byte run.
+constexpr int kMixSlots = 4;
 template <int C>
 __global__ void __launch_bounds__(kTcThreads, 4)
-    tc_mix_kernel(TcGeom g, int B, bool bf16, const int* __restrict__ active, const float* __restrict__ part,
-                  const uint16_t* __restrict__ Rr, uint16_t* __restrict__ chat, int* __restrict__ err) {
+    tc_mix_kernel(TcGeom g, int B, int nbt, bool bf16, const int* __restrict__ active,
+                  const uint16_t* __restrict__ part, const uint16_t* __restrict__ Rr, uint16_t* __restrict__ chat,
+                  int* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ uint64_t mbar;
+  __shared__ uint64_t full[kMixSlots], sfree[kMixSlots], rbar, accb;
   __shared__ uint32_t tbase_s;
   __shared__ int any_active;
   constexpr int C2 = 2 * C;
-  const int mode = blockIdx.x, b0 = blockIdx.y * 128;
+  constexpr uint32_t AB = 128 * C2 * 2, RB = C2 * C2 * 2, SBO = C2 * 16;
+  constexpr uint32_t TCOLS = C2 < 32 ? 32 : C2;
+  const int mode = blockIdx.x, bt = blockIdx.y, b0 = bt * 128;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) any_active = 0;
   __syncthreads();
   if (b0 + tid < B && !tc_inactive(active, b0 + tid)) any_active = 1;
   __syncthreads();
   if (!any_active) return;  // every instance of this tile has stopped
-  uint8_t* sA = smem;              // 128 x C2, K-major, SBO = C2*16
-  uint8_t* sB = sA + 128 * C2 * 2; // C2 x C2,  K-major
-  constexpr uint32_t SBO = C2 * 16;
-  if (warp == 0) tmem_alloc(&tbase_s, C2 < 32 ? 32 : C2);
-  if (tid == 0) mbar_init(&mbar, 1);
-  {
-    // warp w loads rows 32w..32w+31; a row (one instance's C2 values) is one coalesced read
-    // per chunk, the chunks are summed in order
-#pragma unroll 8
-    for (int r = 0; r < 32; ++r) {
-      const int row = warp * 32 + r;
-      const int b = b0 + row;
-      float2 acc = make_float2(0.f, 0.f);
-      if (b < B && 2 * lane < C2) {
-        for (int ch = 0; ch < g.nchunks; ++ch) {
-          const float2 v = *reinterpret_cast<const float2*>(part + (((size_t)b * g.nchunks + ch) * g.nmodes + mode) * C2 +
-                                                            2 * lane);
-          acc.x += v.x;
-          acc.y += v.y;
-        }
-      }
-      if (2 * lane < C2)
-        *reinterpret_cast<uint32_t*>(sA + kmajor_off(row, 2 * lane, 128, SBO)) = pack2(acc.x, acc.y, bf16);
+  const int nch = g.nchunks, MS = nch < kMixSlots ? nch : kMixSlots;
+  uint8_t* sR = smem;       // C2 x C2 image, K-major
+  uint8_t* sA = smem + RB;  // MS slots of 128 x C2 images, K-major
+  if (warp == 0) tmem_alloc(&tbase_s, TCOLS);
+  if (tid == 0) {
+    for (int i = 0; i < MS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&sfree[i], 1);
     }
-    const uint16_t* Rm = Rr + (size_t)mode * C2 * C2;
-    for (int idx = tid; idx < C2 * C2 / 8; idx += kTcThreads) {
-      const int r = idx / (C2 / 8), kc = idx % (C2 / 8);
-      cp_async16(sB + kmajor_off(r, kc * 8, 128, SBO), Rm + r * C2 + kc * 8);
-    }
-    cp_async_commit();
-    cp_async_wait_all();
+    mbar_init(&rbar, 1);
+    mbar_init(&accb, 1);
   }
-  fence_smem_to_async();
   fence_before_sync();
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = tbase_s;
+  bool ok = true;
   if (tid == 0) {
+    const uint16_t* pm = part + (size_t)mode * nch * nbt * 128 * C2;
+    auto load = [&](int ch) {
+      mbar_expect_tx(&full[ch % MS], AB);
+      bulk_g2s(sA + (ch % MS) * AB, pm + ((size_t)ch * nbt + bt) * 128 * C2, AB, &full[ch % MS]);
+    };
+    mbar_expect_tx(&rbar, RB);
+    bulk_g2s(sR, Rr + (size_t)mode * C2 * C2, RB, &rbar);
+    for (int ch = 0; ch < MS; ++ch) load(ch);
+    ok = mbar_wait(&rbar, 0);
     const uint32_t id = idesc_f16(128, C2, bf16, false, false);
-    for (int ks = 0; ks < C2 / 16; ++ks)
-      mma(tbase, desc(smem_addr(sA) + ks * 256, 128, SBO), desc(smem_addr(sB) + ks * 256, 128, SBO), id, ks > 0);
-    commit(&mbar);
+    int issued = MS, mmas = 0;
+    for (int ch = 0; ch < nch && ok; ++ch) {
+      ok = mbar_wait(&full[ch % MS], (ch / MS) & 1);
+      if (!ok) break;
+      const uint32_t sa = smem_addr(sA + (ch % MS) * AB);
+      for (int ks = 0; ks < C2 / 16; ++ks)
+        mma(tbase, desc(sa + ks * 256, 128, SBO), desc(smem_addr(sR) + ks * 256, 128, SBO), id, ch > 0 || ks > 0);
+      commit(&sfree[ch % MS]);
+      mmas = ch + 1;
+      if (issued < nch) {
+        ok = mbar_wait(&sfree[ch % MS], (ch / MS) & 1);  // this slot's MMAs have read it
+        if (ok) load(issued++);
+      }
+    }
+    if (ok) {
+      commit(&accb);
+    } else {
+      for (int u = issued > MS ? issued - MS : 0; u < issued; ++u) mbar_wait(&full[u % MS], (u / MS) & 1);
+      if (mmas > 0) mbar_wait(&sfree[(mmas - 1) % MS], ((mmas - 1) / MS) & 1);
+      atomicExch(err, 1);
+      mbar_arrive(&accb);  // release the other threads (they skip the read-back)
+    }
   }
-  const bool ok = mbar_wait(&mbar, 0);
+  {
+    const bool w = mbar_wait(&accb, 0);
+    ok = __syncthreads_and(ok && w);
+  }
   fence_after_sync();
   if (ok) {
     const int b = b0 + warp * 32 + lane;
@@ -742,12 +769,10 @@ __global__ void __launch_bounds__(kTcThreads, 4)
                                pack2(val[2 * o0 + 12 + t], val[2 * o0 + 14 + t], bf16));
       }
     }
-  } else if (tid == 0) {
-    atomicExch(err, 1);
   }
   fence_before_sync();
   __syncthreads();
-  if (warp == 0) tmem_dealloc(tbase, C2 < 32 ? 32 : C2);
+  if (warp == 0) tmem_dealloc(tbase, TCOLS);
 }
 
 struct SynArgs {
@@ -1132,7 +1157,10 @@ static size_t analysis_smem(const TcGeom& g) {
   return (size_t)ne2 * 32 * g.QC * 2 + (size_t)3 * 128 * g.QC * 2 + (size_t)g.MP * 2 * g.PC * 2 +
          (size_t)g.NPM * 2 * g.PC * 2;
 }
-static size_t mix_smem(int C) { return (size_t)128 * 2 * C * 2 + (size_t)4 * C * C * 2; }
+static size_t mix_smem(const TcGeom& g) {
+  const int ms = g.nchunks < kMixSlots ? g.nchunks : kMixSlots;
+  return (size_t)4 * g.C * g.C * 2 + (size_t)ms * 128 * 2 * g.C * 2;
+}
 // Tile rings of the synthesis kernel: the deepest input ring (2 .. 4 slots, 2 output slots)
 // that keeps two blocks per SM; 4 + 2 (one block per SM) when none does.
 static void synthesis_rings(const TcGeom& g, int& din, int& dout) {
@@ -1154,7 +1182,8 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   TcPrecision& P = T.prec[fp16 ? 1 : 0];
   const int B = op->B;
   const size_t n = op->n;
-  const size_t need_v = (size_t)B * n * C, need_part = (size_t)B * g.nchunks * g.nmodes * C * 2,
+  const int nbt = ceil_div(B, 128);
+  const size_t need_v = (size_t)B * n * C, need_part = (size_t)g.nmodes * g.nchunks * nbt * 128 * 2 * C,
                need_chat = (size_t)B * g.MP * g.KXP;
   if (T.cap_v < need_v || T.cap_part < need_part || T.cap_chat < need_chat) {
     if (T.va) cudaFree(T.va);
@@ -1165,7 +1194,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     T.part = nullptr;
     T.cap_v = T.cap_part = T.cap_chat = 0;
     if (cudaMalloc(&T.va, need_v * 2) != cudaSuccess || cudaMalloc(&T.vb, need_v * 2) != cudaSuccess ||
-        cudaMalloc(&T.part, need_part * 4) != cudaSuccess || cudaMalloc(&T.chat, need_chat * 2) != cudaSuccess) {
+        cudaMalloc(&T.part, need_part * 2) != cudaSuccess || cudaMalloc(&T.chat, need_chat * 2) != cudaSuccess) {
       cudaGetLastError();
       set_last_error("tensor-core preconditioner workspace: out of device memory");
       return FCGNO_ENOMEM;
@@ -1192,7 +1221,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   FCGNO_LAUNCHED();
   int din, dout;
   synthesis_rings(g, din, dout);
-  const size_t sa = analysis_smem(g), ss = synthesis_bytes(g, g.SPC, din, dout), sm = mix_smem(C);
+  const size_t sa = analysis_smem(g), ss = synthesis_bytes(g, g.SPC, din, dout), sm = mix_smem(g);
   // raise the dynamic shared-memory limit only when a larger plan appears (not a stream
   // operation; the first solve iteration runs eagerly, before any graph capture)
   // (the shared-memory carveout is pinned to its maximum so that two blocks of each kernel
@@ -1214,14 +1243,14 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   for (int l = 0; l < d.layers; ++l) {
     {
       TraceScope ts("tc_analysis", st);
-      tc_analysis_kernel<C><<<dim3(g.nchunks, B), kTcThreads, sa, st>>>(g, bf16, active, cur, tab->E2, tab->G,
-                                                                       T.part, d_err);
+      tc_analysis_kernel<C><<<dim3(g.nchunks, B), kAnaThreads, sa, st>>>(g, nbt, bf16, active, cur, tab->E2, tab->G,
+                                                                        T.part, d_err);
     }
     FCGNO_LAUNCHED();
     {
       TraceScope ts("tc_mix", st);
-      tc_mix_kernel<C><<<dim3(g.nmodes, ceil_div(B, 128)), kTcThreads, sm, st>>>(g, B, bf16, active, T.part,
-                                                                                P.Rr[l], T.chat, d_err);
+      tc_mix_kernel<C><<<dim3(g.nmodes, nbt), kTcThreads, sm, st>>>(g, B, nbt, bf16, active, T.part, P.Rr[l],
+                                                                   T.chat, d_err);
     }
     FCGNO_LAUNCHED();
     SynArgs s{};
