@@ -467,6 +467,19 @@ def notay_loss_and_grad(params: dict, desc, ks, rs, es):
     through the decoder, the Fourier layers (pointwise path, the per-mode mixing and the
     adjoints of the truncated transforms) and the encoder.
     """
+    return _loss_and_grad(params, desc, ks, rs, es, energy=True)
+
+
+def l2_loss_and_grad(params: dict, desc, ks, rs, es):
+    """The L2 loss in error form (the ablation loss of Section 3.1, compared with Eq. (11) in
+    Section 3.4): L = mean_j ||z_j - e_j||_2 / ||e_j||_2, and its gradient in blob order.
+    dL/dz_j = (z_j - e_j) / (||z_j - e_j||_2 ||e_j||_2) / batch; the chain rule below dz is the
+    same as for Eq. (11)."""
+    return _loss_and_grad(params, desc, ks, rs, es, energy=False)
+
+
+def _loss_and_grad(params: dict, desc, ks, rs, es, energy: bool):
+    """Shared reverse mode of the two losses: the norm is the A-norm (energy) or the 2-norm."""
     L = len(params["layers"])
     grads = {k: np.zeros_like(params[k]) for k in ("lift_w", "lift_b", "proj1_w", "proj1_b", "proj2_w", "proj2_b")}
     glayers = [{"w": np.zeros_like(p["w"]), "b": np.zeros_like(p["b"]), "r": np.zeros_like(p["r"])}
@@ -476,9 +489,9 @@ def notay_loss_and_grad(params: dict, desc, ks, rs, es):
     for k, r, e in zip(ks, rs, es):
         S = _forward_saved(params, desc, r, np.log(k))
         d = S["z"] - e
-        Ad = apply_A(k, d)
+        Ad = apply_A(k, d) if energy else d
         nd = math.sqrt(float(np.sum(d * Ad)))
-        ne = energy_norm(k, e)
+        ne = energy_norm(k, e) if energy else float(np.linalg.norm(e))
         loss += nd / ne / B
         dz = Ad / (nd * ne) / B
         dzt = S["scale"] * dz
