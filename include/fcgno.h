@@ -165,6 +165,21 @@ fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x
 fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
                               int batch, fcgno_prec prec, float* loss, float* grad, void* stream);
 
+/* Training losses. FCGNO_LOSS_ENERGY is Eq. (11) in error form (the A-norm); FCGNO_LOSS_L2
+ * is the paper's ablation loss in error form, mean_b ||z_b - e_b||_2 / ||e_b||_2 (defined
+ * beside Eq. (11) in Section 2.4.1 and compared with it in Section 3.4). */
+typedef enum {
+  FCGNO_LOSS_ENERGY = 0,
+  FCGNO_LOSS_L2 = 1
+} fcgno_loss;
+
+/* fcgno_train_step with a choice of loss: identical arguments, outputs and errors, plus
+ * `loss_kind` (a fcgno_loss; other values: FCGNO_EINVAL). With FCGNO_LOSS_L2 no operator
+ * is applied in the loss; the op still supplies log k and the grid. */
+fcgno_status fcgno_train_step_loss(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
+                                   int batch, fcgno_prec prec, int loss_kind, float* loss, float* grad,
+                                   void* stream);
+
 /* Serving buckets (continuous batching of independent solves of one grid size). A bucket
  * keeps `capacity` solves resident (operator, iterate, right-hand side and Krylov state of
  * Algorithm 1) and advances all running slots together, `iters_per_step` iterations per

@@ -246,8 +246,9 @@ extern "C" fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, 
   return rc;
 }
 
-extern "C" fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
-                                         int batch, fcgno_prec prec, float* loss, float* grad, void* stream) {
+extern "C" fcgno_status fcgno_train_step_loss(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
+                                              int batch, fcgno_prec prec, int loss_kind, float* loss, float* grad,
+                                              void* stream) {
   if (!model || !op || !r || !e || !loss || !grad || batch != op->B) {
     set_last_error("fcgno_train_step: null argument or batch != op batch");
     return FCGNO_EINVAL;
@@ -256,11 +257,21 @@ extern "C" fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, con
     set_last_error("fcgno_train_step: precision must be FCGNO_FP32 or FCGNO_FP64");
     return FCGNO_EINVAL;
   }
+  if (loss_kind != FCGNO_LOSS_ENERGY && loss_kind != FCGNO_LOSS_L2) {
+    set_last_error("fcgno_train_step_loss: loss_kind must be FCGNO_LOSS_ENERGY or FCGNO_LOSS_L2");
+    return FCGNO_EINVAL;
+  }
   if (op->N < 2 * model->desc.modes) {
     set_last_error("fcgno_train_step: grid smaller than 2*modes");
     return FCGNO_EINVAL;
   }
-  return train_step_simt(model, op, r, e, loss, grad, prec == FCGNO_FP64, (cudaStream_t)stream);
+  return train_step_simt(model, op, r, e, loss, grad, prec == FCGNO_FP64, loss_kind == FCGNO_LOSS_L2,
+                         (cudaStream_t)stream);
+}
+
+extern "C" fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
+                                         int batch, fcgno_prec prec, float* loss, float* grad, void* stream) {
+  return fcgno_train_step_loss(model, op, r, e, batch, prec, FCGNO_LOSS_ENERGY, loss, grad, stream);
 }
 
 extern "C" size_t fcgno_workspace_bytes(int N, int batch, int m_max, const fcgno_model_desc* desc, fcgno_prec prec) {

@@ -176,9 +176,9 @@ void no_workspace_free(fcgno_model* m);
 // Per-instance rms of r: rms[b] = sqrt(mean(r_b^2)).
 fcgno_status launch_rms(const double* r, int B, size_t n, double* rms, cudaStream_t st);
 
-// Training (energy-norm loss, Eq. (11)).
+// Training: energy-norm loss of Eq. (11), or (l2) the 2-norm ablation loss.
 fcgno_status train_step_simt(fcgno_model* m, fcgno_op* op, const double* r, const double* e,
-                             float* loss, float* grad, bool fp64, cudaStream_t st);
+                             float* loss, float* grad, bool fp64, bool l2, cudaStream_t st);
 
 inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 

@@ -586,7 +586,8 @@ __global__ void reduce_partials_kernel(int G, int Co, int Ci, const T* __restric
     gb[o] = (float)s;
 }
 
-// Energy-norm loss pieces: per instance (d, A d) and (e, A e) with d = z - e.
+// Loss pieces: per instance sqrt(d, Ad) and sqrt(e, Ae) with d = z - e; Ad = A d and Ae = A e
+// for the energy norm, Ad = d and Ae = e for the 2-norm.
 __global__ void loss_dots_kernel(size_t n, const double* __restrict__ d, const double* __restrict__ Ad,
                                  const double* __restrict__ e, const double* __restrict__ Ae, double* __restrict__ out) {
   __shared__ double scratch[64];
@@ -610,7 +611,7 @@ __global__ void diff_kernel(size_t total, const double* __restrict__ z, const do
   if (i < total) d[i] = z[i] - e[i];
 }
 
-// loss = mean_b ||d_b||_A / ||e_b||_A  (written as float to *loss)
+// loss = mean_b ||d_b|| / ||e_b||  (written as float to *loss)
 __global__ void loss_value_kernel(int B, const double* __restrict__ norms, float* __restrict__ loss) {
   if (threadIdx.x != 0) return;
   double s = 0.0;
@@ -618,7 +619,8 @@ __global__ void loss_value_kernel(int B, const double* __restrict__ norms, float
   *loss = (float)(s / B);
 }
 
-// dL/dzt[b][x] = h^2 rms_b * (1/B) * (A d)_x / (||d||_A ||e||_A)   (zt = z / (h^2 rms))
+// dL/dzt[b][x] = h^2 rms_b * (1/B) * (A d)_x / (||d|| ||e||)   (zt = z / (h^2 rms); A d -> d for
+// the 2-norm)
 template <typename T>
 __global__ void dzt_kernel(int B, size_t n, double hh, const double* __restrict__ Ad,
                            const double* __restrict__ norms, const double* __restrict__ rms, T* __restrict__ gzt) {
@@ -766,7 +768,7 @@ static fcgno_status outer_reduce(size_t npts, int Co, int Ci, const T* A, const 
 
 template <typename T>
 static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, const double* e, float* loss,
-                               float* grad, cudaStream_t st) {
+                               float* grad, bool l2, cudaStream_t st) {
   const fcgno_model_desc& d = m->desc;
   const int N = op->N, B = op->B, C = d.width, M = d.modes, Cp = d.proj_width, L = d.layers;
   const size_t n = op->n, pts = (size_t)B * n;
@@ -781,14 +783,19 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
   // forward with saves
   FCGNO_TRY(launch_rms(r, B, n, t.rms, st));
   FCGNO_TRY(forward_simt<T>(m, op, wbase, r, t.rms, nullptr, t.zbuf, s, &t, nullptr, st));
-  // loss (FP64): d = z - e, A d, A e
+  // loss (FP64): d = z - e, then A d and A e (energy norm, Eq. (11)) or d and e themselves
+  // (2-norm of the L2 ablation loss)
   double* dv = t.dvec;
-  double* Ad = t.dvec + pts;
-  double* Ae = t.dvec + 2 * pts;
+  const double* Ad = dv;
+  const double* Ae = e;
   diff_kernel<<<ceil_div(pts, 256), 256, 0, st>>>(pts, t.zbuf, e, dv);
   FCGNO_LAUNCHED();
-  FCGNO_TRY(launch_apply_A(op, dv, Ad, st));
-  FCGNO_TRY(launch_apply_A(op, e, Ae, st));
+  if (!l2) {
+    FCGNO_TRY(launch_apply_A(op, dv, t.dvec + pts, st));
+    FCGNO_TRY(launch_apply_A(op, e, t.dvec + 2 * pts, st));
+    Ad = t.dvec + pts;
+    Ae = t.dvec + 2 * pts;
+  }
   loss_dots_kernel<<<B, 256, 0, st>>>(n, dv, Ad, e, Ae, t.lossb);
   FCGNO_LAUNCHED();
   loss_value_kernel<<<1, 32, 0, st>>>(B, t.lossb, loss);
@@ -840,14 +847,14 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
 }
 
 fcgno_status train_step_simt(fcgno_model* m, fcgno_op* op, const double* r, const double* e, float* loss,
-                             float* grad, bool fp64, cudaStream_t st) {
+                             float* grad, bool fp64, bool l2, cudaStream_t st) {
   if (m->desc.width > 32 || m->desc.proj_width > 32 || 256 % m->desc.width != 0) {
     set_last_error("training supports width and proj_width <= 32 dividing 256");
     return FCGNO_EINVAL;
   }
   if (!m->ws) m->ws = new NoWorkspace();
-  if (fp64) return train_impl<double>(m, op, r, e, loss, grad, st);
-  return train_impl<float>(m, op, r, e, loss, grad, st);
+  if (fp64) return train_impl<double>(m, op, r, e, loss, grad, l2, st);
+  return train_impl<float>(m, op, r, e, loss, grad, l2, st);
 }
 
 }  // namespace fcgno

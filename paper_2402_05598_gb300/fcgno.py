@@ -17,6 +17,8 @@ _LIB_PATH = Path(__file__).resolve().parent / "libfcgno.so"
 FCGNO_OK, FCGNO_EINVAL, FCGNO_ENOMEM, FCGNO_ECUDA, FCGNO_ENOCONV, FCGNO_EBREAKDOWN, FCGNO_ETIMEOUT = range(7)
 FCGNO_FP64, FCGNO_BF16, FCGNO_FP16, FCGNO_FP32 = range(4)
 PREC = {"fp64": FCGNO_FP64, "bf16": FCGNO_BF16, "fp16": FCGNO_FP16, "fp32": FCGNO_FP32}
+FCGNO_LOSS_ENERGY, FCGNO_LOSS_L2 = range(2)
+LOSS = {"energy": FCGNO_LOSS_ENERGY, "l2": FCGNO_LOSS_L2}
 
 
 class fcgno_model_desc(Structure):
@@ -59,6 +61,7 @@ def _load():
         "fcgno_solve_jacobi": (c_int, [P, c_int, P, P, POINTER(fcgno_solve_opts), POINTER(fcgno_solve_info), P]),
         "fcgno_krylov_harvest": (c_int, [P, P, P, P, c_int, P, P, POINTER(fcgno_solve_info), P]),
         "fcgno_train_step": (c_int, [P, P, P, P, c_int, c_int, P, P, P]),
+        "fcgno_train_step_loss": (c_int, [P, P, P, P, c_int, c_int, c_int, P, P, P]),
         "fcgno_workspace_bytes": (c_size_t, [c_int, c_int, c_int, POINTER(fcgno_model_desc), c_int]),
         "fcgno_status_str": (c_char_p, [c_int]),
         "fcgno_last_error": (c_char_p, []),
@@ -85,7 +88,7 @@ lib = _load()
 EXPORTS = [
     "fcgno_assemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
-    "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_workspace_bytes", "fcgno_status_str",
+    "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss", "fcgno_workspace_bytes", "fcgno_status_str",
     "fcgno_last_error", "fcgno_launch_count", "fcgno_trace_set", "fcgno_trace_collect",
     "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
     "fcgno_bucket_destroy",
@@ -264,9 +267,15 @@ def krylov_harvest(op: Operator, b, x0, u_star, K, r_out, e_out, stream=None):
     return _info_list(info)
 
 
-def train_step(model: Model, op: Operator, r, e, loss, grad, prec="fp32", stream=None):
-    _check(lib.fcgno_train_step(model.handle, op.handle, _ptr(r), _ptr(e), op.B, PREC[prec], _ptr(loss), _ptr(grad),
-                                _stream(stream)), "fcgno_train_step")
+def train_step(model: Model, op: Operator, r, e, loss, grad, prec="fp32", stream=None, loss_kind="energy"):
+    """One step of Eq. (11) (loss_kind "energy") or of the L2 ablation loss ("l2")."""
+    if loss_kind == "energy":
+        _check(lib.fcgno_train_step(model.handle, op.handle, _ptr(r), _ptr(e), op.B, PREC[prec], _ptr(loss),
+                                    _ptr(grad), _stream(stream)), "fcgno_train_step")
+    else:
+        _check(lib.fcgno_train_step_loss(model.handle, op.handle, _ptr(r), _ptr(e), op.B, PREC[prec],
+                                         LOSS[loss_kind], _ptr(loss), _ptr(grad), _stream(stream)),
+               "fcgno_train_step_loss")
 
 
 def workspace_bytes(N, batch, m_max, desc, prec="bf16") -> int:

@@ -210,3 +210,29 @@ def diffusion_problem(N: int, seed: int):
     k = trig_polynomial(N, rng) + 10.0
     f = trig_polynomial(N, rng)
     return k, f
+
+
+# ------------------------------------------------------------------------------ datasets by name
+DATASETS = ("grf", "poisson", "diffusion")
+
+
+def dataset_problem(name: str, N: int, seed: int, sigma: float = 1.0, ell: float = 0.1):
+    """(k, f) of instance `seed` of a named family: "grf" (k = exp(GRF), f iid N(0,1)),
+    "poisson" or "diffusion" (the paper's datasets, Section 3.2)."""
+    if name == "grf":
+        return make_problem(N, seed, sigma, ell)
+    if name == "poisson":
+        return poisson_problem(N, seed)
+    if name == "diffusion":
+        return diffusion_problem(N, seed)
+    raise ValueError(f"unknown dataset {name!r}")
+
+
+def dataset_rhs(name: str, N: int, rng: np.random.Generator) -> np.ndarray:
+    """A right-hand side f ~ p_f of the named family (for the random-residual data of
+    Section 3.5: f is redrawn per sample, k stays the instance's)."""
+    if name == "grf":
+        return gaussian_rhs(N, rng)
+    if name in ("poisson", "diffusion"):
+        return trig_polynomial(N, rng)
+    raise ValueError(f"unknown dataset {name!r}")

@@ -6,6 +6,10 @@ u* is the same problem solved to a relative residual of 1e-12. The loss is Eq. (
 mean ||NO(r) - e||_A / ||e||_A, and its gradient comes from the library's hand-written
 backward (fcgno_train_step). PyTorch's Adam updates the FP32 master blob.
 
+Ablations (Sections 3.4-3.5): the L2 loss in error form instead of Eq. (11)
+(``loss_kind="l2"``), and random residuals instead of Krylov vectors (``data="random"``):
+u_i ~ N(0, I), f_i ~ p_f, r_i = f_i - A u_i, e_i = A^{-1} f_i - u_i.
+
 Batches hold one sample from each instance of a group of ``batch`` instances (one
 assembled operator per group); the sample index inside each instance's Krylov sequence is
 drawn at random every step.
@@ -32,9 +36,9 @@ class TrainResult:
 class KrylovData:
     """Harvested (r_i, e_i) pairs of one group of instances, resident on the device."""
 
-    def __init__(self, N, seeds, K, device, sigma=1.0, ell=0.1, x0_seed=12345, stream=None):
+    def __init__(self, N, seeds, K, device, sigma=1.0, ell=0.1, x0_seed=12345, stream=None, dataset="grf"):
         import torch
-        k, f = I.make_batch(N, seeds, sigma, ell)
+        k, f = _problems(dataset, N, seeds, sigma, ell)
         B = len(seeds)
         self.B, self.N, self.K = B, N, K
         self.k = torch.from_numpy(k).to(device)
@@ -49,19 +53,58 @@ class KrylovData:
         F.krylov_harvest(self.op, fb, x0, ustar, K, self.r, self.e, stream)
 
 
+class RandomResidualData:
+    """Random residuals (the ablation of Section 3.5): for sample i of each instance,
+    u_i ~ N(0, I) and f_i ~ p_f of the dataset (k stays the instance's); r_i = f_i - A u_i and
+    e_i = A^{-1} f_i - u_i, with A^{-1} f_i from CG to a relative residual of 1e-12."""
+
+    def __init__(self, N, seeds, K, device, sigma=1.0, ell=0.1, x0_seed=12345, stream=None, dataset="grf"):
+        import torch
+        k, _ = _problems(dataset, N, seeds, sigma, ell)
+        B = len(seeds)
+        self.B, self.N, self.K = B, N, K
+        self.k = torch.from_numpy(k).to(device)
+        self.op = F.Operator(self.k, stream)
+        rng = np.random.default_rng(x0_seed)
+        self.r = torch.empty((K, B, N, N), dtype=torch.float64, device=device)
+        self.e = torch.empty_like(self.r)
+        Au = torch.empty((B, N, N), dtype=torch.float64, device=device)
+        for i in range(K):
+            f = torch.from_numpy(np.ascontiguousarray(np.stack([I.dataset_rhs(dataset, N, rng) for _ in range(B)])))
+            f = f.to(device)
+            u = torch.from_numpy(rng.standard_normal((B, N, N))).to(device)
+            x = torch.zeros_like(f)
+            F.solve(self.op, None, f, x, tol=1e-12, m_max=1, max_iter=20 * N * N, prec="fp64", check_every=64,
+                    stream=stream)
+            self.op.apply(u, Au, stream)
+            self.r[i] = f - Au
+            self.e[i] = x - u
+
+
+def _problems(dataset, N, seeds, sigma, ell):
+    if dataset == "grf":
+        return I.make_batch(N, seeds, sigma, ell)
+    pairs = [I.dataset_problem(dataset, N, s) for s in seeds]
+    return (np.ascontiguousarray(np.stack([p[0] for p in pairs])),
+            np.ascontiguousarray(np.stack([p[1] for p in pairs])))
+
+
 def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, lr: float = 1e-3,
           steps: int = 1000, seconds: float | None = None, prec: str = "fp32", seed: int = 0,
-          sigma: float = 1.0, ell: float = 0.1, log_every: int = 0, decay_at=(0.5, 0.75)) -> TrainResult:
+          sigma: float = 1.0, ell: float = 0.1, log_every: int = 0, decay_at=(0.5, 0.75),
+          dataset: str = "grf", data: str = "krylov", loss_kind: str = "energy") -> TrainResult:
     """Trains ``model.weights`` in place; returns the loss history. The learning rate is
     halved at the given fractions of ``steps`` (the paper halves it on a fixed schedule,
-    Table 6)."""
+    Table 6). ``data``: "krylov" (Eq. (9)) or "random" (Section 3.5); ``loss_kind``: "energy"
+    (Eq. (11)) or "l2"."""
     import torch
     dev = model.weights.device
     t0 = time.perf_counter()
     groups = []
     seeds = list(train_seeds)
+    Data = KrylovData if data == "krylov" else RandomResidualData
     for g0 in range(0, len(seeds) - batch + 1, batch):
-        groups.append(KrylovData(N, seeds[g0:g0 + batch], K, dev, sigma, ell, x0_seed=1000 + g0))
+        groups.append(Data(N, seeds[g0:g0 + batch], K, dev, sigma, ell, x0_seed=1000 + g0, dataset=dataset))
     torch.cuda.synchronize()
     t_h = time.perf_counter() - t0
     param = model.weights
@@ -83,7 +126,7 @@ def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, 
         idx = torch.randint(0, K, (batch,), generator=gen, device=dev)
         r = d.r[idx, ar].contiguous()
         e = d.e[idx, ar].contiguous()
-        F.train_step(model, d.op, r, e, loss, grad, prec=prec)
+        F.train_step(model, d.op, r, e, loss, grad, prec=prec, loss_kind=loss_kind)
         param.grad = grad
         opt.step()
         if prec == "fp64":

@@ -262,6 +262,17 @@ def test_train_step_matches_oracle_gradient(lib, dev, prec, tol):
     """Energy-norm loss (Eq. (11)) and its gradient w.r.t. the whole weight blob, from the
     hand-written CUDA backward, against the oracle's reverse mode (itself pinned by finite
     differences). Relative 2-norm error of the gradient: 1e-6 (FP64 arithmetic, FP32 output), 2e-4 (FP32)."""
+    check_train_step(lib, dev, prec, tol, "energy")
+
+
+@pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("fp32", 2e-4)])
+def test_l2_train_step_matches_oracle_gradient(lib, dev, prec, tol):
+    """The L2 ablation loss (2-norm in error form) and its gradient against the oracle's
+    reverse mode (pinned by finite differences), same tolerances as Eq. (11)."""
+    check_train_step(lib, dev, prec, tol, "l2")
+
+
+def check_train_step(lib, dev, prec, tol, kind):
     import torch
     N, B, C, M = 32, 3, 16, 8
     k, f = batch(N, B, 1300)
@@ -270,8 +281,9 @@ def test_train_step_matches_oracle_gradient(lib, dev, prec, tol):
     op = lib.Operator(to_dev(k, dev))
     loss = torch.zeros(1, dtype=torch.float32, device=dev)
     grad = torch.zeros(wdev.numel(), dtype=torch.float32, device=dev)
-    lib.train_step(model, op, to_dev(f, dev), to_dev(es, dev), loss, grad, prec=prec)
-    L_ref, g_ref = O.notay_loss_and_grad(P, desc, list(k), list(f), list(es))
+    lib.train_step(model, op, to_dev(f, dev), to_dev(es, dev), loss, grad, prec=prec, loss_kind=kind)
+    ref = O.notay_loss_and_grad if kind == "energy" else O.l2_loss_and_grad
+    L_ref, g_ref = ref(P, desc, list(k), list(f), list(es))
     assert abs(float(loss.item()) - L_ref) <= max(tol, 1e-6) * L_ref
     g = grad.double().cpu().numpy()
     assert rel(g, g_ref) < tol
