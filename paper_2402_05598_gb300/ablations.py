@@ -33,9 +33,11 @@ FACTORS = (1e-3, 1e-6, 1e-12)
 
 
 def evaluate(model, dataset: str, N: int, seeds, prec: str = "bf16", m_max: int = 5, max_iter: int = 2000,
-             factors=FACTORS) -> dict:
+             factors=FACTORS, detail: dict | None = None) -> dict:
     """Mean FCG-NO iterations to each residual-reduction factor over the given instances
-    (u_0 ~ N(0, 1)); None where an instance did not get there within max_iter."""
+    (u_0 ~ N(0, 1)); None where an instance did not get there within max_iter. ``detail``
+    (optional) receives per factor the outcome counts by status and the best relative
+    residual reached."""
     import torch
     dev = model.weights.device
     pairs = [I.dataset_problem(dataset, N, s) for s in seeds]
@@ -49,6 +51,13 @@ def evaluate(model, dataset: str, N: int, seeds, prec: str = "bf16", m_max: int 
         info = F.solve(op, model, f, x, tol=tol, m_max=m_max, max_iter=max_iter, prec=prec, check_every=8)
         ok = all(i["status"] == F.FCGNO_OK for i in info)
         out[f"{tol:g}"] = float(np.mean([i["iters"] for i in info])) if ok else None
+        if detail is not None:
+            counts = {}
+            for i in info:
+                name = F.status_str(i["status"])
+                counts[name] = counts.get(name, 0) + 1
+            detail[f"{tol:g}"] = {"status": counts, "min_relres": float(min(i["relres"] for i in info)),
+                                  "max_relres": float(max(i["relres"] for i in info))}
     op.close()
     return out
 
@@ -66,11 +75,12 @@ def run_variant(dataset: str, N: int, variant: str, steps: int, width: int = 32,
     res = T.train(model, N, range(N), K=100, batch=32, lr=1e-3, steps=steps, dataset=dataset, data=data,
                   loss_kind=loss_kind, log_every=max(1, steps // 4))
     secs = time.perf_counter() - t0
-    its = evaluate(model, dataset, N, range(30000, 30000 + eval_instances), m_max=m_max)
+    detail = {}
+    its = evaluate(model, dataset, N, range(30000, 30000 + eval_instances), m_max=m_max, detail=detail)
     model.close()
     return {"dataset": dataset, "grid": N, "variant": variant, "loss": loss_kind, "data": data, "steps": res.steps,
             "train_seconds": round(secs, 2), "harvest_seconds": round(res.harvest_seconds, 2),
-            "loss_log": [(s, round(v, 4)) for s, v in res.losses], "iterations": its}
+            "loss_log": [(s, round(v, 4)) for s, v in res.losses], "iterations": its, "outcomes": detail}
 
 
 def format_table(rows) -> str:

@@ -29,7 +29,7 @@ constexpr int kTile = 2048;     // elements per CTA (tiled path)
 constexpr int kThreads = 256;   // threads per CTA (tiled path)
 constexpr int kEPT = kTile / kThreads;
 constexpr int kParts = kMaxWindow + 2;
-constexpr int kFusedEPT = 8;    // elements per thread (fused path)
+constexpr int kFusedMaxEPT = 8;  // elements per thread (fused path)
 constexpr int kFusedMaxN = 80;  // n/8 <= 1024 threads and p + reduction staging fit shared memory
 
 struct IterArgs {
@@ -327,8 +327,9 @@ __global__ void norm_kernel(IterArgs a, State s) {
 }
 
 // ------------------------------------ fused path ---------------------------------------
-// One CTA per instance; thread t owns elements t + j*blockDim (j < 8); p staged in shared
-// memory for the stencil. Four fixed-order block reductions per iteration.
+// One CTA per instance; thread t owns elements t + j*blockDim (j < EPT); p staged in shared
+// memory for the stencil. Three fixed-order block reductions per iteration.
+template <int EPT>
 __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   extern __shared__ double sp[];  // n doubles (p), then kMaxWindow * blockDim (reductions)
   __shared__ double red_out[kMaxWindow];
@@ -339,9 +340,9 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   const int T = blockDim.x;
   const int n = (int)a.n;
   double* red = sp + n;
-  double wv[kFusedEPT], rv[kFusedEPT], sv[kFusedEPT];
+  double wv[EPT], rv[EPT], sv[EPT];
 #pragma unroll
-  for (int j = 0; j < kFusedEPT; ++j) {
+  for (int j = 0; j < EPT; ++j) {
     const int e = threadIdx.x + j * T;
     wv[j] = (e < n) ? s.w[off + e] : 0.0;
   }
@@ -353,7 +354,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
     if (k < wd.m_i) {
       const double* Sk = s.S + (size_t)wd.slots[k] * a.B * a.n + off;
 #pragma unroll
-      for (int j = 0; j < kFusedEPT; ++j) {
+      for (int j = 0; j < EPT; ++j) {
         const int e = threadIdx.x + j * T;
         if (e < n) acc[k] = fma(wv[j], Sk[e], acc[k]);
       }
@@ -367,7 +368,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
       const double beta = acc[k] / s.ps[(size_t)wd.slots[k] * a.B + b];
       const double* Pk = s.P + (size_t)wd.slots[k] * a.B * a.n + off;
 #pragma unroll
-      for (int j = 0; j < kFusedEPT; ++j) {
+      for (int j = 0; j < EPT; ++j) {
         const int e = threadIdx.x + j * T;
         if (e < n) wv[j] = fma(-beta, Pk[e], wv[j]);
       }
@@ -375,7 +376,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   }
   double* Pn = s.P + (size_t)wd.slot_new * a.B * a.n + off;
 #pragma unroll
-  for (int j = 0; j < kFusedEPT; ++j) {
+  for (int j = 0; j < EPT; ++j) {
     const int e = threadIdx.x + j * T;
     if (e < n) {
       sp[e] = wv[j];
@@ -386,7 +387,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   // s = A p, (p, s), (p, r)
   double d2[2] = {0.0, 0.0};
 #pragma unroll
-  for (int j = 0; j < kFusedEPT; ++j) {
+  for (int j = 0; j < EPT; ++j) {
     const int e = threadIdx.x + j * T;
     sv[j] = 0.0;
     rv[j] = 0.0;
@@ -415,7 +416,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   double* Sn = s.S + (size_t)wd.slot_new * a.B * a.n + off;
   double rr[1] = {0.0};
 #pragma unroll
-  for (int j = 0; j < kFusedEPT; ++j) {
+  for (int j = 0; j < EPT; ++j) {
     const int e = threadIdx.x + j * T;
     if (e < n) {
       Sn[e] = sv[j];
@@ -588,6 +589,7 @@ struct HarvestHook {
 
 struct LoopShape {
   bool fused;
+  int fusedEPT;
   int fusedThreads;
   size_t fusedSmem;
 };
@@ -595,9 +597,24 @@ struct LoopShape {
 static LoopShape loop_shape(const fcgno_op* op) {
   LoopShape L;
   L.fused = op->N <= kFusedMaxN;
-  L.fusedThreads = ((int)ceil_div(op->n, kFusedEPT) + 31) / 32 * 32;
+  // 8 elements per thread: measured faster than 4 (1024-thread blocks) at 64 x 64, where the
+  // larger block reductions and shared-memory footprint outweigh the extra loads in flight
+  L.fusedEPT = kFusedMaxEPT;
+  L.fusedThreads = ((int)ceil_div(op->n, L.fusedEPT) + 31) / 32 * 32;
   L.fusedSmem = (op->n + (size_t)kMaxWindow * L.fusedThreads) * sizeof(double);
   return L;
+}
+
+// Raise the fused kernel's shared-memory limit (and pin the carveout to its maximum so that
+// two blocks fit per SM) before its first launch; not a stream operation.
+static fcgno_status prepare_fused(const LoopShape& L) {
+  if (!L.fused) return FCGNO_OK;
+  const void* fn = (const void*)fused_step_kernel<kFusedMaxEPT>;
+  if (L.fusedSmem > 48 * 1024)
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.fusedSmem));
+  FCGNO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
+                                      (int)cudaSharedmemCarveoutMaxShared));
+  return FCGNO_OK;
 }
 
 // The vector part of one iteration (steps a3-a7) plus the iteration-counter advance.
@@ -605,7 +622,7 @@ static fcgno_status launch_vector_step(const IterArgs& a, const State& s, const 
   if (L.fused) {
     {
       TraceScope ts("fcg_fused", cs);
-      fused_step_kernel<<<a.B, L.fusedThreads, L.fusedSmem, cs>>>(a, s);
+      fused_step_kernel<kFusedMaxEPT><<<a.B, L.fusedThreads, L.fusedSmem, cs>>>(a, s);
     }
     FCGNO_LAUNCHED();
   } else {
@@ -739,9 +756,7 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
   a.tol = o.tol;
   a.fixed = o.fixed_iters ? 1 : 0;
   const LoopShape L = loop_shape(op);
-  if (L.fused && L.fusedSmem > 48 * 1024)
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)L.fusedSmem));
+  FCGNO_TRY(prepare_fused(L));
   // the caller's stream orders our internal stream at entry and exit
   FCGNO_CUDA_TRY(cudaEventRecord(w.ev_in, st));
   FCGNO_CUDA_TRY(cudaStreamWaitEvent(cs, w.ev_in, 0));
@@ -1043,9 +1058,7 @@ extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, doubl
   a.tol = o.tol;
   a.fixed = o.fixed_iters ? 1 : 0;
   const LoopShape L = loop_shape(A);
-  if (L.fused && L.fusedSmem > 48 * 1024)
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)L.fusedSmem));
+  FCGNO_TRY(prepare_fused(L));
   // the stopped-instance and iteration counters must start at zero: the array keeps the
   // previous call's data
   FCGNO_CUDA_TRY(cudaMemsetAsync(s.ndone, 0, sizeof(int), st));
@@ -1175,9 +1188,7 @@ extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t m
   k->a.tol = tol;
   k->a.fixed = 0;
   k->L = loop_shape(op);
-  if (k->L.fused && k->L.fusedSmem > 48 * 1024)
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fused_step_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)k->L.fusedSmem));
+  FCGNO_TRY(prepare_fused(k->L));
   *out = k;
   return FCGNO_OK;
 }

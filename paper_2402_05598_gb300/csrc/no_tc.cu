@@ -450,9 +450,11 @@ __global__ void tc_lift_kernel(TcGeom g, const double* __restrict__ r, const flo
 // activations: for N < 128 one bulk copy of (128/C)/PT consecutive tiles, for N >= 128 one
 // copy of QC rows per (column, 8-channel group). M groups of 8 channels are ordered
 // (tile u, channel group cg, column within the tile pl) and sit QC*16 bytes apart.
-// Warp-specialised: warps 0-3 read the Z accumulators back (two TMEM slots alternating by
-// m-tile) and store the result; lane 0 of warp 4 issues the MMAs and lane 0 of warp 5 the
-// bulk copies, through a three-slot ring; the roles meet only on mbarriers.
+// Warp-specialised: warps 0-3 read the Z accumulators back and store the result; lane 0 of
+// warp 4 issues the MMAs and lane 0 of warp 5 the bulk copies, through a three-slot ring; the
+// roles meet only on mbarriers. Z accumulators rotate through up to eight 32-column TMEM
+// slots, which overlap the stage-P accumulators (stage P starts only after every Z has been
+// read back), so that the MMAs are not held back by the read-back.
 constexpr int kAnaThreads = 192;
 template <int C>
 __global__ void __launch_bounds__(kAnaThreads, 2)
@@ -464,7 +466,8 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
   // full[s] step copied in; sfree[s] its MMAs done; zfull[z] / zempty[z] Z slot ready / read
   // back (4 warp arrivals); prob prologue copies; apready stage-P operand complete (4); pfull
   // stage-P accumulators ready
-  __shared__ uint64_t full[NS], sfree[NS], zfull[2], zempty[2], prob, apready, pfull;
+  constexpr int NZ = 8;
+  __shared__ uint64_t full[NS], sfree[NS], zfull[NZ], zempty[NZ], prob, apready, pfull;
   __shared__ uint32_t tbase_s;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(active, b)) return;
@@ -478,14 +481,14 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
   uint8_t* sAP = sA + NS * AB;                    // MP x 2PC, K-major: LBO 128, SBO 2PC*16
   uint8_t* sG = sAP + (size_t)g.MP * 2 * PC * 2;  // NPM x 2PC, K-major: LBO 128, SBO 2PC*16
   const uint32_t SBO_E = QC * 16, SBO_A = QC * 16, SBO_P = 2 * PC * 16, SBO_G = 2 * PC * 16;
-  const uint32_t tcols = (64 + (g.MP / 128) * g.NPM) <= 256 ? 256u : 512u;
+  const uint32_t tcols = ((g.MP / 128) * g.NPM) <= 256 ? 256u : 512u;
   if (warp == 0) tmem_alloc(&tbase_s, tcols);
   if (tid == 128) {
     for (int i = 0; i < NS; ++i) {
       mbar_init(&full[i], 1);
       mbar_init(&sfree[i], 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NZ; ++i) {
       mbar_init(&zfull[i], 1);
       mbar_init(&zempty[i], 4);
     }
@@ -503,7 +506,9 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
   __syncthreads();
   fence_after_sync();
   const uint32_t tbase = tbase_s;
-  const uint32_t tQ = tbase, tP = tbase + 64;  // two Z slots of 32 columns, then the c accumulators
+  const uint32_t tP = tbase;  // stage-P accumulators (after stage Q)
+  const uint32_t tQ = tbase;  // nz Z slots of 32 columns (stage Q)
+  const int nz = (int)(tcols / 32) < NZ ? (int)(tcols / 32) : NZ;
   const int p0 = chunk * PC;
   const int cols_mt = 128 / C;  // grid columns per m-tile
   const int mtiles = PC / cols_mt;
@@ -520,16 +525,16 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
       for (int s = 0; s < nsteps && ok; ++s) {
         const int buf = s % NS, mt = s / qchunks, qc = s % qchunks;
         ok = mbar_wait(&full[buf], (s / NS) & 1);
-        if (ok && qc == 0 && mt >= 2) ok = mbar_wait(&zempty[mt & 1], ((mt >> 1) - 1) & 1);
+        if (ok && qc == 0 && mt >= nz) ok = mbar_wait(&zempty[mt % nz], ((mt / nz) - 1) & 1);
         if (!ok) break;
         fence_after_sync();
-        const uint32_t tq = tQ + (mt & 1) * 32;
+        const uint32_t tq = tQ + (mt % nz) * 32;
         const uint32_t sa = smem_addr(sA + buf * AB);
         const uint32_t e2 = smem_addr(sE2 + (qchunks > 1 ? buf * E2B : 0));
         for (int ks = 0; ks < QC / 16; ++ks)
           mma(tq, desc(sa + ks * 256, 128, SBO_A), desc(e2 + ks * 256, 128, SBO_E), idQ, qc > 0 || ks > 0);
         commit(&sfree[buf]);
-        if (qc == qchunks - 1) commit(&zfull[mt & 1]);
+        if (qc == qchunks - 1) commit(&zfull[mt % nz]);
         mmas = s + 1;
       }
       if (ok) ok = mbar_wait(&apready, 0);  // every Z read back into sAP
@@ -594,10 +599,10 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
     const int u = Gi / ((C / 8) * PT), cg = (Gi / PT) % (C / 8), pl2 = Gi % PT;
     const int c = cg * 8 + (M & 7);
     for (int mt = 0; mt < mtiles && ok; ++mt) {
-      ok = mbar_wait(&zfull[mt & 1], (mt >> 1) & 1);
+      ok = mbar_wait(&zfull[mt % nz], (mt / nz) & 1);
       if (!ok) break;
       fence_after_sync();
-      const uint32_t tq = tQ + (mt & 1) * 32 + ((uint32_t)(warp * 32) << 16);
+      const uint32_t tq = tQ + (mt % nz) * 32 + ((uint32_t)(warp * 32) << 16);
       float z[32];
       float tmp[16];
       tmem_ld16(tq, tmp);
@@ -608,7 +613,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
       for (int i = 0; i < 16; ++i) z[16 + i] = tmp[i];
       fence_before_sync();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&zempty[mt & 1]);
+      if (lane == 0) mbar_arrive(&zempty[mt % nz]);
       const int pl = mt * cols_mt + u * PT + pl2;
 #pragma unroll
       for (int k2 = 0; k2 < 16; ++k2) {  // Ky <= 16: static indices keep z in registers
@@ -621,6 +626,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
     }
     if (ok) {
       fence_smem_to_async();
+      fence_before_sync();  // every Z read of this warp precedes stage P (same TMEM columns)
       __syncwarp();
       if (lane == 0) mbar_arrive(&apready);
       ok = mbar_wait(&pfull, 0);
