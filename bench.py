@@ -145,6 +145,13 @@ def roofline_synthesis(active_per_iter, N, C, M, layers):
     return float(sum(active_per_iter)) * per_inst, int(len(active_per_iter)) * layers
 
 
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one tc_synthesis_kernel launch
+# per active instance, mean of the four layers of an iteration, measured by ncu on this
+# kernel at 64 x 64, 256 instances, width 32, 12 x 12 modes. Scaled by the active instances
+# per launch; None when the kernel has changed since the last capture.
+SYN_TRAFFIC_PER_INSTANCE = None
+
+
 SERVE_SIZES = {64: 0.40, 128: 0.25, 256: 0.20, 512: 0.10, 1024: 0.05}
 SERVE_SIGMAS = (0.5, 1.0, 2.0)
 
@@ -176,23 +183,30 @@ def run_serving(args, model, desc_np, dev, pool_per_key=4, budget_gb=80.0):
     js = rng.integers(0, pool_per_key, args.serve_requests)
     reqs = [S.Request(i, float(arrivals[i]), int(Ns[i]), *pool[(int(Ns[i]), int(sis[i]), int(js[i]))])
             for i in range(args.serve_requests)]
-    caps = S.plan_capacities(SERVE_SIZES, int(budget_gb * 2**30), args.m, F.make_desc(WIDTH, LAYERS, MODES, WIDTH),
+    m = args.serve_m
+    caps = S.plan_capacities(SERVE_SIZES, int(budget_gb * 2**30), m, F.make_desc(WIDTH, LAYERS, MODES, WIDTH),
                              args.prec, max_slots=64)
-    srv = S.Server(model, caps, prec=args.prec, m_max=args.m, tol=TOL, max_iter=args.max_iter, iters_per_step=8)
+    srv = S.Server(model, caps, prec=args.prec, m_max=m, tol=TOL, max_iter=args.max_iter, iters_per_step=8)
     # warm every bucket once (first steps run eagerly and allocate), outside the measurement
     warm = [S.Request(-1, 0.0, N, *pool[(N, 0, 0)]) for N in sizes]
     srv.run(warm, S.ServeStats())
     stats = S.ServeStats(offered_rate=args.serve_rate)
-    stats.bucket_bytes = sum(cap * S.slot_bytes(N, args.m, F.make_desc(WIDTH, LAYERS, MODES, WIDTH), args.prec)
+    stats.bucket_bytes = sum(cap * S.slot_bytes(N, m, F.make_desc(WIDTH, LAYERS, MODES, WIDTH), args.prec)
                              for N, cap in caps.items())
     srv.run(reqs, stats)
     srv.close()
     out = stats.summary()
     out.update({"capacities": {str(N): c for N, c in caps.items()}, "budget_gb": budget_gb,
-                "sizes": {str(N): p for N, p in SERVE_SIZES.items()}, "tol": TOL, "m": args.m,
+                "sizes": {str(N): p for N, p in SERVE_SIZES.items()}, "tol": TOL, "m": m,
                 "max_iter": args.max_iter,
                 "iterations_mean_by_size": {str(N): float(np.mean([r.iters for r in reqs if r.N == N] or [0]))
-                                            for N in sizes}})
+                                            for N in sizes},
+                # requests that reached the tolerance, per grid size and coefficient contrast
+                "converged_by_size_sigma": {f"{N}/{sg}": [sum(1 for r, s_ in zip(reqs, sis)
+                                                              if r.N == N and SERVE_SIGMAS[s_] == sg and r.status == F.FCGNO_OK),
+                                                          sum(1 for r, s_ in zip(reqs, sis)
+                                                              if r.N == N and SERVE_SIGMAS[s_] == sg)]
+                                            for N in sizes for sg in SERVE_SIGMAS}})
     return out
 
 
@@ -244,7 +258,7 @@ def main():
                                                      "measured alongside)")
     ap.add_argument("--m-alt", type=int, default=1, help="second truncation reported next to the headline (0 = none)")
     ap.add_argument("--train-steps", type=int, default=8000)
-    ap.add_argument("--train-instances", type=int, default=256)
+    ap.add_argument("--train-instances", type=int, default=512)
     ap.add_argument("--max-iter", type=int, default=400,
                     help="iteration cap (CG needs ~400 on this workload); capped instances are not counted")
     ap.add_argument("--ref-iters", type=int, default=60)
@@ -253,6 +267,7 @@ def main():
     ap.add_argument("--serve-requests", type=int, default=2000,
                     help="requests in the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate of the serving stream (1/s)")
+    ap.add_argument("--serve-m", type=int, default=1, help="truncation m of the served solves")
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling mode: no training, two solves of --profile-iters fixed iterations")
     ap.add_argument("--profile-iters", type=int, default=8)
@@ -387,6 +402,8 @@ def main():
         with open(peaks_path) as fh:
             peak, peak_src = float(json.load(fh)["hbm_gbs"]), "measured"
     syn_avg_ms = syn_ms / max(syn_launches, 1)
+    active_per_launch = float(sum(active)) * LAYERS * args.steps / max(syn_launches, 1)
+    traffic = SYN_TRAFFIC_PER_INSTANCE * active_per_launch if SYN_TRAFFIC_PER_INSTANCE else None
     achieved = alg_bytes_one * args.steps / (syn_ms / 1000.0) / 1e9 if syn_ms > 0 else None
 
     # ---- kernel shares over one more (untimed) step per family
@@ -419,7 +436,9 @@ def main():
             "clocks": clk,
             "roofline": {"kernel": "tc_synthesis_kernel", "bound": "hbm", "achieved": achieved, "peak": peak,
                          "peak_source": peak_src, "unit": "GB/s",
-                         "frac": (achieved / peak) if achieved else None, "traffic": None,
+                         "frac": (achieved / peak) if achieved else None, "traffic": traffic,
+                         "traffic_note": "ncu dram read+write per active instance x active instances per launch",
+                         "algorithmic_bytes_per_launch": alg_bytes_one * args.steps / max(syn_launches, 1),
                          "avg_launch_ms": syn_avg_ms, "launches": syn_launches,
                          "note": trace_note or None},
             "kernel_ms_one_step": shares,

@@ -333,6 +333,8 @@ template <int EPT>
 __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   extern __shared__ double sp[];  // n doubles (p), then kMaxWindow * blockDim (reductions)
   __shared__ double red_out[kMaxWindow];
+  pdl_wait();  // w (and, with the identity preconditioner, every vector) comes from the kernel before
+  pdl_trigger();
   const int b = blockIdx.x;
   if (s.status[b] != kRunning) return;
   const Window wd = window_of(a, s, b);
@@ -622,7 +624,8 @@ static fcgno_status launch_vector_step(const IterArgs& a, const State& s, const 
   if (L.fused) {
     {
       TraceScope ts("fcg_fused", cs);
-      fused_step_kernel<kFusedMaxEPT><<<a.B, L.fusedThreads, L.fusedSmem, cs>>>(a, s);
+      FCGNO_CUDA_TRY(launch_chained(fused_step_kernel<kFusedMaxEPT>, dim3(a.B), dim3(L.fusedThreads), L.fusedSmem,
+                                    cs, a, s));
     }
     FCGNO_LAUNCHED();
   } else {

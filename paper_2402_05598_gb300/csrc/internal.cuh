@@ -72,6 +72,35 @@ struct TraceScope {
   }
 };
 
+// Programmatic dependent launch. The kernels of one FCG-NO iteration form a chain on one
+// stream, and each link is launched so that it may start while its predecessor still runs:
+// its set-up (shared and tensor memory, barriers, copies of constant tables and of data
+// written two or more kernels earlier) overlaps the predecessor's tail. Rules kept by every
+// chained kernel:
+//  - pdl_wait() comes before any access to global memory that the predecessor writes, and
+//    before any write to global memory that the predecessor reads;
+//  - pdl_trigger() comes only after pdl_wait(), so that when a kernel starts, the kernel two
+//    links back has completed and its writes are visible.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+// Launches `kernel` as a chained link (programmatic stream serialization) on `st`.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                  Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // Per-instance solver status codes kept on the device (negative = still iterating).
 constexpr int kRunning = -1;
 constexpr int kMaxWindow = 8;  // largest m_max supported

@@ -121,10 +121,11 @@ static TcGeom make_geom(int N, int C, int M) {
     g.QT = 128;
     g.KSYN = round_up(2 * M, 16);
   }
-  // synthesis column chunk: 32 columns (fewer blocks, half the per-block set-up per tile)
-  // when two blocks per SM still fit with a 3 + 2 slot tile ring, otherwise 16
+  // synthesis column chunk: 16 columns. A block's latency is its serial set-up plus its tiles
+  // streamed through the input ring; 16-column chunks halve the tiles per block, double the
+  // blocks (more of them in flight while few instances are active) and leave shared memory
+  // for an input ring that holds most of a block's tiles at once.
   g.SPC = 16;
-  if (N < 128 && g.PC >= 32 && (g.MP / 128) * 64 <= 256 && synthesis_bytes(g, 32, 3, 2) <= kSynTwoPerSm) g.SPC = 32;
   while (g.SPC % g.PT != 0) g.SPC *= 2;
   g.snchunks = N / g.SPC;
   g.KB = round_up(g.SPC * 2 * M, 16) + 16;
@@ -394,51 +395,83 @@ __host__ __device__ __forceinline__ void act_tile_of(const TcGeom& g, int q, int
   }
 }
 
-// Encoder: v0 = lift_w [r/rms, log k] + lift_b, written tile-major. One thread per tile row
-// (consecutive threads write consecutive 16-byte rows of each channel group); the only FP64
-// work is reading r (1/rms is formed once per thread in FP32).
+// Encoder: v0 = lift_w [r/rms, log k] + lift_b, written tile-major. One block covers
+// kLiftCols grid columns of kLiftRows(N) = min(N, 128) rows of one instance, i.e. whole tiles:
+// it reads those rows of r (FP64) and log k (FP32) with coalesced row segments into shared
+// memory, then writes the tiles' 16-byte channel-group rows in order, consecutive threads on
+// consecutive tile rows. 1/rms is formed once per thread in FP32.
+constexpr int kLiftCols = 32, kLiftThreads = 256;
+__host__ __device__ constexpr int lift_rows(int N) { return N < 128 ? N : 128; }
 template <int C>
-__global__ void tc_lift_kernel(TcGeom g, const double* __restrict__ r, const float* __restrict__ logk,
-                               const double* __restrict__ rms, const int* __restrict__ active,
-                               const float* __restrict__ lw, const float* __restrict__ lb, uint16_t* __restrict__ v,
-                               bool bf16) {
+__global__ void __launch_bounds__(kLiftThreads) tc_lift_kernel(TcGeom g, const double* __restrict__ r,
+                                                               const float* __restrict__ logk,
+                                                               const double* __restrict__ rms,
+                                                               const int* __restrict__ active,
+                                                               const float* __restrict__ lw,
+                                                               const float* __restrict__ lb,
+                                                               uint16_t* __restrict__ v, bool bf16) {
   __shared__ float w0[C], w1[C], bb[C];
+  __shared__ float2 sv[128][kLiftCols + 1];  // (r / rms, log k) of the block's grid points
+  pdl_wait();  // r, rms and the status flags come from the FCG step just before
+  pdl_trigger();
   const int b = blockIdx.y;
   if (tc_inactive(active, b)) return;
-  for (int c = threadIdx.x; c < C; c += blockDim.x) {
+  const int tid = threadIdx.x;
+  for (int c = tid; c < C; c += kLiftThreads) {
     w0[c] = lw[2 * c];
     w1[c] = lw[2 * c + 1];
     bb[c] = lb[c];
   }
-  __syncthreads();
-  const int N = g.N;
+  const int N = g.N, R = lift_rows(N), ncol = N / kLiftCols;
+  const int p0 = (blockIdx.x % ncol) * kLiftCols, q0 = (blockIdx.x / ncol) * R;
   const size_t n = (size_t)N * N;
-  const size_t x = blockIdx.x * (size_t)blockDim.x + threadIdx.x;  // tile-major row index
-  if (x >= n) return;
-  const int tile = (int)(x / 128), m = (int)(x % 128);
-  int q, p;
-  if (N < 128) {
-    p = tile * g.PT + m / N;
-    q = m % N;
-  } else {
-    p = tile % N;
-    q = (tile / N) * 128 + m;
-  }
-  const size_t pt = (size_t)q * N + p;
   const float s = (float)rms[b];
   const float inv = s > 0.f ? 1.0f / s : 0.f;
-  const float rh = (float)r[(size_t)b * n + pt] * inv;
-  const float lk = logk[(size_t)b * n + pt];
-  uint8_t* dst = reinterpret_cast<uint8_t*>(v + ((size_t)b * n + (size_t)tile * 128) * C) + m * 16;
+  const double* rb = r + (size_t)b * n;
+  const float* lb_ = logk + (size_t)b * n;
+  // every load of the thread is issued before the first shared-memory store
+  constexpr int kLoads = 128 * kLiftCols / kLiftThreads;
+  double rv[kLoads];
+  float lv[kLoads];
 #pragma unroll
-  for (int c0 = 0; c0 < C; c0 += 8) {
+  for (int i = 0; i < kLoads; ++i) {
+    const int idx = tid + i * kLiftThreads, qq = idx / kLiftCols, pp = idx % kLiftCols;
+    if (idx < R * kLiftCols) {
+      const size_t pt = (size_t)(q0 + qq) * N + p0 + pp;
+      rv[i] = rb[pt];
+      lv[i] = lb_[pt];
+    }
+  }
+#pragma unroll
+  for (int i = 0; i < kLoads; ++i) {
+    const int idx = tid + i * kLiftThreads;
+    if (idx < R * kLiftCols) sv[idx / kLiftCols][idx % kLiftCols] = make_float2((float)rv[i] * inv, lv[i]);
+  }
+  __syncthreads();
+  // tiles of the block: N < 128: PT columns x N rows each; N >= 128: one column x 128 rows
+  const int ntl = R * kLiftCols / 128;
+  const size_t tau0 = N < 128 ? (size_t)(p0 / g.PT) : (size_t)(q0 / 128) * N + p0;
+  constexpr int CG = C / 8;
+  for (int idx = tid; idx < ntl * CG * 128; idx += kLiftThreads) {
+    const int m = idx % 128, cg = (idx / 128) % CG, tl = idx / (128 * CG);
+    int row, col;
+    if (N < 128) {
+      col = tl * g.PT + m / N;
+      row = m % N;
+    } else {
+      col = tl;
+      row = m;
+    }
+    const float2 x = sv[row][col];
     uint32_t w[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int c = c0 + 2 * i;
-      w[i] = pack2(fmaf(w0[c], rh, fmaf(w1[c], lk, bb[c])), fmaf(w0[c + 1], rh, fmaf(w1[c + 1], lk, bb[c + 1])), bf16);
+      const int c = cg * 8 + 2 * i;
+      w[i] = pack2(fmaf(w0[c], x.x, fmaf(w1[c], x.y, bb[c])), fmaf(w0[c + 1], x.x, fmaf(w1[c + 1], x.y, bb[c + 1])),
+                   bf16);
     }
-    *reinterpret_cast<uint4*>(dst + (c0 / 8) * 2048) = make_uint4(w[0], w[1], w[2], w[3]);
+    uint8_t* dst = reinterpret_cast<uint8_t*>(v + ((size_t)b * n + (tau0 + tl) * 128) * C) + cg * 2048 + m * 16;
+    *reinterpret_cast<uint4*>(dst) = make_uint4(w[0], w[1], w[2], w[3]);
   }
 }
 
@@ -582,6 +615,8 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
       mbar_expect_tx(&prob, GB + (qchunks == 1 ? E2B : 0));
       bulk_g2s(sG, G + (size_t)chunk * g.NPM * 2 * PC, GB, &prob);
       if (qchunks == 1) bulk_g2s(sE2, E2, E2B, &prob);
+      pdl_wait();  // the activations come from the kernel just before
+      pdl_trigger();
       for (int s = 0; s < nsteps && ok; ++s) {
         if (s >= NS) ok = mbar_wait(&sfree[s % NS], ((s / NS) - 1) & 1);  // step s-NS's MMAs read the slot
         if (ok) stage(s);
@@ -595,6 +630,7 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
   } else {
     // ================================ read-back warps 0-3 ==============================
     // Z of m-tile mt: lane M -> (column, channel), columns (k2, t) -> sAP[(k2, c)][(p, t)]
+    pdl_wait();  // (before their global writes)
     const int M = warp * 32 + lane, Gi = M >> 3;
     const int u = Gi / ((C / 8) * PT), cg = (Gi / PT) % (C / 8), pl2 = Gi % PT;
     const int c = cg * 8 + (M & 7);
@@ -707,6 +743,7 @@ __global__ void __launch_bounds__(kTcThreads, 4)
   fence_after_sync();
   const uint32_t tbase = tbase_s;
   bool ok = true;
+  if (tid != 0) pdl_wait();  // (before the read-back's global writes)
   if (tid == 0) {
     const uint16_t* pm = part + (size_t)mode * nch * nbt * 128 * C2;
     auto load = [&](int ch) {
@@ -715,6 +752,8 @@ __global__ void __launch_bounds__(kTcThreads, 4)
     };
     mbar_expect_tx(&rbar, RB);
     bulk_g2s(sR, Rr + (size_t)mode * C2 * C2, RB, &rbar);
+    pdl_wait();  // the partial coefficients come from the analysis just before
+    pdl_trigger();
     for (int ch = 0; ch < MS; ++ch) load(ch);
     ok = mbar_wait(&rbar, 0);
     const uint32_t id = idesc_f16(128, C2, bf16, false, false);
@@ -825,7 +864,7 @@ struct SynArgs {
 // block by row block (tile t: q tile t / SPC, column t % SPC).
 constexpr int kSynEpi = 256;                 // epilogue threads
 constexpr int kSynThreads = kSynEpi + 96;    // + the MMA, load and store warps
-constexpr int kSynMaxIn = 4, kSynMaxOut = 2;
+constexpr int kSynMaxIn = 8, kSynMaxOut = 2;
 constexpr int kSynAcc = 4;                   // TMEM tile accumulators
 template <int C>
 __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a) {
@@ -852,11 +891,14 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
   const uint32_t SB = 128 * g.KSYN * 2;
   const uint32_t SL = TB + (N >= 128 ? SB : 0);  // input slot: tile, then (N >= 128) its table rows
   const uint32_t bytesA1 = g.MP * g.KXP * 2, bytesH = 2 * PC * g.KXP * 2;
-  // region R0 holds the mixed coefficients for synthesis stage 1, then (aliased, once stage 1
-  // has completed) the input and output rings
+  // region R0 holds the input and output rings and, at its top end (aliased with the last
+  // slots until stage 1 has completed), the mixed coefficients for synthesis stage 1; the
+  // input slots wholly below them are filled from the start of the block
   const uint32_t ring_bytes = DI * SL + DO * TB;
   const uint32_t r0 = bytesA1 > ring_bytes ? bytesA1 : ring_bytes;
-  uint8_t* sA1 = smem;                     // MP x KXP
+  const uint32_t a1_off = (r0 - bytesA1) & ~1023u;
+  const int early = (int)(a1_off / SL) < DI ? (int)(a1_off / SL) : DI;  // slots free during stage 1
+  uint8_t* sA1 = smem + a1_off;            // MP x KXP
   uint8_t* ring = smem;                    // DI input slots of SL bytes (after stage 1)
   uint8_t* oring = smem + DI * SL;         // DO output slots of TB bytes (after stage 1)
   uint8_t* sH = smem + r0;                 // 2PC x KXP
@@ -996,12 +1038,17 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         if (N >= 128) bulk_g2s(dst + TB, a.Asyn + (size_t)(t / PC) * 128 * g.KSYN, SB, &full[s]);
         loads = t + 1;
       };
+      // constant operands and the first input tiles (the layer input was written three
+      // kernels back) before the wait; the mixed coefficients come from the kernel just before
       mbar_expect_tx(&prob, bytesA1 + bytesH + C * C * 2 * (a.project ? 2 : 1) + (N < 128 ? SB : 0));
-      bulk_g2s(sA1, a.chat + (size_t)b * g.MP * g.KXP, bytesA1, &prob);
       bulk_g2s(sH, a.H + (size_t)chunk * 2 * PC * g.KXP, bytesH, &prob);
       bulk_g2s(sW, a.W, C * C * 2, &prob);
       if (a.project) bulk_g2s(sP, a.P1, C * C * 2, &prob);
       if (N < 128) bulk_g2s(sS, a.Asyn, SB, &prob);
+      while (loads < ntiles && loads < early) load_tile(loads);
+      pdl_wait();
+      pdl_trigger();
+      bulk_g2s(sA1, a.chat + (size_t)b * g.MP * g.KXP, bytesA1, &prob);
       ok = mbar_wait(&prob, 0);
       pro_pending = !ok;
       if (ok) ok = mbar_wait(&s1b, 0);  // stage 1 has read sA1: the rings may overwrite it
@@ -1021,6 +1068,7 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
     }
   } else if (warp == kSynEpi / 32 + 2) {
     // ================================ store issuer (one lane) ==========================
+    pdl_wait();  // (before its global writes)
     if (lane == 0 && !a.project) {
       // store the layer output of tile u; release the output slot of tile u - 1 once its
       // store (not the latest one) has read it
@@ -1039,6 +1087,7 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
     }
   } else {
     // ================================ epilogue (256 threads) ===========================
+    pdl_wait();  // (before its global writes)
     const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant, channel/column half
     const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     ok = mbar_wait(&s1b, 0);
@@ -1167,8 +1216,8 @@ static size_t mix_smem(const TcGeom& g) {
   const int ms = g.nchunks < kMixSlots ? g.nchunks : kMixSlots;
   return (size_t)4 * g.C * g.C * 2 + (size_t)ms * 128 * 2 * g.C * 2;
 }
-// Tile rings of the synthesis kernel: the deepest input ring (2 .. 4 slots, 2 output slots)
-// that keeps two blocks per SM; 4 + 2 (one block per SM) when none does.
+// Tile rings of the synthesis kernel: the deepest input ring (2 .. kSynMaxIn slots, 2 output
+// slots) that keeps two blocks per SM; kSynMaxIn + 2 (one block per SM) when none does.
 static void synthesis_rings(const TcGeom& g, int& din, int& dout) {
   dout = kSynMaxOut;
   for (din = kSynMaxIn; din >= 2; --din)
@@ -1221,8 +1270,10 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   const bool bf16 = !fp16;
   {
     TraceScope ts("tc_lift", st);
-    tc_lift_kernel<C><<<dim3(ceil_div(n, 256), B), 256, 0, st>>>(g, r, op->logk32, rms, active, m->w32 + BL.lift_w,
-                                                                 m->w32 + BL.lift_b, T.va, bf16);
+    const int lift_blocks = (op->N / kLiftCols) * (op->N / lift_rows(op->N));
+    FCGNO_CUDA_TRY(launch_chained(tc_lift_kernel<C>, dim3(lift_blocks, B), dim3(kLiftThreads), 0, st, g, r,
+                                  (const float*)op->logk32, rms, active, (const float*)(m->w32 + BL.lift_w),
+                                  (const float*)(m->w32 + BL.lift_b), T.va, bf16));
   }
   FCGNO_LAUNCHED();
   int din, dout;
@@ -1249,14 +1300,16 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   for (int l = 0; l < d.layers; ++l) {
     {
       TraceScope ts("tc_analysis", st);
-      tc_analysis_kernel<C><<<dim3(g.nchunks, B), kAnaThreads, sa, st>>>(g, nbt, bf16, active, cur, tab->E2, tab->G,
-                                                                        T.part, d_err);
+      FCGNO_CUDA_TRY(launch_chained(tc_analysis_kernel<C>, dim3(g.nchunks, B), dim3(kAnaThreads), sa, st, g, nbt,
+                                    bf16, active, (const uint16_t*)cur, (const uint16_t*)tab->E2,
+                                    (const uint16_t*)tab->G, T.part, d_err));
     }
     FCGNO_LAUNCHED();
     {
       TraceScope ts("tc_mix", st);
-      tc_mix_kernel<C><<<dim3(g.nmodes, nbt), kTcThreads, sm, st>>>(g, B, nbt, bf16, active, T.part, P.Rr[l],
-                                                                   T.chat, d_err);
+      FCGNO_CUDA_TRY(launch_chained(tc_mix_kernel<C>, dim3(g.nmodes, nbt), dim3(kTcThreads), sm, st, g, B, nbt,
+                                    bf16, active, (const uint16_t*)T.part, (const uint16_t*)P.Rr[l], T.chat,
+                                    d_err));
     }
     FCGNO_LAUNCHED();
     SynArgs s{};
@@ -1285,7 +1338,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     s.err = d_err;
     {
       TraceScope ts("tc_synthesis", st);
-      tc_synthesis_kernel<C><<<dim3(g.snchunks, B), kSynThreads, ss, st>>>(s);
+      FCGNO_CUDA_TRY(launch_chained(tc_synthesis_kernel<C>, dim3(g.snchunks, B), dim3(kSynThreads), ss, st, s));
     }
     FCGNO_LAUNCHED();
     std::swap(cur, nxt);

@@ -91,20 +91,24 @@ def _problems(dataset, N, seeds, sigma, ell):
 
 def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, lr: float = 1e-3,
           steps: int = 1000, seconds: float | None = None, prec: str = "fp32", seed: int = 0,
-          sigma: float = 1.0, ell: float = 0.1, log_every: int = 0, decay_at=(0.5, 0.75),
+          sigma=1.0, ell: float = 0.1, log_every: int = 0, decay_at=(0.5, 0.75),
           dataset: str = "grf", data: str = "krylov", loss_kind: str = "energy") -> TrainResult:
     """Trains ``model.weights`` in place; returns the loss history. The learning rate is
     halved at the given fractions of ``steps`` (the paper halves it on a fixed schedule,
     Table 6). ``data``: "krylov" (Eq. (9)) or "random" (Section 3.5); ``loss_kind``: "energy"
-    (Eq. (11)) or "l2"."""
+    (Eq. (11)) or "l2". ``sigma`` is the GRF standard deviation of the coefficient fields, or
+    a sequence of them: group g of ``batch`` instances then uses sigma[g % len(sigma)], so
+    that the training distribution covers every coefficient contrast it will be served."""
     import torch
     dev = model.weights.device
     t0 = time.perf_counter()
     groups = []
     seeds = list(train_seeds)
     Data = KrylovData if data == "krylov" else RandomResidualData
-    for g0 in range(0, len(seeds) - batch + 1, batch):
-        groups.append(Data(N, seeds[g0:g0 + batch], K, dev, sigma, ell, x0_seed=1000 + g0, dataset=dataset))
+    sigmas = tuple(sigma) if isinstance(sigma, (tuple, list)) else (sigma,)
+    for gi, g0 in enumerate(range(0, len(seeds) - batch + 1, batch)):
+        groups.append(Data(N, seeds[g0:g0 + batch], K, dev, sigmas[gi % len(sigmas)], ell, x0_seed=1000 + g0,
+                           dataset=dataset))
     torch.cuda.synchronize()
     t_h = time.perf_counter() - t0
     param = model.weights

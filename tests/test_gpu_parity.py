@@ -236,6 +236,33 @@ def test_tensor_core_preconditioner_matches_oracle(lib, dev, N, C, M, B, prec, t
         assert err < tol, (b, err)
 
 
+@pytest.mark.parametrize("N,C,M,B,sample", [
+    (64, 32, 12, 256, range(0, 256, 37)),   # the benchmark's launch configuration
+    (32, 16, 8, 130, (0, 64, 127, 128, 129)),  # crosses the 128-instance block of the mode mixing
+    (1024, 32, 16, 1, (0,)),                # the large-solve grid and mode count
+])
+def test_tensor_core_preconditioner_full_size_sampled(lib, dev, N, C, M, B, sample):
+    """The BF16 tensor-core preconditioner at full launch sizes: every kernel runs on the
+    whole batch, and sampled instances are compared with the FP64 oracle (2e-2 relative);
+    the rest must be finite and zero exactly where r is."""
+    import torch
+    k, r = batch(N, B, 5000 + N)
+    r[B - 1] = 0.0 if B > 1 else r[B - 1]
+    desc, P, model, _w = model_pair(lib, dev, C, M)
+    op = lib.Operator(to_dev(k, dev))
+    z = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    lib.precond_apply(model, op, to_dev(r, dev), z, prec="bf16")
+    zs = z.cpu().numpy()
+    assert np.all(np.isfinite(zs))
+    if B > 1:
+        assert not np.any(zs[B - 1])
+    for b in sample:
+        if b == B - 1 and B > 1:
+            continue
+        err = rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b])))
+        assert err < 2e-2, (b, err)
+
+
 def test_tensor_core_preconditioner_inside_solve(lib, dev):
     """Algorithm 1 with the BF16 preconditioner: every iterate keeps the exact line-search
     property (monotone energy error), and instances that stop leave their batch-mates intact."""
