@@ -22,6 +22,12 @@
  *  - Per-instance solve outcomes are reported in fcgno_solve_info[b].status.
  *  - Every computation runs in CUDA kernels of this library (sm_103a); there is no host
  *    fallback.
+ *  - Concurrency: calls on different operators may run on different streams at the same
+ *    time, also with one shared model, when the preconditioner is FCGNO_BF16 or FCGNO_FP16
+ *    (its activations belong to the operator). The FCGNO_FP64 / FCGNO_FP32 preconditioner and
+ *    fcgno_train_step keep their activations in the model: calls using them on one model
+ *    must not overlap. Calls on one operator must not overlap either. Changing a model's
+ *    weights (fcgno_model_sync) while a solve or bucket uses it is not supported.
  */
 #ifndef FCGNO_H
 #define FCGNO_H

@@ -202,6 +202,7 @@ extern "C" fcgno_status fcgno_model_destroy(fcgno_model_t m) {
 extern "C" fcgno_status fcgno_op_destroy(fcgno_op_t op) {
   if (!op) return FCGNO_OK;
   solver_ws_free(op);
+  tc_acts_free(op);
   double* p[] = {op->aE, op->aN, op->diag, op->logk};
   for (double* x : p)
     if (x) cudaFree(x);

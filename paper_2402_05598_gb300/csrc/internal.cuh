@@ -148,6 +148,10 @@ struct SolverWorkspace {
 
 }  // namespace fcgno
 
+namespace fcgno {
+struct TcActs;  // per-operator activations of the tensor-core preconditioner
+}  // namespace fcgno
+
 struct fcgno_op {
   int N = 0, B = 0;
   size_t n = 0;
@@ -157,6 +161,10 @@ struct fcgno_op {
   double* logk = nullptr;  // [B][n]
   float* logk32 = nullptr; // [B][n] (input of the 16-bit preconditioner)
   fcgno::SolverWorkspace ws;
+  // Activations of the 16-bit preconditioner applied to this operator's batch. They belong to
+  // the operator, not the model, so that solves of different operators with one model may
+  // run concurrently on different streams (a cache: allocated on first use).
+  mutable fcgno::TcActs* tc_acts = nullptr;
 };
 
 namespace fcgno {
@@ -200,6 +208,7 @@ fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, co
                          const int* active, double* z, bool fp16, cudaStream_t st);
 fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t st);
 void tc_model_free(fcgno_model* m);
+void tc_acts_free(fcgno_op* op);
 void no_workspace_free(fcgno_model* m);
 
 // Per-instance rms of r: rms[b] = sqrt(mean(r_b^2)).

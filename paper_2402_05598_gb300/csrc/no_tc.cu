@@ -121,11 +121,13 @@ static TcGeom make_geom(int N, int C, int M) {
     g.QT = 128;
     g.KSYN = round_up(2 * M, 16);
   }
-  // synthesis column chunk: 16 columns. A block's latency is its serial set-up plus its tiles
-  // streamed through the input ring; 16-column chunks halve the tiles per block, double the
-  // blocks (more of them in flight while few instances are active) and leave shared memory
-  // for an input ring that holds most of a block's tiles at once.
+  // synthesis column chunk: 32 columns when two blocks per SM still fit with a 3 + 2 slot
+  // tile ring, otherwise 16. A block's set-up (the instance's mixed coefficients, stage 1 and
+  // the read-back of U) does not shrink with the chunk, so wider chunks spend less of the SM's
+  // copy time on it: at 64 x 64 and 256 instances a hidden layer takes 45 us with 32-column
+  // chunks against 55 us with 16-column chunks (ncu, serialised launches).
   g.SPC = 16;
+  if (N < 128 && g.PC >= 32 && (g.MP / 128) * 64 <= 256 && synthesis_bytes(g, 32, 3, 2) <= kSynTwoPerSm) g.SPC = 32;
   while (g.SPC % g.PT != 0) g.SPC *= 2;
   g.snchunks = N / g.SPC;
   g.KB = round_up(g.SPC * 2 * M, 16) + 16;
@@ -243,12 +245,14 @@ struct TcPrecision {
 
 struct fcgno::TcModel {
   TcPrecision prec[2];  // 0: BF16, 1: FP16
-  // activation workspace
+};
+
+struct fcgno::TcActs {
   size_t cap_v = 0, cap_part = 0, cap_chat = 0;
   uint16_t* va = nullptr;
   uint16_t* vb = nullptr;
   uint16_t* part = nullptr;  // partial-coefficient images [mode][chunk][block of 128][128 x 2C]
-  uint16_t* chat = nullptr;
+  uint16_t* chat = nullptr;  // mixed-coefficient images, one per instance
 };
 
 namespace fcgno {
@@ -299,12 +303,22 @@ static void free_prec(TcPrecision& p) {
 void tc_model_free(fcgno_model* m) {
   if (!m->tc) return;
   for (auto& p : m->tc->prec) free_prec(p);
-  uint16_t* f[] = {m->tc->va, m->tc->vb, m->tc->chat};
-  for (auto x : f)
-    if (x) cudaFree(x);
-  if (m->tc->part) cudaFree(m->tc->part);
   delete m->tc;
   m->tc = nullptr;
+}
+
+static void free_acts(TcActs& A) {
+  uint16_t* f[] = {A.va, A.vb, A.part, A.chat};
+  for (auto x : f)
+    if (x) cudaFree(x);
+  A = TcActs{};
+}
+
+void tc_acts_free(fcgno_op* op) {
+  if (!op->tc_acts) return;
+  free_acts(*op->tc_acts);
+  delete op->tc_acts;
+  op->tc_acts = nullptr;
 }
 
 fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t) {
@@ -1230,24 +1244,29 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
                            double* z, bool fp16, cudaStream_t st) {
   const fcgno_model_desc& d = m->desc;
   const TcGeom g = make_geom(op->N, C, d.modes);
+  const uint64_t gen0 = m->gen;
   FCGNO_TRY(ensure_prec(m, fp16, st));
   TcTables* tab = nullptr;
   FCGNO_TRY(ensure_tables(m, fp16, g, tab, st));
-  TcModel& T = *m->tc;
-  TcPrecision& P = T.prec[fp16 ? 1 : 0];
+  if (m->gen != gen0) {
+    // derived weight images or tables were just built on `st`: finish them before going on,
+    // so that operators solved on other streams never read them half written. This happens
+    // once per model, precision and grid, in the eager first iteration of a solve or bucket;
+    // under stream capture the build kernels are captured ahead of their readers instead.
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    FCGNO_CUDA_TRY(cudaStreamIsCapturing(st, &cap));
+    if (cap == cudaStreamCaptureStatusNone) FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+  }
+  TcPrecision& P = m->tc->prec[fp16 ? 1 : 0];
+  if (!op->tc_acts) op->tc_acts = new TcActs();
+  TcActs& T = *op->tc_acts;
   const int B = op->B;
   const size_t n = op->n;
   const int nbt = ceil_div(B, 128);
   const size_t need_v = (size_t)B * n * C, need_part = (size_t)g.nmodes * g.nchunks * nbt * 128 * 2 * C,
                need_chat = (size_t)B * g.MP * g.KXP;
   if (T.cap_v < need_v || T.cap_part < need_part || T.cap_chat < need_chat) {
-    if (T.va) cudaFree(T.va);
-    if (T.vb) cudaFree(T.vb);
-    if (T.part) cudaFree(T.part);
-    if (T.chat) cudaFree(T.chat);
-    T.va = T.vb = T.chat = nullptr;
-    T.part = nullptr;
-    T.cap_v = T.cap_part = T.cap_chat = 0;
+    free_acts(T);
     if (cudaMalloc(&T.va, need_v * 2) != cudaSuccess || cudaMalloc(&T.vb, need_v * 2) != cudaSuccess ||
         cudaMalloc(&T.part, need_part * 2) != cudaSuccess || cudaMalloc(&T.chat, need_chat * 2) != cudaSuccess) {
       cudaGetLastError();

@@ -2,13 +2,16 @@
 
 Requests (grid size N, coefficient field k, right-hand side f, initial guess u_0) arrive
 over time. Each grid size has one resident bucket (``fcgno.Bucket``) whose capacity was
-admitted against an HBM budget when the server started. The loop repeatedly
+admitted against an HBM budget when the server started. With the 16-bit preconditioner
+every bucket runs on its own CUDA stream, so the steps of different grid sizes overlap on
+the GPU and a small solve does not wait behind a large one. The loop repeatedly
   1. admits every arrived request whose bucket has a free slot (first come, first served;
      the others wait in their bucket's queue),
-  2. advances every bucket that has running slots by one step (a few FCG-NO iterations,
-     replayed as one CUDA graph),
-  3. polls the buckets and retires finished slots (converged, breakdown, or capped),
-     recording each request's completion time.
+  2. starts one step (a few FCG-NO iterations, replayed as one CUDA graph) of every bucket
+     that has running slots and no step in flight,
+  3. for every bucket whose step has finished (an event query, no waiting), reads the slot
+     states and retires finished slots (converged, breakdown, or capped), recording each
+     request's completion time.
 Latency = completion time - arrival time (queueing included).
 """
 from __future__ import annotations
@@ -71,15 +74,27 @@ def plan_capacities(sizes_weights: dict, budget_bytes: int, m_max: int, desc, pr
 
 class Server:
     def __init__(self, model, capacities: dict, prec="bf16", m_max=1, tol=1e-6, max_iter=400, iters_per_step=8):
+        import torch
+        # The CUDA-core FP64/FP32 preconditioner keeps its activations in the model, so its
+        # buckets share one stream; the 16-bit path keeps them per operator (per bucket).
+        concurrent = prec in ("bf16", "fp16")
+        shared = torch.cuda.Stream()
+        self.streams = {N: (torch.cuda.Stream() if concurrent else shared) for N in capacities}
         self.buckets = {N: F.Bucket(N, cap, model, prec=prec, m_max=m_max, tol=tol, max_iter=max_iter,
-                                    iters_per_step=iters_per_step) for N, cap in capacities.items()}
+                                    iters_per_step=iters_per_step, stream=self.streams[N])
+                        for N, cap in capacities.items()}
         self.slots = {N: [None] * cap for N, cap in capacities.items()}
         self.queues = {N: deque() for N in capacities}
+        self.inflight = {N: None for N in capacities}  # event recorded after the bucket's last step
 
     def run(self, requests: list, stats: ServeStats) -> ServeStats:
         """Serves the requests (sorted by arrival) and returns latency statistics."""
         import torch
         pending = deque(sorted(requests, key=lambda r: r.arrival))
+        # requests reference device tensors made on the current stream: order the buckets'
+        # streams after them
+        for s_ in set(self.streams.values()):
+            s_.wait_stream(torch.cuda.current_stream())
         t0 = time.perf_counter()
         outstanding = len(pending)
         while outstanding:
@@ -87,7 +102,7 @@ class Server:
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
                 self.queues[r.N].append(r)
-            # admit into free slots
+            # admit into free slots (ordered after the bucket's step in flight, if any)
             for N, q in self.queues.items():
                 slots = self.slots[N]
                 for i in range(len(slots)):
@@ -95,27 +110,39 @@ class Server:
                         break
                     if slots[i] is None:
                         r = q.popleft()
-                        self.buckets[N].admit(i, r.k, r.f, r.x0)
+                        self.buckets[N].admit(i, r.k, r.f, r.x0, stream=self.streams[N])
                         slots[i] = r
+            # start a step of every bucket with running slots and no step in flight
             busy = [N for N, slots in self.slots.items() if any(s is not None for s in slots)]
-            if not busy:
-                if pending:  # idle until the next arrival
-                    time.sleep(max(0.0, min(0.001, pending[0].arrival - (time.perf_counter() - t0))))
-                continue
             for N in busy:
-                self.buckets[N].step()
-            for N in busy:
-                st, it, rr = self.buckets[N].poll()
+                if self.inflight[N] is None:
+                    self.buckets[N].step(stream=self.streams[N])
+                    ev = torch.cuda.Event()
+                    ev.record(self.streams[N])
+                    self.inflight[N] = ev
+            # retire the slots of every bucket whose step has finished
+            progressed = False
+            for N, ev in self.inflight.items():
+                if ev is None or not ev.query():
+                    continue
+                self.inflight[N] = None
+                progressed = True
+                st, it, rr = self.buckets[N].poll(stream=self.streams[N])
                 tnow = time.perf_counter() - t0
                 for i, r in enumerate(self.slots[N]):
                     if r is not None and st[i] != -1:
-                        self.buckets[N].take(i)
+                        self.buckets[N].take(i, stream=self.streams[N])
                         r.done, r.iters, r.status, r.relres = tnow, int(it[i]), int(st[i]), float(rr[i])
                         stats.latencies_ms.append(1000.0 * (r.done - r.arrival))
                         stats.completed += 1
                         stats.converged += int(r.status == F.FCGNO_OK)
                         self.slots[N][i] = None
                         outstanding -= 1
+            if not progressed:
+                if not busy and pending:  # idle until the next arrival
+                    time.sleep(max(0.0, min(0.001, pending[0].arrival - (time.perf_counter() - t0))))
+                elif busy:
+                    time.sleep(2e-5)
         torch.cuda.synchronize()
         stats.wall_s = time.perf_counter() - t0
         return stats

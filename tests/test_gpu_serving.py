@@ -95,3 +95,35 @@ def test_bucket_slot_matches_oracle_cg_and_stops_itself(lib, dev):
     assert rr[0] <= 1e-8
     true_res = np.linalg.norm(fn - O.apply_A(kn, x.cpu().numpy())) / np.linalg.norm(fn - O.apply_A(kn, x0n))
     assert true_res < 1e-7
+
+
+def test_concurrent_buckets_sharing_a_model_match_alone(lib, dev):
+    """Buckets of two grid sizes that share one BF16 model step concurrently on their own
+    streams (as the serving loop runs them): each slot's result equals its result when its
+    bucket runs alone. The preconditioner's activations belong to each bucket's operator, so
+    the concurrent steps cannot overwrite each other's."""
+    import torch
+    C, M = 32, 12
+    desc = I.ModelDesc(width=C, layers=4, modes=M, proj_width=C)
+    w = torch.from_numpy(I.xavier_weights(desc, 5)).to(dev)
+    model = lib.Model(lib.make_desc(C, 4, M, C), w)
+    sizes = (64, 128)
+    alone = {N: run_alone(lib, dev, model, N, 3300 + N, "bf16", 3, max_iter=24) for N in sizes}
+    streams = {N: torch.cuda.Stream() for N in sizes}
+    bks = {N: lib.Bucket(N, 4, model, prec="bf16", iters_per_step=8, max_iter=24, stream=streams[N]) for N in sizes}
+    for N in sizes:
+        streams[N].wait_stream(torch.cuda.current_stream())
+        bks[N].admit(0, *dev_arrays(N, 3300 + N, dev), stream=streams[N])
+    for _ in range(3):
+        for N in sizes:
+            bks[N].step(stream=streams[N])
+    for N in sizes:
+        st, it, rr = bks[N].poll(stream=streams[N])
+        x = torch.empty((N, N), dtype=torch.float64, device=dev)
+        with torch.cuda.stream(streams[N]):
+            bks[N].take(0, x, stream=streams[N])
+        streams[N].synchronize()
+        xa, ia, ra, sa = alone[N]
+        assert int(it[0]) == ia == 24 and int(st[0]) == sa
+        assert np.array_equal(x.cpu().numpy(), xa)
+        assert float(rr[0]) == ra
