@@ -149,7 +149,7 @@ def roofline_synthesis(active_per_iter, N, C, M, layers):
 # per active instance, mean of the four layers of an iteration, measured by ncu on this
 # kernel at 64 x 64, 256 instances, width 32, 12 x 12 modes. Scaled by the active instances
 # per launch; None when the kernel has changed since the last capture.
-SYN_TRAFFIC_PER_INSTANCE = 355_420
+SYN_TRAFFIC_PER_INSTANCE = 351_168
 
 
 SERVE_SIZES = {64: 0.40, 128: 0.25, 256: 0.20, 512: 0.10, 1024: 0.05}

@@ -864,18 +864,19 @@ struct SynArgs {
 //
 // Warp-specialised: warps 0-7 (256 threads) are the epilogue; warps w and w+4 read the same
 // 32 TMEM lanes (quadrant w % 4) and split the columns (U read-back) and the channels (tile
-// epilogue) between them. Lane 0 of warp 8 issues every MMA, lane 0 of warp 9 every bulk copy
-// into shared memory and lane 0 of warp 10 every bulk store.
-// The three roles meet only on mbarriers; four TMEM accumulators let the MMAs run up to three
+// epilogue) between them. Lane 0 of warp 8 issues every MMA and lane 0 of warp 9 every bulk
+// copy into shared memory (warp 10 has no role left).
+// The roles meet only on mbarriers; four TMEM accumulators let the MMAs run up to three
 // tiles ahead of the epilogue, so that their latency is hidden.
 //
 // Data movement: the chunk-invariant operands arrive by one bulk copy each. The activation
 // tiles (128 grid points x C channels, tile-major, so each is one contiguous block already in
 // the K-major operand layout) stream through a ring of din input slots, each filled by one
-// bulk copy and released as soon as its MMA has completed; the epilogue writes the layer
-// output into a ring of dout output slots (same layout), each drained by one bulk store (or,
-// in the last layer, read by the decoder MMA). For N >= 128 the chunk's tiles are visited row
-// block by row block (tile t: q tile t / SPC, column t % SPC).
+// bulk copy and released as soon as its MMA has completed. A hidden layer's epilogue writes
+// its tile rows straight to the tile-major output (consecutive threads, consecutive 16-byte
+// rows: coalesced), which leaves the copy engine to the loads; the last layer writes them into
+// a ring of dout output slots (same layout) read by the decoder MMA. For N >= 128 the chunk's
+// tiles are visited row block by row block (tile t: q tile t / SPC, column t % SPC).
 constexpr int kSynEpi = 256;                 // epilogue threads
 constexpr int kSynThreads = kSynEpi + 96;    // + the MMA, load and store warps
 constexpr int kSynMaxIn = 8, kSynMaxOut = 2;
@@ -1081,24 +1082,9 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
       }
     }
   } else if (warp == kSynEpi / 32 + 2) {
-    // ================================ store issuer (one lane) ==========================
-    pdl_wait();  // (before its global writes)
-    if (lane == 0 && !a.project) {
-      // store the layer output of tile u; release the output slot of tile u - 1 once its
-      // store (not the latest one) has read it
-      for (int u = 0; u < ntiles && ok; ++u) {
-        ok = mbar_wait(&outready[u % DO], (u / DO) & 1);
-        if (!ok) break;
-        bulk_s2g(a.vout + tile_index(u) * 128 * C, oring + (u % DO) * TB, TB);
-        bulk_commit();
-        if (u >= 1) {
-          bulk_wait_read<1>();
-          mbar_arrive(&outfree[(u - 1) % DO]);
-        }
-      }
-      if (!ok) atomicExch(a.err, 1);
-      bulk_wait_read<0>();
-    }
+    // ================================ (idle warp) =====================================
+    // hidden layers store straight from the epilogue; the last layer's output slots are read
+    // by the decoder MMA
   } else {
     // ================================ epilogue (256 threads) ===========================
     pdl_wait();  // (before its global writes)
@@ -1160,10 +1146,20 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
           const float x = h[i] + bias[i];
           h[i] = a.activate ? gelu16(x) : x;
         }
-        // the output slot's previous tile (t - DO) has been stored / decoded
-        if (t >= DO) ok = mbar_wait(&outfree[t % DO], ((t / DO) - 1) & 1);
+        // the output slot's previous tile (t - DO) has been decoded
+        if (a.project && t >= DO) ok = mbar_wait(&outfree[t % DO], ((t / DO) - 1) & 1);
       }
-      if (ok) {
+      if (ok && !a.project) {
+        // hidden layer: the tile row goes straight to the tile-major output (consecutive
+        // threads write consecutive 16-byte rows), leaving the copy engine to the loads
+        uint8_t* dst = reinterpret_cast<uint8_t*>(a.vout + tile_index(t) * 128 * C) + m * 16;
+#pragma unroll
+        for (int c0 = 0; c0 < CH; c0 += 8) {
+          *reinterpret_cast<uint4*>(dst + ((cbase + c0) / 8) * LBO_T) =
+              make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
+                         pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
+        }
+      } else if (ok) {
         uint8_t* dst = oring + (t % DO) * TB + m * 16;
 #pragma unroll
         for (int c0 = 0; c0 < CH; c0 += 8) {
@@ -1219,6 +1215,8 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
   __syncthreads();
   if (warp == 0) tmem_dealloc(tbase, TCOLS);
 }
+
+
 
 // ------------------------------------ host ---------------------------------------------
 static size_t analysis_smem(const TcGeom& g) {
@@ -1337,8 +1335,12 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     s.g = g;
     s.B = B;
     s.bf16 = bf16;
-    s.din = din;
-    s.dout = dout;
+    // hidden layers store straight from the epilogue: their input ring also takes the
+    // output slots' bytes (same shared-memory size)
+    const bool last = l == d.layers - 1;
+    const size_t slot_in = (size_t)128 * C * 2 + (g.N >= 128 ? (size_t)128 * g.KSYN * 2 : 0);
+    s.din = last ? din : std::min<int>(kSynMaxIn, (int)(((size_t)din * slot_in + (size_t)dout * 128 * C * 2) / slot_in));
+    s.dout = last ? dout : 0;
     s.active = active;
     s.chat = T.chat;
     s.W = P.W[l];
