@@ -73,15 +73,24 @@ def plan_capacities(sizes_weights: dict, budget_bytes: int, m_max: int, desc, pr
 
 
 class Server:
-    def __init__(self, model, capacities: dict, prec="bf16", m_max=1, tol=1e-6, max_iter=400, iters_per_step=8):
-        import torch
+    """``bucket_factory`` (default ``fcgno.Bucket``) and ``cuda`` (default ``torch.cuda``: Stream,
+    Event, current_stream, synchronize) can be replaced, e.g. by host-side fakes that test the
+    scheduling without a GPU."""
+
+    def __init__(self, model, capacities: dict, prec="bf16", m_max=1, tol=1e-6, max_iter=400, iters_per_step=8,
+                 bucket_factory=None, cuda=None):
+        if cuda is None:
+            import torch
+            cuda = torch.cuda
+        self.cuda = cuda
+        bucket_factory = bucket_factory or F.Bucket
         # The CUDA-core FP64/FP32 preconditioner keeps its activations in the model, so its
         # buckets share one stream; the 16-bit path keeps them per operator (per bucket).
         concurrent = prec in ("bf16", "fp16")
-        shared = torch.cuda.Stream()
-        self.streams = {N: (torch.cuda.Stream() if concurrent else shared) for N in capacities}
-        self.buckets = {N: F.Bucket(N, cap, model, prec=prec, m_max=m_max, tol=tol, max_iter=max_iter,
-                                    iters_per_step=iters_per_step, stream=self.streams[N])
+        shared = cuda.Stream()
+        self.streams = {N: (cuda.Stream() if concurrent else shared) for N in capacities}
+        self.buckets = {N: bucket_factory(N, cap, model, prec=prec, m_max=m_max, tol=tol, max_iter=max_iter,
+                                          iters_per_step=iters_per_step, stream=self.streams[N])
                         for N, cap in capacities.items()}
         self.slots = {N: [None] * cap for N, cap in capacities.items()}
         self.queues = {N: deque() for N in capacities}
@@ -89,12 +98,12 @@ class Server:
 
     def run(self, requests: list, stats: ServeStats) -> ServeStats:
         """Serves the requests (sorted by arrival) and returns latency statistics."""
-        import torch
+        cuda = self.cuda
         pending = deque(sorted(requests, key=lambda r: r.arrival))
         # requests reference device tensors made on the current stream: order the buckets'
         # streams after them
         for s_ in set(self.streams.values()):
-            s_.wait_stream(torch.cuda.current_stream())
+            s_.wait_stream(cuda.current_stream())
         t0 = time.perf_counter()
         outstanding = len(pending)
         while outstanding:
@@ -117,7 +126,7 @@ class Server:
             for N in busy:
                 if self.inflight[N] is None:
                     self.buckets[N].step(stream=self.streams[N])
-                    ev = torch.cuda.Event()
+                    ev = cuda.Event()
                     ev.record(self.streams[N])
                     self.inflight[N] = ev
             # retire the slots of every bucket whose step has finished
@@ -143,7 +152,7 @@ class Server:
                     time.sleep(max(0.0, min(0.001, pending[0].arrival - (time.perf_counter() - t0))))
                 elif busy:
                     time.sleep(2e-5)
-        torch.cuda.synchronize()
+        cuda.synchronize()
         stats.wall_s = time.perf_counter() - t0
         return stats
 
