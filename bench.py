@@ -109,7 +109,12 @@ def _oracle_worker(args):
     return time.perf_counter() - t, out["iterations"]
 
 
-def oracle_sample(blob: np.ndarray, n_inst: int, iters: int, cores: int):
+def workload_name(m: int) -> str:
+    return (f"FCG-NO eval: {EVAL_BATCH} instances/GPU, {N_GRID}x{N_GRID} diffusion (k=exp(GRF 0.1, 1)), "
+            f"FNO width {WIDTH}, {LAYERS} layers, {MODES}x{MODES} modes, m={m}, tol {TOL}")
+
+
+def oracle_sample(blob: np.ndarray, n_inst: int, iters: int, cores: int, m_max: int = 5):
     """Times the oracle FCG-NO on n_inst instances, `iters` fixed iterations each, in a pool of
     `cores` spawned single-threaded processes. Returns (wall seconds, total iterations)."""
     import multiprocessing as mp
@@ -118,7 +123,7 @@ def oracle_sample(blob: np.ndarray, n_inst: int, iters: int, cores: int):
     for k in env_old:
         os.environ[k] = "1"
     try:
-        jobs = [(N_GRID, 10000 + i, blob, 1, iters, True) for i in range(n_inst)]
+        jobs = [(N_GRID, 10000 + i, blob, m_max, iters, True) for i in range(n_inst)]
         t = time.perf_counter()
         with ctx.Pool(processes=cores) as pool:
             res = pool.map(_oracle_worker, jobs)
@@ -228,7 +233,7 @@ def run_reference(args):
     iters = args.ref_iters
     vals = []
     for s in range(args.warmup + args.steps):
-        wall, tot_it = oracle_sample(blob, cores, iters, cores)
+        wall, tot_it = oracle_sample(blob, cores, iters, cores, args.m)
         if s >= args.warmup:
             vals.append((wall, tot_it))
     wall = sum(v[0] for v in vals)
@@ -237,8 +242,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1000 * wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"FCG-NO eval, {N_GRID}x{N_GRID} diffusion, width {WIDTH}, {LAYERS} layers, "
-                                   f"{MODES}x{MODES} modes, m=1, tol 1e-6", "grid": N_GRID},
+            "config": {"workload": workload_name(args.m), "grid": N_GRID, "instances_per_gpu": EVAL_BATCH},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores,
                              "sample": f"{cores} instances per step, {iters} FCG-NO iterations each (the GPU arm's "
                                        f"iterations per solve), one single-threaded process per core"},
@@ -423,9 +427,7 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "bf16" if args.prec == "bf16" else "f16", "data": "synthetic",
-            "config": {"workload": f"FCG-NO eval: {EVAL_BATCH} instances/GPU, {N_GRID}x{N_GRID} diffusion "
-                                   f"(k=exp(GRF 0.1, 1)), FNO width {WIDTH}, {LAYERS} layers, {MODES}x{MODES} modes, "
-                                   f"m={args.m}, tol {TOL}", "grid": N_GRID, "instances_per_gpu": EVAL_BATCH,
+            "config": {"workload": workload_name(args.m), "grid": N_GRID, "instances_per_gpu": EVAL_BATCH,
                        "l2": "flushed (256 MB write) between timed steps",
                        "training": None if tr is None else {"steps": tr.steps, "batch": 32, "instances":
                                                             args.train_instances, "krylov_K": 100,
@@ -512,7 +514,7 @@ def main():
         it_solve = max(1, int(round(np.mean(iters))))
         # the oracle's cost per iteration does not depend on the weight values: it runs the seeded
         # initial weights (no value produced by the CUDA path enters the oracle)
-        wall, tot_it = oracle_sample(I.xavier_weights(desc_np, 0), cores, it_solve, cores)
+        wall, tot_it = oracle_sample(I.xavier_weights(desc_np, 0), cores, it_solve, cores, args.m)
         line["cpu_baseline"] = {"kind": "oracle", "value": cores / wall, "unit": UNIT, "cores": cores,
                                 "sample": f"{cores} instances, {it_solve} FCG-NO iterations each (the GPU solve's "
                                           f"mean iterations per solve), FP64 numpy oracle, one single-threaded "
