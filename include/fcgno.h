@@ -171,6 +171,17 @@ fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x
 fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
                               int batch, fcgno_prec prec, float* loss, float* grad, void* stream);
 
+/* Activation checkpointing of fcgno_train_step / fcgno_train_step_loss (a memory option, not
+ * part of the method). The forward keeps every layer's input and its (small) analysis output
+ * for the backward; the layers' pre-activations (batch*N*N*width values each) are kept as well
+ * (mode 2, "never recompute"), or rebuilt one layer at a time during the backward from the
+ * kept input (mode 1, "always": about half the activation memory, one more mixing and
+ * synthesis pass per layer, bit-identical gradients). Mode 0 (default) recomputes when the
+ * kept pre-activations would exceed 2 GiB, e.g. fine-tuning on 1024 x 1024 or 2048 x 2048
+ * grids. Takes effect at the next training step. Errors: EINVAL for a NULL model or another
+ * mode. */
+fcgno_status fcgno_model_set_train_recompute(fcgno_model_t model, int mode);
+
 /* Training losses. FCGNO_LOSS_ENERGY is Eq. (11) in error form (the A-norm); FCGNO_LOSS_L2
  * is the paper's ablation loss in error form, mean_b ||z_b - e_b||_2 / ||e_b||_2 (defined
  * beside Eq. (11) in Section 2.4.1 and compared with it in Section 3.4). */

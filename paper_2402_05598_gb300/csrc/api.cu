@@ -163,6 +163,15 @@ extern "C" fcgno_status fcgno_model_sync(fcgno_model_t m, void* stream) {
   return tc_model_sync(m, st);
 }
 
+extern "C" fcgno_status fcgno_model_set_train_recompute(fcgno_model_t m, int mode) {
+  if (!m || mode < 0 || mode > 2) {
+    set_last_error("fcgno_model_set_train_recompute: need a model and mode 0 (auto), 1 (always) or 2 (never)");
+    return FCGNO_EINVAL;
+  }
+  m->train_recompute = mode;
+  return FCGNO_OK;
+}
+
 extern "C" fcgno_status fcgno_model_create(const fcgno_model_desc* desc, const float* weights, void* stream,
                                            fcgno_model_t* out) {
   if (!out || !weights || !desc_ok(desc)) {

@@ -182,6 +182,7 @@ struct fcgno_model {
   fcgno::NoWorkspace* ws = nullptr;
   fcgno::TcModel* tc = nullptr;
   uint64_t gen = 0;             // bumped whenever a derived device buffer is (re)allocated
+  int train_recompute = 0;      // 0: recompute pre-activations above a size threshold; 1: always; 2: never
 };
 
 namespace fcgno {

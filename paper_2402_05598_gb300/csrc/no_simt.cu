@@ -47,7 +47,8 @@ struct TrainBuffers {
   int L = 0, C = 0, Cp = 0, Kx = 0, Ky = 0, B = 0;
   void* x0 = nullptr;                 // [pts][2]  (r/rms, log k)
   std::vector<void*> vin;             // L+1 activations [pts][C] (inputs of each layer, vin[L] = last output)
-  std::vector<void*> hpre;            // L pre-activations [pts][C]
+  std::vector<void*> hpre;            // L pre-activations [pts][C] (one scratch buffer when recomputing)
+  bool recompute = false;             // pre-activations rebuilt in the backward instead of kept
   std::vector<void*> chat;            // L analysis outputs [B][Kx][Ky][C] complex
   void* apre = nullptr;               // [pts][Cp] decoder pre-activation
   void* ghid = nullptr;               // [pts][Cp] GELU(apre)
@@ -499,7 +500,7 @@ static fcgno_status forward_simt(fcgno_model* m, const fcgno_op* op, const T* wb
     FCGNO_LAUNCHED();
     FCGNO_TRY(launch_synthesis_p<T>(N, B, C, M, active, (Cx<T>*)s.spec2, tw1, (Cx<T>*)s.mid, st));
     FCGNO_TRY(launch_syn_q_pw<T>(N, B, C, M, active, cur, (Cx<T>*)s.mid, tw2, W.w[l], 0, W.b[l], (T)1, (T)2,
-                                 l < L - 1, nxt, tr ? (T*)tr->hpre[l] : nullptr, st));
+                                 l < L - 1, nxt, (tr && !tr->recompute) ? (T*)tr->hpre[l] : nullptr, st));
     cur = nxt;
   }
   const size_t smem = (size_t)Cp * C * sizeof(T);
@@ -698,8 +699,15 @@ static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz)
   const fcgno_model_desc& d = m->desc;
   const size_t pts = (size_t)op->B * op->n;
   const int Kx = 2 * d.modes, Ky = d.modes;
+  // Activation checkpointing: the forward keeps every layer's input and its analysis output
+  // (small); the L pre-activations (pts x C each) are either kept too or rebuilt one layer at a
+  // time in the backward. Automatic mode rebuilds them when keeping them would take more than
+  // kKeepBudget bytes.
+  constexpr size_t kKeepBudget = (size_t)2 << 30;
+  const bool recompute = m->train_recompute == 1 ||
+                         (m->train_recompute == 0 && pts * d.width * esz * (size_t)d.layers > kKeepBudget);
   if (t.cap_pts == pts * esz && t.L == d.layers && t.C == d.width && t.Cp == d.proj_width && t.Kx == Kx &&
-      t.B == op->B)
+      t.B == op->B && t.recompute == recompute)
     return FCGNO_OK;
   // release and reallocate
   cfree(t.x0);
@@ -710,7 +718,7 @@ static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz)
                    (void**)&t.dvec, (void**)&t.zbuf, (void**)&t.rms, (void**)&t.lossb};
   for (void** p : more) cfree(*p);
   t.vin.assign(d.layers + 1, nullptr);
-  t.hpre.assign(d.layers, nullptr);
+  t.hpre.assign(recompute ? 1 : d.layers, nullptr);
   t.chat.assign(d.layers, nullptr);
   bool ok = true;
   auto al = [&](void** p, size_t bytes) {
@@ -740,6 +748,7 @@ static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz)
     return FCGNO_ENOMEM;
   }
   t.cap_pts = pts * esz;
+  t.recompute = recompute;
   t.L = d.layers;
   t.C = d.width;
   t.Cp = d.proj_width;
@@ -821,8 +830,20 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
   const T inv_n = (T)(1.0 / (double)n);
   T* gh = (T*)t.g1;
   for (int l = L - 1; l >= 0; --l) {
+    const T* hpre = (const T*)t.hpre[t.recompute ? 0 : l];
+    if (t.recompute) {
+      // rebuild layer l's pre-activation from its kept input and analysis output: the same
+      // kernels on the same inputs as the forward, so the values are bit-identical (the
+      // layer output, rewritten into vin[l + 1], is unchanged)
+      mix_kernel<T><<<nmodes, 256, C * C * sizeof(Cx<T>), st>>>(B, C, nmodes, nullptr, (const Cx<T>*)t.chat[l],
+                                                                 W.r[l], (Cx<T>*)s.spec2, 0);
+      FCGNO_LAUNCHED();
+      FCGNO_TRY(launch_synthesis_p<T>(N, B, C, M, nullptr, (Cx<T>*)s.spec2, tw1, (Cx<T>*)s.mid, st));
+      FCGNO_TRY(launch_syn_q_pw<T>(N, B, C, M, nullptr, (const T*)t.vin[l], (Cx<T>*)s.mid, tw2, W.w[l], 0, W.b[l],
+                                   (T)1, (T)2, l < L - 1, (T*)t.vin[l + 1], (T*)t.hpre[0], st));
+    }
     // gh = gv * act'(h)
-    act_bwd_kernel<T><<<ceil_div(pts * C, 256), 256, 0, st>>>(pts * C, gv, (const T*)t.hpre[l], l < L - 1, gh);
+    act_bwd_kernel<T><<<ceil_div(pts * C, 256), 256, 0, st>>>(pts * C, gv, hpre, l < L - 1, gh);
     FCGNO_LAUNCHED();
     // pointwise weight and bias
     FCGNO_TRY(outer_reduce<T>(pts, C, C, gh, (const T*)t.vin[l], (T*)t.partials, grad + BL.w[l], grad + BL.b[l], st));

@@ -62,6 +62,7 @@ def _load():
         "fcgno_krylov_harvest": (c_int, [P, P, P, P, c_int, P, P, POINTER(fcgno_solve_info), P]),
         "fcgno_train_step": (c_int, [P, P, P, P, c_int, c_int, P, P, P]),
         "fcgno_train_step_loss": (c_int, [P, P, P, P, c_int, c_int, c_int, P, P, P]),
+        "fcgno_model_set_train_recompute": (c_int, [P, c_int]),
         "fcgno_workspace_bytes": (c_size_t, [c_int, c_int, c_int, POINTER(fcgno_model_desc), c_int]),
         "fcgno_status_str": (c_char_p, [c_int]),
         "fcgno_last_error": (c_char_p, []),
@@ -88,7 +89,8 @@ lib = _load()
 EXPORTS = [
     "fcgno_assemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
-    "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss", "fcgno_workspace_bytes", "fcgno_status_str",
+    "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
+    "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_status_str",
     "fcgno_last_error", "fcgno_launch_count", "fcgno_trace_set", "fcgno_trace_collect",
     "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
     "fcgno_bucket_destroy",
@@ -188,6 +190,11 @@ class Model:
 
     def sync(self, stream=None):
         _check(lib.fcgno_model_sync(self.handle, _stream(stream)), "fcgno_model_sync")
+
+    def set_train_recompute(self, mode: str):
+        """Activation checkpointing of training steps: "auto", "always" or "never"."""
+        code = {"auto": 0, "always": 1, "never": 2}[mode]
+        _check(lib.fcgno_model_set_train_recompute(self.handle, code), "fcgno_model_set_train_recompute")
 
     def close(self):
         if self.handle:

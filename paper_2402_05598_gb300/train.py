@@ -20,6 +20,7 @@ import time
 from dataclasses import dataclass, field
 
 import numpy as np
+import torch
 
 from . import fcgno as F
 from . import inputs as I
@@ -81,6 +82,33 @@ class RandomResidualData:
             self.e[i] = x - u
 
 
+class PreconditionerLoss(torch.autograd.Function):
+    """The training loss of the neural preconditioner as an autograd node: Eq. (11) (energy
+    norm, loss_kind "energy") or the L2 ablation loss. The forward and the backward run in one
+    library call (fcgno_train_step: the reverse mode is hand-written in CUDA): the forward
+    computes the loss and the weight gradient together and keeps the gradient, which the
+    backward scales by the incoming gradient."""
+
+    @staticmethod
+    def forward(ctx, weights, model, op, r, e, prec, loss_kind):
+        loss = torch.zeros(1, dtype=torch.float32, device=weights.device)
+        grad = torch.empty_like(weights)
+        F.train_step(model, op, r, e, loss, grad, prec=prec, loss_kind=loss_kind)
+        ctx.save_for_backward(grad)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, g):
+        (grad,) = ctx.saved_tensors
+        return g * grad, None, None, None, None, None, None
+
+
+def preconditioner_loss(model: "F.Model", op: "F.Operator", r, e, prec: str = "fp32", loss_kind: str = "energy"):
+    """Scalar loss tensor of a batch (r, e) with ``model.weights`` as its autograd input:
+    ``preconditioner_loss(...).backward()`` fills ``model.weights.grad``."""
+    return PreconditionerLoss.apply(model.weights, model, op, r, e, prec, loss_kind)
+
+
 def _problems(dataset, N, seeds, sigma, ell):
     if dataset == "grf":
         return I.make_batch(N, seeds, sigma, ell)
@@ -112,11 +140,10 @@ def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, 
     torch.cuda.synchronize()
     t_h = time.perf_counter() - t0
     param = model.weights
+    param.requires_grad_(True)
     opt = torch.optim.Adam([param], lr=lr)
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
-    loss = torch.zeros(1, dtype=torch.float32, device=dev)
-    grad = torch.zeros_like(param)
     ar = torch.arange(batch, device=dev)
     losses = []
     t1 = time.perf_counter()
@@ -130,14 +157,17 @@ def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, 
         idx = torch.randint(0, K, (batch,), generator=gen, device=dev)
         r = d.r[idx, ar].contiguous()
         e = d.e[idx, ar].contiguous()
-        F.train_step(model, d.op, r, e, loss, grad, prec=prec, loss_kind=loss_kind)
-        param.grad = grad
+        opt.zero_grad(set_to_none=True)
+        loss = preconditioner_loss(model, d.op, r, e, prec=prec, loss_kind=loss_kind)
+        loss.backward()
         opt.step()
         if prec == "fp64":
             model.sync()
         if log_every and step % log_every == 0:
             losses.append((step, float(loss.item())))
         step += 1
+    param.requires_grad_(False)
+    param.grad = None
     model.sync()
     torch.cuda.synchronize()
     return TrainResult(steps=step, seconds=time.perf_counter() - t1, harvest_seconds=t_h, losses=losses)

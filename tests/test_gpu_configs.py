@@ -94,3 +94,36 @@ def test_bf16_iterations_within_15_percent_of_fp64(lib, dev):
     assert np.mean(its["bf16"]) <= 1.15 * np.mean(its["fp64"]), its
     for b in range(B):
         assert its["bf16"][b] <= 1.5 * its["fp64"][b] + 2, (b, its)
+
+
+def test_fine_tuning_step_on_the_large_grid_recomputes_and_matches(lib, dev):
+    """A fine-tuning step of the large-solve configuration (1024 x 1024, 8 instances, width 32,
+    16 x 16 modes) on Krylov vectors of CG (with a coarse CG solution as u*, which only sets
+    the error vectors e_i = u* - u_i): in the automatic mode the step rebuilds the
+    pre-activations (they would take 4 GiB) and returns exactly the loss and gradient of the
+    step that keeps them; both are finite and the loss (a ratio of energy norms) is positive."""
+    import torch
+    N, B = 1024, 8
+    k, f = batch(N, B, 7300, 2.0, 0.05)
+    desc, P, model, wdev = model_pair(lib, dev, 32, 16)
+    op = lib.Operator(to_dev(k, dev))
+    fb = to_dev(f, dev)
+    x0 = to_dev(np.random.default_rng(5).standard_normal((B, N, N)), dev)
+    ustar = torch.zeros_like(fb)
+    lib.solve(op, None, fb, ustar, tol=1e-4, m_max=1, max_iter=2000, prec="fp64", check_every=64)
+    K = 3
+    r_out = torch.empty((K, B, N, N), dtype=torch.float64, device=dev)
+    e_out = torch.empty_like(r_out)
+    lib.krylov_harvest(op, fb, x0, ustar, K, r_out, e_out)
+    r, e = r_out[K - 1].contiguous(), e_out[K - 1].contiguous()
+    out = {}
+    for mode in ("auto", "never"):
+        model.set_train_recompute(mode)
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        grad = torch.zeros(wdev.numel(), dtype=torch.float32, device=dev)
+        lib.train_step(model, op, r, e, loss, grad, prec="fp32")
+        torch.cuda.synchronize()
+        out[mode] = (loss.clone(), grad.clone())
+    assert torch.isfinite(out["auto"][1]).all() and np.isfinite(out["auto"][0].item())
+    assert torch.equal(out["auto"][0], out["never"][0]) and torch.equal(out["auto"][1], out["never"][1])
+    assert out["auto"][0].item() > 0.0

@@ -321,6 +321,51 @@ def check_train_step(lib, dev, prec, tol, kind):
             assert rel(g[o:o + s], g_ref[o:o + s]) < max(tol * 10, 1e-7), name
 
 
+@pytest.mark.parametrize("kind", ["energy", "l2"])
+def test_autograd_loss_gives_the_library_gradient(lib, dev, kind):
+    """The training loss as a torch.autograd.Function: loss.backward() leaves exactly the
+    hand-written gradient of fcgno_train_step in weights.grad (scaled by the upstream
+    gradient), and the forward value is the library's loss."""
+    import torch
+    from paper_2402_05598_gb300 import train as T
+    N, B, C, M = 32, 3, 16, 8
+    k, f = batch(N, B, 1300)
+    es = np.stack([np.linalg.solve(O.dense_A(k[b]), f[b].ravel()).reshape(N, N) for b in range(B)])
+    desc, P, model, wdev = model_pair(lib, dev, C, M, L=4, seed=2)
+    op = lib.Operator(to_dev(k, dev))
+    r, e = to_dev(f, dev), to_dev(es, dev)
+    loss0 = torch.zeros(1, dtype=torch.float32, device=dev)
+    grad0 = torch.zeros(wdev.numel(), dtype=torch.float32, device=dev)
+    lib.train_step(model, op, r, e, loss0, grad0, prec="fp32", loss_kind=kind)
+    wdev.requires_grad_(True)
+    loss = T.preconditioner_loss(model, op, r, e, prec="fp32", loss_kind=kind)
+    (2.5 * loss).backward()
+    assert loss.item() == loss0.item()
+    assert torch.equal(wdev.grad, 2.5 * grad0)
+    wdev.requires_grad_(False)
+
+
+@pytest.mark.parametrize("prec,kind", [("fp32", "energy"), ("fp64", "energy"), ("fp32", "l2")])
+def test_training_with_recomputed_preactivations_is_bit_identical(lib, dev, prec, kind):
+    """Activation checkpointing: a training step that rebuilds every layer's pre-activation
+    in the backward returns exactly the loss and gradient of the step that keeps them."""
+    import torch
+    N, B, C, M = 32, 3, 16, 8
+    k, f = batch(N, B, 1350)
+    es = np.stack([np.linalg.solve(O.dense_A(k[b]), f[b].ravel()).reshape(N, N) for b in range(B)])
+    desc, P, model, wdev = model_pair(lib, dev, C, M, L=4, seed=3)
+    op = lib.Operator(to_dev(k, dev))
+    out = {}
+    for mode in ("never", "always"):
+        model.set_train_recompute(mode)
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        grad = torch.zeros(wdev.numel(), dtype=torch.float32, device=dev)
+        lib.train_step(model, op, to_dev(f, dev), to_dev(es, dev), loss, grad, prec=prec, loss_kind=kind)
+        out[mode] = (loss.clone(), grad.clone())
+    assert torch.equal(out["never"][0], out["always"][0])
+    assert torch.equal(out["never"][1], out["always"][1])
+
+
 @pytest.mark.parametrize("N,B,steps,m", [(32, 2, 4, 1), (100, 2, 3, 2)])
 def test_jacobi_preconditioned_iterates_match_oracle(lib, dev, N, B, steps, m):
     """Algorithm 1 with the Jacobi(k) preconditioner of Eq. (15), fused (N <= 80) and tiled
