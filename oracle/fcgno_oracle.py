@@ -29,6 +29,14 @@ Readings of points the paper leaves open (the same readings the library implemen
   c(k) = (1/n) sum_x v(x) exp(-2 pi i k.x / N), synthesis
   v(x) = Re sum_k w_k2 c(k) exp(+2 pi i k.x / N) with w_0 = 1, w_{k2>0} = 2.
 - GELU is the exact erf form.
+
+Pins (tests/test_oracle_pins.py) fix every component against closed forms, textbook
+algorithms, numpy FFTs and the paper's Table 1. The composed neural-operator forward
+(no_forward with random weights) has no closed form: its analysis, mixing, synthesis,
+pointwise, GELU and encoder/decoder steps are each pinned, and the whole map is checked for
+shift equivariance and positive homogeneity, but the composition itself is parity unpinned
+(the CUDA path is compared with this oracle only). The same holds for FCG-NO iterates with
+that preconditioner.
 """
 from __future__ import annotations
 
