@@ -279,6 +279,8 @@ def main():
     ap.add_argument("--profile", type=int, default=0,
                     help="profiling mode: no training, two solves of --profile-iters fixed iterations")
     ap.add_argument("--profile-iters", type=int, default=8)
+    ap.add_argument("--profile-grid", type=int, default=N_GRID, help="grid side of the profiling workload")
+    ap.add_argument("--profile-batch", type=int, default=EVAL_BATCH, help="instances of the profiling workload")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -304,8 +306,8 @@ def main():
     tr = None
     if args.profile:
         # short fixed-iteration solves with every instance active (the ncu capture workload)
-        seeds = range(10000, 10000 + EVAL_BATCH)
-        k_np, f_np = I.make_batch(N_GRID, seeds)
+        seeds = range(10000, 10000 + args.profile_batch)
+        k_np, f_np = I.make_batch(args.profile_grid, seeds)
         op = F.Operator(torch.from_numpy(k_np).to(dev))
         f = torch.from_numpy(f_np).to(dev)
         x = torch.zeros_like(f)
@@ -314,8 +316,8 @@ def main():
             info = F.solve(op, model, f, x, tol=TOL, m_max=args.m, max_iter=args.profile_iters, prec=args.prec,
                            fixed_iters=True, check_every=args.profile_iters)
         torch.cuda.synchronize()
-        print(json.dumps({"profile": True, "iters": info[0]["iters"], "instances": EVAL_BATCH,
-                          "launches": F.launch_count()}))
+        print(json.dumps({"profile": True, "iters": info[0]["iters"], "instances": args.profile_batch,
+                          "grid": args.profile_grid, "launches": F.launch_count()}))
         return
     if args.train_steps > 0:
         tr = T.train(model, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3, steps=args.train_steps,

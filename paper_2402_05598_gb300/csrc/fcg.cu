@@ -155,15 +155,34 @@ __global__ void __launch_bounds__(kThreads) init_kernel(IterArgs a, State s) {
       acc[0] = fma(rv, rv, acc[0]);
     }
   }
-  block_sum<double, 1>(acc, scratch);
-  if (threadIdx.x == 0) s.part[((size_t)b * a.tiles + blockIdx.x) * kParts] = acc[0];
+  const double tot = block_sum_lane<double, 1>(acc, 1, scratch);
+  if (threadIdx.x == 0) s.part[((size_t)b * a.tiles + blockIdx.x) * kParts] = tot;
 }
 
-__global__ void init_finalize_kernel(IterArgs a, State s) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= a.B) return;
-  double rr = 0.0;
-  for (int t = 0; t < a.tiles; ++t) rr += s.part[((size_t)b * a.tiles + t) * kParts];
+// Per-instance total of the first `count` tile partials (one block of kThreads per instance):
+// thread i adds tiles i, i + kThreads, ... in order, then a fixed-order block reduction;
+// returns the total of partial j in thread j (j < count).
+template <int NV>
+__device__ __forceinline__ double tile_totals(const IterArgs& a, const State& s, int b, int count, int first,
+                                              double* scratch) {
+  double v[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) v[j] = 0.0;
+  for (int t = threadIdx.x; t < a.tiles; t += blockDim.x) {
+    const double* pp = s.part + ((size_t)b * a.tiles + t) * kParts + first;
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < count) v[j] += pp[j];
+  }
+  return block_sum_lane<double, NV>(v, count, scratch);
+}
+
+__global__ void __launch_bounds__(kThreads) init_finalize_kernel(IterArgs a, State s) {
+  __shared__ double scratch[32];
+  const int b = blockIdx.x;
+  const double rr_t = tile_totals<1>(a, s, b, 1, 0, scratch);
+  if (threadIdx.x != 0) return;
+  const double rr = rr_t;
   s.rr[b] = rr;
   s.r0[b] = sqrt(rr);
   s.rms[b] = sqrt(rr / (double)a.n);
@@ -183,36 +202,35 @@ __global__ void __launch_bounds__(kThreads) dots_w_kernel(IterArgs a, State s) {
   const Window w = window_of(a, s, b);
   if (s.status[b] != kRunning || w.m_i == 0) return;
   const size_t off = (size_t)b * a.n;
+  // the tile's w values stay in registers; each window entry is a warp-uniform branch around
+  // its own loads and FMAs (no FP64 work is issued for entries beyond m_i)
+  const size_t e0 = (size_t)blockIdx.x * kTile + threadIdx.x;
+  double wv[kEPT];
+#pragma unroll
+  for (int t = 0; t < kEPT; ++t) wv[t] = (e0 + t * kThreads < a.n) ? s.w[off + e0 + t * kThreads] : 0.0;
   double acc[kMaxWindow];
 #pragma unroll
-  for (int j = 0; j < kMaxWindow; ++j) acc[j] = 0.0;
-  for (int t = 0; t < kEPT; ++t) {
-    const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
-    if (e < a.n) {
-      const double wv = s.w[off + e];
+  for (int j = 0; j < kMaxWindow; ++j) {
+    acc[j] = 0.0;
+    if (j < w.m_i) {
+      const double* Sj = s.S + (size_t)w.slots[j] * a.B * a.n + off + e0;
 #pragma unroll
-      for (int j = 0; j < kMaxWindow; ++j)
-        if (j < w.m_i) acc[j] = fma(wv, s.S[(size_t)w.slots[j] * a.B * a.n + off + e], acc[j]);
+      for (int t = 0; t < kEPT; ++t)
+        if (e0 + t * kThreads < a.n) acc[j] = fma(wv[t], Sj[t * kThreads], acc[j]);
     }
   }
-  block_sum<double, kMaxWindow>(acc, scratch);
-  if (threadIdx.x < w.m_i) {
-    double v = acc[0];
-#pragma unroll
-    for (int j = 1; j < kMaxWindow; ++j)
-      if (threadIdx.x == j) v = acc[j];
-    s.part[((size_t)b * a.tiles + blockIdx.x) * kParts + threadIdx.x] = v;
-  }
+  const double tot = block_sum_lane<double, kMaxWindow>(acc, w.m_i, scratch);
+  if ((int)threadIdx.x < w.m_i) s.part[((size_t)b * a.tiles + blockIdx.x) * kParts + threadIdx.x] = tot;
 }
 
-__global__ void beta_kernel(IterArgs a, State s) {
+__global__ void __launch_bounds__(kThreads) beta_kernel(IterArgs a, State s) {
+  __shared__ double scratch[32 * kMaxWindow];
   const int b = blockIdx.x;
   const int j = threadIdx.x;
   const Window w = window_of(a, s, b);
-  if (s.status[b] != kRunning || j >= w.m_i) return;
-  double sum = 0.0;
-  for (int t = 0; t < a.tiles; ++t) sum += s.part[((size_t)b * a.tiles + t) * kParts + j];
-  s.beta[b * kMaxWindow + j] = sum / s.ps[(size_t)w.slots[j] * a.B + b];
+  if (s.status[b] != kRunning || w.m_i == 0) return;
+  const double sum = tile_totals<kMaxWindow>(a, s, b, w.m_i, 0, scratch);
+  if (j < w.m_i) s.beta[b * kMaxWindow + j] = sum / s.ps[(size_t)w.slots[j] * a.B + b];
 }
 
 __global__ void __launch_bounds__(kThreads) direction_kernel(IterArgs a, State s) {
@@ -224,16 +242,23 @@ __global__ void __launch_bounds__(kThreads) direction_kernel(IterArgs a, State s
 #pragma unroll
   for (int j = 0; j < kMaxWindow; ++j) beta[j] = (j < w.m_i) ? s.beta[b * kMaxWindow + j] : 0.0;
   double* pn = s.P + (size_t)w.slot_new * a.B * a.n + off;
-  for (int t = 0; t < kEPT; ++t) {
-    const size_t e = (size_t)blockIdx.x * kTile + t * kThreads + threadIdx.x;
-    if (e < a.n) {
-      double p = s.w[off + e];
+  const size_t e0 = (size_t)blockIdx.x * kTile + threadIdx.x;
+  double pv[kEPT];
 #pragma unroll
-      for (int j = 0; j < kMaxWindow; ++j)
-        if (j < w.m_i) p = fma(-beta[j], s.P[(size_t)w.slots[j] * a.B * a.n + off + e], p);
-      pn[e] = p;
+  for (int t = 0; t < kEPT; ++t) pv[t] = (e0 + t * kThreads < a.n) ? s.w[off + e0 + t * kThreads] : 0.0;
+  // one warp-uniform branch per window entry (no FP64 work for entries beyond m_i)
+#pragma unroll
+  for (int j = 0; j < kMaxWindow; ++j) {
+    if (j < w.m_i) {
+      const double* Pj = s.P + (size_t)w.slots[j] * a.B * a.n + off + e0;
+#pragma unroll
+      for (int t = 0; t < kEPT; ++t)
+        if (e0 + t * kThreads < a.n) pv[t] = fma(-beta[j], Pj[t * kThreads], pv[t]);
     }
   }
+#pragma unroll
+  for (int t = 0; t < kEPT; ++t)
+    if (e0 + t * kThreads < a.n) pn[e0 + t * kThreads] = pv[t];
 }
 
 __global__ void __launch_bounds__(kThreads) stencil_dots_kernel(IterArgs a, State s) {
@@ -260,24 +285,21 @@ __global__ void __launch_bounds__(kThreads) stencil_dots_kernel(IterArgs a, Stat
       acc[1] = fma(c, s.r[off + e], acc[1]);
     }
   }
-  block_sum<double, 2>(acc, scratch);
-  if (threadIdx.x == 0) {
-    double* pp = s.part + ((size_t)b * a.tiles + blockIdx.x) * kParts;
-    pp[0] = acc[0];
-    pp[1] = acc[1];
-  }
+  const double tot = block_sum_lane<double, 2>(acc, 2, scratch);
+  if (threadIdx.x < 2) s.part[((size_t)b * a.tiles + blockIdx.x) * kParts + threadIdx.x] = tot;
 }
 
-__global__ void alpha_kernel(IterArgs a, State s) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= a.B || s.status[b] != kRunning) return;
+__global__ void __launch_bounds__(kThreads) alpha_kernel(IterArgs a, State s) {
+  __shared__ double scratch[32 * 2];
+  __shared__ double pr_s;
+  const int b = blockIdx.x;
+  if (s.status[b] != kRunning) return;
   const Window w = window_of(a, s, b);
-  double ps = 0.0, pr = 0.0;
-  for (int t = 0; t < a.tiles; ++t) {
-    const double* pp = s.part + ((size_t)b * a.tiles + t) * kParts;
-    ps += pp[0];
-    pr += pp[1];
-  }
+  const double tot = tile_totals<2>(a, s, b, 2, 0, scratch);
+  if (threadIdx.x == 1) pr_s = tot;
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  const double ps = tot, pr = pr_s;
   if (!(ps != 0.0 && isfinite(ps) && isfinite(pr))) {
     s.status[b] = FCGNO_EBREAKDOWN;
     atomicAdd(s.ndone, 1);
@@ -306,16 +328,18 @@ __global__ void __launch_bounds__(kThreads) update_kernel(IterArgs a, State s) {
       acc[0] = fma(rv, rv, acc[0]);
     }
   }
-  block_sum<double, 1>(acc, scratch);
-  if (threadIdx.x == 0) s.part[((size_t)b * a.tiles + blockIdx.x) * kParts + 2] = acc[0];
+  const double tot = block_sum_lane<double, 1>(acc, 1, scratch);
+  if (threadIdx.x == 0) s.part[((size_t)b * a.tiles + blockIdx.x) * kParts + 2] = tot;
 }
 
-__global__ void norm_kernel(IterArgs a, State s) {
-  const int b = blockIdx.x * blockDim.x + threadIdx.x;
-  if (b >= a.B || s.status[b] != kRunning) return;
+__global__ void __launch_bounds__(kThreads) norm_kernel(IterArgs a, State s) {
+  __shared__ double scratch[32];
+  const int b = blockIdx.x;
+  if (s.status[b] != kRunning) return;
   const Window w = window_of(a, s, b);
-  double rr = 0.0;
-  for (int t = 0; t < a.tiles; ++t) rr += s.part[((size_t)b * a.tiles + t) * kParts + 2];
+  const double rr_t = tile_totals<1>(a, s, b, 1, 2, scratch);
+  if (threadIdx.x != 0) return;
+  const double rr = rr_t;
   s.rr[b] = rr;
   s.rms[b] = sqrt(rr / (double)a.n);
   s.iters[b] = w.i + 1;
@@ -333,6 +357,8 @@ template <int EPT>
 __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   extern __shared__ double sp[];  // n doubles (p), then kMaxWindow * blockDim (reductions)
   __shared__ double red_out[kMaxWindow];
+  __shared__ double beta_s[kMaxWindow];
+  __shared__ double alpha_s;
   pdl_wait();  // w (and, with the identity preconditioner, every vector) comes from the kernel before
   pdl_trigger();
   const int b = blockIdx.x;
@@ -363,11 +389,20 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
     }
   }
   if (wd.m_i > 0) block_sums<kMaxWindow>(acc, wd.m_i, red, red_out);
+  // beta_k = (w, s_k) / (p_k, s_k): one division per coefficient, shared through red_out
+  if ((int)threadIdx.x < wd.m_i) {
+    double dk = acc[0];
+#pragma unroll
+    for (int k = 1; k < kMaxWindow; ++k)
+      if ((int)threadIdx.x == k) dk = acc[k];
+    beta_s[threadIdx.x] = dk / s.ps[(size_t)wd.slots[threadIdx.x] * a.B + b];
+  }
+  __syncthreads();
   // p = w - sum beta_k p_k (kept in wv)
 #pragma unroll
   for (int k = 0; k < kMaxWindow; ++k) {
     if (k < wd.m_i) {
-      const double beta = acc[k] / s.ps[(size_t)wd.slots[k] * a.B + b];
+      const double beta = beta_s[k];
       const double* Pk = s.P + (size_t)wd.slots[k] * a.B * a.n + off;
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
@@ -414,7 +449,10 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
     }
     return;
   }
-  const double alpha = pr / ps;
+  // alpha = (p, r) / (p, s): one division, shared
+  if (threadIdx.x == 0) alpha_s = pr / ps;
+  __syncthreads();
+  const double alpha = alpha_s;
   double* Sn = s.S + (size_t)wd.slot_new * a.B * a.n + off;
   double rr[1] = {0.0};
 #pragma unroll
@@ -633,17 +671,17 @@ static fcgno_status launch_vector_step(const IterArgs& a, const State& s, const 
     const dim3 grid(a.tiles, a.B);
     dots_w_kernel<<<grid, kThreads, 0, cs>>>(a, s);
     FCGNO_LAUNCHED();
-    beta_kernel<<<a.B, 32, 0, cs>>>(a, s);
+    beta_kernel<<<a.B, kThreads, 0, cs>>>(a, s);
     FCGNO_LAUNCHED();
     direction_kernel<<<grid, kThreads, 0, cs>>>(a, s);
     FCGNO_LAUNCHED();
     stencil_dots_kernel<<<grid, kThreads, 0, cs>>>(a, s);
     FCGNO_LAUNCHED();
-    alpha_kernel<<<ceil_div(a.B, 128), 128, 0, cs>>>(a, s);
+    alpha_kernel<<<a.B, kThreads, 0, cs>>>(a, s);
     FCGNO_LAUNCHED();
     update_kernel<<<grid, kThreads, 0, cs>>>(a, s);
     FCGNO_LAUNCHED();
-    norm_kernel<<<ceil_div(a.B, 128), 128, 0, cs>>>(a, s);
+    norm_kernel<<<a.B, kThreads, 0, cs>>>(a, s);
     FCGNO_LAUNCHED();
   }
   return FCGNO_OK;
@@ -767,7 +805,7 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
   FCGNO_CUDA_TRY(cudaMemsetAsync(w.iter, 0, sizeof(int), cs));
   init_kernel<<<dim3(a.tiles, op->B), kThreads, 0, cs>>>(a, s);
   FCGNO_LAUNCHED();
-  init_finalize_kernel<<<ceil_div(op->B, 128), 128, 0, cs>>>(a, s);
+  init_finalize_kernel<<<op->B, kThreads, 0, cs>>>(a, s);
   FCGNO_LAUNCHED();
   if (jacobi > 0) {
     inv_diag_kernel<<<ceil_div(op->n * op->B, 256), 256, 0, cs>>>(op->n * op->B, op->diag, w.inv_diag);
@@ -1068,7 +1106,7 @@ extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, doubl
   FCGNO_CUDA_TRY(cudaMemsetAsync(s.iter, 0, sizeof(int), st));
   init_kernel<<<dim3(a.tiles, B), kThreads, 0, st>>>(a, s);
   FCGNO_LAUNCHED();
-  init_finalize_kernel<<<ceil_div(B, 128), 128, 0, st>>>(a, s);
+  init_finalize_kernel<<<B, kThreads, 0, st>>>(a, s);
   FCGNO_LAUNCHED();
   const int check_every = std::max(1, o.check_every);
   int h_ndone = 0;
@@ -1229,7 +1267,7 @@ extern "C" fcgno_status fcgno_bucket_admit(fcgno_bucket_t k, int slot, const dou
   s1.iters += slot;
   init_kernel<<<dim3(a1.tiles, 1), kThreads, 0, st>>>(a1, s1);
   FCGNO_LAUNCHED();
-  init_finalize_kernel<<<1, 128, 0, st>>>(a1, s1);
+  init_finalize_kernel<<<1, kThreads, 0, st>>>(a1, s1);
   FCGNO_LAUNCHED();
   return FCGNO_OK;
 }

@@ -257,6 +257,29 @@ __device__ __forceinline__ void block_sum(T (&v)[NV], T* scratch) {
   __syncthreads();
 }
 
+// Fixed-order block reduction of the first `count` (<= NV) values of every thread. Returns the
+// block total of value j in thread j (j < count) and 0 elsewhere; only those entries are
+// reduced, and one thread per entry adds up the warp partials. scratch must hold 32*NV
+// entries of T. Contains __syncthreads().
+template <typename T, int NV>
+__device__ __forceinline__ T block_sum_lane(T (&v)[NV], int count, T* scratch) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+#pragma unroll
+  for (int j = 0; j < NV; ++j)
+    if (j < count) v[j] = warp_sum(v[j]);
+  if (lane == 0) {
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      if (j < count) scratch[wid * NV + j] = v[j];
+  }
+  __syncthreads();
+  T s = 0;
+  if ((int)threadIdx.x < count)
+    for (int w = 0; w < nw; ++w) s += scratch[w * NV + threadIdx.x];
+  __syncthreads();
+  return s;
+}
+
 __device__ __forceinline__ double gelu_d(double x) { return 0.5 * x * (1.0 + erf(x * 0.70710678118654752440)); }
 __device__ __forceinline__ float gelu_f(float x) { return 0.5f * x * (1.0f + erff(x * 0.70710678118654752440f)); }
 // d/dx GELU(x) = Phi(x) + x phi(x)
