@@ -150,6 +150,49 @@ def roofline_synthesis(active_per_iter, N, C, M, layers):
     return float(sum(active_per_iter)) * per_inst, int(len(active_per_iter)) * layers
 
 
+def window_m(i, m_max):
+    """Truncation window m_i of Algorithm 1 at iteration i (0-based)."""
+    return min(i, max(1, i % (m_max + 1)))
+
+
+def fcg_step_fmas(iters_per_instance, n, m_max):
+    """Algorithmic FP64 multiply-adds of the fused FCG step over a solve: per active instance
+    and iteration i, n (10 + 2 m_i) -- m_i window dots and m_i direction updates, the 5-point
+    stencil (5), the dots (p, s) and (p, r), the updates of u and r and ||r||^2."""
+    return float(sum(n * (10 + 2 * window_m(i, m_max)) for it in iters_per_instance for i in range(it)))
+
+
+# GB300's nominal dense FP64 rate (TFLOP/s). The FMA-chain kernel below reaches about 84 % of
+# it (ncu: FP64 pipe active 84 % of cycles at 2.07 GHz), which is the measured roof.
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def measure_fp64_roof(dev, stream, repeats=5):
+    """FP64 multiply-add rate of this GPU, measured with the library's FMA-chain kernel on
+    every SM (8 CTAs of 256 threads per SM, 2048 steps of 8 chains per thread); CUDA events on
+    the launching stream, best and median of `repeats` launches after two warm-ups."""
+    import torch
+    from paper_2402_05598_gb300 import fcgno as F
+    blocks = torch.cuda.get_device_properties(dev).multi_processor_count * 8
+    out = torch.empty(blocks * 256, dtype=torch.float64, device=dev)
+    a, c = 1.0 - 2.0 ** -10, 2.0 ** -12
+    for _ in range(2):
+        F.fp64_fma_rate(blocks, 2048, a, c, out, stream)
+    ms = []
+    for _ in range(repeats):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fmas = F.fp64_fma_rate(blocks, 2048, a, c, out, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    best, med = min(ms), float(np.median(ms))
+    return {"tflops": 2.0 * fmas / (best / 1000.0) / 1e12, "tflops_median": 2.0 * fmas / (med / 1000.0) / 1e12,
+            "fmas_per_launch": fmas, "blocks": blocks,
+            "how": "fcgno_fp64_fma_rate: independent FP64 FMA chains on every SM; best of %d launches" % repeats}
+
+
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one tc_synthesis_kernel launch
 # per active instance, mean of the four layers of an iteration, measured by ncu on this
 # kernel at 64 x 64, 256 instances, width 32, 12 x 12 modes. Scaled by the active instances
@@ -417,14 +460,45 @@ def main():
     achieved = alg_bytes_one * args.steps / (syn_ms / 1000.0) / 1e9 if syn_ms > 0 else None
 
     # ---- kernel shares over one more (untimed) step per family
-    shares = {}
+    shares, raw = {}, {}
     for fam in ("tc_synthesis", "tc_analysis", "tc_mix", "tc_lift", "fcg_fused"):
         F.trace_set(fam)
         F.trace_collect()
         solve_once()
         ms, cnt = F.trace_collect()
         shares[fam] = {"ms": round(ms, 3), "launches": cnt}
+        raw[fam] = (ms, cnt)
     F.trace_set("")
+
+    # ---- the fused FCG step against the FP64 roof (measured here; no vendor figure exists).
+    # Step average: the traced step above, whose late launches hold few active instances.
+    # Full occupancy: a traced solve of 2 (m + 1) fixed iterations, every instance active.
+    fp64 = measure_fp64_roof(dev, stream)
+    n_pts = N_GRID * N_GRID
+    fused_ms, fused_cnt = raw["fcg_fused"]
+    step_flops = 2.0 * fcg_step_fmas(iters, n_pts, args.m)
+    k_full = 2 * (args.m + 1)
+    F.trace_set("fcg_fused")
+    F.trace_collect()
+    x.copy_(u0)
+    F.solve(op, model, f, x, tol=TOL, m_max=args.m, max_iter=k_full, prec=args.prec, fixed_iters=True,
+            check_every=8)
+    full_ms, full_cnt = F.trace_collect()
+    F.trace_set("")
+    full_flops = 2.0 * fcg_step_fmas([k_full] * EVAL_BATCH, n_pts, args.m)
+
+    def fp64_leg(flops, ms, cnt):
+        ach = flops / (ms / 1000.0) / 1e12 if ms > 0 else None
+        return {"achieved": ach, "frac": (ach / fp64["tflops"]) if ach else None,
+                "frac_of_nominal": (ach / FP64_NOMINAL_TFLOPS) if ach else None, "launches": cnt,
+                "avg_launch_ms": ms / max(cnt, 1), "flops_per_launch": flops / max(cnt, 1)}
+
+    fp64_roofline = {"kernel": "fused_step_kernel", "bound": "fp64", "unit": "TFLOP/s", "peak": fp64["tflops"],
+                     "peak_source": "measured here (" + fp64["how"] + ")", "peak_median": fp64["tflops_median"],
+                     "peak_nominal": FP64_NOMINAL_TFLOPS,
+                     "flops_per_unknown": "2 (10 + 2 m_i) per active instance and iteration",
+                     "step_average": fp64_leg(step_flops, fused_ms, fused_cnt),
+                     "full_occupancy": dict(fp64_leg(full_flops, full_ms, full_cnt), iterations=k_full)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -450,6 +524,7 @@ def main():
                          "avg_launch_ms": syn_avg_ms, "launches": syn_launches,
                          "note": trace_note or None},
             "kernel_ms_one_step": shares,
+            "fp64_roofline": fp64_roofline,
             "other_truncation": alt}
 
     # ---- comparison paths on the same instances (untimed here, reported for context)

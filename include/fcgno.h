@@ -231,6 +231,18 @@ const char* fcgno_last_error(void);
 /* Number of CUDA kernels this library has launched since load (all threads). */
 uint64_t fcgno_launch_count(void);
 
+/* FP64 multiply-add rate (a measurement aid, not part of the method: on GB300 the FP64 Krylov
+ * kernels of Algorithm 1 are bounded by the FP64 pipe, whose rate no vendor figure gives for
+ * this part). Launches `blocks` CTAs of 256 threads on `stream`; every thread runs 8
+ * independent chains x <- fma(x, a, c), started at x = 1 + j/16 (j = 0..7), for `steps` steps
+ * and writes the sum of the 8 final values to out[thread] (out: blocks * 256 doubles, device,
+ * caller-owned). *fmas (host) receives blocks * 256 * 8 * steps, the multiply-adds the launch
+ * performs. The caller times the launch with CUDA events on `stream`; asynchronous.
+ * FCGNO_EINVAL before any launch when blocks is outside 1..2^20, steps outside 1..2^24 or
+ * out/fmas is NULL. */
+fcgno_status fcgno_fp64_fma_rate(int blocks, int steps, double a, double c, double* out, uint64_t* fmas,
+                                 void* stream);
+
 /* Kernel tracing (not part of the method): select a kernel family by name ("tc_synthesis",
  * "tc_analysis", "tc_mix", "tc_lift", "fcg_fused", "fcg_tiled", "" = off). Every later launch
  * of that family is bracketed by two CUDA events recorded on its launch stream.

@@ -480,6 +480,27 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
   }
 }
 
+// FP64 multiply-add rate (a measurement aid, not a step of the method). Every thread runs
+// kRateChains independent chains x <- fma(x, a, c), started at x = 1 + j/16, for `steps`
+// steps, and writes the sum of its chains' final values. The chains keep enough independent
+// multiply-adds in flight to fill the FP64 pipe; nothing else is in the loop.
+constexpr int kRateChains = 8;
+constexpr int kRateThreads = 256;
+__global__ void __launch_bounds__(kRateThreads) fp64_fma_rate_kernel(int steps, double a, double c,
+                                                                    double* __restrict__ out) {
+  double x[kRateChains];
+#pragma unroll
+  for (int j = 0; j < kRateChains; ++j) x[j] = 1.0 + 0.0625 * j;
+  for (int t = 0; t < steps; ++t) {
+#pragma unroll
+    for (int j = 0; j < kRateChains; ++j) x[j] = fma(x[j], a, c);
+  }
+  double sum = 0.0;
+#pragma unroll
+  for (int j = 0; j < kRateChains; ++j) sum += x[j];
+  out[(size_t)blockIdx.x * kRateThreads + threadIdx.x] = sum;
+}
+
 // Jacobi(k) preconditioner, Eq. (15): x_0 = 0, x_{j+1} = x_j + D^-1 (r - A x_j); the first
 // sweep reduces to D^-1 r. x_in == nullptr marks the first sweep.
 __global__ void inv_diag_kernel(size_t total, const double* __restrict__ diag, double* __restrict__ inv) {
@@ -915,6 +936,18 @@ extern "C" fcgno_status fcgno_solve_jacobi(fcgno_op_t A, int steps, const double
   }
   FCGNO_TRY(check_opts(opts));
   return solve_impl(A, nullptr, b, x, *opts, FCGNO_FP64, info, (cudaStream_t)stream, nullptr, steps);
+}
+
+extern "C" fcgno_status fcgno_fp64_fma_rate(int blocks, int steps, double a, double c, double* out,
+                                            uint64_t* fmas, void* stream) {
+  if (blocks < 1 || blocks > (1 << 20) || steps < 1 || steps > (1 << 24) || !out || !fmas) {
+    set_last_error("fcgno_fp64_fma_rate: blocks outside 1..2^20, steps outside 1..2^24, or null out/fmas");
+    return FCGNO_EINVAL;
+  }
+  fp64_fma_rate_kernel<<<blocks, kRateThreads, 0, (cudaStream_t)stream>>>(steps, a, c, out);
+  FCGNO_LAUNCHED();
+  *fmas = (uint64_t)blocks * kRateThreads * kRateChains * (uint64_t)steps;
+  return FCGNO_OK;
 }
 
 extern "C" fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const double* b_host,

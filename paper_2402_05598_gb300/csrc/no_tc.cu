@@ -1299,7 +1299,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   // raise the dynamic shared-memory limit only when a larger plan appears (not a stream
   // operation; the first solve iteration runs eagerly, before any graph capture)
   // (the shared-memory carveout is pinned to its maximum so that two blocks of each kernel
-  // stay resident per SM; left to the driver it may size the carveout for one block)
+  // stay resident per SM; left to the CUDA driver it may size the carveout for one block)
   static size_t set_sa = 0, set_ss = 0, set_sm = 0;
   auto raise = [](const void* fn, size_t bytes, size_t& set) -> cudaError_t {
     if (bytes <= set) return cudaSuccess;

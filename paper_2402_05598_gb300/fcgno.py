@@ -67,6 +67,7 @@ def _load():
         "fcgno_status_str": (c_char_p, [c_int]),
         "fcgno_last_error": (c_char_p, []),
         "fcgno_launch_count": (c_uint64, []),
+        "fcgno_fp64_fma_rate": (c_int, [c_int, c_int, c_double, c_double, P, POINTER(c_uint64), P]),
         "fcgno_bucket_create": (c_int, [c_int, c_int, P, c_int, c_int, c_double, c_int, c_int, P, POINTER(P)]),
         "fcgno_bucket_admit": (c_int, [P, c_int, P, P, P, P]),
         "fcgno_bucket_step": (c_int, [P, P]),
@@ -91,7 +92,7 @@ EXPORTS = [
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
     "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
     "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_status_str",
-    "fcgno_last_error", "fcgno_launch_count", "fcgno_trace_set", "fcgno_trace_collect",
+    "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_trace_set", "fcgno_trace_collect",
     "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
     "fcgno_bucket_destroy",
 ]
@@ -107,6 +108,15 @@ def last_error() -> str:
 
 def launch_count() -> int:
     return int(lib.fcgno_launch_count())
+
+
+def fp64_fma_rate(blocks: int, steps: int, a: float, c: float, out, stream=None) -> int:
+    """Launch the FP64 multiply-add rate kernel (out: blocks * 256 float64 on the device);
+    returns the number of multiply-adds the launch performs. Time it with CUDA events."""
+    n = c_uint64()
+    _check(lib.fcgno_fp64_fma_rate(int(blocks), int(steps), float(a), float(c), _ptr(out), ctypes.byref(n),
+                                   _stream(stream)), "fcgno_fp64_fma_rate")
+    return int(n.value)
 
 
 def trace_set(family: str):
