@@ -135,6 +135,25 @@ def test_fcg_energy_error_monotone_and_window_orthogonality_with_neural_precondi
             assert abs(np.sum(ps[i] * ss[kk])) <= 1e-9 * math.sqrt(np.sum(ps[i] * A(ps[i])) * np.sum(ps[kk] * ss[kk]))
 
 
+def test_fcg_recursive_residual_is_the_true_residual():
+    """Algorithm 1 updates r by r - alpha A p instead of recomputing f - A u: in exact
+    arithmetic the two agree at every iteration, in FP64 they drift only by rounding. A sign
+    or index slip in either update makes them part at the first iteration."""
+    N = 16
+    desc = I.ModelDesc(width=8, layers=2, modes=4, proj_width=8)
+    P = O.unpack_weights(I.xavier_weights(desc, 4), desc)
+    k, f = I.make_problem(N, 6)
+    A = lambda u: O.apply_A(k, u)
+    u0 = np.random.default_rng(7).standard_normal((N, N))
+    for m_max in (1, 5):
+        out = O.fcg(A, lambda r: O.no_forward(P, desc, r, np.log(k)), f, u0, m_max, 30, record=True)
+        assert out["iterations"] == 30
+        for u, r in zip(out["us"], out["rs"]):
+            assert np.linalg.norm(r - (f - A(u))) <= 1e-11 * out["r0"]
+        # the untrained preconditioner barely lowers the residual, but the iterate moves
+        assert np.linalg.norm(out["u"] - u0) >= 0.1 * np.linalg.norm(u0)
+
+
 def test_table1_cg_iteration_counts_soft_pin():
     """Table 1: CG needs 74/130 iterations (Poisson) and 75/132 (Diffusion) at grid 32/64 to
     reach ||r_i||/||r_0|| <= 1e-6 from u_0 ~ N(0, 1). Soft pin (+-15%): the paper's grid
