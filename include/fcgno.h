@@ -20,6 +20,12 @@
  *  - No C++ exception crosses this boundary. Argument errors return FCGNO_EINVAL before
  *    any launch; CUDA failures return FCGNO_ECUDA (fcgno_last_error() gives the text).
  *  - Per-instance solve outcomes are reported in fcgno_solve_info[b].status.
+ *  - The tensor-core kernels bound every wait on an on-chip barrier (about 1 s); one that
+ *    gives up sets its operator's error flag and returns. fcgno_solve and fcgno_bucket_poll
+ *    read and clear that flag after their own synchronisation and then return FCGNO_ETIMEOUT
+ *    (the results of that call are invalid); a timeout inside the asynchronous
+ *    fcgno_precond_apply is reported by the next fcgno_solve or fcgno_bucket_poll on the
+ *    same operator.
  *  - Every computation runs in CUDA kernels of this library (sm_103a); there is no host
  *    fallback.
  *  - Concurrency: calls on different operators may run on different streams at the same

@@ -894,7 +894,7 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
   }
   FCGNO_CUDA_TRY(cudaEventRecord(w.ev_out, cs));
   FCGNO_CUDA_TRY(cudaStreamWaitEvent(st, w.ev_out, 0));
-  return FCGNO_OK;
+  return tc_take_timeout(op, cs);
 }
 
 static fcgno_status check_opts(const fcgno_solve_opts* o) {
@@ -1344,6 +1344,7 @@ extern "C" fcgno_status fcgno_bucket_poll(fcgno_bucket_t k, int32_t* status, int
   FCGNO_CUDA_TRY(cudaMemcpyAsync(k->h_rr, w.rr, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   FCGNO_CUDA_TRY(cudaMemcpyAsync(k->h_r0, w.r0, sizeof(double) * B, cudaMemcpyDeviceToHost, st));
   FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+  FCGNO_TRY(tc_take_timeout(k->op, st));
   for (int i = 0; i < B; ++i) {
     int stt = k->h_status[i];
     if (stt == kRunning && k->h_iters[i] >= k->max_iter) stt = FCGNO_ENOCONV;

@@ -210,6 +210,9 @@ fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, co
 fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t st);
 void tc_model_free(fcgno_model* m);
 void tc_acts_free(fcgno_op* op);
+// Reads and clears the operator's tensor-core timeout flag (synchronises `st`): FCGNO_ETIMEOUT
+// if a kernel of the 16-bit preconditioner gave up one of its bounded waits since the last call.
+fcgno_status tc_take_timeout(const fcgno_op* op, cudaStream_t st);
 void no_workspace_free(fcgno_model* m);
 
 // Per-instance rms of r: rms[b] = sqrt(mean(r_b^2)).

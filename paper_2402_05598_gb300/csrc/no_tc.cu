@@ -20,6 +20,7 @@
 // contiguous bulk copy in and one out.
 // Real and imaginary parts are interleaved along the contracted dimension, so every complex
 // product is a real GEMM.
+#include <mutex>
 #include "internal.cuh"
 #include "umma.cuh"
 
@@ -253,6 +254,7 @@ struct fcgno::TcActs {
   uint16_t* vb = nullptr;
   uint16_t* part = nullptr;  // partial-coefficient images [mode][chunk][block of 128][128 x 2C]
   uint16_t* chat = nullptr;  // mixed-coefficient images, one per instance
+  int* err = nullptr;        // set to 1 by a kernel whose bounded wait ran out (kept across regrowth)
 };
 
 namespace fcgno {
@@ -311,14 +313,29 @@ static void free_acts(TcActs& A) {
   uint16_t* f[] = {A.va, A.vb, A.part, A.chat};
   for (auto x : f)
     if (x) cudaFree(x);
+  int* err = A.err;
   A = TcActs{};
+  A.err = err;
 }
 
 void tc_acts_free(fcgno_op* op) {
   if (!op->tc_acts) return;
   free_acts(*op->tc_acts);
+  if (op->tc_acts->err) cudaFree(op->tc_acts->err);
   delete op->tc_acts;
   op->tc_acts = nullptr;
+}
+
+fcgno_status tc_take_timeout(const fcgno_op* op, cudaStream_t st) {
+  if (!op->tc_acts || !op->tc_acts->err) return FCGNO_OK;
+  int flag = 0;
+  FCGNO_CUDA_TRY(cudaMemcpyAsync(&flag, op->tc_acts->err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (flag == 0) return FCGNO_OK;
+  FCGNO_CUDA_TRY(cudaMemsetAsync(op->tc_acts->err, 0, sizeof(int), st));
+  set_last_error("a tensor-core preconditioner kernel gave up a bounded device wait (about 1 s): "
+                 "preconditioner outputs on this operator since the last check are invalid");
+  return FCGNO_ETIMEOUT;
 }
 
 fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t) {
@@ -1258,6 +1275,15 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   TcPrecision& P = m->tc->prec[fp16 ? 1 : 0];
   if (!op->tc_acts) op->tc_acts = new TcActs();
   TcActs& T = *op->tc_acts;
+  if (!T.err) {
+    if (cudaMalloc(&T.err, sizeof(int)) != cudaSuccess) {
+      cudaGetLastError();
+      T.err = nullptr;
+      set_last_error("tensor-core preconditioner error flag: out of device memory");
+      return FCGNO_ENOMEM;
+    }
+    FCGNO_CUDA_TRY(cudaMemsetAsync(T.err, 0, sizeof(int), st));
+  }
   const int B = op->B;
   const size_t n = op->n;
   const int nbt = ceil_div(B, 128);
@@ -1278,11 +1304,6 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     T.cap_chat = need_chat;
     m->gen++;
   }
-  static int* d_err = nullptr;
-  if (!d_err) {
-    FCGNO_CUDA_TRY(cudaMalloc(&d_err, sizeof(int)));
-    FCGNO_CUDA_TRY(cudaMemset(d_err, 0, sizeof(int)));
-  }
   BlobLayout BL = blob_layout(d);
   const bool bf16 = !fp16;
   {
@@ -1300,7 +1321,9 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   // operation; the first solve iteration runs eagerly, before any graph capture)
   // (the shared-memory carveout is pinned to its maximum so that two blocks of each kernel
   // stay resident per SM; left to the CUDA driver it may size the carveout for one block)
+  static std::mutex set_mu;  // concurrent callers on other threads share these limits
   static size_t set_sa = 0, set_ss = 0, set_sm = 0;
+  std::lock_guard<std::mutex> set_lk(set_mu);
   auto raise = [](const void* fn, size_t bytes, size_t& set) -> cudaError_t {
     if (bytes <= set) return cudaSuccess;
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
@@ -1319,14 +1342,14 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
       TraceScope ts("tc_analysis", st);
       FCGNO_CUDA_TRY(launch_chained(tc_analysis_kernel<C>, dim3(g.nchunks, B), dim3(kAnaThreads), sa, st, g, nbt,
                                     bf16, active, (const uint16_t*)cur, (const uint16_t*)tab->E2,
-                                    (const uint16_t*)tab->G, T.part, d_err));
+                                    (const uint16_t*)tab->G, T.part, T.err));
     }
     FCGNO_LAUNCHED();
     {
       TraceScope ts("tc_mix", st);
       FCGNO_CUDA_TRY(launch_chained(tc_mix_kernel<C>, dim3(g.nmodes, nbt), dim3(kTcThreads), sm, st, g, B, nbt,
                                     bf16, active, (const uint16_t*)T.part, (const uint16_t*)P.Rr[l], T.chat,
-                                    d_err));
+                                    T.err));
     }
     FCGNO_LAUNCHED();
     SynArgs s{};
@@ -1356,7 +1379,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     s.rms = rms;
     s.hh = 1.0 / ((double)(op->N + 1) * (op->N + 1));
     s.z = z;
-    s.err = d_err;
+    s.err = T.err;
     {
       TraceScope ts("tc_synthesis", st);
       FCGNO_CUDA_TRY(launch_chained(tc_synthesis_kernel<C>, dim3(g.snchunks, B), dim3(kSynThreads), ss, st, s));
