@@ -62,3 +62,60 @@ def test_oracle_and_library_do_not_import_each_other():
         assert not re.search(r"^\s*(from|import)\s+oracle", src, flags=re.M), f
     for f in (ROOT / "paper_2402_05598_gb300" / "csrc").glob("*"):
         assert "oracle" not in f.read_text().lower(), f
+
+
+def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
+    """Each C entry point checks its arguments before its first CUDA call: null handles and
+    buffers, out-of-range sizes and modes give FCGNO_EINVAL and a last-error text naming the
+    call, with no GPU present. Destroying a null handle is a no-op."""
+    import numpy as np
+    from paper_2402_05598_gb300 import fcgno as F
+    L, EINVAL = F.lib, F.FCGNO_EINVAL
+    h = ctypes.c_void_p()
+    host = np.zeros(16)
+    hp = host.ctypes.data
+    opts = F.fcgno_solve_opts(1e-6, 1, 10, 0, 1)
+    n = ctypes.c_uint64()
+    ms = ctypes.c_double()
+    w32 = np.zeros(8, dtype=np.float32)
+
+    def rejects(rc, name):
+        assert rc == EINVAL, (name, rc)
+        assert name in F.last_error(), (name, F.last_error())
+
+    for N, B, k, out in ((1, 1, hp, h), (4, 0, hp, h), (4, 1, None, h), (4, 1, hp, None)):
+        rejects(L.fcgno_assemble(N, B, k, None, ctypes.byref(out) if out is not None else None), "fcgno_assemble")
+    rejects(L.fcgno_apply_A(None, hp, hp, None), "fcgno_apply_A")
+    rejects(L.fcgno_model_create(ctypes.byref(F.make_desc(width=0)), w32.ctypes.data, None, ctypes.byref(h)),
+            "fcgno_model_create")
+    rejects(L.fcgno_model_create(ctypes.byref(F.make_desc()), None, None, ctypes.byref(h)), "fcgno_model_create")
+    rejects(L.fcgno_model_sync(None, None), "fcgno_model_sync")
+    for mode in (0, 3, -1):
+        rejects(L.fcgno_model_set_train_recompute(None, mode), "fcgno_model_set_train_recompute")
+    rejects(L.fcgno_precond_apply(None, None, hp, hp, F.PREC["bf16"], None), "fcgno_precond_apply")
+    rejects(L.fcgno_solve(None, None, hp, hp, ctypes.byref(opts), F.PREC["fp64"], None, None), "fcgno_solve")
+    for steps in (0, 65):
+        rejects(L.fcgno_solve_jacobi(None, steps, hp, hp, ctypes.byref(opts), None, None), "fcgno_solve_jacobi")
+    rejects(L.fcgno_solve_host(1, 1, hp, hp, hp, None, ctypes.byref(opts), F.PREC["fp64"], None, None),
+            "fcgno_solve_host")
+    rejects(L.fcgno_solve_host(4, 0, hp, hp, hp, None, ctypes.byref(opts), F.PREC["fp64"], None, None),
+            "fcgno_solve_host")
+    rejects(L.fcgno_krylov_harvest(None, hp, hp, hp, 0, hp, hp, None, None), "fcgno_krylov_harvest")
+    rejects(L.fcgno_train_step_loss(None, None, hp, hp, 1, F.PREC["fp64"], 0, hp, hp, None), "fcgno_train_step")
+    for blocks, steps in ((0, 1), (1, 0), ((1 << 20) + 1, 1), (1, (1 << 24) + 1)):
+        rejects(L.fcgno_fp64_fma_rate(blocks, steps, 1.0, 0.0, hp, ctypes.byref(n), None), "fcgno_fp64_fma_rate")
+    rejects(L.fcgno_fp64_fma_rate(1, 1, 1.0, 0.0, hp, None, None), "fcgno_fp64_fma_rate")
+    bucket_bad = [(1, 4, 1, 1e-6, 10, 8), (64, 0, 1, 1e-6, 10, 8), (64, 4, 0, 1e-6, 10, 8), (64, 4, 9, 1e-6, 10, 8),
+                  (64, 4, 1, -1.0, 10, 8), (64, 4, 1, float("nan"), 10, 8), (64, 4, 1, 1e-6, 0, 8),
+                  (64, 4, 1, 1e-6, 10, 0)]
+    for N, cap, m, tol, mi, g in bucket_bad:
+        rejects(L.fcgno_bucket_create(N, cap, None, F.PREC["fp64"], m, tol, mi, g, None, ctypes.byref(h)),
+                "fcgno_bucket_create")
+    rejects(L.fcgno_bucket_admit(None, 0, hp, hp, hp, None), "fcgno_bucket_admit")
+    rejects(L.fcgno_bucket_step(None, None), "fcgno_bucket_step")
+    rejects(L.fcgno_bucket_poll(None, hp, hp, hp, None), "fcgno_bucket_poll")
+    rejects(L.fcgno_bucket_take(None, 0, None, None), "fcgno_bucket_take")
+    rejects(L.fcgno_trace_collect(None, ctypes.byref(n)), "fcgno_trace_collect")
+    rejects(L.fcgno_trace_collect(ctypes.byref(ms), None), "fcgno_trace_collect")
+    for destroy in (L.fcgno_op_destroy, L.fcgno_model_destroy, L.fcgno_bucket_destroy):
+        assert destroy(None) == F.FCGNO_OK
