@@ -95,8 +95,12 @@ typedef struct {
  * coefficients and log k on the device and returns a handle that owns them.
  * Errors: EINVAL if N < 2, batch < 1, k or out NULL; ENOMEM; ECUDA. */
 fcgno_status fcgno_assemble(int N, int batch, const double* k, void* stream, fcgno_op_t* out);
+/* Releases the handle and everything it owns (solver workspace, graphs, the 16-bit
+ * preconditioner's activations) with cudaFree, which waits for work in flight on the
+ * device. NULL is a no-op. */
 fcgno_status fcgno_op_destroy(fcgno_op_t op);
-/* y = A x for every instance (x, y: [batch][N][N], may not alias). */
+/* y = A x for every instance (x, y: [batch][N][N], may not alias).
+ * Errors: EINVAL for a NULL op, x or y, or x == y. */
 fcgno_status fcgno_apply_A(fcgno_op_t op, const double* x, double* y, void* stream);
 
 /* Neural operator handle. `weights` is a DEVICE float32 blob of fcgno_weight_count(desc)
@@ -104,7 +108,14 @@ fcgno_status fcgno_apply_A(fcgno_op_t op, const double* x, double* y, void* stre
  * (out, in), b_l [C], r_l [2M][M][C][C][2] (x1-mode slot j -> frequency j or j-2M, x2-mode,
  * in, out, re/im); proj1_w [Cp][C], proj1_b [Cp], proj2_w [Cp], proj2_b [1].
  * The handle keeps the pointer (caller keeps the blob alive) and derives reduced-precision
- * copies from it; call fcgno_model_sync after the blob changes. */
+ * copies from it; call fcgno_model_sync after the blob changes.
+ * fcgno_weight_count returns 0 for an invalid desc. create: EINVAL for a NULL desc, weights
+ * or out, width or proj_width outside 1..64, layers outside 1..16, modes outside 1..16, or
+ * in_channels != 2; ENOMEM. Shapes the 16-bit path does not support (it needs width 16 or
+ * 32, proj_width = width, N = 32, 64 or a multiple of 128) make fcgno_precond_apply,
+ * fcgno_solve, fcgno_solve_host and fcgno_bucket_create return EINVAL for FCGNO_BF16 /
+ * FCGNO_FP16, before any launch.
+ * sync: EINVAL for a NULL model. destroy: NULL is a no-op. */
 size_t fcgno_weight_count(const fcgno_model_desc* desc);
 fcgno_status fcgno_model_create(const fcgno_model_desc* desc, const float* weights, void* stream,
                                 fcgno_model_t* out);
@@ -115,7 +126,8 @@ fcgno_status fcgno_model_destroy(fcgno_model_t model);
  * z = h^2 rms(r) * decoder(Fourier layers(encoder(r / rms(r), log k))), z = 0 where r = 0
  * (h = 1/(N+1); the h^2 factor gives the output the units of A^-1).
  * r, z: [batch][N][N]. prec selects the arithmetic (FP64, FP32, BF16, FP16).
- * Errors: EINVAL if N < 2*modes or the precision is unsupported. */
+ * Errors: EINVAL for a NULL argument, N < 2*modes, an unknown precision or a shape the
+ * 16-bit path does not support (all before any launch); ENOMEM; ECUDA. */
 fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, const double* r, double* z,
                                  fcgno_prec prec, void* stream);
 
@@ -123,7 +135,10 @@ fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, const doubl
  * b is [batch][N][N]; Bpc NULL runs the identity preconditioner (plain CG for m_max = 1).
  * info is a HOST array of batch entries. Synchronises on `stream` every check_every
  * iterations and at exit (the call returns when every instance has stopped).
- * Errors: EINVAL for bad opts (tol < 0, m_max outside 1..8, max_iter < 0). */
+ * Errors: EINVAL for a NULL A, b or x, bad opts (tol < 0, m_max outside 1..8,
+ * max_iter < 0), N < 2*modes, an unknown precision or a shape the 16-bit path does not
+ * support; ENOMEM; ECUDA; ETIMEOUT (see the
+ * conventions). Per-instance outcomes (converged, not converged, breakdown) are in info. */
 fcgno_status fcgno_solve(fcgno_op_t A, fcgno_model_t Bpc, const double* b, double* x,
                          const fcgno_solve_opts* opts, fcgno_prec prec, fcgno_solve_info* info,
                          void* stream);
@@ -137,7 +152,8 @@ fcgno_status fcgno_solve_jacobi(fcgno_op_t A, int steps, const double* b, double
 
 /* End-to-end variant of fcgno_solve on HOST buffers: k_host, b_host, x_host are
  * [batch][N][N] host arrays (pinned memory gives the fastest copies). Copies k, b, x in,
- * assembles, solves, copies x out; info is a host array. Synchronous. */
+ * assembles, solves, copies x out; info is a host array. Synchronous.
+ * Errors: EINVAL for N < 2, batch < 1 or a NULL host buffer, then those of fcgno_solve. */
 fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const double* b_host,
                               double* x_host, fcgno_model_t Bpc, const fcgno_solve_opts* opts,
                               fcgno_prec prec, fcgno_solve_info* info, void* stream);
@@ -163,7 +179,8 @@ fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, double* x, const
  * with B = I, m_max = 1) from x0 on every instance and stores, for i = 1..K, the
  * residual r_i and the error e_i = u_star - u_i:
  * r_out, e_out are [K][batch][N][N]; u_star is [batch][N][N] (the converged solution).
- * Rows after an instance has converged repeat its last iterate. info: host array. */
+ * Rows after an instance has converged repeat its last iterate. info: host array.
+ * Errors: EINVAL for a NULL pointer or K < 1; ENOMEM; ECUDA. */
 fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x0,
                                   const double* u_star, int K, double* r_out, double* e_out,
                                   fcgno_solve_info* info, void* stream);
@@ -173,7 +190,9 @@ fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x
  * with respect to every weight of the blob. r, e: [batch][N][N] (batch = op's batch).
  * loss: device float scalar; grad: device float blob (same layout as the weights), both
  * overwritten. prec: FCGNO_FP32 (forward/backward on CUDA cores, FP32) or FCGNO_FP64.
- * Uses the FP32 master blob given to fcgno_model_create. */
+ * Uses the FP32 master blob given to fcgno_model_create.
+ * Errors: EINVAL for a NULL pointer, batch != op's batch, another precision or
+ * N < 2*modes; ENOMEM; ECUDA. */
 fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
                               int batch, fcgno_prec prec, float* loss, float* grad, void* stream);
 
@@ -217,7 +236,11 @@ fcgno_status fcgno_train_step_loss(fcgno_model_t model, fcgno_op_t op, const dou
  *    FCGNO_OK converged, FCGNO_EBREAKDOWN, FCGNO_ENOCONV once iters >= max_iter), iterations,
  *    relative residual.
  *  - take: copy the slot's iterate to x_out (DEVICE [N][N], may be NULL) and stop the slot,
- *    freeing it for the next admit. */
+ *    freeing it for the next admit.
+ *  - Errors: EINVAL for a NULL bucket or pointer, a slot outside 0..capacity-1, and at
+ *    create N < 2 (or < 2*modes), capacity < 1, m_max outside 1..8, tol < 0 or NaN,
+ *    max_iter < 1 or iters_per_step < 1; poll also ETIMEOUT (see the conventions).
+ *    destroy: NULL is a no-op. */
 typedef struct fcgno_bucket* fcgno_bucket_t;
 fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t Bpc, fcgno_prec prec, int m_max, double tol,
                                  int max_iter, int iters_per_step, void* stream, fcgno_bucket_t* out);
@@ -229,10 +252,14 @@ fcgno_status fcgno_bucket_take(fcgno_bucket_t bucket, int slot, double* x_out, v
 fcgno_status fcgno_bucket_destroy(fcgno_bucket_t bucket);
 
 /* Device bytes fcgno_solve needs for one op of this shape (operator, Krylov state and the
- * preconditioner's activations), for admission against an HBM budget. */
+ * preconditioner's activations), for admission against an HBM budget. Host-only; 0 for
+ * N < 2, batch < 1 or m_max < 1; an invalid desc counts no preconditioner. */
 size_t fcgno_workspace_bytes(int N, int batch, int m_max, const fcgno_model_desc* desc, fcgno_prec prec);
 
+/* Static text for a status. */
 const char* fcgno_status_str(fcgno_status s);
+/* Text of the last error set on the calling thread (thread-local; valid until that
+ * thread's next failing call). */
 const char* fcgno_last_error(void);
 /* Number of CUDA kernels this library has launched since load (all threads). */
 uint64_t fcgno_launch_count(void);
@@ -253,7 +280,8 @@ fcgno_status fcgno_fp64_fma_rate(int blocks, int steps, double a, double c, doub
  * "tc_analysis", "tc_mix", "tc_lift", "fcg_fused", "fcg_tiled", "" = off). Every later launch
  * of that family is bracketed by two CUDA events recorded on its launch stream.
  * fcgno_trace_collect waits for the recorded events and returns the summed device time
- * (ms) and the number of traced launches since the previous collect. */
+ * (ms) and the number of traced launches since the previous collect (EINVAL for a NULL
+ * output). An unknown family name traces nothing. */
 fcgno_status fcgno_trace_set(const char* family);
 fcgno_status fcgno_trace_collect(double* total_ms, uint64_t* launches);
 

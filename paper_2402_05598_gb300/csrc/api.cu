@@ -230,6 +230,14 @@ extern "C" fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, 
     set_last_error("fcgno_precond_apply: grid smaller than 2*modes");
     return FCGNO_EINVAL;
   }
+  if (prec < FCGNO_FP64 || prec > FCGNO_FP32) {
+    set_last_error("fcgno_precond_apply: unknown precision");
+    return FCGNO_EINVAL;
+  }
+  if ((prec == FCGNO_BF16 || prec == FCGNO_FP16) && !tc_shape_supported(op->N, model->desc)) {
+    set_last_error(std::string("fcgno_precond_apply: ") + tc_shape_rule());
+    return FCGNO_EINVAL;
+  }
   cudaStream_t st = (cudaStream_t)stream;
   // per-instance rms lives in a small scratch owned by the op's solver workspace
   double* rms = nullptr;

@@ -909,6 +909,26 @@ static fcgno_status check_opts(const fcgno_solve_opts* o) {
 
 using namespace fcgno;
 
+// Checks shared by the solve entry points, made before any allocation or launch: the
+// options, the precision, and the preconditioner's shape on an N x N grid.
+static fcgno_status check_solve_args(const char* who, int N, const fcgno_model* Bpc, const fcgno_solve_opts* opts,
+                                     fcgno_prec prec) {
+  FCGNO_TRY(check_opts(opts));
+  if (prec < FCGNO_FP64 || prec > FCGNO_FP32) {
+    set_last_error(std::string(who) + ": unknown precision");
+    return FCGNO_EINVAL;
+  }
+  if (Bpc && N < 2 * Bpc->desc.modes) {
+    set_last_error(std::string(who) + ": grid smaller than 2*modes");
+    return FCGNO_EINVAL;
+  }
+  if (Bpc && (prec == FCGNO_BF16 || prec == FCGNO_FP16) && !tc_shape_supported(N, Bpc->desc)) {
+    set_last_error(std::string(who) + ": " + tc_shape_rule());
+    return FCGNO_EINVAL;
+  }
+  return FCGNO_OK;
+}
+
 extern "C" fcgno_status fcgno_solve(fcgno_op_t A, fcgno_model_t Bpc, const double* b, double* x,
                                     const fcgno_solve_opts* opts, fcgno_prec prec, fcgno_solve_info* info,
                                     void* stream) {
@@ -916,15 +936,7 @@ extern "C" fcgno_status fcgno_solve(fcgno_op_t A, fcgno_model_t Bpc, const doubl
     set_last_error("fcgno_solve: null operator, b or x");
     return FCGNO_EINVAL;
   }
-  FCGNO_TRY(check_opts(opts));
-  if (Bpc && A->N < 2 * Bpc->desc.modes) {
-    set_last_error("fcgno_solve: grid smaller than 2*modes");
-    return FCGNO_EINVAL;
-  }
-  if (prec < FCGNO_FP64 || prec > FCGNO_FP32) {
-    set_last_error("fcgno_solve: unknown precision");
-    return FCGNO_EINVAL;
-  }
+  FCGNO_TRY(check_solve_args("fcgno_solve", A->N, Bpc, opts, prec));
   return solve_impl(A, Bpc, b, x, *opts, prec, info, (cudaStream_t)stream, nullptr);
 }
 
@@ -957,6 +969,7 @@ extern "C" fcgno_status fcgno_solve_host(int N, int batch, const double* k_host,
     set_last_error("fcgno_solve_host: bad arguments");
     return FCGNO_EINVAL;
   }
+  FCGNO_TRY(check_solve_args("fcgno_solve_host", N, Bpc, opts, prec));
   FCGNO_TRY(check_opts(opts));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)N * N * batch * sizeof(double);
@@ -1205,8 +1218,13 @@ extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t m
                                             fcgno_bucket_t* out) {
   using namespace fcgno;
   if (N < 2 || capacity < 1 || m_max < 1 || m_max > kMaxWindow || !(tol >= 0.0) || max_iter < 1 ||
-      iters_per_step < 1 || !out || (model && N < 2 * model->desc.modes)) {
+      iters_per_step < 1 || !out || (model && N < 2 * model->desc.modes) || prec < FCGNO_FP64 ||
+      prec > FCGNO_FP32) {
     set_last_error("fcgno_bucket_create: bad arguments");
+    return FCGNO_EINVAL;
+  }
+  if (model && (prec == FCGNO_BF16 || prec == FCGNO_FP16) && !tc_shape_supported(N, model->desc)) {
+    set_last_error(std::string("fcgno_bucket_create: ") + tc_shape_rule());
     return FCGNO_EINVAL;
   }
   *out = nullptr;

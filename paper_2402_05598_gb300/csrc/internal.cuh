@@ -207,6 +207,10 @@ fcgno_status no_apply_simt(fcgno_model* m, const fcgno_op* op, const double* r, 
                            const int* active, double* z, bool fp64, cudaStream_t st);
 fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms,
                          const int* active, double* z, bool fp16, cudaStream_t st);
+// Whether the 16-bit (tensor-core) preconditioner supports model shape d on an N x N grid,
+// and the rule in words (for error messages). Host-only.
+bool tc_shape_supported(int N, const fcgno_model_desc& d);
+const char* tc_shape_rule();
 fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t st);
 void tc_model_free(fcgno_model* m);
 void tc_acts_free(fcgno_op* op);

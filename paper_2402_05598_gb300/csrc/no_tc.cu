@@ -1390,12 +1390,20 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   return FCGNO_OK;
 }
 
+bool tc_shape_supported(int N, const fcgno_model_desc& d) {
+  return geom_supported(N, d.width, d.modes, d.proj_width);
+}
+
+const char* tc_shape_rule() {
+  return "the 16-bit preconditioner supports width 16 or 32 (proj_width = width), modes <= 16 and "
+         "N in {32, 64} or a multiple of 128";
+}
+
 fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms, const int* active,
                          double* z, bool fp16, cudaStream_t st) {
   const fcgno_model_desc& d = m->desc;
-  if (!geom_supported(op->N, d.width, d.modes, d.proj_width)) {
-    set_last_error("tensor-core preconditioner supports width 16 or 32 (proj_width = width), modes <= 16 and "
-                   "N in {32, 64} or a multiple of 128");
+  if (!tc_shape_supported(op->N, d)) {
+    set_last_error(tc_shape_rule());
     return FCGNO_EINVAL;
   }
   if (d.width == 16) return run_tc<16>(m, op, r, rms, active, z, fp16, st);

@@ -100,6 +100,13 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
             "fcgno_solve_host")
     rejects(L.fcgno_solve_host(4, 0, hp, hp, hp, None, ctypes.byref(opts), F.PREC["fp64"], None, None),
             "fcgno_solve_host")
+    # options and precision are checked before the host buffers are copied anywhere
+    bad_opts = [F.fcgno_solve_opts(-1.0, 1, 10, 0, 1), F.fcgno_solve_opts(1e-6, 0, 10, 0, 1),
+                F.fcgno_solve_opts(1e-6, 9, 10, 0, 1), F.fcgno_solve_opts(1e-6, 1, -1, 0, 1)]
+    for o in bad_opts:
+        rejects(L.fcgno_solve_host(4, 1, hp, hp, hp, None, ctypes.byref(o), F.PREC["fp64"], None, None), "fcgno_solve")
+    rejects(L.fcgno_solve_host(4, 1, hp, hp, hp, None, None, F.PREC["fp64"], None, None), "fcgno_solve")
+    rejects(L.fcgno_solve_host(4, 1, hp, hp, hp, None, ctypes.byref(opts), 7, None, None), "fcgno_solve_host")
     rejects(L.fcgno_krylov_harvest(None, hp, hp, hp, 0, hp, hp, None, None), "fcgno_krylov_harvest")
     rejects(L.fcgno_train_step_loss(None, None, hp, hp, 1, F.PREC["fp64"], 0, hp, hp, None), "fcgno_train_step")
     for blocks, steps in ((0, 1), (1, 0), ((1 << 20) + 1, 1), (1, (1 << 24) + 1)):
@@ -111,6 +118,8 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
     for N, cap, m, tol, mi, g in bucket_bad:
         rejects(L.fcgno_bucket_create(N, cap, None, F.PREC["fp64"], m, tol, mi, g, None, ctypes.byref(h)),
                 "fcgno_bucket_create")
+    for prec in (-1, 4):
+        rejects(L.fcgno_bucket_create(64, 4, None, prec, 1, 1e-6, 10, 8, None, ctypes.byref(h)), "fcgno_bucket_create")
     rejects(L.fcgno_bucket_admit(None, 0, hp, hp, hp, None), "fcgno_bucket_admit")
     rejects(L.fcgno_bucket_step(None, None), "fcgno_bucket_step")
     rejects(L.fcgno_bucket_poll(None, hp, hp, hp, None), "fcgno_bucket_poll")
