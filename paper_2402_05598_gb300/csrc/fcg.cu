@@ -970,7 +970,6 @@ extern "C" fcgno_status fcgno_solve_host(int N, int batch, const double* k_host,
     return FCGNO_EINVAL;
   }
   FCGNO_TRY(check_solve_args("fcgno_solve_host", N, Bpc, opts, prec));
-  FCGNO_TRY(check_opts(opts));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)N * N * batch * sizeof(double);
   double *dk = nullptr, *db = nullptr, *dx = nullptr;
