@@ -308,6 +308,25 @@ def test_notay_loss_exact_inverse_is_zero_and_zero_output_is_one():
     assert abs(O.l2_loss([np.zeros_like(e)], [e]) - 1.0) < 1e-15
 
 
+def test_losses_are_batch_means_of_norm_ratios():
+    """Eq. (11) as read: the batch mean of ||z - e||_A / ||e||_A, a ratio of norms and not of
+    squared norms (z = e/2 gives 1/2, not 1/4), averaged and not summed (an exact and a zero
+    output give 1/2, not 1); the L2 ablation loss the same with the Euclidean norm. Both are
+    invariant to a common scale of z and e."""
+    N = 6
+    k1, r1 = I.make_problem(N, 8)
+    k2, r2 = I.make_problem(N, 9)
+    e1 = np.linalg.solve(O.dense_A(k1), r1.ravel()).reshape(N, N)
+    e2 = np.linalg.solve(O.dense_A(k2), r2.ravel()).reshape(N, N)
+    assert abs(O.notay_loss([k1], [0.5 * e1], [e1]) - 0.5) < 1e-14
+    assert abs(O.l2_loss([0.5 * e1], [e1]) - 0.5) < 1e-14
+    assert abs(O.notay_loss([k1, k2], [e1.copy(), np.zeros_like(e2)], [e1, e2]) - 0.5) < 1e-12
+    assert abs(O.l2_loss([e1.copy(), np.zeros_like(e2)], [e1, e2]) - 0.5) < 1e-12
+    z1 = e1 + 0.1 * np.random.default_rng(1).standard_normal(e1.shape)
+    assert abs(O.notay_loss([k1], [3.0 * z1], [3.0 * e1]) - O.notay_loss([k1], [z1], [e1])) < 1e-13
+    assert abs(O.l2_loss([3.0 * z1], [3.0 * e1]) - O.l2_loss([z1], [e1])) < 1e-13
+
+
 # --------------------------------------------------------------------------- inputs
 def test_grf_sample_covariance():
     """Statistical check of the GRF generator: empirical covariance of g = log k between
