@@ -33,10 +33,12 @@ Readings of points the paper leaves open (the same readings the library implemen
 Pins (tests/test_oracle_pins.py) fix every component against closed forms, textbook
 algorithms, numpy FFTs and the paper's Table 1. The composed neural-operator forward
 (no_forward with random weights) has no closed form: its analysis, mixing, synthesis,
-pointwise, GELU and encoder/decoder steps are each pinned, and the whole map is checked for
-shift equivariance and positive homogeneity, but the composition itself is parity unpinned
-(the CUDA path is compared with this oracle only). The same holds for FCG-NO iterates with
-that preconditioner.
+pointwise, GELU and encoder/decoder steps are each pinned, the whole map is checked for
+shift equivariance and positive homogeneity, and with zero spectral blocks and identity W it
+is checked node by node against a scalar closed form (encoder channel order, activations,
+biases, decoder, the h^2 rms(r) scale); with nonzero spectral blocks the composition itself
+is parity unpinned (the CUDA path is compared with this oracle only). The same holds for
+FCG-NO iterates with that preconditioner.
 """
 from __future__ import annotations
 

@@ -299,6 +299,68 @@ def test_weight_blob_layout_and_xavier_bounds():
 
 
 # --------------------------------------------------------------------------- losses (Eq. 11-12)
+def test_pointwise_no_reduces_to_a_scalar_closed_form():
+    """With every spectral block R_l = 0 and W_l = I the Fourier layers act node by node, so
+    the whole preconditioner of Appendix A reduces to a scalar function of (r/rms, log k) at
+    each node: encoder a r^ + b log k + c, GELU(u + b_l) on layers 1-3, u + b_4 on the last,
+    decoder s . GELU(P u + q) + t, times h^2 rms(r). Computed here node by node with
+    math.erf, it pins the encoder's channel order, which layers apply GELU, the biases, the
+    decoder and the output scale h^2 rms(r) with h = 1/(N+1)."""
+    N, C, Cp, L, M = 8, 4, 3, 4, 2
+    desc = I.ModelDesc(width=C, layers=L, modes=M, proj_width=Cp)
+    off = I.weight_offsets(desc)
+    blob = np.zeros(I.weight_count(desc), dtype=np.float32)
+    rng = np.random.default_rng(11)
+
+    def put(name, values):
+        o, size = off[name]
+        values = np.asarray(values, dtype=np.float32).ravel()
+        assert values.size == size
+        blob[o:o + size] = values
+
+    lift_w = rng.uniform(-1, 1, (C, 2))
+    lift_b = rng.uniform(-0.5, 0.5, C)
+    put("lift_w", lift_w)
+    put("lift_b", lift_b)
+    biases = [rng.uniform(-0.5, 0.5, C) for _ in range(L)]
+    for l in range(L):
+        put(f"w{l}", np.eye(C))
+        put(f"b{l}", biases[l])
+    P1 = rng.uniform(-1, 1, (Cp, C))
+    q = rng.uniform(-0.5, 0.5, Cp)
+    s2 = rng.uniform(-1, 1, Cp)
+    t = 0.3
+    put("proj1_w", P1)
+    put("proj1_b", q)
+    put("proj2_w", s2)
+    put("proj2_b", [t])
+    # read the parameters back as the stored float32 values
+    lift_w, lift_b = blob[off["lift_w"][0]:][:C * 2].reshape(C, 2).astype(float), blob[off["lift_b"][0]:][:C]
+    biases = [blob[off[f"b{l}"][0]:][:C].astype(float) for l in range(L)]
+    P1 = blob[off["proj1_w"][0]:][:Cp * C].reshape(Cp, C).astype(float)
+    q, s2 = blob[off["proj1_b"][0]:][:Cp].astype(float), blob[off["proj2_w"][0]:][:Cp].astype(float)
+    t = float(blob[off["proj2_b"][0]])
+
+    def g(x):
+        return 0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0)))
+
+    r = rng.standard_normal((N, N))
+    logk = rng.uniform(-1, 1, (N, N))
+    z = O.no_forward(O.unpack_weights(blob, desc), desc, r, logk)
+    rms = math.sqrt(sum(v * v for v in r.ravel()) / (N * N))
+    h = 1.0 / (N + 1)
+    for qq in range(N):
+        for pp in range(N):
+            u = [lift_w[c][0] * r[qq, pp] / rms + lift_w[c][1] * logk[qq, pp] + float(lift_b[c]) for c in range(C)]
+            for l in range(L):
+                u = [u[c] + biases[l][c] for c in range(C)]
+                if l < L - 1:
+                    u = [g(x) for x in u]
+            hid = [g(sum(P1[j][c] * u[c] for c in range(C)) + q[j]) for j in range(Cp)]
+            want = h * h * rms * (sum(s2[j] * hid[j] for j in range(Cp)) + t)
+            assert abs(z[qq, pp] - want) <= 1e-12 * max(1.0, abs(want)) * h * h, (qq, pp, z[qq, pp], want)
+
+
 def test_notay_loss_exact_inverse_is_zero_and_zero_output_is_one():
     N = 6
     k, r = I.make_problem(N, 8)
