@@ -34,6 +34,11 @@
  *    fcgno_train_step keep their activations in the model: calls using them on one model
  *    must not overlap. Calls on one operator must not overlap either. Changing a model's
  *    weights (fcgno_model_sync) while a solve or bucket uses it is not supported.
+ *    Host threads: the library's global state (last error, launch counter, tracing) is
+ *    thread-safe, but a model builds its 16-bit weight images and transform tables on its
+ *    first use for each precision and grid size; that first use must not run concurrently
+ *    with another host thread's call on the same model (issue it once, or serialise the
+ *    calls, before sharing the model across threads).
  */
 #ifndef FCGNO_H
 #define FCGNO_H
