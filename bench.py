@@ -162,6 +162,33 @@ def fcg_step_fmas(iters_per_instance, n, m_max):
     return float(sum(n * (10 + 2 * window_m(i, m_max)) for it in iters_per_instance for i in range(it)))
 
 
+def fcg_step_bytes(iters_per_instance, n, m_max):
+    """Algorithmic HBM bytes of the fused FCG step over a solve: per active instance and
+    iteration i, n (72 + 16 m_i) -- read w and the m_i vectors s_k and p_k, write p and s, read
+    the two face-coefficient arrays, read and write u and r (the stored diagonal, a
+    convenience of this implementation, is not counted)."""
+    return float(sum(n * (72 + 16 * window_m(i, m_max)) for it in iters_per_instance for i in range(it)))
+
+
+def synthesis_flops(active_per_iter, N, C, M, layers, Cp):
+    """Algorithmic FLOPs of all synthesis launches: per active instance and layer, stage 1
+    (16 M^2 C N: the inverse transform over x1 of the 2M x M x C complex coefficients for every
+    column), stage 2 (4 M C N^2: the inverse transform over x2, real part) and the pointwise
+    path W v (2 C^2 N^2); the last layer adds the decoder (2 C Cp + 2 Cp per point)."""
+    n = N * N
+    layer = 16 * M * M * C * N + 4 * M * C * n + 2 * C * C * n
+    last = layer + (2 * C * Cp + 2 * Cp) * n
+    return float(sum(active_per_iter)) * ((layers - 1) * layer + last)
+
+
+def rate_and_frac(amount, ms, scale, peak):
+    """(amount per second / scale, that over peak); (None, None) without a positive time."""
+    if not ms or ms <= 0:
+        return None, None
+    rate = amount / (ms / 1000.0) / scale
+    return rate, (rate / peak if peak else None)
+
+
 # GB300's nominal dense FP64 rate (TFLOP/s). The FMA-chain kernel below reaches about 84 % of
 # it (ncu: FP64 pipe active 84 % of cycles at 2.07 GHz), which is the measured roof.
 FP64_NOMINAL_TFLOPS = 1.25
@@ -451,13 +478,29 @@ def main():
     alg_bytes_one, syn_per_step = roofline_synthesis(active, N_GRID, WIDTH, MODES, LAYERS)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6800.0, "fallback"
+    bf16_peak, bf16_src = 1700.0, "fallback (sustained)"
     if os.path.exists(peaks_path):
         with open(peaks_path) as fh:
-            peak, peak_src = float(json.load(fh)["hbm_gbs"]), "measured"
+            peaks = json.load(fh)
+        peak, peak_src = float(peaks["hbm_gbs"]), "measured"
+        if "bf16_tflops_sustained" in peaks:
+            bf16_peak, bf16_src = float(peaks["bf16_tflops_sustained"]), "measured (sustained)"
     syn_avg_ms = syn_ms / max(syn_launches, 1)
     active_per_launch = float(sum(active)) * LAYERS * args.steps / max(syn_launches, 1)
     traffic = SYN_TRAFFIC_PER_INSTANCE * active_per_launch if SYN_TRAFFIC_PER_INSTANCE else None
     achieved = alg_bytes_one * args.steps / (syn_ms / 1000.0) / 1e9 if syn_ms > 0 else None
+    # the same launches against the tensor pipe (the NO's work is dense contractions)
+    syn_flops_one = synthesis_flops(active, N_GRID, WIDTH, MODES, LAYERS, WIDTH)
+    t_ach, t_frac = rate_and_frac(syn_flops_one * args.steps, syn_ms, 1e12, bf16_peak)
+    intensity = syn_flops_one / alg_bytes_one if alg_bytes_one else None
+    ceiling = intensity * peak / 1e3 if intensity else None  # TFLOP/s at the measured copy peak
+    tensor_roofline = {"kernel": "tc_synthesis_kernel", "bound": "tensor", "unit": "TFLOP/s", "achieved": t_ach,
+                       "peak": bf16_peak, "peak_source": bf16_src, "frac": t_frac,
+                       "flops_per_launch": syn_flops_one * args.steps / max(syn_launches, 1),
+                       "intensity_flop_per_byte": intensity, "ceiling_at_hbm_peak": ceiling,
+                       "frac_of_ceiling": (t_ach / ceiling) if (t_ach and ceiling) else None,
+                       "note": "the activations pass through HBM, so the HBM roof caps the tensor pipe at "
+                               "ceiling_at_hbm_peak"}
 
     # ---- kernel shares over one more (untimed) step per family
     shares, raw = {}, {}
@@ -486,19 +529,25 @@ def main():
     full_ms, full_cnt = F.trace_collect()
     F.trace_set("")
     full_flops = 2.0 * fcg_step_fmas([k_full] * EVAL_BATCH, n_pts, args.m)
+    step_bytes = fcg_step_bytes(iters, n_pts, args.m)
+    full_bytes = fcg_step_bytes([k_full] * EVAL_BATCH, n_pts, args.m)
 
-    def fp64_leg(flops, ms, cnt):
+    def fp64_leg(flops, nbytes, ms, cnt):
         ach = flops / (ms / 1000.0) / 1e12 if ms > 0 else None
+        gbs, gfrac = rate_and_frac(nbytes, ms, 1e9, peak)
         return {"achieved": ach, "frac": (ach / fp64["tflops"]) if ach else None,
                 "frac_of_nominal": (ach / FP64_NOMINAL_TFLOPS) if ach else None, "launches": cnt,
-                "avg_launch_ms": ms / max(cnt, 1), "flops_per_launch": flops / max(cnt, 1)}
+                "avg_launch_ms": ms / max(cnt, 1), "flops_per_launch": flops / max(cnt, 1),
+                "hbm_gbs": gbs, "hbm_frac": gfrac, "bytes_per_launch": nbytes / max(cnt, 1)}
 
     fp64_roofline = {"kernel": "fused_step_kernel", "bound": "fp64", "unit": "TFLOP/s", "peak": fp64["tflops"],
                      "peak_source": "measured here (" + fp64["how"] + ")", "peak_median": fp64["tflops_median"],
                      "peak_nominal": FP64_NOMINAL_TFLOPS,
                      "flops_per_unknown": "2 (10 + 2 m_i) per active instance and iteration",
-                     "step_average": fp64_leg(step_flops, fused_ms, fused_cnt),
-                     "full_occupancy": dict(fp64_leg(full_flops, full_ms, full_cnt), iterations=k_full)}
+                     "bytes_per_unknown": "72 + 16 m_i per active instance and iteration (hbm_frac: of the "
+                                          "measured copy peak)",
+                     "step_average": fp64_leg(step_flops, step_bytes, fused_ms, fused_cnt),
+                     "full_occupancy": dict(fp64_leg(full_flops, full_bytes, full_ms, full_cnt), iterations=k_full)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -525,6 +574,7 @@ def main():
                          "note": trace_note or None},
             "kernel_ms_one_step": shares,
             "fp64_roofline": fp64_roofline,
+            "tensor_roofline": tensor_roofline,
             "other_truncation": alt}
 
     # ---- comparison paths on the same instances (untimed here, reported for context)

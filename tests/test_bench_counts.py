@@ -45,3 +45,26 @@ def test_synthesis_bytes(bench):
     total, launches = bench.roofline_synthesis([256, 200, 3], N, C, M, L)
     assert launches == 3 * L
     assert total == (256 + 200 + 3) * ((L - 1) * hidden + last)
+
+
+def test_fcg_step_bytes(bench):
+    # per active unknown and iteration: 72 + 16 m_i bytes; m = 5 windows 0, 1, 2 for i = 0, 1, 2
+    n = 5
+    assert bench.fcg_step_bytes([3], n, 5) == n * (72 * 3 + 16 * (0 + 1 + 2))
+    assert bench.fcg_step_bytes([0, 1], n, 1) == n * 72
+    assert bench.fcg_step_bytes([], n, 5) == 0
+
+
+def test_synthesis_flops(bench):
+    N, C, M, L, Cp = 64, 32, 12, 4, 32
+    n = N * N
+    per_unknown = 16 * M * M * C / N + 4 * M * C + 2 * C * C
+    assert per_unknown == 4736
+    total = bench.synthesis_flops([256, 7], N, C, M, L, Cp)
+    assert total == (256 + 7) * n * (L * per_unknown + 2 * C * Cp + 2 * Cp)
+
+
+def test_rate_and_frac(bench):
+    assert bench.rate_and_frac(2e12, 1000.0, 1e12, 4.0) == (2.0, 0.5)
+    assert bench.rate_and_frac(1.0, 0.0, 1.0, 1.0) == (None, None)
+    assert bench.rate_and_frac(5e9, 1.0, 1e9, None) == (5000.0, None)
