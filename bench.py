@@ -181,6 +181,26 @@ def synthesis_flops(active_per_iter, N, C, M, layers, Cp):
     return float(sum(active_per_iter)) * ((layers - 1) * layer + last)
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.lower().startswith("model name"):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine() or "unknown"
+
+
 def rate_and_frac(amount, ms, scale, peak):
     """(amount per second / scale, that over peak); (None, None) without a positive time."""
     if not ms or ms <= 0:
@@ -314,6 +334,7 @@ def run_reference(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name(args.m), "grid": N_GRID, "instances_per_gpu": EVAL_BATCH},
             "cpu_baseline": {"kind": "oracle", "value": value, "unit": UNIT, "cores": cores,
+                             "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                              "sample": f"{cores} instances per step, {iters} FCG-NO iterations each (the GPU arm's "
                                        f"iterations per solve), one single-threaded process per core"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -643,6 +664,7 @@ def main():
         # initial weights (no value produced by the CUDA path enters the oracle)
         wall, tot_it = oracle_sample(I.xavier_weights(desc_np, 0), cores, it_solve, cores, args.m)
         line["cpu_baseline"] = {"kind": "oracle", "value": cores / wall, "unit": UNIT, "cores": cores,
+                                "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                                 "sample": f"{cores} instances, {it_solve} FCG-NO iterations each (the GPU solve's "
                                           f"mean iterations per solve), FP64 numpy oracle, one single-threaded "
                                           f"process per core"}
