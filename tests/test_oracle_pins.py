@@ -361,6 +361,51 @@ def test_pointwise_no_reduces_to_a_scalar_closed_form():
             assert abs(z[qq, pp] - want) <= 1e-12 * max(1.0, abs(want)) * h * h, (qq, pp, z[qq, pp], want)
 
 
+def test_spectral_weight_layout_single_mode_closed_form():
+    """The documented layout of the spectral weights r_l [2M][M][C][C][2] (x1 slot j holds
+    frequency j or j - 2M, then the x2 frequency, input channel, output channel, re/im) and the
+    transform conventions, end to end through a one-layer NO. Input r = cos(theta) with
+    theta = 2 pi (k1 p + k2 q) / N, k1 = -2 (slot 2M - 2), k2 = 1; the encoder copies r/rms
+    into channel 0; the only nonzero spectral weight is R[slot, k2, in 0, out 1] = alpha +
+    i beta; the decoder reads channel 1 through one GELU. The kept coefficient of
+    r/rms = sqrt(2) cos(theta) is sqrt(2)/2 at (k1, k2) (its mirror has x2-frequency -1, which
+    is not kept) and synthesis doubles k2 > 0 terms, so
+    z = h^2 rms(r) GELU(sqrt(2) (alpha cos(theta) - beta sin(theta))). The same weight placed
+    at (in 1, out 0) reads the empty channel and gives z = 0."""
+    N, C, Cp, L, M = 8, 2, 2, 1, 3
+    k1, k2 = -2, 1
+    slot = k1 + 2 * M
+    assert O.kx_frequencies(M)[slot] == k1
+    alpha, beta = 0.7, -0.4
+    desc = I.ModelDesc(width=C, layers=L, modes=M, proj_width=Cp)
+    off = I.weight_offsets(desc)
+
+    def blob_with(cin, cout):
+        blob = np.zeros(I.weight_count(desc), dtype=np.float64)
+        blob[off["lift_w"][0] + 0] = 1.0               # lift_w[0][0]: r/rms -> channel 0
+        base = off["r0"][0] + ((((slot * M + k2) * C + cin) * C + cout) * 2)
+        blob[base], blob[base + 1] = alpha, beta
+        blob[off["proj1_w"][0] + 0 * C + 1] = 1.0      # proj1_w[0][1]: channel 1 -> hidden 0
+        blob[off["proj2_w"][0] + 0] = 1.0              # proj2_w[0]
+        return blob
+
+    rng = np.random.default_rng(5)
+    pp, qq = np.meshgrid(np.arange(N), np.arange(N))   # arrays indexed [q][p]
+    theta = 2 * np.pi * (k1 * pp + k2 * qq) / N
+    r = np.cos(theta)
+    logk = rng.uniform(-1, 1, (N, N))
+    h = 1.0 / (N + 1)
+    rms = math.sqrt(0.5)
+    z = O.no_forward(O.unpack_weights(blob_with(0, 1), desc), desc, r, logk)
+    for q_ in range(N):
+        for p_ in range(N):
+            x = math.sqrt(2.0) * (alpha * math.cos(theta[q_, p_]) - beta * math.sin(theta[q_, p_]))
+            want = h * h * rms * 0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0)))
+            assert abs(z[q_, p_] - want) <= 1e-13 * h * h, (q_, p_, z[q_, p_], want)
+    z0 = O.no_forward(O.unpack_weights(blob_with(1, 0), desc), desc, r, logk)
+    assert np.max(np.abs(z0)) <= 1e-15
+
+
 def test_notay_loss_exact_inverse_is_zero_and_zero_output_is_one():
     N = 6
     k, r = I.make_problem(N, 8)
