@@ -36,8 +36,10 @@ algorithms, numpy FFTs and the paper's Table 1. The composed neural-operator for
 pointwise, GELU and encoder/decoder steps are each pinned, the whole map is checked for
 shift equivariance and positive homogeneity, and with zero spectral blocks and identity W it
 is checked node by node against a scalar closed form (encoder channel order, activations,
-biases, decoder, the h^2 rms(r) scale); with nonzero spectral blocks the composition itself
-is parity unpinned (the CUDA path is compared with this oracle only). The same holds for
+biases, decoder, the h^2 rms(r) scale); a one-layer NO with a single nonzero spectral weight
+and a single-mode input is checked against its closed form (the weight layout and transform
+conventions); with general spectral blocks and several layers the composition itself is
+parity unpinned (the CUDA path is compared with this oracle only). The same holds for
 FCG-NO iterates with that preconditioner.
 """
 from __future__ import annotations
