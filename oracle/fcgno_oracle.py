@@ -38,8 +38,10 @@ shift equivariance and positive homogeneity, and with zero spectral blocks and i
 is checked node by node against a scalar closed form (encoder channel order, activations,
 biases, decoder, the h^2 rms(r) scale); a one-layer NO with a single nonzero spectral weight
 and a single-mode input is checked against its closed form (the weight layout and transform
-conventions); with general spectral blocks and several layers the composition itself is
-parity unpinned (the CUDA path is compared with this oracle only). The same holds for
+conventions); constant inputs reduce the four-layer NO with random weights to its mean mode,
+checked against scalar loops; with general spectral blocks, non-constant inputs and several
+layers the composition itself is parity unpinned (the CUDA path is compared with this oracle
+only). The same holds for
 FCG-NO iterates with that preconditioner.
 """
 from __future__ import annotations

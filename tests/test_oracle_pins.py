@@ -406,6 +406,43 @@ def test_spectral_weight_layout_single_mode_closed_form():
     assert np.max(np.abs(z0)) <= 1e-15
 
 
+def test_constant_fields_follow_the_mean_mode_through_every_layer():
+    """For constant r and log k every channel stays constant through the whole NO, so only
+    the mean mode (k1, k2) = (0, 0) is nonzero: each Fourier layer maps the channel vector u
+    to act(W u + b + Re(R_00)^T u) (the mode's synthesis weight is 1 and only the real part
+    of its complex weight acts), with all other weights random and irrelevant. Computed here
+    by scalar loops through all four layers, GELU on the first three, and the decoder."""
+    N, C, Cp, L, M = 8, 3, 2, 4, 3
+    desc = I.ModelDesc(width=C, layers=L, modes=M, proj_width=Cp)
+    blob = I.xavier_weights(desc, 21).astype(np.float64)
+    rng = np.random.default_rng(2)
+    off = I.weight_offsets(desc)
+    for l in range(L):  # nonzero biases so that they are exercised too
+        o, size = off[f"b{l}"]
+        blob[o:o + size] = rng.uniform(-0.3, 0.3, size)
+    P = O.unpack_weights(blob, desc)
+    cr, lk = -0.8, 0.35
+    r = np.full((N, N), cr)
+    logk = np.full((N, N), lk)
+    z = O.no_forward(P, desc, r, logk)
+
+    def g(x):
+        return 0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0)))
+
+    lw, lb = P["lift_w"], P["lift_b"]
+    u = [lw[c][0] * (cr / abs(cr)) + lw[c][1] * lk + lb[c] for c in range(C)]
+    for l, lay in enumerate(P["layers"]):
+        W, b, R00 = lay["w"], lay["b"], lay["r"][0, 0]
+        u = [sum(W[o][i] * u[i] for i in range(C)) + b[o] + sum(R00[i][o].real * u[i] for i in range(C))
+             for o in range(C)]
+        if l < L - 1:
+            u = [g(x) for x in u]
+    hid = [g(sum(P["proj1_w"][j][c] * u[c] for c in range(C)) + P["proj1_b"][j]) for j in range(Cp)]
+    h = 1.0 / (N + 1)
+    want = h * h * abs(cr) * (sum(P["proj2_w"][j] * hid[j] for j in range(Cp)) + P["proj2_b"][0])
+    assert np.max(np.abs(z - want)) <= 1e-12 * h * h * max(1.0, abs(want) / (h * h))
+
+
 def test_notay_loss_exact_inverse_is_zero_and_zero_output_is_one():
     N = 6
     k, r = I.make_problem(N, 8)
