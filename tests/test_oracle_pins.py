@@ -154,6 +154,28 @@ def test_fcg_recursive_residual_is_the_true_residual():
         assert np.linalg.norm(out["u"] - u0) >= 0.1 * np.linalg.norm(u0)
 
 
+def test_fcg_step_is_an_exact_line_search():
+    """alpha = (p_i, r_i) / (p_i, A p_i) minimises the energy error along p_i, so the new
+    residual is orthogonal to the search direction: (p_i, r_{i+1}) = 0 at every iteration,
+    also with a nonlinear preconditioner and a truncated window; and p_i is A-orthogonal to
+    the window it was orthogonalised against."""
+    N = 12
+    desc = I.ModelDesc(width=8, layers=2, modes=3, proj_width=8)
+    P = O.unpack_weights(I.xavier_weights(desc, 9), desc)
+    k, f = I.make_problem(N, 13)
+    A = lambda u: O.apply_A(k, u)
+    for m_max in (1, 3, 5):
+        out = O.fcg(A, lambda r: O.no_forward(P, desc, r, np.log(k)), f, np.zeros_like(f), m_max, 25,
+                    record=True)
+        ps, rs = out["ps"], out["rs"]
+        for i, p in enumerate(ps):
+            rn = rs[i + 1]
+            assert abs(np.sum(p * rn)) <= 1e-10 * np.linalg.norm(p) * np.linalg.norm(rs[i])
+            for kk in range(i - O.truncation_window(i, m_max), i):
+                Ap = A(ps[kk])
+                assert abs(np.sum(p * Ap)) <= 1e-9 * math.sqrt(np.sum(p * A(p)) * np.sum(ps[kk] * Ap))
+
+
 def test_table1_cg_iteration_counts_soft_pin():
     """Table 1: CG needs 74/130 iterations (Poisson) and 75/132 (Diffusion) at grid 32/64 to
     reach ||r_i||/||r_0|| <= 1e-6 from u_0 ~ N(0, 1). Soft pin (+-15%): the paper's grid
