@@ -1,0 +1,62 @@
+"""Degenerate cases of the solve. Shapes the 16-bit (tensor-core) preconditioner does not
+support are argument errors: the solve and the preconditioner application return
+FCGNO_EINVAL before any launch and leave their outputs untouched; the CUDA-core
+preconditioners take the same shape. A preconditioner that returns zero makes
+(p_0, A p_0) = 0: every instance stops at iteration 0 with FCGNO_EBREAKDOWN (Algorithm 1
+cannot take a step), as the oracle does, and x is left as it was."""
+import numpy as np
+import pytest
+
+from paper_2402_05598_gb300 import inputs as I
+
+
+@pytest.mark.gpu
+def test_unsupported_16bit_shape_is_rejected_before_any_launch(lib, dev):
+    import torch
+    N, B, C, M = 48, 2, 32, 12  # N is neither 32, 64 nor a multiple of 128
+    k, f = I.make_batch(N, [3, 4])
+    desc = I.ModelDesc(width=C, layers=4, modes=M, proj_width=C)
+    w = torch.from_numpy(I.xavier_weights(desc, 0)).to(dev)
+    model = lib.Model(lib.make_desc(C, 4, M, C), w)
+    op = lib.Operator(torch.from_numpy(k).to(dev))
+    fb = torch.from_numpy(f).to(dev)
+    x = torch.full((B, N, N), 0.5, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    for prec in ("bf16", "fp16"):
+        n0 = lib.launch_count()
+        with pytest.raises(lib.FcgnoError) as ei:
+            lib.solve(op, model, fb, x, tol=1e-6, m_max=1, max_iter=10, prec=prec)
+        assert ei.value.code == lib.FCGNO_EINVAL and "16-bit" in str(ei.value)
+        with pytest.raises(lib.FcgnoError) as ei:
+            lib.precond_apply(model, op, fb, x, prec=prec)
+        assert ei.value.code == lib.FCGNO_EINVAL and "16-bit" in str(ei.value)
+        assert lib.launch_count() == n0
+    torch.cuda.synchronize()
+    assert bool(torch.all(x == 0.5))
+    x.zero_()
+    info = lib.solve(op, model, fb, x, tol=1e-6, m_max=1, max_iter=3, prec="fp64", fixed_iters=True)
+    assert all(i["iters"] == 3 for i in info)
+    assert np.isfinite(x.cpu().numpy()).all()
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("N,prec", [(32, "fp64"), (32, "bf16"), (128, "bf16")])
+def test_zero_preconditioner_breaks_down_at_the_first_step(lib, dev, N, prec):
+    import torch
+    from oracle import fcgno_oracle as O
+    B, C, M = 2, 32, 12
+    k, f = I.make_batch(N, [7, 8])
+    desc = I.ModelDesc(width=C, layers=4, modes=M, proj_width=C)
+    w = torch.zeros(I.weight_count(desc), dtype=torch.float32, device=dev)
+    model = lib.Model(lib.make_desc(C, 4, M, C), w)
+    op = lib.Operator(torch.from_numpy(k).to(dev))
+    x0 = np.random.default_rng(3).standard_normal((B, N, N))
+    x = torch.from_numpy(x0).to(dev)
+    info = lib.solve(op, model, torch.from_numpy(f).to(dev), x, tol=1e-6, m_max=5, max_iter=50, prec=prec)
+    P = O.unpack_weights(np.zeros(I.weight_count(desc)), desc)
+    for b in range(B):
+        ref = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: O.no_forward(P, desc, r, np.log(k[b])), f[b], x0[b],
+                    5, 50, tol=1e-6)
+        assert ref["status"] == O.STATUS_BREAKDOWN and ref["iterations"] == 0
+        assert info[b]["status"] == lib.FCGNO_EBREAKDOWN and info[b]["iters"] == 0, info[b]
+    assert np.array_equal(x.cpu().numpy(), x0)
