@@ -12,7 +12,11 @@ the GPU and a small solve does not wait behind a large one. The loop repeatedly
   3. for every bucket whose step has finished (an event query, no waiting), reads the slot
      states and retires finished slots (converged, breakdown, or capped), recording each
      request's completion time.
-Latency = completion time - arrival time (queueing included).
+Latency = completion time - arrival time (queueing included). A request the library rejects
+at admission (FcgnoError: bad input, no memory) completes at once with that status and its
+slot stays free; when a bucket's poll reports FCGNO_ETIMEOUT (a bounded device wait gave up
+during its step) every solve running in that bucket completes with that status and the
+bucket goes on serving. Other library errors stop the loop.
 """
 from __future__ import annotations
 
@@ -47,10 +51,11 @@ class ServeStats:
     wall_s: float = 0.0
     offered_rate: float = 0.0
     bucket_bytes: int = 0
+    failed: int = 0
 
     def summary(self) -> dict:
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
-        return {"requests": self.completed, "converged": self.converged,
+        return {"requests": self.completed, "converged": self.converged, "failed": self.failed,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                 "mean_ms": float(lat.mean()), "solves_per_s": self.completed / max(self.wall_s, 1e-9),
                 "offered_per_s": self.offered_rate, "wall_s": self.wall_s, "bucket_bytes": self.bucket_bytes}
@@ -96,6 +101,13 @@ class Server:
         self.queues = {N: deque() for N in capacities}
         self.inflight = {N: None for N in capacities}  # event recorded after the bucket's last step
 
+    @staticmethod
+    def _complete(r, status, iters, relres, tnow, stats):
+        r.done, r.iters, r.status, r.relres = tnow, int(iters), int(status), float(relres)
+        stats.latencies_ms.append(1000.0 * (r.done - r.arrival))
+        stats.completed += 1
+        stats.converged += int(r.status == F.FCGNO_OK)
+
     def run(self, requests: list, stats: ServeStats) -> ServeStats:
         """Serves the requests (sorted by arrival) and returns latency statistics."""
         cuda = self.cuda
@@ -119,7 +131,14 @@ class Server:
                         break
                     if slots[i] is None:
                         r = q.popleft()
-                        self.buckets[N].admit(i, r.k, r.f, r.x0, stream=self.streams[N])
+                        try:
+                            self.buckets[N].admit(i, r.k, r.f, r.x0, stream=self.streams[N])
+                        except F.FcgnoError as e:
+                            # rejected by the library: completes now, the slot stays free
+                            self._complete(r, e.code, 0, 0.0, time.perf_counter() - t0, stats)
+                            stats.failed += 1
+                            outstanding -= 1
+                            continue
                         slots[i] = r
             # start a step of every bucket with running slots and no step in flight
             busy = [N for N, slots in self.slots.items() if any(s is not None for s in slots)]
@@ -136,15 +155,26 @@ class Server:
                     continue
                 self.inflight[N] = None
                 progressed = True
-                st, it, rr = self.buckets[N].poll(stream=self.streams[N])
+                try:
+                    st, it, rr = self.buckets[N].poll(stream=self.streams[N])
+                except F.FcgnoError as e:
+                    if e.code != F.FCGNO_ETIMEOUT:
+                        raise
+                    # this bucket's step is invalid: its running solves complete with the status
+                    tnow = time.perf_counter() - t0
+                    for i, r in enumerate(self.slots[N]):
+                        if r is not None:
+                            self.buckets[N].take(i, stream=self.streams[N])
+                            self._complete(r, e.code, 0, 0.0, tnow, stats)
+                            stats.failed += 1
+                            self.slots[N][i] = None
+                            outstanding -= 1
+                    continue
                 tnow = time.perf_counter() - t0
                 for i, r in enumerate(self.slots[N]):
                     if r is not None and st[i] != -1:
                         self.buckets[N].take(i, stream=self.streams[N])
-                        r.done, r.iters, r.status, r.relres = tnow, int(it[i]), int(st[i]), float(rr[i])
-                        stats.latencies_ms.append(1000.0 * (r.done - r.arrival))
-                        stats.completed += 1
-                        stats.converged += int(r.status == F.FCGNO_OK)
+                        self._complete(r, st[i], it[i], rr[i], tnow, stats)
                         self.slots[N][i] = None
                         outstanding -= 1
             if not progressed:

@@ -117,3 +117,65 @@ def test_capacity_plan_respects_the_budget_and_the_offered_mix(S):
         assert cap * S.slot_bytes(N, 1, desc, "bf16") <= share < (cap + 1) * S.slot_bytes(N, 1, desc, "bf16")
     capped = S.plan_capacities(mix, budget, 1, desc, "bf16", max_slots=16)
     assert max(capped.values()) <= 16
+
+
+class FaultyBucket(FakeBucket):
+    """FakeBucket with host-injected faults: admitting request 13 fails with FCGNO_ENOMEM, and
+    the third poll of the 128 x 128 bucket reports FCGNO_ETIMEOUT (its running solves are
+    recorded in `timed_out`)."""
+    polls = {}
+    timed_out = set()
+
+    def __init__(self, *a, **kw):
+        super().__init__(*a, **kw)
+        self.rid = [None] * self.cap
+
+    def admit(self, slot, k, f, x0, stream=None):
+        from paper_2402_05598_gb300 import fcgno as F
+        if int(f) == 13:
+            raise F.FcgnoError(F.FCGNO_ENOMEM, "fcgno_bucket_admit")
+        super().admit(slot, k, f, x0, stream)
+        self.rid[slot] = int(f)
+
+    def poll(self, stream=None):
+        from paper_2402_05598_gb300 import fcgno as F
+        n = FaultyBucket.polls.get(self.N, 0) + 1
+        FaultyBucket.polls[self.N] = n
+        if self.N == 128 and n == 3:
+            FaultyBucket.timed_out |= {self.rid[s] for s in range(self.cap) if self.state[s] != "free"}
+            raise F.FcgnoError(F.FCGNO_ETIMEOUT, "fcgno_bucket_poll")
+        return super().poll(stream)
+
+    def take(self, slot, x_out=None, stream=None):
+        self.state[slot] = "free"
+        self.rid[slot] = None
+
+
+def test_serve_loop_survives_host_injected_faults(S):
+    """A rejected admission completes that request with its status and leaves the slot free; a
+    timed-out step completes the bucket's running solves with FCGNO_ETIMEOUT; every other
+    request is served as usual and each completes exactly once."""
+    from paper_2402_05598_gb300 import fcgno as F
+    rng = np.random.default_rng(1)
+    FakeBucket.log = []
+    FaultyBucket.polls, FaultyBucket.timed_out = {}, set()
+    reqs = [S.Request(i, 0.0002 * i, int(rng.choice((64, 128))), int(rng.integers(1, 30)), i, None)
+            for i in range(50)]
+    srv = S.Server(None, {64: 3, 128: 2}, prec="bf16", max_iter=200, iters_per_step=8,
+                   bucket_factory=FaultyBucket, cuda=FakeCuda)
+    stats = srv.run(reqs, S.ServeStats())
+    assert stats.completed == len(reqs) and len(stats.latencies_ms) == len(reqs)
+    timed_out = FaultyBucket.timed_out
+    assert timed_out and 13 not in timed_out
+    assert reqs[13].status == F.FCGNO_ENOMEM and reqs[13].iters == 0
+    for r in reqs:
+        if r.rid in timed_out:
+            assert r.status == F.FCGNO_ETIMEOUT and r.N == 128
+        elif r.rid != 13:
+            assert r.status == 0 and r.iters == r.k
+    assert stats.failed == 1 + len(timed_out)
+    assert stats.converged == len(reqs) - stats.failed
+    # the 128 x 128 bucket went on serving after its timed-out step
+    late = [r for r in reqs if r.N == 128 and r.rid not in timed_out and r.done > min(
+        reqs[i].done for i in timed_out)]
+    assert late and all(r.status == 0 for r in late)
