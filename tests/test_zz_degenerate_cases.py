@@ -60,3 +60,35 @@ def test_zero_preconditioner_breaks_down_at_the_first_step(lib, dev, N, prec):
         assert ref["status"] == O.STATUS_BREAKDOWN and ref["iterations"] == 0
         assert info[b]["status"] == lib.FCGNO_EBREAKDOWN and info[b]["iters"] == 0, info[b]
     assert np.array_equal(x.cpu().numpy(), x0)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["bf16", "fp64"])
+def test_a_nan_input_fails_only_its_own_instance(lib, dev, prec):
+    """A NaN in one instance's right-hand side makes its (p_0, A p_0) non-finite: that
+    instance stops at iteration 0 with FCGNO_EBREAKDOWN and x unchanged, and the other
+    instances give bit for bit the results they give when that right-hand side is clean (no
+    kernel mixes instances: the mode-mixing GEMM's rows are independent and every reduction
+    is per instance in a fixed order; the instances keep their positions in the batch)."""
+    import torch
+    N, C, M = 64, 32, 12
+    k, f = I.make_batch(N, [21, 22, 23])
+    f_bad = f.copy()
+    f_bad[1, 5, 7] = np.nan
+    desc = I.ModelDesc(width=C, layers=4, modes=M, proj_width=C)
+    w = torch.from_numpy(I.xavier_weights(desc, 1)).to(dev)
+    model = lib.Model(lib.make_desc(C, 4, M, C), w)
+    x0 = np.random.default_rng(4).standard_normal((3, N, N))
+    op3 = lib.Operator(torch.from_numpy(k).to(dev))
+    x3 = torch.from_numpy(x0).to(dev)
+    info3 = lib.solve(op3, model, torch.from_numpy(f_bad).to(dev), x3, tol=1e-6, m_max=5, max_iter=24, prec=prec)
+    x_clean = torch.from_numpy(x0).to(dev)
+    info_clean = lib.solve(op3, model, torch.from_numpy(f).to(dev), x_clean, tol=1e-6, m_max=5, max_iter=24,
+                           prec=prec)
+    assert info3[1]["status"] == lib.FCGNO_EBREAKDOWN and info3[1]["iters"] == 0
+    assert info_clean[1]["status"] != lib.FCGNO_EBREAKDOWN and info_clean[1]["iters"] > 0
+    xs3, xs_clean = x3.cpu().numpy(), x_clean.cpu().numpy()
+    assert np.array_equal(xs3[1], x0[1])
+    for b in (0, 2):
+        assert info3[b]["iters"] == info_clean[b]["iters"] and info3[b]["status"] == info_clean[b]["status"]
+        assert np.array_equal(xs3[b], xs_clean[b])
