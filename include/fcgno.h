@@ -261,6 +261,12 @@ fcgno_status fcgno_bucket_destroy(fcgno_bucket_t bucket);
  * N < 2, batch < 1 or m_max < 1; an invalid desc counts no preconditioner. */
 size_t fcgno_workspace_bytes(int N, int batch, int m_max, const fcgno_model_desc* desc, fcgno_prec prec);
 
+/* 1 if the preconditioner in precision `prec` supports model shape `desc` on an N x N grid
+ * (the calls taking it would not return FCGNO_EINVAL for the shape), else 0. Host-only.
+ * FCGNO_FP64 / FCGNO_FP32 take any valid desc with N >= 2*modes; FCGNO_BF16 / FCGNO_FP16 also
+ * need width 16 or 32, proj_width = width and N = 32, 64 or a multiple of 128. */
+int fcgno_precision_supported(int N, const fcgno_model_desc* desc, fcgno_prec prec);
+
 /* Static text for a status. */
 const char* fcgno_status_str(fcgno_status s);
 /* Text of the last error set on the calling thread (thread-local; valid until that

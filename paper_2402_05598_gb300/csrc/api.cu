@@ -310,6 +310,19 @@ extern "C" size_t fcgno_workspace_bytes(int N, int batch, int m_max, const fcgno
   return bytes;
 }
 
+extern "C" int fcgno_precision_supported(int N, const fcgno_model_desc* desc, fcgno_prec prec) {
+  if (N < 2 || !desc_ok(desc) || N < 2 * desc->modes) return 0;
+  switch (prec) {
+    case FCGNO_FP64:
+    case FCGNO_FP32:
+      return 1;
+    case FCGNO_BF16:
+    case FCGNO_FP16:
+      return tc_shape_supported(N, *desc) ? 1 : 0;
+  }
+  return 0;
+}
+
 extern "C" const char* fcgno_status_str(fcgno_status s) {
   switch (s) {
     case FCGNO_OK: return "ok";

@@ -64,6 +64,7 @@ def _load():
         "fcgno_train_step_loss": (c_int, [P, P, P, P, c_int, c_int, c_int, P, P, P]),
         "fcgno_model_set_train_recompute": (c_int, [P, c_int]),
         "fcgno_workspace_bytes": (c_size_t, [c_int, c_int, c_int, POINTER(fcgno_model_desc), c_int]),
+        "fcgno_precision_supported": (c_int, [c_int, POINTER(fcgno_model_desc), c_int]),
         "fcgno_status_str": (c_char_p, [c_int]),
         "fcgno_last_error": (c_char_p, []),
         "fcgno_launch_count": (c_uint64, []),
@@ -91,11 +92,16 @@ EXPORTS = [
     "fcgno_assemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
     "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
-    "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_status_str",
+    "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_precision_supported", "fcgno_status_str",
     "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_trace_set", "fcgno_trace_collect",
     "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
     "fcgno_bucket_destroy",
 ]
+
+
+def precision_supported(N: int, desc: fcgno_model_desc, prec: str) -> bool:
+    """Whether the preconditioner in `prec` supports this model shape on an N x N grid."""
+    return bool(lib.fcgno_precision_supported(int(N), ctypes.byref(desc), PREC[prec]))
 
 
 def status_str(code: int) -> str:

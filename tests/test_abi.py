@@ -128,3 +128,27 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
     rejects(L.fcgno_trace_collect(ctypes.byref(ms), None), "fcgno_trace_collect")
     for destroy in (L.fcgno_op_destroy, L.fcgno_model_destroy, L.fcgno_bucket_destroy):
         assert destroy(None) == F.FCGNO_OK
+
+
+def test_precision_supported_query(libpath):
+    """fcgno_precision_supported (host-only) states the shape rule the calls enforce: the
+    CUDA-core precisions take any valid desc with N >= 2*modes, the 16-bit ones also need
+    width 16 or 32, proj_width = width and N in {32, 64} or a multiple of 128."""
+    from paper_2402_05598_gb300 import fcgno as F
+    d32 = F.make_desc(32, 4, 12)
+    d16 = F.make_desc(16, 4, 8)
+    for N in (24, 33, 48, 64, 100, 128, 130, 256, 1024):
+        for prec in ("fp64", "fp32"):
+            assert F.precision_supported(N, d32, prec)
+    for N, ok in ((32, True), (64, True), (128, True), (256, True), (2048, True),
+                  (48, False), (96, False), (100, False), (130, False), (192, False)):
+        for prec in ("bf16", "fp16"):
+            assert F.precision_supported(N, d32, prec) == ok, (N, prec)
+    assert F.precision_supported(32, d16, "bf16")
+    assert not F.precision_supported(64, F.make_desc(24, 4, 12), "bf16")       # width 24
+    assert not F.precision_supported(64, F.make_desc(32, 4, 12, 16), "bf16")   # proj_width != width
+    assert F.precision_supported(64, F.make_desc(32, 4, 12, 16), "fp64")
+    assert not F.precision_supported(22, d32, "fp64")                          # N < 2 * modes
+    assert not F.precision_supported(64, F.make_desc(width=0), "fp64")
+    assert F.lib.fcgno_precision_supported(64, ctypes.byref(d32), 9) == 0      # unknown precision
+    assert F.lib.fcgno_precision_supported(64, None, 0) == 0
