@@ -5,6 +5,7 @@ None of these compare the oracle with itself: each check would fail on a plausib
 mistake (dropped face, wrong sign, transposed axis, wrong window, wrong normalisation).
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -176,18 +177,35 @@ def test_fcg_step_is_an_exact_line_search():
                 assert abs(np.sum(p * Ap)) <= 1e-9 * math.sqrt(np.sum(p * A(p)) * np.sum(ps[kk] * Ap))
 
 
+def table1():
+    """Rows (dataset, grid, CG iterations, Jacobi(4) iterations) of Table 1, from
+    tests/golden/table1_iterations.txt."""
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "table1_iterations.txt")
+    rows = []
+    with open(path) as fh:
+        for ln in fh:
+            if ln.strip() and not ln.startswith("#"):
+                ds, grid, cg, jac = ln.split()
+                rows.append((ds, int(grid), int(cg), int(jac)))
+    return rows
+
+
+GENERATORS = {"poisson": I.poisson_problem, "diffusion": I.diffusion_problem}
+
+
 def test_table1_cg_iteration_counts_soft_pin():
-    """Table 1: CG needs 74/130 iterations (Poisson) and 75/132 (Diffusion) at grid 32/64 to
-    reach ||r_i||/||r_0|| <= 1e-6 from u_0 ~ N(0, 1). Soft pin (+-15%): the paper's grid
-    convention and draws are not published."""
-    for N, poisson, diffusion in ((32, 74, 75), (64, 130, 132)):
-        for gen, target in ((I.poisson_problem, poisson), (I.diffusion_problem, diffusion)):
-            its = []
-            for s in range(3):
-                k, f = gen(N, s)
-                u0 = np.random.default_rng(100 + s).standard_normal((N, N))
-                its.append(O.fcg(lambda u: O.apply_A(k, u), lambda r: r, f, u0, 1, 1000, tol=1e-6)["iterations"])
-            assert abs(np.mean(its) - target) <= 0.15 * target, (N, gen.__name__, its)
+    """Table 1: the iterations CG needs to reach ||r_i||/||r_0|| <= 1e-6 from u_0 ~ N(0, 1) on
+    the Poisson and Diffusion datasets at grids 32, 64 and 128. Soft pin (+-15%): the paper's
+    grid convention and draws are not published."""
+    rows = table1()
+    assert len(rows) == 6
+    for ds, N, target, _ in rows:
+        its = []
+        for s in range(3):
+            k, f = GENERATORS[ds](N, s)
+            u0 = np.random.default_rng(100 + s).standard_normal((N, N))
+            its.append(O.fcg(lambda u: O.apply_A(k, u), lambda r: r, f, u0, 1, 1000, tol=1e-6)["iterations"])
+        assert abs(np.mean(its) - target) <= 0.15 * target, (N, ds, its)
 
 
 def test_jacobi_preconditioner_fixed_point_and_steps():
@@ -572,14 +590,13 @@ def test_loss_gradient_matches_central_differences(kind):
 
 
 def test_table1_jacobi4_iteration_counts_soft_pin():
-    """Table 1: FCG with Jacobi(4) needs 30/58 iterations (Poisson) and 32/61 (Diffusion) at
-    grid 32/64 to reach 1e-6 from u_0 ~ N(0, 1). Soft pin (+-20%)."""
-    for N, poisson, diffusion in ((32, 30, 32), (64, 58, 61)):
-        for gen, target in ((I.poisson_problem, poisson), (I.diffusion_problem, diffusion)):
-            its = []
-            for s in range(2):
-                k, f = gen(N, s)
-                u0 = np.random.default_rng(100 + s).standard_normal((N, N))
-                out = O.fcg(lambda u: O.apply_A(k, u), lambda r: O.jacobi_precond(k, r, 4), f, u0, 1, 1000, tol=1e-6)
-                its.append(out["iterations"])
-            assert abs(np.mean(its) - target) <= 0.2 * target, (N, gen.__name__, its)
+    """Table 1: the iterations FCG with Jacobi(4) needs to reach 1e-6 from u_0 ~ N(0, 1) at
+    grids 32, 64 and 128. Soft pin (+-20%)."""
+    for ds, N, _, target in table1():
+        its = []
+        for s in range(2):
+            k, f = GENERATORS[ds](N, s)
+            u0 = np.random.default_rng(100 + s).standard_normal((N, N))
+            out = O.fcg(lambda u: O.apply_A(k, u), lambda r: O.jacobi_precond(k, r, 4), f, u0, 1, 1000, tol=1e-6)
+            its.append(out["iterations"])
+        assert abs(np.mean(its) - target) <= 0.2 * target, (N, ds, its)
