@@ -22,19 +22,23 @@ LOSS = {"energy": FCGNO_LOSS_ENERGY, "l2": FCGNO_LOSS_L2}
 
 
 class fcgno_model_desc(Structure):
+    """fcgno_model_desc of the C ABI: width C, layers L, modes M, proj_width C_p, in_channels (2)."""
     _fields_ = [("width", c_int), ("layers", c_int), ("modes", c_int), ("proj_width", c_int), ("in_channels", c_int)]
 
 
 class fcgno_solve_opts(Structure):
+    """fcgno_solve_opts of the C ABI: tol, m_max, max_iter, fixed_iters, check_every."""
     _fields_ = [("tol", c_double), ("m_max", c_int), ("max_iter", c_int), ("fixed_iters", c_int),
                 ("check_every", c_int)]
 
 
 class fcgno_solve_info(Structure):
+    """fcgno_solve_info of the C ABI: per-instance iterations, status, relative residual, ||r_0||."""
     _fields_ = [("iters", c_int32), ("status", c_int32), ("relres", c_double), ("r0norm", c_double)]
 
 
 class FcgnoError(RuntimeError):
+    """A non-OK fcgno_status; `code` holds it, the message the call and fcgno_last_error()."""
     def __init__(self, code: int, where: str):
         super().__init__(f"{where}: {status_str(code)} ({last_error()})")
         self.code = code
@@ -105,14 +109,17 @@ def precision_supported(N: int, desc: fcgno_model_desc, prec: str) -> bool:
 
 
 def status_str(code: int) -> str:
+    """fcgno_status_str: static text of a status."""
     return lib.fcgno_status_str(code).decode()
 
 
 def last_error() -> str:
+    """fcgno_last_error: the calling thread's last error text."""
     return lib.fcgno_last_error().decode()
 
 
 def launch_count() -> int:
+    """fcgno_launch_count: this library's kernel launches since load."""
     return int(lib.fcgno_launch_count())
 
 
@@ -159,10 +166,12 @@ def _stream(stream) -> int:
 
 
 def make_desc(width=32, layers=4, modes=12, proj_width=None, in_channels=2) -> fcgno_model_desc:
+    """A fcgno_model_desc (proj_width defaults to width)."""
     return fcgno_model_desc(width, layers, modes, proj_width if proj_width is not None else width, in_channels)
 
 
 def weight_count(desc: fcgno_model_desc) -> int:
+    """fcgno_weight_count: float32 elements of the weight blob (0 for an invalid desc)."""
     return int(lib.fcgno_weight_count(ctypes.byref(desc)))
 
 
@@ -178,6 +187,7 @@ class Operator:
                "fcgno_assemble")
 
     def apply(self, x, y, stream=None):
+        """fcgno_apply_A: y = A x for every instance."""
         _check(lib.fcgno_apply_A(self.handle, _ptr(x), _ptr(y), _stream(stream)), "fcgno_apply_A")
 
     def close(self):
@@ -225,6 +235,7 @@ class Model:
 
 
 def precond_apply(model: Model, op: Operator, r, z, prec="bf16", stream=None):
+    """fcgno_precond_apply: z = NO(r, log k) for every instance of op, in precision `prec`."""
     _check(lib.fcgno_precond_apply(model.handle, op.handle, _ptr(r), _ptr(z), PREC[prec], _stream(stream)),
            "fcgno_precond_apply")
 
@@ -284,6 +295,7 @@ def solve_noalloc(op: Operator, b, x, tol=1e-6, m_max=1, max_iter=1000, fixed_it
 
 
 def krylov_harvest(op: Operator, b, x0, u_star, K, r_out, e_out, stream=None):
+    """fcgno_krylov_harvest: K CG iterates per instance as (r_i, e_i = u_star - u_i) pairs."""
     info = (fcgno_solve_info * op.B)()
     _check(lib.fcgno_krylov_harvest(op.handle, _ptr(b), _ptr(x0), _ptr(u_star), int(K), _ptr(r_out), _ptr(e_out),
                                     info, _stream(stream)), "fcgno_krylov_harvest")
@@ -302,6 +314,7 @@ def train_step(model: Model, op: Operator, r, e, loss, grad, prec="fp32", stream
 
 
 def workspace_bytes(N, batch, m_max, desc, prec="bf16") -> int:
+    """fcgno_workspace_bytes: device bytes a solve of this shape needs (for HBM admission)."""
     return int(lib.fcgno_workspace_bytes(int(N), int(batch), int(m_max), ctypes.byref(desc), PREC[prec]))
 
 
@@ -320,18 +333,22 @@ class Bucket:
         self._relres = np.zeros(self.capacity, dtype=np.float64)
 
     def admit(self, slot, k, f, x0, stream=None):
+        """fcgno_bucket_admit: start a solve (k, f, x0: device [N][N]) in a free slot."""
         _check(lib.fcgno_bucket_admit(self.handle, int(slot), _ptr(k), _ptr(f), _ptr(x0), _stream(stream)),
                "fcgno_bucket_admit")
 
     def step(self, stream=None):
+        """fcgno_bucket_step: advance every running slot by iters_per_step iterations."""
         _check(lib.fcgno_bucket_step(self.handle, _stream(stream)), "fcgno_bucket_step")
 
     def poll(self, stream=None):
+        """fcgno_bucket_poll: (status, iterations, relative residual) per slot; synchronises."""
         _check(lib.fcgno_bucket_poll(self.handle, self._status.ctypes.data, self._iters.ctypes.data,
                                      self._relres.ctypes.data, _stream(stream)), "fcgno_bucket_poll")
         return self._status.copy(), self._iters.copy(), self._relres.copy()
 
     def take(self, slot, x_out=None, stream=None):
+        """fcgno_bucket_take: copy the slot's iterate to x_out (optional) and free the slot."""
         _check(lib.fcgno_bucket_take(self.handle, int(slot), _ptr(x_out) if x_out is not None else None,
                                      _stream(stream)), "fcgno_bucket_take")
 

@@ -31,6 +31,7 @@ from . import fcgno as F
 
 @dataclass
 class Request:
+    """One solve request: arrival time, grid size, device inputs; the loop fills in the outcome."""
     rid: int
     arrival: float          # seconds from the start of the run
     N: int
@@ -45,6 +46,7 @@ class Request:
 
 @dataclass
 class ServeStats:
+    """Latencies and counts of one serving run."""
     latencies_ms: list = field(default_factory=list)
     completed: int = 0
     converged: int = 0
@@ -54,6 +56,7 @@ class ServeStats:
     failed: int = 0
 
     def summary(self) -> dict:
+        """p50/p99/mean latency (ms), served and offered rates, counts."""
         lat = np.array(self.latencies_ms) if self.latencies_ms else np.zeros(1)
         return {"requests": self.completed, "converged": self.converged, "failed": self.failed,
                 "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),

@@ -28,6 +28,7 @@ from . import inputs as I
 
 @dataclass
 class TrainResult:
+    """Outcome of train(): steps taken, wall time (and the Krylov harvest's share), (step, loss) log."""
     steps: int
     seconds: float
     harvest_seconds: float
