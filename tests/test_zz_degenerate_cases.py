@@ -3,7 +3,8 @@ support are argument errors: the solve and the preconditioner application return
 FCGNO_EINVAL before any launch and leave their outputs untouched; the CUDA-core
 preconditioners take the same shape. A preconditioner that returns zero makes
 (p_0, A p_0) = 0: every instance stops at iteration 0 with FCGNO_EBREAKDOWN (Algorithm 1
-cannot take a step), as the oracle does, and x is left as it was."""
+cannot take a step), as the oracle does, and x is left as it was. A NaN in one instance's
+input fails that instance alone."""
 import numpy as np
 import pytest
 
