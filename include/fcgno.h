@@ -172,8 +172,10 @@ fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const doub
  * one file-scope device array of 8 MiB that every GPU loading the library keeps until the
  * process exits. Problems whose state does not fit (about 8*N*N*batch*(2*m_max+3) bytes
  * plus small terms) are rejected with FCGNO_EINVAL and a message giving the size needed.
- * The first call on a device looks up the array's device address (cudaGetSymbolAddress);
- * make that first call before any stream capture. Every call shares the array and leaves
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress)
+ * and keeps it for the life of the process; make that first call before any stream capture.
+ * A cudaDeviceReset invalidates that address together with every handle of this library:
+ * use none of them afterwards. Every call shares the array and leaves
  * its contents behind, so two calls that overlap on the GPU (different streams, threads
  * or processes sharing the context) race and corrupt each other. Arguments and results
  * are those of fcgno_solve with Bpc = NULL and prec = FCGNO_FP64; info is a HOST array. */
@@ -256,9 +258,14 @@ fcgno_status fcgno_bucket_poll(fcgno_bucket_t bucket, int32_t* status, int32_t* 
 fcgno_status fcgno_bucket_take(fcgno_bucket_t bucket, int slot, double* x_out, void* stream);
 fcgno_status fcgno_bucket_destroy(fcgno_bucket_t bucket);
 
-/* Device bytes fcgno_solve needs for one op of this shape (operator, Krylov state and the
- * preconditioner's activations), for admission against an HBM budget. Host-only; 0 for
- * N < 2, batch < 1 or m_max < 1; an invalid desc counts no preconditioner. */
+/* Device bytes fcgno_solve needs for one op of this shape, for admission against an HBM
+ * budget: the assembled operator (aE, aN, diagonal, log k in FP64 and log k in FP32), the
+ * Krylov workspace (r, w, Jacobi scratch, 1/diag, m_max+1 slots of p_k and s_k, per-instance
+ * scalars and partial sums) and the preconditioner's buffers in `prec` (16-bit activations,
+ * which belong to the operator, or the CUDA-core buffers, which belong to the model and are
+ * counted here too). The count is the sum of the sizes the library allocates. A serving
+ * bucket holds its slots' iterates and right-hand sides on top (2 * 8 * N * N per slot).
+ * Host-only; 0 for N < 2, batch < 1 or m_max < 1; an invalid desc counts no preconditioner. */
 size_t fcgno_workspace_bytes(int N, int batch, int m_max, const fcgno_model_desc* desc, fcgno_prec prec);
 
 /* 1 if the preconditioner in precision `prec` supports model shape `desc` on an N x N grid
@@ -286,6 +293,20 @@ uint64_t fcgno_launch_count(void);
  * out/fmas is NULL. */
 fcgno_status fcgno_fp64_fma_rate(int blocks, int steps, double a, double c, double* out, uint64_t* fmas,
                                  void* stream);
+
+/* Failure-detection self-test (not part of the method). Every wait of the tensor-core
+ * kernels on an mbarrier (bulk copies, MMAs, hand-offs between warp roles) is bounded: after
+ * about 1 s the kernel raises a timeout flag that belongs to the operator, drains its own
+ * copies and MMAs, frees its tensor memory and returns; fcgno_solve and fcgno_bucket_poll then
+ * read and clear the flag and return FCGNO_ETIMEOUT. This call checks that path without
+ * faulting or hanging the GPU: it launches one block on `stream` whose single active thread
+ * waits, through the same bounded wait with a limit of `limit_seconds` (1e-6 .. 1), for a
+ * barrier phase that nothing completes (no copy, MMA or other thread arrives), raises the
+ * operator's flag when the wait gives up, then reads and clears the flag (synchronising
+ * `stream`). Returns FCGNO_ETIMEOUT when the wait gave up (always, unless the GPU clock
+ * misbehaves), FCGNO_OK otherwise; the operator stays usable either way. FCGNO_EINVAL for a
+ * NULL operator or a limit outside the range; FCGNO_ENOMEM if the flag cannot be allocated. */
+fcgno_status fcgno_wait_selftest(fcgno_op_t A, double limit_seconds, void* stream);
 
 /* Kernel tracing (not part of the method): select a kernel family by name ("tc_synthesis",
  * "tc_analysis", "tc_mix", "tc_lift", "fcg_fused", "fcg_tiled", "" = off). Every later launch

@@ -294,20 +294,23 @@ extern "C" fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, con
 
 extern "C" size_t fcgno_workspace_bytes(int N, int batch, int m_max, const fcgno_model_desc* desc, fcgno_prec prec) {
   if (N < 2 || batch < 1 || m_max < 1) return 0;
-  const size_t n = (size_t)N * N, vec = n * batch * sizeof(double);
-  size_t bytes = 4 * vec;                      // operator: east, north, diagonal, log k
-  bytes += vec;                                // caller's right-hand side is not counted; x is
-  bytes += 2 * vec;                            // r, w
-  bytes += 2 * (size_t)(m_max + 1) * vec;      // direction ring (p_k, s_k)
-  bytes += (size_t)batch * 256;                // per-instance scalars and partials
+  const size_t n = (size_t)N * N;
+  size_t bytes = operator_bytes(n, batch) + solver_ws_bytes(n, batch, m_max + 1);
   if (desc_ok(desc)) {
-    const size_t C = desc->width, M = desc->modes;
-    const size_t esz = (prec == FCGNO_FP64) ? 8 : (prec == FCGNO_FP32 ? 4 : 2);
-    bytes += 2 * n * batch * C * esz;                         // activation ping-pong
-    bytes += (size_t)batch * M * N * C * 2 * 8;               // separable-transform intermediate
-    bytes += 2 * (size_t)batch * 2 * M * M * C * 2 * 8;       // spectral coefficients
+    if (prec == FCGNO_BF16 || prec == FCGNO_FP16)
+      bytes += tc_acts_bytes(N, batch, *desc);
+    else
+      bytes += simt_buffers_bytes(N, batch, *desc, prec == FCGNO_FP64);
   }
   return bytes;
+}
+
+extern "C" fcgno_status fcgno_wait_selftest(fcgno_op_t A, double limit_seconds, void* stream) {
+  if (!A || !(limit_seconds >= 1e-6 && limit_seconds <= 1.0)) {
+    set_last_error("fcgno_wait_selftest: need an operator and 1e-6 <= limit_seconds <= 1");
+    return FCGNO_EINVAL;
+  }
+  return tc_wait_probe(A, (uint64_t)(limit_seconds * 1e9), (cudaStream_t)stream);
 }
 
 extern "C" int fcgno_precision_supported(int N, const fcgno_model_desc* desc, fcgno_prec prec) {

@@ -22,6 +22,7 @@
 #include <vector>
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 
 namespace fcgno {
 
@@ -571,6 +572,29 @@ void solver_ws_free(fcgno_op* op) {
   op->ws.ev_in = op->ws.ev_out = nullptr;
 }
 
+// Byte sizes of the solver workspace's device buffers, in the order ensure_ws allocates them
+// (r, w, wt, inv_diag, P, S, ps, beta, alpha, r0, rr, rms, part, status, iters, ndone, iter).
+// fcgno_workspace_bytes sums the same list, so admission counts exactly what is allocated.
+constexpr int kWsBuffers = 17;
+static void solver_ws_sizes(size_t n, int B, int slots, size_t (&sz)[kWsBuffers]) {
+  const size_t vec = n * B * sizeof(double);
+  const size_t tiles = ceil_div(n, kTile);
+  const size_t list[kWsBuffers] = {vec, vec, vec, vec, vec * slots, vec * slots,
+                                   sizeof(double) * slots * B, sizeof(double) * kMaxWindow * B,
+                                   sizeof(double) * B, sizeof(double) * B, sizeof(double) * B, sizeof(double) * B,
+                                   sizeof(double) * B * tiles * kParts, sizeof(int) * B, sizeof(int) * B,
+                                   sizeof(int), sizeof(int)};
+  for (int i = 0; i < kWsBuffers; ++i) sz[i] = list[i];
+}
+
+size_t solver_ws_bytes(size_t n, int B, int slots) {
+  size_t sz[kWsBuffers];
+  solver_ws_sizes(n, B, slots, sz);
+  size_t t = 0;
+  for (size_t v : sz) t += v;
+  return t;
+}
+
 static fcgno_status ensure_ws(fcgno_op* op, int slots) {
   SolverWorkspace& w = op->ws;
   if (!w.cs) {
@@ -581,28 +605,16 @@ static fcgno_status ensure_ws(fcgno_op* op, int slots) {
   const int tiles = (int)ceil_div(op->n, kTile);
   if (w.cap_B == op->B && w.cap_n == (int)op->n && w.cap_slots >= slots && w.cap_tiles >= tiles) return FCGNO_OK;
   free_ws(w);
-  const size_t vec = op->n * op->B * sizeof(double);
+  size_t sz[kWsBuffers];
+  solver_ws_sizes(op->n, op->B, slots, sz);
+  void** bufs[kWsBuffers] = {(void**)&w.r,     (void**)&w.w,     (void**)&w.wt,     (void**)&w.inv_diag,
+                             (void**)&w.P,     (void**)&w.S,     (void**)&w.ps,     (void**)&w.beta,
+                             (void**)&w.alpha, (void**)&w.r0,    (void**)&w.rr,     (void**)&w.rms,
+                             (void**)&w.part,  (void**)&w.status, (void**)&w.iters, (void**)&w.ndone,
+                             (void**)&w.iter};
   bool ok = true;
-  auto alloc = [&](void** p, size_t bytes) {
-    if (ok && cudaMalloc(p, bytes) != cudaSuccess) ok = false;
-  };
-  alloc((void**)&w.r, vec);
-  alloc((void**)&w.w, vec);
-  alloc((void**)&w.wt, vec);
-  alloc((void**)&w.inv_diag, vec);
-  alloc((void**)&w.P, vec * slots);
-  alloc((void**)&w.S, vec * slots);
-  alloc((void**)&w.ps, sizeof(double) * slots * op->B);
-  alloc((void**)&w.beta, sizeof(double) * kMaxWindow * op->B);
-  alloc((void**)&w.alpha, sizeof(double) * op->B);
-  alloc((void**)&w.r0, sizeof(double) * op->B);
-  alloc((void**)&w.rr, sizeof(double) * op->B);
-  alloc((void**)&w.rms, sizeof(double) * op->B);
-  alloc((void**)&w.part, sizeof(double) * op->B * tiles * kParts);
-  alloc((void**)&w.status, sizeof(int) * op->B);
-  alloc((void**)&w.iters, sizeof(int) * op->B);
-  alloc((void**)&w.ndone, sizeof(int));
-  alloc((void**)&w.iter, sizeof(int));
+  for (int i = 0; i < kWsBuffers && ok; ++i)
+    if (cudaMalloc(bufs[i], sz[i]) != cudaSuccess) ok = false;
   if (!ok) {
     cudaGetLastError();
     free_ws(w);
@@ -1047,9 +1059,11 @@ namespace fcgno {
 constexpr size_t kNoAllocScratchBytes = (size_t)8 << 20;  // 8 MiB per device
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 static void* g_noalloc_addr[64] = {};  // device address of the array, per device ordinal
+static std::mutex g_noalloc_mu;         // guards g_noalloc_addr
 
 // Device address of the scratch array for the current device. The first call on a device
-// resolves it with cudaGetSymbolAddress (host code cannot use the symbol's own address).
+// resolves it with cudaGetSymbolAddress (host code cannot use the symbol's own address);
+// threads racing on that first call take the lock, so each device is resolved once.
 static fcgno_status noalloc_scratch_address(void** out) {
   int dev = -1;
   FCGNO_CUDA_TRY(cudaGetDevice(&dev));
@@ -1057,6 +1071,7 @@ static fcgno_status noalloc_scratch_address(void** out) {
     set_last_error("fcgno_solve_noalloc: device ordinal out of range");
     return FCGNO_EINVAL;
   }
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_addr[dev]) {
     void* p = nullptr;
     FCGNO_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
@@ -1254,32 +1269,46 @@ extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t m
     set_last_error("fcgno_bucket_create: out of memory");
     return rc;
   }
-  // unused slots: neutral operator values, status "stopped" so that every kernel skips them
-  cudaMemsetAsync(op->aE, 0, vec, st);
-  cudaMemsetAsync(op->aN, 0, vec, st);
-  cudaMemsetAsync(op->logk, 0, vec, st);
-  cudaMemsetAsync(op->logk32, 0, vec / 2, st);
-  cudaMemsetAsync(k->x, 0, vec, st);
-  cudaMemsetAsync(k->b, 0, vec, st);
-  cudaMemsetAsync(op->ws.r, 0, vec, st);
-  cudaMemsetAsync(op->ws.rms, 0, sizeof(double) * capacity, st);
-  cudaMemsetAsync(op->ws.iters, 0, sizeof(int) * capacity, st);
-  std::vector<int> stopped(capacity, FCGNO_OK);
-  FCGNO_CUDA_TRY(cudaMemcpyAsync(op->ws.status, stopped.data(), sizeof(int) * capacity, cudaMemcpyHostToDevice, st));
-  FCGNO_CUDA_TRY(cudaMemsetAsync(op->diag, 0, vec, st));
-  FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
-  SolverWorkspace& w = op->ws;
-  const bool identity = (model == nullptr);
-  k->s = make_state(op, k->b, k->x, identity ? w.r : w.w);
-  k->a.N = N;
-  k->a.B = capacity;
-  k->a.n = op->n;
-  k->a.tiles = (int)ceil_div(op->n, kTile);
-  k->a.nslots = m_max + 1;
-  k->a.tol = tol;
-  k->a.fixed = 0;
-  k->L = loop_shape(op);
-  FCGNO_TRY(prepare_fused(k->L));
+  // Everything after the allocations fails through one path that destroys the bucket (and
+  // its operator, workspace and pinned mirrors).
+  auto setup = [&]() -> fcgno_status {
+    // unused slots: neutral operator values, status "stopped" so that every kernel skips them
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->aE, 0, vec, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->aN, 0, vec, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->logk, 0, vec, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->logk32, 0, vec / 2, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(k->x, 0, vec, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(k->b, 0, vec, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->ws.r, 0, vec, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->ws.rms, 0, sizeof(double) * capacity, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->ws.iters, 0, sizeof(int) * capacity, st));
+    std::vector<int> stopped(capacity, FCGNO_OK);
+    FCGNO_CUDA_TRY(
+        cudaMemcpyAsync(op->ws.status, stopped.data(), sizeof(int) * capacity, cudaMemcpyHostToDevice, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->diag, 0, vec, st));
+    FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
+    SolverWorkspace& w = op->ws;
+    const bool identity = (model == nullptr);
+    k->s = make_state(op, k->b, k->x, identity ? w.r : w.w);
+    k->a.N = N;
+    k->a.B = capacity;
+    k->a.n = op->n;
+    k->a.tiles = (int)ceil_div(op->n, kTile);
+    k->a.nslots = m_max + 1;
+    k->a.tol = tol;
+    k->a.fixed = 0;
+    k->L = loop_shape(op);
+    FCGNO_TRY(prepare_fused(k->L));
+    return FCGNO_OK;
+  };
+  rc = setup();
+  if (rc != FCGNO_OK) {
+    const std::string why = fcgno_last_error();
+    cudaGetLastError();
+    fcgno_bucket_destroy(k);
+    set_last_error("fcgno_bucket_create: " + why);
+    return rc;
+  }
   *out = k;
   return FCGNO_OK;
 }

@@ -211,12 +211,21 @@ fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, co
 // and the rule in words (for error messages). Host-only.
 bool tc_shape_supported(int N, const fcgno_model_desc& d);
 const char* tc_shape_rule();
+// Device bytes of the buffers each path allocates for a batch of B on an N x N grid (the
+// sizes the allocating code uses): tensor-core activations per operator, CUDA-core buffers
+// per model, the solver workspace per operator (slots = m_max + 1) and the assembled operator.
+size_t tc_acts_bytes(int N, int B, const fcgno_model_desc& d);
+size_t simt_buffers_bytes(int N, int B, const fcgno_model_desc& d, bool fp64);
+size_t solver_ws_bytes(size_t n, int B, int slots);
+size_t operator_bytes(size_t n, int B);
 fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t st);
 void tc_model_free(fcgno_model* m);
 void tc_acts_free(fcgno_op* op);
 // Reads and clears the operator's tensor-core timeout flag (synchronises `st`): FCGNO_ETIMEOUT
 // if a kernel of the 16-bit preconditioner gave up one of its bounded waits since the last call.
 fcgno_status tc_take_timeout(const fcgno_op* op, cudaStream_t st);
+// Failure-detection self-test of the bounded wait (see fcgno_wait_selftest).
+fcgno_status tc_wait_probe(const fcgno_op* op, uint64_t limit_ns, cudaStream_t st);
 void no_workspace_free(fcgno_model* m);
 
 // Per-instance rms of r: rms[b] = sqrt(mean(r_b^2)).

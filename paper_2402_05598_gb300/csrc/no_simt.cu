@@ -403,12 +403,26 @@ static Wp<T> wptrs(const fcgno_model* m, const T* base) {
   return p;
 }
 
+// Elements of the CUDA-core preconditioner's buffers for a batch of B on an N x N grid:
+// two activation ping-pong buffers (B n C), the separable-transform intermediate (complex
+// B M N C) and two spectral-coefficient buffers (complex B 2M^2 C).
+static void simt_elems(int N, int B, const fcgno_model_desc& d, size_t& elems, size_t& mid, size_t& spec) {
+  const size_t C = d.width, M = d.modes;
+  elems = (size_t)B * N * N * C;
+  spec = (size_t)B * 2 * M * M * C;
+  mid = (size_t)B * M * N * C;
+}
+
+size_t simt_buffers_bytes(int N, int B, const fcgno_model_desc& d, bool fp64) {
+  size_t elems, mid, spec;
+  simt_elems(N, B, d, elems, mid, spec);
+  return (2 * elems + 2 * mid + 4 * spec) * (fp64 ? 8 : 4);
+}
+
 template <typename T>
 static fcgno_status ensure_simt(fcgno_model* m, const fcgno_op* op, SimtBuffers& s) {
-  const int C = m->desc.width, M = m->desc.modes;
-  const size_t elems = (size_t)op->B * op->n * C;
-  const size_t spec = (size_t)op->B * 2 * M * M * C;
-  const size_t mid = (size_t)op->B * M * op->N * C;
+  size_t elems, mid, spec;
+  simt_elems(op->N, op->B, m->desc, elems, mid, spec);
   if (s.cap_elems >= elems && s.cap_spec >= spec && s.cap_mid >= mid) return FCGNO_OK;
   cfree(s.va);
   cfree(s.vb);

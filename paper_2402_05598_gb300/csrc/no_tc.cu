@@ -136,6 +136,16 @@ static TcGeom make_geom(int N, int C, int M) {
   return g;
 }
 
+// 16-bit elements of an operator's activation buffers for a batch of B: each of the two
+// ping-pong activation images (B n C), the partial spectral coefficients (mode x column chunk
+// x block of 128 instances x 128 x 2C) and the mixed-coefficient images (B x MP x KXP).
+static void tc_acts_elems(const TcGeom& g, int B, size_t& v, size_t& part, size_t& chat) {
+  const size_t nbt = ceil_div(B, 128);
+  v = (size_t)B * g.N * g.N * g.C;
+  part = (size_t)g.nmodes * g.nchunks * nbt * 128 * 2 * g.C;
+  chat = (size_t)B * g.MP * g.KXP;
+}
+
 static bool geom_supported(int N, int C, int M, int Cp) {
   if (!(C == 16 || C == 32) || Cp != C || M < 1 || M > 16 || N < 2 * M) return false;
   if (!(N == 32 || N == 64 || (N >= 128 && N % 128 == 0))) return false;
@@ -326,6 +336,39 @@ void tc_acts_free(fcgno_op* op) {
   op->tc_acts = nullptr;
 }
 
+// The operator's timeout flag, allocated (zeroed on `st`) on first use.
+static fcgno_status ensure_err_flag(const fcgno_op* op, cudaStream_t st) {
+  if (!op->tc_acts) op->tc_acts = new TcActs();
+  TcActs& T = *op->tc_acts;
+  if (T.err) return FCGNO_OK;
+  if (cudaMalloc(&T.err, sizeof(int)) != cudaSuccess) {
+    cudaGetLastError();
+    T.err = nullptr;
+    set_last_error("tensor-core preconditioner error flag: out of device memory");
+    return FCGNO_ENOMEM;
+  }
+  FCGNO_CUDA_TRY(cudaMemsetAsync(T.err, 0, sizeof(int), st));
+  return FCGNO_OK;
+}
+
+// Failure-detection self-test: one thread initialises an mbarrier that expects one arrival,
+// which nothing provides, and waits for its first phase through the bounded wait of the
+// tensor-core kernels with the given limit. When the wait gives up it raises the timeout
+// flag exactly as those kernels do. Nothing is in flight: no copy, MMA or TMEM allocation.
+__global__ void wait_probe_kernel(uint64_t limit_ns, int* __restrict__ err) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  if (!mbar_wait(&bar, 0, limit_ns)) atomicExch(err, 1);
+}
+
+fcgno_status tc_wait_probe(const fcgno_op* op, uint64_t limit_ns, cudaStream_t st) {
+  FCGNO_TRY(ensure_err_flag(op, st));
+  wait_probe_kernel<<<1, 32, 0, st>>>(limit_ns, op->tc_acts->err);
+  FCGNO_LAUNCHED();
+  return tc_take_timeout(op, st);
+}
+
 fcgno_status tc_take_timeout(const fcgno_op* op, cudaStream_t st) {
   if (!op->tc_acts || !op->tc_acts->err) return FCGNO_OK;
   int flag = 0;
@@ -333,7 +376,7 @@ fcgno_status tc_take_timeout(const fcgno_op* op, cudaStream_t st) {
   FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
   if (flag == 0) return FCGNO_OK;
   FCGNO_CUDA_TRY(cudaMemsetAsync(op->tc_acts->err, 0, sizeof(int), st));
-  set_last_error("a tensor-core preconditioner kernel gave up a bounded device wait (about 1 s): "
+  set_last_error("a tensor-core preconditioner kernel gave up a bounded device wait: "
                  "preconditioner outputs on this operator since the last check are invalid");
   return FCGNO_ETIMEOUT;
 }
@@ -1273,22 +1316,13 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     if (cap == cudaStreamCaptureStatusNone) FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
   }
   TcPrecision& P = m->tc->prec[fp16 ? 1 : 0];
-  if (!op->tc_acts) op->tc_acts = new TcActs();
+  FCGNO_TRY(ensure_err_flag(op, st));
   TcActs& T = *op->tc_acts;
-  if (!T.err) {
-    if (cudaMalloc(&T.err, sizeof(int)) != cudaSuccess) {
-      cudaGetLastError();
-      T.err = nullptr;
-      set_last_error("tensor-core preconditioner error flag: out of device memory");
-      return FCGNO_ENOMEM;
-    }
-    FCGNO_CUDA_TRY(cudaMemsetAsync(T.err, 0, sizeof(int), st));
-  }
   const int B = op->B;
   const size_t n = op->n;
   const int nbt = ceil_div(B, 128);
-  const size_t need_v = (size_t)B * n * C, need_part = (size_t)g.nmodes * g.nchunks * nbt * 128 * 2 * C,
-               need_chat = (size_t)B * g.MP * g.KXP;
+  size_t need_v, need_part, need_chat;
+  tc_acts_elems(g, B, need_v, need_part, need_chat);
   if (T.cap_v < need_v || T.cap_part < need_part || T.cap_chat < need_chat) {
     free_acts(T);
     if (cudaMalloc(&T.va, need_v * 2) != cudaSuccess || cudaMalloc(&T.vb, need_v * 2) != cudaSuccess ||
@@ -1388,6 +1422,14 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     std::swap(cur, nxt);
   }
   return FCGNO_OK;
+}
+
+size_t tc_acts_bytes(int N, int B, const fcgno_model_desc& d) {
+  if (!tc_shape_supported(N, d)) return 0;
+  const TcGeom g = make_geom(N, d.width, d.modes);
+  size_t v, part, chat;
+  tc_acts_elems(g, B, v, part, chat);
+  return 2 * (2 * v + part + chat) + sizeof(int);  // 16-bit elements; the timeout flag
 }
 
 bool tc_shape_supported(int N, const fcgno_model_desc& d) {

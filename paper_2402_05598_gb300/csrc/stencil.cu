@@ -88,6 +88,9 @@ fcgno_status launch_rms(const double* r, int B, size_t n, double* rms, cudaStrea
 
 using namespace fcgno;
 
+// An assembled operator holds aE, aN, the diagonal and log k in FP64 and log k in FP32.
+size_t fcgno::operator_bytes(size_t n, int B) { return 4 * n * B * sizeof(double) + n * B * sizeof(float); }
+
 extern "C" fcgno_status fcgno_assemble(int N, int batch, const double* k, void* stream, fcgno_op_t* out) {
   if (N < 2 || batch < 1 || !k || !out) {
     set_last_error("fcgno_assemble: need N >= 2, batch >= 1, non-null k and out");

@@ -79,8 +79,10 @@ __device__ __forceinline__ bool named_barrier_and(int id, int count, bool pred) 
   return r != 0;
 }
 
-// Bounded wait for the given phase parity. Returns false after ~1 s without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
+// Bounded wait for the given phase parity. Returns false after limit_ns (default 1 s) of
+// %globaltimer time without completion; the timer is read every 256 polls.
+constexpr uint64_t kWaitLimitNs = 1000000000ull;
+__device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, uint64_t limit_ns = kWaitLimitNs) {
   const uint32_t a = smem_addr(mbar);
   uint32_t ok = 0;
   uint64_t t0 = 0;
@@ -92,7 +94,7 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity) {
         : "memory");
     if (ok) return true;
     if (it == 0) t0 = globaltimer();
-    if ((it & 255) == 255 && globaltimer() - t0 > 1000000000ull) return false;
+    if ((it & 255) == 255 && globaltimer() - t0 > limit_ns) return false;
   }
 }
 

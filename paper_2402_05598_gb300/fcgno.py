@@ -79,6 +79,7 @@ def _load():
         "fcgno_bucket_poll": (c_int, [P, P, P, P, P]),
         "fcgno_bucket_take": (c_int, [P, c_int, P, P]),
         "fcgno_bucket_destroy": (c_int, [P]),
+        "fcgno_wait_selftest": (c_int, [P, c_double, P]),
         "fcgno_trace_set": (c_int, [c_char_p]),
         "fcgno_trace_collect": (c_int, [POINTER(c_double), POINTER(c_uint64)]),
     }
@@ -97,7 +98,8 @@ EXPORTS = [
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
     "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
     "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_precision_supported", "fcgno_status_str",
-    "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_trace_set", "fcgno_trace_collect",
+    "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_wait_selftest", "fcgno_trace_set",
+    "fcgno_trace_collect",
     "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
     "fcgno_bucket_destroy",
 ]
@@ -130,6 +132,15 @@ def fp64_fma_rate(blocks: int, steps: int, a: float, c: float, out, stream=None)
     _check(lib.fcgno_fp64_fma_rate(int(blocks), int(steps), float(a), float(c), _ptr(out), ctypes.byref(n),
                                    _stream(stream)), "fcgno_fp64_fma_rate")
     return int(n.value)
+
+
+def wait_selftest(op: "Operator", limit_seconds: float, stream=None) -> int:
+    """fcgno_wait_selftest: a bounded wait on a barrier nothing completes; returns the status
+    code (FCGNO_ETIMEOUT when the wait gave up) instead of raising for it."""
+    code = lib.fcgno_wait_selftest(op.handle, float(limit_seconds), _stream(stream))
+    if code not in (FCGNO_OK, FCGNO_ETIMEOUT):
+        raise FcgnoError(code, "fcgno_wait_selftest")
+    return code
 
 
 def trace_set(family: str):

@@ -10,9 +10,10 @@ the GPU and a small solve does not wait behind a large one. The loop repeatedly
   2. starts one step (a few FCG-NO iterations, replayed as one CUDA graph) of every bucket
      that has running slots and no step in flight,
   3. for every bucket whose step has finished (an event query, no waiting), reads the slot
-     states and retires finished slots (converged, breakdown, or capped), recording each
-     request's completion time.
-Latency = completion time - arrival time (queueing included). A request the library rejects
+     states and retires finished slots (converged, breakdown, or capped): each retired
+     slot's iterate is copied into its request's output tensor, and the request completes
+     once that copy has finished.
+Latency = completion time - arrival time (queueing and delivery of the result included). A request the library rejects
 at admission (FcgnoError: bad input, no memory) completes at once with that status and its
 slot stays free; when a bucket's poll reports FCGNO_ETIMEOUT (a bounded device wait gave up
 during its step) every solve running in that bucket completes with that status and the
@@ -38,6 +39,7 @@ class Request:
     k: object               # device [N][N] float64
     f: object
     x0: object
+    out: object = None      # device [N][N] float64 receiving the solution (None: written into x0)
     done: float = -1.0
     iters: int = 0
     status: int = -1
@@ -173,13 +175,17 @@ class Server:
                             self.slots[N][i] = None
                             outstanding -= 1
                     continue
+                retired = [i for i, r in enumerate(self.slots[N]) if r is not None and st[i] != -1]
+                for i in retired:
+                    r = self.slots[N][i]
+                    self.buckets[N].take(i, r.out if r.out is not None else r.x0, stream=self.streams[N])
+                if retired:
+                    self.streams[N].synchronize()  # the results have been delivered
                 tnow = time.perf_counter() - t0
-                for i, r in enumerate(self.slots[N]):
-                    if r is not None and st[i] != -1:
-                        self.buckets[N].take(i, stream=self.streams[N])
-                        self._complete(r, st[i], it[i], rr[i], tnow, stats)
-                        self.slots[N][i] = None
-                        outstanding -= 1
+                for i in retired:
+                    self._complete(self.slots[N][i], st[i], it[i], rr[i], tnow, stats)
+                    self.slots[N][i] = None
+                    outstanding -= 1
             if not progressed:
                 if not busy and pending:  # idle until the next arrival
                     time.sleep(max(0.0, min(0.001, pending[0].arrival - (time.perf_counter() - t0))))

@@ -124,6 +124,9 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
     rejects(L.fcgno_bucket_step(None, None), "fcgno_bucket_step")
     rejects(L.fcgno_bucket_poll(None, hp, hp, hp, None), "fcgno_bucket_poll")
     rejects(L.fcgno_bucket_take(None, 0, None, None), "fcgno_bucket_take")
+    rejects(L.fcgno_wait_selftest(None, 1e-3, None), "fcgno_wait_selftest")
+    rejects(L.fcgno_wait_selftest(ctypes.c_void_p(1), 0.0, None), "fcgno_wait_selftest")
+    rejects(L.fcgno_wait_selftest(ctypes.c_void_p(1), 2.0, None), "fcgno_wait_selftest")
     rejects(L.fcgno_trace_collect(None, ctypes.byref(n)), "fcgno_trace_collect")
     rejects(L.fcgno_trace_collect(ctypes.byref(ms), None), "fcgno_trace_collect")
     for destroy in (L.fcgno_op_destroy, L.fcgno_model_destroy, L.fcgno_bucket_destroy):

@@ -10,7 +10,7 @@ import pytest
 from oracle import fcgno_oracle as O
 from paper_2402_05598_gb300 import inputs as I
 
-from test_gpu_parity import batch, model_pair, rel, to_dev
+from test_gpu_parity import ELEM_TOL, batch, elem_check, model_pair, rel, to_dev
 
 pytestmark = pytest.mark.gpu
 
@@ -32,8 +32,10 @@ def test_preconditioner_at_workload_sizes_sampled(lib, dev, N, M, B, sigma, ell,
     zs = z.cpu().numpy()
     assert np.all(np.isfinite(zs))
     for b in sample:
-        err = rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b])))
+        ref = O.no_forward(P, desc, r[b], np.log(k[b]))
+        err = rel(zs[b], ref)
         assert err < 2e-2, (b, err)
+        elem_check(zs[b], ref, ELEM_TOL["bf16"], ("bf16", N, b))
 
 
 @pytest.mark.parametrize("N,B,prec", [(1024, 8, "bf16"), (2048, 2, "bf16"), (256, 4, "fp64")])
@@ -62,6 +64,7 @@ def test_large_solve_recursive_residual_is_the_true_residual(lib, dev, N, B, pre
         ref = O.fcg(lambda u: O.apply_A(k[0], u), lambda r: O.no_forward(P, desc, r, np.log(k[0])), f[0],
                     np.zeros((N, N)), 5, 6)
         assert rel(xs[0], ref["u"]) < 1e-10
+        elem_check(xs[0], ref["u"], 1e-10, ("fp64 iterate", N))
 
 
 def test_bf16_iterations_within_15_percent_of_fp64(lib, dev):

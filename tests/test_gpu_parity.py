@@ -16,6 +16,32 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
+# Element-wise bounds (beside the 2-norm ones). FP64 paths: the stated tolerance itself, as a
+# fraction of max|oracle|. 16-bit tensor-core preconditioner: every operand is rounded to 8
+# (BF16) or 11 (FP16) significant bits, unit roundoff u = 2^-9 / 2^-12, and each of the four
+# layers adds roughly u times the field's scale through its contractions (FP32 accumulation),
+# so the error of one grid point stays within a few times 4u of max|z|: 4u = 7.8e-3 (BF16),
+# 9.8e-4 (FP16). The bounds below are 5e-2 (BF16) and 1e-2 (FP16) of max|z|.
+ELEM_TOL = {"fp64": 1e-12, "fp32": 1e-4, "bf16": 5e-2, "fp16": 1e-2}
+
+
+def elem_check(z, ref, tol, what=""):
+    """max |z - ref| <= tol * max|ref| over the whole grid, and on each grid edge (q = 0,
+    q = N-1, p = 0, p = N-1) relative to that edge's own max|ref|, so that one wrong grid
+    point, a wrong tile edge or a wrong boundary column cannot hide in a norm."""
+    z, ref = np.asarray(z, dtype=np.float64), np.asarray(ref, dtype=np.float64)
+    assert z.shape == ref.shape and z.ndim == 2
+    err = np.abs(z - ref)
+    scale = float(np.max(np.abs(ref)))
+    worst = np.unravel_index(int(np.argmax(err)), err.shape)
+    assert err.max() <= tol * scale, (what, "max", float(err.max() / max(scale, 1e-300)), worst)
+    edges = {"q=0": (0, slice(None)), "q=N-1": (-1, slice(None)), "p=0": (slice(None), 0),
+             "p=N-1": (slice(None), -1)}
+    for name, sl in edges.items():
+        es, ss = float(err[sl].max()), float(np.max(np.abs(ref[sl])))
+        assert es <= tol * ss, (what, name, es / max(ss, 1e-300))
+
+
 def to_dev(x, dev, dtype=None):
     import torch
     t = torch.from_numpy(np.ascontiguousarray(x))
@@ -40,9 +66,11 @@ def batch(N, B, seed0, sigma=1.0, ell=0.1):
     return I.make_batch(N, range(seed0, seed0 + B), sigma, ell)
 
 
-def model_pair(lib, dev, C, M, L=4, seed=0):
+def model_pair(lib, dev, C, M, L=4, seed=0, wscale=1.0):
+    """Seeded Xavier weights (times `wscale`, which drives the GELUs further from their
+    linear range) with nonzero biases; returns (desc, oracle weights, library model, blob)."""
     desc_np = I.ModelDesc(width=C, layers=L, modes=M, proj_width=C)
-    blob = I.xavier_weights(desc_np, seed)
+    blob = I.xavier_weights(desc_np, seed) * np.float32(wscale)
     # give the biases nonzero values so that every parameter is exercised
     off = I.weight_offsets(desc_np)
     rng = np.random.default_rng(seed + 77)
@@ -64,7 +92,23 @@ def test_stencil_matches_oracle(lib, dev, N, B):
     op.apply(to_dev(f, dev), y)
     torch.cuda.synchronize()
     for b in range(B):
-        assert rel(y[b].cpu().numpy(), O.apply_A(k[b], f[b])) < 1e-14
+        ref = O.apply_A(k[b], f[b])
+        assert rel(y[b].cpu().numpy(), ref) < 1e-14
+        elem_check(y[b].cpu().numpy(), ref, 1e-14, ("stencil", b))
+
+
+@pytest.mark.parametrize("N,axis,j", [(64, 1, 3), (130, 0, 2), (33, 1, 1)])
+def test_stencil_layered_coefficient_closed_form(lib, dev, N, axis, j):
+    """The CUDA stencil against the flux-balance closed form of a layered coefficient (no
+    oracle involved): harmonic-mean interior faces, boundary faces at k of the node, 1/h^2."""
+    import torch
+    import closed_forms as CF
+    k, u, Au = CF.layered_flux_field(N, axis=axis, j=j, seed=N)
+    op = lib.Operator(to_dev(k[None], dev))
+    y = torch.empty((1, N, N), dtype=torch.float64, device=dev)
+    op.apply(to_dev(u[None], dev), y)
+    torch.cuda.synchronize()
+    elem_check(y[0].cpu().numpy(), Au, 1e-12, "layered")
 
 
 # ------------------------------------------------------------------------------- CG / FCG(B=I)
@@ -86,6 +130,7 @@ def test_identity_preconditioned_iterates_match_oracle(lib, dev, N, B, m):
                                            **({} if d is None else {"dot": d}))["u"])
         assert info[b]["iters"] == 20
         assert rel(xs[b], ref["u"]) < tol
+        elem_check(xs[b], ref["u"], tol, ("iterate", b))
         assert abs(info[b]["relres"] - ref["relres"][-1]) <= 1e-8 * ref["relres"][-1]
 
 
@@ -120,7 +165,9 @@ def test_fp64_preconditioner_matches_oracle(lib, dev, N, C, M, B):
     lib.precond_apply(model, op, to_dev(r, dev), z, prec="fp64")
     zs = z.cpu().numpy()
     for b in range(B):
-        assert rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b]))) < 1e-12
+        ref = O.no_forward(P, desc, r[b], np.log(k[b]))
+        assert rel(zs[b], ref) < 1e-12
+        elem_check(zs[b], ref, ELEM_TOL["fp64"], ("fp64 NO", b))
 
 
 @pytest.mark.parametrize("N,C,M,B", [(32, 16, 8, 2), (64, 32, 12, 2)])
@@ -133,7 +180,9 @@ def test_fp32_preconditioner_matches_oracle(lib, dev, N, C, M, B):
     lib.precond_apply(model, op, to_dev(r, dev), z, prec="fp32")
     zs = z.cpu().numpy()
     for b in range(B):
-        assert rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b]))) < 2e-5
+        ref = O.no_forward(P, desc, r[b], np.log(k[b]))
+        assert rel(zs[b], ref) < 2e-5
+        elem_check(zs[b], ref, ELEM_TOL["fp32"], ("fp32 NO", b))
 
 
 def test_fcg_no_fp64_thirty_iterations_match_oracle(lib, dev):
@@ -156,6 +205,7 @@ def test_fcg_no_fp64_thirty_iterations_match_oracle(lib, dev):
                 np.zeros((N, N)), 1, 30)
     assert info[0]["iters"] == 30
     assert rel(x[0].cpu().numpy(), ref["u"]) < 1e-10
+    elem_check(x[0].cpu().numpy(), ref["u"], 1e-10, "30 iterations")
     x.zero_()
     info = lib.solve(op, None, to_dev(f, dev), x, tol=1e-8, m_max=1, max_iter=5000, prec="fp64")
     ref = O.fcg(lambda u: O.apply_A(k[0], u), lambda r: r, f[0], np.zeros((N, N)), 1, 5000, tol=1e-8)
@@ -179,6 +229,7 @@ def test_fcg_no_fp64_window_matches_oracle(lib, dev, N, m):
         ref = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: O.no_forward(P, desc, r, np.log(k[b])), f[b],
                     np.zeros((N, N)), m, 12)
         assert rel(xs[b], ref["u"]) < 1e-10
+        elem_check(xs[b], ref["u"], 1e-10, ("window", b))
 
 
 def test_solve_host_matches_device_solve(lib, dev):
@@ -211,29 +262,37 @@ def test_krylov_harvest_matches_oracle_cg(lib, dev):
         for i in range(K):
             assert rel(rs[i, b], ref["rs"][i + 1]) < 1e-11
             assert rel(es[i, b], ustar[b] - ref["us"][i + 1]) < 1e-11
+            elem_check(rs[i, b], ref["rs"][i + 1], 1e-11, ("harvest r", i, b))
+            elem_check(es[i, b], ustar[b] - ref["us"][i + 1], 1e-11, ("harvest e", i, b))
 
 
 # ------------------------------------------------------------------------------- tensor cores
-@pytest.mark.parametrize("N,C,M,B,prec,tol", [
-    (32, 16, 8, 2, "bf16", 2e-2),
-    (64, 32, 12, 3, "bf16", 2e-2),
-    (64, 32, 12, 2, "fp16", 4e-3),
-    (128, 32, 12, 2, "bf16", 2e-2),
-    (64, 32, 16, 2, "bf16", 2e-2),
+@pytest.mark.parametrize("N,C,M,B,prec,tol,sigma,wscale", [
+    (32, 16, 8, 2, "bf16", 2e-2, 1.0, 1.0),
+    (64, 32, 12, 3, "bf16", 2e-2, 1.0, 1.0),
+    (64, 32, 12, 2, "fp16", 4e-3, 1.0, 1.0),
+    (128, 32, 12, 2, "bf16", 2e-2, 1.0, 1.0),
+    (64, 32, 16, 2, "bf16", 2e-2, 1.0, 1.0),
+    (64, 32, 12, 2, "bf16", 2e-2, 2.0, 1.0),   # the high-contrast coefficient family
+    (32, 16, 8, 2, "bf16", 2e-2, 2.0, 2.5),    # and weights far into the GELUs' nonlinear range
+    (256, 32, 12, 1, "bf16", 2e-2, 0.5, 2.5),
 ])
-def test_tensor_core_preconditioner_matches_oracle(lib, dev, N, C, M, B, prec, tol):
+def test_tensor_core_preconditioner_matches_oracle(lib, dev, N, C, M, B, prec, tol, sigma, wscale):
     """tcgen05 BF16/FP16 preconditioner (FP32 accumulation) against the FP64 oracle:
-    relative 2-norm error per instance within 2e-2 (BF16) / 4e-3 (FP16)."""
+    relative 2-norm error per instance within 2e-2 (BF16) / 4e-3 (FP16), and element by
+    element (including each grid edge) within ELEM_TOL of max|z|."""
     import torch
-    k, r = batch(N, B, 900 + N + M)
-    desc, P, model, _w = model_pair(lib, dev, C, M)
+    k, r = batch(N, B, 900 + N + M, sigma)
+    desc, P, model, _w = model_pair(lib, dev, C, M, wscale=wscale)
     op = lib.Operator(to_dev(k, dev))
     z = torch.empty((B, N, N), dtype=torch.float64, device=dev)
     lib.precond_apply(model, op, to_dev(r, dev), z, prec=prec)
     zs = z.cpu().numpy()
     for b in range(B):
-        err = rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b])))
+        ref = O.no_forward(P, desc, r[b], np.log(k[b]))
+        err = rel(zs[b], ref)
         assert err < tol, (b, err)
+        elem_check(zs[b], ref, ELEM_TOL[prec], (prec, b))
 
 
 @pytest.mark.parametrize("N,C,M,B,sample", [
@@ -259,8 +318,10 @@ def test_tensor_core_preconditioner_full_size_sampled(lib, dev, N, C, M, B, samp
     for b in sample:
         if b == B - 1 and B > 1:
             continue
-        err = rel(zs[b], O.no_forward(P, desc, r[b], np.log(k[b])))
+        ref = O.no_forward(P, desc, r[b], np.log(k[b]))
+        err = rel(zs[b], ref)
         assert err < 2e-2, (b, err)
+        elem_check(zs[b], ref, ELEM_TOL["bf16"], ("bf16 full size", b))
 
 
 def test_tensor_core_preconditioner_inside_solve(lib, dev):
@@ -381,3 +442,26 @@ def test_jacobi_preconditioned_iterates_match_oracle(lib, dev, N, B, steps, m):
                               m, 15, **({} if d is None else {"dot": d}))["u"]
         assert info[b]["iters"] == 15
         assert rel(xs[b], run(None)) < rounding_tol(run)
+
+
+def test_workspace_bytes_counts_what_a_solve_allocates(lib, dev):
+    """fcgno_workspace_bytes (the figure serving admits against) against the device memory a
+    first BF16 solve actually takes (operator, Krylov workspace, 16-bit activations): not
+    below it, and above it by no more than allocation rounding and the model's per-grid
+    tables and weight images (96 MiB). At 512 x 512 x 32 one FP64 vector is 64 MiB, so
+    leaving out even one buffer of the workspace would fail the test."""
+    import torch
+    N, B, m = 512, 32, 5
+    k, f = batch(N, B, 9100)
+    kd, fd = to_dev(k, dev), to_dev(f, dev)
+    x = torch.zeros((B, N, N), dtype=torch.float64, device=dev)
+    desc, P, model, _w = model_pair(lib, dev, 32, 12)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    op = lib.Operator(kd)
+    lib.solve(op, model, fd, x, m_max=m, max_iter=1, fixed_iters=True, prec="bf16")
+    torch.cuda.synchronize()
+    used = free0 - torch.cuda.mem_get_info()[0]
+    predicted = lib.workspace_bytes(N, B, m, lib.make_desc(32, 4, 12, 32), "bf16")
+    assert predicted - (1 << 20) <= used <= predicted + (96 << 20), (used, predicted)
+    op.close()

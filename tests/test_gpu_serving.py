@@ -127,3 +127,29 @@ def test_concurrent_buckets_sharing_a_model_match_alone(lib, dev):
         assert int(it[0]) == ia == 24 and int(st[0]) == sa
         assert np.array_equal(x.cpu().numpy(), xa)
         assert float(rr[0]) == ra
+
+
+def test_server_delivers_each_result_as_solved_alone(lib, dev):
+    """The request loop copies every retired solve's iterate into its request's output
+    tensor: each delivered result equals the same request solved alone in its own bucket,
+    bit for bit, although the requests shared buckets of two sizes and overlapped in time."""
+    import torch
+    from paper_2402_05598_gb300 import serve as S
+    C, M = 32, 12
+    desc = I.ModelDesc(width=C, layers=4, modes=M, proj_width=C)
+    w = torch.from_numpy(I.xavier_weights(desc, 6)).to(dev)
+    model = lib.Model(lib.make_desc(C, 4, M, C), w)
+    reqs = []
+    for i in range(6):
+        N = (64, 128)[i % 2]
+        k, f, x0 = dev_arrays(N, 3400 + i, dev)
+        out = torch.full((N, N), float("nan"), dtype=torch.float64, device=dev)
+        reqs.append(S.Request(i, 0.002 * i, N, k, f, x0, out=out))
+    srv = S.Server(model, {64: 2, 128: 2}, prec="bf16", max_iter=24, iters_per_step=8)
+    stats = srv.run(reqs, S.ServeStats())
+    srv.close()
+    assert stats.completed == len(reqs)
+    for i, r in enumerate(reqs):
+        xa, ia, ra, sa = run_alone(lib, dev, model, r.N, 3400 + i, "bf16", 3, max_iter=24)
+        assert r.iters == ia == 24 and r.status == sa == lib.FCGNO_ENOCONV
+        assert np.array_equal(r.out.cpu().numpy(), xa), i

@@ -13,6 +13,8 @@ import pytest
 from oracle import fcgno_oracle as O
 from paper_2402_05598_gb300 import inputs as I
 
+import closed_forms as CF
+
 
 def rel(a, b):
     return float(np.linalg.norm(np.ravel(a) - np.ravel(b)) / max(np.linalg.norm(np.ravel(b)), 1e-300))
@@ -26,6 +28,30 @@ def test_stencil_equals_dense_matrix(N):
     A = O.dense_A(k)
     u = rng.standard_normal((N, N))
     assert rel(O.apply_A(k, u).ravel(), A @ u.ravel()) < 1e-14
+
+
+@pytest.mark.parametrize("N,axis,j", [(12, 1, 2), (12, 0, 3), (31, 1, 5), (9, 0, 1)])
+def test_layered_coefficient_flux_balance_pins_harmonic_faces(N, axis, j):
+    """Harmonic-mean faces and the boundary-face convention (Eq. (2), finite volumes), pinned
+    without restating the formula: on a coefficient layered along one axis, a grid function
+    that carries a constant flux through series half-cell resistances has a closed-form
+    A u at every node (tests/closed_forms.py). An arithmetic-mean face, a boundary face with
+    a halved or doubled coefficient, a missing 1/h^2, or k taken from the wrong neighbour on
+    the cross faces each breaks the balance."""
+    k, u, Au = CF.layered_flux_field(N, axis=axis, j=j, seed=N + axis)
+    got = O.apply_A(k, u)
+    assert np.max(np.abs(got - Au)) <= 1e-12 * np.max(np.abs(Au))
+    # the dense matrix (assembled separately, row by row) obeys the same balance
+    assert np.max(np.abs((O.dense_A(k) @ u.ravel()).reshape(N, N) - Au)) <= 1e-12 * np.max(np.abs(Au))
+
+
+def test_layered_flux_balance_rejects_an_arithmetic_mean_face(monkeypatch):
+    """The layered-field pin has teeth: the same oracle with the arithmetic mean planted in
+    place of the harmonic one fails it (at every node next to a face between unequal k)."""
+    k, u, Au = CF.layered_flux_field(12, axis=1, j=2, seed=13)
+    monkeypatch.setattr(O, "_harmonic", lambda a, b: 0.5 * (a + b))
+    got = O.apply_A(k, u)
+    assert np.max(np.abs(got - Au)) > 1e-3 * np.max(np.abs(Au))
 
 
 @pytest.mark.parametrize("N", [4, 7])

@@ -19,6 +19,9 @@ class FakeStream:
     def wait_stream(self, other):
         pass
 
+    def synchronize(self):
+        pass
+
 
 class FakeEvent:
     def record(self, stream):
@@ -56,6 +59,8 @@ class FakeBucket:
         assert self.state[slot] == "free", "slot admitted twice"
         self.state[slot] = "run"
         self.need[slot], self.it[slot] = int(k), 0
+        self.owner = getattr(self, "owner", [None] * self.cap)
+        self.owner[slot] = x0
         FakeBucket.log.append(("admit", self.N, int(f)))
 
     def step(self, stream=None):
@@ -72,6 +77,9 @@ class FakeBucket:
 
     def take(self, slot, x_out=None, stream=None):
         assert self.state[slot] == "done"
+        # a retired solve's iterate is delivered into its own request's buffer (x0 here)
+        assert x_out is not None and x_out == self.owner[slot]
+        FakeBucket.log.append(("take", self.N, x_out[1]))
         self.state[slot] = "free"
 
     def close(self):
@@ -86,7 +94,7 @@ def test_serve_loop_admits_retires_and_completes_each_request_once(S):
     for i in range(60):
         N = int(rng.choice(sizes))
         need = int(rng.integers(1, 40)) if i != 7 else 10_000  # one request runs into max_iter
-        reqs.append(S.Request(i, 0.0002 * i, N, need, i, None))
+        reqs.append(S.Request(i, 0.0002 * i, N, need, i, ("x0", i)))
     srv = S.Server(None, {64: 3, 128: 2}, prec="bf16", max_iter=200, iters_per_step=8,
                    bucket_factory=FakeBucket, cuda=FakeCuda)
     stats = srv.run(reqs, S.ServeStats())
@@ -96,6 +104,9 @@ def test_serve_loop_admits_retires_and_completes_each_request_once(S):
         assert r.done >= r.arrival and r.status in (0, 4)
         assert r.iters == (min(r.k, 200) if r.status == 0 else 200)
     assert reqs[7].status == 4
+    # every request's result was delivered exactly once
+    taken = sorted(rid for kind, n, rid in FakeBucket.log if kind == "take")
+    assert taken == list(range(len(reqs)))
     # first come, first served within each grid size
     for N in sizes:
         order = [rid for kind, n, rid in FakeBucket.log if kind == "admit" and n == N]

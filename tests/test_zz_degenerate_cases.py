@@ -4,7 +4,8 @@ FCGNO_EINVAL before any launch and leave their outputs untouched; the CUDA-core
 preconditioners take the same shape. A preconditioner that returns zero makes
 (p_0, A p_0) = 0: every instance stops at iteration 0 with FCGNO_EBREAKDOWN (Algorithm 1
 cannot take a step), as the oracle does, and x is left as it was. A NaN in one instance's
-input fails that instance alone."""
+input fails that instance alone. A bounded device wait that runs out is reported as
+FCGNO_ETIMEOUT and leaves the context usable."""
 import numpy as np
 import pytest
 
@@ -93,3 +94,34 @@ def test_a_nan_input_fails_only_its_own_instance(lib, dev, prec):
     for b in (0, 2):
         assert info3[b]["iters"] == info_clean[b]["iters"] and info3[b]["status"] == info_clean[b]["status"]
         assert np.array_equal(xs3[b], xs_clean[b])
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("limit", [2e-6, 5e-5])
+def test_bounded_wait_gives_up_and_the_context_stays_usable(lib, dev, limit):
+    """Failure detection without a GPU fault: a wait (the tensor-core kernels' bounded mbarrier
+    wait) on a barrier phase that nothing completes gives up after the caller's limit of a few
+    microseconds, and the call reports FCGNO_ETIMEOUT through the operator's timeout flag. The
+    flag is cleared by that report, and a BF16 solve on the same operator and context then
+    matches the FP64 oracle's preconditioner and iterate as in the parity tests."""
+    import torch
+    from oracle import fcgno_oracle as O
+    from test_gpu_parity import ELEM_TOL, batch, elem_check, model_pair, rel, to_dev
+    N, B = 32, 2
+    k, f = batch(N, B, 9300)
+    desc, P, model, _w = model_pair(lib, dev, 16, 8)
+    op = lib.Operator(to_dev(k, dev))
+    assert lib.wait_selftest(op, limit) == lib.FCGNO_ETIMEOUT
+    assert "bounded device wait" in lib.last_error()
+    z = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    lib.precond_apply(model, op, to_dev(f, dev), z, prec="bf16")
+    x = torch.zeros((B, N, N), dtype=torch.float64, device=dev)
+    info = lib.solve(op, model, to_dev(f, dev), x, m_max=1, max_iter=4, fixed_iters=True, prec="fp64")
+    zs, xs = z.cpu().numpy(), x.cpu().numpy()
+    for b in range(B):
+        ref = O.no_forward(P, desc, f[b], np.log(k[b]))
+        assert rel(zs[b], ref) < 2e-2
+        elem_check(zs[b], ref, ELEM_TOL["bf16"], ("after time-out", b))
+        it = O.fcg(lambda u: O.apply_A(k[b], u), lambda r: O.no_forward(P, desc, r, np.log(k[b])), f[b],
+                   np.zeros((N, N)), 1, 4)
+        assert info[b]["status"] == lib.FCGNO_OK and rel(xs[b], it["u"]) < 1e-10
