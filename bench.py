@@ -4,10 +4,16 @@ Workload (the training-plus-solve configuration on a 64 x 64 grid): 256 held-out
 instances (seeds 10000 + 256*rank + i), k = exp(GRF(length 0.1, sigma 1)), f iid N(0, 1),
 u_0 iid N(0, 1) (Algorithm 1), FNO preconditioner of width 32, 4 Fourier layers, 12 x 12
 modes, trained in the setup phase with the energy-norm loss on Krylov vectors harvested
-from CG on seeded training instances. One step = one batched solve of all 256 instances to
-||r_i|| <= 1e-6 ||r_0|| (truncation m = 1) with the BF16 tensor-core preconditioner and the
-FP64 Krylov loop. Inputs are resident in HBM when a timed step starts; L2 is flushed
-(256 MB write) between timed steps.
+from CG on 512 seeded training instances. One step = assembling the batch's operator from k
+(fcgno_reassemble) and one batched solve of all 256 instances to ||r_i|| <= 1e-6 ||r_0||
+(truncation m = 5) with the BF16 tensor-core preconditioner and the FP64 Krylov loop. Inputs
+are resident in HBM when a timed step starts; L2 is flushed (256 MB write) between timed
+steps. The timed steps run untraced; the roofline comes from a traced copy of the same step.
+
+Beside the headline: m = 1; the all-FP64 GPU FCG-NO, CG and Jacobi(4)-PCG on the same 256
+instances (CUDA events, same protocol); the resolution-transfer configuration (128..512 grids,
+sigma in {0.5, 1, 2}); the large single solves (1024 x 1024 x 8, 2048 x 2048 x 2 to 1e-8); the
+serving stream; the end-to-end call on host buffers; the FP64 CPU oracle on a bounded sample.
 
 --impl reference times the FP64 CPU oracle on a bounded sample of the same workload.
 """
@@ -94,11 +100,11 @@ class ClockSampler:
 # --------------------------------------------------------------------------------------- oracle
 def _oracle_worker(args):
     """One instance of the workload solved by the FP64 CPU oracle (runs in a spawned process)."""
-    N, seed, blob, m_max, max_iter, fixed_iters = args
+    N, seed, blob, m_max, max_iter, fixed_iters, out_scale = args
     os.environ.setdefault("OPENBLAS_NUM_THREADS", "1")
     from oracle import fcgno_oracle as O
     from paper_2402_05598_gb300 import inputs as I
-    desc = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=MODES, proj_width=WIDTH)
+    desc = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=MODES, proj_width=WIDTH, output_scale=out_scale)
     P = O.unpack_weights(blob, desc)
     k, f = I.make_problem(N, seed)
     u0 = np.random.default_rng(seed + 777).standard_normal((N, N))
@@ -114,7 +120,7 @@ def workload_name(m: int) -> str:
             f"FNO width {WIDTH}, {LAYERS} layers, {MODES}x{MODES} modes, m={m}, tol {TOL}")
 
 
-def oracle_sample(blob: np.ndarray, n_inst: int, iters: int, cores: int, m_max: int = 5):
+def oracle_sample(blob: np.ndarray, n_inst: int, iters: int, cores: int, m_max: int = 5, out_scale: int = 1):
     """Times the oracle FCG-NO on n_inst instances, `iters` fixed iterations each, in a pool of
     `cores` spawned single-threaded processes. Returns (wall seconds, total iterations)."""
     import multiprocessing as mp
@@ -123,7 +129,7 @@ def oracle_sample(blob: np.ndarray, n_inst: int, iters: int, cores: int, m_max: 
     for k in env_old:
         os.environ[k] = "1"
     try:
-        jobs = [(N_GRID, 10000 + i, blob, m_max, iters, True) for i in range(n_inst)]
+        jobs = [(N_GRID, 10000 + i, blob, m_max, iters, True, out_scale) for i in range(n_inst)]
         t = time.perf_counter()
         with ctx.Pool(processes=cores) as pool:
             res = pool.map(_oracle_worker, jobs)
@@ -251,49 +257,49 @@ SERVE_SIZES = {64: 0.40, 128: 0.25, 256: 0.20, 512: 0.10, 1024: 0.05}
 SERVE_SIGMAS = (0.5, 1.0, 2.0)
 
 
-def run_serving(args, model, desc_np, dev, rate, n_req, pool_per_key=4, budget_gb=80.0):
+def run_serving(args, model, desc_np, dev, rate, n_req, budget_gb=80.0):
     """Serving stream of the configured mix: exponential inter-arrival times (mean 1/rate,
     seed 5), grid sizes drawn with the configured probabilities, sigma uniform in
-    {0.5, 1, 2}, ell = 0.1, f iid N(0,1), u_0 iid N(0,1); problems come from a seeded pool of
-    `pool_per_key` instances per (size, sigma)."""
+    {0.5, 1, 2}, ell = 0.1; every request has its own problem (k, f iid N(0,1), u_0 iid
+    N(0,1), seed 50000 + request index), generated and made resident before the run. Bucket
+    capacities split the HBM budget in proportion to each size's share of the offered
+    unknowns. Each request's solution is delivered into its own output tensor."""
     import torch
     from paper_2402_05598_gb300 import fcgno as F
     from paper_2402_05598_gb300 import inputs as I
     from paper_2402_05598_gb300 import serve as S
     rng = np.random.default_rng(5)
-    pool = {}
-    for N in SERVE_SIZES:
-        for si, sg in enumerate(SERVE_SIGMAS):
-            for j in range(pool_per_key):
-                seed = 50000 + 1000 * si + 100 * int(np.log2(N)) + j
-                kk, ff = I.make_problem(N, seed, sigma=sg, ell=0.1)
-                x0 = np.random.default_rng(seed + 777).standard_normal((N, N))
-                pool[(N, si, j)] = tuple(torch.from_numpy(a).to(dev) for a in (kk, ff, x0))
     sizes = list(SERVE_SIZES)
     probs = np.array([SERVE_SIZES[N] for N in sizes])
     gaps = rng.exponential(1.0 / rate, n_req)
     arrivals = np.cumsum(gaps) - gaps[0]
     Ns = rng.choice(sizes, size=n_req, p=probs / probs.sum())
     sis = rng.integers(0, len(SERVE_SIGMAS), n_req)
-    js = rng.integers(0, pool_per_key, n_req)
-    reqs = [S.Request(i, float(arrivals[i]), int(Ns[i]), *pool[(int(Ns[i]), int(sis[i]), int(js[i]))])
-            for i in range(n_req)]
+    t_gen = time.perf_counter()
+    reqs = []
+    for i in range(n_req):
+        N, sg = int(Ns[i]), SERVE_SIGMAS[int(sis[i])]
+        kk, ff = I.make_problem(N, 50000 + i, sigma=sg, ell=0.1)
+        x0 = np.random.default_rng(50000 + i + 777).standard_normal((N, N))
+        kd, fd, xd = (torch.from_numpy(a).to(dev) for a in (kk, ff, x0))
+        reqs.append(S.Request(i, float(arrivals[i]), N, kd, fd, xd, out=torch.empty_like(xd)))
+    t_gen = time.perf_counter() - t_gen
     m = args.serve_m
-    caps = S.plan_capacities(SERVE_SIZES, int(budget_gb * 2**30), m, F.make_desc(WIDTH, LAYERS, MODES, WIDTH),
-                             args.prec, max_slots=64)
+    mdesc = F.make_desc(WIDTH, LAYERS, MODES, WIDTH, output_scale=args.output_scale)
+    caps = S.plan_capacities(SERVE_SIZES, int(budget_gb * 2**30), m, mdesc, args.prec, max_slots=1 << 16)
     srv = S.Server(model, caps, prec=args.prec, m_max=m, tol=TOL, max_iter=args.max_iter, iters_per_step=8)
     # warm every bucket once (first steps run eagerly and allocate), outside the measurement
-    warm = [S.Request(-1, 0.0, N, *pool[(N, 0, 0)]) for N in sizes]
+    warm = [S.Request(-1, 0.0, N, *(torch.from_numpy(a).to(dev) for a in (*I.make_problem(N, 1), np.zeros((N, N)))))
+            for N in sizes]
     srv.run(warm, S.ServeStats())
     stats = S.ServeStats(offered_rate=rate)
-    stats.bucket_bytes = sum(cap * S.slot_bytes(N, m, F.make_desc(WIDTH, LAYERS, MODES, WIDTH), args.prec)
-                             for N, cap in caps.items())
+    stats.bucket_bytes = sum(cap * S.slot_bytes(N, m, mdesc, args.prec) for N, cap in caps.items())
     srv.run(reqs, stats)
     srv.close()
     out = stats.summary()
     out.update({"capacities": {str(N): c for N, c in caps.items()}, "budget_gb": budget_gb,
                 "sizes": {str(N): p for N, p in SERVE_SIZES.items()}, "tol": TOL, "m": m,
-                "max_iter": args.max_iter,
+                "max_iter": args.max_iter, "problem_generation_s": round(t_gen, 1),
                 "iterations_mean_by_size": {str(N): float(np.mean([r.iters for r in reqs if r.N == N] or [0]))
                                             for N in sizes},
                 # requests that reached the tolerance, per grid size and coefficient contrast
@@ -303,6 +309,192 @@ def run_serving(args, model, desc_np, dev, rate, n_req, pool_per_key=4, budget_g
                                                               if r.N == N and SERVE_SIGMAS[s_] == sg)]
                                             for N in sizes for sg in SERVE_SIGMAS}})
     return out
+
+
+TRANSFER_SIZES = (128, 256, 512)
+TRANSFER_SIGMAS = (0.5, 1.0, 2.0)
+
+
+def run_transfer(args, model, dev, flush, stream):
+    """Resolution transfer: the 64 x 64-trained preconditioner at N in {128, 256, 512}, 64
+    instances per (N, sigma), sigma in {0.5, 1, 2}, length 0.1, f and u_0 iid N(0, 1), tol 1e-6,
+    truncation m. Per cell: the BF16 preconditioner with the FP64 Krylov loop on all 64
+    instances; the all-FP64 FCG-NO (CUDA-core FP64 preconditioner, same weights) and the BF16
+    path on the first `fp64_instances` of them (like for like); Jacobi(4)-PCG on all 64. Each
+    timed with CUDA events after a warm-up solve."""
+    import torch
+    from paper_2402_05598_gb300 import fcgno as F
+    from paper_2402_05598_gb300 import inputs as I
+    out = {}
+    for N in TRANSFER_SIZES:
+        for si, sg in enumerate(TRANSFER_SIGMAS):
+            seeds = range(20000 + 1000 * si + 100 * int(np.log2(N)), 20000 + 1000 * si + 100 * int(np.log2(N)) + 64)
+            k_np, f_np = I.make_batch(N, seeds, sg, 0.1)
+            u0_np = np.stack([np.random.default_rng(s_ + 777).standard_normal((N, N)) for s_ in seeds])
+            cell = {}
+            for label, nb in (("all", 64), ("sub", args.transfer_fp64_instances)):
+                k = torch.from_numpy(np.ascontiguousarray(k_np[:nb])).to(dev)
+                f = torch.from_numpy(np.ascontiguousarray(f_np[:nb])).to(dev)
+                u0 = torch.from_numpy(np.ascontiguousarray(u0_np[:nb])).to(dev)
+                op = F.Operator(k)
+                x = torch.empty_like(u0)
+
+                def step(prec, cap, jac=0):
+                    def fn():
+                        op.reassemble(k)
+                        x.copy_(u0)
+                        if jac:
+                            return F.solve_jacobi(op, jac, f, x, tol=TOL, m_max=1, max_iter=cap, check_every=32)
+                        return F.solve(op, model, f, x, tol=TOL, m_max=args.m, max_iter=cap, prec=prec,
+                                       check_every=8 if prec == "bf16" else 16)
+                    return fn
+
+                if label == "all":
+                    ms, res = timed_steps(step("bf16", args.transfer_max_iter), 1, 1, flush, stream)
+                    cell["bf16"] = solve_summary(ms, res, F)
+                    ms, res = timed_steps(step("fp64", 20000, jac=4), 1, 1, flush, stream)
+                    cell["jacobi4_pcg"] = solve_summary(ms, res, F)
+                else:
+                    ms, res = timed_steps(step("bf16", args.transfer_max_iter), 1, 1, flush, stream)
+                    cell["bf16_subset"] = solve_summary(ms, res, F)
+                    cap = int(1.3 * cell["bf16_subset"]["iterations"]["max"]) + 16
+                    ms, res = timed_steps(step("fp64", cap), 1, 0, flush, stream)
+                    cell["fp64_no_subset"] = dict(solve_summary(ms, res, F), max_iter=cap)
+                del op
+            out[f"{N}/{sg}"] = cell
+    return out
+
+
+LARGE_CASES = ((1024, 8), (2048, 2))
+
+
+def run_large(args, dev, flush, stream):
+    """Large single solves: 1024 x 1024 x 8 and 2048 x 2048 x 2, k = exp(GRF(length 0.05,
+    sigma 2)), f and u_0 iid N(0, 1), tol 1e-8, m = 5. The model (width 32, 16 x 16 modes) is
+    trained at 64 x 64 on the same coefficient family, then fine-tuned at 1024 x 1024 on Krylov
+    vectors of that grid, where the training step rebuilds its pre-activations (activation
+    checkpointing). Reports the fine-tuning steps and, per grid, the BF16 FCG-NO solve and
+    Jacobi(4)-PCG on the same instances (CUDA events, one warm-up each)."""
+    import torch
+    from paper_2402_05598_gb300 import fcgno as F
+    from paper_2402_05598_gb300 import inputs as I
+    from paper_2402_05598_gb300 import train as T
+    M = 16
+    desc = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=M, proj_width=WIDTH, output_scale=args.output_scale)
+    blob = torch.from_numpy(I.xavier_weights(desc, 1)).to(dev)
+    model = F.Model(F.make_desc(WIDTH, LAYERS, M, WIDTH, output_scale=args.output_scale), blob)
+    tr = T.train(model, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3,
+                 steps=args.large_train_steps, sigma=2.0, ell=0.05)
+    out = {"model": {"modes": M, "train_steps_64": tr.steps, "train_seconds_64": round(tr.seconds, 2)}}
+    # fine-tuning at 1024 x 1024 (8 instances): Krylov vectors of CG from u_0 ~ N(0, 1), u* from
+    # Jacobi(4)-PCG to 1e-10; Adam steps on Eq. (11) with recomputed pre-activations
+    Nf, Bf = LARGE_CASES[0]
+    seeds = range(41000, 41000 + Bf)
+    k_np, f_np = I.make_batch(Nf, seeds, 2.0, 0.05)
+    kf = torch.from_numpy(k_np).to(dev)
+    ff = torch.from_numpy(f_np).to(dev)
+    opf = F.Operator(kf)
+    ustar = torch.zeros_like(ff)
+    F.solve_jacobi(opf, 4, ff, ustar, tol=1e-10, m_max=1, max_iter=50000, check_every=64)
+    x0 = torch.from_numpy(np.random.default_rng(41).standard_normal((Bf, Nf, Nf))).to(dev)
+    K = args.large_finetune_k
+    r_out = torch.empty((K, Bf, Nf, Nf), dtype=torch.float64, device=dev)
+    e_out = torch.empty_like(r_out)
+    F.krylov_harvest(opf, ff, x0, ustar, K, r_out, e_out)
+    model.set_train_recompute("auto")
+    opt = torch.optim.Adam([blob.requires_grad_(True)], lr=args.large_finetune_lr)
+    losses = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for it in range(args.large_finetune_steps):
+        i = it % K
+        opt.zero_grad(set_to_none=True)
+        loss = T.preconditioner_loss(model, opf, r_out[i].contiguous(), e_out[i].contiguous(), prec="fp32")
+        loss.backward()
+        opt.step()
+        losses.append(round(float(loss.item()), 4))
+    blob.requires_grad_(False)
+    blob.grad = None
+    model.sync()
+    torch.cuda.synchronize()
+    out["finetune"] = {"grid": Nf, "instances": Bf, "krylov_K": K, "steps": args.large_finetune_steps,
+                       "seconds": round(time.perf_counter() - t0, 2), "losses": losses,
+                       "recompute": "auto (pre-activations rebuilt in the backward above 2 GiB)"}
+    del opf, r_out, e_out, ustar
+    for N, B in LARGE_CASES:
+        seeds = range(42000 + N, 42000 + N + B)
+        k_np, f_np = I.make_batch(N, seeds, 2.0, 0.05)
+        u0_np = np.stack([np.random.default_rng(s_ + 777).standard_normal((N, N)) for s_ in seeds])
+        k = torch.from_numpy(k_np).to(dev)
+        f = torch.from_numpy(f_np).to(dev)
+        u0 = torch.from_numpy(u0_np).to(dev)
+        op = F.Operator(k)
+        x = torch.empty_like(u0)
+
+        def bf16_step():
+            op.reassemble(k)
+            x.copy_(u0)
+            return F.solve(op, model, f, x, tol=1e-8, m_max=5, max_iter=args.large_max_iter, prec="bf16",
+                           check_every=16)
+
+        def jac_step():
+            op.reassemble(k)
+            x.copy_(u0)
+            return F.solve_jacobi(op, 4, f, x, tol=1e-8, m_max=1, max_iter=50000, check_every=64)
+
+        cell = {}
+        ms, res = timed_steps(bf16_step, 1, 1, flush, stream)
+        cell["bf16"] = solve_summary(ms, res, F)
+        # the true residual of the returned iterates, from the library's own stencil
+        Ax = torch.empty_like(x)
+        op.apply(x, Ax)
+        r_true = (f - Ax).flatten(1).norm(dim=1) / (f - _apply(op, u0)).flatten(1).norm(dim=1)
+        cell["bf16"]["true_relres_max"] = float(r_true.max())
+        ms, res = timed_steps(jac_step, 1, 1, flush, stream)
+        cell["jacobi4_pcg"] = solve_summary(ms, res, F)
+        out[f"{N}x{B}"] = cell
+        del op
+    return out
+
+
+def _apply(op, u):
+    import torch
+    y = torch.empty_like(u)
+    op.apply(u, y)
+    return y
+
+
+def timed_steps(fn, steps, warmup, flush, stream):
+    """Runs fn() `warmup` times, then `steps` times with L2 flushed before each, timing each
+    call with CUDA events on `stream`. Returns (per-step ms, per-step results)."""
+    import torch
+    for _ in range(warmup):
+        fn()
+    torch.cuda.synchronize()
+    ms, res = [], []
+    for s_ in range(steps):
+        flush.fill_(float(s_))
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res.append(fn())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    return ms, res
+
+
+def solve_summary(ms, infos, F):
+    """solves/s (converged solves only), ms per step, iteration and residual statistics of the
+    timed solves."""
+    its = [i["iters"] for inf in infos for i in inf]
+    rr = [i["relres"] for inf in infos for i in inf]
+    conv = sum(1 for inf in infos for i in inf if i["status"] == F.FCGNO_OK)
+    return {"value": conv / (sum(ms) / 1000.0), "unit": UNIT, "ms_per_step": float(np.mean(ms)), "steps": len(ms),
+            "instances": len(infos[0]), "iterations": {"mean": float(np.mean(its)), "max": int(max(its))},
+            "converged": conv, "solves": len(its), "relres_max": float(max(rr)),
+            "relres_median": float(np.median(rr))}
 
 
 def dist_env():
@@ -323,7 +515,7 @@ def run_reference(args):
     iters = args.ref_iters
     vals = []
     for s in range(args.warmup + args.steps):
-        wall, tot_it = oracle_sample(blob, cores, iters, cores, args.m)
+        wall, tot_it = oracle_sample(blob, cores, iters, cores, args.m, args.output_scale)
         if s >= args.warmup:
             vals.append((wall, tot_it))
     wall = sum(v[0] for v in vals)
@@ -360,11 +552,28 @@ def main():
                     help="FCG-NO iterations per oracle solve in the reference arm (the GPU arm measures a mean "
                          "of about 20 at m = 5 on this workload)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
+    ap.add_argument("--transfer", type=int, default=1, help="run the resolution-transfer leg (128..512 grids)")
+    ap.add_argument("--large", type=int, default=1, help="run the large-solve leg (1024^2 x 8, 2048^2 x 2, tol 1e-8)")
+    ap.add_argument("--large-max-iter", type=int, default=3000)
+    ap.add_argument("--large-train-steps", type=int, default=4000)
+    ap.add_argument("--large-finetune-steps", type=int, default=4)
+    ap.add_argument("--large-finetune-k", type=int, default=4)
+    ap.add_argument("--large-finetune-lr", type=float, default=2e-4)
+    ap.add_argument("--output-scale", type=int, default=1, choices=[0, 1],
+                    help="model output scale: 0 = h^2 rms(r), 1 = h^2 rms(r) / k")
+    ap.add_argument("--transfer-max-iter", type=int, default=2000)
+    ap.add_argument("--transfer-fp64-instances", type=int, default=4,
+                    help="instances per transfer cell solved by the all-FP64 FCG-NO (and the BF16 path, like for like)")
+    ap.add_argument("--comparators", type=int, default=1,
+                    help="time the all-FP64 FCG-NO, CG and Jacobi(4)-PCG on the headline's instances")
     ap.add_argument("--e2e-steps", type=int, default=2)
-    ap.add_argument("--serve-requests", type=int, default=2000,
+    ap.add_argument("--serve-requests", type=int, default=10000,
                     help="requests in the serving stream (0 = skip the serving measurement)")
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate of the serving stream (1/s)")
     ap.add_argument("--serve-m", type=int, default=1, help="truncation m of the served solves")
+    ap.add_argument("--serve-requests-light", type=int, default=500, help="requests of the lighter stream")
+    ap.add_argument("--mix-train-steps", type=int, default=6000)
+    ap.add_argument("--mix-train-instances", type=int, default=768)
     ap.add_argument("--serve-rate-light", type=float, default=50.0,
                     help="arrival rate of a second, lighter serving stream (0 = skip)")
     ap.add_argument("--profile", type=int, default=0,
@@ -391,9 +600,9 @@ def main():
     from paper_2402_05598_gb300 import replicas as R
 
     # ---- setup: model, training (untimed)
-    desc_np = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=MODES, proj_width=WIDTH)
+    desc_np = I.ModelDesc(width=WIDTH, layers=LAYERS, modes=MODES, proj_width=WIDTH, output_scale=args.output_scale)
     blob = torch.from_numpy(I.xavier_weights(desc_np, 0)).to(dev)
-    model = F.Model(F.make_desc(WIDTH, LAYERS, MODES, WIDTH), blob)
+    model = F.Model(F.make_desc(WIDTH, LAYERS, MODES, WIDTH, output_scale=args.output_scale), blob)
     tr = None
     if args.profile:
         # short fixed-iteration solves with every instance active (the ncu capture workload)
@@ -426,10 +635,12 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream()
 
-    def solve_once():
+    def solve_once(m=None, prec=None, model_=model):
+        # one step: the operator assembled from k (in place), u_0 copied in, the batched solve
+        op.reassemble(k)
         x.copy_(u0)
-        return F.solve(op, model, f, x, tol=TOL, m_max=args.m, max_iter=args.max_iter, prec=args.prec,
-                       check_every=8)
+        return F.solve(op, model_, f, x, tol=TOL, m_max=args.m if m is None else m, max_iter=args.max_iter,
+                       prec=args.prec if prec is None else prec, check_every=8)
 
     for _ in range(args.warmup):
         info = solve_once()
@@ -437,29 +648,13 @@ def main():
     if world > 1:
         torch.distributed.barrier()
 
-    # ---- timed region
+    # ---- timed region (untraced)
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.4)
-    F.trace_set("tc_synthesis")
-    F.trace_collect()
     launches0 = F.launch_count()
-    step_ms = []
-    infos = []
-    for s in range(args.steps):
-        flush.fill_(float(s))
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        infos.append(solve_once())
-        e1.record(stream)
-        torch.cuda.synchronize()
-        step_ms.append(e0.elapsed_time(e1))
+    step_ms, infos = timed_steps(solve_once, args.steps, 0, flush, stream)
     launches = F.launch_count() - launches0
-    syn_ms, syn_launches = F.trace_collect()
-    trace_note = F.last_error() if "trace" in F.last_error() else ""
-    F.trace_set("")
     clk = clocks.stop()
     solved = sum(sum(1 for i in inf if i["status"] == F.FCGNO_OK) for inf in infos)
     total_ms, solved_all = R.reduce_timing(float(sum(step_ms)), solved, dev)
@@ -467,26 +662,21 @@ def main():
     # only solves that reached the tolerance count (capped instances are reported, not counted)
     value = solved_all / (total_ms / 1000.0)
 
+    # ---- the synthesis launches of the same step, traced with CUDA events on their stream
+    F.trace_set("tc_synthesis")
+    F.trace_collect()
+    trace_steps = 2
+    for s_ in range(trace_steps):
+        flush.fill_(float(s_))
+        solve_once()
+    syn_ms, syn_launches = F.trace_collect()
+    trace_note = F.last_error() if "trace" in F.last_error() else ""
+    F.trace_set("")
+
     # ---- the other configured truncation, same protocol (fewer timed steps)
     alt = None
     if args.m_alt and args.m_alt != args.m:
-        def solve_alt():
-            x.copy_(u0)
-            return F.solve(op, model, f, x, tol=TOL, m_max=args.m_alt, max_iter=args.max_iter, prec=args.prec,
-                           check_every=8)
-        for _ in range(2):
-            solve_alt()
-        alt_ms, alt_infos = [], []
-        for s_ in range(3):
-            flush.fill_(float(s_))
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            alt_infos.append(solve_alt())
-            e1.record(stream)
-            torch.cuda.synchronize()
-            alt_ms.append(e0.elapsed_time(e1))
+        alt_ms, alt_infos = timed_steps(lambda: solve_once(m=args.m_alt), 3, 2, flush, stream)
         alt_solved = sum(sum(1 for i in inf if i["status"] == F.FCGNO_OK) for inf in alt_infos)
         alt_total, alt_solved = R.reduce_timing(float(sum(alt_ms)), alt_solved, dev)
         alt_its = [i["iters"] for i in alt_infos[-1]]
@@ -507,17 +697,17 @@ def main():
         if "bf16_tflops_sustained" in peaks:
             bf16_peak, bf16_src = float(peaks["bf16_tflops_sustained"]), "measured (sustained)"
     syn_avg_ms = syn_ms / max(syn_launches, 1)
-    active_per_launch = float(sum(active)) * LAYERS * args.steps / max(syn_launches, 1)
+    active_per_launch = float(sum(active)) * LAYERS * trace_steps / max(syn_launches, 1)
     traffic = SYN_TRAFFIC_PER_INSTANCE * active_per_launch if SYN_TRAFFIC_PER_INSTANCE else None
-    achieved = alg_bytes_one * args.steps / (syn_ms / 1000.0) / 1e9 if syn_ms > 0 else None
+    achieved = alg_bytes_one * trace_steps / (syn_ms / 1000.0) / 1e9 if syn_ms > 0 else None
     # the same launches against the tensor pipe (the NO's work is dense contractions)
     syn_flops_one = synthesis_flops(active, N_GRID, WIDTH, MODES, LAYERS, WIDTH)
-    t_ach, t_frac = rate_and_frac(syn_flops_one * args.steps, syn_ms, 1e12, bf16_peak)
+    t_ach, t_frac = rate_and_frac(syn_flops_one * trace_steps, syn_ms, 1e12, bf16_peak)
     intensity = syn_flops_one / alg_bytes_one if alg_bytes_one else None
     ceiling = intensity * peak / 1e3 if intensity else None  # TFLOP/s at the measured copy peak
     tensor_roofline = {"kernel": "tc_synthesis_kernel", "bound": "tensor", "unit": "TFLOP/s", "achieved": t_ach,
                        "peak": bf16_peak, "peak_source": bf16_src, "frac": t_frac,
-                       "flops_per_launch": syn_flops_one * args.steps / max(syn_launches, 1),
+                       "flops_per_launch": syn_flops_one * trace_steps / max(syn_launches, 1),
                        "intensity_flop_per_byte": intensity, "ceiling_at_hbm_peak": ceiling,
                        "frac_of_ceiling": (t_ach / ceiling) if (t_ach and ceiling) else None,
                        "note": "the activations pass through HBM, so the HBM roof caps the tensor pipe at "
@@ -590,7 +780,7 @@ def main():
                          "peak_source": peak_src, "unit": "GB/s",
                          "frac": (achieved / peak) if achieved else None, "traffic": traffic,
                          "traffic_note": "ncu dram read+write per active instance x active instances per launch",
-                         "algorithmic_bytes_per_launch": alg_bytes_one * args.steps / max(syn_launches, 1),
+                         "algorithmic_bytes_per_launch": alg_bytes_one * trace_steps / max(syn_launches, 1),
                          "avg_launch_ms": syn_avg_ms, "launches": syn_launches,
                          "note": trace_note or None},
             "kernel_ms_one_step": shares,
@@ -598,47 +788,55 @@ def main():
             "tensor_roofline": tensor_roofline,
             "other_truncation": alt}
 
-    # ---- comparison paths on the same instances (untimed here, reported for context)
-    if rank == 0:
-        sub = 32
-        op_s = F.Operator(k[:sub].contiguous())
-        xs = u0[:sub].clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        inf64 = F.solve(op_s, model, f[:sub].contiguous(), xs, tol=TOL, m_max=args.m, max_iter=args.max_iter,
-                        prec="fp64", check_every=4)
-        torch.cuda.synchronize()
-        t64 = time.perf_counter() - t0
-        line["fp64_no"] = {"value": sub / t64, "unit": UNIT, "instances": sub,
-                           "iterations_mean": float(np.mean([i["iters"] for i in inf64]))}
-        xs = u0[:sub].clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        infcg = F.solve(op_s, None, f[:sub].contiguous(), xs, tol=TOL, m_max=1, max_iter=20000, prec="fp64",
-                        check_every=16)
-        torch.cuda.synchronize()
-        tcg = time.perf_counter() - t0
-        line["cg"] = {"value": sub / tcg, "unit": UNIT, "instances": sub,
-                      "iterations_mean": float(np.mean([i["iters"] for i in infcg]))}
+    # ---- comparison paths on the same 256 instances, same protocol (assembly + solve per step,
+    # CUDA events on the launching stream, L2 flushed before each timed step)
+    if rank == 0 and args.comparators:
+        def fp64_step():
+            return solve_once(prec="fp64")
+
+        def cg_step():
+            op.reassemble(k)
+            x.copy_(u0)
+            return F.solve(op, None, f, x, tol=TOL, m_max=1, max_iter=20000, prec="fp64", check_every=16)
+
+        def jac_step():
+            op.reassemble(k)
+            x.copy_(u0)
+            return F.solve_jacobi(op, 4, f, x, tol=TOL, m_max=1, max_iter=20000, check_every=16)
+
+        ms, res = timed_steps(fp64_step, 1, 1, flush, stream)
+        line["fp64_no"] = dict(solve_summary(ms, res, F), m=args.m, preconditioner="FP64 CUDA-core NO (same weights)")
+        ms, res = timed_steps(cg_step, 2, 1, flush, stream)
+        line["cg"] = dict(solve_summary(ms, res, F), m=1, preconditioner="identity")
         # Jacobi(4)-preconditioned CG (Eq. (15), the Jacobi column of Table 1)
-        xs = u0[:sub].clone()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        infj = F.solve_jacobi(op_s, 4, f[:sub].contiguous(), xs, tol=TOL, m_max=1, max_iter=20000, check_every=16)
-        torch.cuda.synchronize()
-        tj = time.perf_counter() - t0
-        line["jacobi4_pcg"] = {"value": sub / tj, "unit": UNIT, "instances": sub,
-                               "iterations_mean": float(np.mean([i["iters"] for i in infj])),
-                               "converged": sum(1 for i in infj if i["status"] == F.FCGNO_OK)}
+        ms, res = timed_steps(jac_step, 2, 1, flush, stream)
+        line["jacobi4_pcg"] = dict(solve_summary(ms, res, F), m=1, preconditioner="Jacobi(4), Eq. (15)")
+
+    # ---- the model served and transferred: trained at 64 x 64 on the sigma mixture the
+    # serving stream and the transfer configuration draw (0.5, 1, 2)
+    model_mix, tr_mix = None, None
+    if rank == 0 and (args.transfer or args.serve_requests > 0):
+        blob_mix = torch.from_numpy(I.xavier_weights(desc_np, 2)).to(dev)
+        model_mix = F.Model(F.make_desc(WIDTH, LAYERS, MODES, WIDTH, output_scale=args.output_scale), blob_mix)
+        tr_mix = T.train(model_mix, N_GRID, range(0, args.mix_train_instances), K=100, batch=32, lr=1e-3,
+                         steps=args.mix_train_steps, sigma=SERVE_SIGMAS)
+        line["config"]["training_mix"] = {"steps": tr_mix.steps, "batch": 32, "instances": args.mix_train_instances,
+                                          "sigmas": list(SERVE_SIGMAS), "seconds": round(tr_mix.seconds, 2)}
+    # ---- resolution transfer (128..512 grids, sigma 0.5 / 1 / 2)
+    if rank == 0 and args.transfer:
+        line["transfer"] = run_transfer(args, model_mix, dev, flush, stream)
+    # ---- large single solves (1024^2 x 8, 2048^2 x 2, sigma 2, length 0.05, tol 1e-8)
+    if rank == 0 and args.large:
+        line["large"] = run_large(args, dev, flush, stream)
 
     # ---- serving stream: continuous batching over size buckets (latency incl. queueing)
     if rank == 0 and args.serve_requests > 0:
         # the configured stream (offered load above what one GPU sustains: latency grows with
         # the queue) and a lighter stream that the GPU keeps up with
-        line["serve"] = run_serving(args, model, desc_np, dev, args.serve_rate, args.serve_requests)
+        line["serve"] = run_serving(args, model_mix, desc_np, dev, args.serve_rate, args.serve_requests)
         if args.serve_rate_light > 0:
-            line["serve_light"] = run_serving(args, model, desc_np, dev, args.serve_rate_light,
-                                              max(1, args.serve_requests // 4))
+            line["serve_light"] = run_serving(args, model_mix, desc_np, dev, args.serve_rate_light,
+                                              args.serve_requests_light)
 
     # ---- end to end through the host-buffer entry point
     kh = torch.from_numpy(k_np).pin_memory()
@@ -662,7 +860,7 @@ def main():
         it_solve = max(1, int(round(np.mean(iters))))
         # the oracle's cost per iteration does not depend on the weight values: it runs the seeded
         # initial weights (no value produced by the CUDA path enters the oracle)
-        wall, tot_it = oracle_sample(I.xavier_weights(desc_np, 0), cores, it_solve, cores, args.m)
+        wall, tot_it = oracle_sample(I.xavier_weights(desc_np, 0), cores, it_solve, cores, args.m, args.output_scale)
         line["cpu_baseline"] = {"kind": "oracle", "value": cores / wall, "unit": UNIT, "cores": cores,
                                 "cpu_model": cpu_model(), "nproc": os.cpu_count(),
                                 "sample": f"{cores} instances, {it_solve} FCG-NO iterations each (the GPU solve's "

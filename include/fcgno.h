@@ -72,13 +72,19 @@ typedef struct fcgno_model* fcgno_model_t;
 
 /* Shape of the Fourier neural operator (Appendix A: encoder, `layers` Fourier layers,
  * decoder). modes = M keeps x1-frequencies 0..M-1 and -M..-1 and x2-frequencies 0..M-1;
- * requires N >= 2M for every grid it is applied to. in_channels must be 2. */
+ * requires N >= 2M for every grid it is applied to. in_channels must be 2.
+ * output_scale chooses how the decoder's output is put back into the units of A^-1 (the
+ * paper leaves the network's scaling open): 0 multiplies it by h^2 rms(r); 1 also divides it,
+ * grid point by grid point, by the coefficient k (z = h^2 rms(r) NO(...) / k), so that the
+ * contrast of k, which the network would otherwise have to reproduce through its GELUs,
+ * enters the way it enters A^-1 at the highest frequencies (about h^2 r / (4 k)). */
 typedef struct {
-  int width;       /* C   */
-  int layers;      /* L   */
-  int modes;       /* M   */
-  int proj_width;  /* C_p */
-  int in_channels; /* 2: (r / rms(r), log k) */
+  int width;        /* C   */
+  int layers;       /* L   */
+  int modes;        /* M   */
+  int proj_width;   /* C_p */
+  int in_channels;  /* 2: (r / rms(r), log k) */
+  int output_scale; /* 0: h^2 rms(r); 1: h^2 rms(r) / k */
 } fcgno_model_desc;
 
 typedef struct {
@@ -100,6 +106,12 @@ typedef struct {
  * coefficients and log k on the device and returns a handle that owns them.
  * Errors: EINVAL if N < 2, batch < 1, k or out NULL; ENOMEM; ECUDA. */
 fcgno_status fcgno_assemble(int N, int batch, const double* k, void* stream, fcgno_op_t* out);
+/* Re-assembles an existing operator in place from new coefficient fields k ([batch][N][N]
+ * with the operator's N and batch; k > 0): same arithmetic as fcgno_assemble, no allocation,
+ * asynchronous on `stream`. The operator's solver workspace, captured graphs and 16-bit
+ * activations stay valid, so a batch of new problems of the same shape reuses them.
+ * Errors: EINVAL for a NULL op or k; ECUDA. */
+fcgno_status fcgno_reassemble(fcgno_op_t op, const double* k, void* stream);
 /* Releases the handle and everything it owns (solver workspace, graphs, the 16-bit
  * preconditioner's activations) with cudaFree, which waits for work in flight on the
  * device. NULL is a no-op. */
@@ -128,7 +140,8 @@ fcgno_status fcgno_model_sync(fcgno_model_t model, void* stream);
 fcgno_status fcgno_model_destroy(fcgno_model_t model);
 
 /* z = NO(r, log k) for every instance of op (Algorithm 1, w_i = B(r_i); Appendix A):
- * z = h^2 rms(r) * decoder(Fourier layers(encoder(r / rms(r), log k))), z = 0 where r = 0
+ * z = s * decoder(Fourier layers(encoder(r / rms(r), log k))), z = 0 where r = 0, with
+ * s = h^2 rms(r) (output_scale 0) or h^2 rms(r) / k at each grid point (output_scale 1)
  * (h = 1/(N+1); the h^2 factor gives the output the units of A^-1).
  * r, z: [batch][N][N]. prec selects the arithmetic (FP64, FP32, BF16, FP16).
  * Errors: EINVAL for a NULL argument, N < 2*modes, an unknown precision or a shape the
@@ -257,6 +270,51 @@ fcgno_status fcgno_bucket_step(fcgno_bucket_t bucket, void* stream);
 fcgno_status fcgno_bucket_poll(fcgno_bucket_t bucket, int32_t* status, int32_t* iters, double* relres, void* stream);
 fcgno_status fcgno_bucket_take(fcgno_bucket_t bucket, int slot, double* x_out, void* stream);
 fcgno_status fcgno_bucket_destroy(fcgno_bucket_t bucket);
+
+/* Device-driven serving of a bucket (continuous batching without a host poll per step). After
+ * fcgno_bucket_serve_enable, the host only appends requests (fcgno_bucket_enqueue), launches
+ * steps (fcgno_bucket_step) and collects results (fcgno_bucket_results); admission and
+ * retirement run on the device at the start of EVERY iteration of every step:
+ *  - a slot whose solve stopped (converged, breakdown, or iters >= max_iter) has its iterate
+ *    copied into its request's x_out, then its result record is published and the slot is
+ *    freed (it takes a new request from the next iteration on);
+ *  - every free slot takes the next queued request (first in, first out): its operator is
+ *    assembled from k, f and x0 are copied in and r_0 = f - A x0 is formed; the solve runs from
+ *    that same iteration on.
+ * The queue and the result ring live in pinned host memory mapped into the device's address
+ * space, so neither side waits for the other: enqueue and results are host-only calls (no
+ * CUDA call, no synchronisation) that any number of steps in flight may overlap. A request's
+ * arithmetic is that of fcgno_bucket_admit and the slot's own solve, so its result does not
+ * depend on the other requests, the slot it gets or when it is admitted.
+ *  - serve_enable: allocates a queue of `queue_capacity` requests and a ring of
+ *    `result_capacity` results; the bucket's slots must all be free (none admitted or taken
+ *    since the last take). Errors: EINVAL (NULL bucket, capacities < 1, a slot still
+ *    running, called twice), ENOMEM.
+ *  - enqueue: copies *req into the queue; the device reads k, f, x0 when the request is
+ *    admitted and writes x_out when it stops, so these DEVICE buffers must stay valid until
+ *    the request's result has been collected. FCGNO_ENOMEM when the queue is full (retry after
+ *    collecting results and stepping); EINVAL for a NULL argument or a bucket not enabled.
+ *  - results: moves up to `max` published results, in completion order, into the HOST array
+ *    `out` and returns their number (0 when none is ready; -1 for a NULL argument or a bucket
+ *    not enabled). A result is published only after its x_out has been written. A ring that
+ *    the host leaves full holds retired slots back (they stay stopped) until it drains. */
+typedef struct {
+  const double* k;   /* [N][N] coefficient field (device) */
+  const double* f;   /* [N][N] right-hand side (device) */
+  const double* x0;  /* [N][N] initial guess u_0 (device) */
+  double* x_out;     /* [N][N] receives the iterate when the solve stops (device) */
+  uint64_t tag;      /* the caller's identifier, returned with the result */
+} fcgno_serve_request;
+typedef struct {
+  uint64_t tag;      /* the request's tag */
+  int32_t status;    /* FCGNO_OK, FCGNO_EBREAKDOWN or FCGNO_ENOCONV */
+  int32_t iters;     /* iterations performed */
+  double relres;     /* ||r|| / ||r_0|| of the returned iterate (recursively updated residual) */
+  uint64_t seq;      /* 1-based publication number (written last) */
+} fcgno_serve_result;
+fcgno_status fcgno_bucket_serve_enable(fcgno_bucket_t bucket, int queue_capacity, int result_capacity);
+fcgno_status fcgno_bucket_enqueue(fcgno_bucket_t bucket, const fcgno_serve_request* req);
+int fcgno_bucket_results(fcgno_bucket_t bucket, fcgno_serve_result* out, int max);
 
 /* Device bytes fcgno_solve needs for one op of this shape, for admission against an HBM
  * budget: the assembled operator (aE, aN, diagonal, log k in FP64 and log k in FP32), the

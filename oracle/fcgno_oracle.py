@@ -24,7 +24,9 @@ Readings of points the paper leaves open (the same readings the library implemen
   positively homogeneous in r and returns 0 for r = 0. The h^2 factor gives the network
   output the units of A^-1 (A carries 1/h^2); FCG is invariant to a constant scale of w_i,
   so it only conditions the training loss, whose target e = A^-1 r is ~h^2 r at high
-  frequencies.
+  frequencies. A model may also divide the output by k grid point by grid point
+  (desc.output_scale = 1: z = h^2 rms(r) NO / k), the way k enters A^-1 ~ h^2 r / (4k) at
+  the highest frequencies; the paper leaves the network's output scaling open.
 - Retained modes: x1-frequencies 0..M-1 and -M..-1, x2-frequencies 0..M-1. Analysis
   c(k) = (1/n) sum_x v(x) exp(-2 pi i k.x / N), synthesis
   v(x) = Re sum_k w_k2 c(k) exp(+2 pi i k.x / N) with w_0 = 1, w_{k2>0} = 2.
@@ -68,6 +70,7 @@ __all__ = [
     "unpack_weights",
     "fourier_layer",
     "no_forward",
+    "output_scale",
     "notay_loss",
     "l2_loss",
     "jacobi_precond",
@@ -391,7 +394,7 @@ def no_forward(params: dict, desc, r: np.ndarray, logk: np.ndarray) -> np.ndarra
 
     r, logk: [N][N]. Encoder: v0 = lift_w [r/rms, log k] + lift_b. Processor: the Fourier
     layers, GELU after all but the last. Decoder: proj2_w . GELU(proj1_w v + proj1_b) +
-    proj2_b. Output multiplied by h^2 rms(r); zero when r = 0.
+    proj2_b. Output multiplied by output_scale(...); zero when r = 0.
     """
     rms = math.sqrt(float(np.mean(r * r)))
     if rms == 0.0:
@@ -403,7 +406,14 @@ def no_forward(params: dict, desc, r: np.ndarray, logk: np.ndarray) -> np.ndarra
         v = fourier_layer(v, layer, desc.modes, activate=(l < L - 1))
     hid = gelu(v @ params["proj1_w"].T + params["proj1_b"])
     zt = hid @ params["proj2_w"] + params["proj2_b"][0]
-    return grid_h(r.shape[0]) ** 2 * rms * zt
+    return output_scale(desc, rms, logk) * zt
+
+
+def output_scale(desc, rms: float, logk: np.ndarray):
+    """Factor that puts the decoder output into the units of A^-1: h^2 rms(r), divided by k at
+    every grid point when desc.output_scale is 1 (a scalar, or an [N][N] array)."""
+    base = grid_h(logk.shape[0]) ** 2 * rms
+    return base * np.exp(-logk) if getattr(desc, "output_scale", 0) else base
 
 
 # ---------------------------------------------------------------------------------------
@@ -469,7 +479,7 @@ def _forward_saved(params: dict, desc, r: np.ndarray, logk: np.ndarray) -> dict:
     a = v @ params["proj1_w"].T + params["proj1_b"]
     g = gelu(a)
     zt = g @ params["proj2_w"] + params["proj2_b"][0]
-    scale = grid_h(r.shape[0]) ** 2 * rms
+    scale = output_scale(desc, rms, logk)
     return {"rms": rms, "scale": scale, "x0": x0, "vs": vs, "hs": hs, "cs": cs, "a": a, "g": g, "z": scale * zt}
 
 

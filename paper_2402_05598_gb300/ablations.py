@@ -63,14 +63,14 @@ def evaluate(model, dataset: str, N: int, seeds, prec: str = "bf16", m_max: int 
 
 
 def run_variant(dataset: str, N: int, variant: str, steps: int, width: int = 32, layers: int = 4, modes: int = 12,
-                eval_instances: int = 32, m_max: int = 5, seed: int = 0, device=None) -> dict:
+                eval_instances: int = 32, m_max: int = 5, seed: int = 0, device=None, output_scale: int = 1) -> dict:
     """Trains one variant from Xavier weights (seed) and evaluates it."""
     import torch
     dev = device or torch.device("cuda:0")
     loss_kind, data = VARIANTS[variant]
-    desc = I.ModelDesc(width=width, layers=layers, modes=modes, proj_width=width)
+    desc = I.ModelDesc(width=width, layers=layers, modes=modes, proj_width=width, output_scale=output_scale)
     w = torch.from_numpy(I.xavier_weights(desc, seed)).to(dev)
-    model = F.Model(F.make_desc(width, layers, modes, width), w)
+    model = F.Model(F.make_desc(width, layers, modes, width, output_scale=output_scale), w)
     t0 = time.perf_counter()
     res = T.train(model, N, range(N), K=100, batch=32, lr=1e-3, steps=steps, dataset=dataset, data=data,
                   loss_kind=loss_kind, log_every=max(1, steps // 4))
@@ -79,6 +79,7 @@ def run_variant(dataset: str, N: int, variant: str, steps: int, width: int = 32,
     its = evaluate(model, dataset, N, range(30000, 30000 + eval_instances), m_max=m_max, detail=detail)
     model.close()
     return {"dataset": dataset, "grid": N, "variant": variant, "loss": loss_kind, "data": data, "steps": res.steps,
+            "output_scale": output_scale,
             "train_seconds": round(secs, 2), "harvest_seconds": round(res.harvest_seconds, 2),
             "loss_log": [(s, round(v, 4)) for s, v in res.losses], "iterations": its, "outcomes": detail}
 
@@ -109,13 +110,14 @@ def main():
     ap.add_argument("--grids", default="32,64")
     ap.add_argument("--variants", default=",".join(VARIANTS))
     ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--output-scale", type=int, default=1, choices=[0, 1])
     ap.add_argument("--out", default="")
     args = ap.parse_args()
     rows = []
     for ds in args.datasets.split(","):
         for N in (int(g) for g in args.grids.split(",")):
             for v in args.variants.split(","):
-                rows.append(run_variant(ds, N, v, args.steps))
+                rows.append(run_variant(ds, N, v, args.steps, output_scale=args.output_scale))
                 print(json.dumps(rows[-1]), flush=True)
     print(format_table(rows))
     if args.out:

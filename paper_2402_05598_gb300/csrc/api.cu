@@ -140,7 +140,8 @@ __global__ void widen_kernel(size_t n, const float* __restrict__ in, double* __r
 
 static bool desc_ok(const fcgno_model_desc* d) {
   return d && d->width >= 1 && d->width <= 64 && d->layers >= 1 && d->layers <= 16 && d->modes >= 1 &&
-         d->modes <= 16 && d->proj_width >= 1 && d->proj_width <= 64 && d->in_channels == 2;
+         d->modes <= 16 && d->proj_width >= 1 && d->proj_width <= 64 && d->in_channels == 2 &&
+         (d->output_scale == 0 || d->output_scale == 1);
 }
 
 }  // namespace fcgno
@@ -216,6 +217,7 @@ extern "C" fcgno_status fcgno_op_destroy(fcgno_op_t op) {
   for (double* x : p)
     if (x) cudaFree(x);
   if (op->logk32) cudaFree(op->logk32);
+  if (op->kinv) cudaFree(op->kinv);
   delete op;
   return FCGNO_OK;
 }

@@ -11,18 +11,21 @@
 // Directions p_k and s_k = A p_k live in a ring of m_max+1 slots; slot(k) = k mod (m_max+1).
 //
 // Two implementations of the vector part:
-//  - fused: one CTA per instance holds the whole instance in registers (+ p in shared
-//    memory for the stencil halo) and performs the step in one launch with block-level
-//    fixed-order reductions (grids up to 90 x 90);
+//  - cluster: one thread-block cluster per instance (grids up to 128 x 128), each CTA holding a
+//    band of 16 rows in registers (+ p in shared memory, halo rows from the neighbouring CTAs
+//    through distributed shared memory); the step is one launch with fixed-order reductions;
 //  - tiled: any N; seven launches per iteration (dots, beta, direction, stencil+dots,
 //    alpha, update+norm, norm) with per-tile partial sums reduced in a fixed order.
 // Both are deterministic: every sum has a fixed association order.
 #include "internal.cuh"
 
+#include <cooperative_groups.h>
+
 #include <vector>
 #include <algorithm>
 #include <cmath>
 #include <mutex>
+#include <cstring>
 
 namespace fcgno {
 
@@ -30,8 +33,7 @@ constexpr int kTile = 2048;     // elements per CTA (tiled path)
 constexpr int kThreads = 256;   // threads per CTA (tiled path)
 constexpr int kEPT = kTile / kThreads;
 constexpr int kParts = kMaxWindow + 2;
-constexpr int kFusedMaxEPT = 8;  // elements per thread (fused path)
-constexpr int kFusedMaxN = 80;  // n/8 <= 1024 threads and p + reduction staging fit shared memory
+constexpr int kNarrowRunning = 64;  // running instances at or below which the narrow launch shape is used
 
 struct IterArgs {
   int N;
@@ -351,29 +353,57 @@ __global__ void __launch_bounds__(kThreads) norm_kernel(IterArgs a, State s) {
   }
 }
 
-// ------------------------------------ fused path ---------------------------------------
-// One CTA per instance; thread t owns elements t + j*blockDim (j < EPT); p staged in shared
-// memory for the stencil. Three fixed-order block reductions per iteration.
-template <int EPT>
-__global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
-  extern __shared__ double sp[];  // n doubles (p), then kMaxWindow * blockDim (reductions)
+// ------------------------------------ cluster path -------------------------------------
+// One thread-block cluster of CL CTAs per instance (N <= kClusterMaxN). CTA c owns the grid rows
+// [c*band, min(N, (c+1)*band)); thread t owns the band's elements t + j*blockDim (j < EPT).
+// The instance's FP64 work is spread over CL SMs: GB300 runs about 2 FP64 multiply-adds per
+// clock per SM, so one SM per instance would bound a 64 x 64 step to ~20 us on its own.
+// Each sum is a fixed-order block reduction per CTA followed by the CL partials summed in rank
+// order, read through distributed shared memory; every CTA forms the same totals, so the
+// per-instance decisions (breakdown, convergence) are taken identically across the cluster.
+// The stencil's halo rows are copied from the neighbouring CTAs' shared memory after a cluster
+// barrier. A final cluster barrier keeps every CTA resident until the others have read its
+// partial sums.
+constexpr int kClusterThreads = 256;
+constexpr int kClusterBand = 16;   // grid rows per CTA
+constexpr int kClusterMaxN = 128;  // kClusterBand * N <= 8 * kClusterThreads and CL <= 8
+constexpr int kWideMaxN = 80;      // one CTA per instance: n / 8 <= 1024 threads
+
+template <int EPT, int MAXT>
+__global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : (EPT >= 8 ? 2 : 4)) cluster_step_kernel(IterArgs a, State s,
+                                                                                                 int band) {
+  namespace cg = cooperative_groups;
+  cg::cluster_group cl = cg::this_cluster();
+  extern __shared__ double smc[];  // (band + 2) * N doubles of p (halo row, band rows, halo row),
+                                   // then kMaxWindow * blockDim doubles (block reductions)
+  __shared__ double part[3][kMaxWindow];  // this CTA's partial sums: window dots; (p,s),(p,r); ||r||^2
   __shared__ double red_out[kMaxWindow];
   __shared__ double beta_s[kMaxWindow];
-  __shared__ double alpha_s;
-  pdl_wait();  // w (and, with the identity preconditioner, every vector) comes from the kernel before
+  pdl_wait();
   pdl_trigger();
-  const int b = blockIdx.x;
-  if (s.status[b] != kRunning) return;
+  const int CL = (int)cl.num_blocks(), c = (int)cl.block_rank();
+  // a cluster of one CTA synchronises and reads its partial sums as a plain block
+  auto csync = [&]() {
+    if (CL > 1)
+      cl.sync();
+    else
+      __syncthreads();
+  };
+  auto at = [&](double* ptr, int rank) -> const double* { return rank == c ? ptr : cl.map_shared_rank(ptr, rank); };
+  const int b = blockIdx.x / CL;
+  if (s.status[b] != kRunning) return;  // the same for every CTA of the cluster
   const Window wd = window_of(a, s, b);
-  const size_t off = (size_t)b * a.n;
-  const int T = blockDim.x;
-  const int n = (int)a.n;
-  double* red = sp + n;
+  const int N = a.N, T = blockDim.x;
+  const int q0 = c * band, q1 = min(N, q0 + band);
+  const int nb = (q1 - q0) * N;  // elements of this CTA
+  const size_t off = (size_t)b * a.n + (size_t)q0 * N;
+  double* ph = smc;                     // ph[N + e] = p of band element e; rows 0 and band+1 are halos
+  double* red = smc + (size_t)(band + 2) * N;
   double wv[EPT], rv[EPT], sv[EPT];
 #pragma unroll
   for (int j = 0; j < EPT; ++j) {
     const int e = threadIdx.x + j * T;
-    wv[j] = (e < n) ? s.w[off + e] : 0.0;
+    wv[j] = (e < nb) ? s.w[off + e] : 0.0;
   }
   // beta_k = (w, s_k) / (p_k, s_k)
   double acc[kMaxWindow];
@@ -385,18 +415,25 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
         const int e = threadIdx.x + j * T;
-        if (e < n) acc[k] = fma(wv[j], Sk[e], acc[k]);
+        if (e < nb) acc[k] = fma(wv[j], Sk[e], acc[k]);
       }
     }
   }
-  if (wd.m_i > 0) block_sums<kMaxWindow>(acc, wd.m_i, red, red_out);
-  // beta_k = (w, s_k) / (p_k, s_k): one division per coefficient, shared through red_out
-  if ((int)threadIdx.x < wd.m_i) {
-    double dk = acc[0];
+  if (wd.m_i > 0) {
+    block_sums<kMaxWindow>(acc, wd.m_i, red, red_out);
+    if ((int)threadIdx.x < wd.m_i) {
+      double v = acc[0];
 #pragma unroll
-    for (int k = 1; k < kMaxWindow; ++k)
-      if ((int)threadIdx.x == k) dk = acc[k];
-    beta_s[threadIdx.x] = dk / s.ps[(size_t)wd.slots[threadIdx.x] * a.B + b];
+      for (int k = 1; k < kMaxWindow; ++k)
+        if ((int)threadIdx.x == k) v = acc[k];
+      part[0][threadIdx.x] = v;
+    }
+  }
+  csync();  // (1) window partials
+  if ((int)threadIdx.x < wd.m_i) {
+    double tot = 0.0;
+    for (int r = 0; r < CL; ++r) tot += at(&part[0][0], r)[threadIdx.x];
+    beta_s[threadIdx.x] = tot / s.ps[(size_t)wd.slots[threadIdx.x] * a.B + b];
   }
   __syncthreads();
   // p = w - sum beta_k p_k (kept in wv)
@@ -408,7 +445,7 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
 #pragma unroll
       for (int j = 0; j < EPT; ++j) {
         const int e = threadIdx.x + j * T;
-        if (e < n) wv[j] = fma(-beta, Pk[e], wv[j]);
+        if (e < nb) wv[j] = fma(-beta, Pk[e], wv[j]);
       }
     }
   }
@@ -416,9 +453,19 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
 #pragma unroll
   for (int j = 0; j < EPT; ++j) {
     const int e = threadIdx.x + j * T;
-    if (e < n) {
-      sp[e] = wv[j];
+    if (e < nb) {
+      ph[N + e] = wv[j];
       Pn[e] = wv[j];
+    }
+  }
+  csync();  // (2) every band of p in shared memory
+  // halo rows: the last row of the CTA above, the first row of the CTA below (zero at the walls)
+  for (int i = threadIdx.x; i < 2 * N; i += T) {
+    const int p = i % N;
+    if (i < N) {
+      ph[p] = (c > 0) ? at(ph, c - 1)[N + (band - 1) * N + p] : 0.0;
+    } else {
+      ph[(size_t)(q1 - q0 + 1) * N + p] = (q1 < N) ? at(ph, c + 1)[N + p] : 0.0;
     }
   }
   __syncthreads();
@@ -429,56 +476,71 @@ __global__ void __launch_bounds__(1024) fused_step_kernel(IterArgs a, State s) {
     const int e = threadIdx.x + j * T;
     sv[j] = 0.0;
     rv[j] = 0.0;
-    if (e < n) {
-      const int q = e / a.N, p = e - q * a.N;
-      const double ue = (p < a.N - 1) ? sp[e + 1] : 0.0;
-      const double uw = (p > 0) ? sp[e - 1] : 0.0;
-      const double un = (q < a.N - 1) ? sp[e + a.N] : 0.0;
-      const double us = (q > 0) ? sp[e - a.N] : 0.0;
-      sv[j] = stencil_at(s, off + e, p, q, a.N, wv[j], ue, uw, un, us);
+    if (e < nb) {
+      const int ql = e / N, p = e - ql * N;
+      const double* row = ph + (size_t)(ql + 1) * N;
+      const double ue = (p < N - 1) ? row[p + 1] : 0.0;
+      const double uw = (p > 0) ? row[p - 1] : 0.0;
+      // halo rows carry the neighbour's p, or zero at the Dirichlet walls
+      sv[j] = stencil_at(s, off + e, p, q0 + ql, N, wv[j], ue, uw, row[p + N], row[p - N]);
       rv[j] = s.r[off + e];
       d2[0] = fma(wv[j], sv[j], d2[0]);
       d2[1] = fma(wv[j], rv[j], d2[1]);
     }
   }
   block_sums<2>(d2, 2, red, red_out);
-  const double ps = d2[0], pr = d2[1];
-  if (!(ps != 0.0 && isfinite(ps) && isfinite(pr))) {
-    if (threadIdx.x == 0) {
+  if (threadIdx.x == 0) {
+    part[1][0] = d2[0];
+    part[1][1] = d2[1];
+  }
+  csync();  // (3) (p, s), (p, r) partials
+  double ps = 0.0, pr = 0.0;
+  for (int r = 0; r < CL; ++r) {
+    const double* pp = at(&part[1][0], r);
+    ps += pp[0];
+    pr += pp[1];
+  }
+  const bool broke = !(ps != 0.0 && isfinite(ps) && isfinite(pr));
+  double rr = 0.0;
+  if (!broke) {
+    const double alpha = pr / ps;
+    double* Sn = s.S + (size_t)wd.slot_new * a.B * a.n + off;
+    double r2[1] = {0.0};
+#pragma unroll
+    for (int j = 0; j < EPT; ++j) {
+      const int e = threadIdx.x + j * T;
+      if (e < nb) {
+        Sn[e] = sv[j];
+        s.u[off + e] = fma(alpha, wv[j], s.u[off + e]);
+        const double r1 = fma(-alpha, sv[j], rv[j]);
+        s.r[off + e] = r1;
+        r2[0] = fma(r1, r1, r2[0]);
+      }
+    }
+    block_sums<1>(r2, 1, red, red_out);
+    if (threadIdx.x == 0) part[2][0] = r2[0];
+  }
+  csync();  // (4) ||r||^2 partials (unused after a breakdown)
+  if (!broke) {
+    for (int r = 0; r < CL; ++r) rr += at(&part[2][0], r)[0];
+  }
+  if (c == 0 && threadIdx.x == 0) {
+    if (broke) {
       s.status[b] = FCGNO_EBREAKDOWN;
       atomicAdd(s.ndone, 1);
-    }
-    return;
-  }
-  // alpha = (p, r) / (p, s): one division, shared
-  if (threadIdx.x == 0) alpha_s = pr / ps;
-  __syncthreads();
-  const double alpha = alpha_s;
-  double* Sn = s.S + (size_t)wd.slot_new * a.B * a.n + off;
-  double rr[1] = {0.0};
-#pragma unroll
-  for (int j = 0; j < EPT; ++j) {
-    const int e = threadIdx.x + j * T;
-    if (e < n) {
-      Sn[e] = sv[j];
-      s.u[off + e] = fma(alpha, wv[j], s.u[off + e]);
-      const double r1 = fma(-alpha, sv[j], rv[j]);
-      s.r[off + e] = r1;
-      rr[0] = fma(r1, r1, rr[0]);
+    } else {
+      s.ps[(size_t)wd.slot_new * a.B + b] = ps;
+      s.alpha[b] = pr / ps;
+      s.rr[b] = rr;
+      s.rms[b] = sqrt(rr / (double)a.n);
+      s.iters[b] = wd.i + 1;
+      if (rr == 0.0 || (!a.fixed && sqrt(rr) <= a.tol * s.r0[b])) {
+        s.status[b] = FCGNO_OK;
+        atomicAdd(s.ndone, 1);
+      }
     }
   }
-  block_sums<1>(rr, 1, red, red_out);
-  if (threadIdx.x == 0) {
-    s.ps[(size_t)wd.slot_new * a.B + b] = ps;
-    s.alpha[b] = alpha;
-    s.rr[b] = rr[0];
-    s.rms[b] = sqrt(rr[0] / (double)a.n);
-    s.iters[b] = wd.i + 1;
-    if (rr[0] == 0.0 || (!a.fixed && sqrt(rr[0]) <= a.tol * s.r0[b])) {
-      s.status[b] = FCGNO_OK;
-      atomicAdd(s.ndone, 1);
-    }
-  }
+  csync();  // (5) no CTA leaves while another still reads its shared memory
 }
 
 // FP64 multiply-add rate (a measurement aid, not a step of the method). Every thread runs
@@ -542,10 +604,14 @@ __global__ void harvest_copy_kernel(size_t total, const double* __restrict__ r, 
 }
 
 // ------------------------------------ host side ----------------------------------------
+static void drop_graph(IterGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  trace_release(g.traced);
+  g = IterGraph();
+}
+
 static void drop_graph(SolverWorkspace& w) {
-  if (w.graph.exec) cudaGraphExecDestroy(w.graph.exec);
-  trace_release(w.graph.traced);
-  w.graph = IterGraph();
+  for (IterGraph& g : w.graph) drop_graph(g);
 }
 
 static void free_ws(SolverWorkspace& w) {
@@ -661,42 +727,92 @@ struct HarvestHook {
 };
 
 struct LoopShape {
-  bool fused;
-  int fusedEPT;
-  int fusedThreads;
-  size_t fusedSmem;
+  bool cluster;      // N <= kClusterMaxN: the step is one launch of cluster_step_kernel
+  int CL;            // CTAs per instance (cluster size)
+  int band;          // grid rows per CTA
+  int EPT;           // elements per thread
+  int threads;       // threads per CTA
+  bool big;          // threads > 256 (the 1024-thread instantiation)
+  size_t smem;       // dynamic shared memory per CTA
 };
 
-static LoopShape loop_shape(const fcgno_op* op) {
-  LoopShape L;
-  L.fused = op->N <= kFusedMaxN;
-  // 8 elements per thread: measured faster than 4 (1024-thread blocks) at 64 x 64, where the
-  // larger block reductions and shared-memory footprint outweigh the extra loads in flight
-  L.fusedEPT = kFusedMaxEPT;
-  L.fusedThreads = ((int)ceil_div(op->n, L.fusedEPT) + 31) / 32 * 32;
-  L.fusedSmem = (op->n + (size_t)kMaxWindow * L.fusedThreads) * sizeof(double);
+// Launch shape of the FCG step. Wide (many instances running): for N <= 80 one CTA holds a whole
+// instance (8 elements per thread, up to 1024 threads), which keeps the FP64 pipe of every SM
+// busy with few synchronisations; larger N and the narrow shape (few instances running) split
+// each instance over a cluster of 16-row bands on 256-thread CTAs, so that one instance's step
+// runs on several SMs.
+static LoopShape loop_shape(const fcgno_op* op, bool narrow = false) {
+  LoopShape L{};
+  L.cluster = op->N <= kClusterMaxN;
+  if (!L.cluster) return L;
+  const int N = op->N;
+  if (!narrow && N <= kWideMaxN) {
+    L.CL = 1;
+    L.band = N;
+    L.EPT = 8;
+    L.threads = (int)((ceil_div(op->n, 8) + 31) / 32 * 32);
+  } else {
+    L.band = std::min(kClusterBand, N);
+    L.CL = (N + L.band - 1) / L.band;
+    const int need = (L.band * N + kClusterThreads - 1) / kClusterThreads;
+    L.EPT = need <= 1 ? 1 : need <= 2 ? 2 : need <= 4 ? 4 : 8;
+    L.threads = kClusterThreads;
+  }
+  L.big = L.threads > kClusterThreads;
+  L.smem = ((size_t)(L.band + 2) * N + (size_t)kMaxWindow * L.threads) * sizeof(double);
   return L;
 }
 
-// Raise the fused kernel's shared-memory limit (and pin the carveout to its maximum so that
-// two blocks fit per SM) before its first launch; not a stream operation.
-static fcgno_status prepare_fused(const LoopShape& L) {
-  if (!L.fused) return FCGNO_OK;
-  const void* fn = (const void*)fused_step_kernel<kFusedMaxEPT>;
-  if (L.fusedSmem > 48 * 1024)
-    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L.fusedSmem));
+template <int EPT, int MAXT>
+static fcgno_status prepare_cluster_kernel(size_t smem) {
+  const void* fn = (const void*)cluster_step_kernel<EPT, MAXT>;
+  if (smem > 48 * 1024)
+    FCGNO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   FCGNO_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout,
                                       (int)cudaSharedmemCarveoutMaxShared));
   return FCGNO_OK;
 }
 
+// Raise the step kernel's shared-memory limit before its first launch (not a stream
+// operation, so it stays outside graph capture).
+static fcgno_status prepare_fused(const LoopShape& L) {
+  if (!L.cluster) return FCGNO_OK;
+  if (L.big) return prepare_cluster_kernel<8, 1024>(L.smem);
+  switch (L.EPT) {
+    case 1: return prepare_cluster_kernel<1, kClusterThreads>(L.smem);
+    case 2: return prepare_cluster_kernel<2, kClusterThreads>(L.smem);
+    case 4: return prepare_cluster_kernel<4, kClusterThreads>(L.smem);
+    default: return prepare_cluster_kernel<8, kClusterThreads>(L.smem);
+  }
+}
+
+template <int EPT, int MAXT>
+static cudaError_t launch_cluster_step(const IterArgs& a, const State& s, const LoopShape& L, cudaStream_t cs) {
+  return launch_chained_cluster(cluster_step_kernel<EPT, MAXT>, dim3(L.CL * a.B), dim3(L.threads), L.smem, cs,
+                                L.CL, a, s, L.band);
+}
+
 // The vector part of one iteration (steps a3-a7) plus the iteration-counter advance.
 static fcgno_status launch_vector_step(const IterArgs& a, const State& s, const LoopShape& L, cudaStream_t cs) {
-  if (L.fused) {
+  if (L.cluster) {
     {
       TraceScope ts("fcg_fused", cs);
-      FCGNO_CUDA_TRY(launch_chained(fused_step_kernel<kFusedMaxEPT>, dim3(a.B), dim3(L.fusedThreads), L.fusedSmem,
-                                    cs, a, s));
+      cudaError_t e;
+      if (L.big) {
+        e = launch_cluster_step<8, 1024>(a, s, L, cs);
+      } else {
+        switch (L.EPT) {
+          case 1: e = launch_cluster_step<1, kClusterThreads>(a, s, L, cs); break;
+          case 2: e = launch_cluster_step<2, kClusterThreads>(a, s, L, cs); break;
+          case 4: e = launch_cluster_step<4, kClusterThreads>(a, s, L, cs); break;
+          default: e = launch_cluster_step<8, kClusterThreads>(a, s, L, cs); break;
+        }
+      }
+      if (e != cudaSuccess) {
+        set_last_error(std::string("cluster step launch: ") + cudaGetErrorString(e));
+        cudaGetLastError();
+        return FCGNO_ECUDA;
+      }
     }
     FCGNO_LAUNCHED();
   } else {
@@ -737,14 +853,19 @@ static fcgno_status launch_jacobi(fcgno_op* op, int steps, cudaStream_t cs) {
   return FCGNO_OK;
 }
 
+struct ServeDev;
+static fcgno_status launch_serve(const ServeDev& v, const IterArgs& a, const State& s, cudaStream_t cs);
+
 static fcgno_status launch_iteration(fcgno_op* op, fcgno_model* model, fcgno_prec prec, const IterArgs& a,
-                                     const State& s, const LoopShape& L, cudaStream_t cs, int jacobi = 0) {
+                                     const State& s, const LoopShape& L, cudaStream_t cs, int jacobi = 0,
+                                     bool narrow = false, const ServeDev* serve = nullptr) {
+  if (serve) FCGNO_TRY(launch_serve(*serve, a, s, cs));
   if (jacobi > 0) {
     FCGNO_TRY(launch_jacobi(op, jacobi, cs));
   } else if (model) {
     SolverWorkspace& w = op->ws;
     if (prec == FCGNO_BF16 || prec == FCGNO_FP16) {
-      FCGNO_TRY(no_apply_tc(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP16, cs));
+      FCGNO_TRY(no_apply_tc(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP16, cs, narrow));
     } else {
       FCGNO_TRY(no_apply_simt(model, op, w.r, w.rms, w.status, w.w, prec == FCGNO_FP64, cs));
     }
@@ -755,20 +876,21 @@ static fcgno_status launch_iteration(fcgno_op* op, fcgno_model* model, fcgno_pre
 // Captures G iterations into a CUDA graph (reused while the baked-in parameters match).
 static fcgno_status ensure_graph(fcgno_op* op, fcgno_model* model, fcgno_prec prec, const IterArgs& a,
                                  const State& s, const LoopShape& L, const double* b, const double* x, int G,
-                                 int jacobi) {
+                                 int jacobi, bool narrow = false, const ServeDev* serve = nullptr) {
   SolverWorkspace& w = op->ws;
-  IterGraph& g = w.graph;
+  IterGraph& g = w.graph[narrow ? 1 : 0];
   const uint64_t gen = model ? model->gen : 0;
   if (g.exec && g.trace_gen == trace_generation() && g.model == model && g.model_gen == gen &&
       g.prec == (int)prec && g.nslots == a.nslots && g.jacobi == jacobi &&
-      g.fixed == a.fixed && g.G == G && g.tol == a.tol && g.b == b && g.x == x)
+      g.fixed == a.fixed && g.G == G && g.tol == a.tol && g.b == b && g.x == x && g.serve == serve)
     return FCGNO_OK;
-  drop_graph(w);
+  drop_graph(g);
   const uint64_t l0 = g_launches.load();
   FCGNO_CUDA_TRY(cudaStreamBeginCapture(w.cs, cudaStreamCaptureModeThreadLocal));
   trace_capture_begin(&g.traced);
   fcgno_status rc = FCGNO_OK;
-  for (int it = 0; it < G && rc == FCGNO_OK; ++it) rc = launch_iteration(op, model, prec, a, s, L, w.cs, jacobi);
+  for (int it = 0; it < G && rc == FCGNO_OK; ++it)
+    rc = launch_iteration(op, model, prec, a, s, L, w.cs, jacobi, narrow, serve);
   trace_capture_end();
   // captured launches did not run: they are counted when the graph replays
   g.kernels = g_launches.load() - l0;
@@ -803,6 +925,7 @@ static fcgno_status ensure_graph(fcgno_op* op, fcgno_model* model, fcgno_prec pr
   g.tol = a.tol;
   g.b = b;
   g.x = x;
+  g.serve = serve;
   return FCGNO_OK;
 }
 
@@ -829,8 +952,9 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
   a.nslots = slots;
   a.tol = o.tol;
   a.fixed = o.fixed_iters ? 1 : 0;
-  const LoopShape L = loop_shape(op);
+  const LoopShape L = loop_shape(op), Ln = loop_shape(op, true);
   FCGNO_TRY(prepare_fused(L));
+  FCGNO_TRY(prepare_fused(Ln));
   // the caller's stream orders our internal stream at entry and exit
   FCGNO_CUDA_TRY(cudaEventRecord(w.ev_in, st));
   FCGNO_CUDA_TRY(cudaStreamWaitEvent(cs, w.ev_in, 0));
@@ -853,15 +977,24 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
   } guard{h_ndone};
   const int G = std::max(1, o.check_every);
   const bool use_graph = !hook && graphs_enabled() && G > 1;
+  // once few instances are still running, the replayed iterations switch to the narrow launch
+  // shapes (more blocks per instance, for the FCG step and the 16-bit preconditioner's
+  // synthesis): the launches are then bound by one instance's serial chain, not by the batch's work
+  const bool tc = model && (prec == FCGNO_BF16 || prec == FCGNO_FP16);
+  const bool can_narrow = (tc && tc_has_narrow(op->N, model->desc)) || Ln.CL != L.CL;
+  int running = op->B;
   int i = 0;
   int since_check = 0;
+  int last_graph = 0;
   while (i < o.max_iter) {
     bool replayed = false;
     if (use_graph && i > 0 && o.max_iter - i >= G) {
       // the first iteration ran eagerly, so every lazily allocated buffer exists before capture
-      FCGNO_TRY(ensure_graph(op, model, prec, a, s, L, b, x, G, jacobi));
-      FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph.exec, cs));
-      g_launches.fetch_add(w.graph.kernels, std::memory_order_relaxed);
+      const bool narrow = can_narrow && running <= kNarrowRunning;
+      last_graph = narrow ? 1 : 0;
+      FCGNO_TRY(ensure_graph(op, model, prec, a, s, narrow ? Ln : L, b, x, G, jacobi, narrow));
+      FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph[last_graph].exec, cs));
+      g_launches.fetch_add(w.graph[last_graph].kernels, std::memory_order_relaxed);
       i += G;
       since_check = G;
       replayed = true;
@@ -881,7 +1014,8 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
       since_check = 0;
       FCGNO_CUDA_TRY(cudaMemcpyAsync(h_ndone, w.ndone, sizeof(int), cudaMemcpyDeviceToHost, cs));
       FCGNO_CUDA_TRY(cudaStreamSynchronize(cs));
-      if (replayed) trace_accumulate(w.graph.traced);
+      if (replayed) trace_accumulate(w.graph[last_graph].traced);
+      running = op->B - *h_ndone;
       if (*h_ndone >= op->B && !hook) break;
     }
   }
@@ -1203,6 +1337,231 @@ extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, doubl
   return FCGNO_OK;
 }
 
+namespace fcgno {
+
+// ------------------------------------ device-driven serving ----------------------------
+// Admission and retirement of a bucket's slots at the start of every iteration, on the device.
+// The request queue and the result ring are pinned host memory mapped into the device's address
+// space: the host publishes requests by advancing req_tail (release), the device publishes
+// results by writing each record's sequence number last (after a system-scope fence). Slot
+// phases: 0 free, 1 solving, 2 retiring (this iteration), 3 admitted (this iteration).
+struct ServeDev {
+  int qcap, dcap, max_iter, grid;
+  const fcgno_serve_request* req;       // [qcap] (mapped)
+  const unsigned long long* req_tail;   // requests published by the host (mapped)
+  unsigned long long* req_head_pub;     // requests taken by the device (mapped, for the host)
+  fcgno_serve_result* res;              // [dcap] (mapped)
+  const unsigned long long* res_head;   // results consumed by the host (mapped)
+  unsigned long long* ctr;              // [2] requests taken, results published (device)
+  fcgno_serve_request* slot_req;        // [B] each slot's request (device)
+  int* phase;                           // [B]
+  int* list;                            // [2][B] retiring slots, admitted slots
+  int* count;                           // [2] their numbers
+  double* x;                            // the bucket's iterates [B][n]
+  double* b;                            // the bucket's right-hand sides [B][n]
+  double* aE;
+  double* aN;
+  double* diag;
+  double* logk;
+  float* logk32;
+  double* kinv;
+};
+
+__device__ __forceinline__ unsigned long long ld_acquire_sys(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.sys.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release_sys(unsigned long long* p, unsigned long long v) {
+  asm volatile("st.release.sys.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Exclusive prefix count of `flag` over the block (1024 threads max) in thread order; *total
+// receives the block's count. Contains two __syncthreads().
+__device__ __forceinline__ int block_rank(bool flag, int* warp_counts, int* total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  const unsigned m = __ballot_sync(0xffffffffu, flag);
+  if (lane == 0) warp_counts[warp] = __popc(m);
+  __syncthreads();
+  int before = 0, tot = 0;
+  for (int w = 0; w < nw; ++w) {
+    if (w < warp) before += warp_counts[w];
+    tot += warp_counts[w];
+  }
+  __syncthreads();
+  *total = tot;
+  return before + __popc(m & ((1u << lane) - 1u));
+}
+
+// (1) one block: lists the slots to retire (their solve stopped, and the result ring has room)
+// and admits queued requests into free slots, both in slot order.
+__global__ void __launch_bounds__(1024) serve_scan_kernel(ServeDev v, State s, int B) {
+  __shared__ int wc[32];
+  __shared__ unsigned long long avail_q, avail_r;
+  if (threadIdx.x == 0) {
+    const unsigned long long tail = ld_acquire_sys(v.req_tail);
+    const unsigned long long head = v.ctr[0];
+    avail_q = tail > head ? tail - head : 0ull;
+    const unsigned long long consumed = ld_acquire_sys(v.res_head);
+    const unsigned long long used = v.ctr[1] - consumed;
+    avail_r = used < (unsigned long long)v.dcap ? (unsigned long long)v.dcap - used : 0ull;
+  }
+  __syncthreads();
+  int nR = 0, nA = 0;
+  for (int base = 0; base < B; base += blockDim.x) {
+    const int slot = base + threadIdx.x;
+    bool isR = false, isF = false;
+    if (slot < B) {
+      const int ph = v.phase[slot];
+      isR = ph == 1 && (s.status[slot] != kRunning || s.iters[slot] >= v.max_iter);
+      isF = ph == 0;
+    }
+    int totR, totF;
+    const int rR = block_rank(isR, wc, &totR);
+    const int rF = block_rank(isF, wc, &totF);
+    if (isR && (unsigned long long)(nR + rR) < avail_r) {
+      v.list[nR + rR] = slot;
+      v.phase[slot] = 2;
+      if (s.status[slot] == kRunning) s.status[slot] = FCGNO_ENOCONV;  // capped: stop it
+    }
+    if (isF && (unsigned long long)(nA + rF) < avail_q) {
+      const unsigned long long idx = v.ctr[0] + (unsigned long long)(nA + rF);
+      const volatile fcgno_serve_request* rq = v.req + idx % (unsigned long long)v.qcap;
+      fcgno_serve_request r;
+      r.k = rq->k;
+      r.f = rq->f;
+      r.x0 = rq->x0;
+      r.x_out = rq->x_out;
+      r.tag = rq->tag;
+      v.slot_req[slot] = r;
+      v.phase[slot] = 3;
+      v.list[B + nA + rF] = slot;
+    }
+    nR = (int)min((unsigned long long)(nR + totR), avail_r);
+    nA = (int)min((unsigned long long)(nA + totF), avail_q);
+  }
+  __syncthreads();  // every thread has read ctr[0]
+  if (threadIdx.x == 0) {
+    v.count[0] = nR;
+    v.count[1] = nA;
+    v.ctr[0] += (unsigned long long)nA;
+    st_release_sys(v.req_head_pub, v.ctr[0]);
+  }
+}
+
+// (2) retiring slots: iterate -> the request's x_out; admitted slots: operator assembled from
+// the request's k, f and x0 copied in. The two lists hold different slots.
+__global__ void __launch_bounds__(256) serve_move_kernel(ServeDev v, int N, size_t n, int B) {
+  const int nR = v.count[0], nA = v.count[1];
+  const size_t total = (size_t)(nR + nA) * n;
+  for (size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x; idx < total;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const int which = (int)(idx / n);
+    const size_t e = idx - (size_t)which * n;
+    if (which < nR) {
+      const int slot = v.list[which];
+      v.slot_req[slot].x_out[e] = v.x[(size_t)slot * n + e];
+    } else {
+      const int slot = v.list[B + which - nR];
+      const fcgno_serve_request& r = v.slot_req[slot];
+      const size_t i = (size_t)slot * n + e;
+      assemble_point(N, (int)e, r.k, i, v.aE, v.aN, v.diag, v.logk, v.logk32, v.kinv);
+      v.b[i] = r.f[e];
+      v.x[i] = r.x0[e];
+    }
+  }
+}
+
+// (3) admitted slots: r_0 = b - A x0 and the per-tile partial sums of ||r_0||^2 (as init_kernel)
+__global__ void __launch_bounds__(kThreads) serve_init_kernel(ServeDev v, IterArgs a, State s) {
+  __shared__ double scratch[32];
+  const int nA = v.count[1];
+  for (int job = blockIdx.x; job < nA * a.tiles; job += gridDim.x) {
+    const int b = v.list[a.B + job / a.tiles], tile = job % a.tiles;
+    const size_t off = (size_t)b * a.n;
+    double acc[1] = {0.0};
+    for (int j = 0; j < kEPT; ++j) {
+      const size_t e = (size_t)tile * kTile + j * kThreads + threadIdx.x;
+      if (e < a.n) {
+        const int q = (int)(e / a.N), p = (int)(e - (size_t)q * a.N);
+        const double* u = s.u + off;
+        const double c = u[e];
+        const double ue = (p < a.N - 1) ? u[e + 1] : 0.0;
+        const double uw = (p > 0) ? u[e - 1] : 0.0;
+        const double un = (q < a.N - 1) ? u[e + a.N] : 0.0;
+        const double us = (q > 0) ? u[e - a.N] : 0.0;
+        const double rv = s.b[off + e] - stencil_at(s, off + e, p, q, a.N, c, ue, uw, un, us);
+        s.r[off + e] = rv;
+        acc[0] = fma(rv, rv, acc[0]);
+      }
+    }
+    const double tot = block_sum_lane<double, 1>(acc, 1, scratch);
+    if (threadIdx.x == 0) s.part[((size_t)b * a.tiles + tile) * kParts] = tot;
+    __syncthreads();
+  }
+}
+
+// (4) one block: publishes the retiring slots' results (their x_out is written) and frees them;
+// finishes the admitted slots (||r_0||, rms, iteration 0, running).
+__global__ void __launch_bounds__(kThreads) serve_finish_kernel(ServeDev v, IterArgs a, State s) {
+  __shared__ double scratch[32];
+  const int nR = v.count[0], nA = v.count[1];
+  for (int i = threadIdx.x; i < nR; i += blockDim.x) {
+    const int slot = v.list[i];
+    const unsigned long long seq = v.ctr[1] + (unsigned long long)i + 1ull;
+    fcgno_serve_result* rec = v.res + (seq - 1ull) % (unsigned long long)v.dcap;
+    rec->tag = v.slot_req[slot].tag;
+    rec->status = s.status[slot];
+    rec->iters = s.iters[slot];
+    rec->relres = s.r0[slot] > 0.0 ? sqrt(s.rr[slot]) / s.r0[slot] : 0.0;
+    __threadfence_system();
+    st_release_sys(reinterpret_cast<unsigned long long*>(&rec->seq), seq);
+    v.phase[slot] = 0;
+  }
+  for (int j = 0; j < nA; ++j) {
+    const int b = v.list[a.B + j];
+    const double rr = tile_totals<1>(a, s, b, 1, 0, scratch);
+    if (threadIdx.x == 0) {
+      s.rr[b] = rr;
+      s.r0[b] = sqrt(rr);
+      s.rms[b] = sqrt(rr / (double)a.n);
+      s.iters[b] = 0;
+      s.status[b] = rr == 0.0 ? FCGNO_OK : kRunning;
+      v.phase[b] = 1;
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) v.ctr[1] += (unsigned long long)nR;
+}
+
+static fcgno_status launch_serve(const ServeDev& v, const IterArgs& a, const State& s, cudaStream_t cs) {
+  serve_scan_kernel<<<1, 1024, 0, cs>>>(v, s, a.B);
+  FCGNO_LAUNCHED();
+  serve_move_kernel<<<v.grid, 256, 0, cs>>>(v, a.N, a.n, a.B);
+  FCGNO_LAUNCHED();
+  serve_init_kernel<<<v.grid, kThreads, 0, cs>>>(v, a, s);
+  FCGNO_LAUNCHED();
+  serve_finish_kernel<<<1, kThreads, 0, cs>>>(v, a, s);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+// Host side of a bucket's device-driven serving: the mapped queue and ring, the device arrays.
+struct ServeRings {
+  void* mapped = nullptr;    // one pinned, mapped allocation holding the pieces below
+  fcgno_serve_request* req = nullptr;
+  unsigned long long* req_tail = nullptr;  // written by the host
+  unsigned long long* req_head = nullptr;  // written by the device
+  fcgno_serve_result* res = nullptr;
+  unsigned long long* res_head = nullptr;  // written by the host
+  void* device = nullptr;    // one device allocation: counters, slot requests, phases, lists
+  ServeDev dev{};
+  unsigned long long host_tail = 0, host_head = 0;
+  std::mutex mu;
+};
+
+}  // namespace fcgno
+
 // ------------------------------------ serving buckets ----------------------------------
 // A bucket keeps `capacity` same-size solves resident on the device (operator, iterate,
 // right-hand side, Krylov state) and advances every active slot together. Slots are
@@ -1225,6 +1584,8 @@ struct fcgno_bucket {
   int* h_iters = nullptr;
   double* h_rr = nullptr;
   double* h_r0 = nullptr;
+  int occupied = 0;         // slots admitted and not yet taken (host-driven mode)
+  fcgno::ServeRings* srv = nullptr;  // device-driven serving (after fcgno_bucket_serve_enable)
 };
 
 extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t model, fcgno_prec prec, int m_max,
@@ -1256,7 +1617,8 @@ extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t m
   const size_t vec = op->n * capacity * sizeof(double);
   bool ok = cudaMalloc(&op->aE, vec) == cudaSuccess && cudaMalloc(&op->aN, vec) == cudaSuccess &&
             cudaMalloc(&op->diag, vec) == cudaSuccess && cudaMalloc(&op->logk, vec) == cudaSuccess &&
-            cudaMalloc(&op->logk32, vec / 2) == cudaSuccess && cudaMalloc(&k->x, vec) == cudaSuccess &&
+            cudaMalloc(&op->logk32, vec / 2) == cudaSuccess && cudaMalloc(&op->kinv, vec) == cudaSuccess &&
+            cudaMalloc(&k->x, vec) == cudaSuccess &&
             cudaMalloc(&k->b, vec) == cudaSuccess &&
             cudaMallocHost(&k->h_status, sizeof(int) * capacity) == cudaSuccess &&
             cudaMallocHost(&k->h_iters, sizeof(int) * capacity) == cudaSuccess &&
@@ -1277,6 +1639,7 @@ extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t m
     FCGNO_CUDA_TRY(cudaMemsetAsync(op->aN, 0, vec, st));
     FCGNO_CUDA_TRY(cudaMemsetAsync(op->logk, 0, vec, st));
     FCGNO_CUDA_TRY(cudaMemsetAsync(op->logk32, 0, vec / 2, st));
+    FCGNO_CUDA_TRY(cudaMemsetAsync(op->kinv, 0, vec, st));
     FCGNO_CUDA_TRY(cudaMemsetAsync(k->x, 0, vec, st));
     FCGNO_CUDA_TRY(cudaMemsetAsync(k->b, 0, vec, st));
     FCGNO_CUDA_TRY(cudaMemsetAsync(op->ws.r, 0, vec, st));
@@ -1316,16 +1679,17 @@ extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t m
 extern "C" fcgno_status fcgno_bucket_admit(fcgno_bucket_t k, int slot, const double* kcoef, const double* f,
                                            const double* x0, void* stream) {
   using namespace fcgno;
-  if (!k || slot < 0 || slot >= k->op->B || !kcoef || !f || !x0) {
-    set_last_error("fcgno_bucket_admit: bad arguments");
+  if (!k || slot < 0 || slot >= k->op->B || !kcoef || !f || !x0 || k->srv) {
+    set_last_error(k && k->srv ? "fcgno_bucket_admit: the bucket serves from its device queue"
+                               : "fcgno_bucket_admit: bad arguments");
     return FCGNO_EINVAL;
   }
+  ++k->occupied;
   cudaStream_t st = (cudaStream_t)stream;
   fcgno_op* op = k->op;
   const size_t n = op->n, off = (size_t)slot * n;
   // the slot's operator, right-hand side and initial guess
-  FCGNO_TRY(launch_assemble(op->N, n, n, kcoef, op->aE + off, op->aN + off, op->diag + off, op->logk + off,
-                            op->logk32 + off, st));
+  FCGNO_TRY(launch_assemble(op, off, n, kcoef, st));
   FCGNO_CUDA_TRY(cudaMemcpyAsync(k->b + off, f, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   FCGNO_CUDA_TRY(cudaMemcpyAsync(k->x + off, x0, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
   // r_0, ||r_0||, status "running", iteration 0 for this slot only
@@ -1361,14 +1725,16 @@ extern "C" fcgno_status fcgno_bucket_step(fcgno_bucket_t k, void* stream) {
   SolverWorkspace& w = k->op->ws;
   FCGNO_CUDA_TRY(cudaEventRecord(w.ev_in, st));
   FCGNO_CUDA_TRY(cudaStreamWaitEvent(w.cs, w.ev_in, 0));
+  const ServeDev* sv = k->srv ? &k->srv->dev : nullptr;
   if (!k->warmed || !graphs_enabled() || k->G == 1) {
     // first step eagerly (lazily allocated buffers exist before any capture)
-    for (int i = 0; i < k->G; ++i) FCGNO_TRY(launch_iteration(k->op, k->model, k->prec, k->a, k->s, k->L, w.cs));
+    for (int i = 0; i < k->G; ++i)
+      FCGNO_TRY(launch_iteration(k->op, k->model, k->prec, k->a, k->s, k->L, w.cs, 0, false, sv));
     k->warmed = true;
   } else {
-    FCGNO_TRY(ensure_graph(k->op, k->model, k->prec, k->a, k->s, k->L, k->b, k->x, k->G, 0));
-    FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph.exec, w.cs));
-    g_launches.fetch_add(w.graph.kernels, std::memory_order_relaxed);
+    FCGNO_TRY(ensure_graph(k->op, k->model, k->prec, k->a, k->s, k->L, k->b, k->x, k->G, 0, false, sv));
+    FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph[0].exec, w.cs));
+    g_launches.fetch_add(w.graph[0].kernels, std::memory_order_relaxed);
   }
   FCGNO_CUDA_TRY(cudaEventRecord(w.ev_out, w.cs));
   FCGNO_CUDA_TRY(cudaStreamWaitEvent(st, w.ev_out, 0));
@@ -1403,10 +1769,12 @@ extern "C" fcgno_status fcgno_bucket_poll(fcgno_bucket_t k, int32_t* status, int
 
 extern "C" fcgno_status fcgno_bucket_take(fcgno_bucket_t k, int slot, double* x_out, void* stream) {
   using namespace fcgno;
-  if (!k || slot < 0 || slot >= k->op->B) {
-    set_last_error("fcgno_bucket_take: bad arguments");
+  if (!k || slot < 0 || slot >= k->op->B || k->srv) {
+    set_last_error(k && k->srv ? "fcgno_bucket_take: the bucket serves from its device queue"
+                               : "fcgno_bucket_take: bad arguments");
     return FCGNO_EINVAL;
   }
+  if (k->occupied > 0) --k->occupied;
   cudaStream_t st = (cudaStream_t)stream;
   const size_t n = k->op->n, off = (size_t)slot * n;
   if (x_out) FCGNO_CUDA_TRY(cudaMemcpyAsync(x_out, k->x + off, n * sizeof(double), cudaMemcpyDeviceToDevice, st));
@@ -1421,8 +1789,124 @@ extern "C" fcgno_status fcgno_bucket_take(fcgno_bucket_t k, int slot, double* x_
   return FCGNO_OK;
 }
 
+extern "C" fcgno_status fcgno_bucket_serve_enable(fcgno_bucket_t k, int queue_capacity, int result_capacity) {
+  using namespace fcgno;
+  if (!k || queue_capacity < 1 || result_capacity < 1 || k->srv || k->occupied != 0) {
+    set_last_error(!k ? "fcgno_bucket_serve_enable: null bucket"
+                      : (k->srv ? "fcgno_bucket_serve_enable: already enabled"
+                                : (k->occupied ? "fcgno_bucket_serve_enable: slots still admitted (take them first)"
+                                               : "fcgno_bucket_serve_enable: capacities must be >= 1")));
+    return FCGNO_EINVAL;
+  }
+  const int B = k->op->B;
+  ServeRings* r = new ServeRings();
+  const size_t q = (size_t)queue_capacity, d = (size_t)result_capacity;
+  // mapped: requests | results | 3 counters (each piece 64-byte aligned)
+  auto al = [](size_t x) { return (x + 63) & ~(size_t)63; };
+  const size_t o_res = al(q * sizeof(fcgno_serve_request)), o_ctr = o_res + al(d * sizeof(fcgno_serve_result));
+  const size_t mapped_bytes = o_ctr + 3 * 64;
+  // device: counters [2] | count [2] | slot requests [B] | phase [B] | lists [2B]
+  const size_t o_cnt = 64, o_sreq = 128, o_ph = o_sreq + al((size_t)B * sizeof(fcgno_serve_request));
+  const size_t o_list = o_ph + al((size_t)B * sizeof(int)), dev_bytes = o_list + al((size_t)2 * B * sizeof(int));
+  void* mdev = nullptr;
+  int sms = 0, devno = 0;
+  cudaError_t e = cudaHostAlloc(&r->mapped, mapped_bytes, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&mdev, r->mapped, 0);
+  if (e == cudaSuccess) e = cudaMalloc(&r->device, dev_bytes);
+  if (e == cudaSuccess) e = cudaGetDevice(&devno);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, devno);
+  if (e == cudaSuccess) e = cudaMemset(r->device, 0, dev_bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    if (r->mapped) cudaFreeHost(r->mapped);
+    if (r->device) cudaFree(r->device);
+    delete r;
+    set_last_error(std::string("fcgno_bucket_serve_enable: ") + cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? FCGNO_ENOMEM : FCGNO_ECUDA;
+  }
+  std::memset(r->mapped, 0, mapped_bytes);
+  unsigned char* hm = (unsigned char*)r->mapped;
+  unsigned char* dm = (unsigned char*)mdev;
+  unsigned char* dd = (unsigned char*)r->device;
+  r->req = (fcgno_serve_request*)hm;
+  r->res = (fcgno_serve_result*)(hm + o_res);
+  r->req_tail = (unsigned long long*)(hm + o_ctr);
+  r->req_head = (unsigned long long*)(hm + o_ctr + 64);
+  r->res_head = (unsigned long long*)(hm + o_ctr + 128);
+  ServeDev& v = r->dev;
+  v.qcap = queue_capacity;
+  v.dcap = result_capacity;
+  v.max_iter = k->max_iter;
+  v.grid = std::max(1, sms) * 8;
+  v.req = (const fcgno_serve_request*)dm;
+  v.res = (fcgno_serve_result*)(dm + o_res);
+  v.req_tail = (const unsigned long long*)(dm + o_ctr);
+  v.req_head_pub = (unsigned long long*)(dm + o_ctr + 64);
+  v.res_head = (const unsigned long long*)(dm + o_ctr + 128);
+  v.ctr = (unsigned long long*)dd;
+  v.count = (int*)(dd + o_cnt);
+  v.slot_req = (fcgno_serve_request*)(dd + o_sreq);
+  v.phase = (int*)(dd + o_ph);
+  v.list = (int*)(dd + o_list);
+  fcgno_op* op = k->op;
+  v.x = k->x;
+  v.b = k->b;
+  v.aE = op->aE;
+  v.aN = op->aN;
+  v.diag = op->diag;
+  v.logk = op->logk;
+  v.logk32 = op->logk32;
+  v.kinv = op->kinv;
+  k->srv = r;
+  drop_graph(op->ws);  // the next step captures the admission and retirement kernels too
+  return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_bucket_enqueue(fcgno_bucket_t k, const fcgno_serve_request* req) {
+  using namespace fcgno;
+  if (!k || !req || !k->srv || !req->k || !req->f || !req->x0 || !req->x_out) {
+    set_last_error("fcgno_bucket_enqueue: null argument or a bucket without fcgno_bucket_serve_enable");
+    return FCGNO_EINVAL;
+  }
+  ServeRings& r = *k->srv;
+  std::lock_guard<std::mutex> lk(r.mu);
+  const unsigned long long taken = __atomic_load_n(r.req_head, __ATOMIC_ACQUIRE);
+  if (r.host_tail - taken >= (unsigned long long)r.dev.qcap) {
+    set_last_error("fcgno_bucket_enqueue: queue full");
+    return FCGNO_ENOMEM;
+  }
+  r.req[r.host_tail % (unsigned long long)r.dev.qcap] = *req;
+  ++r.host_tail;
+  __atomic_store_n(r.req_tail, r.host_tail, __ATOMIC_RELEASE);  // publishes the descriptor
+  return FCGNO_OK;
+}
+
+extern "C" int fcgno_bucket_results(fcgno_bucket_t k, fcgno_serve_result* out, int max) {
+  using namespace fcgno;
+  if (!k || !out || !k->srv || max < 0) return -1;
+  ServeRings& r = *k->srv;
+  std::lock_guard<std::mutex> lk(r.mu);
+  int n = 0;
+  while (n < max) {
+    fcgno_serve_result* rec = r.res + r.host_head % (unsigned long long)r.dev.dcap;
+    const unsigned long long seq = __atomic_load_n(reinterpret_cast<unsigned long long*>(&rec->seq), __ATOMIC_ACQUIRE);
+    if (seq != r.host_head + 1) break;
+    out[n++] = *rec;
+    ++r.host_head;
+  }
+  if (n) __atomic_store_n(r.res_head, r.host_head, __ATOMIC_RELEASE);  // frees the records
+  return n;
+}
+
 extern "C" fcgno_status fcgno_bucket_destroy(fcgno_bucket_t k) {
   if (!k) return FCGNO_OK;
+  if (k->srv) {
+    cudaDeviceSynchronize();  // no step may still read the mapped queue
+    if (k->srv->mapped) cudaFreeHost(k->srv->mapped);
+    if (k->srv->device) cudaFree(k->srv->device);
+    delete k->srv;
+    k->srv = nullptr;
+  }
   if (k->op) fcgno_op_destroy(k->op);
   if (k->x) cudaFree(k->x);
   if (k->b) cudaFree(k->b);

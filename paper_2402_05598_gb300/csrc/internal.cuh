@@ -102,6 +102,27 @@ inline cudaError_t launch_chained(void (*kernel)(KArgs...), dim3 grid, dim3 bloc
 }
 
 // Per-instance solver status codes kept on the device (negative = still iterating).
+// Launches `kernel` as a chained link whose CTAs form clusters of `cluster_x` x 1 x 1.
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_chained_cluster(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                          cudaStream_t st, int cluster_x, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[2];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  attr[1].id = cudaLaunchAttributeClusterDimension;
+  attr[1].val.clusterDim.x = cluster_x;
+  attr[1].val.clusterDim.y = 1;
+  attr[1].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 2;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 constexpr int kRunning = -1;
 constexpr int kMaxWindow = 8;  // largest m_max supported
 
@@ -119,6 +140,7 @@ struct IterGraph {
   double tol = 0.0;
   const void* b = nullptr;
   const void* x = nullptr;
+  const void* serve = nullptr;  // device-driven serving hooks captured in the graph (or none)
   EventPairs traced;
 };
 
@@ -126,7 +148,7 @@ struct SolverWorkspace {
   int cap_B = 0, cap_n = 0, cap_slots = 0, cap_tiles = 0;
   cudaStream_t cs = nullptr;     // internal stream (graph capture needs a non-default stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  IterGraph graph;
+  IterGraph graph[2];       // replayed iterations: [0] wide, [1] narrow 16-bit preconditioner launches
   int* iter = nullptr;      // [1] device iteration counter
   double* r = nullptr;      // [B][n]
   double* w = nullptr;      // [B][n]  preconditioned residual
@@ -160,6 +182,7 @@ struct fcgno_op {
   double* diag = nullptr;  // [B][n] sum of the four face coefficients / h^2
   double* logk = nullptr;  // [B][n]
   float* logk32 = nullptr; // [B][n] (input of the 16-bit preconditioner)
+  double* kinv = nullptr;  // [B][n] 1 / k (output scale of models with output_scale 1)
   fcgno::SolverWorkspace ws;
   // Activations of the 16-bit preconditioner applied to this operator's batch. They belong to
   // the operator, not the model, so that solves of different operators with one model may
@@ -194,9 +217,36 @@ struct BlobLayout {
 };
 BlobLayout blob_layout(const fcgno_model_desc& d);
 
-// Face coefficients, diagonal and log k of `total` grid points (all instances or one slot).
-fcgno_status launch_assemble(int N, size_t n, size_t total, const double* k, double* aE, double* aN, double* diag,
-                             double* logk, float* logk32, cudaStream_t st);
+// Assembly of grid point x of one instance (Eq. (1)-(2), 5-point finite volumes): from that
+// instance's k ([N][N]) it writes, at element i of the operator's arrays, the east and north
+// face coefficients (harmonic mean of the two nodes' k for an interior face, k of the node for a
+// boundary face), the diagonal (sum of the four faces), all scaled by 1/h^2, log k (FP64 and
+// FP32) and 1/k. Each interior face is formed with the (lower node, upper node) argument order,
+// so that the coupling seen from both sides is bit-identical and A is exactly symmetric.
+__device__ __forceinline__ double harmonic_mean(double a, double b) { return 2.0 * a * b / (a + b); }
+__device__ __forceinline__ void assemble_point(int N, int x, const double* __restrict__ kb, size_t i,
+                                               double* __restrict__ aE, double* __restrict__ aN,
+                                               double* __restrict__ diag, double* __restrict__ logk,
+                                               float* __restrict__ logk32, double* __restrict__ kinv) {
+  const int q = x / N, p = x - q * N;
+  const double kP = kb[x];
+  const double inv_h2 = (double)(N + 1) * (double)(N + 1);
+  const double e = (p < N - 1) ? harmonic_mean(kP, kb[x + 1]) : kP;
+  const double w = (p > 0) ? harmonic_mean(kb[x - 1], kP) : kP;
+  const double nn = (q < N - 1) ? harmonic_mean(kP, kb[x + N]) : kP;
+  const double s = (q > 0) ? harmonic_mean(kb[x - N], kP) : kP;
+  aE[i] = e * inv_h2;
+  aN[i] = nn * inv_h2;
+  diag[i] = (e + w + nn + s) * inv_h2;
+  const double lk = log(kP);
+  logk[i] = lk;
+  logk32[i] = (float)lk;
+  kinv[i] = 1.0 / kP;
+}
+
+// Face coefficients, diagonal, log k and 1/k of `total` grid points (all instances or one slot)
+// into the operator's arrays starting at element `off`.
+fcgno_status launch_assemble(const fcgno_op* op, size_t off, size_t total, const double* k, cudaStream_t st);
 // Stencil matvec y = A x for all instances (FP64).
 fcgno_status launch_apply_A(const fcgno_op* op, const double* x, double* y, cudaStream_t st);
 
@@ -205,8 +255,12 @@ fcgno_status launch_apply_A(const fcgno_op* op, const double* x, double* y, cuda
 // active; an instance is skipped when active[b] >= 0).
 fcgno_status no_apply_simt(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms,
                            const int* active, double* z, bool fp64, cudaStream_t st);
+// narrow: launch the synthesis with narrower grid-column chunks (more blocks per instance,
+// shorter serial chains), for launches in which few instances are still active.
 fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms,
-                         const int* active, double* z, bool fp16, cudaStream_t st);
+                         const int* active, double* z, bool fp16, cudaStream_t st, bool narrow = false);
+// Whether the narrow launch shape differs from the wide one for this grid and model.
+bool tc_has_narrow(int N, const fcgno_model_desc& d);
 // Whether the 16-bit (tensor-core) preconditioner supports model shape d on an N x N grid,
 // and the rule in words (for error messages). Host-only.
 bool tc_shape_supported(int N, const fcgno_model_desc& d);

@@ -346,14 +346,14 @@ __global__ void synthesis_q_pointwise_kernel(int N, int C, int Ky, const int* __
   out[oi] = activate ? act_gelu<T>(acc) : acc;
 }
 
-// z[b][x] = h^2 rms * (p2 . GELU(P1 v + p1) + p2b) (hh = h^2); optional saves of the
-// decoder's pre-activation and GELU output.
+// z[b][x] = h^2 rms * (p2 . GELU(P1 v + p1) + p2b) (hh = h^2), times 1/k[b][x] when kinv is
+// given (output_scale 1); optional saves of the decoder's pre-activation and GELU output.
 template <typename T>
 __global__ void project_kernel(size_t n, int C, int Cp, const int* __restrict__ active, const T* __restrict__ v,
                                const T* __restrict__ P1, const T* __restrict__ p1, const T* __restrict__ p2,
                                const T* __restrict__ p2b, const double* __restrict__ rms, double hh,
-                               double* __restrict__ z, T* __restrict__ asave, T* __restrict__ gsave,
-                               double* __restrict__ ztsave) {
+                               const double* __restrict__ kinv, double* __restrict__ z, T* __restrict__ asave,
+                               T* __restrict__ gsave, double* __restrict__ ztsave) {
   extern __shared__ unsigned char smraw[];
   T* P1s = reinterpret_cast<T*>(smraw);  // Cp*C
   for (int t = threadIdx.x; t < Cp * C; t += blockDim.x) P1s[t] = P1[t];
@@ -376,7 +376,8 @@ __global__ void project_kernel(size_t n, int C, int Cp, const int* __restrict__ 
     zt += p2[h] * g;
   }
   if (ztsave) ztsave[(size_t)b * n + x] = (double)zt;
-  z[(size_t)b * n + x] = rms[b] * hh * (double)zt;
+  const double sc = rms[b] * hh;
+  z[(size_t)b * n + x] = (kinv ? sc * kinv[(size_t)b * n + x] : sc) * (double)zt;
 }
 
 // ------------------------------------ host: forward ------------------------------------
@@ -520,7 +521,8 @@ static fcgno_status forward_simt(fcgno_model* m, const fcgno_op* op, const T* wb
   const size_t smem = (size_t)Cp * C * sizeof(T);
   project_kernel<T><<<dim3(ceil_div(n, 128), B), 128, smem, st>>>(n, C, Cp, active, cur, W.proj1_w, W.proj1_b,
                                                                    W.proj2_w, W.proj2_b, rms,
-                                                                   1.0 / ((double)(N + 1) * (N + 1)), z,
+                                                                   1.0 / ((double)(N + 1) * (N + 1)),
+                                                                   d.output_scale ? op->kinv : nullptr, z,
                                                                    tr ? (T*)tr->apre : nullptr,
                                                                    tr ? (T*)tr->ghid : nullptr, ztsave);
   FCGNO_LAUNCHED();
@@ -634,16 +636,18 @@ __global__ void loss_value_kernel(int B, const double* __restrict__ norms, float
   *loss = (float)(s / B);
 }
 
-// dL/dzt[b][x] = h^2 rms_b * (1/B) * (A d)_x / (||d|| ||e||)   (zt = z / (h^2 rms); A d -> d for
-// the 2-norm)
+// dL/dzt[b][x] = s_b(x) * (1/B) * (A d)_x / (||d|| ||e||) with s = h^2 rms_b (times 1/k[b][x]
+// when kinv is given) the output scale z = s zt; A d -> d for the 2-norm
 template <typename T>
 __global__ void dzt_kernel(int B, size_t n, double hh, const double* __restrict__ Ad,
-                           const double* __restrict__ norms, const double* __restrict__ rms, T* __restrict__ gzt) {
+                           const double* __restrict__ norms, const double* __restrict__ rms,
+                           const double* __restrict__ kinv, T* __restrict__ gzt) {
   const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= (size_t)B * n) return;
   const int b = (int)(i / n);
   const double den = norms[2 * b] * norms[2 * b + 1];
-  gzt[i] = (den > 0.0) ? (T)(hh * rms[b] * Ad[i] / (den * B)) : (T)0;
+  const double sc = kinv ? hh * rms[b] * kinv[i] : hh * rms[b];
+  gzt[i] = (den > 0.0) ? (T)(sc * Ad[i] / (den * B)) : (T)0;
 }
 
 // Decoder backward: ga[x][h] = gzt[x] p2[h] GELU'(a[x][h]); gv[x][c] = sum_h ga[x][h] P1[h][c].
@@ -829,7 +833,7 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
   tw_ptrs<T>(m->ws->tw, tw1, tw2);
   T* gzt = (T*)t.gz;
   dzt_kernel<T><<<ceil_div(pts, 256), 256, 0, st>>>(B, n, 1.0 / ((double)(N + 1) * (N + 1)), Ad, t.lossb, t.rms,
-                                                    gzt);
+                                                    m->desc.output_scale ? op->kinv : nullptr, gzt);
   FCGNO_LAUNCHED();
   // decoder: proj2 grads (A = gzt [pts][1], V = GELU(a) [pts][Cp])
   FCGNO_TRY(outer_reduce<T>(pts, 1, Cp, gzt, (const T*)t.ghid, (T*)t.partials, grad + BL.proj2_w,

@@ -916,6 +916,7 @@ struct SynArgs {
   const float* p2b;
   const double* rms;
   double hh;              // h^2 output scale
+  const double* kinv;     // [B][N][N] 1/k, the pointwise output scale of output_scale 1 (else null)
   double* z;              // [B][N][N]
   int* err;
 };
@@ -1266,7 +1267,9 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
             p = p0 + t % PC;
             q = (t / PC) * 128 + own_q;
           }
-          a.z[((size_t)b * N + q) * N + p] = a.rms[b] * a.hh * (double)(a.p2b[0] + zpart[0][m] + zpart[1][m]);
+          const size_t zi = ((size_t)b * N + q) * N + p;
+          const double sc = a.kinv ? a.rms[b] * a.hh * a.kinv[zi] : a.rms[b] * a.hh;
+          a.z[zi] = sc * (double)(a.p2b[0] + zpart[0][m] + zpart[1][m]);
         }
       }
     }
@@ -1297,11 +1300,30 @@ static void synthesis_rings(const TcGeom& g, int& din, int& dout) {
   din = kSynMaxIn;
 }
 
+// The synthesis geometry of the narrow launch shape: 16-column chunks where the wide shape uses
+// 32. The H table's 16-column chunk images are the halves of its 32-column images (rows are
+// grouped by 8 with a fixed stride), so both shapes read the same table.
+static TcGeom narrow_geom(TcGeom g) {
+  if (g.SPC <= 16) return g;
+  g.SPC = 16;
+  while (g.SPC % g.PT != 0) g.SPC *= 2;
+  g.snchunks = g.N / g.SPC;
+  g.KB = round_up(g.SPC * 2 * g.M, 16) + 16;
+  return g;
+}
+
+bool tc_has_narrow(int N, const fcgno_model_desc& d) {
+  if (!tc_shape_supported(N, d)) return false;
+  const TcGeom g = make_geom(N, d.width, d.modes);
+  return narrow_geom(g).SPC != g.SPC;
+}
+
 template <int C>
 static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms, const int* active,
-                           double* z, bool fp16, cudaStream_t st) {
+                           double* z, bool fp16, cudaStream_t st, bool narrow) {
   const fcgno_model_desc& d = m->desc;
   const TcGeom g = make_geom(op->N, C, d.modes);
+  const TcGeom gs = narrow ? narrow_geom(g) : g;  // synthesis geometry
   const uint64_t gen0 = m->gen;
   FCGNO_TRY(ensure_prec(m, fp16, st));
   TcTables* tab = nullptr;
@@ -1349,8 +1371,17 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   }
   FCGNO_LAUNCHED();
   int din, dout;
-  synthesis_rings(g, din, dout);
-  const size_t sa = analysis_smem(g), ss = synthesis_bytes(g, g.SPC, din, dout), sm = mix_smem(g);
+  synthesis_rings(gs, din, dout);
+  const size_t sa = analysis_smem(g), ss = synthesis_bytes(gs, gs.SPC, din, dout), sm = mix_smem(g);
+  // the limit covers both launch shapes, so that the other shape's first (captured) launch
+  // needs no attribute change
+  size_t ss_limit = ss;
+  {
+    const TcGeom go = narrow ? g : narrow_geom(g);
+    int di2, do2;
+    synthesis_rings(go, di2, do2);
+    ss_limit = std::max(ss_limit, synthesis_bytes(go, go.SPC, di2, do2));
+  }
   // raise the dynamic shared-memory limit only when a larger plan appears (not a stream
   // operation; the first solve iteration runs eagerly, before any graph capture)
   // (the shared-memory carveout is pinned to its maximum so that two blocks of each kernel
@@ -1367,7 +1398,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     return e;
   };
   FCGNO_CUDA_TRY(raise((const void*)tc_analysis_kernel<C>, sa, set_sa));
-  FCGNO_CUDA_TRY(raise((const void*)tc_synthesis_kernel<C>, ss, set_ss));
+  FCGNO_CUDA_TRY(raise((const void*)tc_synthesis_kernel<C>, ss_limit, set_ss));
   FCGNO_CUDA_TRY(raise((const void*)tc_mix_kernel<C>, sm, set_sm));
   uint16_t* cur = T.va;
   uint16_t* nxt = T.vb;
@@ -1389,13 +1420,13 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     SynArgs s{};
     s.vin = cur;
     s.vout = nxt;
-    s.g = g;
+    s.g = gs;
     s.B = B;
     s.bf16 = bf16;
     // hidden layers store straight from the epilogue: their input ring also takes the
     // output slots' bytes (same shared-memory size)
     const bool last = l == d.layers - 1;
-    const size_t slot_in = (size_t)128 * C * 2 + (g.N >= 128 ? (size_t)128 * g.KSYN * 2 : 0);
+    const size_t slot_in = (size_t)128 * C * 2 + (gs.N >= 128 ? (size_t)128 * gs.KSYN * 2 : 0);
     s.din = last ? din : std::min<int>(kSynMaxIn, (int)(((size_t)din * slot_in + (size_t)dout * 128 * C * 2) / slot_in));
     s.dout = last ? dout : 0;
     s.active = active;
@@ -1412,11 +1443,12 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     s.p2b = m->w32 + BL.proj2_b;
     s.rms = rms;
     s.hh = 1.0 / ((double)(op->N + 1) * (op->N + 1));
+    s.kinv = d.output_scale ? op->kinv : nullptr;
     s.z = z;
     s.err = T.err;
     {
       TraceScope ts("tc_synthesis", st);
-      FCGNO_CUDA_TRY(launch_chained(tc_synthesis_kernel<C>, dim3(g.snchunks, B), dim3(kSynThreads), ss, st, s));
+      FCGNO_CUDA_TRY(launch_chained(tc_synthesis_kernel<C>, dim3(gs.snchunks, B), dim3(kSynThreads), ss, st, s));
     }
     FCGNO_LAUNCHED();
     std::swap(cur, nxt);
@@ -1442,14 +1474,14 @@ const char* tc_shape_rule() {
 }
 
 fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms, const int* active,
-                         double* z, bool fp16, cudaStream_t st) {
+                         double* z, bool fp16, cudaStream_t st, bool narrow) {
   const fcgno_model_desc& d = m->desc;
   if (!tc_shape_supported(op->N, d)) {
     set_last_error(tc_shape_rule());
     return FCGNO_EINVAL;
   }
-  if (d.width == 16) return run_tc<16>(m, op, r, rms, active, z, fp16, st);
-  return run_tc<32>(m, op, r, rms, active, z, fp16, st);
+  if (d.width == 16) return run_tc<16>(m, op, r, rms, active, z, fp16, st, narrow);
+  return run_tc<32>(m, op, r, rms, active, z, fp16, st, narrow);
 }
 
 }  // namespace fcgno

@@ -12,31 +12,15 @@
 
 namespace fcgno {
 
-__device__ __forceinline__ double harmonic(double a, double b) { return 2.0 * a * b / (a + b); }
-
 __global__ void assemble_kernel(int N, size_t n, size_t total, const double* __restrict__ k,
                                 double* __restrict__ aE, double* __restrict__ aN,
-                                double* __restrict__ diag, double* __restrict__ logk, float* __restrict__ logk32) {
+                                double* __restrict__ diag, double* __restrict__ logk, float* __restrict__ logk32,
+                                double* __restrict__ kinv) {
   size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
   const size_t b = i / n;
   const int x = (int)(i - b * n);
-  const int q = x / N, p = x - q * N;
-  const double* kb = k + b * n;
-  const double kP = kb[x];
-  const double inv_h2 = (double)(N + 1) * (double)(N + 1);
-  // each interior face is formed once with the (lower node, upper node) argument order so
-  // that the coupling seen from both sides is bit-identical
-  const double e = (p < N - 1) ? harmonic(kP, kb[x + 1]) : kP;
-  const double w = (p > 0) ? harmonic(kb[x - 1], kP) : kP;
-  const double nn = (q < N - 1) ? harmonic(kP, kb[x + N]) : kP;
-  const double s = (q > 0) ? harmonic(kb[x - N], kP) : kP;
-  aE[i] = e * inv_h2;
-  aN[i] = nn * inv_h2;
-  diag[i] = (e + w + nn + s) * inv_h2;
-  const double lk = log(kP);
-  logk[i] = lk;
-  logk32[i] = (float)lk;
+  assemble_point(N, x, k + b * n, i, aE, aN, diag, logk, logk32, kinv);
 }
 
 __global__ void apply_A_kernel(int N, size_t n, size_t total, const double* __restrict__ aE,
@@ -71,9 +55,10 @@ fcgno_status launch_apply_A(const fcgno_op* op, const double* x, double* y, cuda
   return FCGNO_OK;
 }
 
-fcgno_status launch_assemble(int N, size_t n, size_t total, const double* k, double* aE, double* aN, double* diag,
-                             double* logk, float* logk32, cudaStream_t st) {
-  assemble_kernel<<<ceil_div(total, 256), 256, 0, st>>>(N, n, total, k, aE, aN, diag, logk, logk32);
+fcgno_status launch_assemble(const fcgno_op* op, size_t off, size_t total, const double* k, cudaStream_t st) {
+  assemble_kernel<<<ceil_div(total, 256), 256, 0, st>>>(op->N, op->n, total, k, op->aE + off, op->aN + off,
+                                                        op->diag + off, op->logk + off, op->logk32 + off,
+                                                        op->kinv + off);
   FCGNO_LAUNCHED();
   return FCGNO_OK;
 }
@@ -88,8 +73,8 @@ fcgno_status launch_rms(const double* r, int B, size_t n, double* rms, cudaStrea
 
 using namespace fcgno;
 
-// An assembled operator holds aE, aN, the diagonal and log k in FP64 and log k in FP32.
-size_t fcgno::operator_bytes(size_t n, int B) { return 4 * n * B * sizeof(double) + n * B * sizeof(float); }
+// An assembled operator holds aE, aN, the diagonal, log k and 1/k in FP64 and log k in FP32.
+size_t fcgno::operator_bytes(size_t n, int B) { return 5 * n * B * sizeof(double) + n * B * sizeof(float); }
 
 extern "C" fcgno_status fcgno_assemble(int N, int batch, const double* k, void* stream, fcgno_op_t* out) {
   if (N < 2 || batch < 1 || !k || !out) {
@@ -105,24 +90,27 @@ extern "C" fcgno_status fcgno_assemble(int N, int batch, const double* k, void* 
   const size_t bytes = op->n * batch * sizeof(double);
   if (cudaMalloc(&op->aE, bytes) != cudaSuccess || cudaMalloc(&op->aN, bytes) != cudaSuccess ||
       cudaMalloc(&op->diag, bytes) != cudaSuccess || cudaMalloc(&op->logk, bytes) != cudaSuccess ||
-      cudaMalloc(&op->logk32, bytes / 2) != cudaSuccess) {
+      cudaMalloc(&op->logk32, bytes / 2) != cudaSuccess || cudaMalloc(&op->kinv, bytes) != cudaSuccess) {
     cudaGetLastError();
     fcgno_op_destroy(op);
     set_last_error("fcgno_assemble: out of device memory");
     return FCGNO_ENOMEM;
   }
-  const size_t total = op->n * batch;
-  assemble_kernel<<<ceil_div(total, 256), 256, 0, st>>>(N, op->n, total, k, op->aE, op->aN, op->diag, op->logk,
-                                                        op->logk32);
-  g_launches.fetch_add(1, std::memory_order_relaxed);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    set_last_error(std::string("assemble launch: ") + cudaGetErrorString(e));
+  const fcgno_status rc = launch_assemble(op, 0, op->n * batch, k, st);
+  if (rc != FCGNO_OK) {
     fcgno_op_destroy(op);
-    return FCGNO_ECUDA;
+    return rc;
   }
   *out = op;
   return FCGNO_OK;
+}
+
+extern "C" fcgno_status fcgno_reassemble(fcgno_op_t op, const double* k, void* stream) {
+  if (!op || !k) {
+    set_last_error("fcgno_reassemble: null operator or k");
+    return FCGNO_EINVAL;
+  }
+  return launch_assemble(op, 0, op->n * op->B, k, (cudaStream_t)stream);
 }
 
 extern "C" fcgno_status fcgno_apply_A(fcgno_op_t op, const double* x, double* y, void* stream) {

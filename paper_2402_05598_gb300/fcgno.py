@@ -22,8 +22,10 @@ LOSS = {"energy": FCGNO_LOSS_ENERGY, "l2": FCGNO_LOSS_L2}
 
 
 class fcgno_model_desc(Structure):
-    """fcgno_model_desc of the C ABI: width C, layers L, modes M, proj_width C_p, in_channels (2)."""
-    _fields_ = [("width", c_int), ("layers", c_int), ("modes", c_int), ("proj_width", c_int), ("in_channels", c_int)]
+    """fcgno_model_desc of the C ABI: width C, layers L, modes M, proj_width C_p, in_channels (2),
+    output_scale (0: h^2 rms(r); 1: h^2 rms(r) / k)."""
+    _fields_ = [("width", c_int), ("layers", c_int), ("modes", c_int), ("proj_width", c_int), ("in_channels", c_int),
+                ("output_scale", c_int)]
 
 
 class fcgno_solve_opts(Structure):
@@ -35,6 +37,16 @@ class fcgno_solve_opts(Structure):
 class fcgno_solve_info(Structure):
     """fcgno_solve_info of the C ABI: per-instance iterations, status, relative residual, ||r_0||."""
     _fields_ = [("iters", c_int32), ("status", c_int32), ("relres", c_double), ("r0norm", c_double)]
+
+
+class fcgno_serve_request(Structure):
+    """fcgno_serve_request of the C ABI: device pointers k, f, x0, x_out ([N][N] float64) and a tag."""
+    _fields_ = [("k", c_void_p), ("f", c_void_p), ("x0", c_void_p), ("x_out", c_void_p), ("tag", c_uint64)]
+
+
+class fcgno_serve_result(Structure):
+    """fcgno_serve_result of the C ABI: tag, status, iterations, relative residual, publication number."""
+    _fields_ = [("tag", c_uint64), ("status", c_int32), ("iters", c_int32), ("relres", c_double), ("seq", c_uint64)]
 
 
 class FcgnoError(RuntimeError):
@@ -51,6 +63,7 @@ def _load():
     P = c_void_p
     sig = {
         "fcgno_assemble": (c_int, [c_int, c_int, P, P, POINTER(P)]),
+        "fcgno_reassemble": (c_int, [P, P, P]),
         "fcgno_op_destroy": (c_int, [P]),
         "fcgno_apply_A": (c_int, [P, P, P, P]),
         "fcgno_weight_count": (c_size_t, [POINTER(fcgno_model_desc)]),
@@ -79,6 +92,9 @@ def _load():
         "fcgno_bucket_poll": (c_int, [P, P, P, P, P]),
         "fcgno_bucket_take": (c_int, [P, c_int, P, P]),
         "fcgno_bucket_destroy": (c_int, [P]),
+        "fcgno_bucket_serve_enable": (c_int, [P, c_int, c_int]),
+        "fcgno_bucket_enqueue": (c_int, [P, POINTER(fcgno_serve_request)]),
+        "fcgno_bucket_results": (c_int, [P, POINTER(fcgno_serve_result), c_int]),
         "fcgno_wait_selftest": (c_int, [P, c_double, P]),
         "fcgno_trace_set": (c_int, [c_char_p]),
         "fcgno_trace_collect": (c_int, [POINTER(c_double), POINTER(c_uint64)]),
@@ -94,14 +110,14 @@ lib = _load()
 
 # Exported symbol names, in the order of include/fcgno.h.
 EXPORTS = [
-    "fcgno_assemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
+    "fcgno_assemble", "fcgno_reassemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
     "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
     "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_precision_supported", "fcgno_status_str",
     "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_wait_selftest", "fcgno_trace_set",
     "fcgno_trace_collect",
     "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
-    "fcgno_bucket_destroy",
+    "fcgno_bucket_destroy", "fcgno_bucket_serve_enable", "fcgno_bucket_enqueue", "fcgno_bucket_results",
 ]
 
 
@@ -176,9 +192,10 @@ def _stream(stream) -> int:
     return getattr(stream, "cuda_stream", stream)
 
 
-def make_desc(width=32, layers=4, modes=12, proj_width=None, in_channels=2) -> fcgno_model_desc:
+def make_desc(width=32, layers=4, modes=12, proj_width=None, in_channels=2, output_scale=0) -> fcgno_model_desc:
     """A fcgno_model_desc (proj_width defaults to width)."""
-    return fcgno_model_desc(width, layers, modes, proj_width if proj_width is not None else width, in_channels)
+    return fcgno_model_desc(width, layers, modes, proj_width if proj_width is not None else width, in_channels,
+                            output_scale)
 
 
 def weight_count(desc: fcgno_model_desc) -> int:
@@ -196,6 +213,11 @@ class Operator:
         self.handle = c_void_p()
         _check(lib.fcgno_assemble(self.N, self.B, _ptr(k), _stream(stream), ctypes.byref(self.handle)),
                "fcgno_assemble")
+
+    def reassemble(self, k, stream=None):
+        """fcgno_reassemble: new coefficient fields (same N and batch) into this operator."""
+        assert k.dtype == __import__("torch").float64 and tuple(k.shape) == (self.B, self.N, self.N)
+        _check(lib.fcgno_reassemble(self.handle, _ptr(k), _stream(stream)), "fcgno_reassemble")
 
     def apply(self, x, y, stream=None):
         """fcgno_apply_A: y = A x for every instance."""
@@ -362,6 +384,37 @@ class Bucket:
         """fcgno_bucket_take: copy the slot's iterate to x_out (optional) and free the slot."""
         _check(lib.fcgno_bucket_take(self.handle, int(slot), _ptr(x_out) if x_out is not None else None,
                                      _stream(stream)), "fcgno_bucket_take")
+
+    def serve_enable(self, queue_capacity=4096, result_capacity=4096):
+        """fcgno_bucket_serve_enable: admission and retirement move onto the device (a mapped
+        request queue and result ring); use enqueue/step/results from then on."""
+        _check(lib.fcgno_bucket_serve_enable(self.handle, int(queue_capacity), int(result_capacity)),
+               "fcgno_bucket_serve_enable")
+        self._res = (fcgno_serve_result * int(result_capacity))()
+        self._keep = {}
+
+    def enqueue(self, k, f, x0, x_out, tag) -> bool:
+        """fcgno_bucket_enqueue (host-only); False when the queue is full. The tensors are kept
+        alive here until the request's result has been collected."""
+        req = fcgno_serve_request(_ptr(k), _ptr(f), _ptr(x0), _ptr(x_out), int(tag))
+        code = lib.fcgno_bucket_enqueue(self.handle, ctypes.byref(req))
+        if code == FCGNO_ENOMEM:
+            return False
+        _check(code, "fcgno_bucket_enqueue")
+        self._keep[int(tag)] = (k, f, x0, x_out)
+        return True
+
+    def results(self):
+        """fcgno_bucket_results (host-only): [(tag, status, iters, relres)] published since the last call."""
+        n = lib.fcgno_bucket_results(self.handle, self._res, len(self._res))
+        if n < 0:
+            raise FcgnoError(FCGNO_EINVAL, "fcgno_bucket_results")
+        out = []
+        for i in range(n):
+            r = self._res[i]
+            out.append((int(r.tag), int(r.status), int(r.iters), float(r.relres)))
+            self._keep.pop(int(r.tag), None)
+        return out
 
     def close(self):
         if self.handle:

@@ -23,6 +23,7 @@ Problem families
 """
 from __future__ import annotations
 
+import functools
 import math
 from dataclasses import dataclass
 
@@ -59,6 +60,7 @@ class ModelDesc:
     modes: int = 12
     proj_width: int = 32
     in_channels: int = 2
+    output_scale: int = 0  # 0: output times h^2 rms(r); 1: also divided by k at every grid point
 
     @property
     def kx(self) -> int:
@@ -143,7 +145,10 @@ def xavier_weights(desc: ModelDesc, seed: int = 0) -> np.ndarray:
     return blob.astype(np.float32)
 
 
+@functools.lru_cache(maxsize=16)
 def _sqrt_corr_1d(N: int, ell: float) -> np.ndarray:
+    """Symmetric square root of the 1-D correlation matrix of the interior nodes (cached: it
+    depends on N and ell only; callers must not modify it)."""
     h = 1.0 / (N + 1)
     x = (np.arange(N) + 1) * h
     d = x[:, None] - x[None, :]

@@ -198,3 +198,103 @@ class Server:
     def close(self):
         for b in self.buckets.values():
             b.close()
+
+
+class DeviceServer:
+    """Continuous batching with admission and retirement on the device
+    (``fcgno_bucket_serve_enable``): every iteration of every step retires the slots whose
+    solve stopped (their iterate copied into the request's output, then the result published)
+    and admits queued requests into free slots. The host only
+      1. appends every arrived request to its bucket's queue (mapped host memory, no CUDA call;
+         a full queue keeps the request waiting on the host),
+      2. keeps up to ``depth`` steps in flight on each bucket that has unfinished requests,
+      3. collects published results (mapped host memory) and completes their requests.
+    It never waits for a step. Latency = time the host reads the result - arrival time.
+    ``bucket_factory`` and ``cuda`` can be replaced by host-side fakes (tests)."""
+
+    def __init__(self, model, capacities: dict, prec="bf16", m_max=1, tol=1e-6, max_iter=400, iters_per_step=4,
+                 queue_capacity=None, depth=2, bucket_factory=None, cuda=None):
+        if cuda is None:
+            import torch
+            cuda = torch.cuda
+        self.cuda = cuda
+        bucket_factory = bucket_factory or F.Bucket
+        concurrent = prec in ("bf16", "fp16")
+        shared = cuda.Stream()
+        self.streams = {N: (cuda.Stream() if concurrent else shared) for N in capacities}
+        self.buckets = {}
+        for N, cap in capacities.items():
+            bk = bucket_factory(N, cap, model, prec=prec, m_max=m_max, tol=tol, max_iter=max_iter,
+                                iters_per_step=iters_per_step, stream=self.streams[N])
+            qcap = queue_capacity or max(64, 4 * cap)
+            bk.serve_enable(qcap, qcap + cap)
+            self.buckets[N] = bk
+        self.depth = depth
+        self.inflight = {N: deque() for N in capacities}
+
+    def run(self, requests: list, stats: ServeStats) -> ServeStats:
+        """Serves the requests (sorted by arrival) and returns latency statistics."""
+        cuda = self.cuda
+        pending = deque(sorted(requests, key=lambda r: r.arrival))
+        for s_ in set(self.streams.values()):
+            s_.wait_stream(cuda.current_stream())
+        waiting = {N: deque() for N in self.buckets}
+        queued = {N: 0 for N in self.buckets}    # enqueued, result not yet collected
+        by_tag = {}
+        t0 = time.perf_counter()
+        outstanding = len(pending)
+        while outstanding:
+            now = time.perf_counter() - t0
+            while pending and pending[0].arrival <= now:
+                r = pending.popleft()
+                waiting[r.N].append(r)
+            progressed = False
+            for N, bk in self.buckets.items():
+                w = waiting[N]
+                while w:
+                    r = w[0]
+                    try:
+                        ok = bk.enqueue(r.k, r.f, r.x0, r.out if r.out is not None else r.x0, r.rid)
+                    except F.FcgnoError as e:
+                        w.popleft()
+                        Server._complete(r, e.code, 0, 0.0, time.perf_counter() - t0, stats)
+                        stats.failed += 1
+                        outstanding -= 1
+                        continue
+                    if not ok:
+                        break
+                    w.popleft()
+                    by_tag[r.rid] = r
+                    queued[N] += 1
+                    progressed = True
+            for N, bk in self.buckets.items():
+                inf = self.inflight[N]
+                while inf and inf[0].query():
+                    inf.popleft()
+                if queued[N] > 0 and len(inf) < self.depth:
+                    bk.step(stream=self.streams[N])
+                    ev = cuda.Event()
+                    ev.record(self.streams[N])
+                    inf.append(ev)
+                    progressed = True
+            for N, bk in self.buckets.items():
+                res = bk.results()
+                if res:
+                    tnow = time.perf_counter() - t0
+                    for tag, st, it, rr in res:
+                        r = by_tag.pop(tag)
+                        Server._complete(r, st, it, rr, tnow, stats)
+                        queued[N] -= 1
+                        outstanding -= 1
+                    progressed = True
+            if not progressed:
+                time.sleep(2e-5 if any(queued.values()) else max(0.0, min(0.001, (pending[0].arrival - now)
+                                                                       if pending else 0.001)))
+        cuda.synchronize()
+        stats.wall_s = time.perf_counter() - t0
+        return stats
+
+    def close(self):
+        self.cuda.synchronize()
+        for b in self.buckets.values():
+            b.close()

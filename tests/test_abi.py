@@ -86,6 +86,8 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
     for N, B, k, out in ((1, 1, hp, h), (4, 0, hp, h), (4, 1, None, h), (4, 1, hp, None)):
         rejects(L.fcgno_assemble(N, B, k, None, ctypes.byref(out) if out is not None else None), "fcgno_assemble")
     rejects(L.fcgno_apply_A(None, hp, hp, None), "fcgno_apply_A")
+    rejects(L.fcgno_reassemble(None, hp, None), "fcgno_reassemble")
+    rejects(L.fcgno_reassemble(ctypes.c_void_p(1), None, None), "fcgno_reassemble")
     rejects(L.fcgno_model_create(ctypes.byref(F.make_desc(width=0)), w32.ctypes.data, None, ctypes.byref(h)),
             "fcgno_model_create")
     rejects(L.fcgno_model_create(ctypes.byref(F.make_desc()), None, None, ctypes.byref(h)), "fcgno_model_create")
@@ -124,6 +126,9 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
     rejects(L.fcgno_bucket_step(None, None), "fcgno_bucket_step")
     rejects(L.fcgno_bucket_poll(None, hp, hp, hp, None), "fcgno_bucket_poll")
     rejects(L.fcgno_bucket_take(None, 0, None, None), "fcgno_bucket_take")
+    rejects(L.fcgno_bucket_serve_enable(None, 16, 16), "fcgno_bucket_serve_enable")
+    rejects(L.fcgno_bucket_enqueue(None, None), "fcgno_bucket_enqueue")
+    assert L.fcgno_bucket_results(None, None, 4) == -1
     rejects(L.fcgno_wait_selftest(None, 1e-3, None), "fcgno_wait_selftest")
     rejects(L.fcgno_wait_selftest(ctypes.c_void_p(1), 0.0, None), "fcgno_wait_selftest")
     rejects(L.fcgno_wait_selftest(ctypes.c_void_p(1), 2.0, None), "fcgno_wait_selftest")

@@ -64,7 +64,7 @@ def test_large_solve_recursive_residual_is_the_true_residual(lib, dev, N, B, pre
         ref = O.fcg(lambda u: O.apply_A(k[0], u), lambda r: O.no_forward(P, desc, r, np.log(k[0])), f[0],
                     np.zeros((N, N)), 5, 6)
         assert rel(xs[0], ref["u"]) < 1e-10
-        elem_check(xs[0], ref["u"], 1e-10, ("fp64 iterate", N))
+        elem_check(xs[0], ref["u"], 1e-10, ("fp64 iterate", N), "global")
 
 
 def test_bf16_iterations_within_15_percent_of_fp64(lib, dev):

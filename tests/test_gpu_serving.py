@@ -153,3 +153,66 @@ def test_server_delivers_each_result_as_solved_alone(lib, dev):
         xa, ia, ra, sa = run_alone(lib, dev, model, r.N, 3400 + i, "bf16", 3, max_iter=24)
         assert r.iters == ia == 24 and r.status == sa == lib.FCGNO_ENOCONV
         assert np.array_equal(r.out.cpu().numpy(), xa), i
+
+
+def test_device_driven_serving_matches_solves_alone(lib, dev):
+    """Admission and retirement on the device (fcgno_bucket_serve_enable): requests of two grid
+    sizes, more than the slots, queued through the mapped queue while steps run; every result
+    equals the same request solved alone in a host-driven bucket, bit for bit (the admission
+    assembles and forms r_0 with the same arithmetic, and a slot's solve does not depend on
+    the others), and is published only after its x_out holds the iterate."""
+    import torch
+    from paper_2402_05598_gb300 import serve as S
+    C, M = 32, 12
+    desc = I.ModelDesc(width=C, layers=4, modes=M, proj_width=C, output_scale=1)
+    w = torch.from_numpy(I.xavier_weights(desc, 7)).to(dev)
+    model = lib.Model(lib.make_desc(C, 4, M, C, output_scale=1), w)
+    reqs = []
+    for i in range(9):
+        N = (64, 128)[i % 2]
+        k, f, x0 = dev_arrays(N, 3500 + i, dev)
+        out = torch.full((N, N), float("nan"), dtype=torch.float64, device=dev)
+        reqs.append(S.Request(i, 0.001 * i, N, k, f, x0, out=out))
+    srv = S.DeviceServer(model, {64: 2, 128: 2}, prec="bf16", max_iter=24, iters_per_step=8)
+    stats = srv.run(reqs, S.ServeStats())
+    srv.close()
+    assert stats.completed == len(reqs)
+    for i, r in enumerate(reqs):
+        xa, ia, ra, sa = run_alone(lib, dev, model, r.N, 3500 + i, "bf16", 3, max_iter=24)
+        assert r.iters == ia == 24 and r.status == lib.FCGNO_ENOCONV, (i, r.iters, r.status)
+        assert np.array_equal(r.out.cpu().numpy(), xa), i
+        assert r.relres == ra
+
+
+def test_device_driven_identity_solves_match_oracle_cg_and_queue_limits(lib, dev):
+    """Identity preconditioner through the device queue: each request converges on its own with
+    the oracle's CG iteration count (within 1 %) and true residual; a full queue refuses the
+    next request until the device has taken some."""
+    import torch
+    N = 24
+    bk = lib.Bucket(N, 2, None, prec="fp64", tol=1e-8, max_iter=5000, iters_per_step=8)
+    bk.serve_enable(3, 8)
+    probs = [dev_arrays(N, 3600 + i, dev) for i in range(4)]
+    outs = [torch.empty((N, N), dtype=torch.float64, device=dev) for _ in probs]
+    assert all(bk.enqueue(*probs[i], outs[i], i) for i in range(3))
+    assert not bk.enqueue(*probs[3], outs[3], 3)  # queue of 3 is full until a step takes requests
+    done = {}
+    pending3 = True
+    for _ in range(2000):
+        bk.step()
+        torch.cuda.synchronize()
+        for tag, st, it, rr in bk.results():
+            done[tag] = (st, it, rr)
+        if pending3 and bk.enqueue(*probs[3], outs[3], 3):
+            pending3 = False
+        if len(done) == 4:
+            break
+    assert len(done) == 4
+    for i in range(4):
+        kn, fn, x0n = (t.cpu().numpy() for t in probs[i])
+        st, it, rr = done[i]
+        ref = O.fcg(lambda u: O.apply_A(kn, u), lambda r: r, fn, x0n, 1, 5000, tol=1e-8)
+        assert st == lib.FCGNO_OK and abs(it - ref["iterations"]) <= max(2, ref["iterations"] // 100)
+        true = np.linalg.norm(fn - O.apply_A(kn, outs[i].cpu().numpy())) / np.linalg.norm(fn - O.apply_A(kn, x0n))
+        assert true < 1e-7 and rr <= 1e-8
+    bk.close()

@@ -365,15 +365,17 @@ def test_weight_blob_layout_and_xavier_bounds():
 
 
 # --------------------------------------------------------------------------- losses (Eq. 11-12)
-def test_pointwise_no_reduces_to_a_scalar_closed_form():
+@pytest.mark.parametrize("out_scale", [0, 1])
+def test_pointwise_no_reduces_to_a_scalar_closed_form(out_scale):
     """With every spectral block R_l = 0 and W_l = I the Fourier layers act node by node, so
     the whole preconditioner of Appendix A reduces to a scalar function of (r/rms, log k) at
     each node: encoder a r^ + b log k + c, GELU(u + b_l) on layers 1-3, u + b_4 on the last,
-    decoder s . GELU(P u + q) + t, times h^2 rms(r). Computed here node by node with
-    math.erf, it pins the encoder's channel order, which layers apply GELU, the biases, the
-    decoder and the output scale h^2 rms(r) with h = 1/(N+1)."""
+    decoder s . GELU(P u + q) + t, times h^2 rms(r) (and divided by the node's k for
+    output_scale 1). Computed here node by node with math.erf and math.exp, it pins the
+    encoder's channel order, which layers apply GELU, the biases, the decoder and the output
+    scale with h = 1/(N+1)."""
     N, C, Cp, L, M = 8, 4, 3, 4, 2
-    desc = I.ModelDesc(width=C, layers=L, modes=M, proj_width=Cp)
+    desc = I.ModelDesc(width=C, layers=L, modes=M, proj_width=Cp, output_scale=out_scale)
     off = I.weight_offsets(desc)
     blob = np.zeros(I.weight_count(desc), dtype=np.float32)
     rng = np.random.default_rng(11)
@@ -424,6 +426,8 @@ def test_pointwise_no_reduces_to_a_scalar_closed_form():
                     u = [g(x) for x in u]
             hid = [g(sum(P1[j][c] * u[c] for c in range(C)) + q[j]) for j in range(Cp)]
             want = h * h * rms * (sum(s2[j] * hid[j] for j in range(Cp)) + t)
+            if out_scale:
+                want /= math.exp(logk[qq, pp])
             assert abs(z[qq, pp] - want) <= 1e-12 * max(1.0, abs(want)) * h * h, (qq, pp, z[qq, pp], want)
 
 
@@ -570,12 +574,14 @@ def test_transform_adjoints_by_inner_products():
 
 
 @pytest.mark.parametrize("kind", ["energy", "l2"])
-def test_loss_gradient_matches_central_differences(kind):
+@pytest.mark.parametrize("out_scale", [0, 1])
+def test_loss_gradient_matches_central_differences(kind, out_scale):
     """The hand-written reverse mode of Eq. (11) (energy) and of the L2 ablation loss against
     central finite differences on every parameter group (random coordinates), FP64,
-    agreement to 1e-6 relative; the loss value equals the separately written loss."""
+    agreement to 1e-6 relative, for both output scales; the loss value equals the separately
+    written loss."""
     N = 10
-    desc = I.ModelDesc(width=4, layers=2, modes=3, proj_width=4)
+    desc = I.ModelDesc(width=4, layers=2, modes=3, proj_width=4, output_scale=out_scale)
     blob = I.xavier_weights(desc, 1).astype(np.float64)
     off = I.weight_offsets(desc)
     rng = np.random.default_rng(0)

@@ -190,3 +190,71 @@ def test_serve_loop_survives_host_injected_faults(S):
     late = [r for r in reqs if r.N == 128 and r.rid not in timed_out and r.done > min(
         reqs[i].done for i in timed_out)]
     assert late and all(r.status == 0 for r in late)
+
+
+class FakeServeBucket:
+    """Host model of a device-driven bucket: at every iteration boundary, slots whose request
+    reached its iteration count (stored in `k`) or max_iter publish a result and free up, then
+    free slots take queued requests in order; running slots advance one iteration."""
+    admitted = []
+
+    def __init__(self, N, cap, model, prec, m_max, tol, max_iter, iters_per_step, stream):
+        self.N, self.cap, self.max_iter, self.g = N, cap, max_iter, iters_per_step
+        self.slots = [None] * cap  # [tag, need, iters]
+
+    def serve_enable(self, qcap, dcap):
+        from collections import deque
+        self.qcap, self.queue, self.out = qcap, deque(), []
+
+    def enqueue(self, k, f, x0, x_out, tag):
+        if len(self.queue) >= self.qcap:
+            return False
+        self.queue.append((tag, int(k)))
+        return True
+
+    def step(self, stream=None):
+        for _ in range(self.g):
+            for i, s in enumerate(self.slots):
+                if s is not None and (s[2] >= s[1] or s[2] >= self.max_iter):
+                    self.out.append((s[0], 0 if s[2] >= s[1] else 4, s[2], 0.0))
+                    self.slots[i] = None
+            for i in range(self.cap):
+                if self.slots[i] is None and self.queue:
+                    tag, need = self.queue.popleft()
+                    FakeServeBucket.admitted.append((self.N, tag))
+                    self.slots[i] = [tag, need, 0]
+            for s in self.slots:
+                if s is not None:
+                    s[2] += 1
+
+    def results(self):
+        out, self.out = self.out, []
+        return out
+
+    def close(self):
+        pass
+
+
+def test_device_server_enqueues_collects_and_completes_each_request_once(S):
+    """The device-driven loop: requests are appended to their bucket's queue (a small queue
+    keeps some waiting on the host), steps are issued only while a bucket has unfinished
+    requests, and every result is collected once; admission is first in, first out per size."""
+    rng = np.random.default_rng(3)
+    FakeServeBucket.admitted = []
+    reqs = []
+    for i in range(80):
+        N = int(rng.choice((64, 128)))
+        need = int(rng.integers(1, 40)) if i != 11 else 10_000
+        reqs.append(S.Request(i, 0.0001 * i, N, need, i, ("x0", i)))
+    srv = S.DeviceServer(None, {64: 3, 128: 2}, prec="bf16", max_iter=200, iters_per_step=4, queue_capacity=4,
+                         bucket_factory=FakeServeBucket, cuda=FakeCuda)
+    stats = srv.run(reqs, S.ServeStats())
+    assert stats.completed == len(reqs) and len(stats.latencies_ms) == len(reqs)
+    assert reqs[11].status == 4 and reqs[11].iters == 200
+    for r in reqs:
+        assert r.done >= r.arrival
+        if r.rid != 11:
+            assert r.status == 0 and r.iters == r.k
+    for N in (64, 128):
+        order = [tag for n, tag in FakeServeBucket.admitted if n == N]
+        assert order == sorted(order) and len(order) == sum(1 for r in reqs if r.N == N)
