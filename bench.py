@@ -258,7 +258,8 @@ SERVE_SIGMAS = (0.5, 1.0, 2.0)
 
 
 def run_serving(args, model, desc_np, dev, rate, n_req, budget_gb=80.0):
-    """Serving stream of the configured mix: exponential inter-arrival times (mean 1/rate,
+    """Serving stream of the configured mix through the device-driven server (admission and
+    retirement on the device every iteration): exponential inter-arrival times (mean 1/rate,
     seed 5), grid sizes drawn with the configured probabilities, sigma uniform in
     {0.5, 1, 2}, ell = 0.1; every request has its own problem (k, f iid N(0,1), u_0 iid
     N(0,1), seed 50000 + request index), generated and made resident before the run. Bucket
@@ -287,10 +288,11 @@ def run_serving(args, model, desc_np, dev, rate, n_req, budget_gb=80.0):
     m = args.serve_m
     mdesc = F.make_desc(WIDTH, LAYERS, MODES, WIDTH, output_scale=args.output_scale)
     caps = S.plan_capacities(SERVE_SIZES, int(budget_gb * 2**30), m, mdesc, args.prec, max_slots=1 << 16)
-    srv = S.Server(model, caps, prec=args.prec, m_max=m, tol=TOL, max_iter=args.max_iter, iters_per_step=8)
+    srv = S.DeviceServer(model, caps, prec=args.prec, m_max=m, tol=TOL, max_iter=args.max_iter, iters_per_step=8)
     # warm every bucket once (first steps run eagerly and allocate), outside the measurement
-    warm = [S.Request(-1, 0.0, N, *(torch.from_numpy(a).to(dev) for a in (*I.make_problem(N, 1), np.zeros((N, N)))))
-            for N in sizes]
+    warm = [S.Request(1_000_000_000 + j, 0.0, N,
+                      *(torch.from_numpy(a).to(dev) for a in (*I.make_problem(N, 1), np.zeros((N, N)))))
+            for j, N in enumerate(sizes)]
     srv.run(warm, S.ServeStats())
     stats = S.ServeStats(offered_rate=rate)
     stats.bucket_bytes = sum(cap * S.slot_bytes(N, m, mdesc, args.prec) for N, cap in caps.items())
@@ -350,12 +352,15 @@ def run_transfer(args, model, dev, flush, stream):
                     return fn
 
                 if label == "all":
-                    ms, res = timed_steps(step("bf16", args.transfer_max_iter), 1, 1, flush, stream)
+                    ms, res = timed_steps(step("bf16", args.transfer_max_iter), 1, 1, flush, stream,
+                                          warm_fn=step("bf16", 16))
                     cell["bf16"] = solve_summary(ms, res, F)
-                    ms, res = timed_steps(step("fp64", 20000, jac=4), 1, 1, flush, stream)
+                    ms, res = timed_steps(step("fp64", 20000, jac=4), 1, 1, flush, stream,
+                                          warm_fn=step("fp64", 64, jac=4))
                     cell["jacobi4_pcg"] = solve_summary(ms, res, F)
                 else:
-                    ms, res = timed_steps(step("bf16", args.transfer_max_iter), 1, 1, flush, stream)
+                    ms, res = timed_steps(step("bf16", args.transfer_max_iter), 1, 1, flush, stream,
+                                          warm_fn=step("bf16", 16))
                     cell["bf16_subset"] = solve_summary(ms, res, F)
                     cap = int(1.3 * cell["bf16_subset"]["iterations"]["max"]) + 16
                     ms, res = timed_steps(step("fp64", cap), 1, 0, flush, stream)
@@ -431,26 +436,26 @@ def run_large(args, dev, flush, stream):
         op = F.Operator(k)
         x = torch.empty_like(u0)
 
-        def bf16_step():
+        def bf16_step(cap=None):
             op.reassemble(k)
             x.copy_(u0)
-            return F.solve(op, model, f, x, tol=1e-8, m_max=5, max_iter=args.large_max_iter, prec="bf16",
+            return F.solve(op, model, f, x, tol=1e-8, m_max=5, max_iter=cap or args.large_max_iter, prec="bf16",
                            check_every=16)
 
-        def jac_step():
+        def jac_step(cap=None):
             op.reassemble(k)
             x.copy_(u0)
-            return F.solve_jacobi(op, 4, f, x, tol=1e-8, m_max=1, max_iter=50000, check_every=64)
+            return F.solve_jacobi(op, 4, f, x, tol=1e-8, m_max=1, max_iter=cap or 50000, check_every=64)
 
         cell = {}
-        ms, res = timed_steps(bf16_step, 1, 1, flush, stream)
+        ms, res = timed_steps(bf16_step, 1, 1, flush, stream, warm_fn=lambda: bf16_step(32))
         cell["bf16"] = solve_summary(ms, res, F)
         # the true residual of the returned iterates, from the library's own stencil
         Ax = torch.empty_like(x)
         op.apply(x, Ax)
         r_true = (f - Ax).flatten(1).norm(dim=1) / (f - _apply(op, u0)).flatten(1).norm(dim=1)
         cell["bf16"]["true_relres_max"] = float(r_true.max())
-        ms, res = timed_steps(jac_step, 1, 1, flush, stream)
+        ms, res = timed_steps(jac_step, 1, 1, flush, stream, warm_fn=lambda: jac_step(128))
         cell["jacobi4_pcg"] = solve_summary(ms, res, F)
         out[f"{N}x{B}"] = cell
         del op
@@ -464,12 +469,13 @@ def _apply(op, u):
     return y
 
 
-def timed_steps(fn, steps, warmup, flush, stream):
-    """Runs fn() `warmup` times, then `steps` times with L2 flushed before each, timing each
-    call with CUDA events on `stream`. Returns (per-step ms, per-step results)."""
+def timed_steps(fn, steps, warmup, flush, stream, warm_fn=None):
+    """Runs `warm_fn` (default fn) `warmup` times, then fn() `steps` times with L2 flushed
+    before each, timing each call with CUDA events on `stream`. Returns (per-step ms,
+    per-step results)."""
     import torch
     for _ in range(warmup):
-        fn()
+        (warm_fn or fn)()
     torch.cuda.synchronize()
     ms, res = [], []
     for s_ in range(steps):

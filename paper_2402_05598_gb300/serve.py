@@ -213,7 +213,8 @@ class DeviceServer:
     ``bucket_factory`` and ``cuda`` can be replaced by host-side fakes (tests)."""
 
     def __init__(self, model, capacities: dict, prec="bf16", m_max=1, tol=1e-6, max_iter=400, iters_per_step=4,
-                 queue_capacity=None, depth=2, bucket_factory=None, cuda=None):
+                 queue_capacity=None, depth=2, bucket_factory=None, cuda=None, stall_s=120.0):
+        self.stall_s = stall_s
         if cuda is None:
             import torch
             cuda = torch.cuda
@@ -243,8 +244,12 @@ class DeviceServer:
         by_tag = {}
         t0 = time.perf_counter()
         outstanding = len(pending)
+        last_result = t0
         while outstanding:
             now = time.perf_counter() - t0
+            if any(queued.values()) and time.perf_counter() - last_result > self.stall_s:
+                raise RuntimeError(f"serving: no result for {self.stall_s} s with requests queued: "
+                                   f"queued={queued}, in flight={ {N: len(v) for N, v in self.inflight.items()} }")
             while pending and pending[0].arrival <= now:
                 r = pending.popleft()
                 waiting[r.N].append(r)
@@ -280,7 +285,8 @@ class DeviceServer:
             for N, bk in self.buckets.items():
                 res = bk.results()
                 if res:
-                    tnow = time.perf_counter() - t0
+                    last_result = time.perf_counter()
+                    tnow = last_result - t0
                     for tag, st, it, rr in res:
                         r = by_tag.pop(tag)
                         Server._complete(r, st, it, rr, tnow, stats)
