@@ -119,6 +119,12 @@ fcgno_status fcgno_op_destroy(fcgno_op_t op);
 /* y = A x for every instance (x, y: [batch][N][N], may not alias).
  * Errors: EINVAL for a NULL op, x or y, or x == y. */
 fcgno_status fcgno_apply_A(fcgno_op_t op, const double* x, double* y, void* stream);
+/* Training pairs for residuals that are not Krylov vectors (the random-residual ablation of
+ * Section 3.5, Eq. (11) in error form): r_out = b - A u and e_out = u_star - u for every
+ * instance (all [batch][N][N], device; u_star solves A u_star = b). Asynchronous.
+ * Errors: EINVAL for a NULL argument or r_out / e_out aliasing u. */
+fcgno_status fcgno_residual_pair(fcgno_op_t op, const double* b, const double* u, const double* u_star,
+                                 double* r_out, double* e_out, void* stream);
 
 /* Neural operator handle. `weights` is a DEVICE float32 blob of fcgno_weight_count(desc)
  * elements in this order (row-major): lift_w [C][2], lift_b [C]; per layer l: w_l [C][C]

@@ -48,6 +48,26 @@ __global__ void rms_kernel(const double* __restrict__ r, size_t n, double* __res
   if (threadIdx.x == 0) rms[blockIdx.x] = sqrt(v[0] / (double)n);
 }
 
+// r = b - A u and e = u_star - u for every instance (the training pairs of random residuals).
+__global__ void residual_pair_kernel(int N, size_t n, size_t total, const double* __restrict__ aE,
+                                     const double* __restrict__ aN, const double* __restrict__ diag,
+                                     const double* __restrict__ b, const double* __restrict__ u,
+                                     const double* __restrict__ ustar, double* __restrict__ r,
+                                     double* __restrict__ e) {
+  size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  const size_t bi = i / n;
+  const int xi = (int)(i - bi * n);
+  const int q = xi / N, p = xi - q * N;
+  double acc = diag[i] * u[i];
+  if (p < N - 1) acc = fma(-aE[i], u[i + 1], acc);
+  if (p > 0) acc = fma(-aE[i - 1], u[i - 1], acc);
+  if (q < N - 1) acc = fma(-aN[i], u[i + N], acc);
+  if (q > 0) acc = fma(-aN[i - N], u[i - N], acc);
+  r[i] = b[i] - acc;
+  e[i] = ustar[i] - u[i];
+}
+
 fcgno_status launch_apply_A(const fcgno_op* op, const double* x, double* y, cudaStream_t st) {
   const size_t total = op->n * op->B;
   apply_A_kernel<<<ceil_div(total, 256), 256, 0, st>>>(op->N, op->n, total, op->aE, op->aN, op->diag, x, y);
@@ -111,6 +131,19 @@ extern "C" fcgno_status fcgno_reassemble(fcgno_op_t op, const double* k, void* s
     return FCGNO_EINVAL;
   }
   return launch_assemble(op, 0, op->n * op->B, k, (cudaStream_t)stream);
+}
+
+extern "C" fcgno_status fcgno_residual_pair(fcgno_op_t op, const double* b, const double* u, const double* u_star,
+                                            double* r_out, double* e_out, void* stream) {
+  if (!op || !b || !u || !u_star || !r_out || !e_out || r_out == u || e_out == u) {
+    set_last_error("fcgno_residual_pair: null or aliasing arguments");
+    return FCGNO_EINVAL;
+  }
+  const size_t total = op->n * op->B;
+  residual_pair_kernel<<<ceil_div(total, 256), 256, 0, (cudaStream_t)stream>>>(
+      op->N, op->n, total, op->aE, op->aN, op->diag, b, u, u_star, r_out, e_out);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
 }
 
 extern "C" fcgno_status fcgno_apply_A(fcgno_op_t op, const double* x, double* y, void* stream) {

@@ -66,6 +66,7 @@ def _load():
         "fcgno_reassemble": (c_int, [P, P, P]),
         "fcgno_op_destroy": (c_int, [P]),
         "fcgno_apply_A": (c_int, [P, P, P, P]),
+        "fcgno_residual_pair": (c_int, [P, P, P, P, P, P, P]),
         "fcgno_weight_count": (c_size_t, [POINTER(fcgno_model_desc)]),
         "fcgno_model_create": (c_int, [POINTER(fcgno_model_desc), P, P, POINTER(P)]),
         "fcgno_model_sync": (c_int, [P, P]),
@@ -110,7 +111,7 @@ lib = _load()
 
 # Exported symbol names, in the order of include/fcgno.h.
 EXPORTS = [
-    "fcgno_assemble", "fcgno_reassemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_weight_count", "fcgno_model_create",
+    "fcgno_assemble", "fcgno_reassemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_residual_pair", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
     "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
     "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_precision_supported", "fcgno_status_str",
@@ -222,6 +223,11 @@ class Operator:
     def apply(self, x, y, stream=None):
         """fcgno_apply_A: y = A x for every instance."""
         _check(lib.fcgno_apply_A(self.handle, _ptr(x), _ptr(y), _stream(stream)), "fcgno_apply_A")
+
+    def residual_pair(self, b, u, u_star, r_out, e_out, stream=None):
+        """fcgno_residual_pair: r_out = b - A u, e_out = u_star - u for every instance."""
+        _check(lib.fcgno_residual_pair(self.handle, _ptr(b), _ptr(u), _ptr(u_star), _ptr(r_out), _ptr(e_out),
+                                       _stream(stream)), "fcgno_residual_pair")
 
     def close(self):
         if self.handle:

@@ -70,7 +70,6 @@ class RandomResidualData:
         rng = np.random.default_rng(x0_seed)
         self.r = torch.empty((K, B, N, N), dtype=torch.float64, device=device)
         self.e = torch.empty_like(self.r)
-        Au = torch.empty((B, N, N), dtype=torch.float64, device=device)
         for i in range(K):
             f = torch.from_numpy(np.ascontiguousarray(np.stack([I.dataset_rhs(dataset, N, rng) for _ in range(B)])))
             f = f.to(device)
@@ -78,9 +77,8 @@ class RandomResidualData:
             x = torch.zeros_like(f)
             F.solve(self.op, None, f, x, tol=1e-12, m_max=1, max_iter=20 * N * N, prec="fp64", check_every=64,
                     stream=stream)
-            self.op.apply(u, Au, stream)
-            self.r[i] = f - Au
-            self.e[i] = x - u
+            # r_i = f_i - A u_i and e_i = A^-1 f_i - u_i, formed by the library
+            self.op.residual_pair(f, u, x, self.r[i], self.e[i], stream)
 
 
 class PreconditionerLoss(torch.autograd.Function):

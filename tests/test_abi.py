@@ -87,6 +87,7 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
         rejects(L.fcgno_assemble(N, B, k, None, ctypes.byref(out) if out is not None else None), "fcgno_assemble")
     rejects(L.fcgno_apply_A(None, hp, hp, None), "fcgno_apply_A")
     rejects(L.fcgno_reassemble(None, hp, None), "fcgno_reassemble")
+    rejects(L.fcgno_residual_pair(None, hp, hp, hp, hp, hp, None), "fcgno_residual_pair")
     rejects(L.fcgno_reassemble(ctypes.c_void_p(1), None, None), "fcgno_reassemble")
     rejects(L.fcgno_model_create(ctypes.byref(F.make_desc(width=0)), w32.ctypes.data, None, ctypes.byref(h)),
             "fcgno_model_create")

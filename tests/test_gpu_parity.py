@@ -115,6 +115,24 @@ def test_stencil_layered_coefficient_closed_form(lib, dev, N, axis, j):
     elem_check(y[0].cpu().numpy(), Au, 1e-12, "layered")
 
 
+@pytest.mark.parametrize("N,B", [(20, 2), (130, 1)])
+def test_residual_pair_matches_oracle(lib, dev, N, B):
+    """fcgno_residual_pair (the random-residual training pairs): r = b - A u against the
+    oracle's stencil element by element (1e-14 of max|r|), e = u_star - u exactly."""
+    import torch
+    k, f = batch(N, B, 9500 + N)
+    rng = np.random.default_rng(N)
+    u, us = rng.standard_normal((B, N, N)), rng.standard_normal((B, N, N))
+    op = lib.Operator(to_dev(k, dev))
+    r = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    e = torch.empty_like(r)
+    op.residual_pair(to_dev(f, dev), to_dev(u, dev), to_dev(us, dev), r, e)
+    rs, es = r.cpu().numpy(), e.cpu().numpy()
+    for b in range(B):
+        elem_check(rs[b], f[b] - O.apply_A(k[b], u[b]), 1e-14, ("residual pair", b))
+        assert np.array_equal(es[b], us[b] - u[b])
+
+
 # ------------------------------------------------------------------------------- CG / FCG(B=I)
 @pytest.mark.parametrize("N,B,m", [(33, 2, 1), (64, 3, 5), (100, 2, 1), (130, 1, 3)])
 def test_identity_preconditioned_iterates_match_oracle(lib, dev, N, B, m):
