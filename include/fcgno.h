@@ -372,6 +372,15 @@ fcgno_status fcgno_fp64_fma_rate(int blocks, int steps, double a, double c, doub
  * NULL operator or a limit outside the range; FCGNO_ENOMEM if the flag cannot be allocated. */
 fcgno_status fcgno_wait_selftest(fcgno_op_t A, double limit_seconds, void* stream);
 
+/* Launch-shape policy of the solves (a performance control; results agree up to the summation
+ * order of the FCG step's dot products, and the preconditioner's output is the same in both
+ * shapes). 0 (default): a solve replays its iterations in the wide shapes while more than 64
+ * instances are running and in the narrow shapes after (the FCG step on a cluster of CTAs per
+ * instance, 16-bit synthesis in narrower grid-column chunks: shorter serial chains when few
+ * instances are left); 1: always wide; 2: always narrow (also fcgno_precond_apply). Applies to
+ * calls made after it, from every thread. EINVAL for another mode. */
+fcgno_status fcgno_set_launch_shape(int mode);
+
 /* Kernel tracing (not part of the method): select a kernel family by name ("tc_synthesis",
  * "tc_analysis", "tc_mix", "tc_lift", "fcg_fused", "fcg_tiled", "" = off). Every later launch
  * of that family is bracketed by two CUDA events recorded on its launch stream.

@@ -2,6 +2,7 @@
 #include "internal.cuh"
 
 #include <mutex>
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -255,7 +256,7 @@ extern "C" fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, 
         break;
       case FCGNO_BF16:
       case FCGNO_FP16:
-        rc = no_apply_tc(model, op, r, rms, nullptr, z, prec == FCGNO_FP16, st);
+        rc = no_apply_tc(model, op, r, rms, nullptr, z, prec == FCGNO_FP16, st, launch_shape_mode() == 2);
         break;
       default:
         set_last_error("fcgno_precond_apply: unknown precision");
@@ -313,6 +314,20 @@ extern "C" fcgno_status fcgno_wait_selftest(fcgno_op_t A, double limit_seconds, 
     return FCGNO_EINVAL;
   }
   return tc_wait_probe(A, (uint64_t)(limit_seconds * 1e9), (cudaStream_t)stream);
+}
+
+namespace fcgno {
+static std::atomic<int> g_launch_shape{0};
+int launch_shape_mode() { return g_launch_shape.load(std::memory_order_relaxed); }
+}  // namespace fcgno
+
+extern "C" fcgno_status fcgno_set_launch_shape(int mode) {
+  if (mode < 0 || mode > 2) {
+    set_last_error("fcgno_set_launch_shape: mode must be 0 (automatic), 1 (wide) or 2 (narrow)");
+    return FCGNO_EINVAL;
+  }
+  g_launch_shape.store(mode, std::memory_order_relaxed);
+  return FCGNO_OK;
 }
 
 extern "C" int fcgno_precision_supported(int N, const fcgno_model_desc* desc, fcgno_prec prec) {

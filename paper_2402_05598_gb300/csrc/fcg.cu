@@ -990,7 +990,8 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
     bool replayed = false;
     if (use_graph && i > 0 && o.max_iter - i >= G) {
       // the first iteration ran eagerly, so every lazily allocated buffer exists before capture
-      const bool narrow = can_narrow && running <= kNarrowRunning;
+      const int mode = launch_shape_mode();
+      const bool narrow = mode == 2 || (mode == 0 && can_narrow && running <= kNarrowRunning);
       last_graph = narrow ? 1 : 0;
       FCGNO_TRY(ensure_graph(op, model, prec, a, s, narrow ? Ln : L, b, x, G, jacobi, narrow));
       FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph[last_graph].exec, cs));
@@ -999,7 +1000,8 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
       since_check = G;
       replayed = true;
     } else {
-      FCGNO_TRY(launch_iteration(op, model, prec, a, s, L, cs, jacobi));
+      const bool narrow = launch_shape_mode() == 2;
+      FCGNO_TRY(launch_iteration(op, model, prec, a, s, narrow ? Ln : L, cs, jacobi, narrow));
       if (hook) {
         const size_t total = op->n * op->B;
         const size_t o2 = (size_t)i * total;

@@ -261,6 +261,8 @@ fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, co
                          const int* active, double* z, bool fp16, cudaStream_t st, bool narrow = false);
 // Whether the narrow launch shape differs from the wide one for this grid and model.
 bool tc_has_narrow(int N, const fcgno_model_desc& d);
+// Launch-shape policy set by fcgno_set_launch_shape: 0 automatic, 1 always wide, 2 always narrow.
+int launch_shape_mode();
 // Whether the 16-bit (tensor-core) preconditioner supports model shape d on an N x N grid,
 // and the rule in words (for error messages). Host-only.
 bool tc_shape_supported(int N, const fcgno_model_desc& d);

@@ -1158,12 +1158,27 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
       for (int ut = 0; ut < utiles; ++ut) {
         const int row = ut * 128 + quad * 32 + lane;
         const int k2 = row / C, c = row % C;
-        for (int c0 = half * PC; c0 < (half + 1) * PC; c0 += 16) {
-          float val[16];
-          tmem_ld16(tU + ut * 2 * PC + c0 + lane_off, val);
+        if (PC % 16 == 0) {
+          for (int c0 = half * PC; c0 < (half + 1) * PC; c0 += 16) {
+            float val[16];
+            tmem_ld16(tU + ut * 2 * PC + c0 + lane_off, val);
+            if (row < Ky * C) {
+#pragma unroll
+              for (int i = 0; i < 16; i += 2) {
+                const int pl = (c0 + i) >> 1;
+                *reinterpret_cast<uint32_t*>(sB + kmajor_off(c, pl * 2 * Ky + 2 * k2, 128, SBO_B)) =
+                    pack2(val[i], val[i + 1], bf16);
+              }
+            }
+          }
+        } else {
+          // 8-column chunks (narrow launch shape): each half reads its 8 of U's 16 columns
+          const int c0 = half * PC;
+          float val[8];
+          tmem_ld8(tU + ut * 2 * PC + c0 + lane_off, val);
           if (row < Ky * C) {
 #pragma unroll
-            for (int i = 0; i < 16; i += 2) {
+            for (int i = 0; i < 8; i += 2) {
               const int pl = (c0 + i) >> 1;
               *reinterpret_cast<uint32_t*>(sB + kmajor_off(c, pl * 2 * Ky + 2 * k2, 128, SBO_B)) =
                   pack2(val[i], val[i + 1], bf16);
@@ -1300,12 +1315,13 @@ static void synthesis_rings(const TcGeom& g, int& din, int& dout) {
   din = kSynMaxIn;
 }
 
-// The synthesis geometry of the narrow launch shape: 16-column chunks where the wide shape uses
-// 32. The H table's 16-column chunk images are the halves of its 32-column images (rows are
-// grouped by 8 with a fixed stride), so both shapes read the same table.
+// The synthesis geometry of the narrow launch shape: 8-column chunks for N < 128 (4 tiles per
+// block at 64 x 64 instead of 16). The H table's chunk images of any width that is a multiple of
+// 4 columns are consecutive slices of the same bytes (its rows are grouped by 8 with a fixed
+// stride), so both shapes read one table.
 static TcGeom narrow_geom(TcGeom g) {
-  if (g.SPC <= 16) return g;
-  g.SPC = 16;
+  if (g.N >= 128 || g.SPC <= 8) return g;
+  g.SPC = 8;
   while (g.SPC % g.PT != 0) g.SPC *= 2;
   g.snchunks = g.N / g.SPC;
   g.KB = round_up(g.SPC * 2 * g.M, 16) + 16;

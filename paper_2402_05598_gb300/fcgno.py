@@ -97,6 +97,7 @@ def _load():
         "fcgno_bucket_enqueue": (c_int, [P, POINTER(fcgno_serve_request)]),
         "fcgno_bucket_results": (c_int, [P, POINTER(fcgno_serve_result), c_int]),
         "fcgno_wait_selftest": (c_int, [P, c_double, P]),
+        "fcgno_set_launch_shape": (c_int, [c_int]),
         "fcgno_trace_set": (c_int, [c_char_p]),
         "fcgno_trace_collect": (c_int, [POINTER(c_double), POINTER(c_uint64)]),
     }
@@ -115,7 +116,7 @@ EXPORTS = [
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
     "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
     "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_precision_supported", "fcgno_status_str",
-    "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_wait_selftest", "fcgno_trace_set",
+    "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_wait_selftest", "fcgno_set_launch_shape", "fcgno_trace_set",
     "fcgno_trace_collect",
     "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
     "fcgno_bucket_destroy", "fcgno_bucket_serve_enable", "fcgno_bucket_enqueue", "fcgno_bucket_results",
@@ -158,6 +159,11 @@ def wait_selftest(op: "Operator", limit_seconds: float, stream=None) -> int:
     if code not in (FCGNO_OK, FCGNO_ETIMEOUT):
         raise FcgnoError(code, "fcgno_wait_selftest")
     return code
+
+
+def set_launch_shape(mode: str):
+    """fcgno_set_launch_shape: "auto", "wide" or "narrow"."""
+    _check(lib.fcgno_set_launch_shape({"auto": 0, "wide": 1, "narrow": 2}[mode]), "fcgno_set_launch_shape")
 
 
 def trace_set(family: str):

@@ -131,6 +131,8 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
     rejects(L.fcgno_bucket_enqueue(None, None), "fcgno_bucket_enqueue")
     assert L.fcgno_bucket_results(None, None, 4) == -1
     rejects(L.fcgno_wait_selftest(None, 1e-3, None), "fcgno_wait_selftest")
+    rejects(L.fcgno_set_launch_shape(3), "fcgno_set_launch_shape")
+    rejects(L.fcgno_set_launch_shape(-1), "fcgno_set_launch_shape")
     rejects(L.fcgno_wait_selftest(ctypes.c_void_p(1), 0.0, None), "fcgno_wait_selftest")
     rejects(L.fcgno_wait_selftest(ctypes.c_void_p(1), 2.0, None), "fcgno_wait_selftest")
     rejects(L.fcgno_trace_collect(None, ctypes.byref(n)), "fcgno_trace_collect")

@@ -545,3 +545,26 @@ def test_narrow_launch_shapes_match_the_wide_ones(lib, dev, N, C, M):
             ustar = np.linalg.solve(O.dense_A(k[b]), f[b].ravel()).reshape(N, N) if N <= 32 else None
             if ustar is not None:
                 assert O.energy_norm(k[b], ustar - xh[b]) <= O.energy_norm(k[b], ustar)
+
+
+@pytest.mark.parametrize("N,C,M,B,prec", [(64, 32, 12, 5, "bf16"), (32, 16, 8, 130, "bf16"), (64, 32, 12, 3, "fp16")])
+def test_narrow_synthesis_gives_the_same_preconditioner_output(lib, dev, N, C, M, B, prec):
+    """The narrow launch shape runs the 16-bit synthesis in 8-column chunks (4 tiles per block
+    at 64 x 64) instead of 32: every tile's arithmetic is unchanged, so the preconditioner's
+    output is bit-identical in both shapes (fcgno_set_launch_shape forces one or the other)."""
+    import torch
+    k, r = batch(N, B, 9600 + N)
+    desc, P, model, _w = model_pair(lib, dev, C, M, out_scale=1)
+    op = lib.Operator(to_dev(k, dev))
+    z = {}
+    try:
+        for mode in ("wide", "narrow"):
+            lib.set_launch_shape(mode)
+            zz = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+            lib.precond_apply(model, op, to_dev(r, dev), zz, prec=prec)
+            z[mode] = zz.cpu().numpy()
+    finally:
+        lib.set_launch_shape("auto")
+    assert np.array_equal(z["wide"], z["narrow"])
+    ref = O.no_forward(P, desc, r[0], np.log(k[0]))
+    assert rel(z["narrow"][0] * k[0], ref * k[0]) < 2e-2
