@@ -177,10 +177,16 @@ fcgno_status fcgno_solve_jacobi(fcgno_op_t A, int steps, const double* b, double
 /* End-to-end variant of fcgno_solve on HOST buffers: k_host, b_host, x_host are
  * [batch][N][N] host arrays (pinned memory gives the fastest copies). Copies k, b, x in,
  * assembles, solves, copies x out; info is a host array. Synchronous.
+ * The device copies of k, b, x and the assembled operator (with its Krylov workspace and
+ * captured graphs) of the last 4 shapes (device, N, batch) are kept for the next call of the
+ * same shape, which then re-assembles in place (fcgno_reassemble); fcgno_solve_host_release
+ * frees them. A call whose shape is being solved by another thread uses temporary buffers.
  * Errors: EINVAL for N < 2, batch < 1 or a NULL host buffer, then those of fcgno_solve. */
 fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const double* b_host,
                               double* x_host, fcgno_model_t Bpc, const fcgno_solve_opts* opts,
                               fcgno_prec prec, fcgno_solve_info* info, void* stream);
+/* Frees the device state fcgno_solve_host keeps between calls (waits for work in flight). */
+fcgno_status fcgno_solve_host_release(void);
 
 /* Allocation-free variant of fcgno_solve for the identity preconditioner (B = I; plain CG
  * for m_max = 1). The paper has no counterpart: this entry point exists for callers that

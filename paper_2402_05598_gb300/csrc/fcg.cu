@@ -1110,6 +1110,62 @@ extern "C" fcgno_status fcgno_fp64_fma_rate(int blocks, int steps, double a, dou
   return FCGNO_OK;
 }
 
+namespace fcgno {
+// Device state of fcgno_solve_host kept between calls: the copies of k, b, x and the assembled
+// operator (with its Krylov workspace and captured graphs) of the last shapes seen per device,
+// so that repeated end-to-end solves of one shape re-assemble in place instead of allocating,
+// assembling from scratch and capturing new graphs. Each entry has its own lock; a call that
+// finds its entry in use by another thread works on temporary buffers instead.
+struct HostSolveEntry {
+  int dev = -1, N = 0, B = 0;
+  double* dk = nullptr;
+  double* db = nullptr;
+  double* dx = nullptr;
+  fcgno_op_t op = nullptr;
+  uint64_t used = 0;
+  std::mutex mu;
+};
+constexpr int kHostSolveEntries = 4;
+static HostSolveEntry g_host_solve[kHostSolveEntries];
+static std::mutex g_host_solve_mu;  // guards the entries' keys and the use counter
+static uint64_t g_host_solve_clock = 0;
+
+static void host_entry_free(HostSolveEntry& e) {
+  if (e.op) fcgno_op_destroy(e.op);
+  if (e.dk) cudaFree(e.dk);
+  if (e.db) cudaFree(e.db);
+  if (e.dx) cudaFree(e.dx);
+  e.op = nullptr;
+  e.dk = e.db = e.dx = nullptr;
+  e.dev = -1;
+  e.N = e.B = 0;
+}
+
+static fcgno_status host_solve_on(int N, int batch, double* dk, double* db, double* dx, fcgno_op_t* op_io,
+                                  const double* k_host, const double* b_host, double* x_host, fcgno_model_t Bpc,
+                                  const fcgno_solve_opts* opts, fcgno_prec prec, fcgno_solve_info* info,
+                                  cudaStream_t st) {
+  const size_t bytes = (size_t)N * N * batch * sizeof(double);
+  if (cudaMemcpyAsync(dk, k_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(db, b_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    set_last_error("fcgno_solve_host: host-to-device copy failed");
+    return FCGNO_ECUDA;
+  }
+  if (*op_io)
+    FCGNO_TRY(fcgno_reassemble(*op_io, dk, st));
+  else
+    FCGNO_TRY(fcgno_assemble(N, batch, dk, st, op_io));
+  FCGNO_TRY(fcgno_solve(*op_io, Bpc, db, dx, opts, prec, info, st));
+  if (cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    set_last_error("fcgno_solve_host: device-to-host copy failed");
+    return FCGNO_ECUDA;
+  }
+  return FCGNO_OK;
+}
+}  // namespace fcgno
+
 extern "C" fcgno_status fcgno_solve_host(int N, int batch, const double* k_host, const double* b_host,
                                          double* x_host, fcgno_model_t Bpc, const fcgno_solve_opts* opts,
                                          fcgno_prec prec, fcgno_solve_info* info, void* stream) {
@@ -1120,6 +1176,51 @@ extern "C" fcgno_status fcgno_solve_host(int N, int batch, const double* k_host,
   FCGNO_TRY(check_solve_args("fcgno_solve_host", N, Bpc, opts, prec));
   cudaStream_t st = (cudaStream_t)stream;
   const size_t bytes = (size_t)N * N * batch * sizeof(double);
+  int dev = 0;
+  FCGNO_CUDA_TRY(cudaGetDevice(&dev));
+  // the cached entry of this shape (or the least recently used free one)
+  HostSolveEntry* e = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_host_solve_mu);
+    for (auto& c : g_host_solve)
+      if (c.dev == dev && c.N == N && c.B == batch) e = &c;
+    if (e && !e->mu.try_lock()) e = nullptr;
+    if (!e) {
+      HostSolveEntry* victim = nullptr;
+      for (auto& c : g_host_solve) {
+        if (!c.mu.try_lock()) continue;
+        if (!victim || c.used < victim->used) {
+          if (victim) victim->mu.unlock();
+          victim = &c;
+        } else {
+          c.mu.unlock();
+        }
+      }
+      e = victim;
+      if (e && !(e->dev == dev && e->N == N && e->B == batch)) host_entry_free(*e);
+    }
+    if (e) e->used = ++g_host_solve_clock;
+  }
+  if (e) {
+    std::lock_guard<std::mutex> hold(e->mu, std::adopt_lock);
+    if (!e->dk) {
+      if (cudaMalloc(&e->dk, bytes) != cudaSuccess || cudaMalloc(&e->db, bytes) != cudaSuccess ||
+          cudaMalloc(&e->dx, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        host_entry_free(*e);
+        set_last_error("fcgno_solve_host: out of device memory");
+        return FCGNO_ENOMEM;
+      }
+      e->dev = dev;
+      e->N = N;
+      e->B = batch;
+    }
+    const fcgno_status rc = host_solve_on(N, batch, e->dk, e->db, e->dx, &e->op, k_host, b_host, x_host, Bpc, opts,
+                                          prec, info, st);
+    if (rc != FCGNO_OK && rc != FCGNO_ETIMEOUT) host_entry_free(*e);
+    return rc;
+  }
+  // every entry is in use by another thread: temporary buffers
   double *dk = nullptr, *db = nullptr, *dx = nullptr;
   if (cudaMallocAsync(&dk, bytes, st) != cudaSuccess || cudaMallocAsync(&db, bytes, st) != cudaSuccess ||
       cudaMallocAsync(&dx, bytes, st) != cudaSuccess) {
@@ -1129,31 +1230,23 @@ extern "C" fcgno_status fcgno_solve_host(int N, int batch, const double* k_host,
     set_last_error("fcgno_solve_host: out of device memory");
     return FCGNO_ENOMEM;
   }
-  fcgno_status rc = FCGNO_OK;
   fcgno_op_t op = nullptr;
-  do {
-    if (cudaMemcpyAsync(dk, k_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(db, b_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, st) != cudaSuccess) {
-      set_last_error("fcgno_solve_host: host-to-device copy failed");
-      rc = FCGNO_ECUDA;
-      break;
-    }
-    rc = fcgno_assemble(N, batch, dk, stream, &op);
-    if (rc != FCGNO_OK) break;
-    rc = fcgno_solve(op, Bpc, db, dx, opts, prec, info, stream);
-    if (rc != FCGNO_OK) break;
-    if (cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess) {
-      set_last_error("fcgno_solve_host: device-to-host copy failed");
-      rc = FCGNO_ECUDA;
-    }
-  } while (0);
+  const fcgno_status rc = host_solve_on(N, batch, dk, db, dx, &op, k_host, b_host, x_host, Bpc, opts, prec, info, st);
   if (op) fcgno_op_destroy(op);
   cudaFreeAsync(dk, st);
   cudaFreeAsync(db, st);
   cudaFreeAsync(dx, st);
   return rc;
+}
+
+extern "C" fcgno_status fcgno_solve_host_release(void) {
+  using namespace fcgno;
+  std::lock_guard<std::mutex> lk(g_host_solve_mu);
+  for (auto& c : g_host_solve) {
+    std::lock_guard<std::mutex> hold(c.mu);
+    host_entry_free(c);
+  }
+  return FCGNO_OK;
 }
 
 extern "C" fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x0,

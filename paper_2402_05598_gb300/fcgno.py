@@ -75,6 +75,7 @@ def _load():
         "fcgno_solve": (c_int, [P, P, P, P, POINTER(fcgno_solve_opts), c_int, POINTER(fcgno_solve_info), P]),
         "fcgno_solve_host": (c_int, [c_int, c_int, P, P, P, P, POINTER(fcgno_solve_opts), c_int,
                                      POINTER(fcgno_solve_info), P]),
+        "fcgno_solve_host_release": (c_int, []),
         "fcgno_solve_noalloc": (c_int, [P, P, P, POINTER(fcgno_solve_opts), POINTER(fcgno_solve_info), P]),
         "fcgno_solve_jacobi": (c_int, [P, c_int, P, P, POINTER(fcgno_solve_opts), POINTER(fcgno_solve_info), P]),
         "fcgno_krylov_harvest": (c_int, [P, P, P, P, c_int, P, P, POINTER(fcgno_solve_info), P]),
@@ -114,6 +115,7 @@ lib = _load()
 EXPORTS = [
     "fcgno_assemble", "fcgno_reassemble", "fcgno_op_destroy", "fcgno_apply_A", "fcgno_residual_pair", "fcgno_weight_count", "fcgno_model_create",
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
+    "fcgno_solve_host_release",
     "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
     "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_precision_supported", "fcgno_status_str",
     "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_wait_selftest", "fcgno_set_launch_shape", "fcgno_trace_set",
@@ -316,6 +318,11 @@ def solve_host(k: np.ndarray, b: np.ndarray, x: np.ndarray, model=None, tol=1e-6
                                 model.handle if model is not None else None, ctypes.byref(opts), PREC[prec], info,
                                 _stream(stream)), "fcgno_solve_host")
     return _info_list(info)
+
+
+def solve_host_release():
+    """fcgno_solve_host_release: frees the device state fcgno_solve_host keeps between calls."""
+    _check(lib.fcgno_solve_host_release(), "fcgno_solve_host_release")
 
 
 def solve_jacobi(op: Operator, steps, b, x, tol=1e-6, m_max=1, max_iter=1000, fixed_iters=False, check_every=8,

@@ -268,6 +268,33 @@ def test_solve_host_matches_device_solve(lib, dev):
     assert np.array_equal(x_host, x.cpu().numpy())
 
 
+def test_solve_host_reuses_its_device_state_across_problems(lib, dev):
+    """fcgno_solve_host keeps the device buffers and the operator of a shape between calls:
+    a second call with different k, f and u_0 of the same shape (re-assembled in place, same
+    captured graphs), a call of another shape in between, and a call after releasing the state
+    each equal a device solve of their own problem, bit for bit."""
+    import torch
+    desc, P, model, _w = model_pair(lib, dev, 32, 12, out_scale=1)
+
+    def both(N, B, seed):
+        k, f = batch(N, B, seed)
+        x0 = np.random.default_rng(seed).standard_normal((B, N, N))
+        xh = x0.copy()
+        ih = lib.solve_host(k, f, xh, model, tol=1e-6, m_max=5, max_iter=60, prec="bf16")
+        op = lib.Operator(to_dev(k, dev))
+        x = to_dev(x0, dev)
+        idv = lib.solve(op, model, to_dev(f, dev), x, tol=1e-6, m_max=5, max_iter=60, prec="bf16")
+        assert [i["iters"] for i in ih] == [i["iters"] for i in idv]
+        assert np.array_equal(xh, x.cpu().numpy())
+
+    both(64, 3, 710)
+    both(64, 3, 720)   # same shape, new problem: cached state re-assembled
+    both(32, 2, 730)   # another shape
+    both(64, 3, 740)
+    lib.solve_host_release()
+    both(64, 3, 750)
+
+
 def test_krylov_harvest_matches_oracle_cg(lib, dev):
     """Eq. (9): residuals r_i and errors e_i = u* - u_i of CG from u_0 ~ N(0, 1)."""
     import torch
