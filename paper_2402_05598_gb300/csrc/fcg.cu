@@ -1672,6 +1672,8 @@ struct fcgno_bucket {
   fcgno::IterArgs a{};
   fcgno::State s{};
   fcgno::LoopShape L{};
+  fcgno::LoopShape Ln{};  // narrow shape (few running slots)
+  bool can_narrow = false;
   int G = 8;
   int max_iter = 1000;
   bool warmed = false;
@@ -1756,7 +1758,11 @@ extern "C" fcgno_status fcgno_bucket_create(int N, int capacity, fcgno_model_t m
     k->a.tol = tol;
     k->a.fixed = 0;
     k->L = loop_shape(op);
+    k->Ln = loop_shape(op, true);
     FCGNO_TRY(prepare_fused(k->L));
+    FCGNO_TRY(prepare_fused(k->Ln));
+    const bool tc = model && (prec == FCGNO_BF16 || prec == FCGNO_FP16);
+    k->can_narrow = (tc && tc_has_narrow(N, model->desc)) || k->Ln.CL != k->L.CL;
     return FCGNO_OK;
   };
   rc = setup();
@@ -1821,15 +1827,26 @@ extern "C" fcgno_status fcgno_bucket_step(fcgno_bucket_t k, void* stream) {
   FCGNO_CUDA_TRY(cudaEventRecord(w.ev_in, st));
   FCGNO_CUDA_TRY(cudaStreamWaitEvent(w.cs, w.ev_in, 0));
   const ServeDev* sv = k->srv ? &k->srv->dev : nullptr;
+  // an upper bound on the running slots, known on the host: requests enqueued and not yet
+  // collected (device-driven) or slots admitted and not yet taken; few running slots take the
+  // narrow launch shapes (shorter serial chains), as a solve does
+  long long bound = k->occupied;
+  if (k->srv) {
+    std::lock_guard<std::mutex> lk(k->srv->mu);
+    bound = (long long)(k->srv->host_tail - k->srv->host_head);
+  }
+  const int mode = launch_shape_mode();
+  const bool narrow = mode == 2 || (mode == 0 && k->can_narrow && bound <= kNarrowRunning);
+  const LoopShape& L = narrow ? k->Ln : k->L;
   if (!k->warmed || !graphs_enabled() || k->G == 1) {
     // first step eagerly (lazily allocated buffers exist before any capture)
     for (int i = 0; i < k->G; ++i)
-      FCGNO_TRY(launch_iteration(k->op, k->model, k->prec, k->a, k->s, k->L, w.cs, 0, false, sv));
+      FCGNO_TRY(launch_iteration(k->op, k->model, k->prec, k->a, k->s, L, w.cs, 0, narrow, sv));
     k->warmed = true;
   } else {
-    FCGNO_TRY(ensure_graph(k->op, k->model, k->prec, k->a, k->s, k->L, k->b, k->x, k->G, 0, false, sv));
-    FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph[0].exec, w.cs));
-    g_launches.fetch_add(w.graph[0].kernels, std::memory_order_relaxed);
+    FCGNO_TRY(ensure_graph(k->op, k->model, k->prec, k->a, k->s, L, k->b, k->x, k->G, 0, narrow, sv));
+    FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph[narrow ? 1 : 0].exec, w.cs));
+    g_launches.fetch_add(w.graph[narrow ? 1 : 0].kernels, std::memory_order_relaxed);
   }
   FCGNO_CUDA_TRY(cudaEventRecord(w.ev_out, w.cs));
   FCGNO_CUDA_TRY(cudaStreamWaitEvent(st, w.ev_out, 0));
