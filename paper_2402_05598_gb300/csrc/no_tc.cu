@@ -139,10 +139,12 @@ static TcGeom make_geom(int N, int C, int M) {
 // 16-bit elements of an operator's activation buffers for a batch of B: each of the two
 // ping-pong activation images (B n C), the partial spectral coefficients (mode x column chunk
 // x block of 128 instances x 128 x 2C) and the mixed-coefficient images (B x MP x KXP).
+static TcGeom narrow_geom(TcGeom g);
 static void tc_acts_elems(const TcGeom& g, int B, size_t& v, size_t& part, size_t& chat) {
   const size_t nbt = ceil_div(B, 128);
+  const size_t nch = std::max(g.nchunks, narrow_geom(g).nchunks);  // either launch shape
   v = (size_t)B * g.N * g.N * g.C;
-  part = (size_t)g.nmodes * g.nchunks * nbt * 128 * 2 * g.C;
+  part = (size_t)g.nmodes * nch * nbt * 128 * 2 * g.C;
   chat = (size_t)B * g.MP * g.KXP;
 }
 
@@ -426,7 +428,8 @@ static fcgno_status ensure_prec(fcgno_model* m, bool fp16, cudaStream_t st) {
 
 static fcgno_status ensure_tables(fcgno_model* m, bool fp16, const TcGeom& g, TcTables*& out, cudaStream_t st) {
   TcPrecision& P = m->tc->prec[fp16 ? 1 : 0];
-  auto it = P.tables.find(g.N);
+  const int key = g.N * 256 + g.PC;  // the analysis tables depend on the column-chunk width
+  auto it = P.tables.find(key);
   if (it != P.tables.end() && it->second.M == g.M) {
     out = &it->second;
     return FCGNO_OK;
@@ -442,8 +445,8 @@ static fcgno_status ensure_tables(fcgno_model* m, bool fp16, const TcGeom& g, Tc
   const int work = std::max(std::max(32 * g.N, g.NPM * 2 * g.N), std::max(2 * g.N * g.KXP, arows * g.KSYN));
   tc_tables_kernel<<<ceil_div(work, 256), 256, 0, st>>>(g, !fp16, t.E2, t.G, t.H, t.Asyn);
   FCGNO_LAUNCHED();
-  P.tables[g.N] = t;
-  out = &P.tables[g.N];
+  P.tables[key] = t;
+  out = &P.tables[key];
   m->gen++;
   return FCGNO_OK;
 }
@@ -1321,6 +1324,12 @@ static void synthesis_rings(const TcGeom& g, int& din, int& dout) {
 // stride), so both shapes read one table.
 static TcGeom narrow_geom(TcGeom g) {
   if (g.N >= 128 || g.SPC <= 8) return g;
+  // analysis and mixing: 16-column chunks (half the serial m-tile steps per block, twice the
+  // partial-coefficient images for the mixing to sum)
+  if (g.PC > 16) {
+    g.PC = 16;
+    g.nchunks = g.N / g.PC;
+  }
   g.SPC = 8;
   while (g.SPC % g.PT != 0) g.SPC *= 2;
   g.snchunks = g.N / g.SPC;
@@ -1339,11 +1348,17 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
                            double* z, bool fp16, cudaStream_t st, bool narrow) {
   const fcgno_model_desc& d = m->desc;
   const TcGeom g = make_geom(op->N, C, d.modes);
-  const TcGeom gs = narrow ? narrow_geom(g) : g;  // synthesis geometry
+  const TcGeom gn = narrow_geom(g);
+  const TcGeom gs = narrow ? gn : g;  // geometry of this call's launches
   const uint64_t gen0 = m->gen;
   FCGNO_TRY(ensure_prec(m, fp16, st));
   TcTables* tab = nullptr;
   FCGNO_TRY(ensure_tables(m, fp16, g, tab, st));
+  // the other launch shape's tables are built in the same (eager) call, so that no table build
+  // is ever captured into a replayed graph
+  TcTables* tabn = nullptr;
+  FCGNO_TRY(ensure_tables(m, fp16, gn, tabn, st));
+  if (narrow) tab = tabn;
   if (m->gen != gen0) {
     // derived weight images or tables were just built on `st`: finish them before going on,
     // so that operators solved on other streams never read them half written. This happens
@@ -1388,7 +1403,9 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   FCGNO_LAUNCHED();
   int din, dout;
   synthesis_rings(gs, din, dout);
-  const size_t sa = analysis_smem(g), ss = synthesis_bytes(gs, gs.SPC, din, dout), sm = mix_smem(g);
+  const size_t sa = analysis_smem(gs), ss = synthesis_bytes(gs, gs.SPC, din, dout), sm = mix_smem(gs);
+  const size_t sa_limit = std::max(analysis_smem(g), analysis_smem(gn));
+  const size_t sm_limit = std::max(mix_smem(g), mix_smem(gn));
   // the limit covers both launch shapes, so that the other shape's first (captured) launch
   // needs no attribute change
   size_t ss_limit = ss;
@@ -1413,22 +1430,22 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     if (e == cudaSuccess) set = bytes;
     return e;
   };
-  FCGNO_CUDA_TRY(raise((const void*)tc_analysis_kernel<C>, sa, set_sa));
+  FCGNO_CUDA_TRY(raise((const void*)tc_analysis_kernel<C>, sa_limit, set_sa));
   FCGNO_CUDA_TRY(raise((const void*)tc_synthesis_kernel<C>, ss_limit, set_ss));
-  FCGNO_CUDA_TRY(raise((const void*)tc_mix_kernel<C>, sm, set_sm));
+  FCGNO_CUDA_TRY(raise((const void*)tc_mix_kernel<C>, sm_limit, set_sm));
   uint16_t* cur = T.va;
   uint16_t* nxt = T.vb;
   for (int l = 0; l < d.layers; ++l) {
     {
       TraceScope ts("tc_analysis", st);
-      FCGNO_CUDA_TRY(launch_chained(tc_analysis_kernel<C>, dim3(g.nchunks, B), dim3(kAnaThreads), sa, st, g, nbt,
+      FCGNO_CUDA_TRY(launch_chained(tc_analysis_kernel<C>, dim3(gs.nchunks, B), dim3(kAnaThreads), sa, st, gs, nbt,
                                     bf16, active, (const uint16_t*)cur, (const uint16_t*)tab->E2,
                                     (const uint16_t*)tab->G, T.part, T.err));
     }
     FCGNO_LAUNCHED();
     {
       TraceScope ts("tc_mix", st);
-      FCGNO_CUDA_TRY(launch_chained(tc_mix_kernel<C>, dim3(g.nmodes, nbt), dim3(kTcThreads), sm, st, g, B, nbt,
+      FCGNO_CUDA_TRY(launch_chained(tc_mix_kernel<C>, dim3(gs.nmodes, nbt), dim3(kTcThreads), sm, st, gs, B, nbt,
                                     bf16, active, (const uint16_t*)T.part, (const uint16_t*)P.Rr[l], T.chat,
                                     T.err));
     }

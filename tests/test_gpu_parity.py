@@ -575,10 +575,12 @@ def test_narrow_launch_shapes_match_the_wide_ones(lib, dev, N, C, M):
 
 
 @pytest.mark.parametrize("N,C,M,B,prec", [(64, 32, 12, 5, "bf16"), (32, 16, 8, 130, "bf16"), (64, 32, 12, 3, "fp16")])
-def test_narrow_synthesis_gives_the_same_preconditioner_output(lib, dev, N, C, M, B, prec):
-    """The narrow launch shape runs the 16-bit synthesis in 8-column chunks (4 tiles per block
-    at 64 x 64) instead of 32: every tile's arithmetic is unchanged, so the preconditioner's
-    output is bit-identical in both shapes (fcgno_set_launch_shape forces one or the other)."""
+def test_narrow_shape_preconditioner_matches_oracle(lib, dev, N, C, M, B, prec):
+    """The narrow launch shape (fcgno_set_launch_shape forces it) runs the 16-bit analysis in
+    16-column chunks (the mixing sums twice as many 16-bit partial coefficients) and the
+    synthesis in 8-column chunks. Its output meets the same bounds against the FP64 oracle as
+    the wide shape's (2-norm and element-wise, on the network output z k), and the two shapes
+    agree within that 16-bit tolerance."""
     import torch
     k, r = batch(N, B, 9600 + N)
     desc, P, model, _w = model_pair(lib, dev, C, M, out_scale=1)
@@ -592,6 +594,10 @@ def test_narrow_synthesis_gives_the_same_preconditioner_output(lib, dev, N, C, M
             z[mode] = zz.cpu().numpy()
     finally:
         lib.set_launch_shape("auto")
-    assert np.array_equal(z["wide"], z["narrow"])
-    ref = O.no_forward(P, desc, r[0], np.log(k[0]))
-    assert rel(z["narrow"][0] * k[0], ref * k[0]) < 2e-2
+    tol = 2e-2 if prec == "bf16" else 4e-3
+    for b in sorted({0, B // 2, B - 1}):
+        ref = O.no_forward(P, desc, r[b], np.log(k[b])) * k[b]
+        for mode in ("wide", "narrow"):
+            assert rel(z[mode][b] * k[b], ref) < tol, (mode, b)
+            elem_check(z[mode][b] * k[b], ref, ELEM_TOL[prec], (mode, b))
+        assert rel(z["narrow"][b] * k[b], z["wide"][b] * k[b]) < tol
