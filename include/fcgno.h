@@ -379,10 +379,10 @@ fcgno_status fcgno_fp64_fma_rate(int blocks, int steps, double a, double c, doub
 fcgno_status fcgno_wait_selftest(fcgno_op_t A, double limit_seconds, void* stream);
 
 /* Launch-shape policy of the solves and serving buckets (a performance control). 0 (default):
- * a solve replays its iterations in the wide shapes while more than 64 instances are running and
+ * a solve replays its iterations in the wide shapes while more than 80 instances are running and
  * in the narrow shapes after (the FCG step on a cluster of CTAs per instance; the 16-bit
  * analysis, mixing and synthesis in narrower grid-column chunks: shorter serial chains when few
- * instances are left); a bucket takes the narrow shapes while at most 64 of its slots can be
+ * instances are left); a bucket takes the narrow shapes while at most 80 of its slots can be
  * running; 1: always wide; 2: always narrow (also fcgno_precond_apply). The shapes differ only in
  * the FCG step's summation order (FP64 rounding) and in where the 16-bit preconditioner rounds
  * its partial coefficients (within its 16-bit tolerance). Applies to calls made after it, from

@@ -33,7 +33,7 @@ constexpr int kTile = 2048;     // elements per CTA (tiled path)
 constexpr int kThreads = 256;   // threads per CTA (tiled path)
 constexpr int kEPT = kTile / kThreads;
 constexpr int kParts = kMaxWindow + 2;
-constexpr int kNarrowRunning = 64;  // running instances at or below which the narrow launch shape is used
+constexpr int kNarrowRunning = 80;  // running instances at or below which the narrow launch shape is used
 
 struct IterArgs {
   int N;
