@@ -550,7 +550,7 @@ def main():
     ap.add_argument("--m", type=int, default=5, help="truncation m of Algorithm 1 for the headline (5; m = 1 is "
                                                      "measured alongside)")
     ap.add_argument("--m-alt", type=int, default=1, help="second truncation reported next to the headline (0 = none)")
-    ap.add_argument("--train-steps", type=int, default=8000)
+    ap.add_argument("--train-steps", type=int, default=16000)
     ap.add_argument("--train-instances", type=int, default=512)
     ap.add_argument("--max-iter", type=int, default=400,
                     help="iteration cap (CG needs ~400 on this workload); capped instances are not counted")
