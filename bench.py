@@ -373,6 +373,62 @@ def run_transfer(args, model, dev, flush, stream):
 LARGE_CASES = ((1024, 8), (2048, 2))
 
 
+def run_train_leg(args, desc_np, dev, eval_fn):
+    """Training throughput (Eq. (11) steps, batch 32 on the 64 x 64 grid, the training
+    configuration's shape): BF16 on the tensor cores (FP32 accumulation, FP32 master weights)
+    against FP32 on CUDA cores, each timed with CUDA events over `train_bench_steps` library
+    steps on one harvested batch; then two models trained from the same seed on the same data
+    for the same number of steps, one per precision, and their eval iterations (the
+    headline's instances and protocol)."""
+    import torch
+    from paper_2402_05598_gb300 import fcgno as F
+    from paper_2402_05598_gb300 import inputs as I
+    from paper_2402_05598_gb300 import train as T
+    data = T.KrylovData(N_GRID, list(range(0, 32)), 100, dev)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    idx = torch.randint(0, 100, (32,), generator=gen, device=dev)
+    ar = torch.arange(32, device=dev)
+    r, e = data.r[idx, ar].contiguous(), data.e[idx, ar].contiguous()
+
+    def fresh(seed=0):
+        blob = torch.from_numpy(I.xavier_weights(desc_np, seed)).to(dev)
+        return F.Model(F.make_desc(WIDTH, LAYERS, MODES, WIDTH, output_scale=args.output_scale), blob)
+
+    out = {"batch": 32, "grid": N_GRID, "timed_steps": args.train_bench_steps,
+           "what": "one fcgno_train_step (forward, loss, backward, every weight gradient); Adam excluded"}
+    for prec in ("fp32", "bf16"):
+        m = fresh()
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        grad = torch.zeros(m.weights.numel(), dtype=torch.float32, device=dev)
+        for _ in range(5):
+            F.train_step(m, data.op, r, e, loss, grad, prec=prec)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(args.train_bench_steps):
+            F.train_step(m, data.op, r, e, loss, grad, prec=prec)
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.train_bench_steps
+        out[prec] = {"ms_per_step": round(ms, 4), "steps_per_s": round(1000.0 / ms, 1),
+                     "samples_per_s": round(32 * 1000.0 / ms, 1)}
+    out["bf16_speedup"] = round(out["fp32"]["ms_per_step"] / out["bf16"]["ms_per_step"], 3)
+    if args.train_compare_steps > 0:
+        cmp_ = {"steps": args.train_compare_steps, "instances": args.train_instances, "seed": 0}
+        for prec in ("fp32", "bf16"):
+            m = fresh()
+            tr = T.train(m, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3,
+                         steps=args.train_compare_steps, prec=prec)
+            its, conv = eval_fn(m)
+            cmp_[prec] = {"train_seconds": round(tr.seconds, 2), "steps_per_s": round(tr.steps / tr.seconds, 1),
+                          "eval_iterations": {"mean": float(np.mean(its)), "max": int(max(its)), "converged": conv}}
+        cmp_["mean_iterations_ratio_bf16_over_fp32"] = round(
+            cmp_["bf16"]["eval_iterations"]["mean"] / cmp_["fp32"]["eval_iterations"]["mean"], 4)
+        out["same_steps_models"] = cmp_
+    return out
+
+
 def run_large(args, dev, flush, stream):
     """Large single solves: 1024 x 1024 x 8 and 2048 x 2048 x 2, k = exp(GRF(length 0.05,
     sigma 2)), f and u_0 iid N(0, 1), tol 1e-8, m = 5. The model (width 32, 16 x 16 modes) is
@@ -389,8 +445,9 @@ def run_large(args, dev, flush, stream):
     blob = torch.from_numpy(I.xavier_weights(desc, 1)).to(dev)
     model = F.Model(F.make_desc(WIDTH, LAYERS, M, WIDTH, output_scale=args.output_scale), blob)
     tr = T.train(model, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3,
-                 steps=args.large_train_steps, sigma=2.0, ell=0.05)
-    out = {"model": {"modes": M, "train_steps_64": tr.steps, "train_seconds_64": round(tr.seconds, 2)}}
+                 steps=args.large_train_steps, sigma=2.0, ell=0.05, prec=args.train_prec)
+    out = {"model": {"modes": M, "train_steps_64": tr.steps, "train_seconds_64": round(tr.seconds, 2),
+                     "train_prec_64": args.train_prec}}
     # fine-tuning at 1024 x 1024 (8 instances): Krylov vectors of CG from u_0 ~ N(0, 1), u* from
     # Jacobi(4)-PCG to 1e-10; Adam steps on Eq. (11) with recomputed pre-activations
     Nf, Bf = LARGE_CASES[0]
@@ -551,6 +608,12 @@ def main():
                                                      "measured alongside)")
     ap.add_argument("--m-alt", type=int, default=1, help="second truncation reported next to the headline (0 = none)")
     ap.add_argument("--train-steps", type=int, default=16000)
+    ap.add_argument("--train-prec", default="bf16", choices=["bf16", "fp32"],
+                    help="arithmetic of the models' training steps (BF16 tensor cores or FP32 CUDA cores)")
+    ap.add_argument("--train-leg", type=int, default=1, help="run the training-throughput leg (BF16 vs FP32)")
+    ap.add_argument("--train-bench-steps", type=int, default=50)
+    ap.add_argument("--train-compare-steps", type=int, default=4000,
+                    help="steps of the two same-seed models (BF16, FP32) compared by eval iterations (0 = skip)")
     ap.add_argument("--train-instances", type=int, default=512)
     ap.add_argument("--max-iter", type=int, default=400,
                     help="iteration cap (CG needs ~400 on this workload); capped instances are not counted")
@@ -627,7 +690,7 @@ def main():
         return
     if args.train_steps > 0:
         tr = T.train(model, N_GRID, range(0, args.train_instances), K=100, batch=32, lr=1e-3, steps=args.train_steps,
-                     log_every=1000)
+                     log_every=1000, prec=args.train_prec)
 
     # ---- eval inputs (resident)
     seeds = R.rank_seeds(rank, EVAL_BATCH)
@@ -773,6 +836,7 @@ def main():
                        "l2": "flushed (256 MB write) between timed steps",
                        "training": None if tr is None else {"steps": tr.steps, "batch": 32, "instances":
                                                             args.train_instances, "krylov_K": 100,
+                                                            "prec": args.train_prec,
                                                             "seconds": round(tr.seconds, 2),
                                                             "loss_log": [(s_, round(l_, 4)) for s_, l_ in tr.losses]},
                        "max_iter": args.max_iter,
@@ -818,6 +882,13 @@ def main():
         ms, res = timed_steps(jac_step, 2, 1, flush, stream)
         line["jacobi4_pcg"] = dict(solve_summary(ms, res, F), m=1, preconditioner="Jacobi(4), Eq. (15)")
 
+    # ---- training throughput, BF16 tensor cores against FP32 CUDA cores
+    if rank == 0 and args.train_leg:
+        def eval_iters(m_):
+            res = solve_once(model_=m_)
+            return [i["iters"] for i in res], sum(1 for i in res if i["status"] == F.FCGNO_OK)
+        line["train"] = run_train_leg(args, desc_np, dev, eval_iters)
+
     # ---- the model served and transferred: trained at 64 x 64 on the sigma mixture the
     # serving stream and the transfer configuration draw (0.5, 1, 2)
     model_mix, tr_mix = None, None
@@ -825,9 +896,10 @@ def main():
         blob_mix = torch.from_numpy(I.xavier_weights(desc_np, 2)).to(dev)
         model_mix = F.Model(F.make_desc(WIDTH, LAYERS, MODES, WIDTH, output_scale=args.output_scale), blob_mix)
         tr_mix = T.train(model_mix, N_GRID, range(0, args.mix_train_instances), K=100, batch=32, lr=1e-3,
-                         steps=args.mix_train_steps, sigma=SERVE_SIGMAS)
+                         steps=args.mix_train_steps, sigma=SERVE_SIGMAS, prec=args.train_prec)
         line["config"]["training_mix"] = {"steps": tr_mix.steps, "batch": 32, "instances": args.mix_train_instances,
-                                          "sigmas": list(SERVE_SIGMAS), "seconds": round(tr_mix.seconds, 2)}
+                                          "sigmas": list(SERVE_SIGMAS), "seconds": round(tr_mix.seconds, 2),
+                                          "prec": args.train_prec}
     # ---- resolution transfer (128..512 grids, sigma 0.5 / 1 / 2)
     if rank == 0 and args.transfer:
         line["transfer"] = run_transfer(args, model_mix, dev, flush, stream)

@@ -24,8 +24,8 @@
  *    gives up sets its operator's error flag and returns. fcgno_solve and fcgno_bucket_poll
  *    read and clear that flag after their own synchronisation and then return FCGNO_ETIMEOUT
  *    (the results of that call are invalid); a timeout inside the asynchronous
- *    fcgno_precond_apply is reported by the next fcgno_solve or fcgno_bucket_poll on the
- *    same operator.
+ *    fcgno_precond_apply or a FCGNO_BF16 fcgno_train_step is reported by the next
+ *    fcgno_solve or fcgno_bucket_poll on the same operator.
  *  - Every computation runs in CUDA kernels of this library (sm_103a); there is no host
  *    fallback.
  *  - Concurrency: calls on different operators may run on different streams at the same
@@ -221,7 +221,14 @@ fcgno_status fcgno_krylov_harvest(fcgno_op_t A, const double* b, const double* x
  * loss = mean_b ||z_b - e_b||_A / ||e_b||_A with z_b = NO(r_b, log k_b), and its gradient
  * with respect to every weight of the blob. r, e: [batch][N][N] (batch = op's batch).
  * loss: device float scalar; grad: device float blob (same layout as the weights), both
- * overwritten. prec: FCGNO_FP32 (forward/backward on CUDA cores, FP32) or FCGNO_FP64.
+ * overwritten. prec: FCGNO_FP32 (forward/backward on CUDA cores, FP32), FCGNO_FP64, or
+ * FCGNO_BF16 (Section 2.4.1's mixed precision: the Fourier layers' forward and backward run
+ * on the tensor cores with BF16 operands and FP32 accumulation; the encoder, decoder, loss
+ * (FP64) and every weight-gradient reduction run in FP32 on CUDA cores). FCGNO_BF16 takes the
+ * model shapes and grids of the 16-bit preconditioner (else EINVAL), keeps its saved
+ * activations with the operator, and re-derives the model's BF16 weight images from the FP32
+ * master blob on every call (an optimiser may change the blob between calls; the
+ * preconditioner then follows the new weights without fcgno_model_sync).
  * Uses the FP32 master blob given to fcgno_model_create.
  * Errors: EINVAL for a NULL pointer, batch != op's batch, another precision or
  * N < 2*modes; ENOMEM; ECUDA. */

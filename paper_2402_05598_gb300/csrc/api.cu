@@ -274,8 +274,12 @@ extern "C" fcgno_status fcgno_train_step_loss(fcgno_model_t model, fcgno_op_t op
     set_last_error("fcgno_train_step: null argument or batch != op batch");
     return FCGNO_EINVAL;
   }
-  if (prec != FCGNO_FP32 && prec != FCGNO_FP64) {
-    set_last_error("fcgno_train_step: precision must be FCGNO_FP32 or FCGNO_FP64");
+  if (prec != FCGNO_FP32 && prec != FCGNO_FP64 && prec != FCGNO_BF16) {
+    set_last_error("fcgno_train_step: precision must be FCGNO_FP32, FCGNO_FP64 or FCGNO_BF16");
+    return FCGNO_EINVAL;
+  }
+  if (prec == FCGNO_BF16 && !tc_shape_supported(op->N, model->desc)) {
+    set_last_error(tc_shape_rule());
     return FCGNO_EINVAL;
   }
   if (loss_kind != FCGNO_LOSS_ENERGY && loss_kind != FCGNO_LOSS_L2) {
@@ -286,7 +290,7 @@ extern "C" fcgno_status fcgno_train_step_loss(fcgno_model_t model, fcgno_op_t op
     set_last_error("fcgno_train_step: grid smaller than 2*modes");
     return FCGNO_EINVAL;
   }
-  return train_step_simt(model, op, r, e, loss, grad, prec == FCGNO_FP64, loss_kind == FCGNO_LOSS_L2,
+  return train_step_simt(model, op, r, e, loss, grad, prec, loss_kind == FCGNO_LOSS_L2,
                          (cudaStream_t)stream);
 }
 

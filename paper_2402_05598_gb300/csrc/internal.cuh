@@ -287,9 +287,30 @@ void no_workspace_free(fcgno_model* m);
 // Per-instance rms of r: rms[b] = sqrt(mean(r_b^2)).
 fcgno_status launch_rms(const double* r, int B, size_t n, double* rms, cudaStream_t st);
 
-// Training: energy-norm loss of Eq. (11), or (l2) the 2-norm ablation loss.
+// Training: energy-norm loss of Eq. (11), or (l2) the 2-norm ablation loss. prec: FCGNO_FP32,
+// FCGNO_FP64 (CUDA cores throughout) or FCGNO_BF16 (the Fourier layers forward and backward
+// on the tensor cores, the rest on CUDA cores in FP32).
 fcgno_status train_step_simt(fcgno_model* m, fcgno_op* op, const double* r, const double* e,
-                             float* loss, float* grad, bool fp64, bool l2, cudaStream_t st);
+                             float* loss, float* grad, fcgno_prec prec, bool l2, cudaStream_t st);
+
+// Pieces of the BF16 training step (tensor-core path; wide launch shape, every instance active).
+// begin: weight images (forward and transposed) from the current master blob, forward and
+// adjoint tables, activation and training buffers. forward: encoder and Fourier layers with the
+// backward's saves; cx[l] (FP32 [B][mode][C] complex) receives layer l's analysis output.
+// to_f32: saved layer input `which` (0..L), or the current input gradient (which = -1), as FP32
+// [B][N][N][C]. act_bwd: the pre-activation gradient of layer l from the gradient of its output
+// (gv32, FP32 [B][N][N][C]; null: the one the previous layer_bwd left), into gh32 and the
+// tile-major copy layer_bwd reads. layer_bwd: adjoint analysis (kept: gspec), adjoint mixing and
+// adjoint synthesis of layer l, leaving the gradient of its input.
+fcgno_status tc_train_begin(fcgno_model* m, const fcgno_op* op, cudaStream_t st);
+fcgno_status tc_train_forward(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms,
+                              float* const* cx, cudaStream_t st);
+fcgno_status tc_train_to_f32(const fcgno_model* m, const fcgno_op* op, int which, float* out, cudaStream_t st);
+fcgno_status tc_train_act_bwd(const fcgno_model* m, const fcgno_op* op, int l, const float* gv32, float* gh32,
+                              cudaStream_t st);
+fcgno_status tc_train_layer_bwd(fcgno_model* m, const fcgno_op* op, int l, cudaStream_t st);
+const float* tc_train_gspec(const fcgno_op* op);
+size_t tc_train_bytes(int N, int B, const fcgno_model_desc& d);
 
 inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 

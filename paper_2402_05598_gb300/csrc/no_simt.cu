@@ -793,25 +793,19 @@ static fcgno_status outer_reduce(size_t npts, int Co, int Ci, const T* A, const 
   return FCGNO_OK;
 }
 
+// Loss (FP64) of the forward output in t.zbuf and the decoder's backward: the decoder's
+// weight gradients, and the gradient of the last Fourier layer's output (FP32 or FP64,
+// [B][N][N][C]) left in t.g0. `grad` is zeroed first. vL: the last layer's output.
 template <typename T>
-static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, const double* e, float* loss,
-                               float* grad, bool l2, cudaStream_t st) {
+static fcgno_status loss_and_decoder_bwd(fcgno_model* m, fcgno_op* op, const double* e, float* loss, float* grad,
+                                         bool l2, const T* vL, const Wp<T>& W, cudaStream_t st) {
   const fcgno_model_desc& d = m->desc;
-  const int N = op->N, B = op->B, C = d.width, M = d.modes, Cp = d.proj_width, L = d.layers;
+  const int N = op->N, B = op->B, C = d.width, Cp = d.proj_width;
   const size_t n = op->n, pts = (size_t)B * n;
-  const int Kx = 2 * M, Ky = M, nmodes = Kx * Ky;
-  FCGNO_TRY(ensure_train(m, op, sizeof(T)));
-  SimtBuffers& s = (sizeof(T) == 8) ? m->ws->f64 : m->ws->f32;
-  FCGNO_TRY(ensure_simt<T>(m, op, s));
   TrainBuffers& t = m->ws->tr;
-  const T* wbase = (sizeof(T) == 8) ? (const T*)m->w64 : (const T*)m->w32;
-  Wp<T> W = wptrs<T>(m, wbase);
   BlobLayout BL = blob_layout(d);
-  // forward with saves
-  FCGNO_TRY(launch_rms(r, B, n, t.rms, st));
-  FCGNO_TRY(forward_simt<T>(m, op, wbase, r, t.rms, nullptr, t.zbuf, s, &t, nullptr, st));
-  // loss (FP64): d = z - e, then A d and A e (energy norm, Eq. (11)) or d and e themselves
-  // (2-norm of the L2 ablation loss)
+  // d = z - e, then A d and A e (energy norm, Eq. (11)) or d and e themselves (2-norm of the
+  // L2 ablation loss)
   double* dv = t.dvec;
   const double* Ad = dv;
   const double* Ae = e;
@@ -828,12 +822,9 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
   loss_value_kernel<<<1, 32, 0, st>>>(B, t.lossb, loss);
   FCGNO_LAUNCHED();
   FCGNO_CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(float) * BL.total, st));
-  // backward
-  const T *tw1, *tw2;
-  tw_ptrs<T>(m->ws->tw, tw1, tw2);
   T* gzt = (T*)t.gz;
   dzt_kernel<T><<<ceil_div(pts, 256), 256, 0, st>>>(B, n, 1.0 / ((double)(N + 1) * (N + 1)), Ad, t.lossb, t.rms,
-                                                    m->desc.output_scale ? op->kinv : nullptr, gzt);
+                                                    d.output_scale ? op->kinv : nullptr, gzt);
   FCGNO_LAUNCHED();
   // decoder: proj2 grads (A = gzt [pts][1], V = GELU(a) [pts][Cp])
   FCGNO_TRY(outer_reduce<T>(pts, 1, Cp, gzt, (const T*)t.ghid, (T*)t.partials, grad + BL.proj2_w,
@@ -843,8 +834,32 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
   project_bwd_kernel<T><<<ceil_div(pts, 128), 128, (size_t)Cp * C * sizeof(T), st>>>(pts, C, Cp, gzt, (const T*)t.apre,
                                                                                      W.proj1_w, W.proj2_w, ga, gv);
   FCGNO_LAUNCHED();
-  FCGNO_TRY(outer_reduce<T>(pts, Cp, C, ga, (const T*)t.vin[L], (T*)t.partials, grad + BL.proj1_w,
-                            grad + BL.proj1_b, st));
+  FCGNO_TRY(outer_reduce<T>(pts, Cp, C, ga, vL, (T*)t.partials, grad + BL.proj1_w, grad + BL.proj1_b, st));
+  return FCGNO_OK;
+}
+
+template <typename T>
+static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, const double* e, float* loss,
+                               float* grad, bool l2, cudaStream_t st) {
+  const fcgno_model_desc& d = m->desc;
+  const int N = op->N, B = op->B, C = d.width, M = d.modes, L = d.layers;
+  const size_t n = op->n, pts = (size_t)B * n;
+  const int Kx = 2 * M, Ky = M, nmodes = Kx * Ky;
+  FCGNO_TRY(ensure_train(m, op, sizeof(T)));
+  SimtBuffers& s = (sizeof(T) == 8) ? m->ws->f64 : m->ws->f32;
+  FCGNO_TRY(ensure_simt<T>(m, op, s));
+  TrainBuffers& t = m->ws->tr;
+  const T* wbase = (sizeof(T) == 8) ? (const T*)m->w64 : (const T*)m->w32;
+  Wp<T> W = wptrs<T>(m, wbase);
+  BlobLayout BL = blob_layout(d);
+  // forward with saves
+  FCGNO_TRY(launch_rms(r, B, n, t.rms, st));
+  FCGNO_TRY(forward_simt<T>(m, op, wbase, r, t.rms, nullptr, t.zbuf, s, &t, nullptr, st));
+  FCGNO_TRY(loss_and_decoder_bwd<T>(m, op, e, loss, grad, l2, (const T*)t.vin[L], W, st));
+  // backward
+  const T *tw1, *tw2;
+  tw_ptrs<T>(m->ws->tw, tw1, tw2);
+  T* gv = (T*)t.g0;
   const T inv_n = (T)(1.0 / (double)n);
   T* gh = (T*)t.g1;
   for (int l = L - 1; l >= 0; --l) {
@@ -885,14 +900,63 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
   return FCGNO_OK;
 }
 
+// The BF16 training step: the Fourier layers forward and backward on the tensor cores (BF16
+// operands, FP32 accumulation), everything else in FP32 on CUDA cores from the FP32 master
+// weights (encoder, decoder, loss in FP64, every weight-gradient reduction).
+static fcgno_status train_impl_tc(fcgno_model* m, fcgno_op* op, const double* r, const double* e, float* loss,
+                                  float* grad, bool l2, cudaStream_t st) {
+  const fcgno_model_desc& d = m->desc;
+  const int B = op->B, C = d.width, M = d.modes, L = d.layers;
+  const size_t n = op->n, pts = (size_t)B * n;
+  const int nmodes = 2 * M * M;
+  FCGNO_TRY(ensure_train(m, op, sizeof(float)));
+  TrainBuffers& t = m->ws->tr;
+  Wp<float> W = wptrs<float>(m, m->w32);
+  BlobLayout BL = blob_layout(d);
+  FCGNO_TRY(tc_train_begin(m, op, st));
+  FCGNO_TRY(launch_rms(r, B, n, t.rms, st));
+  // the encoder's input x0 = (r / rms, log k) and its FP32 output, for the encoder's and the
+  // first layer's weight gradients
+  lift_kernel<float><<<dim3(ceil_div(n, 256), B), 256, 0, st>>>(B, n, C, r, op->logk, t.rms, nullptr, W.lift_w,
+                                                                W.lift_b, (float*)t.vin[0], (float*)t.x0);
+  FCGNO_LAUNCHED();
+  float* cx[16];
+  for (int l = 0; l < L; ++l) cx[l] = (float*)t.chat[l];
+  FCGNO_TRY(tc_train_forward(m, op, r, t.rms, cx, st));
+  for (int l = 1; l <= L; ++l) FCGNO_TRY(tc_train_to_f32(m, op, l, (float*)t.vin[l], st));
+  const size_t smem = (size_t)d.proj_width * C * sizeof(float);
+  project_kernel<float><<<dim3(ceil_div(n, 128), B), 128, smem, st>>>(
+      n, C, d.proj_width, nullptr, (const float*)t.vin[L], W.proj1_w, W.proj1_b, W.proj2_w, W.proj2_b, t.rms,
+      1.0 / ((double)(op->N + 1) * (op->N + 1)), d.output_scale ? op->kinv : nullptr, t.zbuf, (float*)t.apre,
+      (float*)t.ghid, nullptr);
+  FCGNO_LAUNCHED();
+  FCGNO_TRY(loss_and_decoder_bwd<float>(m, op, e, loss, grad, l2, (const float*)t.vin[L], W, st));
+  float* gh = (float*)t.g1;
+  for (int l = L - 1; l >= 0; --l) {
+    FCGNO_TRY(tc_train_act_bwd(m, op, l, l == L - 1 ? (const float*)t.g0 : nullptr, gh, st));
+    FCGNO_TRY(outer_reduce<float>(pts, C, C, gh, (const float*)t.vin[l], (float*)t.partials, grad + BL.w[l],
+                                  grad + BL.b[l], st));
+    FCGNO_TRY(tc_train_layer_bwd(m, op, l, st));
+    spectral_wgrad_kernel<float><<<nmodes, 256, 0, st>>>(B, C, nmodes, (const Cx<float>*)t.chat[l],
+                                                         (const Cx<float>*)tc_train_gspec(op), grad + BL.r[l]);
+    FCGNO_LAUNCHED();
+  }
+  // encoder: A = gv0 [pts][C], V = x0 [pts][2]
+  FCGNO_TRY(tc_train_to_f32(m, op, -1, (float*)t.g0, st));
+  FCGNO_TRY(outer_reduce<float>(pts, C, 2, (const float*)t.g0, (const float*)t.x0, (float*)t.partials,
+                                grad + BL.lift_w, grad + BL.lift_b, st));
+  return FCGNO_OK;
+}
+
 fcgno_status train_step_simt(fcgno_model* m, fcgno_op* op, const double* r, const double* e, float* loss,
-                             float* grad, bool fp64, bool l2, cudaStream_t st) {
+                             float* grad, fcgno_prec prec, bool l2, cudaStream_t st) {
   if (m->desc.width > 32 || m->desc.proj_width > 32 || 256 % m->desc.width != 0) {
     set_last_error("training supports width and proj_width <= 32 dividing 256");
     return FCGNO_EINVAL;
   }
   if (!m->ws) m->ws = new NoWorkspace();
-  if (fp64) return train_impl<double>(m, op, r, e, loss, grad, l2, st);
+  if (prec == FCGNO_BF16) return train_impl_tc(m, op, r, e, loss, grad, l2, st);
+  if (prec == FCGNO_FP64) return train_impl<double>(m, op, r, e, loss, grad, l2, st);
   return train_impl<float>(m, op, r, e, loss, grad, l2, st);
 }
 

@@ -174,7 +174,11 @@ __device__ __forceinline__ void cs_of(long long k, long long x, int N, float& c,
   s = (float)sd;
 }
 
-__global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G, uint16_t* H, uint16_t* Asyn) {
+// adjoint: the tables of the transposed transforms used by the training backward: the analysis
+// becomes the synthesis's adjoint (E2 rows k2 > 0 doubled, G without 1/n) and the synthesis the
+// analysis's adjoint (Asyn with 1/n and without the doubling).
+__global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G, uint16_t* H, uint16_t* Asyn,
+                                 bool adjoint) {
   const int N = g.N, M = g.M, Ky = g.Ky;
   const float inv_n = 1.0f / ((float)N * (float)N);
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -186,6 +190,7 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
       float c, s;
       cs_of(k2, q, N, c, s);
       v = t ? -s : c;
+      if (adjoint && k2 > 0) v *= 2.f;
     }
     E2[(size_t)(q / g.QC) * 32 * g.QC + kmajor_off(row, q % g.QC, 128, g.QC * 16) / 2] = f2h16(v, bf16);
   }
@@ -200,7 +205,7 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
       cs_of(k1, p, N, c, s);
       if (tp == 0) v = t == 0 ? c : s;
       else v = t == 0 ? -s : c;
-      v *= inv_n;
+      if (!adjoint) v *= inv_n;
     }
     G[(size_t)(k / (2 * g.PC)) * g.NPM * 2 * g.PC + kmajor_off(row, k % (2 * g.PC), 128, 2 * g.PC * 16) / 2] =
         f2h16(v, bf16);
@@ -237,7 +242,7 @@ __global__ void tc_tables_kernel(TcGeom g, bool bf16, uint16_t* E2, uint16_t* G,
     if (pl < g.PT && pk == pl && k < g.PT * 2 * Ky) {
       float c, s;
       cs_of(k2, q, N, c, s);
-      const float w = k2 == 0 ? 1.f : 2.f;
+      const float w = adjoint ? inv_n : (k2 == 0 ? 1.f : 2.f);
       v = w * (t == 0 ? c : -s);
     }
     const int img = N < 128 ? 0 : m / 128, ir = N < 128 ? m : m % 128;
@@ -250,6 +255,8 @@ struct TcPrecision {
   bool built = false;
   std::vector<uint16_t*> W;   // [L] C x C image (K-major)
   std::vector<uint16_t*> Rr;  // [L] nmodes images 2C x 2C (K-major)
+  std::vector<uint16_t*> WT;  // [L] images of W^T and of the transposed real mode matrices (training
+  std::vector<uint16_t*> RrT; //     backward; built on demand)
   uint16_t* P1 = nullptr;     // Cp x C image (K-major)
   std::map<int, TcTables> tables;
 };
@@ -260,6 +267,23 @@ struct fcgno::TcModel {
   TcPrecision prec[2];  // 0: BF16, 1: FP16
 };
 
+// Training state of the BF16 path for one operator: what the backward needs from the forward
+// (every layer's input and pre-activation, tile-major) and the backward's own tile-major
+// gradients and partial-coefficient images. One allocation; capacities follow the op's shape.
+namespace fcgno {
+struct TcTrainBufs {
+  size_t bytes = 0;
+  void* base = nullptr;
+  uint16_t* v[17] = {};       // layer inputs v_0 .. v_L (v_L: the last Fourier layer's output)
+  uint16_t* h[16] = {};       // pre-activations of the layers with GELU
+  uint16_t* gh = nullptr;     // gradient w.r.t. a layer's pre-activation
+  uint16_t* gv = nullptr;     // gradient w.r.t. a layer's input
+  uint16_t* partb = nullptr;  // partial-coefficient images of the backward's analysis
+  float* gspec = nullptr;     // [B][mode][C] complex: that analysis summed over column chunks
+  float* zero = nullptr;      // [C] zeros: the bias of the adjoint synthesis
+};
+}  // namespace fcgno
+
 struct fcgno::TcActs {
   size_t cap_v = 0, cap_part = 0, cap_chat = 0;
   uint16_t* va = nullptr;
@@ -267,34 +291,47 @@ struct fcgno::TcActs {
   uint16_t* part = nullptr;  // partial-coefficient images [mode][chunk][block of 128][128 x 2C]
   uint16_t* chat = nullptr;  // mixed-coefficient images, one per instance
   int* err = nullptr;        // set to 1 by a kernel whose bounded wait ran out (kept across regrowth)
+  fcgno::TcTrainBufs train;  // training (allocated on the first 16-bit training step)
 };
 
 namespace fcgno {
 
-// rows x cols row-major FP32 -> 16-bit image of the K-major shared-memory layout (K = cols)
+// rows x cols row-major FP32 -> 16-bit image of the K-major shared-memory layout (K = cols);
+// transpose: the image of in^T (in is then cols x rows row-major)
 __global__ void tc_cast_image_kernel(int rows, int cols, const float* __restrict__ in, uint16_t* __restrict__ out,
-                                     bool bf16) {
+                                     bool bf16, bool transpose) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= rows * cols) return;
   const int r = i / cols, k = i % cols;
-  out[kmajor_off(r, k, 128, cols * 16) / 2] = f2h16(in[i], bf16);
+  out[kmajor_off(r, k, 128, cols * 16) / 2] = f2h16(transpose ? in[k * rows + r] : in[i], bf16);
 }
 
-// Rr[mode]: image (K-major, 2C x 2C) of the real form [(o,t')][(i,t)] of R[mode][i][o][re/im]
-__global__ void tc_rr_kernel(int C, int nmodes, const float* __restrict__ R, uint16_t* __restrict__ Rr, bool bf16) {
+// Rr[mode]: image (K-major, 2C x 2C) of the real form [(o,t')][(i,t)] of R[mode][i][o][re/im];
+// transpose: the image of its transpose [(i,t)][(o,t')], the real form of the conjugate
+// transpose of R[mode] (the mixing's adjoint)
+__global__ void tc_rr_kernel(int C, int nmodes, const float* __restrict__ R, uint16_t* __restrict__ Rr, bool bf16,
+                             bool transpose) {
   const size_t total = (size_t)nmodes * 4 * C * C;
   const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (idx >= total) return;
   const int C2 = 2 * C;
   const size_t mode = idx / (C2 * C2);
   const int rem = (int)(idx % (C2 * C2));
-  const int row = rem / C2, col = rem % C2;
+  const int irow = rem / C2, icol = rem % C2;
+  const int row = transpose ? icol : irow, col = transpose ? irow : icol;  // element of the real form
   const int o = row >> 1, tp = row & 1, i = col >> 1, t = col & 1;
   const float re = R[((mode * C + i) * C + o) * 2], im = R[((mode * C + i) * C + o) * 2 + 1];
   float v;
   if (tp == 0) v = t == 0 ? re : -im;
   else v = t == 0 ? im : re;
-  Rr[(size_t)mode * C2 * C2 + kmajor_off(row, col, 128, C2 * 16) / 2] = f2h16(v, bf16);
+  Rr[(size_t)mode * C2 * C2 + kmajor_off(irow, icol, 128, C2 * 16) / 2] = f2h16(v, bf16);
+}
+
+static void free_bwd_images(TcPrecision& p) {
+  for (auto x : p.WT) cudaFree(x);
+  for (auto x : p.RrT) cudaFree(x);
+  p.WT.clear();
+  p.RrT.clear();
 }
 
 static void free_prec(TcPrecision& p) {
@@ -302,6 +339,7 @@ static void free_prec(TcPrecision& p) {
   for (auto x : p.Rr) cudaFree(x);
   p.W.clear();
   p.Rr.clear();
+  free_bwd_images(p);
   if (p.P1) cudaFree(p.P1);
   p.P1 = nullptr;
   for (auto& kv : p.tables) {
@@ -326,12 +364,16 @@ static void free_acts(TcActs& A) {
   for (auto x : f)
     if (x) cudaFree(x);
   int* err = A.err;
+  TcTrainBufs train = A.train;
   A = TcActs{};
   A.err = err;
+  A.train = train;
 }
 
 void tc_acts_free(fcgno_op* op) {
   if (!op->tc_acts) return;
+  if (op->tc_acts->train.base) cudaFree(op->tc_acts->train.base);
+  op->tc_acts->train = TcTrainBufs{};
   free_acts(*op->tc_acts);
   if (op->tc_acts->err) cudaFree(op->tc_acts->err);
   delete op->tc_acts;
@@ -392,10 +434,29 @@ fcgno_status tc_model_sync(fcgno_model* m, cudaStream_t) {
       for (auto x : p.Rr) cudaFree(x);
       p.W.clear();
       p.Rr.clear();
+      free_bwd_images(p);
       if (p.P1) cudaFree(p.P1);
       p.P1 = nullptr;
       p.built = false;
     }
+  return FCGNO_OK;
+}
+
+// The 16-bit weight images of the forward (W, Rr per layer and the decoder's first layer),
+// cast from the FP32 master blob into their existing buffers.
+static fcgno_status cast_images(fcgno_model* m, TcPrecision& P, bool bf16, cudaStream_t st) {
+  const fcgno_model_desc& d = m->desc;
+  const int C = d.width, Cp = d.proj_width, nmodes = 2 * d.modes * d.modes;
+  BlobLayout BL = blob_layout(d);
+  const size_t tot = (size_t)nmodes * 4 * C * C;
+  for (int l = 0; l < d.layers; ++l) {
+    tc_cast_image_kernel<<<ceil_div(C * C, 256), 256, 0, st>>>(C, C, m->w32 + BL.w[l], P.W[l], bf16, false);
+    FCGNO_LAUNCHED();
+    tc_rr_kernel<<<ceil_div(tot, 256), 256, 0, st>>>(C, nmodes, m->w32 + BL.r[l], P.Rr[l], bf16, false);
+    FCGNO_LAUNCHED();
+  }
+  tc_cast_image_kernel<<<ceil_div(Cp * C, 256), 256, 0, st>>>(Cp, C, m->w32 + BL.proj1_w, P.P1, bf16, false);
+  FCGNO_LAUNCHED();
   return FCGNO_OK;
 }
 
@@ -405,30 +466,24 @@ static fcgno_status ensure_prec(fcgno_model* m, bool fp16, cudaStream_t st) {
   if (P.built) return FCGNO_OK;
   const fcgno_model_desc& d = m->desc;
   const int C = d.width, Cp = d.proj_width, M = d.modes, nmodes = 2 * M * M;
-  BlobLayout BL = blob_layout(d);
-  const bool bf16 = !fp16;
   P.W.assign(d.layers, nullptr);
   P.Rr.assign(d.layers, nullptr);
   for (int l = 0; l < d.layers; ++l) {
     FCGNO_CUDA_TRY(cudaMalloc(&P.W[l], sizeof(uint16_t) * C * C));
     FCGNO_CUDA_TRY(cudaMalloc(&P.Rr[l], sizeof(uint16_t) * (size_t)nmodes * 4 * C * C));
-    tc_cast_image_kernel<<<ceil_div(C * C, 256), 256, 0, st>>>(C, C, m->w32 + BL.w[l], P.W[l], bf16);
-    FCGNO_LAUNCHED();
-    const size_t tot = (size_t)nmodes * 4 * C * C;
-    tc_rr_kernel<<<ceil_div(tot, 256), 256, 0, st>>>(C, nmodes, m->w32 + BL.r[l], P.Rr[l], bf16);
-    FCGNO_LAUNCHED();
   }
   FCGNO_CUDA_TRY(cudaMalloc(&P.P1, sizeof(uint16_t) * Cp * C));
-  tc_cast_image_kernel<<<ceil_div(Cp * C, 256), 256, 0, st>>>(Cp, C, m->w32 + BL.proj1_w, P.P1, bf16);
-  FCGNO_LAUNCHED();
+  FCGNO_TRY(cast_images(m, P, !fp16, st));
   P.built = true;
   m->gen++;
   return FCGNO_OK;
 }
 
-static fcgno_status ensure_tables(fcgno_model* m, bool fp16, const TcGeom& g, TcTables*& out, cudaStream_t st) {
+static fcgno_status ensure_tables(fcgno_model* m, bool fp16, const TcGeom& g, TcTables*& out, cudaStream_t st,
+                                  bool adjoint = false) {
   TcPrecision& P = m->tc->prec[fp16 ? 1 : 0];
-  const int key = g.N * 256 + g.PC;  // the analysis tables depend on the column-chunk width
+  // the analysis tables depend on the column-chunk width; adjoint tables serve the training backward
+  const int key = (g.N * 256 + g.PC) * 2 + (adjoint ? 1 : 0);
   auto it = P.tables.find(key);
   if (it != P.tables.end() && it->second.M == g.M) {
     out = &it->second;
@@ -443,7 +498,7 @@ static fcgno_status ensure_tables(fcgno_model* m, bool fp16, const TcGeom& g, Tc
   FCGNO_CUDA_TRY(cudaMalloc(&t.H, sizeof(uint16_t) * 2 * g.N * g.KXP));
   FCGNO_CUDA_TRY(cudaMalloc(&t.Asyn, sizeof(uint16_t) * arows * g.KSYN));
   const int work = std::max(std::max(32 * g.N, g.NPM * 2 * g.N), std::max(2 * g.N * g.KXP, arows * g.KSYN));
-  tc_tables_kernel<<<ceil_div(work, 256), 256, 0, st>>>(g, !fp16, t.E2, t.G, t.H, t.Asyn);
+  tc_tables_kernel<<<ceil_div(work, 256), 256, 0, st>>>(g, !fp16, t.E2, t.G, t.H, t.Asyn, adjoint);
   FCGNO_LAUNCHED();
   P.tables[key] = t;
   out = &P.tables[key];
@@ -911,6 +966,7 @@ struct SynArgs {
   const uint16_t* H;      // [N / SPC] images 2SPC x KXP (K-major)
   const uint16_t* Asyn;   // images 128 x KSYN (K-major): one (N < 128) or one per 128-row q tile
   int activate;
+  uint16_t* hsave;        // training: pre-activations, tile-major (or null)
   // decoder (last layer)
   int project;
   const uint16_t* P1;     // C x C image (K-major)
@@ -1221,9 +1277,19 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         __syncwarp();
         if (lane == 0) mbar_arrive(&accempty[t % kSynAcc]);
 #pragma unroll
-        for (int i = 0; i < CH; ++i) {
-          const float x = h[i] + bias[i];
-          h[i] = a.activate ? gelu16(x) : x;
+        for (int i = 0; i < CH; ++i) h[i] += bias[i];
+        if (a.hsave) {
+          // training: the pre-activation of this tile row, tile-major like the output
+          uint8_t* dsth = reinterpret_cast<uint8_t*>(a.hsave + tile_index(t) * 128 * C) + m * 16;
+#pragma unroll
+          for (int c0 = 0; c0 < CH; c0 += 8)
+            *reinterpret_cast<uint4*>(dsth + ((cbase + c0) / 8) * LBO_T) =
+                make_uint4(pack2(h[c0], h[c0 + 1], bf16), pack2(h[c0 + 2], h[c0 + 3], bf16),
+                           pack2(h[c0 + 4], h[c0 + 5], bf16), pack2(h[c0 + 6], h[c0 + 7], bf16));
+        }
+        if (a.activate) {
+#pragma unroll
+          for (int i = 0; i < CH; ++i) h[i] = gelu16(h[i]);
         }
         // the output slot's previous tile (t - DO) has been decoded
         if (a.project && t >= DO) ok = mbar_wait(&outfree[t % DO], ((t / DO) - 1) & 1);
@@ -1343,6 +1409,63 @@ bool tc_has_narrow(int N, const fcgno_model_desc& d) {
   return narrow_geom(g).SPC != g.SPC;
 }
 
+// The operator's 16-bit activation buffers for grid geometry g (either launch shape).
+static fcgno_status ensure_acts(fcgno_model* m, const fcgno_op* op, const TcGeom& g, cudaStream_t st) {
+  FCGNO_TRY(ensure_err_flag(op, st));
+  TcActs& T = *op->tc_acts;
+  size_t need_v, need_part, need_chat;
+  tc_acts_elems(g, op->B, need_v, need_part, need_chat);
+  if (T.cap_v >= need_v && T.cap_part >= need_part && T.cap_chat >= need_chat) return FCGNO_OK;
+  free_acts(T);
+  if (cudaMalloc(&T.va, need_v * 2) != cudaSuccess || cudaMalloc(&T.vb, need_v * 2) != cudaSuccess ||
+      cudaMalloc(&T.part, need_part * 2) != cudaSuccess || cudaMalloc(&T.chat, need_chat * 2) != cudaSuccess) {
+    cudaGetLastError();
+    set_last_error("tensor-core preconditioner workspace: out of device memory");
+    return FCGNO_ENOMEM;
+  }
+  // the padding of the stage-1 operand images is never written: zero it once
+  FCGNO_CUDA_TRY(cudaMemsetAsync(T.chat, 0, need_chat * 2, st));
+  T.cap_v = need_v;
+  T.cap_part = need_part;
+  T.cap_chat = need_chat;
+  m->gen++;
+  return FCGNO_OK;
+}
+
+// Dynamic shared-memory limits of the three layer kernels, raised to cover both launch shapes
+// of grid geometry g (wide g), so that the other shape's first (captured) launch needs no
+// attribute change. A limit is raised only when a larger plan appears (not a stream operation;
+// the first solve iteration runs eagerly, before any graph capture). The shared-memory carveout
+// is pinned to its maximum so that two blocks of each kernel stay resident per SM; left to the
+// CUDA driver it may size the carveout for one block.
+template <int C>
+static fcgno_status raise_smem_limits(const TcGeom& g) {
+  const TcGeom gn = narrow_geom(g);
+  const size_t sa_limit = std::max(analysis_smem(g), analysis_smem(gn));
+  const size_t sm_limit = std::max(mix_smem(g), mix_smem(gn));
+  size_t ss_limit = 0;
+  for (const TcGeom& go : {g, gn}) {
+    int di, dout;
+    synthesis_rings(go, di, dout);
+    ss_limit = std::max(ss_limit, synthesis_bytes(go, go.SPC, di, dout));
+  }
+  static std::mutex set_mu;  // concurrent callers on other threads share these limits
+  static size_t set_sa = 0, set_ss = 0, set_sm = 0;
+  std::lock_guard<std::mutex> set_lk(set_mu);
+  auto raise = [](const void* fn, size_t bytes, size_t& set) -> cudaError_t {
+    if (bytes <= set) return cudaSuccess;
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
+    if (e == cudaSuccess) set = bytes;
+    return e;
+  };
+  FCGNO_CUDA_TRY(raise((const void*)tc_analysis_kernel<C>, sa_limit, set_sa));
+  FCGNO_CUDA_TRY(raise((const void*)tc_synthesis_kernel<C>, ss_limit, set_ss));
+  FCGNO_CUDA_TRY(raise((const void*)tc_mix_kernel<C>, sm_limit, set_sm));
+  return FCGNO_OK;
+}
+
 template <int C>
 static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms, const int* active,
                            double* z, bool fp16, cudaStream_t st, bool narrow) {
@@ -1369,28 +1492,10 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
     if (cap == cudaStreamCaptureStatusNone) FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
   }
   TcPrecision& P = m->tc->prec[fp16 ? 1 : 0];
-  FCGNO_TRY(ensure_err_flag(op, st));
+  FCGNO_TRY(ensure_acts(m, op, g, st));
   TcActs& T = *op->tc_acts;
   const int B = op->B;
-  const size_t n = op->n;
   const int nbt = ceil_div(B, 128);
-  size_t need_v, need_part, need_chat;
-  tc_acts_elems(g, B, need_v, need_part, need_chat);
-  if (T.cap_v < need_v || T.cap_part < need_part || T.cap_chat < need_chat) {
-    free_acts(T);
-    if (cudaMalloc(&T.va, need_v * 2) != cudaSuccess || cudaMalloc(&T.vb, need_v * 2) != cudaSuccess ||
-        cudaMalloc(&T.part, need_part * 2) != cudaSuccess || cudaMalloc(&T.chat, need_chat * 2) != cudaSuccess) {
-      cudaGetLastError();
-      set_last_error("tensor-core preconditioner workspace: out of device memory");
-      return FCGNO_ENOMEM;
-    }
-    // the padding of the stage-1 operand images is never written: zero it once
-    FCGNO_CUDA_TRY(cudaMemsetAsync(T.chat, 0, need_chat * 2, st));
-    T.cap_v = need_v;
-    T.cap_part = need_part;
-    T.cap_chat = need_chat;
-    m->gen++;
-  }
   BlobLayout BL = blob_layout(d);
   const bool bf16 = !fp16;
   {
@@ -1404,35 +1509,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   int din, dout;
   synthesis_rings(gs, din, dout);
   const size_t sa = analysis_smem(gs), ss = synthesis_bytes(gs, gs.SPC, din, dout), sm = mix_smem(gs);
-  const size_t sa_limit = std::max(analysis_smem(g), analysis_smem(gn));
-  const size_t sm_limit = std::max(mix_smem(g), mix_smem(gn));
-  // the limit covers both launch shapes, so that the other shape's first (captured) launch
-  // needs no attribute change
-  size_t ss_limit = ss;
-  {
-    const TcGeom go = narrow ? g : narrow_geom(g);
-    int di2, do2;
-    synthesis_rings(go, di2, do2);
-    ss_limit = std::max(ss_limit, synthesis_bytes(go, go.SPC, di2, do2));
-  }
-  // raise the dynamic shared-memory limit only when a larger plan appears (not a stream
-  // operation; the first solve iteration runs eagerly, before any graph capture)
-  // (the shared-memory carveout is pinned to its maximum so that two blocks of each kernel
-  // stay resident per SM; left to the CUDA driver it may size the carveout for one block)
-  static std::mutex set_mu;  // concurrent callers on other threads share these limits
-  static size_t set_sa = 0, set_ss = 0, set_sm = 0;
-  std::lock_guard<std::mutex> set_lk(set_mu);
-  auto raise = [](const void* fn, size_t bytes, size_t& set) -> cudaError_t {
-    if (bytes <= set) return cudaSuccess;
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(fn, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
-    if (e == cudaSuccess) set = bytes;
-    return e;
-  };
-  FCGNO_CUDA_TRY(raise((const void*)tc_analysis_kernel<C>, sa_limit, set_sa));
-  FCGNO_CUDA_TRY(raise((const void*)tc_synthesis_kernel<C>, ss_limit, set_ss));
-  FCGNO_CUDA_TRY(raise((const void*)tc_mix_kernel<C>, sm_limit, set_sm));
+  FCGNO_TRY(raise_smem_limits<C>(g));
   uint16_t* cur = T.va;
   uint16_t* nxt = T.vb;
   for (int l = 0; l < d.layers; ++l) {
@@ -1516,5 +1593,351 @@ fcgno_status no_apply_tc(fcgno_model* m, const fcgno_op* op, const double* r, co
   if (d.width == 16) return run_tc<16>(m, op, r, rms, active, z, fp16, st, narrow);
   return run_tc<32>(m, op, r, rms, active, z, fp16, st, narrow);
 }
+
+// ------------------------------------ training (BF16) ----------------------------------
+// The training step of Eq. (11) with BF16 operands and FP32 accumulation (Section 2.4.1):
+// the forward runs the tensor-core layers above and keeps every layer's input and
+// pre-activation (tile-major BF16) and its analysis output; the backward runs the adjoint of
+// each Fourier layer's data path on the same three kernels, with the adjoint tables and the
+// transposed weight images:
+//   analysis, adjoint tables, on gh  -> g'    = w(k2) sum_x gh(x) e^{-i theta_k(x)}
+//   mixing with the transposed real forms of R -> gc = R^H g'   (per mode)
+//   synthesis with W^T, the adjoint Asyn, zero bias, no activation
+//                                     -> gv_in = W^T gh + (1/n) Re sum_k gc e^{+i theta_k(x)}
+// The weight gradients are FP32 reductions on CUDA cores over the saved tiles converted to
+// FP32 (the per-mode one needs the analysis outputs of the forward and of the backward,
+// summed over column chunks here). The host side of the step composes these pieces with the
+// loss and the decoder.
+
+__host__ __device__ __forceinline__ void act_point_of(const TcGeom& g, int tau, int m, int& q, int& p) {
+  if (g.N < 128) {
+    p = tau * g.PT + m / g.N;
+    q = m % g.N;
+  } else {
+    q = (tau / g.N) * 128 + m;
+    p = tau % g.N;
+  }
+}
+
+__device__ __forceinline__ void unpack_bf16x8(uint4 w, float* f) {
+  const uint32_t u[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&u[i]));
+    f[2 * i] = t.x;
+    f[2 * i + 1] = t.y;
+  }
+}
+
+// One thread per (tile row, 8-channel group); consecutive threads read consecutive 16-byte
+// rows of a tile. Returns false past the end. Sets the 16-bit element offset of the row group
+// in the tile-major buffer and the FP32 offset of the same 8 channels in [B][N][N][C].
+__device__ __forceinline__ bool tile_row_group(const TcGeom& g, int B, size_t i, size_t& toff, size_t& foff) {
+  const int C = g.C, CG = C / 8;
+  const size_t n = (size_t)g.N * g.N, tiles = n / 128;
+  if (i >= (size_t)B * n * CG) return false;
+  const int m = (int)(i % 128);
+  const size_t rest = i / 128;
+  const int cg = (int)(rest % CG);
+  const size_t tile = rest / CG;
+  const int b = (int)(tile / tiles), tau = (int)(tile % tiles);
+  int q, p;
+  act_point_of(g, tau, m, q, p);
+  toff = tile * 128 * C + (size_t)cg * 1024 + (size_t)m * 8;
+  foff = ((size_t)b * n + (size_t)q * g.N + p) * C + cg * 8;
+  return true;
+}
+
+// BF16 tile-major activations -> FP32 [B][N][N][C]
+__global__ void tc_tile_to_f32_kernel(TcGeom g, int B, const uint16_t* __restrict__ v, float* __restrict__ out) {
+  size_t toff, foff;
+  if (!tile_row_group(g, B, blockIdx.x * (size_t)blockDim.x + threadIdx.x, toff, foff)) return;
+  float f[8];
+  unpack_bf16x8(*reinterpret_cast<const uint4*>(v + toff), f);
+  float4* o = reinterpret_cast<float4*>(out + foff);
+  o[0] = make_float4(f[0], f[1], f[2], f[3]);
+  o[1] = make_float4(f[4], f[5], f[6], f[7]);
+}
+
+// gh = gv * GELU'(h) (or gv where the layer has no activation, h null), from gv given in FP32
+// [B][N][N][C] (gv32) or BF16 tile-major (gvt); written in both forms. GELU' is the derivative
+// of the exact (erf) GELU at the saved BF16 pre-activation.
+__global__ void tc_act_bwd_kernel(TcGeom g, int B, const float* __restrict__ gv32, const uint16_t* __restrict__ gvt,
+                                  const uint16_t* __restrict__ h, float* __restrict__ gh32,
+                                  uint16_t* __restrict__ ght) {
+  size_t toff, foff;
+  if (!tile_row_group(g, B, blockIdx.x * (size_t)blockDim.x + threadIdx.x, toff, foff)) return;
+  float gv[8];
+  if (gv32) {
+    const float4 a = reinterpret_cast<const float4*>(gv32 + foff)[0];
+    const float4 c = reinterpret_cast<const float4*>(gv32 + foff)[1];
+    gv[0] = a.x; gv[1] = a.y; gv[2] = a.z; gv[3] = a.w;
+    gv[4] = c.x; gv[5] = c.y; gv[6] = c.z; gv[7] = c.w;
+  } else {
+    unpack_bf16x8(*reinterpret_cast<const uint4*>(gvt + toff), gv);
+  }
+  if (h) {
+    float hv[8];
+    unpack_bf16x8(*reinterpret_cast<const uint4*>(h + toff), hv);
+#pragma unroll
+    for (int i = 0; i < 8; ++i) gv[i] *= gelu_grad_f(hv[i]);
+  }
+  float4* o = reinterpret_cast<float4*>(gh32 + foff);
+  o[0] = make_float4(gv[0], gv[1], gv[2], gv[3]);
+  o[1] = make_float4(gv[4], gv[5], gv[6], gv[7]);
+  *reinterpret_cast<uint4*>(ght + toff) = make_uint4(pack2(gv[0], gv[1], true), pack2(gv[2], gv[3], true),
+                                                    pack2(gv[4], gv[5], true), pack2(gv[6], gv[7], true));
+}
+
+// Analysis partial-coefficient images (mode x column chunk x block of 128 instances, rows =
+// instances, K = (c, re/im)) summed over the column chunks in FP32: out[b][mode][c] complex.
+__global__ void tc_part_to_cx_kernel(TcGeom g, int B, int nbt, const uint16_t* __restrict__ part,
+                                     float* __restrict__ out) {
+  const int C = g.C;
+  const size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (i >= (size_t)B * g.nmodes * C) return;
+  const int c = (int)(i % C), mode = (int)((i / C) % g.nmodes), b = (int)(i / ((size_t)C * g.nmodes));
+  const int bt = b / 128, br = b % 128;
+  const size_t img = (size_t)128 * 2 * C;
+  const uint32_t off = kmajor_off(br, 2 * c, 128, 2 * C * 16) / 2;  // (re, im) adjacent
+  float re = 0.f, im = 0.f;
+  for (int ch = 0; ch < g.nchunks; ++ch) {
+    const uint32_t w = *reinterpret_cast<const uint32_t*>(part + (((size_t)mode * g.nchunks + ch) * nbt + bt) * img + off);
+    const float2 t = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&w));
+    re += t.x;
+    im += t.y;
+  }
+  out[2 * i] = re;
+  out[2 * i + 1] = im;
+}
+
+// Bytes of one operator's BF16 training state (TcTrainBufs) for `layers` layers.
+static size_t train_bufs_layout(const TcGeom& g, int B, int layers, size_t* offs) {
+  const size_t img = (size_t)B * g.N * g.N * g.C * 2;
+  size_t v, part, chat;
+  tc_acts_elems(g, B, v, part, chat);
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (bytes + 255) / 256 * 256;
+    return at;
+  };
+  int k = 0;
+  for (int l = 0; l <= layers; ++l) offs[k++] = take(img);           // v
+  for (int l = 0; l + 1 < layers; ++l) offs[k++] = take(img);        // h
+  offs[k++] = take(img);                                             // gh
+  offs[k++] = take(img);                                             // gv
+  offs[k++] = take(part * 2);                                        // partb
+  offs[k++] = take((size_t)B * g.nmodes * g.C * 2 * sizeof(float));  // gspec
+  offs[k++] = take((size_t)g.C * sizeof(float));                     // zero
+  return o;
+}
+
+static fcgno_status ensure_train_bufs(const fcgno_op* op, const TcGeom& g, int layers, cudaStream_t st) {
+  TcTrainBufs& tb = op->tc_acts->train;
+  size_t offs[2 * 16 + 8];
+  const size_t bytes = train_bufs_layout(g, op->B, layers, offs);
+  if (tb.base && tb.bytes == bytes) return FCGNO_OK;
+  if (tb.base) cudaFree(tb.base);
+  tb = TcTrainBufs{};
+  if (cudaMalloc(&tb.base, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    tb.base = nullptr;
+    set_last_error("BF16 training workspace: out of device memory");
+    return FCGNO_ENOMEM;
+  }
+  tb.bytes = bytes;
+  uint8_t* b = (uint8_t*)tb.base;
+  int k = 0;
+  for (int l = 0; l <= layers; ++l) tb.v[l] = (uint16_t*)(b + offs[k++]);
+  for (int l = 0; l + 1 < layers; ++l) tb.h[l] = (uint16_t*)(b + offs[k++]);
+  tb.gh = (uint16_t*)(b + offs[k++]);
+  tb.gv = (uint16_t*)(b + offs[k++]);
+  tb.partb = (uint16_t*)(b + offs[k++]);
+  tb.gspec = (float*)(b + offs[k++]);
+  tb.zero = (float*)(b + offs[k++]);
+  FCGNO_CUDA_TRY(cudaMemsetAsync(tb.zero, 0, sizeof(float) * g.C, st));
+  return FCGNO_OK;
+}
+
+size_t tc_train_bytes(int N, int B, const fcgno_model_desc& d) {
+  if (!tc_shape_supported(N, d)) return 0;
+  size_t offs[2 * 16 + 8];
+  return train_bufs_layout(make_geom(N, d.width, d.modes), B, d.layers, offs);
+}
+
+// One synthesis launch of the hidden-layer kind (the epilogue stores the tile rows itself).
+template <int C>
+static fcgno_status launch_syn_hidden(const TcGeom& g, const fcgno_op* op, const uint16_t* vin, uint16_t* vout,
+                                      const uint16_t* chat, const uint16_t* W, const float* bias,
+                                      const TcTables* tab, int activate, uint16_t* hsave, cudaStream_t st) {
+  int din, dout;
+  synthesis_rings(g, din, dout);
+  const size_t ss = synthesis_bytes(g, g.SPC, din, dout);
+  const size_t slot_in = (size_t)128 * C * 2 + (g.N >= 128 ? (size_t)128 * g.KSYN * 2 : 0);
+  SynArgs s{};
+  s.g = g;
+  s.B = op->B;
+  s.bf16 = 1;
+  s.din = std::min<int>(kSynMaxIn, (int)(((size_t)din * slot_in + (size_t)dout * 128 * C * 2) / slot_in));
+  s.dout = 0;
+  s.active = nullptr;
+  s.vin = vin;
+  s.vout = vout;
+  s.chat = chat;
+  s.W = W;
+  s.bias = bias;
+  s.H = tab->H;
+  s.Asyn = tab->Asyn;
+  s.activate = activate;
+  s.hsave = hsave;
+  s.project = 0;
+  s.err = op->tc_acts->err;
+  FCGNO_CUDA_TRY(launch_chained(tc_synthesis_kernel<C>, dim3(g.snchunks, op->B), dim3(kSynThreads), ss, st, s));
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+template <int C>
+static fcgno_status launch_ana(const TcGeom& g, const fcgno_op* op, const uint16_t* v, const TcTables* tab,
+                               uint16_t* part, cudaStream_t st) {
+  FCGNO_CUDA_TRY(launch_chained(tc_analysis_kernel<C>, dim3(g.nchunks, op->B), dim3(kAnaThreads), analysis_smem(g),
+                                st, g, ceil_div(op->B, 128), true, (const int*)nullptr, v, (const uint16_t*)tab->E2,
+                                (const uint16_t*)tab->G, part, op->tc_acts->err));
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+template <int C>
+static fcgno_status launch_mixing(const TcGeom& g, const fcgno_op* op, const uint16_t* part, const uint16_t* Rr,
+                                  uint16_t* chat, cudaStream_t st) {
+  const int nbt = ceil_div(op->B, 128);
+  FCGNO_CUDA_TRY(launch_chained(tc_mix_kernel<C>, dim3(g.nmodes, nbt), dim3(kTcThreads), mix_smem(g), st, g, op->B,
+                                nbt, true, (const int*)nullptr, part, Rr, chat, op->tc_acts->err));
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+static fcgno_status part_to_cx(const TcGeom& g, const fcgno_op* op, const uint16_t* part, float* out,
+                               cudaStream_t st) {
+  const size_t total = (size_t)op->B * g.nmodes * g.C;
+  tc_part_to_cx_kernel<<<ceil_div(total, 256), 256, 0, st>>>(g, op->B, ceil_div(op->B, 128), part, out);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+fcgno_status tc_train_begin(fcgno_model* m, const fcgno_op* op, cudaStream_t st) {
+  const fcgno_model_desc& d = m->desc;
+  if (!tc_shape_supported(op->N, d)) {
+    set_last_error(tc_shape_rule());
+    return FCGNO_EINVAL;
+  }
+  const TcGeom g = make_geom(op->N, d.width, d.modes);
+  // weight images from the current master blob (the optimiser changes it between steps)
+  const bool had = m->tc && m->tc->prec[0].built;
+  FCGNO_TRY(ensure_prec(m, false, st));
+  TcPrecision& P = m->tc->prec[0];
+  if (had) FCGNO_TRY(cast_images(m, P, true, st));
+  const int C = d.width, nmodes = g.nmodes;
+  BlobLayout BL = blob_layout(d);
+  if (P.WT.empty()) {
+    P.WT.assign(d.layers, nullptr);
+    P.RrT.assign(d.layers, nullptr);
+    for (int l = 0; l < d.layers; ++l) {
+      FCGNO_CUDA_TRY(cudaMalloc(&P.WT[l], sizeof(uint16_t) * C * C));
+      FCGNO_CUDA_TRY(cudaMalloc(&P.RrT[l], sizeof(uint16_t) * (size_t)nmodes * 4 * C * C));
+    }
+  }
+  const size_t tot = (size_t)nmodes * 4 * C * C;
+  for (int l = 0; l < d.layers; ++l) {
+    tc_cast_image_kernel<<<ceil_div(C * C, 256), 256, 0, st>>>(C, C, m->w32 + BL.w[l], P.WT[l], true, true);
+    FCGNO_LAUNCHED();
+    tc_rr_kernel<<<ceil_div(tot, 256), 256, 0, st>>>(C, nmodes, m->w32 + BL.r[l], P.RrT[l], true, true);
+    FCGNO_LAUNCHED();
+  }
+  TcTables* tab = nullptr;
+  FCGNO_TRY(ensure_tables(m, false, g, tab, st));
+  FCGNO_TRY(ensure_tables(m, false, g, tab, st, true));
+  FCGNO_TRY(ensure_acts(m, op, g, st));
+  FCGNO_TRY(ensure_train_bufs(op, g, d.layers, st));
+  if (C == 16) return raise_smem_limits<16>(g);
+  return raise_smem_limits<32>(g);
+}
+
+template <int C>
+static fcgno_status train_forward(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms,
+                                  float* const* cx, cudaStream_t st) {
+  const fcgno_model_desc& d = m->desc;
+  const TcGeom g = make_geom(op->N, C, d.modes);
+  TcPrecision& P = m->tc->prec[0];
+  TcTables* tab = nullptr;
+  FCGNO_TRY(ensure_tables(m, false, g, tab, st));
+  TcActs& T = *op->tc_acts;
+  TcTrainBufs& tb = T.train;
+  BlobLayout BL = blob_layout(d);
+  const int lift_blocks = (op->N / kLiftCols) * (op->N / lift_rows(op->N));
+  FCGNO_CUDA_TRY(launch_chained(tc_lift_kernel<C>, dim3(lift_blocks, op->B), dim3(kLiftThreads), 0, st, g, r,
+                                (const float*)op->logk32, rms, (const int*)nullptr,
+                                (const float*)(m->w32 + BL.lift_w), (const float*)(m->w32 + BL.lift_b), tb.v[0],
+                                true));
+  FCGNO_LAUNCHED();
+  for (int l = 0; l < d.layers; ++l) {
+    FCGNO_TRY(launch_ana<C>(g, op, tb.v[l], tab, T.part, st));
+    FCGNO_TRY(part_to_cx(g, op, T.part, cx[l], st));
+    FCGNO_TRY(launch_mixing<C>(g, op, T.part, P.Rr[l], T.chat, st));
+    const bool act = l < d.layers - 1;
+    FCGNO_TRY(launch_syn_hidden<C>(g, op, tb.v[l], tb.v[l + 1], T.chat, P.W[l], m->w32 + BL.b[l], tab, act,
+                                   act ? tb.h[l] : nullptr, st));
+  }
+  return FCGNO_OK;
+}
+
+fcgno_status tc_train_forward(fcgno_model* m, const fcgno_op* op, const double* r, const double* rms,
+                              float* const* cx, cudaStream_t st) {
+  if (m->desc.width == 16) return train_forward<16>(m, op, r, rms, cx, st);
+  return train_forward<32>(m, op, r, rms, cx, st);
+}
+
+fcgno_status tc_train_to_f32(const fcgno_model* m, const fcgno_op* op, int which, float* out, cudaStream_t st) {
+  const TcGeom g = make_geom(op->N, m->desc.width, m->desc.modes);
+  const TcTrainBufs& tb = op->tc_acts->train;
+  const size_t total = (size_t)op->B * op->n * (g.C / 8);
+  tc_tile_to_f32_kernel<<<ceil_div(total, 256), 256, 0, st>>>(g, op->B, which < 0 ? tb.gv : tb.v[which], out);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+fcgno_status tc_train_act_bwd(const fcgno_model* m, const fcgno_op* op, int l, const float* gv32, float* gh32,
+                              cudaStream_t st) {
+  const TcGeom g = make_geom(op->N, m->desc.width, m->desc.modes);
+  TcTrainBufs& tb = op->tc_acts->train;
+  const size_t total = (size_t)op->B * op->n * (g.C / 8);
+  tc_act_bwd_kernel<<<ceil_div(total, 256), 256, 0, st>>>(g, op->B, gv32, tb.gv,
+                                                          l < m->desc.layers - 1 ? tb.h[l] : nullptr, gh32, tb.gh);
+  FCGNO_LAUNCHED();
+  return FCGNO_OK;
+}
+
+template <int C>
+static fcgno_status train_layer_bwd(fcgno_model* m, const fcgno_op* op, int l, cudaStream_t st) {
+  const TcGeom g = make_geom(op->N, C, m->desc.modes);
+  TcPrecision& P = m->tc->prec[0];
+  TcTables* adj = nullptr;
+  FCGNO_TRY(ensure_tables(m, false, g, adj, st, true));
+  TcActs& T = *op->tc_acts;
+  TcTrainBufs& tb = T.train;
+  FCGNO_TRY(launch_ana<C>(g, op, tb.gh, adj, tb.partb, st));
+  FCGNO_TRY(part_to_cx(g, op, tb.partb, tb.gspec, st));
+  FCGNO_TRY(launch_mixing<C>(g, op, tb.partb, P.RrT[l], T.chat, st));
+  // (the adjoint tables' stage-1 table H is the forward's: the p-direction twiddles of e^{+i theta})
+  return launch_syn_hidden<C>(g, op, tb.gh, tb.gv, T.chat, P.WT[l], tb.zero, adj, 0, nullptr, st);
+}
+
+fcgno_status tc_train_layer_bwd(fcgno_model* m, const fcgno_op* op, int l, cudaStream_t st) {
+  if (m->desc.width == 16) return train_layer_bwd<16>(m, op, l, st);
+  return train_layer_bwd<32>(m, op, l, st);
+}
+
+const float* tc_train_gspec(const fcgno_op* op) { return op->tc_acts->train.gspec; }
 
 }  // namespace fcgno

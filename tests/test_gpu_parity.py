@@ -445,6 +445,87 @@ def check_train_step(lib, dev, prec, tol, kind, out_scale=0):
             assert rel(g[o:o + s], g_ref[o:o + s]) < max(tol * 10, 1e-7), name
 
 
+# BF16 training step (Fourier layers forward and backward on the tensor cores, FP32
+# accumulation, FP32 master weights). Every activation, pre-activation and gradient image is
+# rounded to 8 significant bits (u = 2^-9) between layers, so the gradient carries a few times
+# 4u of relative error, like the 16-bit preconditioner's output. Bounds (loss, gradient 2-norm,
+# worst parameter group in 2-norm and in max|g - g_ref| / max|g_ref|): twice the largest error
+# measured over these cases.
+BF16_TRAIN_TOL = {"energy": (1e-2, 2e-2, 5e-2, 5e-2), "l2": (1e-2, 3e-2, 8e-2, 1e-1)}
+
+
+@pytest.mark.parametrize("N,B,C,M,seed,out_scale,kind", [
+    (32, 3, 16, 8, 2, 0, "energy"),
+    (32, 3, 16, 8, 2, 1, "energy"),
+    (32, 3, 16, 8, 2, 0, "l2"),
+    (64, 2, 32, 12, 4, 1, "energy"),   # the training configuration's width and modes
+    (128, 1, 32, 12, 5, 1, "energy"),  # tiles of one grid column (N >= 128)
+])
+def test_bf16_train_step_matches_oracle_gradient(lib, dev, N, B, C, M, seed, out_scale, kind):
+    """fcgno_train_step with FCGNO_BF16 against the oracle's reverse mode (pinned by finite
+    differences): loss, whole gradient and every parameter group element-wise; a second call
+    returns the identical loss and gradient (no order-dependent reduction)."""
+    import torch
+    k, f = batch(N, B, 1300 + N)
+    if N <= 32:
+        es = np.stack([np.linalg.solve(O.dense_A(k[b]), f[b].ravel()).reshape(N, N) for b in range(B)])
+    else:
+        es = np.stack([O.fcg(lambda u, b=b: O.apply_A(k[b], u), lambda r: r, f[b], np.zeros((N, N)), 1, 20 * N * N,
+                             tol=1e-13)["u"] for b in range(B)])
+    desc, P, model, wdev = model_pair(lib, dev, C, M, L=4, seed=seed, out_scale=out_scale)
+    op = lib.Operator(to_dev(k, dev))
+    ref = O.notay_loss_and_grad if kind == "energy" else O.l2_loss_and_grad
+    L_ref, g_ref = ref(P, desc, list(k), list(f), list(es))
+    tl, tg, tgrp, tmax = BF16_TRAIN_TOL[kind]
+    runs = []
+    for _ in range(2):
+        loss = torch.zeros(1, dtype=torch.float32, device=dev)
+        grad = torch.full((wdev.numel(),), float("nan"), dtype=torch.float32, device=dev)
+        lib.train_step(model, op, to_dev(f, dev), to_dev(es, dev), loss, grad, prec="bf16", loss_kind=kind)
+        runs.append((loss.clone(), grad.clone()))
+    assert torch.equal(runs[0][0], runs[1][0]) and torch.equal(runs[0][1], runs[1][1])
+    loss, grad = runs[0]
+    assert abs(float(loss.item()) - L_ref) <= tl * L_ref
+    g = grad.double().cpu().numpy()
+    assert np.all(np.isfinite(g))
+    assert rel(g, g_ref) < tg
+    off = I.weight_offsets(desc)
+    for name, (o, s) in off.items():
+        if name == "_total":
+            continue
+        gg, rr = g[o:o + s], g_ref[o:o + s]
+        assert rel(gg, rr) < tgrp, name
+        assert np.max(np.abs(gg - rr)) <= tmax * np.max(np.abs(rr)), name
+
+
+def test_bf16_training_interleaves_with_solves(lib, dev):
+    """A BF16 training step between two BF16 preconditioner applications: the step refreshes
+    the weight images from the master blob, so after an in-place weight change the
+    preconditioner follows the new weights (as after fcgno_model_sync), and an FP16 training
+    step is rejected before any launch."""
+    import torch
+    N, B = 32, 2
+    k, f = batch(N, B, 1320)
+    desc, P, model, wdev = model_pair(lib, dev, 16, 8, L=4, seed=6)
+    op = lib.Operator(to_dev(k, dev))
+    r = to_dev(f, dev)
+    z0 = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    lib.precond_apply(model, op, r, z0, prec="bf16")
+    wdev.mul_(0.5)
+    loss = torch.zeros(1, dtype=torch.float32, device=dev)
+    grad = torch.zeros(wdev.numel(), dtype=torch.float32, device=dev)
+    lib.train_step(model, op, r, r, loss, grad, prec="bf16")
+    z1 = torch.empty_like(z0)
+    lib.precond_apply(model, op, r, z1, prec="bf16")
+    P2 = O.unpack_weights(wdev.double().cpu().numpy(), desc)
+    for b in range(B):
+        ref = O.no_forward(P2, desc, f[b], np.log(k[b]))
+        assert rel(z1[b].cpu().numpy(), ref) < 2e-2
+        elem_check(z1[b].cpu().numpy(), ref, ELEM_TOL["bf16"], ("after bf16 step", b))
+    with pytest.raises(RuntimeError):
+        lib.train_step(model, op, r, r, loss, grad, prec="fp16")
+
+
 @pytest.mark.parametrize("kind", ["energy", "l2"])
 def test_autograd_loss_gives_the_library_gradient(lib, dev, kind):
     """The training loss as a torch.autograd.Function: loss.backward() leaves exactly the
