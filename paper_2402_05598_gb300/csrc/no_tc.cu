@@ -1009,9 +1009,8 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
   // written (8); outfree[o] output slot o read by its store or decoder MMA; prob prologue
   // copies; s1b stage 1 done; ubar U staged in shared memory (8); decdone decoder MMA done
   __shared__ uint64_t full[kSynMaxIn], infree[kSynMaxIn], outready[kSynMaxOut], outfree[kSynMaxOut];
-  __shared__ uint64_t accfull[kSynAcc], accempty[kSynAcc], prob, s1b, ubar, decdone;
+  __shared__ uint64_t accfull[kSynAcc], accempty[kSynAcc], prob, s1b, ubar, decdone[2];
   __shared__ uint32_t tbase_s;
-  __shared__ float zpart[2][128];
   const TcGeom& g = a.g;
   const int chunk = blockIdx.x, b = blockIdx.y;
   if (tc_inactive(a.active, b)) return;
@@ -1059,7 +1058,8 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
     mbar_init(&prob, 1);
     mbar_init(&s1b, 1);
     mbar_init(&ubar, kSynEpi / 32);
-    mbar_init(&decdone, 1);
+    mbar_init(&decdone[0], 1);
+    mbar_init(&decdone[1], 1);
   }
   // zero the K tail of the staged U columns (read by padded synthesis K steps)
   const int kvalid = PC * 2 * Ky;
@@ -1075,7 +1075,7 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
   const uint32_t tbase = tbase_s;
   const uint32_t tU = tbase;                   // (MP/128) x 2PC columns (stage 1)
   const uint32_t tD = tbase;                   // kSynAcc x C tile accumulators (reuse U's columns)
-  const uint32_t tE = tbase + kSynAcc * C;     // C decoder accumulator
+  const uint32_t tE = tbase + kSynAcc * C;     // 2 x C decoder accumulators (tile parity)
   const int utiles = g.MP / 128;
   const int ntiles = (N < 128) ? PC / g.PT : PC * (N / 128);
   const size_t inst_tiles = (size_t)N * N / 128;
@@ -1119,8 +1119,8 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         const uint64_t slot = (uint64_t)(((u % DO) * TB) >> 4);
 #pragma unroll
         for (int ks = 0; ks < C / 16; ++ks)
-          mma(tE, dO0 + slot + ks * (2 * LBO_T >> 4), dP0 + ks * 16, idD, ks > 0);
-        commit(&decdone);
+          mma(tE + (u & 1) * C, dO0 + slot + ks * (2 * LBO_T >> 4), dP0 + ks * 16, idD, ks > 0);
+        commit(&decdone[u & 1]);
         commit(&outfree[u % DO]);
         decs = u + 1;
         return true;
@@ -1139,7 +1139,7 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         if (ok) s1_pending = false;
         fence_after_sync();
       }
-      constexpr int LAG = kSynAcc - 1;  // decoder of tile t - LAG issued after tile t's MMAs
+      constexpr int LAG = 2;  // decoder of tile t - LAG issued after tile t's MMAs
       for (int t = 0; t < ntiles && ok; ++t) {
         ok = mbar_wait(&full[t % DI], (t / DI) & 1);
         if (ok && t >= kSynAcc) ok = mbar_wait(&accempty[t % kSynAcc], ((t / kSynAcc) - 1) & 1);
@@ -1156,7 +1156,7 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         if (s1_pending) mbar_wait(&s1b, 0);
         for (int u = mmas > kSynAcc ? mmas - kSynAcc : 0; u < mmas; ++u)
           mbar_wait(&accfull[u % kSynAcc], (u / kSynAcc) & 1);
-        if (decs > 0) mbar_wait(&decdone, (decs - 1) & 1);
+        if (decs > 0) mbar_wait(&decdone[(decs - 1) & 1], ((decs - 1) >> 1) & 1);
         atomicExch(a.err, 1);
       }
     }
@@ -1260,6 +1260,42 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
     float bias[CH];
 #pragma unroll
     for (int c = 0; c < CH; ++c) bias[c] = a.bias[cbase + c];
+    // Last layer: the MMA warp multiplies tile u's output slot by the decoder weights into
+    // accumulator u & 1; the epilogue half u & 1 (warps 0-3 even tiles, 4-7 odd tiles) finishes
+    // tile u (GELU, -> 1, output scale, z) from all C columns of its TMEM lanes, after it has
+    // written tile u + 1's slot, so that the decoder MMA's latency overlaps that work and the
+    // halves exchange nothing. A thread's read of accumulator u & 1 precedes its arrival on tile
+    // u + 2's slot, which the MMA of decoder u + 2 (the accumulator's next use) waits for.
+    const double zscale = a.project ? a.rms[b] * a.hh : 0.0;
+    auto decoder_part = [&](int u, bool okd) -> bool {
+      if (half != (u & 1)) return okd;
+      if (okd) {
+        okd = mbar_wait(&decdone[u & 1], (u >> 1) & 1);
+        fence_after_sync();
+      }
+      if (okd) {
+        float zt = a.p2b[0];
+#pragma unroll
+        for (int c0 = 0; c0 < C; c0 += 16) {
+          float val[16];
+          tmem_ld16(tE + (u & 1) * C + c0 + lane_off, val);
+#pragma unroll
+          for (int i = 0; i < 16; ++i) zt = fmaf(a.p2[c0 + i], gelu16(val[i] + a.p1[c0 + i]), zt);
+        }
+        int q, p;
+        if (N < 128) {
+          q = own_q;
+          p = p0 + u * g.PT + own_pl;
+        } else {
+          p = p0 + u % PC;
+          q = (u / PC) * 128 + own_q;
+        }
+        const size_t zi = ((size_t)b * N + q) * N + p;
+        a.z[zi] = (a.kinv ? zscale * a.kinv[zi] : zscale) * (double)zt;
+      }
+      fence_before_sync();
+      return okd;
+    };
     for (int t = 0; t < ntiles; ++t) {
       if (ok) {
         ok = mbar_wait(&accfull[t % kSynAcc], (t / kSynAcc) & 1);
@@ -1316,47 +1352,11 @@ __global__ void __launch_bounds__(kSynThreads, 2) tc_synthesis_kernel(SynArgs a)
         __syncwarp();
         if (lane == 0) mbar_arrive(&outready[t % DO]);
       }
-      if (!a.project) {
-        if (!ok) break;
-      } else {
-        // decoder: the MMA warp multiplies the output slot by the decoder weights into tE
-        if (ok) {
-          ok = mbar_wait(&decdone, t & 1);
-          fence_after_sync();
-        }
-        float zt = 0.f;
-        if (ok) {
-          float val[CH];
-          if constexpr (CH == 16) {
-            tmem_ld16(tE + cbase + lane_off, val);
-          } else {
-            tmem_ld8(tE + cbase + lane_off, val);
-          }
-#pragma unroll
-          for (int i = 0; i < CH; ++i) zt = fmaf(a.p2[cbase + i], gelu16(val[i] + a.p1[cbase + i]), zt);
-        }
-        zpart[half][m] = zt;
-        // epilogue-only barrier (named barrier 1); every epilogue thread reaches it once per
-        // tile, and the AND keeps the decision to stop uniform. It also orders every thread's
-        // read of tE before the next tile's outready arrival, which releases the next decoder MMA.
-        fence_before_sync();
-        ok = named_barrier_and(1, kSynEpi, ok);
-        if (!ok) break;
-        if (half == 0) {
-          int q, p;
-          if (N < 128) {
-            q = own_q;
-            p = p0 + t * g.PT + own_pl;
-          } else {
-            p = p0 + t % PC;
-            q = (t / PC) * 128 + own_q;
-          }
-          const size_t zi = ((size_t)b * N + q) * N + p;
-          const double sc = a.kinv ? a.rms[b] * a.hh * a.kinv[zi] : a.rms[b] * a.hh;
-          a.z[zi] = sc * (double)(a.p2b[0] + zpart[0][m] + zpart[1][m]);
-        }
-      }
+      // last layer: the previous tile's decoder output, whose MMA ran while this tile was finished
+      if (a.project && t > 0) ok = decoder_part(t - 1, ok);
+      if (!ok) break;
     }
+    if (a.project && ok) decoder_part(ntiles - 1, ok);
   }
   fence_before_sync();
   __syncthreads();
