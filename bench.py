@@ -144,14 +144,15 @@ def oracle_sample(blob: np.ndarray, n_inst: int, iters: int, cores: int, m_max: 
 
 
 # --------------------------------------------------------------------------------------- helpers
-def roofline_synthesis(active_per_iter, N, C, M, layers):
+def roofline_synthesis(active_per_iter, N, C, M, layers, output_scale=0):
     """Algorithmic HBM bytes of all synthesis launches: per active instance and layer, read
     the layer input (n*C*2 B) and the mixed coefficients (M*C*4M*2 B); hidden layers write
-    the next activation (n*C*2 B), the last layer writes z (n*8 B)."""
+    the next activation (n*C*2 B), the last layer writes z (n*8 B) and, with output_scale 1,
+    reads the pointwise 1/k (n*8 B)."""
     n = N * N
     chat = M * C * 4 * M * 2
     hidden = 2 * n * C * 2 + chat
-    last = n * C * 2 + chat + n * 8
+    last = n * C * 2 + chat + n * 8 + (n * 8 if output_scale else 0)
     per_inst = (layers - 1) * hidden + last
     return float(sum(active_per_iter)) * per_inst, int(len(active_per_iter)) * layers
 
@@ -248,9 +249,9 @@ def measure_fp64_roof(dev, stream, repeats=5):
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one tc_synthesis_kernel launch
 # per active instance, mean of the four layers of an iteration, measured by ncu on this
-# kernel at 64 x 64, 256 instances, width 32, 12 x 12 modes. Scaled by the active instances
-# per launch; None when the kernel has changed since the last capture.
-SYN_TRAFFIC_PER_INSTANCE = 351_168
+# kernel at 64 x 64, 256 instances, width 32, 12 x 12 modes, output_scale 1. Scaled by the
+# active instances per launch; None when the kernel has changed since the last capture.
+SYN_TRAFFIC_PER_INSTANCE = 364_695
 
 
 SERVE_SIZES = {64: 0.40, 128: 0.25, 256: 0.20, 512: 0.10, 1024: 0.05}
@@ -607,7 +608,7 @@ def main():
     ap.add_argument("--m", type=int, default=5, help="truncation m of Algorithm 1 for the headline (5; m = 1 is "
                                                      "measured alongside)")
     ap.add_argument("--m-alt", type=int, default=1, help="second truncation reported next to the headline (0 = none)")
-    ap.add_argument("--train-steps", type=int, default=16000)
+    ap.add_argument("--train-steps", type=int, default=48000)
     ap.add_argument("--train-prec", default="bf16", choices=["bf16", "fp32"],
                     help="arithmetic of the models' training steps (BF16 tensor cores or FP32 CUDA cores)")
     ap.add_argument("--train-leg", type=int, default=1, help="run the training-throughput leg (BF16 vs FP32)")
@@ -641,7 +642,7 @@ def main():
     ap.add_argument("--serve-rate", type=float, default=2000.0, help="mean arrival rate of the serving stream (1/s)")
     ap.add_argument("--serve-m", type=int, default=1, help="truncation m of the served solves")
     ap.add_argument("--serve-requests-light", type=int, default=500, help="requests of the lighter stream")
-    ap.add_argument("--mix-train-steps", type=int, default=6000)
+    ap.add_argument("--mix-train-steps", type=int, default=16000)
     ap.add_argument("--mix-train-instances", type=int, default=768)
     ap.add_argument("--serve-rate-light", type=float, default=50.0,
                     help="arrival rate of a second, lighter serving stream (0 = skip)")
@@ -755,7 +756,7 @@ def main():
     # ---- roofline of the dominant kernel (synthesis): algorithmic bytes / traced device time
     max_it = max(iters)
     active = [sum(1 for it in iters if it > i) for i in range(max_it)]
-    alg_bytes_one, syn_per_step = roofline_synthesis(active, N_GRID, WIDTH, MODES, LAYERS)
+    alg_bytes_one, syn_per_step = roofline_synthesis(active, N_GRID, WIDTH, MODES, LAYERS, args.output_scale)
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peak, peak_src = 6800.0, "fallback"
     bf16_peak, bf16_src = 1700.0, "fallback (sustained)"

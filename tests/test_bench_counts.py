@@ -45,6 +45,9 @@ def test_synthesis_bytes(bench):
     total, launches = bench.roofline_synthesis([256, 200, 3], N, C, M, L)
     assert launches == 3 * L
     assert total == (256 + 200 + 3) * ((L - 1) * hidden + last)
+    # output_scale 1: the last layer also reads the pointwise 1/k in FP64
+    total1, _ = bench.roofline_synthesis([256, 200, 3], N, C, M, L, output_scale=1)
+    assert total1 == total + (256 + 200 + 3) * n * 8
 
 
 def test_fcg_step_bytes(bench):
