@@ -454,6 +454,42 @@ def check_train_step(lib, dev, prec, tol, kind, out_scale=0):
 BF16_TRAIN_TOL = {"energy": (1e-2, 2e-2, 5e-2, 5e-2), "l2": (1e-2, 3e-2, 8e-2, 1e-1)}
 
 
+@pytest.fixture(scope="module")
+def trained_pair(lib, dev):
+    """A preconditioner trained briefly (600 BF16 steps on Krylov vectors of 64 x 64 problems,
+    sigma in {0.5, 1, 2}): weights no longer Xavier, GELUs away from their linear range. Returns
+    (desc, oracle weights, model, blob); the oracle weights are the trained blob's."""
+    from paper_2402_05598_gb300 import train as T
+    desc, _P, model, wdev = model_pair(lib, dev, 32, 12, seed=11, out_scale=1)
+    T.train(model, 64, range(0, 96), K=40, batch=32, lr=1e-3, steps=600, prec="bf16", sigma=(0.5, 1.0, 2.0))
+    return desc, O.unpack_weights(wdev.double().cpu().numpy(), desc), model, wdev
+
+
+@pytest.mark.parametrize("prec,tol", [("bf16", 2e-2), ("fp16", 4e-3), ("fp64", 1e-12)])
+@pytest.mark.parametrize("sigma", [0.5, 2.0])
+def test_trained_preconditioner_matches_oracle(lib, dev, trained_pair, prec, tol, sigma):
+    """The preconditioner with trained weights on held-out fields of low and high contrast,
+    against the oracle with the same weights: relative 2-norm error of the network output
+    (z k, output_scale 1) within 2e-2 (BF16), 4e-3 (FP16), 1e-12 (FP64), and element by element
+    (every grid edge included) within ELEM_TOL of max|z k|. The residuals are those a solve
+    sees: r = f - A u for a random u."""
+    import torch
+    desc, P, model, _w = trained_pair
+    N, B = 64, 3
+    k, f = batch(N, B, 4400 + int(10 * sigma), sigma)
+    u = np.random.default_rng(5).standard_normal((B, N, N))
+    r = np.stack([f[b] - O.apply_A(k[b], u[b]) for b in range(B)])
+    op = lib.Operator(to_dev(k, dev))
+    z = torch.empty((B, N, N), dtype=torch.float64, device=dev)
+    lib.precond_apply(model, op, to_dev(r, dev), z, prec=prec)
+    zs = z.cpu().numpy()
+    for b in range(B):
+        ref = O.no_forward(P, desc, r[b], np.log(k[b])) * k[b]
+        zk = zs[b] * k[b]
+        assert rel(zk, ref) < tol, (b, rel(zk, ref))
+        elem_check(zk, ref, ELEM_TOL[prec], ("trained " + prec, sigma, b))
+
+
 @pytest.mark.parametrize("N,B,C,M,seed,out_scale,kind", [
     (32, 3, 16, 8, 2, 0, "energy"),
     (32, 3, 16, 8, 2, 1, "energy"),
