@@ -119,13 +119,16 @@ def _problems(dataset, N, seeds, sigma, ell):
 def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, lr: float = 1e-3,
           steps: int = 1000, seconds: float | None = None, prec: str = "fp32", seed: int = 0,
           sigma=1.0, ell: float = 0.1, log_every: int = 0, decay_at=(0.5, 0.75),
-          dataset: str = "grf", data: str = "krylov", loss_kind: str = "energy") -> TrainResult:
+          dataset: str = "grf", data: str = "krylov", loss_kind: str = "energy",
+          weight_decay: float = 0.0) -> TrainResult:
     """Trains ``model.weights`` in place; returns the loss history. The learning rate is
     halved at the given fractions of ``steps`` (the paper halves it on a fixed schedule,
     Table 6). ``data``: "krylov" (Eq. (9)) or "random" (Section 3.5); ``loss_kind``: "energy"
     (Eq. (11)) or "l2". ``sigma`` is the GRF standard deviation of the coefficient fields, or
     a sequence of them: group g of ``batch`` instances then uses sigma[g % len(sigma)], so
-    that the training distribution covers every coefficient contrast it will be served."""
+    that the training distribution covers every coefficient contrast it will be served.
+    ``weight_decay`` > 0 applies decoupled weight decay (AdamW) of that rate (Table 6 lists
+    1e-2)."""
     import torch
     dev = model.weights.device
     t0 = time.perf_counter()
@@ -140,7 +143,8 @@ def train(model: "F.Model", N: int, train_seeds, K: int = 100, batch: int = 32, 
     t_h = time.perf_counter() - t0
     param = model.weights
     param.requires_grad_(True)
-    opt = torch.optim.Adam([param], lr=lr)
+    opt = (torch.optim.AdamW([param], lr=lr, weight_decay=weight_decay) if weight_decay > 0
+           else torch.optim.Adam([param], lr=lr))
     gen = torch.Generator(device=dev)
     gen.manual_seed(seed)
     ar = torch.arange(batch, device=dev)
