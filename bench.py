@@ -464,7 +464,7 @@ def run_large(args, dev, flush, stream):
     r_out = torch.empty((K, Bf, Nf, Nf), dtype=torch.float64, device=dev)
     e_out = torch.empty_like(r_out)
     F.krylov_harvest(opf, ff, x0, ustar, K, r_out, e_out)
-    model.set_train_recompute("auto")
+    model.set_train_recompute("always")
     opt = torch.optim.Adam([blob.requires_grad_(True)], lr=args.large_finetune_lr)
     losses = []
     torch.cuda.synchronize()
@@ -472,17 +472,19 @@ def run_large(args, dev, flush, stream):
     for it in range(args.large_finetune_steps):
         i = it % K
         opt.zero_grad(set_to_none=True)
-        loss = T.preconditioner_loss(model, opf, r_out[i].contiguous(), e_out[i].contiguous(), prec="fp32")
+        loss = T.preconditioner_loss(model, opf, r_out[i].contiguous(), e_out[i].contiguous(), prec=args.train_prec)
         loss.backward()
         opt.step()
-        losses.append(round(float(loss.item()), 4))
+        if it % max(1, args.large_finetune_steps // 10) == 0 or it == args.large_finetune_steps - 1:
+            losses.append((it, round(float(loss.item()), 4)))
     blob.requires_grad_(False)
     blob.grad = None
     model.sync()
     torch.cuda.synchronize()
     out["finetune"] = {"grid": Nf, "instances": Bf, "krylov_K": K, "steps": args.large_finetune_steps,
+                       "prec": args.train_prec, "lr": args.large_finetune_lr,
                        "seconds": round(time.perf_counter() - t0, 2), "losses": losses,
-                       "recompute": "auto (pre-activations rebuilt in the backward above 2 GiB)"}
+                       "recompute": "always (every layer's pre-activation rebuilt in the backward)"}
     del opf, r_out, e_out, ustar
     for N, B in LARGE_CASES:
         seeds = range(42000 + N, 42000 + N + B)
@@ -626,8 +628,8 @@ def main():
     ap.add_argument("--large", type=int, default=1, help="run the large-solve leg (1024^2 x 8, 2048^2 x 2, tol 1e-8)")
     ap.add_argument("--large-max-iter", type=int, default=3000)
     ap.add_argument("--large-train-steps", type=int, default=4000)
-    ap.add_argument("--large-finetune-steps", type=int, default=4)
-    ap.add_argument("--large-finetune-k", type=int, default=4)
+    ap.add_argument("--large-finetune-steps", type=int, default=600)
+    ap.add_argument("--large-finetune-k", type=int, default=16)
     ap.add_argument("--large-finetune-lr", type=float, default=2e-4)
     ap.add_argument("--output-scale", type=int, default=1, choices=[0, 1],
                     help="model output scale: 0 = h^2 rms(r), 1 = h^2 rms(r) / k")

@@ -240,10 +240,11 @@ fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* 
  * for the backward; the layers' pre-activations (batch*N*N*width values each) are kept as well
  * (mode 2, "never recompute"), or rebuilt one layer at a time during the backward from the
  * kept input (mode 1, "always": about half the activation memory, one more mixing and
- * synthesis pass per layer, bit-identical gradients). Mode 0 (default) recomputes when the
- * kept pre-activations would exceed 2 GiB, e.g. fine-tuning on 1024 x 1024 or 2048 x 2048
- * grids. Takes effect at the next training step. Errors: EINVAL for a NULL model or another
- * mode. */
+ * synthesis pass per layer, bit-identical gradients; FCGNO_BF16 also repeats the layer's
+ * analysis). Mode 0 (default) recomputes when the kept pre-activations would exceed 2 GiB
+ * (FP32/FP64: e.g. fine-tuning on 1024 x 1024 or 2048 x 2048 grids; FCGNO_BF16 keeps them in
+ * 16 bits, half the bytes). Takes effect at the next training step. Errors: EINVAL for a NULL
+ * model or another mode. */
 fcgno_status fcgno_model_set_train_recompute(fcgno_model_t model, int mode);
 
 /* Training losses. FCGNO_LOSS_ENERGY is Eq. (11) in error form (the A-norm); FCGNO_LOSS_L2

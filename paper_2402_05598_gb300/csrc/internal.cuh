@@ -309,8 +309,12 @@ fcgno_status tc_train_to_f32(const fcgno_model* m, const fcgno_op* op, int which
 fcgno_status tc_train_act_bwd(const fcgno_model* m, const fcgno_op* op, int l, const float* gv32, float* gh32,
                               cudaStream_t st);
 fcgno_status tc_train_layer_bwd(fcgno_model* m, const fcgno_op* op, int l, cudaStream_t st);
+// recompute: with activation checkpointing (fcgno_model_set_train_recompute), rebuilds layer l's
+// pre-activation from its kept input before act_bwd reads it (no-op otherwise).
+fcgno_status tc_train_recompute_layer(fcgno_model* m, const fcgno_op* op, int l, cudaStream_t st);
+bool tc_train_recompute(const fcgno_model* m, const fcgno_op* op);
 const float* tc_train_gspec(const fcgno_op* op);
-size_t tc_train_bytes(int N, int B, const fcgno_model_desc& d);
+size_t tc_train_bytes(int N, int B, const fcgno_model_desc& d, bool recompute);
 
 inline unsigned ceil_div(size_t a, size_t b) { return (unsigned)((a + b - 1) / b); }
 

@@ -49,6 +49,7 @@ struct TrainBuffers {
   std::vector<void*> vin;             // L+1 activations [pts][C] (inputs of each layer, vin[L] = last output)
   std::vector<void*> hpre;            // L pre-activations [pts][C] (one scratch buffer when recomputing)
   bool recompute = false;             // pre-activations rebuilt in the backward instead of kept
+  bool no_hpre = false;               // BF16 step: its pre-activations are kept in 16 bits elsewhere
   std::vector<void*> chat;            // L analysis outputs [B][Kx][Ky][C] complex
   void* apre = nullptr;               // [pts][Cp] decoder pre-activation
   void* ghid = nullptr;               // [pts][Cp] GELU(apre)
@@ -712,7 +713,7 @@ __global__ void add_kernel(size_t total, const void* a, void* out, int fp64) {
 }
 
 // ------------------------------------ host: training -----------------------------------
-static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz) {
+static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz, bool no_hpre = false) {
   TrainBuffers& t = m->ws->tr;
   const fcgno_model_desc& d = m->desc;
   const size_t pts = (size_t)op->B * op->n;
@@ -725,7 +726,7 @@ static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz)
   const bool recompute = m->train_recompute == 1 ||
                          (m->train_recompute == 0 && pts * d.width * esz * (size_t)d.layers > kKeepBudget);
   if (t.cap_pts == pts * esz && t.L == d.layers && t.C == d.width && t.Cp == d.proj_width && t.Kx == Kx &&
-      t.B == op->B && t.recompute == recompute)
+      t.B == op->B && t.recompute == recompute && t.no_hpre == no_hpre)
     return FCGNO_OK;
   // release and reallocate
   cfree(t.x0);
@@ -736,7 +737,7 @@ static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz)
                    (void**)&t.dvec, (void**)&t.zbuf, (void**)&t.rms, (void**)&t.lossb};
   for (void** p : more) cfree(*p);
   t.vin.assign(d.layers + 1, nullptr);
-  t.hpre.assign(recompute ? 1 : d.layers, nullptr);
+  t.hpre.assign(no_hpre ? 0 : (recompute ? 1 : d.layers), nullptr);
   t.chat.assign(d.layers, nullptr);
   bool ok = true;
   auto al = [&](void** p, size_t bytes) {
@@ -767,6 +768,7 @@ static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz)
   }
   t.cap_pts = pts * esz;
   t.recompute = recompute;
+  t.no_hpre = no_hpre;
   t.L = d.layers;
   t.C = d.width;
   t.Cp = d.proj_width;
@@ -909,7 +911,7 @@ static fcgno_status train_impl_tc(fcgno_model* m, fcgno_op* op, const double* r,
   const int B = op->B, C = d.width, M = d.modes, L = d.layers;
   const size_t n = op->n, pts = (size_t)B * n;
   const int nmodes = 2 * M * M;
-  FCGNO_TRY(ensure_train(m, op, sizeof(float)));
+  FCGNO_TRY(ensure_train(m, op, sizeof(float), true));
   TrainBuffers& t = m->ws->tr;
   Wp<float> W = wptrs<float>(m, m->w32);
   BlobLayout BL = blob_layout(d);
@@ -933,6 +935,7 @@ static fcgno_status train_impl_tc(fcgno_model* m, fcgno_op* op, const double* r,
   FCGNO_TRY(loss_and_decoder_bwd<float>(m, op, e, loss, grad, l2, (const float*)t.vin[L], W, st));
   float* gh = (float*)t.g1;
   for (int l = L - 1; l >= 0; --l) {
+    FCGNO_TRY(tc_train_recompute_layer(m, op, l, st));
     FCGNO_TRY(tc_train_act_bwd(m, op, l, l == L - 1 ? (const float*)t.g0 : nullptr, gh, st));
     FCGNO_TRY(outer_reduce<float>(pts, C, C, gh, (const float*)t.vin[l], (float*)t.partials, grad + BL.w[l],
                                   grad + BL.b[l], st));

@@ -281,6 +281,7 @@ struct TcTrainBufs {
   uint16_t* partb = nullptr;  // partial-coefficient images of the backward's analysis
   float* gspec = nullptr;     // [B][mode][C] complex: that analysis summed over column chunks
   float* zero = nullptr;      // [C] zeros: the bias of the adjoint synthesis
+  bool recompute = false;     // pre-activations rebuilt per layer in the backward (h[0] is scratch)
 };
 }  // namespace fcgno
 
@@ -1712,7 +1713,7 @@ __global__ void tc_part_to_cx_kernel(TcGeom g, int B, int nbt, const uint16_t* _
 }
 
 // Bytes of one operator's BF16 training state (TcTrainBufs) for `layers` layers.
-static size_t train_bufs_layout(const TcGeom& g, int B, int layers, size_t* offs) {
+static size_t train_bufs_layout(const TcGeom& g, int B, int layers, bool recompute, size_t* offs) {
   const size_t img = (size_t)B * g.N * g.N * g.C * 2;
   size_t v, part, chat;
   tc_acts_elems(g, B, v, part, chat);
@@ -1724,7 +1725,8 @@ static size_t train_bufs_layout(const TcGeom& g, int B, int layers, size_t* offs
   };
   int k = 0;
   for (int l = 0; l <= layers; ++l) offs[k++] = take(img);           // v
-  for (int l = 0; l + 1 < layers; ++l) offs[k++] = take(img);        // h
+  const int nh = recompute ? (layers > 1 ? 1 : 0) : layers - 1;
+  for (int l = 0; l < nh; ++l) offs[k++] = take(img);                // h
   offs[k++] = take(img);                                             // gh
   offs[k++] = take(img);                                             // gv
   offs[k++] = take(part * 2);                                        // partb
@@ -1733,11 +1735,12 @@ static size_t train_bufs_layout(const TcGeom& g, int B, int layers, size_t* offs
   return o;
 }
 
-static fcgno_status ensure_train_bufs(const fcgno_op* op, const TcGeom& g, int layers, cudaStream_t st) {
+static fcgno_status ensure_train_bufs(const fcgno_op* op, const TcGeom& g, int layers, bool recompute,
+                                      cudaStream_t st) {
   TcTrainBufs& tb = op->tc_acts->train;
   size_t offs[2 * 16 + 8];
-  const size_t bytes = train_bufs_layout(g, op->B, layers, offs);
-  if (tb.base && tb.bytes == bytes) return FCGNO_OK;
+  const size_t bytes = train_bufs_layout(g, op->B, layers, recompute, offs);
+  if (tb.base && tb.bytes == bytes && tb.recompute == recompute) return FCGNO_OK;
   if (tb.base) cudaFree(tb.base);
   tb = TcTrainBufs{};
   if (cudaMalloc(&tb.base, bytes) != cudaSuccess) {
@@ -1750,7 +1753,9 @@ static fcgno_status ensure_train_bufs(const fcgno_op* op, const TcGeom& g, int l
   uint8_t* b = (uint8_t*)tb.base;
   int k = 0;
   for (int l = 0; l <= layers; ++l) tb.v[l] = (uint16_t*)(b + offs[k++]);
-  for (int l = 0; l + 1 < layers; ++l) tb.h[l] = (uint16_t*)(b + offs[k++]);
+  const int nh = recompute ? (layers > 1 ? 1 : 0) : layers - 1;
+  for (int l = 0; l < nh; ++l) tb.h[l] = (uint16_t*)(b + offs[k++]);
+  tb.recompute = recompute;
   tb.gh = (uint16_t*)(b + offs[k++]);
   tb.gv = (uint16_t*)(b + offs[k++]);
   tb.partb = (uint16_t*)(b + offs[k++]);
@@ -1760,10 +1765,19 @@ static fcgno_status ensure_train_bufs(const fcgno_op* op, const TcGeom& g, int l
   return FCGNO_OK;
 }
 
-size_t tc_train_bytes(int N, int B, const fcgno_model_desc& d) {
+size_t tc_train_bytes(int N, int B, const fcgno_model_desc& d, bool recompute) {
   if (!tc_shape_supported(N, d)) return 0;
   size_t offs[2 * 16 + 8];
-  return train_bufs_layout(make_geom(N, d.width, d.modes), B, d.layers, offs);
+  return train_bufs_layout(make_geom(N, d.width, d.modes), B, d.layers, recompute, offs);
+}
+
+// Whether a BF16 training step on this operator rebuilds its pre-activations: mode 1 always,
+// 2 never, 0 when keeping the L - 1 pre-activation images would take more than 2 GiB.
+bool tc_train_recompute(const fcgno_model* m, const fcgno_op* op) {
+  if (m->train_recompute == 1) return true;
+  if (m->train_recompute == 2) return false;
+  const size_t img = (size_t)op->B * op->n * m->desc.width * 2;
+  return img * (size_t)(m->desc.layers - 1) > ((size_t)2 << 30);
 }
 
 // One synthesis launch of the hidden-layer kind (the epilogue stores the tile rows itself).
@@ -1859,7 +1873,7 @@ fcgno_status tc_train_begin(fcgno_model* m, const fcgno_op* op, cudaStream_t st)
   FCGNO_TRY(ensure_tables(m, false, g, tab, st));
   FCGNO_TRY(ensure_tables(m, false, g, tab, st, true));
   FCGNO_TRY(ensure_acts(m, op, g, st));
-  FCGNO_TRY(ensure_train_bufs(op, g, d.layers, st));
+  FCGNO_TRY(ensure_train_bufs(op, g, d.layers, tc_train_recompute(m, op), st));
   if (C == 16) return raise_smem_limits<16>(g);
   return raise_smem_limits<32>(g);
 }
@@ -1887,7 +1901,7 @@ static fcgno_status train_forward(fcgno_model* m, const fcgno_op* op, const doub
     FCGNO_TRY(launch_mixing<C>(g, op, T.part, P.Rr[l], T.chat, st));
     const bool act = l < d.layers - 1;
     FCGNO_TRY(launch_syn_hidden<C>(g, op, tb.v[l], tb.v[l + 1], T.chat, P.W[l], m->w32 + BL.b[l], tab, act,
-                                   act ? tb.h[l] : nullptr, st));
+                                   (act && !tb.recompute) ? tb.h[l] : nullptr, st));
   }
   return FCGNO_OK;
 }
@@ -1913,9 +1927,34 @@ fcgno_status tc_train_act_bwd(const fcgno_model* m, const fcgno_op* op, int l, c
   TcTrainBufs& tb = op->tc_acts->train;
   const size_t total = (size_t)op->B * op->n * (g.C / 8);
   tc_act_bwd_kernel<<<ceil_div(total, 256), 256, 0, st>>>(g, op->B, gv32, tb.gv,
-                                                          l < m->desc.layers - 1 ? tb.h[l] : nullptr, gh32, tb.gh);
+                                                          l < m->desc.layers - 1 ? tb.h[tb.recompute ? 0 : l] : nullptr,
+                                                          gh32, tb.gh);
   FCGNO_LAUNCHED();
   return FCGNO_OK;
+}
+
+// Activation checkpointing of the BF16 step: layer l's pre-activation rebuilt from its kept
+// input by the forward's own kernels on the same inputs (analysis, mixing, synthesis), so the
+// values are bit-identical; the synthesis rewrites v[l + 1] with the same bytes.
+template <int C>
+static fcgno_status train_recompute_layer(fcgno_model* m, const fcgno_op* op, int l, cudaStream_t st) {
+  const fcgno_model_desc& d = m->desc;
+  const TcGeom g = make_geom(op->N, C, d.modes);
+  TcPrecision& P = m->tc->prec[0];
+  TcTables* tab = nullptr;
+  FCGNO_TRY(ensure_tables(m, false, g, tab, st));
+  TcActs& T = *op->tc_acts;
+  TcTrainBufs& tb = T.train;
+  BlobLayout BL = blob_layout(d);
+  FCGNO_TRY(launch_ana<C>(g, op, tb.v[l], tab, T.part, st));
+  FCGNO_TRY(launch_mixing<C>(g, op, T.part, P.Rr[l], T.chat, st));
+  return launch_syn_hidden<C>(g, op, tb.v[l], tb.v[l + 1], T.chat, P.W[l], m->w32 + BL.b[l], tab, 1, tb.h[0], st);
+}
+
+fcgno_status tc_train_recompute_layer(fcgno_model* m, const fcgno_op* op, int l, cudaStream_t st) {
+  if (!op->tc_acts->train.recompute || l >= m->desc.layers - 1) return FCGNO_OK;
+  if (m->desc.width == 16) return train_recompute_layer<16>(m, op, l, st);
+  return train_recompute_layer<32>(m, op, l, st);
 }
 
 template <int C>

@@ -586,7 +586,8 @@ def test_autograd_loss_gives_the_library_gradient(lib, dev, kind):
     wdev.requires_grad_(False)
 
 
-@pytest.mark.parametrize("prec,kind", [("fp32", "energy"), ("fp64", "energy"), ("fp32", "l2")])
+@pytest.mark.parametrize("prec,kind", [("fp32", "energy"), ("fp64", "energy"), ("fp32", "l2"), ("bf16", "energy"),
+                                       ("bf16", "l2")])
 def test_training_with_recomputed_preactivations_is_bit_identical(lib, dev, prec, kind):
     """Activation checkpointing: a training step that rebuilds every layer's pre-activation
     in the backward returns exactly the loss and gradient of the step that keeps them."""
