@@ -262,6 +262,14 @@ fcgno_status fcgno_train_step_loss(fcgno_model_t model, fcgno_op_t op, const dou
                                    int batch, fcgno_prec prec, int loss_kind, float* loss, float* grad,
                                    void* stream);
 
+/* fcgno_train_step_loss in FP64 with the loss and the gradient stored in FP64 (double* loss:
+ * device scalar; double* grad: device array laid out like the weight blob), for gradient checks
+ * below FP32 resolution. Forward and backward run on CUDA cores in FP64 from the model's FP64
+ * copy of the weights (made by fcgno_model_create / fcgno_model_sync). Arguments, loss kinds
+ * and errors as fcgno_train_step_loss (no precision argument). */
+fcgno_status fcgno_train_step_f64(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
+                                  int batch, int loss_kind, double* loss, double* grad, void* stream);
+
 /* Serving buckets (continuous batching of independent solves of one grid size). A bucket
  * keeps `capacity` solves resident (operator, iterate, right-hand side and Krylov state of
  * Algorithm 1) and advances all running slots together, `iters_per_step` iterations per

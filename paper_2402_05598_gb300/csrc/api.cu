@@ -294,6 +294,23 @@ extern "C" fcgno_status fcgno_train_step_loss(fcgno_model_t model, fcgno_op_t op
                          (cudaStream_t)stream);
 }
 
+extern "C" fcgno_status fcgno_train_step_f64(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
+                                             int batch, int loss_kind, double* loss, double* grad, void* stream) {
+  if (!model || !op || !r || !e || !loss || !grad || batch != op->B) {
+    set_last_error("fcgno_train_step_f64: null argument or batch != op batch");
+    return FCGNO_EINVAL;
+  }
+  if (loss_kind != FCGNO_LOSS_ENERGY && loss_kind != FCGNO_LOSS_L2) {
+    set_last_error("fcgno_train_step_f64: loss_kind must be FCGNO_LOSS_ENERGY or FCGNO_LOSS_L2");
+    return FCGNO_EINVAL;
+  }
+  if (op->N < 2 * model->desc.modes) {
+    set_last_error("fcgno_train_step_f64: grid smaller than 2*modes");
+    return FCGNO_EINVAL;
+  }
+  return train_step_f64(model, op, r, e, loss, grad, loss_kind == FCGNO_LOSS_L2, (cudaStream_t)stream);
+}
+
 extern "C" fcgno_status fcgno_train_step(fcgno_model_t model, fcgno_op_t op, const double* r, const double* e,
                                          int batch, fcgno_prec prec, float* loss, float* grad, void* stream) {
   return fcgno_train_step_loss(model, op, r, e, batch, prec, FCGNO_LOSS_ENERGY, loss, grad, stream);

@@ -292,6 +292,9 @@ fcgno_status launch_rms(const double* r, int B, size_t n, double* rms, cudaStrea
 // on the tensor cores, the rest on CUDA cores in FP32).
 fcgno_status train_step_simt(fcgno_model* m, fcgno_op* op, const double* r, const double* e,
                              float* loss, float* grad, fcgno_prec prec, bool l2, cudaStream_t st);
+// The FP64 step with its loss and gradient stored in FP64 (fcgno_train_step_f64).
+fcgno_status train_step_f64(fcgno_model* m, fcgno_op* op, const double* r, const double* e,
+                            double* loss, double* grad, bool l2, cudaStream_t st);
 
 // Pieces of the BF16 training step (tensor-core path; wide launch shape, every instance active).
 // begin: weight images (forward and transposed) from the current master blob, forward and

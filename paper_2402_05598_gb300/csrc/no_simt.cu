@@ -589,9 +589,10 @@ __global__ void outer_reduce_kernel(size_t npts, int Co, int Ci, const T* __rest
 }
 
 // grad_w[o*Ci+i] = sum_g partial[g][o][i]; grad_b[o] = sum_g partial[g][o][Ci] (grad_b may be null).
-template <typename T>
-__global__ void reduce_partials_kernel(int G, int Co, int Ci, const T* __restrict__ partial, float* __restrict__ gw,
-                                       float* __restrict__ gb) {
+// Gr: the gradient's storage type (float, or double for the FP64-output step).
+template <typename T, typename Gr>
+__global__ void reduce_partials_kernel(int G, int Co, int Ci, const T* __restrict__ partial, Gr* __restrict__ gw,
+                                       Gr* __restrict__ gb) {
   const int idx = blockIdx.x * blockDim.x + threadIdx.x;
   const int nout = Co * (Ci + 1);
   if (idx >= nout) return;
@@ -599,9 +600,9 @@ __global__ void reduce_partials_kernel(int G, int Co, int Ci, const T* __restric
   for (int g = 0; g < G; ++g) s += partial[(size_t)g * nout + idx];
   const int o = idx / (Ci + 1), i = idx % (Ci + 1);
   if (i < Ci)
-    gw[o * Ci + i] = (float)s;
+    gw[o * Ci + i] = (Gr)s;
   else if (gb)
-    gb[o] = (float)s;
+    gb[o] = (Gr)s;
 }
 
 // Loss pieces: per instance sqrt(d, Ad) and sqrt(e, Ae) with d = z - e; Ad = A d and Ae = A e
@@ -629,12 +630,13 @@ __global__ void diff_kernel(size_t total, const double* __restrict__ z, const do
   if (i < total) d[i] = z[i] - e[i];
 }
 
-// loss = mean_b ||d_b|| / ||e_b||  (written as float to *loss)
-__global__ void loss_value_kernel(int B, const double* __restrict__ norms, float* __restrict__ loss) {
+// loss = mean_b ||d_b|| / ||e_b||  (written to *loss as float, or double)
+template <typename Gr>
+__global__ void loss_value_kernel(int B, const double* __restrict__ norms, Gr* __restrict__ loss) {
   if (threadIdx.x != 0) return;
   double s = 0.0;
   for (int b = 0; b < B; ++b) s += norms[2 * b] / norms[2 * b + 1];
-  *loss = (float)(s / B);
+  *loss = (Gr)(s / B);
 }
 
 // dL/dzt[b][x] = s_b(x) * (1/B) * (A d)_x / (||d|| ||e||) with s = h^2 rms_b (times 1/k[b][x]
@@ -685,9 +687,9 @@ __global__ void act_bwd_kernel(size_t total, const T* __restrict__ gv, const T* 
 }
 
 // dR[mode][i][o] = sum_b conj(c[b][mode][i]) g[b][mode][o]   (block per mode, thread per (i,o))
-template <typename T>
+template <typename T, typename Gr>
 __global__ void spectral_wgrad_kernel(int B, int C, int nmodes, const Cx<T>* __restrict__ c, const Cx<T>* __restrict__ g,
-                                      float* __restrict__ dR) {
+                                      Gr* __restrict__ dR) {
   const int mode = blockIdx.x;
   for (int t = threadIdx.x; t < C * C; t += blockDim.x) {
     const int i = t / C, o = t % C;
@@ -698,8 +700,8 @@ __global__ void spectral_wgrad_kernel(int B, int C, int nmodes, const Cx<T>* __r
       re += a.re * w.re + a.im * w.im;
       im += a.re * w.im - a.im * w.re;
     }
-    dR[((size_t)mode * C * C + t) * 2] = (float)re;
-    dR[((size_t)mode * C * C + t) * 2 + 1] = (float)im;
+    dR[((size_t)mode * C * C + t) * 2] = (Gr)re;
+    dR[((size_t)mode * C * C + t) * 2 + 1] = (Gr)im;
   }
 }
 
@@ -778,9 +780,9 @@ static fcgno_status ensure_train(fcgno_model* m, const fcgno_op* op, size_t esz,
   return FCGNO_OK;
 }
 
-template <typename T>
-static fcgno_status outer_reduce(size_t npts, int Co, int Ci, const T* A, const T* V, T* partials, float* gw,
-                                 float* gb, cudaStream_t st) {
+template <typename T, typename Gr>
+static fcgno_status outer_reduce(size_t npts, int Co, int Ci, const T* A, const T* V, T* partials, Gr* gw,
+                                 Gr* gb, cudaStream_t st) {
   const int G = 512;
   const int threads = 256;
   if (Co * (Ci + 1) > threads * 8) {
@@ -790,7 +792,7 @@ static fcgno_status outer_reduce(size_t npts, int Co, int Ci, const T* A, const 
   const size_t smem = (size_t)32 * (Co + Ci) * sizeof(T);
   outer_reduce_kernel<T><<<G, threads, smem, st>>>(npts, Co, Ci, A, V, partials);
   FCGNO_LAUNCHED();
-  reduce_partials_kernel<T><<<ceil_div((size_t)Co * (Ci + 1), 256), 256, 0, st>>>(G, Co, Ci, partials, gw, gb);
+  reduce_partials_kernel<T, Gr><<<ceil_div((size_t)Co * (Ci + 1), 256), 256, 0, st>>>(G, Co, Ci, partials, gw, gb);
   FCGNO_LAUNCHED();
   return FCGNO_OK;
 }
@@ -798,8 +800,8 @@ static fcgno_status outer_reduce(size_t npts, int Co, int Ci, const T* A, const 
 // Loss (FP64) of the forward output in t.zbuf and the decoder's backward: the decoder's
 // weight gradients, and the gradient of the last Fourier layer's output (FP32 or FP64,
 // [B][N][N][C]) left in t.g0. `grad` is zeroed first. vL: the last layer's output.
-template <typename T>
-static fcgno_status loss_and_decoder_bwd(fcgno_model* m, fcgno_op* op, const double* e, float* loss, float* grad,
+template <typename T, typename Gr>
+static fcgno_status loss_and_decoder_bwd(fcgno_model* m, fcgno_op* op, const double* e, Gr* loss, Gr* grad,
                                          bool l2, const T* vL, const Wp<T>& W, cudaStream_t st) {
   const fcgno_model_desc& d = m->desc;
   const int N = op->N, B = op->B, C = d.width, Cp = d.proj_width;
@@ -821,9 +823,9 @@ static fcgno_status loss_and_decoder_bwd(fcgno_model* m, fcgno_op* op, const dou
   }
   loss_dots_kernel<<<B, 256, 0, st>>>(n, dv, Ad, e, Ae, t.lossb);
   FCGNO_LAUNCHED();
-  loss_value_kernel<<<1, 32, 0, st>>>(B, t.lossb, loss);
+  loss_value_kernel<Gr><<<1, 32, 0, st>>>(B, t.lossb, loss);
   FCGNO_LAUNCHED();
-  FCGNO_CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(float) * BL.total, st));
+  FCGNO_CUDA_TRY(cudaMemsetAsync(grad, 0, sizeof(Gr) * BL.total, st));
   T* gzt = (T*)t.gz;
   dzt_kernel<T><<<ceil_div(pts, 256), 256, 0, st>>>(B, n, 1.0 / ((double)(N + 1) * (N + 1)), Ad, t.lossb, t.rms,
                                                     d.output_scale ? op->kinv : nullptr, gzt);
@@ -840,9 +842,9 @@ static fcgno_status loss_and_decoder_bwd(fcgno_model* m, fcgno_op* op, const dou
   return FCGNO_OK;
 }
 
-template <typename T>
-static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, const double* e, float* loss,
-                               float* grad, bool l2, cudaStream_t st) {
+template <typename T, typename Gr>
+static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, const double* e, Gr* loss,
+                               Gr* grad, bool l2, cudaStream_t st) {
   const fcgno_model_desc& d = m->desc;
   const int N = op->N, B = op->B, C = d.width, M = d.modes, L = d.layers;
   const size_t n = op->n, pts = (size_t)B * n;
@@ -857,7 +859,7 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
   // forward with saves
   FCGNO_TRY(launch_rms(r, B, n, t.rms, st));
   FCGNO_TRY(forward_simt<T>(m, op, wbase, r, t.rms, nullptr, t.zbuf, s, &t, nullptr, st));
-  FCGNO_TRY(loss_and_decoder_bwd<T>(m, op, e, loss, grad, l2, (const T*)t.vin[L], W, st));
+  FCGNO_TRY((loss_and_decoder_bwd<T, Gr>(m, op, e, loss, grad, l2, (const T*)t.vin[L], W, st)));
   // backward
   const T *tw1, *tw2;
   tw_ptrs<T>(m->ws->tw, tw1, tw2);
@@ -885,7 +887,7 @@ static fcgno_status train_impl(fcgno_model* m, fcgno_op* op, const double* r, co
     // spectral: g' = w(k2) * sum_x gh e^{-i theta}  (analysis without 1/n, weights 1 / 2)
     Cx<T>* gspec = (Cx<T>*)s.spec2;
     FCGNO_TRY(launch_analysis<T>(N, B, C, M, nullptr, gh, (Cx<T>*)s.mid, gspec, (T)1, (T)2, tw1, tw2, st));
-    spectral_wgrad_kernel<T><<<nmodes, 256, 0, st>>>(B, C, nmodes, (const Cx<T>*)t.chat[l], gspec, grad + BL.r[l]);
+    spectral_wgrad_kernel<T, Gr><<<nmodes, 256, 0, st>>>(B, C, nmodes, (const Cx<T>*)t.chat[l], gspec, grad + BL.r[l]);
     FCGNO_LAUNCHED();
     // gc = R^H g'
     mix_kernel<T><<<nmodes, 256, C * C * sizeof(Cx<T>), st>>>(B, C, nmodes, nullptr, gspec, W.r[l], (Cx<T>*)s.spec, 1);
@@ -932,7 +934,7 @@ static fcgno_status train_impl_tc(fcgno_model* m, fcgno_op* op, const double* r,
       1.0 / ((double)(op->N + 1) * (op->N + 1)), d.output_scale ? op->kinv : nullptr, t.zbuf, (float*)t.apre,
       (float*)t.ghid, nullptr);
   FCGNO_LAUNCHED();
-  FCGNO_TRY(loss_and_decoder_bwd<float>(m, op, e, loss, grad, l2, (const float*)t.vin[L], W, st));
+  FCGNO_TRY((loss_and_decoder_bwd<float, float>(m, op, e, loss, grad, l2, (const float*)t.vin[L], W, st)));
   float* gh = (float*)t.g1;
   for (int l = L - 1; l >= 0; --l) {
     FCGNO_TRY(tc_train_recompute_layer(m, op, l, st));
@@ -940,7 +942,7 @@ static fcgno_status train_impl_tc(fcgno_model* m, fcgno_op* op, const double* r,
     FCGNO_TRY(outer_reduce<float>(pts, C, C, gh, (const float*)t.vin[l], (float*)t.partials, grad + BL.w[l],
                                   grad + BL.b[l], st));
     FCGNO_TRY(tc_train_layer_bwd(m, op, l, st));
-    spectral_wgrad_kernel<float><<<nmodes, 256, 0, st>>>(B, C, nmodes, (const Cx<float>*)t.chat[l],
+    spectral_wgrad_kernel<float, float><<<nmodes, 256, 0, st>>>(B, C, nmodes, (const Cx<float>*)t.chat[l],
                                                          (const Cx<float>*)tc_train_gspec(op), grad + BL.r[l]);
     FCGNO_LAUNCHED();
   }
@@ -959,8 +961,18 @@ fcgno_status train_step_simt(fcgno_model* m, fcgno_op* op, const double* r, cons
   }
   if (!m->ws) m->ws = new NoWorkspace();
   if (prec == FCGNO_BF16) return train_impl_tc(m, op, r, e, loss, grad, l2, st);
-  if (prec == FCGNO_FP64) return train_impl<double>(m, op, r, e, loss, grad, l2, st);
-  return train_impl<float>(m, op, r, e, loss, grad, l2, st);
+  if (prec == FCGNO_FP64) return train_impl<double, float>(m, op, r, e, loss, grad, l2, st);
+  return train_impl<float, float>(m, op, r, e, loss, grad, l2, st);
+}
+
+fcgno_status train_step_f64(fcgno_model* m, fcgno_op* op, const double* r, const double* e, double* loss,
+                            double* grad, bool l2, cudaStream_t st) {
+  if (m->desc.width > 32 || m->desc.proj_width > 32 || 256 % m->desc.width != 0) {
+    set_last_error("training supports width and proj_width <= 32 dividing 256");
+    return FCGNO_EINVAL;
+  }
+  if (!m->ws) m->ws = new NoWorkspace();
+  return train_impl<double, double>(m, op, r, e, loss, grad, l2, st);
 }
 
 }  // namespace fcgno

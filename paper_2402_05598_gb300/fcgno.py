@@ -81,6 +81,7 @@ def _load():
         "fcgno_krylov_harvest": (c_int, [P, P, P, P, c_int, P, P, POINTER(fcgno_solve_info), P]),
         "fcgno_train_step": (c_int, [P, P, P, P, c_int, c_int, P, P, P]),
         "fcgno_train_step_loss": (c_int, [P, P, P, P, c_int, c_int, c_int, P, P, P]),
+        "fcgno_train_step_f64": (c_int, [P, P, P, P, c_int, c_int, P, P, P]),
         "fcgno_model_set_train_recompute": (c_int, [P, c_int]),
         "fcgno_workspace_bytes": (c_size_t, [c_int, c_int, c_int, POINTER(fcgno_model_desc), c_int]),
         "fcgno_precision_supported": (c_int, [c_int, POINTER(fcgno_model_desc), c_int]),
@@ -117,7 +118,7 @@ EXPORTS = [
     "fcgno_model_sync", "fcgno_model_destroy", "fcgno_precond_apply", "fcgno_solve", "fcgno_solve_host",
     "fcgno_solve_host_release",
     "fcgno_solve_noalloc", "fcgno_solve_jacobi", "fcgno_krylov_harvest", "fcgno_train_step", "fcgno_train_step_loss",
-    "fcgno_model_set_train_recompute", "fcgno_workspace_bytes", "fcgno_precision_supported", "fcgno_status_str",
+    "fcgno_model_set_train_recompute", "fcgno_train_step_f64", "fcgno_workspace_bytes", "fcgno_precision_supported", "fcgno_status_str",
     "fcgno_last_error", "fcgno_launch_count", "fcgno_fp64_fma_rate", "fcgno_wait_selftest", "fcgno_set_launch_shape", "fcgno_trace_set",
     "fcgno_trace_collect",
     "fcgno_bucket_create", "fcgno_bucket_admit", "fcgno_bucket_step", "fcgno_bucket_poll", "fcgno_bucket_take",
@@ -363,6 +364,12 @@ def train_step(model: Model, op: Operator, r, e, loss, grad, prec="fp32", stream
         _check(lib.fcgno_train_step_loss(model.handle, op.handle, _ptr(r), _ptr(e), op.B, PREC[prec],
                                          LOSS[loss_kind], _ptr(loss), _ptr(grad), _stream(stream)),
                "fcgno_train_step_loss")
+
+
+def train_step_f64(model: Model, op: Operator, r, e, loss, grad, stream=None, loss_kind="energy"):
+    """fcgno_train_step_f64: the FP64 step with loss and gradient stored in FP64 (float64 tensors)."""
+    _check(lib.fcgno_train_step_f64(model.handle, op.handle, _ptr(r), _ptr(e), op.B, LOSS[loss_kind], _ptr(loss),
+                                    _ptr(grad), _stream(stream)), "fcgno_train_step_f64")
 
 
 def workspace_bytes(N, batch, m_max, desc, prec="bf16") -> int:

@@ -112,6 +112,7 @@ def test_every_entry_rejects_bad_arguments_before_cuda(libpath):
     rejects(L.fcgno_solve_host(4, 1, hp, hp, hp, None, ctypes.byref(opts), 7, None, None), "fcgno_solve_host")
     rejects(L.fcgno_krylov_harvest(None, hp, hp, hp, 0, hp, hp, None, None), "fcgno_krylov_harvest")
     rejects(L.fcgno_train_step_loss(None, None, hp, hp, 1, F.PREC["fp64"], 0, hp, hp, None), "fcgno_train_step")
+    rejects(L.fcgno_train_step_f64(None, None, hp, hp, 1, 0, hp, hp, None), "fcgno_train_step_f64")
     for blocks, steps in ((0, 1), (1, 0), ((1 << 20) + 1, 1), (1, (1 << 24) + 1)):
         rejects(L.fcgno_fp64_fma_rate(blocks, steps, 1.0, 0.0, hp, ctypes.byref(n), None), "fcgno_fp64_fma_rate")
     rejects(L.fcgno_fp64_fma_rate(1, 1, 1.0, 0.0, hp, None, None), "fcgno_fp64_fma_rate")

@@ -416,6 +416,33 @@ def test_train_step_matches_oracle_gradient(lib, dev, prec, tol, out_scale):
     check_train_step(lib, dev, prec, tol, "energy", out_scale)
 
 
+@pytest.mark.parametrize("kind,out_scale", [("energy", 0), ("energy", 1), ("l2", 0)])
+def test_fp64_output_train_step_matches_oracle_gradient_to_1e8(lib, dev, kind, out_scale):
+    """fcgno_train_step_f64 (FP64 arithmetic, loss and gradient stored in FP64) against the
+    oracle's reverse mode: loss within 1e-12 relative, the whole gradient within 1e-8 relative
+    (2-norm), and every parameter group element by element within 1e-8 of its largest entry.
+    Both sides are FP64 throughout and differ only in summation order."""
+    import torch
+    N, B, C, M = 32, 3, 16, 8
+    k, f = batch(N, B, 1300)
+    es = np.stack([np.linalg.solve(O.dense_A(k[b]), f[b].ravel()).reshape(N, N) for b in range(B)])
+    desc, P, model, wdev = model_pair(lib, dev, C, M, L=4, seed=2, out_scale=out_scale)
+    op = lib.Operator(to_dev(k, dev))
+    loss = torch.zeros(1, dtype=torch.float64, device=dev)
+    grad = torch.full((wdev.numel(),), float("nan"), dtype=torch.float64, device=dev)
+    lib.train_step_f64(model, op, to_dev(f, dev), to_dev(es, dev), loss, grad, loss_kind=kind)
+    ref = O.notay_loss_and_grad if kind == "energy" else O.l2_loss_and_grad
+    L_ref, g_ref = ref(P, desc, list(k), list(f), list(es))
+    assert abs(float(loss.item()) - L_ref) <= 1e-12 * L_ref
+    g = grad.cpu().numpy()
+    assert rel(g, g_ref) < 1e-8, rel(g, g_ref)
+    off = I.weight_offsets(desc)
+    for name, (o, s_) in off.items():
+        if name != "_total":
+            gg, rr = g[o:o + s_], g_ref[o:o + s_]
+            assert np.max(np.abs(gg - rr)) <= 1e-8 * np.max(np.abs(rr)), name
+
+
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-6), ("fp32", 2e-4)])
 def test_l2_train_step_matches_oracle_gradient(lib, dev, prec, tol):
     """The L2 ablation loss (2-norm in error form) and its gradient against the oracle's
