@@ -399,7 +399,7 @@ __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : (EPT >= 8 ? 2 : 4)) clu
   const size_t off = (size_t)b * a.n + (size_t)q0 * N;
   double* ph = smc;                     // ph[N + e] = p of band element e; rows 0 and band+1 are halos
   double* red = smc + (size_t)(band + 2) * N;
-  double wv[EPT], rv[EPT], sv[EPT];
+  double wv[EPT], sv[EPT];  // r is re-read in the update (it is still in L1): fewer live registers
 #pragma unroll
   for (int j = 0; j < EPT; ++j) {
     const int e = threadIdx.x + j * T;
@@ -475,7 +475,6 @@ __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : (EPT >= 8 ? 2 : 4)) clu
   for (int j = 0; j < EPT; ++j) {
     const int e = threadIdx.x + j * T;
     sv[j] = 0.0;
-    rv[j] = 0.0;
     if (e < nb) {
       const int ql = e / N, p = e - ql * N;
       const double* row = ph + (size_t)(ql + 1) * N;
@@ -483,9 +482,8 @@ __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : (EPT >= 8 ? 2 : 4)) clu
       const double uw = (p > 0) ? row[p - 1] : 0.0;
       // halo rows carry the neighbour's p, or zero at the Dirichlet walls
       sv[j] = stencil_at(s, off + e, p, q0 + ql, N, wv[j], ue, uw, row[p + N], row[p - N]);
-      rv[j] = s.r[off + e];
       d2[0] = fma(wv[j], sv[j], d2[0]);
-      d2[1] = fma(wv[j], rv[j], d2[1]);
+      d2[1] = fma(wv[j], s.r[off + e], d2[1]);
     }
   }
   block_sums<2>(d2, 2, red, red_out);
@@ -512,7 +510,7 @@ __global__ void __launch_bounds__(MAXT, MAXT > 256 ? 1 : (EPT >= 8 ? 2 : 4)) clu
       if (e < nb) {
         Sn[e] = sv[j];
         s.u[off + e] = fma(alpha, wv[j], s.u[off + e]);
-        const double r1 = fma(-alpha, sv[j], rv[j]);
+        const double r1 = fma(-alpha, sv[j], s.r[off + e]);
         s.r[off + e] = r1;
         r2[0] = fma(r1, r1, r2[0]);
       }
