@@ -832,6 +832,251 @@ __global__ void __launch_bounds__(kAnaThreads, 2)
   if (warp == 0) tmem_dealloc(tbase, tcols);
 }
 
+// Persistent form of tc_analysis_kernel for the wide launch shape at N < 128 (one q chunk):
+// each block keeps one column chunk and walks the active instances b0, b0 + stride, ... of it,
+// so that one item's stage P, read-back and stores overlap the next item's copies and stage-Q
+// MMAs. Roles: warps 0-3 read the Z accumulators back into the stage-P operand, lane 0 of
+// warp 4 issues the MMAs, lane 0 of warp 5 the bulk copies (ring of NS slots, continuing across
+// items), warps 6-9 read stage P back and store the partial coefficients. TMEM: the stage-P
+// accumulators in the first ptiles x NPM columns, NZ Z slots of 32 columns in the last ones
+// (disjoint, so the next item's stage Q runs while stage P is read back). Hand-offs per item:
+// apready (every Z of the item staged), pfull (stage P done: its accumulators readable, the
+// stage-P operand free again), pempty (stage P read back: its accumulators free again).
+constexpr int kAnaPipeThreads = 320, kAnaPipeZ = 3;
+template <int C>
+__global__ void __launch_bounds__(kAnaPipeThreads, 2)
+    tc_analysis_pipe_kernel(TcGeom g, int B, int nbt, bool bf16, const int* __restrict__ active,
+                            const uint16_t* __restrict__ v, const uint16_t* __restrict__ E2,
+                            const uint16_t* __restrict__ G, uint16_t* __restrict__ part, int* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem[];
+  constexpr int NS = 3, NZ = kAnaPipeZ;
+  __shared__ uint64_t full[NS], sfree[NS], zfull[NZ], zempty[NZ], prob, apready, pfull, pempty;
+  __shared__ uint32_t tbase_s;
+  const int N = g.N, PC = g.PC, QC = g.QC, Ky = g.Ky, PT = g.PT;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const uint32_t E2B = 32 * QC * 2, AB = 128 * QC * 2, GB = g.NPM * 2 * PC * 2;
+  uint8_t* sE2 = smem;                            // 32 x QC, K-major: LBO 128, SBO QC*16
+  uint8_t* sA = sE2 + E2B;                        // NS x (128 x QC), MN-major: LBO 128, SBO QC*16
+  uint8_t* sAP = sA + NS * AB;                    // MP x 2PC, K-major: LBO 128, SBO 2PC*16
+  uint8_t* sG = sAP + (size_t)g.MP * 2 * PC * 2;  // NPM x 2PC, K-major: LBO 128, SBO 2PC*16
+  const uint32_t SBO_E = QC * 16, SBO_A = QC * 16, SBO_P = 2 * PC * 16, SBO_G = 2 * PC * 16;
+  constexpr uint32_t tcols = 256;
+  const int chunk = blockIdx.x % g.nchunks;
+  const int b0 = blockIdx.x / g.nchunks, bstride = gridDim.x / g.nchunks;
+  if (warp == 0) tmem_alloc(&tbase_s, tcols);
+  if (tid == 128) {
+    for (int i = 0; i < NS; ++i) {
+      mbar_init(&full[i], 1);
+      mbar_init(&sfree[i], 1);
+    }
+    for (int i = 0; i < NZ; ++i) {
+      mbar_init(&zfull[i], 1);
+      mbar_init(&zempty[i], 4);
+    }
+    mbar_init(&prob, 1);
+    mbar_init(&apready, 4);
+    mbar_init(&pfull, 1);
+    mbar_init(&pempty, 4);
+  }
+  // zero the padding rows of sAP (never written by the Z read-back)
+  for (int idx = tid; idx < (g.MP - Ky * C) * (2 * PC / 8); idx += kAnaPipeThreads) {
+    const int row = Ky * C + idx / (2 * PC / 8), kc = idx % (2 * PC / 8);
+    *reinterpret_cast<uint4*>(sAP + kmajor_off(row, kc * 8, 128, SBO_P)) = make_uint4(0, 0, 0, 0);
+  }
+  fence_smem_to_async();
+  fence_before_sync();
+  __syncthreads();
+  fence_after_sync();
+  const uint32_t tbase = tbase_s;
+  const uint32_t tP = tbase;                        // ptiles x NPM stage-P columns
+  const uint32_t tQ = tbase + tcols - NZ * 32;      // NZ Z slots
+  const int p0 = chunk * PC;
+  const int cols_mt = 128 / C;                      // grid columns per m-tile
+  const int mtiles = PC / cols_mt;
+  const int ptiles = g.MP / 128;
+  bool ok = true;
+  if (warp == 4) {
+    // ================================ MMA issuer (one lane) ============================
+    if (lane == 0) {
+      int gstep = 0, mmas = 0, item = 0, pissued = 0;
+      const uint32_t idQ = idesc_f16(128, 32, bf16, true, false);
+      const uint32_t idP = idesc_f16(128, g.NPM, bf16, false, false);
+      ok = mbar_wait(&prob, 0);
+      for (int b = b0; b < B && ok; b += bstride) {
+        if (tc_inactive(active, b)) continue;
+        for (int mt = 0; mt < mtiles && ok; ++mt, ++gstep) {
+          const int buf = gstep % NS;
+          ok = mbar_wait(&full[buf], (gstep / NS) & 1);
+          if (ok && gstep >= NZ) ok = mbar_wait(&zempty[gstep % NZ], ((gstep / NZ) - 1) & 1);
+          if (!ok) break;
+          fence_after_sync();
+          const uint32_t tq = tQ + (gstep % NZ) * 32;
+          const uint32_t sa = smem_addr(sA + buf * AB), e2 = smem_addr(sE2);
+          for (int ks = 0; ks < QC / 16; ++ks)
+            mma(tq, desc(sa + ks * 256, 128, SBO_A), desc(e2 + ks * 256, 128, SBO_E), idQ, ks > 0);
+          commit(&sfree[buf]);
+          commit(&zfull[gstep % NZ]);
+          mmas = gstep + 1;
+        }
+        if (ok) ok = mbar_wait(&apready, item & 1);                       // every Z of the item staged
+        if (ok && item > 0) ok = mbar_wait(&pempty, (item - 1) & 1);      // previous stage P read back
+        if (ok) {
+          fence_after_sync();
+          for (int pt = 0; pt < ptiles; ++pt)
+            for (int ks = 0; ks < 2 * PC / 16; ++ks) {
+              const uint64_t ad = desc(smem_addr(sAP) + pt * 16 * SBO_P + ks * 2 * 128, 128, SBO_P);
+              const uint64_t bd = desc(smem_addr(sG) + ks * 2 * 128, 128, SBO_G);
+              mma(tP + pt * g.NPM, ad, bd, idP, ks > 0);
+            }
+          commit(&pfull);
+          pissued = item + 1;
+        }
+        ++item;
+      }
+      if (!ok) {
+        // error path: let the MMAs this block started finish (bounded)
+        for (int u = mmas > NS ? mmas - NS : 0; u < mmas; ++u) mbar_wait(&sfree[u % NS], (u / NS) & 1);
+        if (pissued > 0) mbar_wait(&pfull, (pissued - 1) & 1);
+        atomicExch(err, 1);
+      }
+    }
+  } else if (warp == 5) {
+    // ================================ load issuer (one lane) ===========================
+    if (lane == 0) {
+      int gstep = 0, loads = 0;
+      mbar_expect_tx(&prob, GB + E2B);
+      bulk_g2s(sG, G + (size_t)chunk * g.NPM * 2 * PC, GB, &prob);
+      bulk_g2s(sE2, E2, E2B, &prob);
+      pdl_wait();  // the activations come from the kernel just before
+      pdl_trigger();
+      for (int b = b0; b < B && ok; b += bstride) {
+        if (tc_inactive(active, b)) continue;
+        const uint16_t* vb = v + (size_t)b * N * N * C;
+        for (int mt = 0; mt < mtiles && ok; ++mt, ++gstep) {
+          if (gstep >= NS) ok = mbar_wait(&sfree[gstep % NS], ((gstep / NS) - 1) & 1);  // slot read
+          if (!ok) break;
+          const int buf = gstep % NS, pm = p0 + mt * cols_mt;
+          mbar_expect_tx(&full[buf], AB);
+          bulk_g2s(sA + buf * AB, vb + (size_t)(pm / PT) * 128 * C, AB, &full[buf]);
+          loads = gstep + 1;
+        }
+      }
+      if (!ok) {
+        for (int u = loads > NS ? loads - NS : 0; u < loads; ++u) mbar_wait(&full[u % NS], (u / NS) & 1);
+        atomicExch(err, 1);
+      }
+      mbar_wait(&prob, 0);
+    }
+  } else if (warp < 4) {
+    // ================================ Z read-back warps 0-3 ============================
+    // Z of an m-tile: lane M -> (column, channel), columns (k2, t) -> sAP[(k2, c)][(p, t)]
+    const int M = warp * 32 + lane, Gi = M >> 3;
+    const int u = Gi / ((C / 8) * PT), cg = (Gi / PT) % (C / 8), pl2 = Gi % PT;
+    const int c = cg * 8 + (M & 7);
+    int gmt = 0, item = 0;
+    for (int b = b0; b < B && ok; b += bstride) {
+      if (tc_inactive(active, b)) continue;
+      if (item > 0) {
+        ok = mbar_wait(&pfull, (item - 1) & 1);  // the previous item's stage P has read sAP
+        fence_after_sync();
+      }
+      for (int mt = 0; mt < mtiles && ok; ++mt, ++gmt) {
+        ok = mbar_wait(&zfull[gmt % NZ], (gmt / NZ) & 1);
+        if (!ok) break;
+        fence_after_sync();
+        const uint32_t tq = tQ + (gmt % NZ) * 32 + ((uint32_t)(warp * 32) << 16);
+        float z[32];
+        float tmp[16];
+        tmem_ld16(tq, tmp);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[i] = tmp[i];
+        tmem_ld16(tq + 16, tmp);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) z[16 + i] = tmp[i];
+        fence_before_sync();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&zempty[gmt % NZ]);
+        const int pl = mt * cols_mt + u * PT + pl2;
+#pragma unroll
+        for (int k2 = 0; k2 < 16; ++k2) {  // Ky <= 16: static indices keep z in registers
+          if (k2 < Ky) {
+            const int row = k2 * C + c;
+            *reinterpret_cast<uint32_t*>(sAP + kmajor_off(row, 2 * pl, 128, SBO_P)) =
+                pack2(z[2 * k2], z[2 * k2 + 1], bf16);
+          }
+        }
+      }
+      if (!ok) break;
+      fence_smem_to_async();
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&apready);
+      ++item;
+    }
+  } else {
+    // ================================ stage-P read-back warps 6-9 ======================
+    pdl_wait();  // (before their global writes)
+    const int q = warp & 3;  // TMEM lane quadrant of this warp
+    const size_t img = (size_t)128 * 2 * C;  // elements per image
+    int item = 0;
+    for (int b = b0; b < B && ok; b += bstride) {
+      if (tc_inactive(active, b)) continue;
+      ok = mbar_wait(&pfull, item & 1);
+      if (!ok) break;
+      fence_after_sync();
+      // P row (k2, c), columns (j, t') -> image of mode j*Ky + k2, row b % 128, K (c, t')
+      const int bt = b / 128, br = b % 128;
+      for (int pt = 0; pt < ptiles; ++pt) {
+        const int row = pt * 128 + q * 32 + lane;
+        const int k2 = row / C, cc = row % C;
+        const uint32_t off = kmajor_off(br, 2 * cc, 128, 2 * C * 16) / 2;
+        for (int c0 = 0; c0 < g.NPM; c0 += 16) {
+          float val[16];
+          tmem_ld16(tP + pt * g.NPM + c0 + ((uint32_t)(q * 32) << 16), val);
+          if (row < Ky * C) {
+#pragma unroll
+            for (int i = 0; i < 16; i += 2) {
+              const int j = (c0 + i) >> 1;
+              if (j < 2 * g.M) {
+                const int mode = j * Ky + k2;
+                uint16_t* dst = part + (((size_t)mode * g.nchunks + chunk) * nbt + bt) * img + off;
+                *reinterpret_cast<uint32_t*>(dst) = pack2(val[i], val[i + 1], bf16);
+              }
+            }
+          }
+        }
+      }
+      fence_before_sync();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&pempty);
+      ++item;
+    }
+  }
+  fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tbase, tcols);
+}
+
+// Whether the persistent analysis applies to geometry g: one q chunk (N < 128) and the stage-P
+// accumulators beside the Z slots in a block's 256 TMEM columns.
+static bool ana_pipe_ok(const TcGeom& g) {
+  return g.N < 128 && g.N / g.QC == 1 && (g.MP / 128) * g.NPM + kAnaPipeZ * 32 <= 256;
+}
+
+// Blocks of the persistent analysis: two per SM (a multiple of the column chunks), at most one
+// per (chunk, instance).
+static int ana_pipe_blocks(const TcGeom& g, int B) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const int per = std::max(1, (2 * sms) / g.nchunks);
+  return g.nchunks * std::min(per, B);
+}
+
 // Per-mode complex channel mixing across instances: rows = instances (128 per CTA).
 // Input: for each column chunk the 16-bit partial-coefficient image of this (mode, block of
 // 128 instances), 128 x 2C K-major (K = (c, re/im)); the MMA sums the chunks in its FP32
@@ -1451,7 +1696,7 @@ static fcgno_status raise_smem_limits(const TcGeom& g) {
     ss_limit = std::max(ss_limit, synthesis_bytes(go, go.SPC, di, dout));
   }
   static std::mutex set_mu;  // concurrent callers on other threads share these limits
-  static size_t set_sa = 0, set_ss = 0, set_sm = 0;
+  static size_t set_sa = 0, set_ss = 0, set_sm = 0, set_sp = 0;
   std::lock_guard<std::mutex> set_lk(set_mu);
   auto raise = [](const void* fn, size_t bytes, size_t& set) -> cudaError_t {
     if (bytes <= set) return cudaSuccess;
@@ -1462,6 +1707,7 @@ static fcgno_status raise_smem_limits(const TcGeom& g) {
     return e;
   };
   FCGNO_CUDA_TRY(raise((const void*)tc_analysis_kernel<C>, sa_limit, set_sa));
+  if (ana_pipe_ok(g)) FCGNO_CUDA_TRY(raise((const void*)tc_analysis_pipe_kernel<C>, analysis_smem(g), set_sp));
   FCGNO_CUDA_TRY(raise((const void*)tc_synthesis_kernel<C>, ss_limit, set_ss));
   FCGNO_CUDA_TRY(raise((const void*)tc_mix_kernel<C>, sm_limit, set_sm));
   return FCGNO_OK;
@@ -1516,9 +1762,17 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
   for (int l = 0; l < d.layers; ++l) {
     {
       TraceScope ts("tc_analysis", st);
-      FCGNO_CUDA_TRY(launch_chained(tc_analysis_kernel<C>, dim3(gs.nchunks, B), dim3(kAnaThreads), sa, st, gs, nbt,
-                                    bf16, active, (const uint16_t*)cur, (const uint16_t*)tab->E2,
-                                    (const uint16_t*)tab->G, T.part, T.err));
+      if (!narrow && ana_pipe_ok(gs)) {
+        // wide shape: persistent blocks, each walking the instances of one column chunk
+        FCGNO_CUDA_TRY(launch_chained(tc_analysis_pipe_kernel<C>, dim3(ana_pipe_blocks(gs, B)),
+                                      dim3(kAnaPipeThreads), sa, st, gs, B, nbt, bf16, active,
+                                      (const uint16_t*)cur, (const uint16_t*)tab->E2, (const uint16_t*)tab->G,
+                                      T.part, T.err));
+      } else {
+        FCGNO_CUDA_TRY(launch_chained(tc_analysis_kernel<C>, dim3(gs.nchunks, B), dim3(kAnaThreads), sa, st, gs,
+                                      nbt, bf16, active, (const uint16_t*)cur, (const uint16_t*)tab->E2,
+                                      (const uint16_t*)tab->G, T.part, T.err));
+      }
     }
     FCGNO_LAUNCHED();
     {
