@@ -46,18 +46,25 @@ def test_noalloc_solve_matches_solve_on_two_calls_in_a_row(lib, dev):
             assert torch.cuda.mem_get_info()[0] == free_before
         assert [i["iters"] for i in ib] == [i["iters"] for i in ia]
         assert [i["status"] for i in ib] == [i["status"] for i in ia] == [lib.FCGNO_OK] * B
-        for b in range(B):
-            assert abs(ib[b]["relres"] - ia[b]["relres"]) <= 1e-10 * max(ia[b]["relres"], 1e-300) + 1e-14
-        assert rel(xb.cpu().numpy(), xa.cpu().numpy()) < 1e-10
         if fixed:
-            xs = xb.cpu().numpy()
+            # 20 fixed iterations: the two paths sum the dot products of Algorithm 1 in different
+            # orders (one CTA per instance or a cluster of bands), and the recurrences amplify
+            # that rounding; both are held to 10x the oracle's own sensitivity to the order
+            xs, xas = xb.cpu().numpy(), xa.cpu().numpy()
             for b in range(B):
                 run = lambda d: O.fcg(lambda u: O.apply_A(k[b], u), lambda r: r, f[b], x0[b], m, iters,
                                       **({} if d is None else {"dot": d}))["u"]
                 ref = run(None)
                 sens = rel(run(lambda a_, b_: math.fsum(np.ravel(a_ * b_))), ref)
+                tol = max(1e-10, 10.0 * sens)
                 assert ib[b]["iters"] == iters
-                assert rel(xs[b], ref) < max(1e-10, 10.0 * sens)
+                assert rel(xs[b], ref) < tol
+                assert rel(xs[b], xas[b]) < tol
+                assert abs(ib[b]["relres"] - ia[b]["relres"]) <= tol * max(ia[b]["relres"], 1e-300) + 1e-14
+        else:
+            for b in range(B):
+                assert abs(ib[b]["relres"] - ia[b]["relres"]) <= 1e-10 * max(ia[b]["relres"], 1e-300) + 1e-14
+            assert rel(xb.cpu().numpy(), xa.cpu().numpy()) < 1e-10
 
 
 def test_noalloc_solve_rejects_problems_beyond_its_fixed_scratch(lib, dev):
