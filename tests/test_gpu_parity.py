@@ -675,6 +675,35 @@ def test_workspace_bytes_counts_what_a_solve_allocates(lib, dev):
     op.close()
 
 
+def test_stopped_instances_do_not_change_the_others(lib, dev):
+    """200 instances at 64 x 64 in the wide launch shape, where the analysis runs as persistent
+    blocks that walk two instances each: with every third instance stopped at iteration 0 (zero
+    right-hand side, so the kernels skip it), every other instance's iterate after 6 BF16
+    FCG-NO iterations is bit-identical to the run in which all 200 are active. Every step works
+    per instance (the mode mixing per row of its 128-instance tile), so the batch around an
+    instance must not change it."""
+    import torch
+    N, B = 64, 200
+    k, f = batch(N, B, 4700)
+    desc, P, model, _w = model_pair(lib, dev, 32, 12, out_scale=1)
+    op = lib.Operator(to_dev(k, dev))
+    fa = to_dev(f, dev)
+    fz = fa.clone()
+    fz[::3] = 0.0
+    lib.set_launch_shape("wide")
+    try:
+        xa = torch.zeros_like(fa)
+        lib.solve(op, model, fa, xa, m_max=5, max_iter=6, fixed_iters=True, prec="bf16")
+        xz = torch.zeros_like(fa)
+        info = lib.solve(op, model, fz, xz, m_max=5, max_iter=6, fixed_iters=True, prec="bf16")
+    finally:
+        lib.set_launch_shape("auto")
+    keep = [b for b in range(B) if b % 3 != 0]
+    assert all(info[b]["iters"] == 0 for b in range(0, B, 3))
+    assert all(info[b]["iters"] == 6 for b in keep)
+    assert torch.equal(xz[keep], xa[keep])
+
+
 @pytest.mark.parametrize("N,C,M", [(64, 32, 12), (32, 16, 8), (100, 16, 8)])
 def test_narrow_launch_shapes_match_the_wide_ones(lib, dev, N, C, M):
     """Once few instances are still running, replayed iterations switch to the narrow launch
