@@ -1066,13 +1066,13 @@ static bool ana_pipe_ok(const TcGeom& g) {
 // Blocks of the persistent analysis: two per SM (a multiple of the column chunks), at most one
 // per (chunk, instance).
 static int ana_pipe_blocks(const TcGeom& g, int B) {
-  static int sms = 0;
-  if (sms == 0) {
-    int dev = 0;
+  // the SM count, read once (a function-local static: initialised once even with concurrent callers)
+  static const int sms = [] {
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 1;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 1;
+  }();
   const int per = std::max(1, (2 * sms) / g.nchunks);
   return g.nchunks * std::min(per, B);
 }
