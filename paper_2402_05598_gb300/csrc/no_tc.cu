@@ -847,7 +847,10 @@ template <int C>
 __global__ void __launch_bounds__(kAnaPipeThreads, 2)
     tc_analysis_pipe_kernel(TcGeom g, int B, int nbt, bool bf16, const int* __restrict__ active,
                             const uint16_t* __restrict__ v, const uint16_t* __restrict__ E2,
-                            const uint16_t* __restrict__ G, uint16_t* __restrict__ part, int* __restrict__ err) {
+                            const uint16_t* __restrict__ G, uint16_t* __restrict__ part, int* __restrict__ err,
+                            int rev) {
+  // rev: walk the instances from the last to the first. The layer input was written in
+  // increasing instance order, so its last instances are the likeliest to be still in L2.
   extern __shared__ __align__(1024) uint8_t smem[];
   constexpr int NS = 3, NZ = kAnaPipeZ;
   __shared__ uint64_t full[NS], sfree[NS], zfull[NZ], zempty[NZ], prob, apready, pfull, pempty;
@@ -902,7 +905,8 @@ __global__ void __launch_bounds__(kAnaPipeThreads, 2)
       const uint32_t idQ = idesc_f16(128, 32, bf16, true, false);
       const uint32_t idP = idesc_f16(128, g.NPM, bf16, false, false);
       ok = mbar_wait(&prob, 0);
-      for (int b = b0; b < B && ok; b += bstride) {
+      for (int bb = b0; bb < B && ok; bb += bstride) {
+        const int b = rev ? B - 1 - bb : bb;
         if (tc_inactive(active, b)) continue;
         for (int mt = 0; mt < mtiles && ok; ++mt, ++gstep) {
           const int buf = gstep % NS;
@@ -949,7 +953,8 @@ __global__ void __launch_bounds__(kAnaPipeThreads, 2)
       bulk_g2s(sE2, E2, E2B, &prob);
       pdl_wait();  // the activations come from the kernel just before
       pdl_trigger();
-      for (int b = b0; b < B && ok; b += bstride) {
+      for (int bb = b0; bb < B && ok; bb += bstride) {
+        const int b = rev ? B - 1 - bb : bb;
         if (tc_inactive(active, b)) continue;
         const uint16_t* vb = v + (size_t)b * N * N * C;
         for (int mt = 0; mt < mtiles && ok; ++mt, ++gstep) {
@@ -974,7 +979,8 @@ __global__ void __launch_bounds__(kAnaPipeThreads, 2)
     const int u = Gi / ((C / 8) * PT), cg = (Gi / PT) % (C / 8), pl2 = Gi % PT;
     const int c = cg * 8 + (M & 7);
     int gmt = 0, item = 0;
-    for (int b = b0; b < B && ok; b += bstride) {
+    for (int bb = b0; bb < B && ok; bb += bstride) {
+        const int b = rev ? B - 1 - bb : bb;
       if (tc_inactive(active, b)) continue;
       if (item > 0) {
         ok = mbar_wait(&pfull, (item - 1) & 1);  // the previous item's stage P has read sAP
@@ -1019,7 +1025,8 @@ __global__ void __launch_bounds__(kAnaPipeThreads, 2)
     const int q = warp & 3;  // TMEM lane quadrant of this warp
     const size_t img = (size_t)128 * 2 * C;  // elements per image
     int item = 0;
-    for (int b = b0; b < B && ok; b += bstride) {
+    for (int bb = b0; bb < B && ok; bb += bstride) {
+        const int b = rev ? B - 1 - bb : bb;
       if (tc_inactive(active, b)) continue;
       ok = mbar_wait(&pfull, item & 1);
       if (!ok) break;
@@ -1767,7 +1774,7 @@ static fcgno_status run_tc(fcgno_model* m, const fcgno_op* op, const double* r, 
         FCGNO_CUDA_TRY(launch_chained(tc_analysis_pipe_kernel<C>, dim3(ana_pipe_blocks(gs, B)),
                                       dim3(kAnaPipeThreads), sa, st, gs, B, nbt, bf16, active,
                                       (const uint16_t*)cur, (const uint16_t*)tab->E2, (const uint16_t*)tab->G,
-                                      T.part, T.err));
+                                      T.part, T.err, 1));
       } else {
         FCGNO_CUDA_TRY(launch_chained(tc_analysis_kernel<C>, dim3(gs.nchunks, B), dim3(kAnaThreads), sa, st, gs,
                                       nbt, bf16, active, (const uint16_t*)cur, (const uint16_t*)tab->E2,
