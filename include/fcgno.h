@@ -92,7 +92,8 @@ typedef struct {
   int m_max;       /* truncation m_max of Algorithm 1, 1 <= m_max <= 8                       */
   int max_iter;    /* iteration cap                                                          */
   int fixed_iters; /* nonzero: ignore tol and run exactly max_iter iterations                */
-  int check_every; /* host reads the convergence counter every this many iterations (>=1)  */
+  int check_every; /* host reads the convergence counter every this many iterations (>=1); */
+                   /* once 32 or fewer instances run, every min(check_every, 2) iterations   */
 } fcgno_solve_opts;
 
 typedef struct {
@@ -158,7 +159,8 @@ fcgno_status fcgno_precond_apply(fcgno_model_t model, fcgno_op_t op, const doubl
 /* Algorithm 1 for every instance of A: x holds u_0 on entry and the iterate on exit;
  * b is [batch][N][N]; Bpc NULL runs the identity preconditioner (plain CG for m_max = 1).
  * info is a HOST array of batch entries. Synchronises on `stream` every check_every
- * iterations and at exit (the call returns when every instance has stopped).
+ * iterations (every min(check_every, 2) once 32 or fewer instances run) and at exit (the
+ * call returns when every instance has stopped).
  * Errors: EINVAL for a NULL A, b or x, bad opts (tol < 0, m_max outside 1..8,
  * max_iter < 0), N < 2*modes, an unknown precision or a shape the 16-bit path does not
  * support; ENOMEM; ECUDA; ETIMEOUT (see the

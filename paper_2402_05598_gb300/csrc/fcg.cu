@@ -34,6 +34,8 @@ constexpr int kThreads = 256;   // threads per CTA (tiled path)
 constexpr int kEPT = kTile / kThreads;
 constexpr int kParts = kMaxWindow + 2;
 constexpr int kNarrowRunning = 80;  // running instances at or below which the narrow launch shape is used
+constexpr int kTailRunning = 32;    // running instances at or below which a solve checks every kTailReplay
+constexpr int kTailReplay = 2;      //   iterations (or check_every, if smaller)
 
 struct IterArgs {
   int N;
@@ -874,9 +876,9 @@ static fcgno_status launch_iteration(fcgno_op* op, fcgno_model* model, fcgno_pre
 // Captures G iterations into a CUDA graph (reused while the baked-in parameters match).
 static fcgno_status ensure_graph(fcgno_op* op, fcgno_model* model, fcgno_prec prec, const IterArgs& a,
                                  const State& s, const LoopShape& L, const double* b, const double* x, int G,
-                                 int jacobi, bool narrow = false, const ServeDev* serve = nullptr) {
+                                 int jacobi, bool narrow = false, const ServeDev* serve = nullptr, int slot = -1) {
   SolverWorkspace& w = op->ws;
-  IterGraph& g = w.graph[narrow ? 1 : 0];
+  IterGraph& g = w.graph[slot >= 0 ? slot : (narrow ? 1 : 0)];
   const uint64_t gen = model ? model->gen : 0;
   if (g.exec && g.trace_gen == trace_generation() && g.model == model && g.model_gen == gen &&
       g.prec == (int)prec && g.nslots == a.nslots && g.jacobi == jacobi &&
@@ -984,18 +986,25 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
   int i = 0;
   int since_check = 0;
   int last_graph = 0;
+  // the tail of a batch (few instances left, converging over a few iterations) replays
+  // shorter graphs, so that the solve ends closer to the last instance's convergence
+  const int Gt = std::min(G, kTailReplay);
+  int curG = G;
   while (i < o.max_iter) {
     bool replayed = false;
-    if (use_graph && i > 0 && o.max_iter - i >= G) {
+    const bool tail = Gt < G && running <= kTailRunning;
+    const int Gx = tail ? Gt : G;
+    if (use_graph && i > 0 && o.max_iter - i >= Gx) {
       // the first iteration ran eagerly, so every lazily allocated buffer exists before capture
       const int mode = launch_shape_mode();
       const bool narrow = mode == 2 || (mode == 0 && can_narrow && running <= kNarrowRunning);
-      last_graph = narrow ? 1 : 0;
-      FCGNO_TRY(ensure_graph(op, model, prec, a, s, narrow ? Ln : L, b, x, G, jacobi, narrow));
+      last_graph = (narrow ? 1 : 0) + (tail ? 2 : 0);
+      FCGNO_TRY(ensure_graph(op, model, prec, a, s, narrow ? Ln : L, b, x, Gx, jacobi, narrow, nullptr, last_graph));
       FCGNO_CUDA_TRY(cudaGraphLaunch(w.graph[last_graph].exec, cs));
       g_launches.fetch_add(w.graph[last_graph].kernels, std::memory_order_relaxed);
-      i += G;
-      since_check = G;
+      i += Gx;
+      since_check = Gx;
+      curG = Gx;
       replayed = true;
     } else {
       const bool narrow = launch_shape_mode() == 2;
@@ -1009,8 +1018,9 @@ static fcgno_status solve_impl(fcgno_op* op, fcgno_model* model, const double* b
       }
       ++i;
       ++since_check;
+      curG = Gx;
     }
-    if (since_check >= G || i >= o.max_iter || (use_graph && i == 1)) {
+    if (since_check >= curG || i >= o.max_iter || (use_graph && i == 1)) {
       since_check = 0;
       FCGNO_CUDA_TRY(cudaMemcpyAsync(h_ndone, w.ndone, sizeof(int), cudaMemcpyDeviceToHost, cs));
       FCGNO_CUDA_TRY(cudaStreamSynchronize(cs));
@@ -1396,13 +1406,15 @@ extern "C" fcgno_status fcgno_solve_noalloc(fcgno_op_t A, const double* b, doubl
   init_finalize_kernel<<<B, kThreads, 0, st>>>(a, s);
   FCGNO_LAUNCHED();
   const int check_every = std::max(1, o.check_every);
-  int h_ndone = 0;
+  int h_ndone = 0, since_check = 0, cur = check_every;
   for (int i = 0; i < o.max_iter; ++i) {
     FCGNO_TRY(launch_vector_step(a, s, L, st));
-    if ((i + 1) % check_every == 0 || i + 1 == o.max_iter) {
+    if (++since_check >= cur || i + 1 == o.max_iter) {
       FCGNO_CUDA_TRY(cudaMemcpyAsync(&h_ndone, s.ndone, sizeof(int), cudaMemcpyDeviceToHost, st));
       FCGNO_CUDA_TRY(cudaStreamSynchronize(st));
       if (h_ndone >= B) break;
+      since_check = 0;
+      cur = B - h_ndone <= kTailRunning ? std::min(check_every, kTailReplay) : check_every;
     }
   }
   // per-instance results, copied through fixed-size host buffers

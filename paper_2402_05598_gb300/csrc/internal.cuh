@@ -148,7 +148,8 @@ struct SolverWorkspace {
   int cap_B = 0, cap_n = 0, cap_slots = 0, cap_tiles = 0;
   cudaStream_t cs = nullptr;     // internal stream (graph capture needs a non-default stream)
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
-  IterGraph graph[2];       // replayed iterations: [0] wide, [1] narrow 16-bit preconditioner launches
+  IterGraph graph[4];       // replayed iterations: [0] wide, [1] narrow 16-bit preconditioner launches;
+                            // [2], [3] the same, shorter, for the tail of a batch
   int* iter = nullptr;      // [1] device iteration counter
   double* r = nullptr;      // [B][n]
   double* w = nullptr;      // [B][n]  preconditioned residual
