@@ -748,6 +748,44 @@ def test_narrow_launch_shapes_match_the_wide_ones(lib, dev, N, C, M):
                 assert O.energy_norm(k[b], ustar - xh[b]) <= O.energy_norm(k[b], ustar)
 
 
+@pytest.mark.gpu
+@pytest.mark.parametrize("prec", ["bf16", None])
+def test_host_check_cadence_does_not_change_the_solve(lib, dev, trained_pair, prec):
+    """Each instance stops on the device at its own convergence (Algorithm 1's test on
+    ||r_i||), so how often the host reads the convergence counter changes neither an iterate
+    nor an iteration count. Checked with the launch shape held wide: iteration by iteration
+    (check_every 1, no graph), and replayed 8- or 16-iteration graphs that drop to
+    2-iteration replays once 32 or fewer of the 48 instances run. BF16 FCG-NO at 64 x 64 with
+    the briefly trained preconditioner (m = 5, tol 1e-6, cap 400: some instances converge, the
+    others stop at the cap) and plain CG at 32 x 32 (tol 1e-8, 198 to 512 iterations in the
+    oracle): bit-identical iterates and the same per-instance iteration counts and statuses."""
+    import torch
+    N, B = (64, 48) if prec else (32, 48)
+    k, f = batch(N, B, 5100 + N)
+    model = trained_pair[2] if prec else None
+    op = lib.Operator(to_dev(k, dev))
+    fd = to_dev(f, dev)
+    tol = 1e-6 if prec else 1e-8
+    out = {}
+    lib.set_launch_shape("wide")
+    try:
+        for check in (1, 8, 16):
+            x = torch.zeros_like(fd)
+            info = lib.solve(op, model, fd, x, tol=tol, m_max=5 if prec else 1, max_iter=400 if prec else 2000,
+                             prec=prec or "fp64", check_every=check)
+            out[check] = (x.cpu(), [(i["iters"], i["status"]) for i in info])
+    finally:
+        lib.set_launch_shape("auto")
+    its = [t[0] for t in out[1][1]]
+    if not prec:
+        assert all(t[1] == lib.FCGNO_OK for t in out[1][1]), out[1][1]
+    assert sum(t[1] == lib.FCGNO_OK for t in out[1][1]) >= 8, out[1][1]
+    assert max(its) > min(its), its  # the instances stop at different iterations
+    for check in (8, 16):
+        assert out[check][1] == out[1][1], check
+        assert torch.equal(out[check][0], out[1][0]), check
+
+
 @pytest.mark.parametrize("N,C,M,B,prec", [(64, 32, 12, 5, "bf16"), (32, 16, 8, 130, "bf16"), (64, 32, 12, 3, "fp16")])
 def test_narrow_shape_preconditioner_matches_oracle(lib, dev, N, C, M, B, prec):
     """The narrow launch shape (fcgno_set_launch_shape forces it) runs the 16-bit analysis in
