@@ -898,6 +898,10 @@ __global__ void __launch_bounds__(kAnaPipeThreads, 2)
   const int mtiles = PC / cols_mt;
   const int ptiles = g.MP / 128;
   bool ok = true;
+  // Every role skips the stopped instances on its own, and the MMA issuer and the Z read-back
+  // read the status flags without waiting on the programmatic link. They all see the same flags
+  // because this kernel never directly follows the FCG step that sets them: the encoder or a
+  // synthesis runs in between, and those trigger their successor only after their own wait.
   if (warp == 4) {
     // ================================ MMA issuer (one lane) ============================
     if (lane == 0) {
