@@ -41,10 +41,13 @@ is checked node by node against a scalar closed form (encoder channel order, act
 biases, decoder, the h^2 rms(r) scale); a one-layer NO with a single nonzero spectral weight
 and a single-mode input is checked against its closed form (the weight layout and transform
 conventions); constant inputs reduce the four-layer NO with random weights to its mean mode,
-checked against scalar loops; with general spectral blocks, non-constant inputs and several
-layers the composition itself is parity unpinned (the CUDA path is compared with this oracle
-only). The same holds for
-FCG-NO iterates with that preconditioner.
+checked against scalar loops; with random weights in every block and non-constant inputs the
+four-layer composition is checked against a second statement that reaches the kept modes
+through numpy's full-grid FFTs and explicit channel loops (it shares this module's readings of
+the paper, not its arithmetic; planted slips in the mixing, the slot order or the grid axes fail
+it). FCG-NO iterates with such a preconditioner have no closed form; they are pinned through
+properties Algorithm 1 guarantees for any preconditioner: monotone energy error, A-orthogonal
+window directions, an exact line search and a recursively updated residual equal to f - A u.
 """
 from __future__ import annotations
 

@@ -513,6 +513,86 @@ def test_constant_fields_follow_the_mean_mode_through_every_layer():
     assert np.max(np.abs(z - want)) <= 1e-12 * h * h * max(1.0, abs(want) / (h * h))
 
 
+def _no_by_full_grid_fft(P, desc, r, logk):
+    """The neural operator stated a second way, for the pin below: each spectral layer takes the
+    whole grid's discrete Fourier transform with numpy's FFT, picks the kept modes out of it,
+    mixes them, places the mixed coefficients (doubled for x2-frequencies above 0) into an
+    otherwise empty N x N spectrum and returns the real part of numpy's inverse FFT, instead of
+    the oracle's dense truncated twiddle products. GELU comes from math.erf, the pointwise maps
+    are explicit loops over channels."""
+    N, C, M = r.shape[0], desc.width, desc.modes
+    n = N * N
+    gelu = np.vectorize(lambda x: 0.5 * x * (1.0 + math.erf(x / math.sqrt(2.0))))
+    rms = math.sqrt(float(np.sum(r * r)) / n)
+    x_in = [r / rms, logk]
+    v = np.stack([sum(P["lift_w"][c][i] * x_in[i] for i in range(2)) + P["lift_b"][c] for c in range(C)], axis=-1)
+    k1_of_slot = list(range(M)) + list(range(-M, 0))
+    L = len(P["layers"])
+    for l, lay in enumerate(P["layers"]):
+        spec_in = np.fft.fft2(v, axes=(0, 1)) / n          # [x2 frequency][x1 frequency][channel]
+        full = np.zeros((N, N, C), dtype=complex)
+        for j, k1 in enumerate(k1_of_slot):
+            for k2 in range(M):
+                cin = spec_in[k2, k1 % N, :]
+                cout = np.array([sum(cin[i] * lay["r"][j, k2, i, o] for i in range(C)) for o in range(C)])
+                full[k2, k1 % N, :] += (1.0 if k2 == 0 else 2.0) * cout
+        spec = np.real(np.fft.ifft2(full, axes=(0, 1))) * n
+        h = np.stack([sum(lay["w"][o][i] * v[..., i] for i in range(C)) + lay["b"][o] for o in range(C)], axis=-1)
+        h = h + spec
+        v = gelu(h) if l < L - 1 else h
+    Cp = desc.proj_width
+    hid = [gelu(sum(P["proj1_w"][j][c] * v[..., c] for c in range(C)) + P["proj1_b"][j]) for j in range(Cp)]
+    zt = sum(P["proj2_w"][j] * hid[j] for j in range(Cp)) + P["proj2_b"][0]
+    scale = (1.0 / (N + 1)) ** 2 * rms
+    if desc.output_scale:
+        scale = scale * np.exp(-logk)
+    return scale * zt
+
+
+@pytest.mark.parametrize("N,C,M,out_scale", [(16, 4, 4, 0), (12, 3, 5, 1), (20, 4, 3, 1)])
+def test_composed_no_with_random_weights_matches_a_full_grid_fft_statement(N, C, M, out_scale):
+    """The whole four-layer neural operator with random weights in every block (encoder, W_l,
+    b_l, all 2M x M spectral blocks, decoder) against the second statement above, which reaches
+    the kept modes through full-grid FFTs: a slip anywhere in the oracle's truncated transforms,
+    their slot order, the mixing's index order, the synthesis weights, the layer composition or
+    the output scale that the one-mode and constant-field pins leave open shows up here with all
+    modes active at once. N = 12 and 20 are not powers of two; at N = 12, M = 5 the x1
+    frequencies -5..4 nearly fill the grid."""
+    desc = I.ModelDesc(width=C, layers=4, modes=M, proj_width=C, output_scale=out_scale)
+    blob = I.xavier_weights(desc, 40 + N).astype(np.float64)
+    rng = np.random.default_rng(N)
+    off = I.weight_offsets(desc)
+    for name in ["lift_b", "proj1_b", "proj2_b"] + [f"b{l}" for l in range(4)]:
+        o, size = off[name]
+        blob[o:o + size] = rng.uniform(-0.3, 0.3, size)
+    P = O.unpack_weights(blob, desc)
+    k, r = I.make_problem(N, 7 + N)
+    logk = np.log(k)
+    z = O.no_forward(P, desc, r, logk)
+    want = _no_by_full_grid_fft(P, desc, r, logk)
+    assert rel(z, want) < 1e-12
+    assert np.max(np.abs(z - want)) <= 1e-12 * np.max(np.abs(want))
+
+
+@pytest.mark.parametrize("slip", ["mixing transposed", "conjugated weights", "x1 slots reversed",
+                                  "grid axes swapped"])
+def test_full_grid_fft_statement_rejects_planted_slips(monkeypatch, slip):
+    """The pin above fails when a plausible slip is planted in the oracle: the mixing's
+    input/output indices exchanged, the spectral weights conjugated, the negative x1 frequencies
+    stored in reverse slot order, or the analysis taken over the grid's axes exchanged."""
+    mix, kx, ana = O.mode_mix, O.kx_frequencies, O.analysis
+    if slip == "mixing transposed":
+        monkeypatch.setattr(O, "mode_mix", lambda c, R: mix(c, np.swapaxes(R, 2, 3)))
+    elif slip == "conjugated weights":
+        monkeypatch.setattr(O, "mode_mix", lambda c, R: mix(c, np.conj(R)))
+    elif slip == "x1 slots reversed":
+        monkeypatch.setattr(O, "kx_frequencies", lambda M: np.concatenate([np.arange(M), -np.arange(1, M + 1)]))
+    else:
+        monkeypatch.setattr(O, "analysis", lambda v, M: ana(np.swapaxes(v, 0, 1), M))
+    with pytest.raises(AssertionError):
+        test_composed_no_with_random_weights_matches_a_full_grid_fft_statement(16, 4, 4, 0)
+
+
 def test_notay_loss_exact_inverse_is_zero_and_zero_output_is_one():
     N = 6
     k, r = I.make_problem(N, 8)
