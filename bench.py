@@ -620,9 +620,9 @@ def main():
     ap.add_argument("--train-instances", type=int, default=512)
     ap.add_argument("--max-iter", type=int, default=400,
                     help="iteration cap (CG needs ~400 on this workload); capped instances are not counted")
-    ap.add_argument("--ref-iters", type=int, default=17,
+    ap.add_argument("--ref-iters", type=int, default=15,
                     help="FCG-NO iterations per oracle solve in the reference arm (the GPU arm measures a mean "
-                         "of 17.2 at m = 5 on this workload)")
+                         "of 14.7 at m = 5 on this workload)")
     ap.add_argument("--cpu-baseline", type=int, default=1)
     ap.add_argument("--transfer", type=int, default=1, help="run the resolution-transfer leg (128..512 grids)")
     ap.add_argument("--large", type=int, default=1, help="run the large-solve leg (1024^2 x 8, 2048^2 x 2, tol 1e-8)")
